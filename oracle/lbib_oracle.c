@@ -1,0 +1,828 @@
+/*
+ * lbib_oracle.c -- plain, slow, FP64 CPU oracle of the LB-IB time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * loads this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header, table or helper with the CUDA
+ * path (the CUDA path lives in paper_1907_00080_gb300/csrc and include/).
+ *
+ * What it computes (one time step n -> n+1, state (f^n, X^n, X^{n-1}, B^n, n)),
+ * in the order below, each step following the paper passage it cites
+ * (Coclite, "Vascular journey and adhesion mechanics of micro-sized carriers in
+ * narrow capillaries", arXiv 1907.00080):
+ *
+ *   1. bond spring forces at X^n                       Eq. adhFor (Sec. 2.2)
+ *   2. inter-membrane repulsion                        Eq. repFor (Sec. 2.2)
+ *   3. stretching                                      Eq. strainFor
+ *   4. bending                                         Eq. bendFor
+ *   5. enclosed-area penalty                           Eq. areaFor
+ *   6. IB weights: 3x3 nearest-node stencil, MLS with  Sec. 2.2 (MLS of Vanella
+ *      a linear basis and Roma 3-point weights            et al.), Sec. 2.3
+ *   7. spreading G = G_body + sum_v phi_v F_v          Sec. 2.2, Eq. ForcingTerm
+ *   8. BGK collide with Guo forcing, pull streaming,   Eqs. BGK, feq,
+ *      half-way bounce-back walls, periodic x            GaussHermite, forcedBGK,
+ *                                                        ForcingTerm; Sec. 3
+ *   9. interpolation U_v = sum_j phi_v(x_j) u(x_j)     Sec. 2.3 (blood cells)
+ *  10. kinematic marker advance (BDF2)                 Eq. kinematicPos
+ *  11. bond rupture then formation at X^{n+1}          Sec. 2.2 (wall-particle)
+ *  12. diagnostics (mass, enclosed area)               Sec. 2.1, Eq. areaFor
+ *
+ * Readings of passages the paper leaves open (all listed in the design notes):
+ *  - Eq. ForcingTerm is read as the standard Guo term
+ *      F_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . G
+ *    and the momentum as rho u = sum_i f_i e_i + G/2 (Sec. 2.2, the "f_lb" in
+ *    the text being the same body force).
+ *  - walls are half-way bounce-back at y = -1/2 and y = NY - 1/2.
+ *  - the MLS weight is the Roma 3-point kernel on the nine nearest nodes; where
+ *    all nine nodes are fluid the MLS shape function equals the Roma weight
+ *    exactly and is taken as such; near walls the out-of-fluid nodes are dropped
+ *    and the 3x3 MLS system is solved.
+ *  - bending: theta is the signed turning angle, n_v the normalised sum of the
+ *    two adjacent outward edge normals; the left neighbour gets l_L/(l_L+l_R).
+ *  - area: shoelace on the vertices, p_ref = 1/3, force split 1/2 + 1/2.
+ *  - repulsion acts for d < d_rep, along the vertex's own inward normal.
+ *  - bond force is along ligand->receptor; bond kinetics are Dembo-type forward
+ *    and reverse probabilities (the paper defers their form to a citation).
+ *  - first step advances with forward Euler (BDF2 needs two past positions).
+ *  - random numbers: Philox4x64-10 (Salmon et al., SC'11), counter
+ *    (step, ligand, receptor, tag), key (seed, instance); u = (x0 >> 11) 2^-53.
+ *
+ * Build:  gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared lbib_oracle.c -lm
+ * (no FMA contraction, so every product and sum is rounded as written).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef __FP_FAST_FMA
+/* contraction is disabled on the command line; nothing here relies on it */
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* D2Q9 lattice, Eq. GaussHermite and the weights that follow it (Sec. 2.1).  */
+/* i = 0: rest; i = 1..4: (cos((i-1)pi/2), sin((i-1)pi/2));                    */
+/* i = 5..8: sqrt(2) (cos((2i-9)pi/4), sin((2i-9)pi/4)).                        */
+/* ------------------------------------------------------------------------- */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double W9[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                             1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+static int opposite(int i) {
+    /* the direction with e_j = -e_i, found by search rather than a table */
+    for (int j = 0; j < 9; ++j)
+        if (EX[j] == -EX[i] && EY[j] == -EY[i]) return j;
+    return -1;
+}
+
+static long imod(long a, long m) {
+    long r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Simulation state                                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int nx, ny;
+    double tau;
+    double gx, gy;    /* uniform body force G_body (Sec. 3 drive)        */
+    int walls;        /* 0: periodic in y too; 1: bounce-back walls in y */
+    double *f;        /* f^n, [9][ny][nx], pre-collision                 */
+    double *rho, *ux, *uy; /* moments of the last collide                */
+    double *Gx, *Gy;  /* force field used by the last collide           */
+    double *ftmp;
+
+    /* membranes (closed rings, CCW) */
+    int nmem, nv;
+    int *mem_off, *mem_n, *mem_kind;
+    double *mem_ks, *mem_kb, *mem_ka, *mem_A0;
+    int *vert_mem;
+    double *x, *y, *xp, *yp;   /* X^n and X^{n-1}, unwrapped */
+    double *fx, *fy;           /* F^n                         */
+    double *l0, *th0;          /* rest length of element v=(v,v+1); rest angle at v */
+    double *wgt;               /* 9 weights per vertex, last step */
+    long *widx;                /* 9 node indices per vertex      */
+    double *Ux, *Uy;           /* interpolated velocity, last step */
+
+    /* ligands (one per listed element) and receptors */
+    int nlig;
+    int *lig_elem;             /* global element id (= first vertex id) */
+    int nrec;
+    double *rx, *ry;
+    int *bond_of_lig, *owner_of_rec;
+    double d_cut, y_eq, sigma, kf_dt, kr0_dt, beta_f, beta_r, d_break;
+    uint64_t seed, instance;
+
+    double d_rep, p_ref;
+    long step;
+} orc_sim;
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its        */
+/* published definition: ten rounds of two 64x64->128 multiplies, a key       */
+/* schedule bumped by the Weyl constants between rounds.                      */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t K0 = 0x9E3779B97F4A7C15ULL, K1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += K0; k1 += K1; }
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ x1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ x3 ^ k1;
+        uint64_t n3 = lo0;
+        x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* uniform draw in [0,1) for bond decision `tag` (0 = formation, 1 = rupture) */
+double orc_uniform(uint64_t seed, uint64_t instance, long step, long lig, long rec, long tag) {
+    uint64_t c[4] = {(uint64_t)step, (uint64_t)lig, (uint64_t)rec, (uint64_t)tag};
+    uint64_t k[2] = {seed, instance};
+    uint64_t o[4];
+    orc_philox4x64_10(c, k, o);
+    return (double)(o[0] >> 11) * (1.0 / 9007199254740992.0); /* 2^-53 */
+}
+
+/* ------------------------------------------------------------------------- */
+/* LB pieces                                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. feq with c_s^2 = 1/3: w_i rho [1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u.u] */
+void orc_equilibrium(double rho, double ux, double uy, double feq[9]) {
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        feq[i] = W9[i] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+/* Eq. ForcingTerm (Guo): (1 - 1/(2 tau)) w_i [(e_i - u)/c_s^2 + (e_i.u) e_i / c_s^4] . G */
+void orc_guo_source(double tau, double ux, double uy, double gx, double gy, double F[9]) {
+    double pre = 1.0 - 1.0 / (2.0 * tau);
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        double cx = 3.0 * (EX[i] - ux) + 9.0 * eu * EX[i];
+        double cy = 3.0 * (EY[i] - uy) + 9.0 * eu * EY[i];
+        F[i] = pre * W9[i] * (cx * gx + cy * gy);
+    }
+}
+
+/* moments with the Guo half-force correction (Sec. 2.1, Sec. 2.2):
+ * rho = sum f_i ; rho u = sum f_i e_i + G/2 */
+static void moments_at(const double *f, long N, long node, double gx, double gy,
+                       double *rho, double *ux, double *uy) {
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        double fi = f[i * N + node];
+        r += fi;
+        jx += fi * EX[i];
+        jy += fi * EY[i];
+    }
+    jx += 0.5 * gx;
+    jy += 0.5 * gy;
+    *rho = r;
+    *ux = jx / r;
+    *uy = jy / r;
+}
+
+/* streaming of a post-collision field fstar into fout (Eq. BGK left-hand side):
+ * f_i(x, t+1) = f*_i(x - e_i); periodic in x; in y periodic (walls = 0) or
+ * half-way bounce-back f_i(x, t+1) = f*_opp(i)(x) when x - e_i is a wall. */
+void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
+    long nx = s->nx, ny = s->ny, N = nx * ny;
+    for (int i = 0; i < 9; ++i) {
+        int o = opposite(i);
+        for (long y = 0; y < ny; ++y) {
+            for (long x = 0; x < nx; ++x) {
+                long sy = y - EY[i];
+                long sx = imod(x - EX[i], nx);
+                double v;
+                if (s->walls && (sy < 0 || sy >= ny)) {
+                    v = fstar[o * N + y * nx + x];
+                } else {
+                    sy = imod(sy, ny);
+                    v = fstar[i * N + sy * nx + sx];
+                }
+                fout[i * N + y * nx + x] = v;
+            }
+        }
+    }
+}
+
+void orc_moments(const orc_sim *s, const double *f, const double *Gx, const double *Gy,
+                 double *rho, double *ux, double *uy) {
+    long N = (long)s->nx * s->ny;
+    for (long n = 0; n < N; ++n)
+        moments_at(f, N, n, Gx ? Gx[n] : s->gx, Gy ? Gy[n] : s->gy, &rho[n], &ux[n], &uy[n]);
+}
+
+/* Eq. forcedBGK with Delta t = 1, then streaming; stores rho, u */
+static void collide_and_stream(orc_sim *s) {
+    long N = (long)s->nx * s->ny;
+    double feq[9], F[9];
+    for (long n = 0; n < N; ++n) {
+        double rho, ux, uy;
+        double gx = s->Gx[n], gy = s->Gy[n];
+        moments_at(s->f, N, n, gx, gy, &rho, &ux, &uy);
+        s->rho[n] = rho; s->ux[n] = ux; s->uy[n] = uy;
+        orc_equilibrium(rho, ux, uy, feq);
+        orc_guo_source(s->tau, ux, uy, gx, gy, F);
+        for (int i = 0; i < 9; ++i) {
+            double fi = s->f[i * N + n];
+            s->ftmp[i * N + n] = fi - (fi - feq[i]) / s->tau + F[i];
+        }
+    }
+    orc_stream(s, s->ftmp, s->f);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Immersed boundary: Roma kernel, MLS shape functions, interp and spread     */
+/* ------------------------------------------------------------------------- */
+
+/* Roma, Peskin & Berger (1999) three-point regularised delta */
+double orc_roma(double r) {
+    double a = fabs(r);
+    if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) / 3.0;
+    if (a <= 1.5) {
+        double b = 1.0 - a;
+        return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * b * b)) / 6.0;
+    }
+    return 0.0;
+}
+
+/* Shape functions of one Lagrangian point (Sec. 2.2 MLS exchange; Sec. 2.3
+ * nine Eulerian points).  Nodes are (i0+a, j0+b), a,b in {-1,0,1}, stored
+ * row-major in b then a; idx receives the linear node index (-1 if dropped). */
+void orc_ib_weights(const orc_sim *s, double px, double py, double w[9], long idx[9]) {
+    long i0 = (long)floor(px + 0.5), j0 = (long)floor(py + 0.5);
+    double Wr[9], rx[9], ry[9];
+    int nvalid = 0;
+    for (int b = -1; b <= 1; ++b) {
+        for (int a = -1; a <= 1; ++a) {
+            int k = (b + 1) * 3 + (a + 1);
+            long i = i0 + a, j = j0 + b;
+            rx[k] = (double)i - px;
+            ry[k] = (double)j - py;
+            int inside = s->walls ? (j >= 0 && j < s->ny) : 1;
+            if (inside) {
+                Wr[k] = orc_roma(rx[k]) * orc_roma(ry[k]);
+                idx[k] = imod(j, s->ny) * s->nx + imod(i, s->nx);
+                ++nvalid;
+            } else {
+                Wr[k] = 0.0;
+                idx[k] = -1;
+            }
+        }
+    }
+    if (nvalid == 9) {
+        /* full stencil: the MLS system is diag(1, ., .) and phi_j = W_j */
+        for (int k = 0; k < 9; ++k) w[k] = Wr[k];
+        return;
+    }
+    /* MLS with basis p = [1, rx, ry]: A = sum W p p^T, phi_j = W_j p_j^T A^{-1} e_1 */
+    double A[3][3] = {{0}};
+    double sumW = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        double p[3] = {1.0, rx[k], ry[k]};
+        sumW += Wr[k];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[r][c] += Wr[k] * p[r] * p[c];
+    }
+    /* first column of the inverse by cofactors: c = A^{-1} e_1 */
+    double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    double c10 = -(A[1][0] * A[2][2] - A[1][2] * A[2][0]);
+    double c20 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    double det = A[0][0] * c00 + A[0][1] * c10 + A[0][2] * c20;
+    if (det > 1e-10) {
+        double cv[3] = {c00 / det, c10 / det, c20 / det};
+        for (int k = 0; k < 9; ++k)
+            w[k] = Wr[k] * (cv[0] + cv[1] * rx[k] + cv[2] * ry[k]);
+    } else if (sumW > 0.0) {
+        /* degenerate support (point outside the fluid): normalised weights */
+        for (int k = 0; k < 9; ++k) w[k] = Wr[k] / sumW;
+    } else {
+        for (int k = 0; k < 9; ++k) w[k] = 0.0;
+    }
+}
+
+/* interpolation of a node field (ux, uy) to points (Sec. 2.3) */
+void orc_interp(const orc_sim *s, const double *ux, const double *uy, int np,
+                const double *px, const double *py, double *Ux, double *Uy) {
+    for (int v = 0; v < np; ++v) {
+        double w[9];
+        long idx[9];
+        orc_ib_weights(s, px[v], py[v], w, idx);
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            if (idx[k] < 0) continue;
+            a += w[k] * ux[idx[k]];
+            b += w[k] * uy[idx[k]];
+        }
+        Ux[v] = a;
+        Uy[v] = b;
+    }
+}
+
+/* spreading of point forces with the same shape functions (adds into Gx, Gy) */
+void orc_spread(const orc_sim *s, int np, const double *px, const double *py,
+                const double *Fx, const double *Fy, double *Gx, double *Gy) {
+    for (int v = 0; v < np; ++v) {
+        double w[9];
+        long idx[9];
+        orc_ib_weights(s, px[v], py[v], w, idx);
+        for (int k = 0; k < 9; ++k) {
+            if (idx[k] < 0) continue;
+            Gx[idx[k]] += w[k] * Fx[v];
+            Gy[idx[k]] += w[k] * Fy[v];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Membrane mechanics on one closed ring (vertex v joins v+1 mod n)           */
+/* ------------------------------------------------------------------------- */
+
+/* enclosed area by the shoelace formula, taken about vertex 0 (Eq. areaFor's
+ * Green's-theorem area of the polygon) */
+double orc_ring_area(int n, const double *x, const double *y) {
+    double s = 0.0;
+    double xr = x[0], yr = y[0];
+    for (int v = 0; v < n; ++v) {
+        int w = (v + 1) % n;
+        s += (x[v] - xr) * (y[w] - yr) - (x[w] - xr) * (y[v] - yr);
+    }
+    return 0.5 * s;
+}
+
+/* signed turning angle at v and the vertex outward normal */
+static void vertex_geometry(int n, const double *x, const double *y, int v,
+                            double *theta, double *nvx, double *nvy,
+                            double *lL, double *lR) {
+    int L = (v + n - 1) % n, R = (v + 1) % n;
+    double eLx = x[v] - x[L], eLy = y[v] - y[L];
+    double eRx = x[R] - x[v], eRy = y[R] - y[v];
+    double a = sqrt(eLx * eLx + eLy * eLy);
+    double b = sqrt(eRx * eRx + eRy * eRy);
+    double cr = eLx * eRy - eLy * eRx;
+    double dt = eLx * eRx + eLy * eRy;
+    *theta = atan2(cr, dt);
+    /* outward edge normal of a CCW ring: (e_y, -e_x)/|e| */
+    double nx_ = eLy / a + eRy / b;
+    double ny_ = -eLx / a - eRx / b;
+    double nn = sqrt(nx_ * nx_ + ny_ * ny_);
+    *nvx = nx_ / nn;
+    *nvy = ny_ / nn;
+    *lL = a;
+    *lR = b;
+}
+
+/* rest state: element lengths, vertex angles and area (stress-free shape) */
+void orc_ring_rest(int n, const double *x, const double *y, double *l0, double *th0, double *A0) {
+    for (int v = 0; v < n; ++v) {
+        int w = (v + 1) % n;
+        double dx = x[v] - x[w], dy = y[v] - y[w];
+        l0[v] = sqrt(dx * dx + dy * dy);
+        double th, a, b, c, d;
+        vertex_geometry(n, x, y, v, &th, &a, &b, &c, &d);
+        th0[v] = th;
+    }
+    *A0 = orc_ring_area(n, x, y);
+}
+
+/* internal forces of one ring; `which` bit 1 stretch, 2 bend, 4 area.
+ * Adds into fx, fy. */
+void orc_ring_forces(int n, const double *x, const double *y, const double *l0,
+                     const double *th0, double A0, double ks, double kb, double ka,
+                     double p_ref, int which, double *fx, double *fy) {
+    if (which & 1) {
+        /* Eq. strainFor: F_1 = -k_s (l - l_0) r_12 / l, F_2 = -k_s (l - l_0) r_21 / l */
+        for (int v = 0; v < n; ++v) {
+            int w = (v + 1) % n;
+            double r12x = x[v] - x[w], r12y = y[v] - y[w];
+            double l = sqrt(r12x * r12x + r12y * r12y);
+            double c = -ks * (l - l0[v]) / l;
+            fx[v] += c * r12x;
+            fy[v] += c * r12y;
+            fx[w] -= c * r12x;
+            fy[w] -= c * r12y;
+        }
+    }
+    if (which & 2) {
+        /* Eq. bendFor */
+        for (int v = 0; v < n; ++v) {
+            int L = (v + n - 1) % n, R = (v + 1) % n;
+            double th, nvx, nvy, lL, lR;
+            vertex_geometry(n, x, y, v, &th, &nvx, &nvy, &lL, &lR);
+            double m = kb * (th - th0[v]);
+            double sL = lL / (lL + lR), sR = lR / (lL + lR);
+            fx[L] += m * sL * nvx;
+            fy[L] += m * sL * nvy;
+            fx[v] -= m * nvx;
+            fy[v] -= m * nvy;
+            fx[R] += m * sR * nvx;
+            fy[R] += m * sR * nvy;
+        }
+    }
+    if (which & 4) {
+        /* Eq. areaFor: F_l = -k_a (1 - A/A_0) p_ref n_l^- l_l, half to each end */
+        double A = orc_ring_area(n, x, y);
+        double c = -ka * (1.0 - A / A0) * p_ref;
+        for (int v = 0; v < n; ++v) {
+            int w = (v + 1) % n;
+            double ex = x[w] - x[v], ey = y[w] - y[v];
+            /* inward unit normal times the element length: (-e_y, e_x) */
+            double Fx = c * (-ey), Fy = c * ex;
+            fx[v] += 0.5 * Fx;
+            fy[v] += 0.5 * Fy;
+            fx[w] += 0.5 * Fx;
+            fy[w] += 0.5 * Fy;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Simulation object                                                          */
+/* ------------------------------------------------------------------------- */
+
+orc_sim *orc_create(int nx, int ny, double tau, double gx, double gy, int walls) {
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    long N = (long)nx * ny;
+    s->nx = nx; s->ny = ny; s->tau = tau; s->gx = gx; s->gy = gy; s->walls = walls;
+    s->f = (double *)calloc(9 * N, sizeof(double));
+    s->ftmp = (double *)calloc(9 * N, sizeof(double));
+    s->rho = (double *)calloc(N, sizeof(double));
+    s->ux = (double *)calloc(N, sizeof(double));
+    s->uy = (double *)calloc(N, sizeof(double));
+    s->Gx = (double *)calloc(N, sizeof(double));
+    s->Gy = (double *)calloc(N, sizeof(double));
+    for (int i = 0; i < 9; ++i)
+        for (long n = 0; n < N; ++n) s->f[i * N + n] = W9[i];
+    s->d_rep = 2.0;
+    s->p_ref = 1.0 / 3.0;
+    s->d_cut = 1.5; s->y_eq = 0.75; s->d_break = 3.0;
+    return s;
+}
+
+void orc_destroy(orc_sim *s) {
+    if (!s) return;
+    free(s->f); free(s->ftmp); free(s->rho); free(s->ux); free(s->uy);
+    free(s->Gx); free(s->Gy);
+    free(s->mem_off); free(s->mem_n); free(s->mem_kind); free(s->mem_ks); free(s->mem_kb);
+    free(s->mem_ka); free(s->mem_A0); free(s->vert_mem);
+    free(s->x); free(s->y); free(s->xp); free(s->yp); free(s->fx); free(s->fy);
+    free(s->l0); free(s->th0); free(s->wgt); free(s->widx); free(s->Ux); free(s->Uy);
+    free(s->lig_elem); free(s->rx); free(s->ry); free(s->bond_of_lig); free(s->owner_of_rec);
+    free(s);
+}
+
+void orc_set_populations(orc_sim *s, const double *f) {
+    memcpy(s->f, f, sizeof(double) * 9 * (size_t)s->nx * s->ny);
+}
+void orc_get_populations(const orc_sim *s, double *f) {
+    memcpy(f, s->f, sizeof(double) * 9 * (size_t)s->nx * s->ny);
+}
+void orc_get_fields(const orc_sim *s, double *rho, double *ux, double *uy) {
+    size_t N = (size_t)s->nx * s->ny;
+    memcpy(rho, s->rho, N * sizeof(double));
+    memcpy(ux, s->ux, N * sizeof(double));
+    memcpy(uy, s->uy, N * sizeof(double));
+}
+void orc_get_force_field(const orc_sim *s, double *gx, double *gy) {
+    size_t N = (size_t)s->nx * s->ny;
+    memcpy(gx, s->Gx, N * sizeof(double));
+    memcpy(gy, s->Gy, N * sizeof(double));
+}
+
+/* Poiseuille start (Sec. 3 drive; tau = 1 discrete fixed point): post-collision
+ * f* = feq(1, u(y)) + F(u(y), G) with u(y) = 3 G (y + 1/2)(NY - 1/2 - y) + G/4,
+ * streamed once to give the pre-collision state f^0. */
+void orc_init_poiseuille(orc_sim *s) {
+    long nx = s->nx, ny = s->ny, N = nx * ny;
+    double feq[9], F[9];
+    double G = s->gx;
+    double nu = (s->tau - 0.5) / 3.0;
+    for (long y = 0; y < ny; ++y) {
+        double yy = (double)y;
+        double u = G / (2.0 * nu) * (yy + 0.5) * ((double)ny - 0.5 - yy) + 0.25 * G;
+        orc_equilibrium(1.0, u, 0.0, feq);
+        orc_guo_source(s->tau, u, 0.0, s->gx, s->gy, F);
+        for (long x = 0; x < nx; ++x)
+            for (int i = 0; i < 9; ++i) s->ftmp[i * N + y * nx + x] = feq[i] + F[i];
+    }
+    orc_stream(s, s->ftmp, s->f);
+}
+
+static void *grow(void *p, size_t n, size_t sz) { return realloc(p, n * sz); }
+
+/* add a closed CCW ring of n vertices, rest shape = given positions.
+ * kind 0: kinematic (Eq. kinematicPos); kind 1: velocities projected on a rigid
+ * motion before the advance. ligand_elems are local element ids. */
+int orc_add_membrane(orc_sim *s, const double *xy, int n, double ks, double kb, double ka,
+                     int kind, const int *ligand_elems, int nlig) {
+    int m = s->nmem++;
+    int off = s->nv;
+    int nv = s->nv + n;
+    s->mem_off = grow(s->mem_off, s->nmem, sizeof(int));
+    s->mem_n = grow(s->mem_n, s->nmem, sizeof(int));
+    s->mem_kind = grow(s->mem_kind, s->nmem, sizeof(int));
+    s->mem_ks = grow(s->mem_ks, s->nmem, sizeof(double));
+    s->mem_kb = grow(s->mem_kb, s->nmem, sizeof(double));
+    s->mem_ka = grow(s->mem_ka, s->nmem, sizeof(double));
+    s->mem_A0 = grow(s->mem_A0, s->nmem, sizeof(double));
+    s->vert_mem = grow(s->vert_mem, nv, sizeof(int));
+    s->x = grow(s->x, nv, sizeof(double)); s->y = grow(s->y, nv, sizeof(double));
+    s->xp = grow(s->xp, nv, sizeof(double)); s->yp = grow(s->yp, nv, sizeof(double));
+    s->fx = grow(s->fx, nv, sizeof(double)); s->fy = grow(s->fy, nv, sizeof(double));
+    s->l0 = grow(s->l0, nv, sizeof(double)); s->th0 = grow(s->th0, nv, sizeof(double));
+    s->Ux = grow(s->Ux, nv, sizeof(double)); s->Uy = grow(s->Uy, nv, sizeof(double));
+    s->wgt = grow(s->wgt, (size_t)nv * 9, sizeof(double));
+    s->widx = grow(s->widx, (size_t)nv * 9, sizeof(long));
+    s->mem_off[m] = off; s->mem_n[m] = n; s->mem_kind[m] = kind;
+    s->mem_ks[m] = ks; s->mem_kb[m] = kb; s->mem_ka[m] = ka;
+    for (int v = 0; v < n; ++v) {
+        s->x[off + v] = xy[2 * v];
+        s->y[off + v] = xy[2 * v + 1];
+        s->xp[off + v] = xy[2 * v];
+        s->yp[off + v] = xy[2 * v + 1];
+        s->fx[off + v] = 0.0; s->fy[off + v] = 0.0;
+        s->Ux[off + v] = 0.0; s->Uy[off + v] = 0.0;
+        s->vert_mem[off + v] = m;
+    }
+    orc_ring_rest(n, s->x + off, s->y + off, s->l0 + off, s->th0 + off, &s->mem_A0[m]);
+    s->nv = nv;
+    if (nlig > 0) {
+        s->lig_elem = grow(s->lig_elem, s->nlig + nlig, sizeof(int));
+        s->bond_of_lig = grow(s->bond_of_lig, s->nlig + nlig, sizeof(int));
+        for (int k = 0; k < nlig; ++k) {
+            s->lig_elem[s->nlig + k] = off + ligand_elems[k];
+            s->bond_of_lig[s->nlig + k] = -1;
+        }
+        s->nlig += nlig;
+    }
+    return m;
+}
+
+void orc_set_receptors(orc_sim *s, const double *xy, int n, double d_cut, double y_eq,
+                       double sigma, double kf_dt, double kr0_dt, double beta_f,
+                       double beta_r, double d_break, uint64_t seed, uint64_t instance) {
+    s->nrec = n;
+    s->rx = grow(s->rx, n > 0 ? n : 1, sizeof(double));
+    s->ry = grow(s->ry, n > 0 ? n : 1, sizeof(double));
+    s->owner_of_rec = grow(s->owner_of_rec, n > 0 ? n : 1, sizeof(int));
+    for (int r = 0; r < n; ++r) {
+        s->rx[r] = xy[2 * r];
+        s->ry[r] = xy[2 * r + 1];
+        s->owner_of_rec[r] = -1;
+    }
+    s->d_cut = d_cut; s->y_eq = y_eq; s->sigma = sigma;
+    s->kf_dt = kf_dt; s->kr0_dt = kr0_dt; s->beta_f = beta_f; s->beta_r = beta_r;
+    s->d_break = d_break; s->seed = seed; s->instance = instance;
+}
+
+void orc_set_repulsion(orc_sim *s, double d_rep) { s->d_rep = d_rep; }
+
+/* x distance with the periodic minimum image (and y when y is periodic) */
+static void min_image(const orc_sim *s, double *dx, double *dy) {
+    *dx -= s->nx * floor(*dx / s->nx + 0.5);
+    if (!s->walls) *dy -= s->ny * floor(*dy / s->ny + 0.5);
+}
+
+/* ligand point: centroid of its element (Sec. 2.2, wall-particle interaction) */
+static void ligand_point(const orc_sim *s, int l, double *cx, double *cy) {
+    int a = s->lig_elem[l];
+    int m = s->vert_mem[a];
+    int b = s->mem_off[m] + (a - s->mem_off[m] + 1) % s->mem_n[m];
+    *cx = 0.5 * (s->x[a] + s->x[b]);
+    *cy = 0.5 * (s->y[a] + s->y[b]);
+}
+
+static double ligand_receptor_dist(const orc_sim *s, int l, int r, double *ddx, double *ddy) {
+    double cx, cy;
+    ligand_point(s, l, &cx, &cy);
+    double dx = s->rx[r] - cx, dy = s->ry[r] - cy;
+    min_image(s, &dx, &dy);
+    if (ddx) *ddx = dx;
+    if (ddy) *ddy = dy;
+    return sqrt(dx * dx + dy * dy);
+}
+
+/* forward (formation) and reverse (rupture) probabilities per step */
+double orc_p_form(const orc_sim *s, double d) {
+    double z = (d - s->y_eq) / s->y_eq;
+    return 1.0 - exp(-s->kf_dt * exp(-s->beta_f * z * z));
+}
+double orc_p_rupture(const orc_sim *s, double d) {
+    double z = (d - s->y_eq) / s->y_eq;
+    return 1.0 - exp(-s->kr0_dt * exp(s->beta_r * z * z));
+}
+
+/* steps 1-5: all Lagrangian forces at X^n */
+void orc_compute_forces(orc_sim *s) {
+    int nv = s->nv;
+    for (int v = 0; v < nv; ++v) { s->fx[v] = 0.0; s->fy[v] = 0.0; }
+    /* 1. bonds, Eq. adhFor, along ligand->receptor, half to each end vertex */
+    for (int l = 0; l < s->nlig; ++l) {
+        int r = s->bond_of_lig[l];
+        if (r < 0) continue;
+        double dx, dy;
+        double d = ligand_receptor_dist(s, l, r, &dx, &dy);
+        double c = s->sigma * (d - s->y_eq) / d;
+        int a = s->lig_elem[l];
+        int m = s->vert_mem[a];
+        int b = s->mem_off[m] + (a - s->mem_off[m] + 1) % s->mem_n[m];
+        s->fx[a] += 0.5 * c * dx; s->fy[a] += 0.5 * c * dy;
+        s->fx[b] += 0.5 * c * dx; s->fy[b] += 0.5 * c * dy;
+    }
+    /* 2. repulsion, Eq. repFor (Delta x = 1), along the vertex's inward normal */
+    if (s->nmem > 1) {
+        const double c0 = 1e-4 / (8.0 * sqrt(2.0));
+        for (int a = 0; a < nv; ++a) {
+            int ma = s->vert_mem[a];
+            int off = s->mem_off[ma], n = s->mem_n[ma];
+            double th, nvx, nvy, lL, lR;
+            vertex_geometry(n, s->x + off, s->y + off, a - off, &th, &nvx, &nvy, &lL, &lR);
+            for (int b = 0; b < nv; ++b) {
+                if (s->vert_mem[b] == ma) continue;
+                double dx = s->x[a] - s->x[b], dy = s->y[a] - s->y[b];
+                min_image(s, &dx, &dy);
+                double d = sqrt(dx * dx + dy * dy);
+                if (d < s->d_rep) {
+                    double mag = c0 * sqrt(1.0 / (d * d * d * d * d));
+                    s->fx[a] -= mag * nvx;
+                    s->fy[a] -= mag * nvy;
+                }
+            }
+        }
+    }
+    /* 3-5. stretch, bend, area per ring */
+    for (int m = 0; m < s->nmem; ++m) {
+        int off = s->mem_off[m], n = s->mem_n[m];
+        orc_ring_forces(n, s->x + off, s->y + off, s->l0 + off, s->th0 + off, s->mem_A0[m],
+                        s->mem_ks[m], s->mem_kb[m], s->mem_ka[m], s->p_ref, 7,
+                        s->fx + off, s->fy + off);
+    }
+}
+
+/* step 11: rupture, then formation (lowest ligand id wins a receptor) */
+void orc_bonds_update(orc_sim *s, long step) {
+    int *was_free = (int *)malloc(sizeof(int) * (s->nrec > 0 ? s->nrec : 1));
+    int *claimed = (int *)malloc(sizeof(int) * (s->nrec > 0 ? s->nrec : 1));
+    for (int r = 0; r < s->nrec; ++r) {
+        was_free[r] = s->owner_of_rec[r] < 0;
+        claimed[r] = 0;
+    }
+    for (int l = 0; l < s->nlig; ++l) {
+        int r = s->bond_of_lig[l];
+        if (r < 0) continue;
+        double d = ligand_receptor_dist(s, l, r, NULL, NULL);
+        int rupture = d >= s->d_break;
+        if (!rupture) rupture = orc_uniform(s->seed, s->instance, step, l, r, 1) < orc_p_rupture(s, d);
+        if (rupture) {
+            s->bond_of_lig[l] = -1;
+            s->owner_of_rec[r] = -1;
+        }
+    }
+    for (int l = 0; l < s->nlig; ++l) {
+        if (s->bond_of_lig[l] >= 0) continue;
+        for (int r = 0; r < s->nrec; ++r) {
+            if (!was_free[r]) continue;
+            double d = ligand_receptor_dist(s, l, r, NULL, NULL);
+            if (!(d < s->d_cut)) continue;
+            if (orc_uniform(s->seed, s->instance, step, l, r, 0) < orc_p_form(s, d)) {
+                /* first accepted receptor is this ligand's candidate */
+                if (!claimed[r]) {
+                    claimed[r] = 1;
+                    s->bond_of_lig[l] = r;
+                    s->owner_of_rec[r] = l;
+                }
+                break;
+            }
+        }
+    }
+    free(was_free);
+    free(claimed);
+}
+
+/* one full step n -> n+1 */
+static void step_once(orc_sim *s) {
+    long N = (long)s->nx * s->ny;
+    int nv = s->nv;
+    orc_compute_forces(s);
+    /* 6. weights at X^n */
+    for (int v = 0; v < nv; ++v) orc_ib_weights(s, s->x[v], s->y[v], s->wgt + 9 * v, s->widx + 9 * v);
+    /* 7. spread */
+    for (long n = 0; n < N; ++n) { s->Gx[n] = s->gx; s->Gy[n] = s->gy; }
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < 9; ++k) {
+            long j = s->widx[9 * v + k];
+            if (j < 0) continue;
+            s->Gx[j] += s->wgt[9 * v + k] * s->fx[v];
+            s->Gy[j] += s->wgt[9 * v + k] * s->fy[v];
+        }
+    /* 8. collide + stream */
+    collide_and_stream(s);
+    /* 9. interpolate u^n at X^n */
+    for (int v = 0; v < nv; ++v) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            long j = s->widx[9 * v + k];
+            if (j < 0) continue;
+            a += s->wgt[9 * v + k] * s->ux[j];
+            b += s->wgt[9 * v + k] * s->uy[j];
+        }
+        s->Ux[v] = a;
+        s->Uy[v] = b;
+    }
+    /* 10. advance (rigid projection first for kind 1) */
+    for (int m = 0; m < s->nmem; ++m) {
+        int off = s->mem_off[m], n = s->mem_n[m];
+        if (s->mem_kind[m] == 1) {
+            double xc = 0, yc = 0, uc = 0, vc = 0;
+            for (int v = off; v < off + n; ++v) { xc += s->x[v]; yc += s->y[v]; uc += s->Ux[v]; vc += s->Uy[v]; }
+            xc /= n; yc /= n; uc /= n; vc /= n;
+            double num = 0, den = 0;
+            for (int v = off; v < off + n; ++v) {
+                double rx = s->x[v] - xc, ry = s->y[v] - yc;
+                num += rx * (s->Uy[v] - vc) - ry * (s->Ux[v] - uc);
+                den += rx * rx + ry * ry;
+            }
+            double om = num / den;
+            for (int v = off; v < off + n; ++v) {
+                double rx = s->x[v] - xc, ry = s->y[v] - yc;
+                s->Ux[v] = uc - om * ry;
+                s->Uy[v] = vc + om * rx;
+            }
+        }
+        for (int v = off; v < off + n; ++v) {
+            double xn, yn;
+            if (s->step == 0) {
+                xn = s->x[v] + s->Ux[v];
+                yn = s->y[v] + s->Uy[v];
+            } else {
+                xn = (2.0 / 3.0) * (2.0 * s->x[v] - 0.5 * s->xp[v] + s->Ux[v]);
+                yn = (2.0 / 3.0) * (2.0 * s->y[v] - 0.5 * s->yp[v] + s->Uy[v]);
+            }
+            s->xp[v] = s->x[v]; s->yp[v] = s->y[v];
+            s->x[v] = xn; s->y[v] = yn;
+        }
+    }
+    /* 11. bonds at X^{n+1}, counter n */
+    if (s->nlig > 0 && s->nrec > 0) orc_bonds_update(s, s->step);
+    s->step += 1;
+}
+
+void orc_step(orc_sim *s, long nsteps) {
+    for (long k = 0; k < nsteps; ++k) step_once(s);
+}
+
+/* accessors */
+int orc_num_vertices(const orc_sim *s) { return s->nv; }
+int orc_num_ligands(const orc_sim *s) { return s->nlig; }
+long orc_get_step(const orc_sim *s) { return s->step; }
+void orc_get_markers(const orc_sim *s, double *xy) {
+    for (int v = 0; v < s->nv; ++v) { xy[2 * v] = s->x[v]; xy[2 * v + 1] = s->y[v]; }
+}
+void orc_get_prev_markers(const orc_sim *s, double *xy) {
+    for (int v = 0; v < s->nv; ++v) { xy[2 * v] = s->xp[v]; xy[2 * v + 1] = s->yp[v]; }
+}
+void orc_set_markers(orc_sim *s, const double *xy, const double *xy_prev) {
+    for (int v = 0; v < s->nv; ++v) {
+        s->x[v] = xy[2 * v]; s->y[v] = xy[2 * v + 1];
+        if (xy_prev) { s->xp[v] = xy_prev[2 * v]; s->yp[v] = xy_prev[2 * v + 1]; }
+    }
+}
+void orc_get_forces(const orc_sim *s, double *fxy) {
+    for (int v = 0; v < s->nv; ++v) { fxy[2 * v] = s->fx[v]; fxy[2 * v + 1] = s->fy[v]; }
+}
+void orc_get_marker_velocity(const orc_sim *s, double *uxy) {
+    for (int v = 0; v < s->nv; ++v) { uxy[2 * v] = s->Ux[v]; uxy[2 * v + 1] = s->Uy[v]; }
+}
+void orc_get_bonds(const orc_sim *s, int *bond_of_lig) {
+    for (int l = 0; l < s->nlig; ++l) bond_of_lig[l] = s->bond_of_lig[l];
+}
+void orc_set_bond(orc_sim *s, int l, int r) {
+    if (s->bond_of_lig[l] >= 0) s->owner_of_rec[s->bond_of_lig[l]] = -1;
+    s->bond_of_lig[l] = r;
+    if (r >= 0) s->owner_of_rec[r] = l;
+}
+double orc_mass(const orc_sim *s) {
+    long N = (long)s->nx * s->ny;
+    double m = 0.0;
+    for (long k = 0; k < 9 * N; ++k) m += s->f[k];
+    return m;
+}
+double orc_membrane_area(const orc_sim *s, int m) {
+    return orc_ring_area(s->mem_n[m], s->x + s->mem_off[m], s->y + s->mem_off[m]);
+}
+double orc_membrane_rest_area(const orc_sim *s, int m) { return s->mem_A0[m]; }

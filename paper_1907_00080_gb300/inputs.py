@@ -1,0 +1,274 @@
+"""Seeded synthetic workloads for the LB-IB capillary problem.
+
+This module only generates inputs (geometry, parameters in lattice units,
+receptor arrays); it contains none of the time-step arithmetic, so the CUDA
+path and the CPU oracle can both be fed from it without sharing any of the
+method's code.  It imports nothing else from this package.
+
+Paper set-up it follows (Coclite, arXiv 1907.00080, Sec. 3):
+  * channel of height H, periodic in x, no-slip walls in y, Poiseuille drive
+    with Re = u_max H / nu = 1e-2 and tau = 1 (nu = 1/6 lattice units);
+  * red-cell rest contour, Eq. rbcShape;
+  * capillary number Ca = rho nu u_max / k_s; bending E_b = k_b / (k_s r^2);
+  * bond strength sigma in units rho nu^2 / H; ligand density rho_L = 0.5.
+All randomness comes from numpy PCG64 with an explicit seed.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+NU_TAU1 = 1.0 / 6.0  # kinematic viscosity at tau = 1 in lattice units
+
+# Bond-kinetics defaults (forward/reverse probabilities per step).  The paper
+# gives only k_f / k_r0 = 8.5e3 (Sec. 3); the rest is this library's choice.
+DEFAULT_BONDS = dict(d_cut=1.5, y_eq=0.75, kf_dt=1e-2, kr0_dt=1e-2 / 8.5e3,
+                     beta_f=0.5, beta_r=2.0, d_break=3.0)
+STRESS_BONDS = dict(d_cut=1.5, y_eq=0.75, kf_dt=0.05, kr0_dt=0.01,
+                    beta_f=0.5, beta_r=2.0, d_break=3.0)
+
+
+@dataclass
+class Membrane:
+    xy: np.ndarray            # (n, 2) CCW rest shape, unwrapped x
+    ks: float
+    kb: float
+    ka: float
+    kind: int = 0             # 0 kinematic, 1 rigid-projected
+    ligands: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    tau: float = 1.0
+    body_force: tuple = (0.0, 0.0)
+    walls: int = 1
+    init: str = "poiseuille"
+    precision: str = "f32"
+    membranes: List[Membrane] = field(default_factory=list)
+    receptors: Optional[np.ndarray] = None    # (R, 2)
+    bonds: dict = field(default_factory=lambda: dict(DEFAULT_BONDS))
+    sigma_lu: float = 0.0
+    seed: int = 0
+    instance: int = 0
+    d_rep: float = 2.0
+    steps: int = 1000
+
+    @property
+    def n_vertices(self):
+        return sum(len(m.xy) for m in self.membranes)
+
+    @property
+    def n_ligands(self):
+        return sum(len(m.ligands) for m in self.membranes)
+
+
+# ------------------------------------------------------------ parameter maps
+def body_force_for(u_max: float, ny: int, nu: float = NU_TAU1) -> float:
+    """Uniform body force giving a plane Poiseuille centreline speed u_max in a
+    channel of height H = ny (walls half a node outside the fluid rows)."""
+    return 8.0 * nu * u_max / float(ny) ** 2
+
+
+def u_max_for_re(re: float, ny: int, nu: float = NU_TAU1) -> float:
+    return re * nu / float(ny)
+
+
+def sigma_lattice(sigma: float, ny: int, nu: float = NU_TAU1) -> float:
+    """sigma given in units rho nu^2 / H (Sec. 2.2) -> lattice units."""
+    return sigma * nu * nu / float(ny)
+
+
+def ks_for_ca(ca: float, u_max: float, nu: float = NU_TAU1) -> float:
+    """Ca = rho nu u_max / k_s (Sec. 3)."""
+    return nu * u_max / ca
+
+
+# ------------------------------------------------------------------ shapes
+def circle(cx, cy, r, n, phase=0.5):
+    """n vertices CCW on a circle, vertex k at angle 2 pi (k + phase) / n."""
+    k = np.arange(n, dtype=np.float64)
+    t = 2.0 * np.pi * (k + phase) / n
+    return np.stack([cx + r * np.cos(t), cy + r * np.sin(t)], axis=1)
+
+
+def _rbc_raw(alpha, q):
+    x = alpha * np.sin(q)
+    s = np.sin(q) ** 2
+    y = 0.5 * alpha * (0.207 + 2.003 * s - 1.123 * s * s) * np.cos(q)
+    return x, y
+
+
+def rbc_contour(alpha: float, n: int, dense: int = 20000) -> np.ndarray:
+    """Eq. rbcShape (a = 1, q in [-pi/2, 3pi/2]) resampled uniformly by arc
+    length into n vertices, centred at the origin and oriented CCW."""
+    q = np.linspace(-0.5 * np.pi, 1.5 * np.pi, dense, endpoint=False)
+    x, y = _rbc_raw(alpha, q)
+    pts = np.stack([x, y], axis=1)
+    seg = np.linalg.norm(np.roll(pts, -1, axis=0) - pts, axis=1)
+    s = np.concatenate([[0.0], np.cumsum(seg)])
+    total = s[-1]
+    targets = np.arange(n) * total / n
+    closed = np.concatenate([pts, pts[:1]], axis=0)
+    xs = np.interp(targets, s, closed[:, 0])
+    ys = np.interp(targets, s, closed[:, 1])
+    out = np.stack([xs, ys], axis=1)
+    if _signed_area(out) < 0:
+        out = out[::-1].copy()
+    return out - out.mean(axis=0)
+
+
+def _signed_area(xy):
+    x, y = xy[:, 0], xy[:, 1]
+    return 0.5 * np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y)
+
+
+def _rotate(xy, ang):
+    c, s = math.cos(ang), math.sin(ang)
+    return xy @ np.array([[c, s], [-s, c]])
+
+
+def _point_in_poly(px, py, poly, nx):
+    # ray casting, with x taken at the periodic image closest to the polygon centre
+    cx = poly[:, 0].mean()
+    px = px - nx * math.floor((px - cx) / nx + 0.5)
+    inside = False
+    n = len(poly)
+    for i in range(n):
+        x1, y1 = poly[i]
+        x2, y2 = poly[(i + 1) % n]
+        if (y1 > py) != (y2 > py):
+            xin = x1 + (py - y1) * (x2 - x1) / (y2 - y1)
+            if px < xin:
+                inside = not inside
+    return inside
+
+
+def place_membranes(shapes, nx, ny, rng, gap=2.0, wall_gap=2.0, y_range=None, max_tries=20000):
+    """Random non-overlapping placement (uniform centre, uniform orientation).
+    Vertices keep >= gap from every other membrane (periodic x) and >= wall_gap
+    from the walls (at y = -1/2 and ny - 1/2)."""
+    placed = []
+    for k, shape in enumerate(shapes):
+        ok = False
+        for _ in range(max_tries):
+            ang = rng.uniform(0.0, 2.0 * np.pi)
+            xy = _rotate(shape, ang)
+            ymin, ymax = xy[:, 1].min(), xy[:, 1].max()
+            lo = -0.5 + wall_gap - ymin
+            hi = ny - 0.5 - wall_gap - ymax
+            if y_range is not None:
+                lo, hi = max(lo, y_range[k][0]), min(hi, y_range[k][1])
+            if hi <= lo:
+                continue
+            cx = rng.uniform(0.0, nx)
+            cy = rng.uniform(lo, hi)
+            cand = xy + np.array([cx, cy])
+            bad = False
+            for other in placed:
+                d = cand[:, None, :] - other[None, :, :]
+                d[..., 0] -= nx * np.floor(d[..., 0] / nx + 0.5)
+                if np.min(np.hypot(d[..., 0], d[..., 1])) < gap:
+                    bad = True
+                    break
+                c_o = other.mean(axis=0)
+                c_n = cand.mean(axis=0)
+                if _point_in_poly(c_n[0], c_n[1], other, nx) or _point_in_poly(c_o[0], c_o[1], cand, nx):
+                    bad = True
+                    break
+            if not bad:
+                placed.append(cand)
+                ok = True
+                break
+        if not ok:
+            raise RuntimeError("could not place membrane %d" % k)
+    return placed
+
+
+def wall_receptors(nx, ny, lower=True, upper=True):
+    """One receptor per wall node: (i, -1/2) on the lower wall and
+    (i, ny - 1/2) on the upper wall, lower wall first, ascending i."""
+    out = []
+    i = np.arange(nx, dtype=np.float64)
+    if lower:
+        out.append(np.stack([i, np.full(nx, -0.5)], axis=1))
+    if upper:
+        out.append(np.stack([i, np.full(nx, ny - 0.5)], axis=1))
+    return np.concatenate(out, axis=0) if out else np.zeros((0, 2))
+
+
+# --------------------------------------------------------------- workloads
+def capsule_128x32(precision="f64", bonds="default") -> Workload:
+    """Plain FP64 case: 128x32 channel, u_max = 0.02, one circular capsule of
+    radius 4 with 32 markers, k_s = 0.05, k_b = 0.005, area penalty 0.1, 32
+    ligands, receptors on every lower-wall node, sigma = 1, cutoff 1.5."""
+    nx, ny = 128, 32
+    g = body_force_for(0.02, ny)
+    mem = Membrane(xy=circle(32.0, 4.75, 4.0, 32), ks=0.05, kb=0.005, ka=0.1, kind=0,
+                   ligands=np.arange(32, dtype=np.int32))
+    wl = Workload(name="capsule_128x32", nx=nx, ny=ny, body_force=(g, 0.0), walls=1,
+                  init="poiseuille", precision=precision, membranes=[mem],
+                  receptors=wall_receptors(nx, ny, lower=True, upper=False),
+                  sigma_lu=sigma_lattice(1.0, ny), seed=0, steps=1000)
+    wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
+    return wl
+
+
+def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carriers=4,
+              carrier_radius=8.0, carrier_markers=50, ca_carrier=(0.0, 1e-2), sigma=1.0,
+              re=1e-2, seed=0, precision="f32", steps=200000, name=None,
+              bonds="default", release_y=None) -> Workload:
+    """Coarse capillary: 10x40 um at dx = 62.5 nm is a 160x640 lattice; 8
+    biconcave red cells (8 um major axis -> alpha = 64 lu, 200 markers each),
+    4 carriers of 1 um diameter (radius 8 lu, 50 markers), alternating rigid
+    (Ca = 0, rigid-projected) and soft (Ca = 1e-2) carriers, ligand density
+    0.5 (every other element), receptors on both walls, sigma = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u_max = u_max_for_re(re, ny)
+    g = body_force_for(u_max, ny)
+    ks_rbc = ks_for_ca(1e-2, u_max)
+    rbc = rbc_contour(rbc_alpha, rbc_markers)
+    carrier = circle(0.0, 0.0, carrier_radius, carrier_markers)
+    shapes = [rbc] * n_rbc + [carrier] * n_carriers
+    y_range = None
+    if release_y is not None:
+        y_range = [(-1e9, 1e9)] * n_rbc + [(y - 1e-6, y + 1e-6) for y in release_y]
+    placed = place_membranes(shapes, nx, ny, rng, y_range=y_range)
+    mems = []
+    for k in range(n_rbc):
+        mems.append(Membrane(xy=placed[k], ks=ks_rbc, kb=0.0, ka=1.0, kind=0))
+    lig = np.arange(0, carrier_markers, 2, dtype=np.int32)
+    for c in range(n_carriers):
+        ca = ca_carrier[c % len(ca_carrier)]
+        if ca == 0.0:
+            ks = ks_rbc
+            kind = 1
+        else:
+            ks = ks_for_ca(ca, u_max)
+            kind = 0
+        kb = 0.05 * ks * carrier_radius ** 2
+        mems.append(Membrane(xy=placed[n_rbc + c], ks=ks, kb=kb, ka=1.0, kind=kind, ligands=lig.copy()))
+    wl = Workload(name=name or "capillary_%dx%d" % (nx, ny), nx=nx, ny=ny, body_force=(g, 0.0),
+                  walls=1, init="poiseuille", precision=precision, membranes=mems,
+                  receptors=wall_receptors(nx, ny), sigma_lu=sigma_lattice(sigma, ny),
+                  seed=seed, steps=steps)
+    wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
+    return wl
+
+
+def coarse_capillary_640x160(precision="f32", seed=0, steps=200000) -> Workload:
+    return capillary(precision=precision, seed=seed, steps=steps, name="capillary_640x160")
+
+
+def random_populations(nx, ny, base, seed=0, amp=1e-2):
+    """Random positive populations base_i * (1 + amp * U(-1, 1)) per node; the
+    caller supplies the nine base values (for unit parity tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = np.asarray(base, dtype=np.float64).reshape(9, 1, 1)
+    return base * (1.0 + amp * rng.uniform(-1.0, 1.0, size=(9, ny, nx)))
