@@ -1,0 +1,205 @@
+/*
+ * lbib.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann / immersed-boundary
+ * solver for red cells and adhesive carriers in a capillary.
+ *
+ * Method: Coclite, "Vascular journey and adhesion mechanics of micro-sized
+ * carriers in narrow capillaries", arXiv 1907.00080.  One time step runs, on
+ * the GPU, in this order:
+ *   forces at X^n (bond springs Eq. adhFor, repulsion Eq. repFor, stretching
+ *   Eq. strainFor, bending Eq. bendFor, enclosed area Eq. areaFor) ->
+ *   IB shape functions (MLS with Roma weights on the nine nearest nodes,
+ *   Sec. 2.2 / 2.3) -> spreading of the marker forces into the Guo body force
+ *   (Eq. ForcingTerm) fused into the D2Q9 BGK collide-and-stream (Eqs. BGK,
+ *   feq, GaussHermite, forcedBGK) -> interpolation of u^n to the markers
+ *   (Sec. 2.3) -> kinematic advance (Eq. kinematicPos; forward Euler on the
+ *   first step) -> bond rupture and formation at X^{n+1} (Sec. 2.2,
+ *   wall-particle interaction).
+ *
+ * Units: lattice units throughout (dx = dt = 1, rho_0 = 1).  The lattice has
+ * NX nodes along the periodic x axis and NY fluid rows y = 0..NY-1; with
+ * LBIB_WALLS_Y_BOUNCEBACK the walls sit half a node outside, at y = -1/2 and
+ * y = NY - 1/2 (half-way bounce-back), otherwise y is periodic as well.
+ *
+ * Conventions for every call:
+ *  - every call returns an lbib_status; lbib_last_error() gives a message;
+ *  - inputs are copied, the caller keeps ownership of every pointer it passes;
+ *    the library owns all device state it allocates in lbib_create /
+ *    lbib_add_membrane / lbib_set_receptors and frees it in lbib_destroy;
+ *  - `on_device` = 1 means the pointer is CUDA device memory on the context's
+ *    device, 0 means host memory;
+ *  - work is enqueued on the context's stream; read-backs synchronise it;
+ *  - a context is not thread-safe: one host thread drives it at a time;
+ *  - after LBIB_E_NONFINITE the context is poisoned and lbib_step returns
+ *    LBIB_E_STATE.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbib_ctx lbib_ctx;
+
+typedef enum {
+    LBIB_OK = 0,
+    LBIB_E_INVALID = 1,   /* bad argument (null pointer, size, range)        */
+    LBIB_E_CUDA = 2,      /* a CUDA runtime call failed                       */
+    LBIB_E_OOM = 3,       /* device allocation failed                         */
+    LBIB_E_TIMEOUT = 4,   /* a bounded device-side wait gave up               */
+    LBIB_E_NONFINITE = 5, /* a marker position became NaN/Inf                 */
+    LBIB_E_STATE = 6      /* call not valid in the current state              */
+} lbib_status;
+
+/* Population storage.  All forms store the deviation d_i = f_i - w_i of each
+ * population from its lattice weight (round-off reduction); the 16-bit forms
+ * store d_i * 2^k with k chosen at creation and compute in FP32. */
+typedef enum {
+    LBIB_F64 = 0,
+    LBIB_F32 = 1,
+    LBIB_F32_STORE_F16 = 2,
+    LBIB_F32_STORE_BF16 = 3
+} lbib_precision;
+
+typedef enum {
+    LBIB_WALLS_NONE = 0,          /* periodic in x and y (e.g. shear-wave tests) */
+    LBIB_WALLS_Y_BOUNCEBACK = 1   /* half-way bounce-back walls in y            */
+} lbib_walls;
+
+typedef enum {
+    LBIB_INIT_REST = 0,        /* f_i = w_i (rho = 1, u = 0)                        */
+    LBIB_INIT_POISEUILLE = 1   /* tau = 1 discrete Poiseuille fixed point of the
+                                  body force along x (needs bounce-back walls)   */
+} lbib_init;
+
+typedef enum {
+    LBIB_MEMBRANE_KINEMATIC = 0,       /* Eq. kinematicPos with the interpolated velocity */
+    LBIB_MEMBRANE_RIGID_PROJECTED = 1  /* same, velocity first projected on the
+                                          least-squares rigid motion of the ring  */
+} lbib_kind;
+
+typedef struct {
+    int32_t nx, ny;          /* lattice size; nx, ny >= 4                       */
+    lbib_precision prec;
+    lbib_init init;
+} lbib_lattice;
+
+/* Bond model (Sec. 2.2): spring sigma (y - y_eq) along ligand->receptor,
+ * ligand point = centroid of its element, force split half/half to the two
+ * element vertices.  Per step, at X^{n+1}: rupture first (if d >= d_break or
+ * u < P_r(d)), then formation (ligands free after rupture, receptors free at the
+ * start of the step, d < d_cut, first receptor in ascending id with
+ * u < P_f(d); a receptor goes to the lowest ligand id), where
+ *   P_f(d) = 1 - exp(-kf_dt * exp(-beta_f ((d - y_eq)/y_eq)^2)),
+ *   P_r(d) = 1 - exp(-kr0_dt * exp( beta_r ((d - y_eq)/y_eq)^2)),
+ * and u is the Philox4x64-10 draw for counter (step, ligand, receptor, tag)
+ * (tag 0 formation, 1 rupture), key (seed, instance): u = (x0 >> 11) 2^-53. */
+typedef struct {
+    double d_cut, y_eq, sigma, kf_dt, kr0_dt, beta_f, beta_r, d_break;
+    uint64_t seed, instance;
+} lbib_bond_params;
+
+/* Create a context.  tau: BGK relaxation time (Eq. BGK; nu = (tau - 1/2)/3).
+ * body_force: uniform G_body (2 doubles) added to the spread IB force.
+ * cuda_stream: a cudaStream_t to enqueue on, or NULL for a library-owned
+ * stream.  Allocates the two population buffers (9 NX NY elements each).
+ * Errors: LBIB_E_INVALID (sizes, tau <= 1/2, POISEUILLE without walls),
+ * LBIB_E_OOM, LBIB_E_CUDA. */
+lbib_status lbib_create(const lbib_lattice* lattice, double tau, const double body_force[2],
+                        lbib_walls walls, void* cuda_stream, lbib_ctx** out);
+
+/* Add a closed membrane ring (Sec. 2.2): xy holds 2n doubles (x0,y0,x1,y1,..),
+ * counter-clockwise, unwrapped x; the given shape is the stress-free state that
+ * fixes the rest lengths l_0, rest angles theta_0 and rest area A_0.  Element k
+ * joins vertices k and (k+1) mod n.  k_s, k_b, k_area: Eqs. strainFor, bendFor,
+ * areaFor (p_ref = 1/3).  ligand_elems: local element ids carrying one ligand
+ * each (NULL if n_ligands = 0).  Must precede the first lbib_step.
+ * membrane_id_out may be NULL.  Errors: LBIB_E_INVALID, LBIB_E_STATE. */
+lbib_status lbib_add_membrane(lbib_ctx* ctx, const double* xy, int32_t n, double k_s, double k_b,
+                              double k_area, lbib_kind kind, const int32_t* ligand_elems,
+                              int32_t n_ligands, int32_t* membrane_id_out);
+
+/* Receptors: xy holds 2n doubles (fixed positions, typically one per wall
+ * node at y = -1/2 or NY - 1/2).  Replaces any earlier set; all bonds are
+ * cleared.  Must precede the first lbib_step.  Errors: LBIB_E_INVALID, LBIB_E_STATE. */
+lbib_status lbib_set_receptors(lbib_ctx* ctx, const double* xy, int32_t n,
+                               const lbib_bond_params* params);
+
+/* Cut-off distance of the inter-membrane repulsion, Eq. repFor (default 2). */
+lbib_status lbib_set_repulsion(lbib_ctx* ctx, double d_rep);
+
+/* Advance n time steps (enqueued; replays captured CUDA graphs).  Errors from
+ * launching are returned; device-side failures are reported by lbib_sync or
+ * the next read. */
+lbib_status lbib_step(lbib_ctx* ctx, int64_t n);
+
+/* Wait for the context's stream and report device-side status. */
+lbib_status lbib_sync(lbib_ctx* ctx);
+
+/* Steps taken so far. */
+int64_t lbib_step_count(const lbib_ctx* ctx);
+
+/* rho^n, u^n of the last completed step (Sec. 2.1 moments with the Guo
+ * half-force, Sec. 2.2), each NY*NX doubles, row-major (y, x).  Any pointer may
+ * be NULL.  LBIB_E_STATE before the first step or after write_populations. */
+lbib_status lbib_read_fields(lbib_ctx* ctx, double* rho, double* ux, double* uy, int on_device);
+
+/* Pre-collision populations f^n at the current step, 9*NY*NX doubles laid out
+ * [i][y][x] with the velocity order of Eq. GaussHermite. */
+lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, int on_device);
+
+/* Replace the populations by f (same layout as lbib_read_populations). */
+lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, int on_device);
+
+/* Marker positions X^n (2 doubles per vertex, unwrapped x) of one membrane, or
+ * of all membranes concatenated in creation order when membrane_id = -1. */
+lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t membrane_id, double* xy);
+
+/* Overwrite X^n and X^{n-1} of all membranes (2*nv doubles each, host memory);
+ * xy_prev may be NULL (then X^{n-1} = X^n). */
+lbib_status lbib_write_markers(lbib_ctx* ctx, const double* xy, const double* xy_prev);
+
+/* Total Lagrangian force F^n and interpolated velocity U^n used by the last
+ * step, 2 doubles per vertex (all membranes, host memory). */
+lbib_status lbib_read_marker_forces(lbib_ctx* ctx, double* fxy);
+lbib_status lbib_read_marker_velocity(lbib_ctx* ctx, double* uxy);
+
+/* Current bonds as (ligand, receptor) pairs, ascending ligand id; at most cap
+ * pairs are written, *n_out receives the number of bonds. */
+lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t* ligand_ids, int32_t* receptor_ids,
+                            int32_t cap, int32_t* n_out);
+
+/* FP64 invariants: total mass sum_x sum_i f_i (Sec. 2.1) and, if areas is not
+ * NULL, the enclosed area of each membrane (Eq. areaFor's Green area). */
+lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
+
+/* Tile shape of the fused kernel: vec consecutive x nodes per thread, ty rows
+ * per block (vec in {1,2,4,8} dividing NX, storage-aligned; ty in 1..16).
+ * Must precede the first step.  0,0 picks the default. */
+lbib_status lbib_set_tiling(lbib_ctx* ctx, int32_t vec, int32_t ty);
+lbib_status lbib_get_tiling(const lbib_ctx* ctx, int32_t* vec, int32_t* ty);
+
+/* Profiling aid: launch only the fused collide-stream kernel `reps` times on
+ * the context's stream (ping-pong between the two population buffers, with the
+ * IB force of the last completed step frozen), bracketed by CUDA events, and
+ * return the mean duration of one launch in milliseconds.  This advances the
+ * populations without the Lagrangian part, so use it on a scratch context.
+ * Errors: LBIB_E_STATE before the first step. */
+lbib_status lbib_profile_fused(lbib_ctx* ctx, int32_t reps, double* ms_per_launch);
+
+/* Number of kernels one time step launches (for launch accounting). */
+int32_t lbib_kernels_per_step(const lbib_ctx* ctx);
+
+/* Scale exponent k of the 16-bit storage (d_i * 2^k); 0 for F32/F64. */
+int32_t lbib_storage_scale_exponent(const lbib_ctx* ctx);
+
+const char* lbib_last_error(const lbib_ctx* ctx);
+void lbib_destroy(lbib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIB_H */

@@ -1,0 +1,819 @@
+// C ABI of the lbib library: context set-up, device arena, captured step
+// graphs and read-backs.  Every step of the time integration runs in the CUDA
+// kernels of lb_kernels.cu, ib_kernels.cu and bond_kernels.cu; this file only
+// arranges memory, validates arguments and enqueues work.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "lbib_internal.cuh"
+
+using namespace lbib;
+
+namespace {
+
+constexpr int kChunk = 16;  // steps per captured chunk graph (even)
+
+lbib_status fail(lbib_ctx* c, lbib_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+lbib_status cuda_fail(lbib_ctx* c, cudaError_t e, const char* where) {
+    if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LBIB_E_OOM : LBIB_E_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+size_t elem_size(lbib_precision p) {
+    switch (p) {
+        case LBIB_F64: return 8;
+        case LBIB_F32: return 4;
+        default: return 2;
+    }
+}
+
+struct Arena {
+    char* base = nullptr;
+    size_t used = 0;
+    template <typename T>
+    T* take(size_t n) {
+        used = (used + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + used);
+        used += sizeof(T) * (n ? n : 1);
+        return p;
+    }
+};
+
+bool valid_vec(lbib_precision p, int vec, int nx) {
+    if (vec <= 0 || nx % vec) return false;
+    switch (p) {
+        case LBIB_F64: return vec == 1 || vec == 2;
+        case LBIB_F32: return vec == 1 || vec == 2 || vec == 4;
+        default: return vec == 2 || vec == 4 || vec == 8;
+    }
+}
+
+void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
+    int v = c->prec == LBIB_F64 ? 2 : (c->prec == LBIB_F32 ? 4 : 8);
+    while (v > 1 && !valid_vec(c->prec, v, c->nx)) v /= 2;
+    const long long N = (long long)c->nx * c->ny;
+    // small lattices: fewer nodes per thread so that every SM has warps to switch between
+    while (v > 1 && N / v < 152LL * 1024 && valid_vec(c->prec, v / 2, c->nx)) v /= 2;
+    const long long tiles_x = (c->nx + 32LL * v - 1) / (32LL * v);
+    int t = 4;
+    while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 8) t /= 2;
+    *vec = v;
+    *ty = t;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ create
+extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const double body_force[2],
+                                   lbib_walls walls, void* cuda_stream, lbib_ctx** out) {
+    if (!lat || !out) return LBIB_E_INVALID;
+    *out = nullptr;
+    if (lat->nx < 4 || lat->ny < 4) return LBIB_E_INVALID;
+    if (!(tau > 0.5)) return LBIB_E_INVALID;
+    if (lat->prec < LBIB_F64 || lat->prec > LBIB_F32_STORE_BF16) return LBIB_E_INVALID;
+    if (walls != LBIB_WALLS_NONE && walls != LBIB_WALLS_Y_BOUNCEBACK) return LBIB_E_INVALID;
+    if (lat->init == LBIB_INIT_POISEUILLE && (walls != LBIB_WALLS_Y_BOUNCEBACK || tau != 1.0))
+        return LBIB_E_INVALID;
+    if (lat->prec != LBIB_F64 && lat->prec != LBIB_F32 && (lat->nx % 2)) return LBIB_E_INVALID;
+    lbib_ctx* c = new lbib_ctx();
+    c->nx = lat->nx;
+    c->ny = lat->ny;
+    c->prec = lat->prec;
+    c->init = lat->init;
+    c->tau = tau;
+    c->gx = body_force ? body_force[0] : 0.0;
+    c->gy = body_force ? body_force[1] : 0.0;
+    c->walls = walls;
+    c->pop_elem = elem_size(c->prec);
+    c->cmp_elem = c->prec == LBIB_F64 ? 8 : 4;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return LBIB_E_CUDA;
+    }
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return LBIB_E_CUDA;
+        }
+        c->own_stream = true;
+    }
+    if (c->prec == LBIB_F32_STORE_F16) {
+        // scale the deviations so that the expected peak (a few times the
+        // Poiseuille peak deviation w_1 * 3 u_max) sits near 2^12 in FP16
+        const double nu = (tau - 0.5) / 3.0;
+        const double umax = std::max(1e-12, std::fabs(c->gx) * (double)c->ny * c->ny / (8.0 * nu) +
+                                                 std::fabs(c->gy) * (double)c->nx * c->nx / (8.0 * nu));
+        const double dmax = std::max(umax / 3.0, 1e-9);
+        int k = (int)std::floor(std::log2(4096.0 / dmax));
+        k = std::max(0, std::min(k, 40));
+        c->scale_exp = k;
+        c->inv_scale = std::ldexp(1.0f, -k);
+    }
+    const size_t N = (size_t)c->nx * c->ny;
+    cudaError_t e;
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMalloc(&c->f[b], 9 * N * c->pop_elem);
+        if (e != cudaSuccess) {
+            lbib_destroy(c);
+            return LBIB_E_OOM;
+        }
+    }
+    e = cudaMalloc(&c->ux, N * c->cmp_elem);
+    if (e == cudaSuccess) e = cudaMalloc(&c->uy, N * c->cmp_elem);
+    c->n_partials = 1024;
+    if (e == cudaSuccess) e = cudaMalloc(&c->partials, sizeof(double) * c->n_partials);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dscalar, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_step, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e != cudaSuccess) {
+        lbib_destroy(c);
+        return LBIB_E_OOM;
+    }
+    e = cudaMemsetAsync(c->ux, 0, N * c->cmp_elem, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->uy, 0, N * c->cmp_elem, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    // rest: all deviations zero; Poiseuille: the fixed point's post-collision state
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, 9 * N * c->pop_elem, c->stream);
+    if (e == cudaSuccess && c->init == LBIB_INIT_POISEUILLE)
+        e = launch_init_poiseuille(c->prec, c->f[0], c->nx, c->ny, tau, c->gx, c->inv_scale, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lbib_destroy(c);
+        return LBIB_E_CUDA;
+    }
+    c->cur = 0;
+    *out = c;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t n, double k_s,
+                                         double k_b, double k_area, lbib_kind kind,
+                                         const int32_t* ligand_elems, int32_t n_ligands,
+                                         int32_t* membrane_id_out) {
+    if (!c) return LBIB_E_INVALID;
+    if (c->finalized) return fail(c, LBIB_E_STATE, "membranes must be added before the first step");
+    if (!xy || n < 3) return fail(c, LBIB_E_INVALID, "a membrane needs >= 3 vertices");
+    if (kind != LBIB_MEMBRANE_KINEMATIC && kind != LBIB_MEMBRANE_RIGID_PROJECTED)
+        return fail(c, LBIB_E_INVALID, "unknown membrane kind");
+    if (n_ligands < 0 || (n_ligands > 0 && !ligand_elems))
+        return fail(c, LBIB_E_INVALID, "ligand list");
+    for (int k = 0; k < 2 * n; ++k)
+        if (!std::isfinite(xy[k])) return fail(c, LBIB_E_INVALID, "non-finite vertex");
+    std::vector<char> used(n, 0);
+    for (int k = 0; k < n_ligands; ++k) {
+        if (ligand_elems[k] < 0 || ligand_elems[k] >= n) return fail(c, LBIB_E_INVALID, "ligand element out of range");
+        if (used[ligand_elems[k]]) return fail(c, LBIB_E_INVALID, "at most one ligand per element");
+        used[ligand_elems[k]] = 1;
+    }
+    const int m = c->nmem;
+    c->h_mem_off.push_back(c->nv);
+    c->h_mem_n.push_back(n);
+    c->h_mem_kind.push_back((int)kind);
+    c->h_ks.push_back(k_s);
+    c->h_kb.push_back(k_b);
+    c->h_ka.push_back(k_area);
+    c->h_xy.insert(c->h_xy.end(), xy, xy + 2 * n);
+    if (c->h_mem_lig_off.empty()) c->h_mem_lig_off.push_back(0);
+    for (int k = 0; k < n_ligands; ++k) c->h_lig_elem_local.push_back(c->nv + ligand_elems[k]);
+    c->nlig += n_ligands;
+    c->h_mem_lig_off.push_back(c->nlig);
+    c->nv += n;
+    c->nmem += 1;
+    c->max_mem_n = std::max(c->max_mem_n, n);
+    if (membrane_id_out) *membrane_id_out = m;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_set_receptors(lbib_ctx* c, const double* xy, int32_t n,
+                                          const lbib_bond_params* p) {
+    if (!c) return LBIB_E_INVALID;
+    if (c->finalized) return fail(c, LBIB_E_STATE, "receptors must be set before the first step");
+    if (n < 0 || (n > 0 && !xy) || !p) return fail(c, LBIB_E_INVALID, "receptor arguments");
+    if (n > 0 && c->walls != LBIB_WALLS_Y_BOUNCEBACK)
+        return fail(c, LBIB_E_INVALID, "receptors need bounce-back walls");
+    if (!(p->d_cut > 0.0) || !(p->y_eq > 0.0) || !(p->d_break > 0.0))
+        return fail(c, LBIB_E_INVALID, "bond lengths must be positive");
+    for (int k = 0; k < 2 * n; ++k)
+        if (!std::isfinite(xy[k])) return fail(c, LBIB_E_INVALID, "non-finite receptor");
+    c->h_rec.assign(xy, xy + 2 * n);
+    c->bp = *p;
+    c->have_receptors = true;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_set_repulsion(lbib_ctx* c, double d_rep) {
+    if (!c || !(d_rep >= 0.0)) return LBIB_E_INVALID;
+    c->d_rep = d_rep;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_set_tiling(lbib_ctx* c, int32_t vec, int32_t ty) {
+    if (!c) return LBIB_E_INVALID;
+    if (c->finalized) return fail(c, LBIB_E_STATE, "tiling is fixed at the first step");
+    if (vec == 0 && ty == 0) {
+        c->vec = c->ty = 0;
+        return LBIB_OK;
+    }
+    if (!valid_vec(c->prec, vec, c->nx) || ty < 1 || ty > 16)
+        return fail(c, LBIB_E_INVALID, "unsupported tiling");
+    c->vec = vec;
+    c->ty = ty;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_get_tiling(const lbib_ctx* c, int32_t* vec, int32_t* ty) {
+    if (!c || !vec || !ty) return LBIB_E_INVALID;
+    if (c->vec) {
+        *vec = c->vec;
+        *ty = c->ty;
+    } else {
+        default_tiling(c, vec, ty);
+    }
+    return LBIB_OK;
+}
+
+// ------------------------------------------------------------------ finalize
+static lbib_status finalize(lbib_ctx* c) {
+    if (c->finalized) return LBIB_OK;
+    if (!c->vec) default_tiling(c, &c->vec, &c->ty);
+    c->tile_w = 32 * c->vec;
+    c->tile_h = c->ty;
+    c->tiles_x = (c->nx + c->tile_w - 1) / c->tile_w;
+    c->tiles_y = (c->ny + c->tile_h - 1) / c->tile_h;
+    c->ntiles = c->tiles_x * c->tiles_y;
+
+    const int nv = c->nv, nm = c->nmem, nl = c->nlig;
+    const int nr = c->have_receptors ? (int)(c->h_rec.size() / 2) : 0;
+    // segments of 32 consecutive vertices per membrane
+    std::vector<int> seg_mem, seg_v0, seg_n, mem_seg_off(nm + 1, 0);
+    for (int m = 0; m < nm; ++m) {
+        mem_seg_off[m] = (int)seg_mem.size();
+        for (int s = 0; s < c->h_mem_n[m]; s += 32) {
+            seg_mem.push_back(m);
+            seg_v0.push_back(c->h_mem_off[m] + s);
+            seg_n.push_back(std::min(32, c->h_mem_n[m] - s));
+        }
+    }
+    mem_seg_off[nm] = (int)seg_mem.size();
+    c->nseg = (int)seg_mem.size();
+    // ligand element vertices and element -> ligand map
+    std::vector<int> lig_a(nl), lig_b(nl), elem_lig(std::max(nv, 1), -1), vmem(std::max(nv, 1));
+    for (int m = 0; m < nm; ++m)
+        for (int k = 0; k < c->h_mem_n[m]; ++k) vmem[c->h_mem_off[m] + k] = m;
+    for (int l = 0; l < nl; ++l) {
+        const int a = c->h_lig_elem_local[l];
+        const int m = vmem[a];
+        lig_a[l] = a;
+        lig_b[l] = c->h_mem_off[m] + (a - c->h_mem_off[m] + 1) % c->h_mem_n[m];
+        elem_lig[a] = l;
+    }
+    std::vector<int> mem_lig_off = c->h_mem_lig_off;
+    if (mem_lig_off.empty()) mem_lig_off.assign(nm + 1, 0);
+    // receptor grid: cells at least d_cut wide so a 3x3 block covers the cut-off disc
+    int rc_nx = 1, rc_ny = 1;
+    double rc_w = c->nx, rc_h = 1.0, rc_y0 = 0.0;
+    std::vector<int> rcell_start(2, 0), rcell_ids;
+    if (nr > 0) {
+        const double dc = c->bp.d_cut;
+        rc_nx = std::max(1, (int)std::floor(c->nx / dc));
+        rc_w = (double)c->nx / rc_nx;
+        double ymin = 1e300, ymax = -1e300;
+        for (int r = 0; r < nr; ++r) {
+            ymin = std::min(ymin, c->h_rec[2 * r + 1]);
+            ymax = std::max(ymax, c->h_rec[2 * r + 1]);
+        }
+        const double span = ymax - ymin;
+        rc_ny = std::max(1, (int)std::floor(span / dc));
+        rc_h = span > 0 ? std::max(span / rc_ny, dc) : dc;
+        rc_y0 = ymin;
+        std::vector<int> cell(nr);
+        std::vector<int> cnt((size_t)rc_nx * rc_ny + 1, 0);
+        for (int r = 0; r < nr; ++r) {
+            const double x = c->h_rec[2 * r] - c->nx * std::floor(c->h_rec[2 * r] / c->nx);
+            int gx = std::min(rc_nx - 1, (int)std::floor(x / rc_w));
+            int gy = std::min(rc_ny - 1, std::max(0, (int)std::floor((c->h_rec[2 * r + 1] - rc_y0) / rc_h)));
+            cell[r] = gy * rc_nx + gx;
+            cnt[cell[r] + 1]++;
+        }
+        for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+        rcell_start = cnt;
+        rcell_ids.assign(nr, 0);
+        std::vector<int> cur(cnt.begin(), cnt.end() - 1);
+        for (int r = 0; r < nr; ++r) rcell_ids[cur[cell[r]]++] = r;  // ascending id within a cell
+    }
+    c->list_cap = 6 * std::max(nv, 1);
+
+    // ---- one arena for every marker / tile / bond array
+    const size_t cs = c->cmp_elem;
+    size_t bytes = 0;
+    {
+        Arena probe;
+        probe.base = nullptr;
+        auto add = [&](size_t b) { probe.used = ((probe.used + 255) & ~size_t(255)) + (b ? b : 1); };
+        add(4 * (nm + 1)); add(4 * (nm + 1)); add(4 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1));
+        add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
+        add(16 * nv); add(16 * nv); add(2 * cs * nv); add(2 * cs * nv); add(9 * cs * nv); add(8 * nv);
+        add(24 * nv); add(8 * nv); add(8 * nv); add(4 * nv);
+        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(32 * c->nseg); add(4 * (nm + 1));
+        add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
+        add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
+        add(4 * c->ntiles); add(4 * (c->ntiles + 1)); add(4 * c->ntiles);
+        add(4 * c->list_cap); add(4 * c->list_cap); add(4 * c->list_cap); add(8 * (nm + 1));
+        bytes = probe.used + 256;
+    }
+    lbib_status st = LBIB_OK;
+    cudaError_t e = cudaMalloc(&c->dmem, bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "arena");
+    c->dmem_bytes = bytes;
+    Arena ar;
+    ar.base = static_cast<char*>(c->dmem);
+    MarkerArgs& a = c->ma;
+    a = MarkerArgs{};
+    a.nx = c->nx; a.ny = c->ny; a.walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK ? 1 : 0;
+    a.nmem = nm; a.nv = nv;
+    int* mem_off = ar.take<int>(nm + 1);
+    int* mem_n = ar.take<int>(nm + 1);
+    int* mem_kind = ar.take<int>(nm + 1);
+    double* ks = ar.take<double>(nm + 1);
+    double* kb = ar.take<double>(nm + 1);
+    double* ka = ar.take<double>(nm + 1);
+    double* A0 = ar.take<double>(nm + 1);
+    int* lig_off = ar.take<int>(nm + 2);
+    a.X = ar.take<double>(2 * (size_t)nv);
+    a.Xp = ar.take<double>(2 * (size_t)nv);
+    a.F = ar.take<char>(2 * cs * nv);
+    a.U = ar.take<char>(2 * cs * nv);
+    a.W = ar.take<char>(9 * cs * nv);
+    a.stencil = ar.take<int>(2 * (size_t)nv);
+    a.vtiles = ar.take<int>(6 * (size_t)nv);
+    double* l0 = ar.take<double>(nv);
+    double* th0 = ar.take<double>(nv);
+    int* elig = ar.take<int>(nv);
+    int* d_seg_mem = ar.take<int>(c->nseg);
+    int* d_seg_v0 = ar.take<int>(c->nseg);
+    int* d_seg_n = ar.take<int>(c->nseg);
+    a.seg_box = ar.take<double>(4 * (size_t)c->nseg);
+    int* d_mem_seg_off = ar.take<int>(nm + 1);
+    int* d_lig_a = ar.take<int>(nl);
+    int* d_lig_b = ar.take<int>(nl);
+    a.bond_of_lig = ar.take<int>(nl);
+    a.cand = ar.take<int>(nl);
+    a.rupt = ar.take<int>(nl);
+    double* rec_xy = ar.take<double>(2 * (size_t)nr);
+    a.owner = ar.take<int>(nr);
+    a.claim = ar.take<int>(nr);
+    int* d_rcs = ar.take<int>(rcell_start.size());
+    int* d_rci = ar.take<int>(rcell_ids.size());
+    c->tile_count = ar.take<int>(c->ntiles);
+    c->tile_off = ar.take<int>(c->ntiles + 1);
+    c->tile_cursor = ar.take<int>(c->ntiles);
+    c->list_raw = ar.take<int>(c->list_cap);
+    c->list_tile = ar.take<int>(c->list_cap);
+    c->list_sorted = ar.take<int>(c->list_cap);
+    c->d_areas = ar.take<double>(nm + 1);
+    if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
+
+    auto H2D = [&](void* d, const void* h, size_t b) -> cudaError_t {
+        if (b == 0) return cudaSuccess;
+        return cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, c->stream);
+    };
+    std::vector<double> zeros;
+    if (nm > 0) {
+        CK(H2D(mem_off, c->h_mem_off.data(), 4 * nm));
+        CK(H2D(mem_n, c->h_mem_n.data(), 4 * nm));
+        CK(H2D(mem_kind, c->h_mem_kind.data(), 4 * nm));
+        CK(H2D(ks, c->h_ks.data(), 8 * nm));
+        CK(H2D(kb, c->h_kb.data(), 8 * nm));
+        CK(H2D(ka, c->h_ka.data(), 8 * nm));
+        CK(H2D(lig_off, mem_lig_off.data(), 4 * (nm + 1)));
+        CK(H2D(a.X, c->h_xy.data(), 16 * (size_t)nv));
+        CK(H2D(a.Xp, c->h_xy.data(), 16 * (size_t)nv));
+        CK(cudaMemsetAsync(a.F, 0, 2 * cs * nv, c->stream));
+        CK(cudaMemsetAsync(a.U, 0, 2 * cs * nv, c->stream));
+        CK(H2D(elig, elem_lig.data(), 4 * (size_t)nv));
+        CK(H2D(d_seg_mem, seg_mem.data(), 4 * seg_mem.size()));
+        CK(H2D(d_seg_v0, seg_v0.data(), 4 * seg_v0.size()));
+        CK(H2D(d_seg_n, seg_n.data(), 4 * seg_n.size()));
+        CK(H2D(d_mem_seg_off, mem_seg_off.data(), 4 * (nm + 1)));
+    }
+    if (nl > 0) {
+        CK(H2D(d_lig_a, lig_a.data(), 4 * nl));
+        CK(H2D(d_lig_b, lig_b.data(), 4 * nl));
+        CK(cudaMemsetAsync(a.bond_of_lig, 0xFF, 4 * nl, c->stream));
+        CK(cudaMemsetAsync(a.cand, 0xFF, 4 * nl, c->stream));
+        CK(cudaMemsetAsync(a.rupt, 0xFF, 4 * nl, c->stream));
+    }
+    if (nr > 0) {
+        CK(H2D(rec_xy, c->h_rec.data(), 16 * (size_t)nr));
+        CK(cudaMemsetAsync(a.owner, 0xFF, 4 * nr, c->stream));
+        CK(cudaMemsetAsync(a.claim, 0x7F, 4 * nr, c->stream));  // 0x7F7F7F7F: no claim
+    }
+    CK(H2D(d_rcs, rcell_start.data(), 4 * rcell_start.size()));
+    if (!rcell_ids.empty()) CK(H2D(d_rci, rcell_ids.data(), 4 * rcell_ids.size()));
+    CK(cudaMemsetAsync(c->tile_count, 0, 4 * c->ntiles, c->stream));
+    CK(cudaMemsetAsync(c->tile_off, 0, 4 * (c->ntiles + 1), c->stream));
+
+    a.mem_off = mem_off; a.mem_n = mem_n; a.mem_kind = mem_kind;
+    a.mem_ks = ks; a.mem_kb = kb; a.mem_ka = ka; a.mem_A0 = A0; a.mem_lig_off = lig_off;
+    a.l0 = l0; a.th0 = th0; a.elem_lig = elig;
+    a.d_rep = c->d_rep; a.nseg = c->nseg;
+    a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
+    a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
+    a.rec_xy = rec_xy; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
+    a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
+    a.sigma = c->bp.sigma; a.y_eq = c->bp.y_eq; a.d_cut = c->bp.d_cut; a.d_break = c->bp.d_break;
+    a.kf_dt = c->bp.kf_dt; a.kr0_dt = c->bp.kr0_dt; a.beta_f = c->bp.beta_f; a.beta_r = c->bp.beta_r;
+    a.seed = c->bp.seed; a.instance = c->bp.instance;
+    a.tile_w = c->tile_w; a.tile_h = c->tile_h; a.tiles_x = c->tiles_x; a.tiles_y = c->tiles_y;
+    a.tile_count = c->tile_count;
+    a.d_step = c->d_step; a.status = c->d_status;
+    a.ux = c->ux; a.uy = c->uy;
+
+    if (nm > 0) {
+        CK(launch_rest(c->prec, a, l0, th0, A0, c->stream));
+        CK(launch_seg_boxes(a, c->stream));
+        CK(set_forces_smem(c->prec, c->max_mem_n));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->finalized = true;
+    return st;
+}
+
+// ------------------------------------------------------------------ one step
+static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
+    MarkerArgs& a = c->ma;
+    cudaError_t e;
+    const bool has_ib = c->nv > 0;
+    if (has_ib) {
+        if ((e = launch_forces(c->prec, a, c->max_mem_n, s)) != cudaSuccess) return e;
+        if ((e = launch_scan_tiles(c->tile_count, c->tile_off, c->tile_cursor, c->ntiles, s)) != cudaSuccess) return e;
+        if ((e = launch_fill_tiles(a, c->tile_cursor, c->list_raw, c->list_tile, s)) != cudaSuccess) return e;
+        if ((e = launch_sort_tiles(c->tile_off, c->list_raw, c->list_tile, c->list_sorted, c->list_cap,
+                                   c->ntiles, s)) != cudaSuccess)
+            return e;
+    }
+    LbArgs l{};
+    l.src = c->f[src];
+    l.dst = c->f[1 - src];
+    l.ux = c->ux;
+    l.uy = c->uy;
+    l.tile_off = c->tile_off;
+    l.list = c->list_sorted;
+    l.wts = a.W;
+    l.stencil = a.stencil;
+    l.force = a.F;
+    l.nx = c->nx;
+    l.ny = c->ny;
+    l.omega = 1.0 / c->tau;
+    l.gx = c->gx;
+    l.gy = c->gy;
+    l.inv_scale = c->inv_scale;
+    l.fields_only = 0;
+    if ((e = launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, has_ib, l, s)) != cudaSuccess)
+        return e;
+    if (has_ib) {
+        if ((e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
+    }
+    return launch_bonds(a, s);
+}
+
+static lbib_status build_graphs(lbib_ctx* c) {
+    if (c->graphs_ready) return LBIB_OK;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    for (int start = 0; start < 2; ++start) {
+        for (int kind = 0; kind < 2; ++kind) {
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return cuda_fail(c, e, "begin capture");
+            }
+            const int nsteps = kind == 0 ? 1 : kChunk;
+            int src = start;
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < nsteps && le == cudaSuccess; ++k) {
+                le = enqueue_step(c, src, cap);
+                src = 1 - src;
+            }
+            e = cudaStreamEndCapture(cap, &g);
+            if (le != cudaSuccess || e != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return cuda_fail(c, le != cudaSuccess ? le : e, "capture step");
+            }
+            e = cudaGraphInstantiate(&c->graph[start][kind], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return cuda_fail(c, e, "instantiate step graph");
+            }
+        }
+    }
+    cudaStreamDestroy(cap);
+    c->graphs_ready = true;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_step(lbib_ctx* c, int64_t n) {
+    if (!c || n < 0) return LBIB_E_INVALID;
+    if (c->poisoned) return fail(c, LBIB_E_STATE, "context poisoned by an earlier device-side failure");
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    st = build_graphs(c);
+    if (st != LBIB_OK) return st;
+    int64_t left = n;
+    while (left >= kChunk) {
+        CK(cudaGraphLaunch(c->graph[c->cur][1], c->stream));
+        left -= kChunk;  // even number of steps: the buffer roles are unchanged
+    }
+    while (left > 0) {
+        CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
+        c->cur = 1 - c->cur;
+        --left;
+    }
+    c->steps += n;
+    if (n > 0) c->fields_valid = true;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_sync(lbib_ctx* c) {
+    if (!c) return LBIB_E_INVALID;
+    CK(cudaStreamSynchronize(c->stream));
+    int st = 0;
+    CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & ST_NONFINITE) {
+        c->poisoned = true;
+        return fail(c, LBIB_E_NONFINITE, "a marker position became non-finite");
+    }
+    return LBIB_OK;
+}
+
+extern "C" int64_t lbib_step_count(const lbib_ctx* c) { return c ? c->steps : -1; }
+
+extern "C" int32_t lbib_kernels_per_step(const lbib_ctx* c) {
+    if (!c) return -1;
+    int k = 1;  // fused LB
+    if (c->nv > 0) k += 5;  // forces, scan, fill, sort, advance
+    k += (c->nlig > 0 && c->have_receptors && !c->h_rec.empty()) ? 2 : 1;
+    return k;
+}
+
+extern "C" int32_t lbib_storage_scale_exponent(const lbib_ctx* c) { return c ? c->scale_exp : 0; }
+
+// ------------------------------------------------------------------ read / write
+static lbib_status ensure_stage(lbib_ctx* c) {
+    if (c->stage) return LBIB_OK;
+    CK(cudaMalloc(&c->stage, 9 * sizeof(double) * (size_t)c->nx * c->ny));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_fields(lbib_ctx* c, double* rho, double* ux, double* uy, int on_device) {
+    if (!c) return LBIB_E_INVALID;
+    if (!c->fields_valid) return fail(c, LBIB_E_STATE, "no completed step since the populations were set");
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    const size_t N = (size_t)c->nx * c->ny;
+    double *dr = rho, *du = ux, *dv = uy;
+    if (!on_device) {
+        if ((st = ensure_stage(c)) != LBIB_OK) return st;
+        dr = rho ? c->stage : nullptr;
+        du = ux ? c->stage + N : nullptr;
+        dv = uy ? c->stage + 2 * N : nullptr;
+    }
+    LbArgs l{};
+    l.src = c->f[1 - c->cur];
+    l.dst = nullptr;
+    l.ux = c->ux;
+    l.uy = c->uy;
+    l.rho_out = dr;
+    l.ux_out = du;
+    l.uy_out = dv;
+    l.tile_off = c->tile_off;
+    l.list = c->list_sorted;
+    l.wts = c->ma.W;
+    l.stencil = c->ma.stencil;
+    l.force = c->ma.F;
+    l.nx = c->nx;
+    l.ny = c->ny;
+    l.omega = 1.0 / c->tau;
+    l.gx = c->gx;
+    l.gy = c->gy;
+    l.inv_scale = c->inv_scale;
+    l.fields_only = 1;
+    CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
+    if (!on_device) {
+        if (rho) CK(cudaMemcpyAsync(rho, dr, N * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (ux) CK(cudaMemcpyAsync(ux, du, N * 8, cudaMemcpyDeviceToHost, c->stream));
+        if (uy) CK(cudaMemcpyAsync(uy, dv, N * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_populations(lbib_ctx* c, double* f, int on_device) {
+    if (!c || !f) return LBIB_E_INVALID;
+    const size_t N = (size_t)c->nx * c->ny;
+    lbib_status st;
+    double* out = f;
+    if (!on_device) {
+        if ((st = ensure_stage(c)) != LBIB_OK) return st;
+        out = c->stage;
+    }
+    CK(launch_stream_out(c->prec, c->f[c->cur], out, c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
+                         c->inv_scale, c->stream));
+    if (!on_device) CK(cudaMemcpyAsync(f, out, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_write_populations(lbib_ctx* c, const double* f, int on_device) {
+    if (!c || !f) return LBIB_E_INVALID;
+    const size_t N = (size_t)c->nx * c->ny;
+    lbib_status st;
+    const double* in = f;
+    if (!on_device) {
+        if ((st = ensure_stage(c)) != LBIB_OK) return st;
+        CK(cudaMemcpyAsync(c->stage, f, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
+        in = c->stage;
+    }
+    CK(launch_stream_in(c->prec, in, c->f[c->cur], c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
+                        c->inv_scale, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->fields_valid = false;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_markers(lbib_ctx* c, int32_t m, double* xy) {
+    if (!c || !xy || m < -1 || m >= c->nmem) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (c->nv == 0) return LBIB_OK;
+    const int off = m < 0 ? 0 : c->h_mem_off[m];
+    const int n = m < 0 ? c->nv : c->h_mem_n[m];
+    CK(cudaMemcpyAsync(xy, c->ma.X + 2 * (size_t)off, 16 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_write_markers(lbib_ctx* c, const double* xy, const double* xy_prev) {
+    if (!c || !xy) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (c->nv == 0) return LBIB_OK;
+    const size_t b = 16 * (size_t)c->nv;
+    CK(cudaMemcpyAsync(c->ma.X, xy, b, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->ma.Xp, xy_prev ? xy_prev : xy, b, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_seg_boxes(c->ma, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+template <typename C>
+static void widen(const std::vector<char>& raw, double* out, size_t n) {
+    const C* p = reinterpret_cast<const C*>(raw.data());
+    for (size_t k = 0; k < n; ++k) out[k] = (double)p[k];
+}
+
+static lbib_status read_cvec(lbib_ctx* c, const void* dptr, double* out) {
+    if (!out) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (c->nv == 0) return LBIB_OK;
+    const size_t n = 2 * (size_t)c->nv;
+    std::vector<char> raw(n * c->cmp_elem);
+    CK(cudaMemcpyAsync(raw.data(), dptr, raw.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->cmp_elem == 8) widen<double>(raw, out, n);
+    else widen<float>(raw, out, n);
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_marker_forces(lbib_ctx* c, double* fxy) {
+    if (!c) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    return read_cvec(c, c->ma.F, fxy);
+}
+
+extern "C" lbib_status lbib_read_marker_velocity(lbib_ctx* c, double* uxy) {
+    if (!c) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    return read_cvec(c, c->ma.U, uxy);
+}
+
+extern "C" lbib_status lbib_read_bonds(lbib_ctx* c, int32_t* lig, int32_t* rec, int32_t cap, int32_t* n_out) {
+    if (!c || cap < 0 || (cap > 0 && (!lig || !rec))) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    std::vector<int> b(c->nlig);
+    if (c->nlig > 0) {
+        CK(cudaMemcpyAsync(b.data(), c->ma.bond_of_lig, 4 * (size_t)c->nlig, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    int cnt = 0;
+    for (int l = 0; l < c->nlig; ++l) {
+        if (b[l] < 0) continue;
+        if (cnt < cap) {
+            lig[cnt] = l;
+            rec[cnt] = b[l];
+        }
+        ++cnt;
+    }
+    if (n_out) *n_out = cnt;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_diagnostics(lbib_ctx* c, double* mass, double* areas) {
+    if (!c) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (mass) {
+        const long long n = 9LL * c->nx * c->ny;
+        CK(launch_mass(c->prec, c->f[c->cur], n, c->partials, c->n_partials, c->dscalar, c->inv_scale,
+                       c->stream));
+        CK(cudaMemcpyAsync(mass, c->dscalar, 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (areas && c->nmem > 0) {
+        CK(launch_areas(c->ma, c->d_areas, c->stream));
+        CK(cudaMemcpyAsync(areas, c->d_areas, 8 * (size_t)c->nmem, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_per_launch) {
+    if (!c || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
+    if (!c->finalized || c->steps == 0) return fail(c, LBIB_E_STATE, "profile after at least one step");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    LbArgs l{};
+    l.ux = c->ux;
+    l.uy = c->uy;
+    l.tile_off = c->tile_off;
+    l.list = c->list_sorted;
+    l.wts = c->ma.W;
+    l.stencil = c->ma.stencil;
+    l.force = c->ma.F;
+    l.nx = c->nx;
+    l.ny = c->ny;
+    l.omega = 1.0 / c->tau;
+    l.gx = c->gx;
+    l.gy = c->gy;
+    l.inv_scale = c->inv_scale;
+    CK(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < reps; ++r) {
+        l.src = c->f[c->cur];
+        l.dst = c->f[1 - c->cur];
+        CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
+        c->cur = 1 - c->cur;
+    }
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = (double)ms / reps;
+    c->fields_valid = false;
+    return LBIB_OK;
+}
+
+extern "C" const char* lbib_last_error(const lbib_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" void lbib_destroy(lbib_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 2; ++k)
+            if (c->graph[s][k]) cudaGraphExecDestroy(c->graph[s][k]);
+    for (int b = 0; b < 2; ++b)
+        if (c->f[b]) cudaFree(c->f[b]);
+    if (c->ux) cudaFree(c->ux);
+    if (c->uy) cudaFree(c->uy);
+    if (c->stage) cudaFree(c->stage);
+    if (c->partials) cudaFree(c->partials);
+    if (c->dscalar) cudaFree(c->dscalar);
+    if (c->d_step) cudaFree(c->d_step);
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->dmem) cudaFree(c->dmem);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}

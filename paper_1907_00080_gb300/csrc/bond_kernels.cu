@@ -1,0 +1,135 @@
+// Ligand-receptor bond kinetics: rupture, then formation, decided in FP64 with
+// counter-based Philox draws so that the bond history is reproducible and
+// independent of thread scheduling.
+//
+// Paper: Coclite, arXiv 1907.00080, Sec. 2.2 (wall-particle interaction: bonds
+// form below a critical separation, a forward probability governs formation
+// and a reverse probability governs rupture each step) and Sec. 3 (k_f/k_r0).
+// Philox4x64-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11 -- implemented here from that definition.
+#include <climits>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+        const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+        const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// uniform in [0,1) from the top 53 bits of the first output word
+__device__ __forceinline__ double bond_uniform(const MarkerArgs& a, long long step, int lig, int rec,
+                                               int tag) {
+    unsigned long long c[4] = {(unsigned long long)step, (unsigned long long)lig,
+                               (unsigned long long)rec, (unsigned long long)tag};
+    philox4x64_10(c, a.seed, a.instance);
+    return (double)(c[0] >> 11) * 0x1.0p-53;
+}
+
+__device__ __forceinline__ double p_form(const MarkerArgs& a, double d) {
+    const double z = (d - a.y_eq) / a.y_eq;
+    return 1.0 - exp(-a.kf_dt * exp(-a.beta_f * z * z));
+}
+__device__ __forceinline__ double p_rupture(const MarkerArgs& a, double d) {
+    const double z = (d - a.y_eq) / a.y_eq;
+    return 1.0 - exp(-a.kr0_dt * exp(a.beta_r * z * z));
+}
+
+__device__ __forceinline__ double wrapd(double d, double L) { return d - L * floor(d / L + 0.5); }
+
+__device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, double cyp, int r) {
+    const double dx = wrapd(a.rec_xy[2 * r] - cxp, (double)a.nx);
+    double dy = a.rec_xy[2 * r + 1] - cyp;
+    if (!a.walls) dy = wrapd(dy, (double)a.ny);
+    return sqrt(dx * dx + dy * dy);
+}
+
+// one thread per ligand: rupture test, then the formation candidate (the
+// lowest receptor id that passes), claimed with atomicMin (lowest ligand wins)
+__global__ void k_bonds_decide(const MarkerArgs a) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.nlig) return;
+    const long long step = *a.d_step;
+    const int va = a.lig_a[l], vb = a.lig_b[l];
+    const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
+    const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
+    int r = a.bond_of_lig[l];
+    if (r >= 0) {
+        const double d = lig_rec_dist(a, cxp, cyp, r);
+        bool rupture = d >= a.d_break;
+        if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+        if (!rupture) return;
+        a.rupt[l] = r;
+        a.bond_of_lig[l] = -1;
+    }
+    // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
+    const double xw = cxp - (double)a.nx * floor(cxp / (double)a.nx);
+    int gx = (int)floor(xw / a.rc_w);
+    gx = gx >= a.rc_nx ? a.rc_nx - 1 : gx;
+    const int gy = (int)floor((cyp - a.rc_y0) / a.rc_h);
+    int best = INT_MAX;
+    for (int qy = gy - 1; qy <= gy + 1; ++qy) {
+        const int cyc = qy;
+        if (cyc < 0 || cyc >= a.rc_ny) continue;
+        for (int qx = gx - 1; qx <= gx + 1; ++qx) {
+            const int cxc = ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
+            const int cell = cyc * a.rc_nx + cxc;
+            for (int p = a.rcell_start[cell]; p < a.rcell_start[cell + 1]; ++p) {
+                const int rr = a.rcell_ids[p];
+                if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
+                const double d = lig_rec_dist(a, cxp, cyp, rr);
+                if (!(d < a.d_cut)) continue;
+                if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
+            }
+        }
+    }
+    if (best != INT_MAX) {
+        a.cand[l] = best;
+        atomicMin(&a.claim[best], l);
+    }
+}
+
+// one thread per ligand: apply ruptures and the winning claims; bump the step
+__global__ void k_bonds_apply(const MarkerArgs a, int has_bonds) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l == 0) *a.d_step += 1;
+    if (!has_bonds || l >= a.nlig) return;
+    const int r_old = a.rupt[l];
+    if (r_old >= 0) {
+        a.owner[r_old] = -1;
+        a.rupt[l] = -1;
+    }
+    const int c = a.cand[l];
+    if (c >= 0 && a.claim[c] == l) {
+        a.bond_of_lig[l] = c;
+        a.owner[c] = l;
+    }
+}
+
+cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s) {
+    const bool has = a.nlig > 0 && a.nrec > 0;
+    if (has) k_bonds_decide<<<(a.nlig + 127) / 128, 128, 0, s>>>(a);
+    const int n = a.nlig > 0 ? a.nlig : 1;
+    k_bonds_apply<<<(n + 127) / 128, 128, 0, s>>>(a, has ? 1 : 0);
+    return cudaGetLastError();
+}
+
+int bond_kernel_count(const MarkerArgs& a) { return (a.nlig > 0 && a.nrec > 0) ? 2 : 1; }
+
+}  // namespace lbib

@@ -1,0 +1,583 @@
+// Lagrangian-side kernels: membrane forces (stretching, bending, enclosed
+// area, repulsion, bond springs), IB shape functions and tile binning, the
+// deterministic tile lists, and the interpolation + kinematic advance.
+//
+// Paper: Coclite, arXiv 1907.00080, Sec. 2.2 (Eqs. strainFor, bendFor,
+// areaFor, repFor, adhFor; MLS exchange), Sec. 2.3 (nine Eulerian points per
+// vertex, Eq. kinematicPos).
+#include <climits>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ double wrap_d(double d, double L) { return d - L * floor(d / L + 0.5); }
+
+// Roma, Peskin & Berger three-point regularised delta
+template <typename C>
+__device__ __forceinline__ C roma(C r) {
+    const C a = fabs(r);
+    if (a <= C(0.5)) return (C(1) + sqrt(C(1) - C(3) * a * a)) / C(3);
+    if (a <= C(1.5)) {
+        const C b = C(1) - a;
+        return (C(5) - C(3) * a - sqrt(C(1) - C(3) * b * b)) / C(6);
+    }
+    return C(0);
+}
+
+// Signed turning angle at a vertex, outward unit normal (normalised sum of the
+// two adjacent outward edge normals of a CCW ring) and the two edge lengths.
+template <typename C>
+struct VGeom {
+    C th, nx, ny, lL, lR;
+};
+
+template <typename C>
+__device__ __forceinline__ VGeom<C> vertex_geom(double xL, double yL, double xv, double yv,
+                                                double xR, double yR) {
+    const C eLx = C(xv - xL), eLy = C(yv - yL), eRx = C(xR - xv), eRy = C(yR - yv);
+    VGeom<C> g;
+    g.lL = sqrt(eLx * eLx + eLy * eLy);
+    g.lR = sqrt(eRx * eRx + eRy * eRy);
+    g.th = atan2(eLx * eRy - eLy * eRx, eLx * eRx + eLy * eRy);
+    C nx = eLy / g.lL + eRy / g.lR;
+    C ny = -eLx / g.lL - eRx / g.lR;
+    const C nn = sqrt(nx * nx + ny * ny);
+    g.nx = nx / nn;
+    g.ny = ny / nn;
+    return g;
+}
+
+// block-wide FP64 sum (blockDim multiple of 32, <= 1024); all threads get it
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// ---------------------------------------------------------------- rest state
+// Captures l_0, theta_0 (with the same arithmetic the force kernel uses, so
+// the rest shape gives exactly zero force) and A_0 per membrane.
+template <typename C>
+__global__ void k_rest(const MarkerArgs a, double* l0, double* th0, double* A0) {
+    const int m = blockIdx.x;
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    __shared__ double red[33];
+    const double* X = a.X;
+    const double xr = X[2 * off], yr = X[2 * off + 1];
+    double ap = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
+        const VGeom<C> g = vertex_geom<C>(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1], X[2 * R],
+                                          X[2 * R + 1]);
+        th0[v] = (double)g.th;
+        l0[v] = (double)g.lR;
+        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+    }
+    const double s = block_sum(ap, red);
+    if (threadIdx.x == 0) A0[m] = 0.5 * s;
+}
+
+// ---------------------------------------------------------------- forces
+template <typename C>
+__device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, double nxd, double nyd,
+                                                C& Fx, C& Fy) {
+    const int l = a.elem_lig[e];
+    if (l < 0) return;
+    const int r = a.bond_of_lig[l];
+    if (r < 0) return;
+    const int va = a.lig_a[l], vb = a.lig_b[l];
+    const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
+    const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
+    const double dx = wrap_d(a.rec_xy[2 * r] - cxp, nxd);
+    double dy = a.rec_xy[2 * r + 1] - cyp;
+    if (!a.walls) dy = wrap_d(dy, nyd);
+    const double d = sqrt(dx * dx + dy * dy);
+    const double c = a.sigma * (d - a.y_eq) / d;
+    Fx += C(0.5 * c * dx);
+    Fy += C(0.5 * c * dy);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
+    const int m = blockIdx.x;
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    extern __shared__ __align__(16) unsigned char smem[];
+    C* s_mnx = reinterpret_cast<C*>(smem);
+    C* s_mny = s_mnx + n;
+    C* s_sL = s_mny + n;
+    C* s_sR = s_sL + n;
+    C* s_nx = s_sR + n;
+    C* s_ny = s_nx + n;
+    __shared__ double red[33];
+    const double* X = a.X;
+    const double nxd = (double)a.nx, nyd = (double)a.ny;
+    const double xr = X[2 * off], yr = X[2 * off + 1];
+    const C kb = C(a.mem_kb[m]);
+
+    // pass 1: vertex geometry (bending) and the shoelace area about vertex 0
+    double ap = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
+        const VGeom<C> g = vertex_geom<C>(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1], X[2 * R],
+                                          X[2 * R + 1]);
+        const C mb = kb * (g.th - C(a.th0[v]));
+        s_mnx[k] = mb * g.nx;
+        s_mny[k] = mb * g.ny;
+        s_sL[k] = g.lL / (g.lL + g.lR);
+        s_sR[k] = g.lR / (g.lL + g.lR);
+        s_nx[k] = g.nx;
+        s_ny[k] = g.ny;
+        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+    }
+    const double A = 0.5 * block_sum(ap, red);  // includes a __syncthreads
+    // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
+    const C ca = C(-a.mem_ka[m] * (1.0 - A / a.mem_A0[m]) * (1.0 / 3.0));
+    const C ks = C(a.mem_ks[m]);
+
+    // the previous step's formation candidates of this membrane's ligands
+    for (int l = a.mem_lig_off[m] + threadIdx.x; l < a.mem_lig_off[m + 1]; l += blockDim.x) {
+        const int c = a.cand[l];
+        if (c >= 0) {
+            a.claim[c] = INT_MAX;
+            a.cand[l] = -1;
+        }
+    }
+
+    C* F = static_cast<C*>(a.F);
+    C* W = static_cast<C*>(a.W);
+    const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int kL = k == 0 ? n - 1 : k - 1, kR = k == n - 1 ? 0 : k + 1;
+        const int v = off + k, L = off + kL, R = off + kR;
+        const double xv = X[2 * v], yv = X[2 * v + 1];
+        const double xl = X[2 * L], yl = X[2 * L + 1], xR = X[2 * R], yR = X[2 * R + 1];
+        C Fx = C(0), Fy = C(0);
+        // Eq. adhFor on the two elements sharing v, half each
+        if (a.nlig > 0) {
+            bond_on_element<C>(a, L, nxd, nyd, Fx, Fy);
+            bond_on_element<C>(a, v, nxd, nyd, Fx, Fy);
+        }
+        // Eq. repFor against vertices of other membranes closer than d_rep
+        if (a.nmem > 1) {
+            for (int sg = 0; sg < a.nseg; ++sg) {
+                if (a.seg_mem[sg] == m) continue;
+                const double* bx = a.seg_box + 4 * sg;
+                double ddx = wrap_d(xv - bx[0], nxd);
+                double ddy = yv - bx[1];
+                if (!a.walls) ddy = wrap_d(ddy, nyd);
+                if (fabs(ddx) > bx[2] + a.d_rep || fabs(ddy) > bx[3] + a.d_rep) continue;
+                const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
+                for (int b = b0; b < b0 + nb; ++b) {
+                    const C dx = C(wrap_d(xv - X[2 * b], nxd));
+                    C dy = C(yv - X[2 * b + 1]);
+                    if (!a.walls) dy = C(wrap_d((double)dy, nyd));
+                    const C d = sqrt(dx * dx + dy * dy);
+                    if (d < C(a.d_rep)) {
+                        const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
+                        Fx -= mag * s_nx[k];
+                        Fy -= mag * s_ny[k];
+                    }
+                }
+            }
+        }
+        // Eq. strainFor on elements (v, R) and (L, v)
+        {
+            const C dx = C(xv - xR), dy = C(yv - yR);
+            const C l = sqrt(dx * dx + dy * dy);
+            const C c = -ks * (l - C(a.l0[v])) / l;
+            Fx += c * dx;
+            Fy += c * dy;
+            const C ex = C(xv - xl), ey = C(yv - yl);
+            const C l2 = sqrt(ex * ex + ey * ey);
+            const C c2 = -ks * (l2 - C(a.l0[L])) / l2;
+            Fx += c2 * ex;
+            Fy += c2 * ey;
+        }
+        // Eq. bendFor gathered: own term plus the neighbours' shares
+        Fx += -s_mnx[k] + s_mnx[kR] * s_sL[kR] + s_mnx[kL] * s_sR[kL];
+        Fy += -s_mny[k] + s_mny[kR] * s_sL[kR] + s_mny[kL] * s_sR[kL];
+        // Eq. areaFor, half of each adjacent element
+        Fx += C(0.5) * ca * C(-(yR - yl));
+        Fy += C(0.5) * ca * C(xR - xl);
+        F[2 * (size_t)v] = Fx;
+        F[2 * (size_t)v + 1] = Fy;
+
+        // ---- IB shape functions at X^n: nine nearest nodes, Roma weights,
+        // MLS (basis 1, dx, dy) re-solved where wall rows drop out
+        const double fi0 = floor(xv + 0.5), fj0 = floor(yv + 0.5);
+        const long long i0 = (long long)fi0;
+        const int j0 = (int)fj0;
+        C rx[3], ry[3], wx[3], wy[3];
+        bool rowok[3];
+        bool all = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            rx[q] = C((fi0 + (q - 1)) - xv);
+            ry[q] = C((fj0 + (q - 1)) - yv);
+            wx[q] = roma<C>(rx[q]);
+            wy[q] = roma<C>(ry[q]);
+            const int j = j0 + q - 1;
+            rowok[q] = a.walls ? (j >= 0 && j < a.ny) : true;
+            all = all && rowok[q];
+        }
+        C w[9];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) w[b * 3 + q] = rowok[b] ? wx[q] * wy[b] : C(0);
+        if (!all) {
+            C M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0, sw = 0;
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const C ww = w[b * 3 + q];
+                    sw += ww;
+                    M00 += ww;
+                    M01 += ww * rx[q];
+                    M02 += ww * ry[b];
+                    M11 += ww * rx[q] * rx[q];
+                    M12 += ww * rx[q] * ry[b];
+                    M22 += ww * ry[b] * ry[b];
+                }
+            // first column of the inverse of the symmetric 3x3 moment matrix
+            const C c0 = M11 * M22 - M12 * M12;
+            const C c1 = -(M01 * M22 - M12 * M02);
+            const C c2 = M01 * M12 - M11 * M02;
+            const C det = M00 * c0 + M01 * c1 + M02 * c2;
+            if (det > C(1e-10)) {
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        w[b * 3 + q] = w[b * 3 + q] * (c0 + c1 * rx[q] + c2 * ry[b]) / det;
+            } else if (sw > C(0)) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) w[q] = w[q] / sw;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) w[q] = C(0);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) W[9 * (size_t)v + q] = w[q];
+        const int i0w = (int)(((i0 % a.nx) + a.nx) % a.nx);
+        const int j0s = a.walls ? j0 : (((j0 % a.ny) + a.ny) % a.ny);
+        a.stencil[2 * (size_t)v] = i0w;
+        a.stencil[2 * (size_t)v + 1] = j0s;
+
+        // ---- tiles of the fused kernel touched by the stencil
+        int tl[6];
+        int nt = 0;
+        for (int b = -1; b <= 1; ++b) {
+            int j = j0 + b;
+            if (a.walls) {
+                if (j < 0 || j >= a.ny) continue;
+            } else {
+                j = ((j % a.ny) + a.ny) % a.ny;
+            }
+            const int tr = j / a.tile_h;
+            for (int q = -1; q <= 1; ++q) {
+                int i = i0w + q;
+                i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
+                const int t = tr * a.tiles_x + i / a.tile_w;
+                bool seen = false;
+                for (int z = 0; z < nt; ++z) seen = seen || (tl[z] == t);
+                if (!seen && nt < 6) tl[nt++] = t;
+            }
+        }
+        for (int z = 0; z < 6; ++z) {
+            const int t = z < nt ? tl[z] : -1;
+            a.vtiles[6 * (size_t)v + z] = t;
+            if (t >= 0) atomicAdd(&a.tile_count[t], 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- tile lists
+// exclusive scan of the per-tile counts (one block), resets the counts
+__global__ void k_scan_tiles(int* count, int* off, int* cursor, int ntiles) {
+    __shared__ int wsum[32];
+    const int T = blockDim.x;
+    const int per = (ntiles + T - 1) / T;
+    const int beg = threadIdx.x * per, end = min(ntiles, beg + per);
+    int s = 0;
+    for (int i = beg; i < end; ++i) s += count[i];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int v = lane < (T >> 5) ? wsum[lane] : 0;
+        int iv = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, iv, o);
+            if (lane >= o) iv += t;
+        }
+        wsum[lane] = iv - v;
+    }
+    __syncthreads();
+    int run = wsum[w] + incl - s;
+    for (int i = beg; i < end; ++i) {
+        const int c = count[i];
+        off[i] = run;
+        cursor[i] = run;
+        count[i] = 0;
+        run += c;
+    }
+    if (threadIdx.x == T - 1) off[ntiles] = run;
+}
+
+__global__ void k_fill_tiles(const int* vtiles, int nv, int* cursor, int* list_raw, int* list_tile) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    for (int z = 0; z < 6; ++z) {
+        const int t = vtiles[6 * (size_t)v + z];
+        if (t < 0) break;
+        const int p = atomicAdd(&cursor[t], 1);
+        list_raw[p] = v;
+        list_tile[p] = t;
+    }
+}
+
+// rank of each entry among its tile's entries -> ascending vertex order
+__global__ void k_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
+                             int* list_sorted, int cap, int ntiles) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cap || e >= off[ntiles]) return;
+    const int t = list_tile[e], v = list_raw[e];
+    const int beg = off[t], end = off[t + 1];
+    int rank = 0;
+    for (int q = beg; q < end; ++q) rank += list_raw[q] < v;
+    list_sorted[beg + rank] = v;
+}
+
+// ---------------------------------------------------------------- advance
+template <typename C>
+__global__ void __launch_bounds__(256) k_advance(const MarkerArgs a) {
+    const int m = blockIdx.x;
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    __shared__ double red[33];
+    const long long step = *a.d_step;
+    const C* ux = static_cast<const C*>(a.ux);
+    const C* uy = static_cast<const C*>(a.uy);
+    const C* W = static_cast<const C*>(a.W);
+    C* U = static_cast<C*>(a.U);
+    double* X = a.X;
+    double* Xp = a.Xp;
+    // interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k;
+        const int i0 = a.stencil[2 * v], j0 = a.stencil[2 * v + 1];
+        C sx = C(0), sy = C(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int j = j0 + b - 1;
+            if (a.walls) {
+                if (j < 0 || j >= a.ny) continue;
+            } else {
+                j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                int i = i0 + q - 1;
+                i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
+                const C w = W[9 * (size_t)v + b * 3 + q];
+                const size_t node = (size_t)j * a.nx + i;
+                sx += w * ux[node];
+                sy += w * uy[node];
+            }
+        }
+        U[2 * v] = sx;
+        U[2 * v + 1] = sy;
+    }
+    if (a.mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) {
+        // least-squares rigid motion U_c + omega x (x - x_c) of the ring
+        __syncthreads();
+        const double xr = X[2 * off], yr = X[2 * off + 1];
+        double sx = 0, sy = 0, su = 0, sv = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            sx += X[2 * v] - xr;
+            sy += X[2 * v + 1] - yr;
+            su += (double)U[2 * v];
+            sv += (double)U[2 * v + 1];
+        }
+        const double mx = block_sum(sx, red) / n, my = block_sum(sy, red) / n;
+        const double mu = block_sum(su, red) / n, mv = block_sum(sv, red) / n;
+        double num = 0, den = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
+            num += rx * ((double)U[2 * v + 1] - mv) - ry * ((double)U[2 * v] - mu);
+            den += rx * rx + ry * ry;
+        }
+        const double om = block_sum(num, red) / block_sum(den, red);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
+            U[2 * v] = C(mu - om * ry);
+            U[2 * v + 1] = C(mv + om * rx);
+        }
+    }
+    // Eq. kinematicPos (BDF2); forward Euler on the very first step
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k;
+        const double Ux = (double)U[2 * v], Uy = (double)U[2 * v + 1];
+        const double x = X[2 * v], y = X[2 * v + 1];
+        double xn, yn;
+        if (step == 0) {
+            xn = x + Ux;
+            yn = y + Uy;
+        } else {
+            xn = (2.0 / 3.0) * (2.0 * x - 0.5 * Xp[2 * v] + Ux);
+            yn = (2.0 / 3.0) * (2.0 * y - 0.5 * Xp[2 * v + 1] + Uy);
+        }
+        if (!isfinite(xn) || !isfinite(yn)) atomicOr(a.status, ST_NONFINITE);
+        Xp[2 * v] = x;
+        Xp[2 * v + 1] = y;
+        X[2 * v] = xn;
+        X[2 * v + 1] = yn;
+    }
+    __syncthreads();
+    // bounding boxes of this membrane's 32-vertex segments (repulsion pruning)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) {
+        const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
+        const int v = v0 + (lane < nb ? lane : 0);
+        double lo_x = X[2 * v], hi_x = lo_x, lo_y = X[2 * v + 1], hi_y = lo_y;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
+            hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
+            lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
+            hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
+        }
+        if (lane == 0) {
+            double* bx = a.seg_box + 4 * sg;
+            bx[0] = 0.5 * (lo_x + hi_x);
+            bx[1] = 0.5 * (lo_y + hi_y);
+            bx[2] = 0.5 * (hi_x - lo_x);
+            bx[3] = 0.5 * (hi_y - lo_y);
+        }
+    }
+}
+
+// segment boxes alone (before the first step)
+__global__ void k_seg_boxes(const MarkerArgs a) {
+    const int sg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (sg >= a.nseg) return;
+    const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
+    const int v = v0 + (lane < nb ? lane : 0);
+    double lo_x = a.X[2 * v], hi_x = lo_x, lo_y = a.X[2 * v + 1], hi_y = lo_y;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
+        hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
+        lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
+        hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
+    }
+    if (lane == 0) {
+        double* bx = a.seg_box + 4 * sg;
+        bx[0] = 0.5 * (lo_x + hi_x);
+        bx[1] = 0.5 * (lo_y + hi_y);
+        bx[2] = 0.5 * (hi_x - lo_x);
+        bx[3] = 0.5 * (hi_y - lo_y);
+    }
+}
+
+__global__ void k_areas(const MarkerArgs a, double* areas) {
+    const int m = blockIdx.x;
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    __shared__ double red[33];
+    const double* X = a.X;
+    const double xr = X[2 * off], yr = X[2 * off + 1];
+    double ap = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k, R = off + (k == n - 1 ? 0 : k + 1);
+        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+    }
+    const double s = block_sum(ap, red);
+    if (threadIdx.x == 0) areas[m] = 0.5 * s;
+}
+
+// ---------------------------------------------------------------- launchers
+static bool is_f64(lbib_precision p) { return p == LBIB_F64; }
+
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* l0, double* th0,
+                        double* A0, cudaStream_t s) {
+    if (is_f64(prec)) k_rest<double><<<a.nmem, 256, 0, s>>>(a, l0, th0, A0);
+    else k_rest<float><<<a.nmem, 256, 0, s>>>(a, l0, th0, A0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s) {
+    if (is_f64(prec)) {
+        const size_t sm = 6 * sizeof(double) * (size_t)max_n;
+        k_forces<double><<<a.nmem, 256, sm, s>>>(a);
+    } else {
+        const size_t sm = 6 * sizeof(float) * (size_t)max_n;
+        k_forces<float><<<a.nmem, 256, sm, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_forces_smem(lbib_precision prec, int max_n) {
+    const size_t sm = 6 * (is_f64(prec) ? sizeof(double) : sizeof(float)) * (size_t)max_n;
+    if (sm <= 48 * 1024) return cudaSuccess;
+    if (is_f64(prec))
+        return cudaFuncSetAttribute(k_forces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaFuncSetAttribute(k_forces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s) {
+    k_scan_tiles<<<1, 1024, 0, s>>>(count, off, cursor, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_tiles(const MarkerArgs& a, int* cursor, int* list_raw, int* list_tile,
+                              cudaStream_t s) {
+    k_fill_tiles<<<(a.nv + 255) / 256, 256, 0, s>>>(a.vtiles, a.nv, cursor, list_raw, list_tile);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
+                              int* list_sorted, int cap, int ntiles, cudaStream_t s) {
+    k_sort_tiles<<<(cap + 255) / 256, 256, 0, s>>>(off, list_raw, list_tile, list_sorted, cap, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
+    if (is_f64(prec)) k_advance<double><<<a.nmem, 256, 0, s>>>(a);
+    else k_advance<float><<<a.nmem, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s) {
+    if (a.nseg == 0) return cudaSuccess;
+    k_seg_boxes<<<(a.nseg + 7) / 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_areas(const MarkerArgs& a, double* areas, cudaStream_t s) {
+    k_areas<<<a.nmem, 256, 0, s>>>(a, areas);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

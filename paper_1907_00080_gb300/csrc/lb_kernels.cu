@@ -1,0 +1,411 @@
+// Lattice-Boltzmann kernels: the fused pull-stream + bounce-back + moments +
+// Guo-forced BGK collision with the IB force gathered per tile (the hot
+// kernel), and the small helpers that convert between the stored
+// post-collision deviations and user-facing populations.
+//
+// Paper: Coclite, arXiv 1907.00080, Sec. 2.1 (Eqs. BGK, feq, GaussHermite),
+// Sec. 2.2 (Eqs. forcedBGK, ForcingTerm; momentum with the half-force),
+// Sec. 3 (periodic x, no-slip walls in y).
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int IB_CHUNK = 128;   // tile-list entries staged in shared memory at a time
+
+template <typename S, int VEC>
+struct alignas(sizeof(S) * VEC) Pack {
+    S v[VEC];
+};
+
+// One IB list entry staged in shared memory: stencil origin, nine shape
+// functions and the marker force.
+template <typename C>
+struct IbEntry {
+    C w[9];
+    C fx, fy;
+    int i0, j0;
+};
+
+template <typename S, int VEC>
+__device__ __forceinline__ void load_pack(const S* __restrict__ row, int x0, bool ok, float inv,
+                                          typename Storage<S>::C (&out)[VEC]) {
+    using C = typename Storage<S>::C;
+    if (ok) {
+        const Pack<S, VEC> p = *reinterpret_cast<const Pack<S, VEC>*>(row + x0);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) out[k] = Storage<S>::load(p.v[k], inv);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) out[k] = C(0);
+    }
+}
+
+// Fused step over one tile of (32*VEC) x blockDim.y nodes.  One warp covers
+// 32*VEC consecutive x of one row, so every row predicate is warp-uniform; the
+// x-shifted pulls load aligned vectors and take the single off-vector element
+// from the neighbouring lane (or, at the warp edge, with one scalar load).
+template <typename S, int VEC, bool WALLS, bool HAS_IB>
+__global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
+    using C = typename Storage<S>::C;
+    const int lane = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x0 = (blockIdx.x * 32 + lane) * VEC;
+    const bool ok = (y < ny) && (x0 < nx);
+    const size_t N = (size_t)nx * ny;
+    const S* __restrict__ src = static_cast<const S*>(a.src);
+    const float inv = a.inv_scale;
+
+    // ---- pull streaming (Eq. BGK left side) with half-way bounce-back
+    C f[9][VEC];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int sy = y - cy(i);
+        bool bb = false;
+        if (WALLS) {
+            bb = (sy < 0) || (sy >= ny);
+        } else {
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        }
+        if (bb) {
+            // the population that left this node toward the wall comes back reversed
+            const S* row = src + (size_t)opp(i) * N + (size_t)y * nx;
+            load_pack<S, VEC>(row, x0, ok, inv, f[i]);
+            continue;
+        }
+        const S* row = src + (size_t)i * N + (size_t)sy * nx;
+        C v[VEC];
+        load_pack<S, VEC>(row, x0, ok, inv, v);
+        if (cx(i) == 0) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) f[i][k] = v[k];
+        } else if (cx(i) == 1) {
+            // needs x0-1 .. x0+VEC-2
+            C prev = __shfl_up_sync(FULL, v[VEC - 1], 1);
+            if (lane == 0 && ok) prev = Storage<S>::load(row[x0 == 0 ? nx - 1 : x0 - 1], inv);
+            f[i][0] = prev;
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) f[i][k] = v[k - 1];
+        } else {
+            // needs x0+1 .. x0+VEC
+            C next = __shfl_down_sync(FULL, v[0], 1);
+            if (ok && (lane == 31 || x0 + VEC >= nx))
+                next = Storage<S>::load(row[x0 + VEC >= nx ? 0 : x0 + VEC], inv);
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) f[i][k] = v[k + 1];
+            f[i][VEC - 1] = next;
+        }
+    }
+
+    // ---- IB spreading as a gather over this tile's vertex list (Eq. ForcingTerm's f_ib)
+    C Gx[VEC], Gy[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        Gx[k] = C(a.gx);
+        Gy[k] = C(a.gy);
+    }
+    bool flagged = false;
+    if (HAS_IB) {
+        const int t = blockIdx.y * gridDim.x + blockIdx.x;
+        const int beg = a.tile_off[t], end = a.tile_off[t + 1];
+        flagged = end > beg;
+        if (flagged) {
+            __shared__ IbEntry<C> ent[IB_CHUNK];
+            const int nthr = blockDim.x * blockDim.y;
+            const int tid = threadIdx.y * 32 + lane;
+            const C* __restrict__ W = static_cast<const C*>(a.wts);
+            const C* __restrict__ F = static_cast<const C*>(a.force);
+            for (int c0 = beg; c0 < end; c0 += IB_CHUNK) {
+                const int m = min(IB_CHUNK, end - c0);
+                __syncthreads();
+                for (int e = tid; e < m; e += nthr) {
+                    const int v = a.list[c0 + e];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) ent[e].w[q] = W[9 * (size_t)v + q];
+                    ent[e].fx = F[2 * (size_t)v];
+                    ent[e].fy = F[2 * (size_t)v + 1];
+                    ent[e].i0 = a.stencil[2 * (size_t)v];
+                    ent[e].j0 = a.stencil[2 * (size_t)v + 1];
+                }
+                __syncthreads();
+                if (ok) {
+                    for (int e = 0; e < m; ++e) {
+                        int dy = y - ent[e].j0;
+                        if (!WALLS) dy = dy > ny / 2 ? dy - ny : (dy < -(ny / 2) ? dy + ny : dy);
+                        if (dy < -1 || dy > 1) continue;
+                        const C fx = ent[e].fx, fy = ent[e].fy;
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k) {
+                            int dx = x0 + k - ent[e].i0;
+                            dx = dx > nx / 2 ? dx - nx : (dx < -(nx / 2) ? dx + nx : dx);
+                            if (dx >= -1 && dx <= 1) {
+                                const C w = ent[e].w[(dy + 1) * 3 + dx + 1];
+                                Gx[k] += w * fx;
+                                Gy[k] += w * fy;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- moments, Guo-corrected velocity, BGK collision with Guo source
+    const C om = C(a.omega);
+    const C pre = C(1) - C(0.5) * om;
+    C out[9][VEC];
+    C rho_v[VEC], ux_v[VEC], uy_v[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        C drho = C(0), jx = C(0), jy = C(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            drho += f[i][k];
+            if (cx(i) != 0) jx += C(cx(i)) * f[i][k];
+            if (cy(i) != 0) jy += C(cy(i)) * f[i][k];
+        }
+        const C rho = C(1) + drho;
+        const C rinv = C(1) / rho;
+        const C ux = (jx + C(0.5) * Gx[k]) * rinv;
+        const C uy = (jy + C(0.5) * Gy[k]) * rinv;
+        const C uu = ux * ux + uy * uy;
+        rho_v[k] = rho;
+        ux_v[k] = ux;
+        uy_v[k] = uy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const C eu = C(cx(i)) * ux + C(cy(i)) * uy;
+            const C deq = wgt<C>(i) * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
+            const C gx = C(3) * (C(cx(i)) - ux) + C(9) * eu * C(cx(i));
+            const C gy = C(3) * (C(cy(i)) - uy) + C(9) * eu * C(cy(i));
+            const C src_i = pre * wgt<C>(i) * (gx * Gx[k] + gy * Gy[k]);
+            out[i][k] = f[i][k] - om * (f[i][k] - deq) + src_i;
+        }
+    }
+
+    if (!ok) return;
+    const size_t node = (size_t)y * nx + x0;
+    if (a.fields_only) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            if (a.rho_out) a.rho_out[node + k] = (double)rho_v[k];
+            if (a.ux_out) a.ux_out[node + k] = (double)ux_v[k];
+            if (a.uy_out) a.uy_out[node + k] = (double)uy_v[k];
+        }
+        return;
+    }
+    S* __restrict__ dst = static_cast<S*>(a.dst);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        Pack<S, VEC> p;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) p.v[k] = Storage<S>::store(out[i][k], inv);
+        *reinterpret_cast<Pack<S, VEC>*>(dst + (size_t)i * N + node) = p;
+    }
+    if (HAS_IB && flagged) {
+        // velocity for the interpolation to the markers (Sec. 2.3)
+        Pack<C, VEC> pu, pv;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            pu.v[k] = ux_v[k];
+            pv.v[k] = uy_v[k];
+        }
+        *reinterpret_cast<Pack<C, VEC>*>(static_cast<C*>(a.ux) + node) = pu;
+        *reinterpret_cast<Pack<C, VEC>*>(static_cast<C*>(a.uy) + node) = pv;
+    }
+}
+
+template <typename S, int VEC>
+static cudaError_t launch_lb_t(int ty, bool walls, bool has_ib, const LbArgs& a, cudaStream_t s) {
+    dim3 block(32, ty);
+    dim3 grid((a.nx + 32 * VEC - 1) / (32 * VEC), (a.ny + ty - 1) / ty);
+    if (walls) {
+        if (has_ib) k_lb_step<S, VEC, true, true><<<grid, block, 0, s>>>(a);
+        else k_lb_step<S, VEC, true, false><<<grid, block, 0, s>>>(a);
+    } else {
+        if (has_ib) k_lb_step<S, VEC, false, true><<<grid, block, 0, s>>>(a);
+        else k_lb_step<S, VEC, false, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,
+                           const LbArgs& a, cudaStream_t s) {
+    switch (prec) {
+        case LBIB_F64:
+            if (vec == 1) return launch_lb_t<double, 1>(ty, walls, has_ib, a, s);
+            if (vec == 2) return launch_lb_t<double, 2>(ty, walls, has_ib, a, s);
+            break;
+        case LBIB_F32:
+            if (vec == 1) return launch_lb_t<float, 1>(ty, walls, has_ib, a, s);
+            if (vec == 2) return launch_lb_t<float, 2>(ty, walls, has_ib, a, s);
+            if (vec == 4) return launch_lb_t<float, 4>(ty, walls, has_ib, a, s);
+            break;
+        case LBIB_F32_STORE_F16:
+            if (vec == 2) return launch_lb_t<__half, 2>(ty, walls, has_ib, a, s);
+            if (vec == 4) return launch_lb_t<__half, 4>(ty, walls, has_ib, a, s);
+            if (vec == 8) return launch_lb_t<__half, 8>(ty, walls, has_ib, a, s);
+            break;
+        case LBIB_F32_STORE_BF16:
+            if (vec == 2) return launch_lb_t<__nv_bfloat16, 2>(ty, walls, has_ib, a, s);
+            if (vec == 4) return launch_lb_t<__nv_bfloat16, 4>(ty, walls, has_ib, a, s);
+            if (vec == 8) return launch_lb_t<__nv_bfloat16, 8>(ty, walls, has_ib, a, s);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- helpers
+
+// f^n_i(x) = w_i + d*_i(x - e_i) (or the reversed population at a wall): the
+// pre-collision populations the next step starts from, as doubles.
+template <typename S>
+__global__ void k_stream_out(const S* __restrict__ src, double* __restrict__ out, int nx, int ny,
+                             int walls, float inv) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(n / nx), x = (int)(n % nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            int sy = y - cy(i), sx = x - cx(i);
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            double d;
+            if (walls && (sy < 0 || sy >= ny)) {
+                d = (double)Storage<S>::load(src[(size_t)opp(i) * N + n], inv);
+            } else {
+                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                d = (double)Storage<S>::load(src[(size_t)i * N + (size_t)sy * nx + sx], inv);
+            }
+            out[(size_t)i * N + n] = wgt<double>(i) + d;
+        }
+    }
+}
+
+// inverse of k_stream_out: scatter f^n back to the post-collision slots it came from
+template <typename S>
+__global__ void k_stream_in(const double* __restrict__ in, S* __restrict__ dst, int nx, int ny,
+                            int walls, float inv) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(n / nx), x = (int)(n % nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double d = in[(size_t)i * N + n] - wgt<double>(i);
+            const auto sv = Storage<S>::store((typename Storage<S>::C)d, inv);
+            int sy = y - cy(i), sx = x - cx(i);
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            if (walls && (sy < 0 || sy >= ny)) {
+                dst[(size_t)opp(i) * N + n] = sv;
+            } else {
+                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                dst[(size_t)i * N + (size_t)sy * nx + sx] = sv;
+            }
+        }
+    }
+}
+
+// tau = 1 discrete Poiseuille fixed point (Sec. 3 drive): the post-collision
+// state is feq(1, u(y)) + Guo source with u(y) = G/(2 nu) (y+1/2)(NY-1/2-y) + G/4.
+template <typename S>
+__global__ void k_init_poiseuille(S* __restrict__ dst, int nx, int ny, double tau, double G, float inv) {
+    const size_t N = (size_t)nx * ny;
+    const double nu = (tau - 0.5) / 3.0;
+    const double pre = 1.0 - 0.5 / tau;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const double y = (double)(n / nx);
+        const double u = G / (2.0 * nu) * (y + 0.5) * ((double)ny - 0.5 - y) + 0.25 * G;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double eu = cx(i) * u;
+            const double deq = wgt<double>(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u);
+            const double src = pre * wgt<double>(i) * (3.0 * (cx(i) - u) + 9.0 * eu * cx(i)) * G;
+            dst[(size_t)i * N + n] = Storage<S>::store((typename Storage<S>::C)(deq + src), inv);
+        }
+    }
+}
+
+// FP64 sum of all stored deviations: per-block partials, then one block adds
+// them in a fixed order (run-to-run deterministic).
+template <typename S>
+__global__ void k_sum_dev(const S* __restrict__ src, long long n, double* partials, float inv) {
+    double acc = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        acc += (double)Storage<S>::load(src[k], inv);
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+        if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    }
+}
+
+__global__ void k_sum_partials(const double* partials, int n, double base, double* out) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(FULL, acc, o);
+        if (threadIdx.x == 0) *out = base + acc;
+    }
+}
+
+static int grid_for(size_t n, int block) {
+    size_t g = (n + block - 1) / block;
+    return (int)(g > 4096 ? 4096 : (g == 0 ? 1 : g));
+}
+
+#define LBIB_DISPATCH_S(prec, CALL)                                          \
+    switch (prec) {                                                          \
+        case LBIB_F64: { using S = double; CALL; } break;                    \
+        case LBIB_F32: { using S = float; CALL; } break;                     \
+        case LBIB_F32_STORE_F16: { using S = __half; CALL; } break;          \
+        case LBIB_F32_STORE_BF16: { using S = __nv_bfloat16; CALL; } break;  \
+        default: return cudaErrorInvalidValue;                               \
+    }
+
+cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
+                              bool walls, float inv_scale, cudaStream_t s) {
+    const int g = grid_for((size_t)nx * ny, 256);
+    LBIB_DISPATCH_S(prec, (k_stream_out<S><<<g, 256, 0, s>>>(static_cast<const S*>(src), out, nx,
+                                                              ny, walls ? 1 : 0, inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
+                             bool walls, float inv_scale, cudaStream_t s) {
+    const int g = grid_for((size_t)nx * ny, 256);
+    LBIB_DISPATCH_S(prec, (k_stream_in<S><<<g, 256, 0, s>>>(in, static_cast<S*>(dst), nx, ny,
+                                                             walls ? 1 : 0, inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int ny, double tau,
+                                   double gx, float inv_scale, cudaStream_t s) {
+    const int g = grid_for((size_t)nx * ny, 256);
+    LBIB_DISPATCH_S(prec, (k_init_poiseuille<S><<<g, 256, 0, s>>>(static_cast<S*>(dst), nx, ny,
+                                                                   tau, gx, inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
+                        int n_partials, double* out, float inv_scale, cudaStream_t s) {
+    LBIB_DISPATCH_S(prec, (k_sum_dev<S><<<n_partials, 256, 0, s>>>(static_cast<const S*>(src),
+                                                                    n_elems, partials, inv_scale)));
+    // sum_i w_i = 1 per node, so the mass is N + sum of deviations
+    k_sum_partials<<<1, 1024, 0, s>>>(partials, n_partials, (double)(n_elems / 9), out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

@@ -1,0 +1,249 @@
+// Internal declarations of the lbib CUDA library (not part of the public ABI).
+//
+// Layout in HBM (one context):
+//   populations  two buffers A/B, [9][NY][NX] of the storage type, x fastest;
+//                each holds the post-collision deviations d*_i = f*_i - w_i of
+//                one step (pull scheme: the fused kernel streams while reading)
+//   u field      ux, uy [NY][NX] of the compute type, written by the fused
+//                kernel only in tiles that IB stencils touch
+//   markers      X^n, X^{n-1} as interleaved (x, y) doubles; F^n, U^n, the nine
+//                shape-function weights and the stencil origin per vertex
+//   tile lists   per fused-kernel tile, the ids (ascending) of the vertices whose
+//                3x3 stencil touches the tile (counts, offsets, entries)
+//   adhesion     per ligand: element vertices, bond, candidate; per receptor:
+//                position, owner, claim; receptors bucketed in a uniform grid
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lbib.h"
+
+namespace lbib {
+
+// ---------------------------------------------------------------- D2Q9
+// Velocity set of Eq. GaussHermite: 0 rest; 1..4 axis (E, N, W, S);
+// 5..8 diagonals (NE, NW, SW, SE).  Weights 4/9, 1/9, 1/36.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+template <typename C>
+__host__ __device__ constexpr C wgt(int i) {
+    return i == 0 ? C(4.0 / 9.0) : (i <= 4 ? C(1.0 / 9.0) : C(1.0 / 36.0));
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "axis opposites");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagonal opposites");
+
+// ---------------------------------------------------------------- storage
+// Conversion between stored values and the compute type; 16-bit forms carry a
+// power-of-two scale (d_i * 2^k).
+template <typename S> struct Storage;
+template <> struct Storage<double> {
+    using C = double;
+    __device__ static double load(double s, float) { return s; }
+    __device__ static double store(double d, float) { return d; }
+};
+template <> struct Storage<float> {
+    using C = float;
+    __device__ static float load(float s, float) { return s; }
+    __device__ static float store(float d, float) { return d; }
+};
+template <> struct Storage<__half> {
+    using C = float;
+    __device__ static float load(__half s, float inv) { return __half2float(s) * inv; }
+    __device__ static __half store(float d, float inv) { return __float2half_rn(d / inv); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using C = float;
+    __device__ static float load(__nv_bfloat16 s, float inv) { return __bfloat162float(s) * inv; }
+    __device__ static __nv_bfloat16 store(float d, float inv) { return __float2bfloat16_rn(d / inv); }
+};
+
+// ---------------------------------------------------------------- kernel args
+struct LbArgs {
+    const void* src;       // post-collision deviations of step n-1
+    void* dst;             // post-collision deviations of step n
+    void* ux;              // u field (compute type), written in flagged tiles
+    void* uy;
+    double* rho_out;       // fields mode: rho, ux, uy as doubles (may be null)
+    double* ux_out;
+    double* uy_out;
+    const int* tile_off;   // [ntiles + 1]
+    const int* list;       // sorted vertex ids per tile
+    const void* wts;       // [nv][9] shape functions in the compute type
+    const int* stencil;    // [nv][2] i0 (wrapped to [0,nx)), j0
+    const void* force;     // [nv][2] F^n in the compute type
+    int nx, ny;
+    double omega;          // 1/tau
+    double gx, gy;         // body force
+    float inv_scale;       // 2^-k for 16-bit storage, 1 otherwise
+    int fields_only;       // 1: write rho/ux/uy doubles, skip populations
+};
+
+struct MarkerArgs {
+    int nx, ny, walls;
+    int nmem, nv;
+    const int* mem_off;
+    const int* mem_n;
+    const int* mem_kind;
+    const double* mem_ks;
+    const double* mem_kb;
+    const double* mem_ka;
+    const double* mem_A0;
+    const int* mem_lig_off;   // ligands of membrane m: [lig_off[m], lig_off[m+1])
+    double* X;                // [nv][2] current positions (unwrapped)
+    double* Xp;               // [nv][2] previous positions
+    void* F;                  // [nv][2] compute type
+    void* U;                  // [nv][2] compute type
+    void* W;                  // [nv][9] compute type
+    int* stencil;             // [nv][2]
+    int* vtiles;              // [nv][6] touched tiles (-1 padded)
+    const double* l0;         // [nv] rest length of element (v, v+1)
+    const double* th0;        // [nv] rest turning angle at v
+    const int* elem_lig;      // [nv] ligand on element (v, v+1) or -1
+    // repulsion
+    double d_rep;
+    int nseg;
+    const int* seg_mem;       // [nseg]
+    const int* seg_v0;        // [nseg] first global vertex
+    const int* seg_n;         // [nseg]
+    double* seg_box;          // [nseg][4] cx, cy, hx, hy
+    const int* mem_seg_off;   // segments of membrane m: [mem_seg_off[m], mem_seg_off[m+1])
+    // bonds
+    int nlig, nrec;
+    const int* lig_a;         // [nlig] first vertex of the ligand element
+    const int* lig_b;         // [nlig] second vertex
+    int* bond_of_lig;         // [nlig]
+    int* cand;                // [nlig]
+    int* rupt;                // [nlig]
+    const double* rec_xy;     // [nrec][2]
+    int* owner;               // [nrec]
+    int* claim;               // [nrec]
+    const int* rcell_start;   // [ncell + 1]
+    const int* rcell_ids;     // [nrec]
+    int rc_nx, rc_ny;         // receptor grid
+    double rc_w, rc_h, rc_y0; // cell size, y origin
+    double sigma, y_eq, d_cut, d_break, kf_dt, kr0_dt, beta_f, beta_r;
+    uint64_t seed, instance;
+    // tiles
+    int tile_w, tile_h, tiles_x, tiles_y;
+    int* tile_count;
+    // step counter and status
+    long long* d_step;
+    int* status;
+    int bump_in_advance;
+    // u field (compute type)
+    const void* ux;
+    const void* uy;
+};
+
+enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2 };
+
+// ---------------------------------------------------------------- launchers
+// lb_kernels.cu
+cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,
+                           const LbArgs& a, cudaStream_t s);
+cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
+                              bool walls, float inv_scale, cudaStream_t s);
+cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
+                             bool walls, float inv_scale, cudaStream_t s);
+cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int ny, double tau,
+                                   double gx, float inv_scale, cudaStream_t s);
+cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
+                        int n_partials, double* out, float inv_scale, cudaStream_t s);
+// ib_kernels.cu
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* l0, double* th0,
+                        double* A0, cudaStream_t s);
+cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
+cudaError_t set_forces_smem(lbib_precision prec, int max_n);
+cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s);
+cudaError_t launch_fill_tiles(const MarkerArgs& a, int* cursor, int* list_raw, int* list_tile,
+                              cudaStream_t s);
+cudaError_t launch_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
+                              int* list_sorted, int cap, int ntiles, cudaStream_t s);
+cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
+cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s);
+cudaError_t launch_areas(const MarkerArgs& a, double* areas, cudaStream_t s);
+// bond_kernels.cu
+cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s);
+int bond_kernel_count(const MarkerArgs& a);
+
+}  // namespace lbib
+
+// ---------------------------------------------------------------- context
+struct lbib_ctx {
+    int nx = 0, ny = 0;
+    lbib_precision prec = LBIB_F32;
+    lbib_init init = LBIB_INIT_REST;
+    double tau = 1.0, gx = 0.0, gy = 0.0;
+    lbib_walls walls = LBIB_WALLS_Y_BOUNCEBACK;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t pop_elem = 4;      // bytes per stored population
+    size_t cmp_elem = 4;      // bytes per compute-type value
+    int scale_exp = 0;        // 16-bit storage scale 2^k
+    float inv_scale = 1.0f;
+
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;              // buffer holding d*^{n-1}
+    void* ux = nullptr;
+    void* uy = nullptr;
+    double* stage = nullptr;  // 9*N doubles, lazily allocated for read/write
+    double* partials = nullptr;
+    double* dscalar = nullptr; // small device scratch for results
+    int n_partials = 0;
+
+    int vec = 0, ty = 0;      // tiling of the fused kernel
+    int tile_w = 0, tile_h = 0, tiles_x = 0, tiles_y = 0, ntiles = 0;
+
+    // host-side membrane staging
+    std::vector<double> h_xy;
+    std::vector<int> h_mem_off, h_mem_n, h_mem_kind, h_lig_elem_local, h_mem_lig_off;
+    std::vector<double> h_ks, h_kb, h_ka;
+    int nmem = 0, nv = 0, nlig = 0;
+    // receptors
+    std::vector<double> h_rec;
+    lbib_bond_params bp{};
+    bool have_receptors = false;
+    double d_rep = 2.0;
+
+    // device marker state (allocated at finalize)
+    bool finalized = false;
+    int max_mem_n = 0;
+    int nseg = 0;
+    int list_cap = 0;
+    void* dmem = nullptr;     // one arena for all marker/tile/bond arrays
+    size_t dmem_bytes = 0;
+    lbib::MarkerArgs ma{};
+    int* tile_count = nullptr;
+    int* tile_off = nullptr;
+    int* tile_cursor = nullptr;
+    int* list_raw = nullptr;
+    int* list_tile = nullptr;
+    int* list_sorted = nullptr;
+    double* d_areas = nullptr;
+
+    long long* d_step = nullptr;
+    int* d_status = nullptr;
+    long long steps = 0;
+    bool fields_valid = false;
+    bool poisoned = false;
+
+    // captured step graphs: [start buffer][0: one step, 1: chunk of kChunk steps]
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool graphs_ready = false;
+
+    std::string err;
+};

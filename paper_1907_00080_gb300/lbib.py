@@ -1,0 +1,339 @@
+"""Thin ctypes binding of the lbib C ABI (include/lbib.h).
+
+Functions keep the C names and only marshal arguments: every step of the
+time integration runs in the CUDA kernels of ``liblbib.so``.  A missing
+library raises immediately; there is no CPU fallback.  Device pointers may be
+passed as integers (e.g. ``torch.Tensor.data_ptr()``) with ``on_device=1``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbib.so")
+
+# enums (mirror include/lbib.h)
+LBIB_OK, LBIB_E_INVALID, LBIB_E_CUDA, LBIB_E_OOM, LBIB_E_TIMEOUT, LBIB_E_NONFINITE, LBIB_E_STATE = range(7)
+LBIB_F64, LBIB_F32, LBIB_F32_STORE_F16, LBIB_F32_STORE_BF16 = range(4)
+LBIB_WALLS_NONE, LBIB_WALLS_Y_BOUNCEBACK = 0, 1
+LBIB_INIT_REST, LBIB_INIT_POISEUILLE = 0, 1
+LBIB_MEMBRANE_KINEMATIC, LBIB_MEMBRANE_RIGID_PROJECTED = 0, 1
+
+PRECISIONS = {"f64": LBIB_F64, "f32": LBIB_F32, "f16": LBIB_F32_STORE_F16, "bf16": LBIB_F32_STORE_BF16}
+STATUS_NAMES = {0: "LBIB_OK", 1: "LBIB_E_INVALID", 2: "LBIB_E_CUDA", 3: "LBIB_E_OOM",
+                4: "LBIB_E_TIMEOUT", 5: "LBIB_E_NONFINITE", 6: "LBIB_E_STATE"}
+
+
+class lbib_lattice(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("prec", ctypes.c_int),
+                ("init", ctypes.c_int)]
+
+
+class lbib_bond_params(ctypes.Structure):
+    _fields_ = [("d_cut", ctypes.c_double), ("y_eq", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("kf_dt", ctypes.c_double), ("kr0_dt", ctypes.c_double), ("beta_f", ctypes.c_double),
+                ("beta_r", ctypes.c_double), ("d_break", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("instance", ctypes.c_uint64)]
+
+
+class LbibError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_DP = ctypes.POINTER(ctypes.c_double)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "lbib_create": (_I, [ctypes.POINTER(lbib_lattice), _D, _DP, _I, _P, ctypes.POINTER(_P)]),
+    "lbib_add_membrane": (_I, [_P, _DP, _I32, _D, _D, _D, _I, _I32P, _I32, _I32P]),
+    "lbib_set_receptors": (_I, [_P, _DP, _I32, ctypes.POINTER(lbib_bond_params)]),
+    "lbib_set_repulsion": (_I, [_P, _D]),
+    "lbib_step": (_I, [_P, _I64]),
+    "lbib_sync": (_I, [_P]),
+    "lbib_step_count": (_I64, [_P]),
+    "lbib_read_fields": (_I, [_P, _P, _P, _P, _I]),
+    "lbib_read_populations": (_I, [_P, _P, _I]),
+    "lbib_write_populations": (_I, [_P, _P, _I]),
+    "lbib_read_markers": (_I, [_P, _I32, _DP]),
+    "lbib_write_markers": (_I, [_P, _DP, _DP]),
+    "lbib_read_marker_forces": (_I, [_P, _DP]),
+    "lbib_read_marker_velocity": (_I, [_P, _DP]),
+    "lbib_read_bonds": (_I, [_P, _I32P, _I32P, _I32, _I32P]),
+    "lbib_diagnostics": (_I, [_P, _DP, _DP]),
+    "lbib_set_tiling": (_I, [_P, _I32, _I32]),
+    "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
+    "lbib_profile_fused": (_I, [_P, _I32, _DP]),
+    "lbib_kernels_per_step": (_I32, [_P]),
+    "lbib_storage_scale_exponent": (_I32, [_P]),
+    "lbib_last_error": (ctypes.c_char_p, [_P]),
+    "lbib_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbib.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("liblbib.so is not built: run __graft_entry__.build() "
+                               "(or python -m paper_1907_00080_gb300.build)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, st):
+    if st != LBIB_OK:
+        msg = load().lbib_last_error(ctx).decode() if ctx else ""
+        raise LbibError(st, msg)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ptr(x):
+    """host numpy array -> pointer; int -> device address; None -> NULL"""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ C names
+def lbib_create(nx, ny, prec=LBIB_F32, init=LBIB_INIT_REST, tau=1.0, body_force=(0.0, 0.0),
+                walls=LBIB_WALLS_Y_BOUNCEBACK, cuda_stream=None):
+    lat = lbib_lattice(int(nx), int(ny), int(prec), int(init))
+    bf = (ctypes.c_double * 2)(float(body_force[0]), float(body_force[1]))
+    out = _P()
+    st = load().lbib_create(ctypes.byref(lat), float(tau), bf, int(walls),
+                            None if cuda_stream is None else ctypes.c_void_p(int(cuda_stream)),
+                            ctypes.byref(out))
+    if st != LBIB_OK:
+        raise LbibError(st, "lbib_create(%d, %d) failed" % (nx, ny))
+    return out
+
+
+def lbib_add_membrane(ctx, xy, k_s, k_b, k_area, kind=LBIB_MEMBRANE_KINEMATIC, ligand_elems=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    lig = np.ascontiguousarray(ligand_elems if ligand_elems is not None else [], dtype=np.int32)
+    mid = _I32()
+    st = load().lbib_add_membrane(ctx, _dptr(xy), len(xy), float(k_s), float(k_b), float(k_area),
+                                  int(kind), lig.ctypes.data_as(_I32P) if len(lig) else None,
+                                  len(lig), ctypes.byref(mid))
+    _check(ctx, st)
+    return mid.value
+
+
+def lbib_set_receptors(ctx, xy, d_cut=1.5, y_eq=0.75, sigma=0.0, kf_dt=1e-2, kr0_dt=1e-2 / 8.5e3,
+                       beta_f=0.5, beta_r=2.0, d_break=3.0, seed=0, instance=0):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+    p = lbib_bond_params(d_cut, y_eq, sigma, kf_dt, kr0_dt, beta_f, beta_r, d_break, int(seed), int(instance))
+    _check(ctx, load().lbib_set_receptors(ctx, _dptr(xy), len(xy), ctypes.byref(p)))
+
+
+def lbib_set_repulsion(ctx, d_rep):
+    _check(ctx, load().lbib_set_repulsion(ctx, float(d_rep)))
+
+
+def lbib_step(ctx, n):
+    _check(ctx, load().lbib_step(ctx, int(n)))
+
+
+def lbib_sync(ctx):
+    _check(ctx, load().lbib_sync(ctx))
+
+
+def lbib_step_count(ctx):
+    return load().lbib_step_count(ctx)
+
+
+def lbib_read_fields(ctx, rho=None, ux=None, uy=None, on_device=0):
+    _check(ctx, load().lbib_read_fields(ctx, _ptr(rho), _ptr(ux), _ptr(uy), int(on_device)))
+
+
+def lbib_read_populations(ctx, f, on_device=0):
+    _check(ctx, load().lbib_read_populations(ctx, _ptr(f), int(on_device)))
+
+
+def lbib_write_populations(ctx, f, on_device=0):
+    _check(ctx, load().lbib_write_populations(ctx, _ptr(f), int(on_device)))
+
+
+def lbib_read_markers(ctx, membrane_id, xy):
+    _check(ctx, load().lbib_read_markers(ctx, int(membrane_id), _dptr(xy)))
+
+
+def lbib_write_markers(ctx, xy, xy_prev=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    xp = None if xy_prev is None else _dptr(np.ascontiguousarray(xy_prev, dtype=np.float64))
+    _check(ctx, load().lbib_write_markers(ctx, _dptr(xy), xp))
+
+
+def lbib_read_marker_forces(ctx, fxy):
+    _check(ctx, load().lbib_read_marker_forces(ctx, _dptr(fxy)))
+
+
+def lbib_read_marker_velocity(ctx, uxy):
+    _check(ctx, load().lbib_read_marker_velocity(ctx, _dptr(uxy)))
+
+
+def lbib_read_bonds(ctx, cap):
+    lig = np.zeros(max(cap, 1), dtype=np.int32)
+    rec = np.zeros(max(cap, 1), dtype=np.int32)
+    n = _I32()
+    _check(ctx, load().lbib_read_bonds(ctx, lig.ctypes.data_as(_I32P), rec.ctypes.data_as(_I32P),
+                                       int(cap), ctypes.byref(n)))
+    k = min(n.value, cap)
+    return lig[:k].copy(), rec[:k].copy(), n.value
+
+
+def lbib_diagnostics(ctx, n_membranes=0):
+    mass = np.zeros(1)
+    areas = np.zeros(max(n_membranes, 1))
+    _check(ctx, load().lbib_diagnostics(ctx, _dptr(mass), _dptr(areas) if n_membranes else None))
+    return float(mass[0]), areas[:n_membranes]
+
+
+def lbib_set_tiling(ctx, vec, ty):
+    _check(ctx, load().lbib_set_tiling(ctx, int(vec), int(ty)))
+
+
+def lbib_get_tiling(ctx):
+    v, t = _I32(), _I32()
+    _check(ctx, load().lbib_get_tiling(ctx, ctypes.byref(v), ctypes.byref(t)))
+    return v.value, t.value
+
+
+def lbib_profile_fused(ctx, reps):
+    ms = np.zeros(1)
+    _check(ctx, load().lbib_profile_fused(ctx, int(reps), _dptr(ms)))
+    return float(ms[0])
+
+
+def lbib_kernels_per_step(ctx):
+    return load().lbib_kernels_per_step(ctx)
+
+
+def lbib_storage_scale_exponent(ctx):
+    return load().lbib_storage_scale_exponent(ctx)
+
+
+def lbib_last_error(ctx):
+    return load().lbib_last_error(ctx).decode()
+
+
+def lbib_destroy(ctx):
+    if ctx:
+        load().lbib_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience
+class Simulation:
+    """Owns one lbib context built from an ``inputs.Workload`` (marshalling only)."""
+
+    def __init__(self, wl, precision=None, tiling=None, cuda_stream=None):
+        prec = PRECISIONS[precision or wl.precision]
+        init = LBIB_INIT_POISEUILLE if wl.init == "poiseuille" else LBIB_INIT_REST
+        self.wl = wl
+        self.nx, self.ny = wl.nx, wl.ny
+        self.ctx = lbib_create(wl.nx, wl.ny, prec, init, wl.tau, wl.body_force, wl.walls, cuda_stream)
+        self.mem_sizes = []
+        for m in wl.membranes:
+            lbib_add_membrane(self.ctx, m.xy, m.ks, m.kb, m.ka, m.kind, m.ligands)
+            self.mem_sizes.append(len(m.xy))
+        self.nv = sum(self.mem_sizes)
+        self.nlig = wl.n_ligands
+        if wl.receptors is not None and len(wl.receptors):
+            b = wl.bonds
+            lbib_set_receptors(self.ctx, wl.receptors, d_cut=b["d_cut"], y_eq=b["y_eq"],
+                               sigma=wl.sigma_lu, kf_dt=b["kf_dt"], kr0_dt=b["kr0_dt"],
+                               beta_f=b["beta_f"], beta_r=b["beta_r"], d_break=b["d_break"],
+                               seed=wl.seed, instance=wl.instance)
+        lbib_set_repulsion(self.ctx, wl.d_rep)
+        if tiling is not None:
+            lbib_set_tiling(self.ctx, *tiling)
+
+    def close(self):
+        if self.ctx:
+            lbib_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbib_step(self.ctx, n)
+
+    def sync(self):
+        lbib_sync(self.ctx)
+
+    def fields(self):
+        r, a, b = (np.zeros((self.ny, self.nx)) for _ in range(3))
+        lbib_read_fields(self.ctx, r, a, b)
+        return r, a, b
+
+    def populations(self):
+        f = np.zeros((9, self.ny, self.nx))
+        lbib_read_populations(self.ctx, f)
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
+        lbib_write_populations(self.ctx, f)
+
+    def markers(self):
+        xy = np.zeros((self.nv, 2))
+        if self.nv:
+            lbib_read_markers(self.ctx, -1, xy)
+        return xy
+
+    def forces(self):
+        f = np.zeros((self.nv, 2))
+        if self.nv:
+            lbib_read_marker_forces(self.ctx, f)
+        return f
+
+    def marker_velocity(self):
+        u = np.zeros((self.nv, 2))
+        if self.nv:
+            lbib_read_marker_velocity(self.ctx, u)
+        return u
+
+    def bonds(self):
+        """bond_of_ligand array (-1 = free), like the oracle's"""
+        lig, rec, n = lbib_read_bonds(self.ctx, self.nlig)
+        out = -np.ones(self.nlig, dtype=np.int32)
+        out[lig] = rec
+        return out
+
+    def diagnostics(self):
+        return lbib_diagnostics(self.ctx, len(self.mem_sizes))
+
+    @property
+    def tiling(self):
+        return lbib_get_tiling(self.ctx)
+
+    @property
+    def kernels_per_step(self):
+        return lbib_kernels_per_step(self.ctx)
