@@ -69,6 +69,7 @@ __global__ void k_bonds_decide(const MarkerArgs a) {
     const int va = a.lig_a[l], vb = a.lig_b[l];
     const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
     const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
+    if (!isfinite(cxp) || !isfinite(cyp)) return;  // reported by the advance kernel
     int r = a.bond_of_lig[l];
     if (r >= 0) {
         const double d = lig_rec_dist(a, cxp, cyp, r);

@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
 
         // ---- IB shape functions at X^n: nine nearest nodes, Roma weights,
         // MLS (basis 1, dx, dy) re-solved where wall rows drop out
-        const double fi0 = floor(xv + 0.5), fj0 = floor(yv + 0.5);
+        // clamped so that a runaway (or NaN) position still yields in-range integers;
+        // the advance kernel flags non-finite positions
+        const double fi0 = fmin(fmax(floor(xv + 0.5), -1.0e9), 1.0e9);
+        const double fj0 = fmin(fmax(floor(yv + 0.5), -1.0e6), 1.0e6);
         const long long i0 = (long long)fi0;
         const int j0 = (int)fj0;
         C rx[3], ry[3], wx[3], wy[3];
