@@ -82,7 +82,8 @@ def test_poiseuille_fixed_point_on_gpu(prec):
     assert rel_err(ux, ux0) < TOL[prec]["field"]
     yy = np.arange(ny)
     closed = 3 * g * (yy + 0.5) * (ny - 0.5 - yy) + 0.25 * g
-    assert np.max(np.abs(ux - closed[:, None])) / closed.max() < (1e-12 if prec == "f64" else 1e-6)
+    # FP32 stores the deviations of f from w_i; u then carries ~1e-6 relative rounding
+    assert np.max(np.abs(ux - closed[:, None])) / closed.max() < (1e-12 if prec == "f64" else 5e-6)
 
 
 def test_tilings_agree_bitwise():
