@@ -329,8 +329,8 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * (nm + 1)); add(4 * (nm + 1)); add(4 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1));
         add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
         add(16 * nv); add(16 * nv); add(2 * cs * nv); add(2 * cs * nv); add(9 * cs * nv); add(8 * nv);
-        add(24 * nv); add(8 * nv); add(8 * nv); add(4 * nv);
-        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(32 * c->nseg); add(4 * (nm + 1));
+        add(24 * nv); add(32 * nv); add(4 * nv);
+        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
         add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
         add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
         add(4 * c->ntiles); add(4 * (c->ntiles + 1)); add(4 * c->ntiles);
@@ -346,6 +346,7 @@ static lbib_status finalize(lbib_ctx* c) {
     MarkerArgs& a = c->ma;
     a = MarkerArgs{};
     a.nx = c->nx; a.ny = c->ny; a.walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK ? 1 : 0;
+    a.inv_nx = 1.0 / c->nx; a.inv_ny = 1.0 / c->ny;
     a.nmem = nm; a.nv = nv;
     int* mem_off = ar.take<int>(nm + 1);
     int* mem_n = ar.take<int>(nm + 1);
@@ -362,13 +363,12 @@ static lbib_status finalize(lbib_ctx* c) {
     a.W = ar.take<char>(9 * cs * nv);
     a.stencil = ar.take<int>(2 * (size_t)nv);
     a.vtiles = ar.take<int>(6 * (size_t)nv);
-    double* l0 = ar.take<double>(nv);
-    double* th0 = ar.take<double>(nv);
+    double* rest = ar.take<double>(4 * (size_t)nv);
     int* elig = ar.take<int>(nv);
     int* d_seg_mem = ar.take<int>(c->nseg);
     int* d_seg_v0 = ar.take<int>(c->nseg);
     int* d_seg_n = ar.take<int>(c->nseg);
-    a.seg_box = ar.take<double>(4 * (size_t)c->nseg);
+    a.seg_box = ar.take<float4>(c->nseg);
     int* d_mem_seg_off = ar.take<int>(nm + 1);
     int* d_lig_a = ar.take<int>(nl);
     int* d_lig_b = ar.take<int>(nl);
@@ -431,7 +431,7 @@ static lbib_status finalize(lbib_ctx* c) {
 
     a.mem_off = mem_off; a.mem_n = mem_n; a.mem_kind = mem_kind;
     a.mem_ks = ks; a.mem_kb = kb; a.mem_ka = ka; a.mem_A0 = A0; a.mem_lig_off = lig_off;
-    a.l0 = l0; a.th0 = th0; a.elem_lig = elig;
+    a.rest = rest; a.elem_lig = elig;
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
@@ -446,7 +446,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.ux = c->ux; a.uy = c->uy;
 
     if (nm > 0) {
-        CK(launch_rest(c->prec, a, l0, th0, A0, c->stream));
+        CK(launch_rest(c->prec, a, rest, A0, c->stream));
         CK(launch_seg_boxes(a, c->stream));
         CK(set_forces_smem(c->prec, c->max_mem_n));
     }

@@ -51,12 +51,13 @@ __device__ __forceinline__ double p_rupture(const MarkerArgs& a, double d) {
     return 1.0 - exp(-a.kr0_dt * exp(a.beta_r * z * z));
 }
 
-__device__ __forceinline__ double wrapd(double d, double L) { return d - L * floor(d / L + 0.5); }
+// periodic minimum image (multiplication by 1/L: no FP64 division)
+__device__ __forceinline__ double wrapd(double d, double L, double invL) { return d - L * floor(d * invL + 0.5); }
 
 __device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, double cyp, int r) {
-    const double dx = wrapd(a.rec_xy[2 * r] - cxp, (double)a.nx);
+    const double dx = wrapd(a.rec_xy[2 * r] - cxp, (double)a.nx, a.inv_nx);
     double dy = a.rec_xy[2 * r + 1] - cyp;
-    if (!a.walls) dy = wrapd(dy, (double)a.ny);
+    if (!a.walls) dy = wrapd(dy, (double)a.ny, a.inv_ny);
     return sqrt(dx * dx + dy * dy);
 }
 
@@ -80,7 +81,7 @@ __global__ void k_bonds_decide(const MarkerArgs a) {
         a.bond_of_lig[l] = -1;
     }
     // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
-    const double xw = cxp - (double)a.nx * floor(cxp / (double)a.nx);
+    const double xw = cxp - (double)a.nx * floor(cxp * a.inv_nx);
     int gx = (int)floor(xw / a.rc_w);
     gx = gx >= a.rc_nx ? a.rc_nx - 1 : gx;
     const int gy = (int)floor((cyp - a.rc_y0) / a.rc_h);

@@ -13,7 +13,14 @@ namespace lbib {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-__device__ __forceinline__ double wrap_d(double d, double L) { return d - L * floor(d / L + 0.5); }
+// periodic minimum image, multiplying by 1/L (an FP64 division is a long
+// instruction sequence on this part)
+__device__ __forceinline__ double wrap_m(double d, double L, double invL) {
+    return d - L * floor(d * invL + 0.5);
+}
+__device__ __forceinline__ float wrap_half(float d, float L) {
+    return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+}
 
 // Roma, Peskin & Berger three-point regularised delta
 template <typename C>
@@ -27,27 +34,22 @@ __device__ __forceinline__ C roma(C r) {
     return C(0);
 }
 
-// Signed turning angle at a vertex, outward unit normal (normalised sum of the
-// two adjacent outward edge normals of a CCW ring) and the two edge lengths.
-template <typename C>
-struct VGeom {
-    C th, nx, ny, lL, lR;
+// Edge products at a vertex, in FP64 with every product and sum rounded as
+// written (no contraction), so the rest shape reproduces them bit for bit:
+// squared length of e_R = x_{v+1} - x_v, cross and dot of e_L = x_v - x_{v-1}
+// with e_R.
+struct EdgeProducts {
+    double lsqR, cross, dot;
 };
-
-template <typename C>
-__device__ __forceinline__ VGeom<C> vertex_geom(double xL, double yL, double xv, double yv,
-                                                double xR, double yR) {
-    const C eLx = C(xv - xL), eLy = C(yv - yL), eRx = C(xR - xv), eRy = C(yR - yv);
-    VGeom<C> g;
-    g.lL = sqrt(eLx * eLx + eLy * eLy);
-    g.lR = sqrt(eRx * eRx + eRy * eRy);
-    g.th = atan2(eLx * eRy - eLy * eRx, eLx * eRx + eLy * eRy);
-    C nx = eLy / g.lL + eRy / g.lR;
-    C ny = -eLx / g.lL - eRx / g.lR;
-    const C nn = sqrt(nx * nx + ny * ny);
-    g.nx = nx / nn;
-    g.ny = ny / nn;
-    return g;
+__device__ __forceinline__ EdgeProducts edge_products(double xL, double yL, double xv, double yv,
+                                                      double xR, double yR) {
+    const double eLx = __dsub_rn(xv, xL), eLy = __dsub_rn(yv, yL);
+    const double eRx = __dsub_rn(xR, xv), eRy = __dsub_rn(yR, yv);
+    EdgeProducts p;
+    p.lsqR = __dadd_rn(__dmul_rn(eRx, eRx), __dmul_rn(eRy, eRy));
+    p.cross = __dsub_rn(__dmul_rn(eLx, eRy), __dmul_rn(eLy, eRx));
+    p.dot = __dadd_rn(__dmul_rn(eLx, eRx), __dmul_rn(eLy, eRy));
+    return p;
 }
 
 // block-wide FP64 sum (blockDim multiple of 32, <= 1024); all threads get it
@@ -67,10 +69,11 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- rest state
-// Captures l_0, theta_0 (with the same arithmetic the force kernel uses, so
-// the rest shape gives exactly zero force) and A_0 per membrane.
-template <typename C>
-__global__ void k_rest(const MarkerArgs a, double* l0, double* th0, double* A0) {
+// Captures, per vertex, the squared and plain rest length of the element
+// (v, v+1) and the rest cross/dot products of the two edges at v (which fix the
+// rest turning angle theta_0), plus A_0 per membrane -- with the arithmetic the
+// force kernel repeats, so the rest shape gives exactly zero force.
+__global__ void k_rest(const MarkerArgs a, double* rest, double* A0) {
     const int m = blockIdx.x;
     const int off = a.mem_off[m], n = a.mem_n[m];
     __shared__ double red[33];
@@ -79,10 +82,12 @@ __global__ void k_rest(const MarkerArgs a, double* l0, double* th0, double* A0) 
     double ap = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
-        const VGeom<C> g = vertex_geom<C>(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1], X[2 * R],
-                                          X[2 * R + 1]);
-        th0[v] = (double)g.th;
-        l0[v] = (double)g.lR;
+        const EdgeProducts p = edge_products(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1],
+                                             X[2 * R], X[2 * R + 1]);
+        rest[4 * (size_t)v + 0] = p.lsqR;
+        rest[4 * (size_t)v + 1] = sqrt(p.lsqR);
+        rest[4 * (size_t)v + 2] = p.cross;
+        rest[4 * (size_t)v + 3] = p.dot;
         ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
     }
     const double s = block_sum(ap, red);
@@ -100,9 +105,9 @@ __device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, doub
     const int va = a.lig_a[l], vb = a.lig_b[l];
     const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
     const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
-    const double dx = wrap_d(a.rec_xy[2 * r] - cxp, nxd);
+    const double dx = wrap_m(a.rec_xy[2 * r] - cxp, nxd, a.inv_nx);
     double dy = a.rec_xy[2 * r + 1] - cyp;
-    if (!a.walls) dy = wrap_d(dy, nyd);
+    if (!a.walls) dy = wrap_m(dy, nyd, a.inv_ny);
     const double d = sqrt(dx * dx + dy * dy);
     const double c = a.sigma * (d - a.y_eq) / d;
     Fx += C(0.5 * c * dx);
@@ -126,20 +131,36 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
     const double xr = X[2 * off], yr = X[2 * off + 1];
     const C kb = C(a.mem_kb[m]);
 
-    // pass 1: vertex geometry (bending) and the shoelace area about vertex 0
+    // pass 1: vertex geometry (bending) and the shoelace area about vertex 0.
+    // theta - theta_0 comes from the rotation between the rest and the current
+    // edge pair, atan2(c d0 - d c0, d d0 + c c0), free of the cancellation of
+    // subtracting two nearly equal angles.
     double ap = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
-        const VGeom<C> g = vertex_geom<C>(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1], X[2 * R],
-                                          X[2 * R + 1]);
-        const C mb = kb * (g.th - C(a.th0[v]));
-        s_mnx[k] = mb * g.nx;
-        s_mny[k] = mb * g.ny;
-        s_sL[k] = g.lL / (g.lL + g.lR);
-        s_sR[k] = g.lR / (g.lL + g.lR);
-        s_nx[k] = g.nx;
-        s_ny[k] = g.ny;
-        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+        const double xL = X[2 * L], yL = X[2 * L + 1], xv = X[2 * v], yv = X[2 * v + 1];
+        const double xR = X[2 * R], yR = X[2 * R + 1];
+        const EdgeProducts p = edge_products(xL, yL, xv, yv, xR, yR);
+        const double c0 = a.rest[4 * (size_t)v + 2], d0 = a.rest[4 * (size_t)v + 3];
+        const double sn = __dsub_rn(__dmul_rn(p.cross, d0), __dmul_rn(p.dot, c0));
+        const double cs = __dadd_rn(__dmul_rn(p.dot, d0), __dmul_rn(p.cross, c0));
+        const C dth = atan2(C(sn), C(cs));
+        const C eLx = C(xv - xL), eLy = C(yv - yL), eRx = C(xR - xv), eRy = C(yR - yv);
+        const C lL = sqrt(eLx * eLx + eLy * eLy), lR = sqrt(eRx * eRx + eRy * eRy);
+        // outward vertex normal: normalised sum of the outward edge normals (CCW ring)
+        C nx_ = eLy / lL + eRy / lR;
+        C ny_ = -eLx / lL - eRx / lR;
+        const C nn = sqrt(nx_ * nx_ + ny_ * ny_);
+        nx_ /= nn;
+        ny_ /= nn;
+        const C mb = kb * dth;
+        s_mnx[k] = mb * nx_;
+        s_mny[k] = mb * ny_;
+        s_sL[k] = lL / (lL + lR);
+        s_sR[k] = lR / (lL + lR);
+        s_nx[k] = nx_;
+        s_ny[k] = ny_;
+        ap += (xv - xr) * (yR - yr) - (xR - xr) * (yv - yr);
     }
     const double A = 0.5 * block_sum(ap, red);  // includes a __syncthreads
     // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
@@ -169,20 +190,26 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
             bond_on_element<C>(a, L, nxd, nyd, Fx, Fy);
             bond_on_element<C>(a, v, nxd, nyd, Fx, Fy);
         }
-        // Eq. repFor against vertices of other membranes closer than d_rep
+        // Eq. repFor against vertices of other membranes closer than d_rep:
+        // segment boxes are screened in FP32 (wrapped x), close pairs in FP64
         if (a.nmem > 1) {
+            const float Lx = float(a.nx), Ly = float(a.ny);
+            const float xvw = float(xv - nxd * floor(xv * a.inv_nx));
+            const float yvf = float(yv);
+            const float reach = float(a.d_rep) + 1e-3f;
             for (int sg = 0; sg < a.nseg; ++sg) {
                 if (a.seg_mem[sg] == m) continue;
-                const double* bx = a.seg_box + 4 * sg;
-                double ddx = wrap_d(xv - bx[0], nxd);
-                double ddy = yv - bx[1];
-                if (!a.walls) ddy = wrap_d(ddy, nyd);
-                if (fabs(ddx) > bx[2] + a.d_rep || fabs(ddy) > bx[3] + a.d_rep) continue;
+                const float4 bx = a.seg_box[sg];
+                const float ddx = wrap_half(xvw - bx.x, Lx);
+                float ddy = yvf - bx.y;
+                if (!a.walls) ddy = wrap_half(ddy, Ly);
+                if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
                 const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
                 for (int b = b0; b < b0 + nb; ++b) {
-                    const C dx = C(wrap_d(xv - X[2 * b], nxd));
-                    C dy = C(yv - X[2 * b + 1]);
-                    if (!a.walls) dy = C(wrap_d((double)dy, nyd));
+                    const C dx = C(wrap_m(xv - X[2 * b], nxd, a.inv_nx));
+                    double dyd = yv - X[2 * b + 1];
+                    if (!a.walls) dyd = wrap_m(dyd, nyd, a.inv_ny);
+                    const C dy = C(dyd);
                     const C d = sqrt(dx * dx + dy * dy);
                     if (d < C(a.d_rep)) {
                         const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
@@ -192,18 +219,21 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
                 }
             }
         }
-        // Eq. strainFor on elements (v, R) and (L, v)
+        // Eq. strainFor on elements (v, R) and (L, v); l - l_0 is formed as
+        // (l^2 - l_0^2) / (l + l_0) with the squares in FP64
         {
-            const C dx = C(xv - xR), dy = C(yv - yR);
-            const C l = sqrt(dx * dx + dy * dy);
-            const C c = -ks * (l - C(a.l0[v])) / l;
-            Fx += c * dx;
-            Fy += c * dy;
-            const C ex = C(xv - xl), ey = C(yv - yl);
-            const C l2 = sqrt(ex * ex + ey * ey);
-            const C c2 = -ks * (l2 - C(a.l0[L])) / l2;
-            Fx += c2 * ex;
-            Fy += c2 * ey;
+            const double ex = __dsub_rn(xR, xv), ey = __dsub_rn(yR, yv);
+            const double lsq = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+            const C l = sqrt(C(lsq));
+            const C c = ks * C(__dsub_rn(lsq, a.rest[4 * (size_t)v])) / ((l + C(a.rest[4 * (size_t)v + 1])) * l);
+            Fx += c * C(ex);
+            Fy += c * C(ey);
+            const double gx = __dsub_rn(xv, xl), gy = __dsub_rn(yv, yl);
+            const double lsq2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
+            const C l2 = sqrt(C(lsq2));
+            const C c2 = -ks * C(__dsub_rn(lsq2, a.rest[4 * (size_t)L])) / ((l2 + C(a.rest[4 * (size_t)L + 1])) * l2);
+            Fx += c2 * C(gx);
+            Fy += c2 * C(gy);
         }
         // Eq. bendFor gathered: own term plus the neighbours' shares
         Fx += -s_mnx[k] + s_mnx[kR] * s_sL[kR] + s_mnx[kL] * s_sR[kL];
@@ -373,6 +403,26 @@ __global__ void k_sort_tiles(const int* off, const int* list_raw, const int* lis
 }
 
 // ---------------------------------------------------------------- advance
+// one warp: bounding box of a 32-vertex segment, stored as FP32 with the
+// centre's x wrapped into [0, nx)
+__device__ void seg_box_warp(const MarkerArgs& a, int sg, int lane) {
+    const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
+    const int v = v0 + (lane < nb ? lane : 0);
+    double lo_x = a.X[2 * v], hi_x = lo_x, lo_y = a.X[2 * v + 1], hi_y = lo_y;
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
+        hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
+        lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
+        hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
+    }
+    if (lane == 0) {
+        const double cxd = 0.5 * (lo_x + hi_x);
+        const double cxw = cxd - (double)a.nx * floor(cxd * a.inv_nx);
+        a.seg_box[sg] = make_float4(float(cxw), float(0.5 * (lo_y + hi_y)),
+                                    float(0.5 * (hi_x - lo_x)), float(0.5 * (hi_y - lo_y)));
+    }
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_advance(const MarkerArgs a) {
     const int m = blockIdx.x;
@@ -462,47 +512,14 @@ __global__ void __launch_bounds__(256) k_advance(const MarkerArgs a) {
     __syncthreads();
     // bounding boxes of this membrane's 32-vertex segments (repulsion pruning)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) {
-        const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
-        const int v = v0 + (lane < nb ? lane : 0);
-        double lo_x = X[2 * v], hi_x = lo_x, lo_y = X[2 * v + 1], hi_y = lo_y;
-        for (int o = 16; o > 0; o >>= 1) {
-            lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
-            hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
-            lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
-            hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
-        }
-        if (lane == 0) {
-            double* bx = a.seg_box + 4 * sg;
-            bx[0] = 0.5 * (lo_x + hi_x);
-            bx[1] = 0.5 * (lo_y + hi_y);
-            bx[2] = 0.5 * (hi_x - lo_x);
-            bx[3] = 0.5 * (hi_y - lo_y);
-        }
-    }
+    for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) seg_box_warp(a, sg, lane);
 }
 
-// segment boxes alone (before the first step)
+// segment boxes alone (before the first step and after user-written markers)
 __global__ void k_seg_boxes(const MarkerArgs a) {
     const int sg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
     if (sg >= a.nseg) return;
-    const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
-    const int v = v0 + (lane < nb ? lane : 0);
-    double lo_x = a.X[2 * v], hi_x = lo_x, lo_y = a.X[2 * v + 1], hi_y = lo_y;
-    for (int o = 16; o > 0; o >>= 1) {
-        lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
-        hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
-        lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
-        hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
-    }
-    if (lane == 0) {
-        double* bx = a.seg_box + 4 * sg;
-        bx[0] = 0.5 * (lo_x + hi_x);
-        bx[1] = 0.5 * (lo_y + hi_y);
-        bx[2] = 0.5 * (hi_x - lo_x);
-        bx[3] = 0.5 * (hi_y - lo_y);
-    }
+    seg_box_warp(a, sg, threadIdx.x & 31);
 }
 
 __global__ void k_areas(const MarkerArgs a, double* areas) {
@@ -523,10 +540,8 @@ __global__ void k_areas(const MarkerArgs a, double* areas) {
 // ---------------------------------------------------------------- launchers
 static bool is_f64(lbib_precision p) { return p == LBIB_F64; }
 
-cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* l0, double* th0,
-                        double* A0, cudaStream_t s) {
-    if (is_f64(prec)) k_rest<double><<<a.nmem, 256, 0, s>>>(a, l0, th0, A0);
-    else k_rest<float><<<a.nmem, 256, 0, s>>>(a, l0, th0, A0);
+cudaError_t launch_rest(lbib_precision, const MarkerArgs& a, double* rest, double* A0, cudaStream_t s) {
+    k_rest<<<a.nmem, 256, 0, s>>>(a, rest, A0);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ struct LbArgs {
 
 struct MarkerArgs {
     int nx, ny, walls;
+    double inv_nx, inv_ny;    // 1/nx, 1/ny (periodic wrapping without a division)
     int nmem, nv;
     const int* mem_off;
     const int* mem_n;
@@ -109,8 +110,8 @@ struct MarkerArgs {
     void* W;                  // [nv][9] compute type
     int* stencil;             // [nv][2]
     int* vtiles;              // [nv][6] touched tiles (-1 padded)
-    const double* l0;         // [nv] rest length of element (v, v+1)
-    const double* th0;        // [nv] rest turning angle at v
+    const double* rest;       // [nv][4] rest state: |x_{v+1}-x_v|^2, |x_{v+1}-x_v|, and the
+                              // cross and dot products of the two edges at v
     const int* elem_lig;      // [nv] ligand on element (v, v+1) or -1
     // repulsion
     double d_rep;
@@ -118,7 +119,7 @@ struct MarkerArgs {
     const int* seg_mem;       // [nseg]
     const int* seg_v0;        // [nseg] first global vertex
     const int* seg_n;         // [nseg]
-    double* seg_box;          // [nseg][4] cx, cy, hx, hy
+    float4* seg_box;          // [nseg] centre x wrapped to [0,nx), centre y, half extents
     const int* mem_seg_off;   // segments of membrane m: [mem_seg_off[m], mem_seg_off[m+1])
     // bonds
     int nlig, nrec;
@@ -163,8 +164,8 @@ cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int n
 cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
                         int n_partials, double* out, float inv_scale, cudaStream_t s);
 // ib_kernels.cu
-cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* l0, double* th0,
-                        double* A0, cudaStream_t s);
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* rest, double* A0,
+                        cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
 cudaError_t set_forces_smem(lbib_precision prec, int max_n);
 cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s);

@@ -30,3 +30,17 @@ def dev_err(a, b, w):
 
 
 W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def vel_err(ux, uy, ux0, uy0):
+    """max componentwise velocity error over the reference speed scale"""
+    d = max(np.max(np.abs(ux - ux0)), np.max(np.abs(uy - uy0)))
+    s = max(np.max(np.abs(ux0)), np.max(np.abs(uy0)))
+    return d / s
+
+
+def f64_field_tol(u_scale):
+    """FP64 field tolerance: 1e-12, or the plain-f oracle's own rounding floor
+    (about 50 eps / u_scale relative, from O(1) population sums carrying an
+    O(u) signal) when the flow is slow."""
+    return max(1e-12, 50 * 2.22e-16 / u_scale)
