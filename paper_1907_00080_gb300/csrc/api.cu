@@ -318,6 +318,16 @@ static lbib_status finalize(lbib_ctx* c) {
         for (int r = 0; r < nr; ++r) rcell_ids[cur[cell[r]]++] = r;  // ascending id within a cell
     }
     c->list_cap = 6 * std::max(nv, 1);
+    std::vector<int> fu, au;
+    for (int m = 0; m < nm; ++m) {
+        const int n = c->h_mem_n[m];
+        for (int k0 = 0; k0 < n; k0 += kChunkV) {
+            fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0)});
+            if (c->h_mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED)
+                au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0)});
+        }
+        if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) au.insert(au.end(), {m, 0, n});
+    }
 
     // ---- one arena for every marker / tile / bond array
     const size_t cs = c->cmp_elem;
@@ -335,6 +345,7 @@ static lbib_status finalize(lbib_ctx* c) {
         add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
         add(4 * c->ntiles); add(4 * (c->ntiles + 1)); add(4 * c->ntiles);
         add(4 * c->list_cap); add(4 * c->list_cap); add(4 * c->list_cap); add(8 * (nm + 1));
+        add(4 * fu.size()); add(4 * au.size());
         bytes = probe.used + 256;
     }
     lbib_status st = LBIB_OK;
@@ -387,6 +398,8 @@ static lbib_status finalize(lbib_ctx* c) {
     c->list_tile = ar.take<int>(c->list_cap);
     c->list_sorted = ar.take<int>(c->list_cap);
     c->d_areas = ar.take<double>(nm + 1);
+    int* d_fu = ar.take<int>(fu.size());
+    int* d_au = ar.take<int>(au.size());
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
 
     auto H2D = [&](void* d, const void* h, size_t b) -> cudaError_t {
@@ -411,6 +424,8 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(d_seg_v0, seg_v0.data(), 4 * seg_v0.size()));
         CK(H2D(d_seg_n, seg_n.data(), 4 * seg_n.size()));
         CK(H2D(d_mem_seg_off, mem_seg_off.data(), 4 * (nm + 1)));
+        CK(H2D(d_fu, fu.data(), 4 * fu.size()));
+        CK(H2D(d_au, au.data(), 4 * au.size()));
     }
     if (nl > 0) {
         CK(H2D(d_lig_a, lig_a.data(), 4 * nl));
@@ -434,6 +449,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.rest = rest; a.elem_lig = elig;
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
+    a.nfu = (int)(fu.size() / 3); a.nau = (int)(au.size() / 3); a.fu = d_fu; a.au = d_au;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
     a.rec_xy = rec_xy; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
@@ -448,7 +464,6 @@ static lbib_status finalize(lbib_ctx* c) {
     if (nm > 0) {
         CK(launch_rest(c->prec, a, rest, A0, c->stream));
         CK(launch_seg_boxes(a, c->stream));
-        CK(set_forces_smem(c->prec, c->max_mem_n));
     }
     CK(cudaStreamSynchronize(c->stream));
     c->finalized = true;

@@ -61,47 +61,60 @@ __device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, 
     return sqrt(dx * dx + dy * dy);
 }
 
-// one thread per ligand: rupture test, then the formation candidate (the
-// lowest receptor id that passes), claimed with atomicMin (lowest ligand wins)
+// one warp per ligand: lane 0 tests the existing bond for rupture; then the
+// lanes share the receptors of the 3x3 cell block around the ligand point, each
+// keeps the lowest id that passes the formation test, a warp minimum gives the
+// candidate (the first accepted receptor in ascending id), claimed with
+// atomicMin so that the lowest ligand id wins
 __global__ void k_bonds_decide(const MarkerArgs a) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= a.nlig) return;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (l >= a.nlig) return;  // warp-uniform
     const long long step = *a.d_step;
     const int va = a.lig_a[l], vb = a.lig_b[l];
     const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
     const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
     if (!isfinite(cxp) || !isfinite(cyp)) return;  // reported by the advance kernel
-    int r = a.bond_of_lig[l];
+    const int r = a.bond_of_lig[l];
     if (r >= 0) {
-        const double d = lig_rec_dist(a, cxp, cyp, r);
-        bool rupture = d >= a.d_break;
-        if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+        int rupture = 0;
+        if (lane == 0) {
+            const double d = lig_rec_dist(a, cxp, cyp, r);
+            rupture = d >= a.d_break;
+            if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+            if (rupture) {
+                a.rupt[l] = r;
+                a.bond_of_lig[l] = -1;
+            }
+        }
+        rupture = __shfl_sync(0xffffffffu, rupture, 0);
         if (!rupture) return;
-        a.rupt[l] = r;
-        a.bond_of_lig[l] = -1;
     }
     // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
     const double xw = cxp - (double)a.nx * floor(cxp * a.inv_nx);
     int gx = (int)floor(xw / a.rc_w);
-    gx = gx >= a.rc_nx ? a.rc_nx - 1 : gx;
-    const int gy = (int)floor((cyp - a.rc_y0) / a.rc_h);
+    gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
+    const int gy = (int)fmin(fmax(floor((cyp - a.rc_y0) / a.rc_h), -4.0), (double)a.rc_ny + 4.0);
     int best = INT_MAX;
+    int t = 0;  // running index over the candidate receptors
     for (int qy = gy - 1; qy <= gy + 1; ++qy) {
-        const int cyc = qy;
-        if (cyc < 0 || cyc >= a.rc_ny) continue;
+        if (qy < 0 || qy >= a.rc_ny) continue;
         for (int qx = gx - 1; qx <= gx + 1; ++qx) {
             const int cxc = ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
-            const int cell = cyc * a.rc_nx + cxc;
-            for (int p = a.rcell_start[cell]; p < a.rcell_start[cell + 1]; ++p) {
+            const int cell = qy * a.rc_nx + cxc;
+            const int p0 = a.rcell_start[cell], p1 = a.rcell_start[cell + 1];
+            for (int p = p0 + ((lane - t) % 32 + 32) % 32; p < p1; p += 32) {
                 const int rr = a.rcell_ids[p];
                 if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
                 const double d = lig_rec_dist(a, cxp, cyp, rr);
                 if (!(d < a.d_cut)) continue;
                 if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
             }
+            t += p1 - p0;
         }
     }
-    if (best != INT_MAX) {
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0 && best != INT_MAX) {
         a.cand[l] = best;
         atomicMin(&a.claim[best], l);
     }
@@ -126,7 +139,7 @@ __global__ void k_bonds_apply(const MarkerArgs a, int has_bonds) {
 
 cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s) {
     const bool has = a.nlig > 0 && a.nrec > 0;
-    if (has) k_bonds_decide<<<(a.nlig + 127) / 128, 128, 0, s>>>(a);
+    if (has) k_bonds_decide<<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
     const int n = a.nlig > 0 ? a.nlig : 1;
     k_bonds_apply<<<(n + 127) / 128, 128, 0, s>>>(a, has ? 1 : 0);
     return cudaGetLastError();

@@ -114,29 +114,41 @@ __device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, doub
     Fy += C(0.5 * c * dy);
 }
 
+// One block per work unit (a chunk of up to kChunkV consecutive vertices of one
+// membrane); one thread per vertex.  The enclosed area of the whole membrane is
+// summed by every unit of that membrane in the same fixed order (so all units
+// agree bit for bit), and the bending geometry of the chunk plus one halo
+// vertex on each side is staged in shared memory.
 template <typename C>
-__global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
-    const int m = blockIdx.x;
+__global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
+    const int m = a.fu[3 * blockIdx.x], k0 = a.fu[3 * blockIdx.x + 1], kn = a.fu[3 * blockIdx.x + 2];
     const int off = a.mem_off[m], n = a.mem_n[m];
-    extern __shared__ __align__(16) unsigned char smem[];
-    C* s_mnx = reinterpret_cast<C*>(smem);
-    C* s_mny = s_mnx + n;
-    C* s_sL = s_mny + n;
-    C* s_sR = s_sL + n;
-    C* s_nx = s_sR + n;
-    C* s_ny = s_nx + n;
+    __shared__ C s_mnx[kChunkV + 2], s_mny[kChunkV + 2], s_sL[kChunkV + 2], s_sR[kChunkV + 2];
+    __shared__ C s_nx[kChunkV + 2], s_ny[kChunkV + 2];
     __shared__ double red[33];
     const double* X = a.X;
     const double nxd = (double)a.nx, nyd = (double)a.ny;
     const double xr = X[2 * off], yr = X[2 * off + 1];
     const C kb = C(a.mem_kb[m]);
 
-    // pass 1: vertex geometry (bending) and the shoelace area about vertex 0.
+    // shoelace area about vertex 0 over the whole ring (FP64)
+    double ap = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k, R = off + (k == n - 1 ? 0 : k + 1);
+        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+    }
+    const double A = 0.5 * block_sum(ap, red);
+    // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
+    const C ca = C(-a.mem_ka[m] * (1.0 - A / a.mem_A0[m]) * (1.0 / 3.0));
+    const C ks = C(a.mem_ks[m]);
+
+    // vertex geometry of local slots j = 0..kn+1 (vertex k0 - 1 + j, wrapped).
     // theta - theta_0 comes from the rotation between the rest and the current
     // edge pair, atan2(c d0 - d c0, d d0 + c c0), free of the cancellation of
     // subtracting two nearly equal angles.
-    double ap = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int j = threadIdx.x; j < kn + 2; j += blockDim.x) {
+        int k = k0 - 1 + j;
+        k = k < 0 ? k + n : (k >= n ? k - n : k);
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
         const double xL = X[2 * L], yL = X[2 * L + 1], xv = X[2 * v], yv = X[2 * v + 1];
         const double xR = X[2 * R], yR = X[2 * R + 1];
@@ -154,34 +166,34 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
         nx_ /= nn;
         ny_ /= nn;
         const C mb = kb * dth;
-        s_mnx[k] = mb * nx_;
-        s_mny[k] = mb * ny_;
-        s_sL[k] = lL / (lL + lR);
-        s_sR[k] = lR / (lL + lR);
-        s_nx[k] = nx_;
-        s_ny[k] = ny_;
-        ap += (xv - xr) * (yR - yr) - (xR - xr) * (yv - yr);
+        s_mnx[j] = mb * nx_;
+        s_mny[j] = mb * ny_;
+        s_sL[j] = lL / (lL + lR);
+        s_sR[j] = lR / (lL + lR);
+        s_nx[j] = nx_;
+        s_ny[j] = ny_;
     }
-    const double A = 0.5 * block_sum(ap, red);  // includes a __syncthreads
-    // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
-    const C ca = C(-a.mem_ka[m] * (1.0 - A / a.mem_A0[m]) * (1.0 / 3.0));
-    const C ks = C(a.mem_ks[m]);
+    __syncthreads();
 
     // the previous step's formation candidates of this membrane's ligands
-    for (int l = a.mem_lig_off[m] + threadIdx.x; l < a.mem_lig_off[m + 1]; l += blockDim.x) {
-        const int c = a.cand[l];
-        if (c >= 0) {
-            a.claim[c] = INT_MAX;
-            a.cand[l] = -1;
+    if (k0 == 0) {
+        for (int l = a.mem_lig_off[m] + threadIdx.x; l < a.mem_lig_off[m + 1]; l += blockDim.x) {
+            const int c = a.cand[l];
+            if (c >= 0) {
+                a.claim[c] = INT_MAX;
+                a.cand[l] = -1;
+            }
         }
     }
 
     C* F = static_cast<C*>(a.F);
     C* W = static_cast<C*>(a.W);
     const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    for (int j = threadIdx.x; j < kn; j += blockDim.x) {
+        const int k = k0 + j;
         const int kL = k == 0 ? n - 1 : k - 1, kR = k == n - 1 ? 0 : k + 1;
         const int v = off + k, L = off + kL, R = off + kR;
+        const int sj = j + 1;  // shared-memory slot of vertex k
         const double xv = X[2 * v], yv = X[2 * v + 1];
         const double xl = X[2 * L], yl = X[2 * L + 1], xR = X[2 * R], yR = X[2 * R + 1];
         C Fx = C(0), Fy = C(0);
@@ -213,8 +225,8 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
                     const C d = sqrt(dx * dx + dy * dy);
                     if (d < C(a.d_rep)) {
                         const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
-                        Fx -= mag * s_nx[k];
-                        Fy -= mag * s_ny[k];
+                        Fx -= mag * s_nx[sj];
+                        Fy -= mag * s_ny[sj];
                     }
                 }
             }
@@ -236,8 +248,8 @@ __global__ void __launch_bounds__(256) k_forces(const MarkerArgs a) {
             Fy += c2 * C(gy);
         }
         // Eq. bendFor gathered: own term plus the neighbours' shares
-        Fx += -s_mnx[k] + s_mnx[kR] * s_sL[kR] + s_mnx[kL] * s_sR[kL];
-        Fy += -s_mny[k] + s_mny[kR] * s_sL[kR] + s_mny[kL] * s_sR[kL];
+        Fx += -s_mnx[sj] + s_mnx[sj + 1] * s_sL[sj + 1] + s_mnx[sj - 1] * s_sR[sj - 1];
+        Fy += -s_mny[sj] + s_mny[sj + 1] * s_sL[sj + 1] + s_mny[sj - 1] * s_sR[sj - 1];
         // Eq. areaFor, half of each adjacent element
         Fx += C(0.5) * ca * C(-(yR - yl));
         Fy += C(0.5) * ca * C(xR - xl);
@@ -423,95 +435,113 @@ __device__ void seg_box_warp(const MarkerArgs& a, int sg, int lane) {
     }
 }
 
+// interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
 template <typename C>
-__global__ void __launch_bounds__(256) k_advance(const MarkerArgs a) {
-    const int m = blockIdx.x;
-    const int off = a.mem_off[m], n = a.mem_n[m];
-    __shared__ double red[33];
-    const long long step = *a.d_step;
+__device__ __forceinline__ void interp_vertex(const MarkerArgs& a, int v) {
     const C* ux = static_cast<const C*>(a.ux);
     const C* uy = static_cast<const C*>(a.uy);
     const C* W = static_cast<const C*>(a.W);
     C* U = static_cast<C*>(a.U);
+    const int i0 = a.stencil[2 * v], j0 = a.stencil[2 * v + 1];
+    C sx = C(0), sy = C(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        int j = j0 + b - 1;
+        if (a.walls) {
+            if (j < 0 || j >= a.ny) continue;
+        } else {
+            j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            int i = i0 + q - 1;
+            i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
+            const C w = W[9 * (size_t)v + b * 3 + q];
+            const size_t node = (size_t)j * a.nx + i;
+            sx += w * ux[node];
+            sy += w * uy[node];
+        }
+    }
+    U[2 * v] = sx;
+    U[2 * v + 1] = sy;
+}
+
+// Eq. kinematicPos (BDF2); forward Euler on the very first step
+template <typename C>
+__device__ __forceinline__ void advance_vertex(const MarkerArgs& a, int v, long long step) {
+    const C* U = static_cast<const C*>(a.U);
     double* X = a.X;
     double* Xp = a.Xp;
-    // interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k;
-        const int i0 = a.stencil[2 * v], j0 = a.stencil[2 * v + 1];
-        C sx = C(0), sy = C(0);
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            int j = j0 + b - 1;
-            if (a.walls) {
-                if (j < 0 || j >= a.ny) continue;
-            } else {
-                j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                int i = i0 + q - 1;
-                i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
-                const C w = W[9 * (size_t)v + b * 3 + q];
-                const size_t node = (size_t)j * a.nx + i;
-                sx += w * ux[node];
-                sy += w * uy[node];
-            }
-        }
-        U[2 * v] = sx;
-        U[2 * v + 1] = sy;
+    const double Ux = (double)U[2 * v], Uy = (double)U[2 * v + 1];
+    const double x = X[2 * v], y = X[2 * v + 1];
+    double xn, yn;
+    if (step == 0) {
+        xn = x + Ux;
+        yn = y + Uy;
+    } else {
+        xn = (2.0 / 3.0) * (2.0 * x - 0.5 * Xp[2 * v] + Ux);
+        yn = (2.0 / 3.0) * (2.0 * y - 0.5 * Xp[2 * v + 1] + Uy);
     }
-    if (a.mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) {
-        // least-squares rigid motion U_c + omega x (x - x_c) of the ring
+    if (!isfinite(xn) || !isfinite(yn)) atomicOr(a.status, ST_NONFINITE);
+    Xp[2 * v] = x;
+    Xp[2 * v + 1] = y;
+    X[2 * v] = xn;
+    X[2 * v + 1] = yn;
+}
+
+// One block per unit: a chunk of a kinematic membrane (independent vertices)
+// or a whole rigid-projected membrane (needs its centroid and mean rotation).
+template <typename C>
+__global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
+    const int m = a.au[3 * blockIdx.x], k0 = a.au[3 * blockIdx.x + 1], kn = a.au[3 * blockIdx.x + 2];
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    __shared__ double red[33];
+    const long long step = *a.d_step;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (a.mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED) {
+        for (int j = threadIdx.x; j < kn; j += blockDim.x) {
+            interp_vertex<C>(a, off + k0 + j);
+            advance_vertex<C>(a, off + k0 + j, step);
+        }
         __syncthreads();
-        const double xr = X[2 * off], yr = X[2 * off + 1];
-        double sx = 0, sy = 0, su = 0, sv = 0;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int v = off + k;
-            sx += X[2 * v] - xr;
-            sy += X[2 * v + 1] - yr;
-            su += (double)U[2 * v];
-            sv += (double)U[2 * v + 1];
-        }
-        const double mx = block_sum(sx, red) / n, my = block_sum(sy, red) / n;
-        const double mu = block_sum(su, red) / n, mv = block_sum(sv, red) / n;
-        double num = 0, den = 0;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int v = off + k;
-            const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
-            num += rx * ((double)U[2 * v + 1] - mv) - ry * ((double)U[2 * v] - mu);
-            den += rx * rx + ry * ry;
-        }
-        const double om = block_sum(num, red) / block_sum(den, red);
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const int v = off + k;
-            const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
-            U[2 * v] = C(mu - om * ry);
-            U[2 * v + 1] = C(mv + om * rx);
-        }
+        // boxes of the 32-vertex segments this chunk covers (chunks are 32-aligned)
+        const int s0 = a.mem_seg_off[m] + k0 / 32, s1 = a.mem_seg_off[m] + (k0 + kn + 31) / 32;
+        for (int sg = s0 + wid; sg < s1; sg += nw) seg_box_warp(a, sg, lane);
+        return;
     }
-    // Eq. kinematicPos (BDF2); forward Euler on the very first step
+    C* U = static_cast<C*>(a.U);
+    double* X = a.X;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) interp_vertex<C>(a, off + k);
+    __syncthreads();
+    // least-squares rigid motion U_c + omega x (x - x_c) of the ring
+    const double xr = X[2 * off], yr = X[2 * off + 1];
+    double sx = 0, sy = 0, su = 0, sv = 0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int v = off + k;
-        const double Ux = (double)U[2 * v], Uy = (double)U[2 * v + 1];
-        const double x = X[2 * v], y = X[2 * v + 1];
-        double xn, yn;
-        if (step == 0) {
-            xn = x + Ux;
-            yn = y + Uy;
-        } else {
-            xn = (2.0 / 3.0) * (2.0 * x - 0.5 * Xp[2 * v] + Ux);
-            yn = (2.0 / 3.0) * (2.0 * y - 0.5 * Xp[2 * v + 1] + Uy);
-        }
-        if (!isfinite(xn) || !isfinite(yn)) atomicOr(a.status, ST_NONFINITE);
-        Xp[2 * v] = x;
-        Xp[2 * v + 1] = y;
-        X[2 * v] = xn;
-        X[2 * v + 1] = yn;
+        sx += X[2 * v] - xr;
+        sy += X[2 * v + 1] - yr;
+        su += (double)U[2 * v];
+        sv += (double)U[2 * v + 1];
+    }
+    const double mx = block_sum(sx, red) / n, my = block_sum(sy, red) / n;
+    const double mu = block_sum(su, red) / n, mv = block_sum(sv, red) / n;
+    double num = 0, den = 0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k;
+        const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
+        num += rx * ((double)U[2 * v + 1] - mv) - ry * ((double)U[2 * v] - mu);
+        den += rx * rx + ry * ry;
+    }
+    const double om = block_sum(num, red) / block_sum(den, red);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int v = off + k;
+        const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
+        U[2 * v] = C(mu - om * ry);
+        U[2 * v + 1] = C(mv + om * rx);
     }
     __syncthreads();
-    // bounding boxes of this membrane's 32-vertex segments (repulsion pruning)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) advance_vertex<C>(a, off + k, step);
+    __syncthreads();
     for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) seg_box_warp(a, sg, lane);
 }
 
@@ -545,23 +575,10 @@ cudaError_t launch_rest(lbib_precision, const MarkerArgs& a, double* rest, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s) {
-    if (is_f64(prec)) {
-        const size_t sm = 6 * sizeof(double) * (size_t)max_n;
-        k_forces<double><<<a.nmem, 256, sm, s>>>(a);
-    } else {
-        const size_t sm = 6 * sizeof(float) * (size_t)max_n;
-        k_forces<float><<<a.nmem, 256, sm, s>>>(a);
-    }
+cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int, cudaStream_t s) {
+    if (is_f64(prec)) k_forces<double><<<a.nfu, kChunkV, 0, s>>>(a);
+    else k_forces<float><<<a.nfu, kChunkV, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t set_forces_smem(lbib_precision prec, int max_n) {
-    const size_t sm = 6 * (is_f64(prec) ? sizeof(double) : sizeof(float)) * (size_t)max_n;
-    if (sm <= 48 * 1024) return cudaSuccess;
-    if (is_f64(prec))
-        return cudaFuncSetAttribute(k_forces<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    return cudaFuncSetAttribute(k_forces<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s) {
@@ -582,8 +599,8 @@ cudaError_t launch_sort_tiles(const int* off, const int* list_raw, const int* li
 }
 
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
-    if (is_f64(prec)) k_advance<double><<<a.nmem, 256, 0, s>>>(a);
-    else k_advance<float><<<a.nmem, 256, 0, s>>>(a);
+    if (is_f64(prec)) k_advance<double><<<a.nau, kChunkV, 0, s>>>(a);
+    else k_advance<float><<<a.nau, kChunkV, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -121,6 +121,12 @@ struct MarkerArgs {
     const int* seg_n;         // [nseg]
     float4* seg_box;          // [nseg] centre x wrapped to [0,nx), centre y, half extents
     const int* mem_seg_off;   // segments of membrane m: [mem_seg_off[m], mem_seg_off[m+1])
+    // work units: (membrane, first local vertex, vertex count); the force kernel
+    // cuts every membrane into chunks of kChunkV vertices, the advance kernel
+    // cuts kinematic membranes the same way and keeps rigid-projected ones whole
+    int nfu, nau;
+    const int* fu;            // [nfu][3]
+    const int* au;            // [nau][3]
     // bonds
     int nlig, nrec;
     const int* lig_a;         // [nlig] first vertex of the ligand element
@@ -151,6 +157,8 @@ struct MarkerArgs {
 
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2 };
 
+constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of 32)
+
 // ---------------------------------------------------------------- launchers
 // lb_kernels.cu
 cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,
@@ -167,7 +175,6 @@ cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems,
 cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* rest, double* A0,
                         cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
-cudaError_t set_forces_smem(lbib_precision prec, int max_n);
 cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s);
 cudaError_t launch_fill_tiles(const MarkerArgs& a, int* cursor, int* list_raw, int* list_tile,
                               cudaStream_t s);
