@@ -317,7 +317,6 @@ static lbib_status finalize(lbib_ctx* c) {
         std::vector<int> cur(cnt.begin(), cnt.end() - 1);
         for (int r = 0; r < nr; ++r) rcell_ids[cur[cell[r]]++] = r;  // ascending id within a cell
     }
-    c->list_cap = 6 * std::max(nv, 1);
     std::vector<int> fu, au;
     for (int m = 0; m < nm; ++m) {
         const int n = c->h_mem_n[m];
@@ -339,12 +338,11 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * (nm + 1)); add(4 * (nm + 1)); add(4 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1));
         add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
         add(16 * nv); add(16 * nv); add(2 * cs * nv); add(2 * cs * nv); add(9 * cs * nv); add(8 * nv);
-        add(24 * nv); add(32 * nv); add(4 * nv);
-        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
+        add(32 * nv); add(4 * nv); add(8 * nv);
+        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
         add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
         add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
-        add(4 * c->ntiles); add(4 * (c->ntiles + 1)); add(4 * c->ntiles);
-        add(4 * c->list_cap); add(4 * c->list_cap); add(4 * c->list_cap); add(8 * (nm + 1));
+        add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
         bytes = probe.used + 256;
     }
@@ -373,13 +371,14 @@ static lbib_status finalize(lbib_ctx* c) {
     a.U = ar.take<char>(2 * cs * nv);
     a.W = ar.take<char>(9 * cs * nv);
     a.stencil = ar.take<int>(2 * (size_t)nv);
-    a.vtiles = ar.take<int>(6 * (size_t)nv);
     double* rest = ar.take<double>(4 * (size_t)nv);
     int* elig = ar.take<int>(nv);
+    a.xoff = ar.take<float2>(nv);
     int* d_seg_mem = ar.take<int>(c->nseg);
     int* d_seg_v0 = ar.take<int>(c->nseg);
     int* d_seg_n = ar.take<int>(c->nseg);
     a.seg_box = ar.take<float4>(c->nseg);
+    a.seg_anchor = ar.take<double2>(c->nseg);
     int* d_mem_seg_off = ar.take<int>(nm + 1);
     int* d_lig_a = ar.take<int>(nl);
     int* d_lig_b = ar.take<int>(nl);
@@ -391,13 +390,10 @@ static lbib_status finalize(lbib_ctx* c) {
     a.claim = ar.take<int>(nr);
     int* d_rcs = ar.take<int>(rcell_start.size());
     int* d_rci = ar.take<int>(rcell_ids.size());
-    c->tile_count = ar.take<int>(c->ntiles);
-    c->tile_off = ar.take<int>(c->ntiles + 1);
-    c->tile_cursor = ar.take<int>(c->ntiles);
-    c->list_raw = ar.take<int>(c->list_cap);
-    c->list_tile = ar.take<int>(c->list_cap);
-    c->list_sorted = ar.take<int>(c->list_cap);
+    c->flags[0] = ar.take<int>(c->ntiles);
+    c->flags[1] = ar.take<int>(c->ntiles);
     c->d_areas = ar.take<double>(nm + 1);
+    c->tickets = ar.take<unsigned int>(4);
     int* d_fu = ar.take<int>(fu.size());
     int* d_au = ar.take<int>(au.size());
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
@@ -441,8 +437,16 @@ static lbib_status finalize(lbib_ctx* c) {
     }
     CK(H2D(d_rcs, rcell_start.data(), 4 * rcell_start.size()));
     if (!rcell_ids.empty()) CK(H2D(d_rci, rcell_ids.data(), 4 * rcell_ids.size()));
-    CK(cudaMemsetAsync(c->tile_count, 0, 4 * c->ntiles, c->stream));
-    CK(cudaMemsetAsync(c->tile_off, 0, 4 * (c->ntiles + 1), c->stream));
+    CK(cudaMemsetAsync(c->flags[0], 0, 4 * c->ntiles, c->stream));
+    CK(cudaMemsetAsync(c->flags[1], 0, 4 * c->ntiles, c->stream));
+    CK(cudaMemsetAsync(c->tickets, 0, 16, c->stream));
+    if (nv > 0) {
+        const size_t gb = sizeof(longlong2) * (size_t)c->nx * c->ny;
+        for (int p = 0; p < 2; ++p) {
+            CK(cudaMalloc(&c->G[p], gb));
+            CK(cudaMemsetAsync(c->G[p], 0, gb, c->stream));
+        }
+    }
 
     a.mem_off = mem_off; a.mem_n = mem_n; a.mem_kind = mem_kind;
     a.mem_ks = ks; a.mem_kb = kb; a.mem_ka = ka; a.mem_A0 = A0; a.mem_lig_off = lig_off;
@@ -453,12 +457,14 @@ static lbib_status finalize(lbib_ctx* c) {
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
     a.rec_xy = rec_xy; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
+    a.inv_rc_w = 1.0 / rc_w; a.inv_rc_h = 1.0 / rc_h;
+    a.inv_y_eq = c->bp.y_eq > 0 ? 1.0 / c->bp.y_eq : 0.0;
     a.sigma = c->bp.sigma; a.y_eq = c->bp.y_eq; a.d_cut = c->bp.d_cut; a.d_break = c->bp.d_break;
     a.kf_dt = c->bp.kf_dt; a.kr0_dt = c->bp.kr0_dt; a.beta_f = c->bp.beta_f; a.beta_r = c->bp.beta_r;
     a.seed = c->bp.seed; a.instance = c->bp.instance;
     a.tile_w = c->tile_w; a.tile_h = c->tile_h; a.tiles_x = c->tiles_x; a.tiles_y = c->tiles_y;
-    a.tile_count = c->tile_count;
-    a.d_step = c->d_step; a.status = c->d_status;
+    a.d_step = c->d_step; a.status = c->d_status; a.tickets = c->tickets;
+    a.bump_in_advance = (nv > 0 && !(nl > 0 && nr > 0)) ? 1 : 0;
     a.ux = c->ux; a.uy = c->uy;
 
     if (nm > 0) {
@@ -471,28 +477,17 @@ static lbib_status finalize(lbib_ctx* c) {
 }
 
 // ------------------------------------------------------------------ one step
-static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
-    MarkerArgs& a = c->ma;
-    cudaError_t e;
-    const bool has_ib = c->nv > 0;
-    if (has_ib) {
-        if ((e = launch_forces(c->prec, a, c->max_mem_n, s)) != cudaSuccess) return e;
-        if ((e = launch_scan_tiles(c->tile_count, c->tile_off, c->tile_cursor, c->ntiles, s)) != cudaSuccess) return e;
-        if ((e = launch_fill_tiles(a, c->tile_cursor, c->list_raw, c->list_tile, s)) != cudaSuccess) return e;
-        if ((e = launch_sort_tiles(c->tile_off, c->list_raw, c->list_tile, c->list_sorted, c->list_cap,
-                                   c->ntiles, s)) != cudaSuccess)
-            return e;
-    }
+static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     LbArgs l{};
     l.src = c->f[src];
     l.dst = c->f[1 - src];
     l.ux = c->ux;
     l.uy = c->uy;
-    l.tile_off = c->tile_off;
-    l.list = c->list_sorted;
-    l.wts = a.W;
-    l.stencil = a.stencil;
-    l.force = a.F;
+    l.gsum = c->G[gpar];
+    l.gclear = c->G[1 - gpar];
+    l.flags = c->flags[gpar];
+    l.flags_other = c->flags[1 - gpar];
+    l.clear_other = clear_other;
     l.nx = c->nx;
     l.ny = c->ny;
     l.omega = 1.0 / c->tau;
@@ -500,11 +495,22 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     l.gy = c->gy;
     l.inv_scale = c->inv_scale;
     l.fields_only = 0;
+    return l;
+}
+
+// one time step from population buffer `src`: forces + weights + spreading,
+// fused collide-stream, interpolation + advance, bond kinetics
+static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
+    MarkerArgs a = c->ma;
+    a.gsum = c->G[src];
+    a.flags = c->flags[src];
+    cudaError_t e;
+    const bool has_ib = c->nv > 0;
+    if (has_ib && (e = launch_forces(c->prec, a, c->max_mem_n, s)) != cudaSuccess) return e;
+    const LbArgs l = lb_args(c, src, src, 1);
     if ((e = launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, has_ib, l, s)) != cudaSuccess)
         return e;
-    if (has_ib) {
-        if ((e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
-    }
+    if (has_ib && (e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
     return launch_bonds(a, s);
 }
 
@@ -584,8 +590,8 @@ extern "C" int64_t lbib_step_count(const lbib_ctx* c) { return c ? c->steps : -1
 extern "C" int32_t lbib_kernels_per_step(const lbib_ctx* c) {
     if (!c) return -1;
     int k = 1;  // fused LB
-    if (c->nv > 0) k += 5;  // forces, scan, fill, sort, advance
-    k += (c->nlig > 0 && c->have_receptors && !c->h_rec.empty()) ? 2 : 1;
+    if (c->nv > 0) k += 2;  // forces (with spreading), interpolation + advance
+    if (c->nlig > 0 && c->have_receptors && !c->h_rec.empty()) k += 1;  // bond kinetics
     return k;
 }
 
@@ -611,25 +617,12 @@ extern "C" lbib_status lbib_read_fields(lbib_ctx* c, double* rho, double* ux, do
         du = ux ? c->stage + N : nullptr;
         dv = uy ? c->stage + 2 * N : nullptr;
     }
-    LbArgs l{};
-    l.src = c->f[1 - c->cur];
+    // recompute rho^n, u^n from the buffer the last step read, with its force field
+    LbArgs l = lb_args(c, 1 - c->cur, 1 - c->cur, 0);
     l.dst = nullptr;
-    l.ux = c->ux;
-    l.uy = c->uy;
     l.rho_out = dr;
     l.ux_out = du;
     l.uy_out = dv;
-    l.tile_off = c->tile_off;
-    l.list = c->list_sorted;
-    l.wts = c->ma.W;
-    l.stencil = c->ma.stencil;
-    l.force = c->ma.F;
-    l.nx = c->nx;
-    l.ny = c->ny;
-    l.omega = 1.0 / c->tau;
-    l.gx = c->gx;
-    l.gy = c->gy;
-    l.inv_scale = c->inv_scale;
     l.fields_only = 1;
     CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
     if (!on_device) {
@@ -779,24 +772,15 @@ extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    LbArgs l{};
-    l.ux = c->ux;
-    l.uy = c->uy;
-    l.tile_off = c->tile_off;
-    l.list = c->list_sorted;
-    l.wts = c->ma.W;
-    l.stencil = c->ma.stencil;
-    l.force = c->ma.F;
-    l.nx = c->nx;
-    l.ny = c->ny;
-    l.omega = 1.0 / c->tau;
-    l.gx = c->gx;
-    l.gy = c->gy;
-    l.inv_scale = c->inv_scale;
+    // the force field of the last completed step stays fixed for every launch
+    const int gpar = 1 - c->cur;
+    LbArgs l = lb_args(c, c->cur, gpar, 0);
     CK(cudaEventRecord(e0, c->stream));
     for (int r = 0; r < reps; ++r) {
         l.src = c->f[c->cur];
         l.dst = c->f[1 - c->cur];
+        l.gsum = c->G[gpar];
+        l.flags = c->flags[gpar];
         CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
         c->cur = 1 - c->cur;
     }
@@ -829,6 +813,8 @@ extern "C" void lbib_destroy(lbib_ctx* c) {
     if (c->d_step) cudaFree(c->d_step);
     if (c->d_status) cudaFree(c->d_status);
     if (c->dmem) cudaFree(c->dmem);
+    for (int p = 0; p < 2; ++p)
+        if (c->G[p]) cudaFree(c->G[p]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -43,11 +43,11 @@ __device__ __forceinline__ double bond_uniform(const MarkerArgs& a, long long st
 }
 
 __device__ __forceinline__ double p_form(const MarkerArgs& a, double d) {
-    const double z = (d - a.y_eq) / a.y_eq;
+    const double z = (d - a.y_eq) * a.inv_y_eq;
     return 1.0 - exp(-a.kf_dt * exp(-a.beta_f * z * z));
 }
 __device__ __forceinline__ double p_rupture(const MarkerArgs& a, double d) {
-    const double z = (d - a.y_eq) / a.y_eq;
+    const double z = (d - a.y_eq) * a.inv_y_eq;
     return 1.0 - exp(-a.kr0_dt * exp(a.beta_r * z * z));
 }
 
@@ -61,90 +61,113 @@ __device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, 
     return sqrt(dx * dx + dy * dy);
 }
 
-// one warp per ligand: lane 0 tests the existing bond for rupture; then the
+// Last-block epilogue: every block counts itself in once it is done; the block
+// that arrives last (it sees all other blocks' writes after the fences) runs the
+// epilogue and resets the counter.  No block ever waits for another.
+__device__ bool arrive_last_b(unsigned int* counter) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// One warp per ligand: lane 0 tests the existing bond for rupture; then the
 // lanes share the receptors of the 3x3 cell block around the ligand point, each
 // keeps the lowest id that passes the formation test, a warp minimum gives the
 // candidate (the first accepted receptor in ascending id), claimed with
-// atomicMin so that the lowest ligand id wins
-__global__ void k_bonds_decide(const MarkerArgs a) {
+// atomicMin so that the lowest ligand id wins.  The last block to finish applies
+// ruptures and winning claims for all ligands, clears the claims and advances
+// the step counter.
+__global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (l >= a.nlig) return;  // warp-uniform
     const long long step = *a.d_step;
-    const int va = a.lig_a[l], vb = a.lig_b[l];
-    const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
-    const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
-    if (!isfinite(cxp) || !isfinite(cyp)) return;  // reported by the advance kernel
-    const int r = a.bond_of_lig[l];
-    if (r >= 0) {
-        int rupture = 0;
-        if (lane == 0) {
-            const double d = lig_rec_dist(a, cxp, cyp, r);
-            rupture = d >= a.d_break;
-            if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
-            if (rupture) {
-                a.rupt[l] = r;
-                a.bond_of_lig[l] = -1;
+    if (l < a.nlig) {  // warp-uniform
+        const int va = a.lig_a[l], vb = a.lig_b[l];
+        const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
+        const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
+        bool look = isfinite(cxp) && isfinite(cyp);  // non-finite positions: reported by the advance
+        const int r = a.bond_of_lig[l];
+        if (look && r >= 0) {
+            int rupture = 0;
+            if (lane == 0) {
+                const double d = lig_rec_dist(a, cxp, cyp, r);
+                rupture = d >= a.d_break;
+                if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+                if (rupture) a.rupt[l] = r;
             }
+            look = __shfl_sync(0xffffffffu, rupture, 0) != 0;
         }
-        rupture = __shfl_sync(0xffffffffu, rupture, 0);
-        if (!rupture) return;
-    }
-    // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
-    const double xw = cxp - (double)a.nx * floor(cxp * a.inv_nx);
-    int gx = (int)floor(xw / a.rc_w);
-    gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
-    const int gy = (int)fmin(fmax(floor((cyp - a.rc_y0) / a.rc_h), -4.0), (double)a.rc_ny + 4.0);
-    int best = INT_MAX;
-    int t = 0;  // running index over the candidate receptors
-    for (int qy = gy - 1; qy <= gy + 1; ++qy) {
-        if (qy < 0 || qy >= a.rc_ny) continue;
-        for (int qx = gx - 1; qx <= gx + 1; ++qx) {
-            const int cxc = ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
-            const int cell = qy * a.rc_nx + cxc;
-            const int p0 = a.rcell_start[cell], p1 = a.rcell_start[cell + 1];
-            for (int p = p0 + ((lane - t) % 32 + 32) % 32; p < p1; p += 32) {
-                const int rr = a.rcell_ids[p];
-                if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
-                const double d = lig_rec_dist(a, cxp, cyp, rr);
-                if (!(d < a.d_cut)) continue;
-                if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
+        int best = INT_MAX;
+        if (look) {
+            // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
+            const double xw = cxp - (double)a.nx * floor(cxp * a.inv_nx);
+            int gx = (int)floor(xw * a.inv_rc_w);
+            gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
+            const int gy = (int)fmin(fmax(floor((cyp - a.rc_y0) * a.inv_rc_h), -4.0), (double)a.rc_ny + 4.0);
+            int t = 0;  // running index over the candidate receptors
+            for (int qy = gy - 1; qy <= gy + 1; ++qy) {
+                if (qy < 0 || qy >= a.rc_ny) continue;
+                for (int qx = gx - 1; qx <= gx + 1; ++qx) {
+                    const int cxc = ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
+                    const int cell = qy * a.rc_nx + cxc;
+                    const int p0 = a.rcell_start[cell], p1 = a.rcell_start[cell + 1];
+                    for (int p = p0 + ((lane - t) % 32 + 32) % 32; p < p1; p += 32) {
+                        const int rr = a.rcell_ids[p];
+                        if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
+                        const double d = lig_rec_dist(a, cxp, cyp, rr);
+                        if (!(d < a.d_cut)) continue;
+                        if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
+                    }
+                    t += p1 - p0;
+                }
             }
-            t += p1 - p0;
+            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        }
+        if (lane == 0 && best != INT_MAX) {
+            a.cand[l] = best;
+            atomicMin(&a.claim[best], l);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0 && best != INT_MAX) {
-        a.cand[l] = best;
-        atomicMin(&a.claim[best], l);
+    if (!arrive_last_b(&a.tickets[1])) return;
+    // epilogue (last block): other blocks' writes are read past L1
+    for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
+        const int r_old = __ldcg(&a.rupt[q]);
+        if (r_old >= 0) {
+            a.owner[r_old] = -1;
+            a.bond_of_lig[q] = -1;
+            a.rupt[q] = -1;
+        }
+        const int c = __ldcg(&a.cand[q]);
+        if (c >= 0 && __ldcg(&a.claim[c]) == q) {
+            a.bond_of_lig[q] = c;
+            a.owner[c] = q;
+        }
     }
-}
-
-// one thread per ligand: apply ruptures and the winning claims; bump the step
-__global__ void k_bonds_apply(const MarkerArgs a, int has_bonds) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l == 0) *a.d_step += 1;
-    if (!has_bonds || l >= a.nlig) return;
-    const int r_old = a.rupt[l];
-    if (r_old >= 0) {
-        a.owner[r_old] = -1;
-        a.rupt[l] = -1;
+    __syncthreads();
+    for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
+        const int c = __ldcg(&a.cand[q]);
+        if (c >= 0) {
+            a.claim[c] = INT_MAX;
+            a.cand[q] = -1;
+        }
     }
-    const int c = a.cand[l];
-    if (c >= 0 && a.claim[c] == l) {
-        a.bond_of_lig[l] = c;
-        a.owner[c] = l;
+    if (threadIdx.x == 0) {
+        *a.d_step += 1;
+        a.tickets[1] = 0;
     }
 }
 
 cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s) {
-    const bool has = a.nlig > 0 && a.nrec > 0;
-    if (has) k_bonds_decide<<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
-    const int n = a.nlig > 0 ? a.nlig : 1;
-    k_bonds_apply<<<(n + 127) / 128, 128, 0, s>>>(a, has ? 1 : 0);
+    if (a.nlig > 0 && a.nrec > 0) k_bonds<<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int bond_kernel_count(const MarkerArgs& a) { return (a.nlig > 0 && a.nrec > 0) ? 2 : 1; }
+int bond_kernel_count(const MarkerArgs& a) { return (a.nlig > 0 && a.nrec > 0) ? 1 : 0; }
 
 }  // namespace lbib

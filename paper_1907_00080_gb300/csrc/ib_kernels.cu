@@ -22,6 +22,15 @@ __device__ __forceinline__ float wrap_half(float d, float L) {
     return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
 }
 
+// force value to the fixed-point grid of the spread field (scaled by 2^52)
+template <typename C> __device__ __forceinline__ long long to_fix(C v);
+template <> __device__ __forceinline__ long long to_fix<float>(float v) {
+    return __float2ll_rn(v * 4503599627370496.0f);
+}
+template <> __device__ __forceinline__ long long to_fix<double>(double v) {
+    return __double2ll_rn(v * kFixScale);
+}
+
 // Roma, Peskin & Berger three-point regularised delta
 template <typename C>
 __device__ __forceinline__ C roma(C r) {
@@ -175,17 +184,6 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
     }
     __syncthreads();
 
-    // the previous step's formation candidates of this membrane's ligands
-    if (k0 == 0) {
-        for (int l = a.mem_lig_off[m] + threadIdx.x; l < a.mem_lig_off[m + 1]; l += blockDim.x) {
-            const int c = a.cand[l];
-            if (c >= 0) {
-                a.claim[c] = INT_MAX;
-                a.cand[l] = -1;
-            }
-        }
-    }
-
     C* F = static_cast<C*>(a.F);
     C* W = static_cast<C*>(a.W);
     const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));
@@ -217,16 +215,35 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
                 if (!a.walls) ddy = wrap_half(ddy, Ly);
                 if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
                 const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
-                for (int b = b0; b < b0 + nb; ++b) {
-                    const C dx = C(wrap_m(xv - X[2 * b], nxd, a.inv_nx));
-                    double dyd = yv - X[2 * b + 1];
-                    if (!a.walls) dyd = wrap_m(dyd, nyd, a.inv_ny);
-                    const C dy = C(dyd);
-                    const C d = sqrt(dx * dx + dy * dy);
-                    if (d < C(a.d_rep)) {
-                        const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
-                        Fx -= mag * s_nx[sj];
-                        Fy -= mag * s_ny[sj];
+                if (sizeof(C) == 4) {
+                    // one FP64 offset to the segment anchor, then FP32 per vertex
+                    const double2 an = a.seg_anchor[sg];
+                    const float bxo = float(wrap_m(xv - an.x, nxd, a.inv_nx));
+                    double byd = yv - an.y;
+                    if (!a.walls) byd = wrap_m(byd, nyd, a.inv_ny);
+                    const float byo = float(byd);
+                    for (int b = b0; b < b0 + nb; ++b) {
+                        const float2 o = a.xoff[b];
+                        const C dx = C(bxo - o.x), dy = C(byo - o.y);
+                        const C d = sqrt(dx * dx + dy * dy);
+                        if (d < C(a.d_rep)) {
+                            const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
+                            Fx -= mag * s_nx[sj];
+                            Fy -= mag * s_ny[sj];
+                        }
+                    }
+                } else {
+                    for (int b = b0; b < b0 + nb; ++b) {
+                        const C dx = C(wrap_m(xv - X[2 * b], nxd, a.inv_nx));
+                        double dyd = yv - X[2 * b + 1];
+                        if (!a.walls) dyd = wrap_m(dyd, nyd, a.inv_ny);
+                        const C dy = C(dyd);
+                        const C d = sqrt(dx * dx + dy * dy);
+                        if (d < C(a.d_rep)) {
+                            const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
+                            Fx -= mag * s_nx[sj];
+                            Fy -= mag * s_ny[sj];
+                        }
                     }
                 }
             }
@@ -323,95 +340,34 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         a.stencil[2 * (size_t)v] = i0w;
         a.stencil[2 * (size_t)v + 1] = j0s;
 
-        // ---- tiles of the fused kernel touched by the stencil
-        int tl[6];
-        int nt = 0;
-        for (int b = -1; b <= 1; ++b) {
-            int j = j0 + b;
+        // ---- spreading (Sec. 2.2, the transpose of the interpolation): w_j F_v
+        // into the fixed-point force field, and flag the fused-kernel tiles hit
+        int last_t = -1;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int j = j0 + b - 1;
             if (a.walls) {
                 if (j < 0 || j >= a.ny) continue;
             } else {
-                j = ((j % a.ny) + a.ny) % a.ny;
+                j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
             }
-            const int tr = j / a.tile_h;
-            for (int q = -1; q <= 1; ++q) {
-                int i = i0w + q;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                int i = i0w + q - 1;
                 i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
-                const int t = tr * a.tiles_x + i / a.tile_w;
-                bool seen = false;
-                for (int z = 0; z < nt; ++z) seen = seen || (tl[z] == t);
-                if (!seen && nt < 6) tl[nt++] = t;
+                const size_t node = (size_t)j * a.nx + i;
+                const C wq = w[b * 3 + q];
+                unsigned long long* gp = reinterpret_cast<unsigned long long*>(a.gsum + node);
+                atomicAdd(gp, (unsigned long long)to_fix<C>(wq * Fx));
+                atomicAdd(gp + 1, (unsigned long long)to_fix<C>(wq * Fy));
+                const int t = (j / a.tile_h) * a.tiles_x + i / a.tile_w;
+                if (t != last_t) {
+                    a.flags[t] = 1;
+                    last_t = t;
+                }
             }
         }
-        for (int z = 0; z < 6; ++z) {
-            const int t = z < nt ? tl[z] : -1;
-            a.vtiles[6 * (size_t)v + z] = t;
-            if (t >= 0) atomicAdd(&a.tile_count[t], 1);
-        }
     }
-}
-
-// ---------------------------------------------------------------- tile lists
-// exclusive scan of the per-tile counts (one block), resets the counts
-__global__ void k_scan_tiles(int* count, int* off, int* cursor, int ntiles) {
-    __shared__ int wsum[32];
-    const int T = blockDim.x;
-    const int per = (ntiles + T - 1) / T;
-    const int beg = threadIdx.x * per, end = min(ntiles, beg + per);
-    int s = 0;
-    for (int i = beg; i < end; ++i) s += count[i];
-    // block exclusive scan of s
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int incl = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        int v = lane < (T >> 5) ? wsum[lane] : 0;
-        int iv = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(FULL, iv, o);
-            if (lane >= o) iv += t;
-        }
-        wsum[lane] = iv - v;
-    }
-    __syncthreads();
-    int run = wsum[w] + incl - s;
-    for (int i = beg; i < end; ++i) {
-        const int c = count[i];
-        off[i] = run;
-        cursor[i] = run;
-        count[i] = 0;
-        run += c;
-    }
-    if (threadIdx.x == T - 1) off[ntiles] = run;
-}
-
-__global__ void k_fill_tiles(const int* vtiles, int nv, int* cursor, int* list_raw, int* list_tile) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    for (int z = 0; z < 6; ++z) {
-        const int t = vtiles[6 * (size_t)v + z];
-        if (t < 0) break;
-        const int p = atomicAdd(&cursor[t], 1);
-        list_raw[p] = v;
-        list_tile[p] = t;
-    }
-}
-
-// rank of each entry among its tile's entries -> ascending vertex order
-__global__ void k_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
-                             int* list_sorted, int cap, int ntiles) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= cap || e >= off[ntiles]) return;
-    const int t = list_tile[e], v = list_raw[e];
-    const int beg = off[t], end = off[t + 1];
-    int rank = 0;
-    for (int q = beg; q < end; ++q) rank += list_raw[q] < v;
-    list_sorted[beg + rank] = v;
 }
 
 // ---------------------------------------------------------------- advance
@@ -420,7 +376,10 @@ __global__ void k_sort_tiles(const int* off, const int* list_raw, const int* lis
 __device__ void seg_box_warp(const MarkerArgs& a, int sg, int lane) {
     const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
     const int v = v0 + (lane < nb ? lane : 0);
-    double lo_x = a.X[2 * v], hi_x = lo_x, lo_y = a.X[2 * v + 1], hi_y = lo_y;
+    const double ax = a.X[2 * v0], ay = a.X[2 * v0 + 1];
+    const double px = a.X[2 * v], py = a.X[2 * v + 1];
+    if (lane < nb) a.xoff[v] = make_float2(float(px - ax), float(py - ay));
+    double lo_x = px, hi_x = px, lo_y = py, hi_y = py;
     for (int o = 16; o > 0; o >>= 1) {
         lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
         hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
@@ -432,7 +391,23 @@ __device__ void seg_box_warp(const MarkerArgs& a, int sg, int lane) {
         const double cxw = cxd - (double)a.nx * floor(cxd * a.inv_nx);
         a.seg_box[sg] = make_float4(float(cxw), float(0.5 * (lo_y + hi_y)),
                                     float(0.5 * (hi_x - lo_x)), float(0.5 * (hi_y - lo_y)));
+        a.seg_anchor[sg] = make_double2(ax, ay);
     }
+}
+
+// Last-block epilogue: every block counts itself in once it is done; the block
+// that arrives last (it sees all other blocks' writes after the fences) runs the
+// epilogue and resets the counter.  No block ever waits for another.
+__device__ bool arrive_last(unsigned int* counter) {
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
 }
 
 // interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
@@ -507,42 +482,51 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         // boxes of the 32-vertex segments this chunk covers (chunks are 32-aligned)
         const int s0 = a.mem_seg_off[m] + k0 / 32, s1 = a.mem_seg_off[m] + (k0 + kn + 31) / 32;
         for (int sg = s0 + wid; sg < s1; sg += nw) seg_box_warp(a, sg, lane);
-        return;
+    } else {
+        C* U = static_cast<C*>(a.U);
+        double* X = a.X;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) interp_vertex<C>(a, off + k);
+        __syncthreads();
+        // least-squares rigid motion U_c + omega x (x - x_c) of the ring; the
+        // sums run in the compute precision on positions taken about vertex 0
+        const double xr = X[2 * off], yr = X[2 * off + 1];
+        C sx = 0, sy = 0, su = 0, sv = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            sx += C(X[2 * v] - xr);
+            sy += C(X[2 * v + 1] - yr);
+            su += U[2 * v];
+            sv += U[2 * v + 1];
+        }
+        const C inv_n = C(1) / C(n);
+        const C mx = C(block_sum((double)sx, red)) * inv_n, my = C(block_sum((double)sy, red)) * inv_n;
+        const C mu = C(block_sum((double)su, red)) * inv_n, mv = C(block_sum((double)sv, red)) * inv_n;
+        C num = 0, den = 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            const C rx = C(X[2 * v] - xr) - mx, ry = C(X[2 * v + 1] - yr) - my;
+            num += rx * (U[2 * v + 1] - mv) - ry * (U[2 * v] - mu);
+            den += rx * rx + ry * ry;
+        }
+        const C om = C(block_sum((double)num, red)) / C(block_sum((double)den, red));
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            const int v = off + k;
+            const C rx = C(X[2 * v] - xr) - mx, ry = C(X[2 * v + 1] - yr) - my;
+            U[2 * v] = mu - om * ry;
+            U[2 * v + 1] = mv + om * rx;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += blockDim.x) advance_vertex<C>(a, off + k, step);
+        __syncthreads();
+        for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) seg_box_warp(a, sg, lane);
     }
-    C* U = static_cast<C*>(a.U);
-    double* X = a.X;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) interp_vertex<C>(a, off + k);
-    __syncthreads();
-    // least-squares rigid motion U_c + omega x (x - x_c) of the ring
-    const double xr = X[2 * off], yr = X[2 * off + 1];
-    double sx = 0, sy = 0, su = 0, sv = 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k;
-        sx += X[2 * v] - xr;
-        sy += X[2 * v + 1] - yr;
-        su += (double)U[2 * v];
-        sv += (double)U[2 * v + 1];
+    // without bond kinetics nothing later in the step reads the step counter
+    if (a.bump_in_advance && arrive_last(&a.tickets[0])) {
+        if (threadIdx.x == 0) {
+            *a.d_step += 1;
+            a.tickets[0] = 0;
+        }
     }
-    const double mx = block_sum(sx, red) / n, my = block_sum(sy, red) / n;
-    const double mu = block_sum(su, red) / n, mv = block_sum(sv, red) / n;
-    double num = 0, den = 0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k;
-        const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
-        num += rx * ((double)U[2 * v + 1] - mv) - ry * ((double)U[2 * v] - mu);
-        den += rx * rx + ry * ry;
-    }
-    const double om = block_sum(num, red) / block_sum(den, red);
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k;
-        const double rx = X[2 * v] - xr - mx, ry = X[2 * v + 1] - yr - my;
-        U[2 * v] = C(mu - om * ry);
-        U[2 * v + 1] = C(mv + om * rx);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < n; k += blockDim.x) advance_vertex<C>(a, off + k, step);
-    __syncthreads();
-    for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) seg_box_warp(a, sg, lane);
 }
 
 // segment boxes alone (before the first step and after user-written markers)
@@ -578,23 +562,6 @@ cudaError_t launch_rest(lbib_precision, const MarkerArgs& a, double* rest, doubl
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int, cudaStream_t s) {
     if (is_f64(prec)) k_forces<double><<<a.nfu, kChunkV, 0, s>>>(a);
     else k_forces<float><<<a.nfu, kChunkV, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s) {
-    k_scan_tiles<<<1, 1024, 0, s>>>(count, off, cursor, ntiles);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill_tiles(const MarkerArgs& a, int* cursor, int* list_raw, int* list_tile,
-                              cudaStream_t s) {
-    k_fill_tiles<<<(a.nv + 255) / 256, 256, 0, s>>>(a.vtiles, a.nv, cursor, list_raw, list_tile);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
-                              int* list_sorted, int cap, int ntiles, cudaStream_t s) {
-    k_sort_tiles<<<(cap + 255) / 256, 256, 0, s>>>(off, list_raw, list_tile, list_sorted, cap, ntiles);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // Lattice-Boltzmann kernels: the fused pull-stream + bounce-back + moments +
-// Guo-forced BGK collision with the IB force gathered per tile (the hot
-// kernel), and the small helpers that convert between the stored
+// Guo-forced BGK collision with the spread IB force read per flagged tile (the
+// hot kernel), and the small helpers that convert between the stored
 // post-collision deviations and user-facing populations.
 //
 // Paper: Coclite, arXiv 1907.00080, Sec. 2.1 (Eqs. BGK, feq, GaussHermite),
@@ -11,21 +11,20 @@
 namespace lbib {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int IB_CHUNK = 128;   // tile-list entries staged in shared memory at a time
 
 template <typename S, int VEC>
 struct alignas(sizeof(S) * VEC) Pack {
     S v[VEC];
 };
 
-// One IB list entry staged in shared memory: stencil origin, nine shape
-// functions and the marker force.
-template <typename C>
-struct IbEntry {
-    C w[9];
-    C fx, fy;
-    int i0, j0;
-};
+// fixed-point force value (scaled by 2^52) to the compute type
+template <typename C> __device__ __forceinline__ C from_fix(long long v);
+template <> __device__ __forceinline__ float from_fix<float>(long long v) {
+    return __ll2float_rn(v) * 2.220446049250313e-16f;
+}
+template <> __device__ __forceinline__ double from_fix<double>(long long v) {
+    return __ll2double_rn(v) * kFixInv;
+}
 
 template <typename S, int VEC>
 __device__ __forceinline__ void load_pack(const S* __restrict__ row, int x0, bool ok, float inv,
@@ -98,7 +97,9 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
         }
     }
 
-    // ---- IB spreading as a gather over this tile's vertex list (Eq. ForcingTerm's f_ib)
+    // ---- IB force of this tile (Eq. ForcingTerm's f_ib): the fixed-point field
+    // the spreading filled, plus the body force; the previous step's field is
+    // zeroed here so that it is clean when the next step spreads into it
     C Gx[VEC], Gy[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
@@ -108,46 +109,24 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     bool flagged = false;
     if (HAS_IB) {
         const int t = blockIdx.y * gridDim.x + blockIdx.x;
-        const int beg = a.tile_off[t], end = a.tile_off[t + 1];
-        flagged = end > beg;
-        if (flagged) {
-            __shared__ IbEntry<C> ent[IB_CHUNK];
-            const int nthr = blockDim.x * blockDim.y;
-            const int tid = threadIdx.y * 32 + lane;
-            const C* __restrict__ W = static_cast<const C*>(a.wts);
-            const C* __restrict__ F = static_cast<const C*>(a.force);
-            for (int c0 = beg; c0 < end; c0 += IB_CHUNK) {
-                const int m = min(IB_CHUNK, end - c0);
-                __syncthreads();
-                for (int e = tid; e < m; e += nthr) {
-                    const int v = a.list[c0 + e];
+        flagged = a.flags[t] != 0;
+        const bool fo = a.clear_other && a.flags_other[t] != 0;
+        __syncthreads();  // every warp has read flags_other[t] before it is cleared
+        const size_t node = (size_t)y * nx + x0;
+        if (flagged && ok) {
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) ent[e].w[q] = W[9 * (size_t)v + q];
-                    ent[e].fx = F[2 * (size_t)v];
-                    ent[e].fy = F[2 * (size_t)v + 1];
-                    ent[e].i0 = a.stencil[2 * (size_t)v];
-                    ent[e].j0 = a.stencil[2 * (size_t)v + 1];
-                }
-                __syncthreads();
-                if (ok) {
-                    for (int e = 0; e < m; ++e) {
-                        int dy = y - ent[e].j0;
-                        if (!WALLS) dy = dy > ny / 2 ? dy - ny : (dy < -(ny / 2) ? dy + ny : dy);
-                        if (dy < -1 || dy > 1) continue;
-                        const C fx = ent[e].fx, fy = ent[e].fy;
-#pragma unroll
-                        for (int k = 0; k < VEC; ++k) {
-                            int dx = x0 + k - ent[e].i0;
-                            dx = dx > nx / 2 ? dx - nx : (dx < -(nx / 2) ? dx + nx : dx);
-                            if (dx >= -1 && dx <= 1) {
-                                const C w = ent[e].w[(dy + 1) * 3 + dx + 1];
-                                Gx[k] += w * fx;
-                                Gy[k] += w * fy;
-                            }
-                        }
-                    }
-                }
+            for (int k = 0; k < VEC; ++k) {
+                const longlong2 g = a.gsum[node + k];
+                Gx[k] += from_fix<C>(g.x);
+                Gy[k] += from_fix<C>(g.y);
             }
+        }
+        if (fo) {
+            if (ok) {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) a.gclear[node + k] = make_longlong2(0, 0);
+            }
+            if (threadIdx.x == 0 && threadIdx.y == 0) a.flags_other[t] = 0;
         }
     }
 

@@ -8,8 +8,8 @@
 //                kernel only in tiles that IB stencils touch
 //   markers      X^n, X^{n-1} as interleaved (x, y) doubles; F^n, U^n, the nine
 //                shape-function weights and the stencil origin per vertex
-//   tile lists   per fused-kernel tile, the ids (ascending) of the vertices whose
-//                3x3 stencil touches the tile (counts, offsets, entries)
+//   IB force     two fixed-point (int64 x 2) per-node fields alternating with the
+//                step parity, plus a flag per fused-kernel tile that spreading touched
 //   adhesion     per ligand: element vertices, bond, candidate; per receptor:
 //                position, owner, claim; receptors bucketed in a uniform grid
 #pragma once
@@ -71,6 +71,14 @@ template <> struct Storage<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------- kernel args
+// The IB force is spread into a per-node fixed-point field (int64 pairs scaled
+// by 2^52): integer addition is associative, so the atomics of the spreading
+// give the same bits in any order.  Two fields alternate with the step parity;
+// tiles that a step's spreading touched are flagged, and the fused kernel of
+// the following step zeroes them again.
+constexpr double kFixScale = 4503599627370496.0;          // 2^52
+constexpr double kFixInv = 1.0 / 4503599627370496.0;      // 2^-52
+
 struct LbArgs {
     const void* src;       // post-collision deviations of step n-1
     void* dst;             // post-collision deviations of step n
@@ -79,11 +87,11 @@ struct LbArgs {
     double* rho_out;       // fields mode: rho, ux, uy as doubles (may be null)
     double* ux_out;
     double* uy_out;
-    const int* tile_off;   // [ntiles + 1]
-    const int* list;       // sorted vertex ids per tile
-    const void* wts;       // [nv][9] shape functions in the compute type
-    const int* stencil;    // [nv][2] i0 (wrapped to [0,nx)), j0
-    const void* force;     // [nv][2] F^n in the compute type
+    const longlong2* gsum; // [N] fixed-point IB force of this step (flagged tiles)
+    longlong2* gclear;     // [N] the other parity's field, zeroed in its flagged tiles
+    const int* flags;      // [ntiles] tiles this step's spreading touched
+    int* flags_other;      // [ntiles] tiles the previous step's spreading touched
+    int clear_other;       // 1 during a step, 0 for read-backs and profiling
     int nx, ny;
     double omega;          // 1/tau
     double gx, gy;         // body force
@@ -109,7 +117,6 @@ struct MarkerArgs {
     void* U;                  // [nv][2] compute type
     void* W;                  // [nv][9] compute type
     int* stencil;             // [nv][2]
-    int* vtiles;              // [nv][6] touched tiles (-1 padded)
     const double* rest;       // [nv][4] rest state: |x_{v+1}-x_v|^2, |x_{v+1}-x_v|, and the
                               // cross and dot products of the two edges at v
     const int* elem_lig;      // [nv] ligand on element (v, v+1) or -1
@@ -120,6 +127,8 @@ struct MarkerArgs {
     const int* seg_v0;        // [nseg] first global vertex
     const int* seg_n;         // [nseg]
     float4* seg_box;          // [nseg] centre x wrapped to [0,nx), centre y, half extents
+    double2* seg_anchor;      // [nseg] position of the segment's first vertex
+    float2* xoff;             // [nv] vertex position relative to its segment's anchor
     const int* mem_seg_off;   // segments of membrane m: [mem_seg_off[m], mem_seg_off[m+1])
     // work units: (membrane, first local vertex, vertex count); the force kernel
     // cuts every membrane into chunks of kChunkV vertices, the advance kernel
@@ -141,14 +150,17 @@ struct MarkerArgs {
     const int* rcell_ids;     // [nrec]
     int rc_nx, rc_ny;         // receptor grid
     double rc_w, rc_h, rc_y0; // cell size, y origin
+    double inv_rc_w, inv_rc_h, inv_y_eq;
     double sigma, y_eq, d_cut, d_break, kf_dt, kr0_dt, beta_f, beta_r;
     uint64_t seed, instance;
-    // tiles
+    // tiles of the fused kernel, spreading target of this step
     int tile_w, tile_h, tiles_x, tiles_y;
-    int* tile_count;
-    // step counter and status
+    longlong2* gsum;
+    int* flags;
+    // step counter, status and the arrival counters of the last-block epilogues
     long long* d_step;
     int* status;
+    unsigned int* tickets;    // [2]: advance, bond decisions
     int bump_in_advance;
     // u field (compute type)
     const void* ux;
@@ -175,11 +187,6 @@ cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems,
 cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* rest, double* A0,
                         cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
-cudaError_t launch_scan_tiles(int* count, int* off, int* cursor, int ntiles, cudaStream_t s);
-cudaError_t launch_fill_tiles(const MarkerArgs& a, int* cursor, int* list_raw, int* list_tile,
-                              cudaStream_t s);
-cudaError_t launch_sort_tiles(const int* off, const int* list_raw, const int* list_tile,
-                              int* list_sorted, int cap, int ntiles, cudaStream_t s);
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_areas(const MarkerArgs& a, double* areas, cudaStream_t s);
@@ -231,17 +238,13 @@ struct lbib_ctx {
     bool finalized = false;
     int max_mem_n = 0;
     int nseg = 0;
-    int list_cap = 0;
-    void* dmem = nullptr;     // one arena for all marker/tile/bond arrays
+    void* dmem = nullptr;     // one arena for all marker / tile / bond arrays
     size_t dmem_bytes = 0;
     lbib::MarkerArgs ma{};
-    int* tile_count = nullptr;
-    int* tile_off = nullptr;
-    int* tile_cursor = nullptr;
-    int* list_raw = nullptr;
-    int* list_tile = nullptr;
-    int* list_sorted = nullptr;
+    longlong2* G[2] = {nullptr, nullptr};   // fixed-point IB force fields (by parity)
+    int* flags[2] = {nullptr, nullptr};      // spread-touched tiles (by parity)
     double* d_areas = nullptr;
+    unsigned int* tickets = nullptr;
 
     long long* d_step = nullptr;
     int* d_status = nullptr;
