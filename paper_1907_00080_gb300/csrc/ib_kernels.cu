@@ -182,7 +182,54 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         s_nx[j] = nx_;
         s_ny[j] = ny_;
     }
+
+    // Eq. repFor screening, once per block: the segments of other membranes
+    // whose box comes within d_rep of a box of this chunk's own segments, kept in
+    // ascending segment order (ballot prefix per warp) so sums are reproducible
+    constexpr int kMaxCand = 256;
+    __shared__ int s_cand[kMaxCand];
+    __shared__ int s_wcnt[kChunkV / 32];
+    __shared__ int s_ncand;
+    if (threadIdx.x == 0) s_ncand = 0;
+    const bool repel = a.nmem > 1;
+    if (repel) {
+        const float Lx = float(a.nx), Ly = float(a.ny);
+        const float reach = float(a.d_rep) + 2e-3f;
+        const int sown0 = a.mem_seg_off[m] + k0 / 32, sown1 = a.mem_seg_off[m] + (k0 + kn + 31) / 32;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int base = 0; base < a.nseg; base += blockDim.x) {
+            const int sg = base + threadIdx.x;
+            bool hit = false;
+            if (sg < a.nseg && a.seg_mem[sg] != m) {
+                const float4 b = a.seg_box[sg];
+                for (int so = sown0; so < sown1 && !hit; ++so) {
+                    const float4 o = a.seg_box[so];
+                    const float dx = wrap_half(b.x - o.x, Lx);
+                    float dy = b.y - o.y;
+                    if (!a.walls) dy = wrap_half(dy, Ly);
+                    hit = fabsf(dx) <= b.z + o.z + reach && fabsf(dy) <= b.w + o.w + reach;
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            __syncthreads();  // s_ncand of the previous pass is final
+            if (lane == 0) s_wcnt[wid] = __popc(bal);
+            __syncthreads();
+            int pos = s_ncand;
+            for (int w = 0; w < wid; ++w) pos += s_wcnt[w];
+            pos += __popc(bal & ((1u << lane) - 1u));
+            if (hit && pos < kMaxCand) s_cand[pos] = sg;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int t = s_ncand;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_wcnt[w];
+                s_ncand = t;
+            }
+        }
+    }
     __syncthreads();
+    // more candidates than the list holds: fall back to screening every segment
+    const int ncand = s_ncand;
+    const bool all_segs = ncand > kMaxCand;
 
     C* F = static_cast<C*>(a.F);
     C* W = static_cast<C*>(a.W);
@@ -202,12 +249,14 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         }
         // Eq. repFor against vertices of other membranes closer than d_rep:
         // segment boxes are screened in FP32 (wrapped x), close pairs in FP64
-        if (a.nmem > 1) {
+        if (repel && (ncand > 0)) {
             const float Lx = float(a.nx), Ly = float(a.ny);
             const float xvw = float(xv - nxd * floor(xv * a.inv_nx));
             const float yvf = float(yv);
             const float reach = float(a.d_rep) + 1e-3f;
-            for (int sg = 0; sg < a.nseg; ++sg) {
+            const int nscan = all_segs ? a.nseg : ncand;
+            for (int ci = 0; ci < nscan; ++ci) {
+                const int sg = all_segs ? ci : s_cand[ci];
                 if (a.seg_mem[sg] == m) continue;
                 const float4 bx = a.seg_box[sg];
                 const float ddx = wrap_half(xvw - bx.x, Lx);
