@@ -260,14 +260,14 @@ static lbib_status finalize(lbib_ctx* c) {
 
     const int nv = c->nv, nm = c->nmem, nl = c->nlig;
     const int nr = c->have_receptors ? (int)(c->h_rec.size() / 2) : 0;
-    // segments of 32 consecutive vertices per membrane
+    // repulsion-screening segments of kSegV consecutive vertices per membrane
     std::vector<int> seg_mem, seg_v0, seg_n, mem_seg_off(nm + 1, 0);
     for (int m = 0; m < nm; ++m) {
         mem_seg_off[m] = (int)seg_mem.size();
-        for (int s = 0; s < c->h_mem_n[m]; s += 32) {
+        for (int s = 0; s < c->h_mem_n[m]; s += kSegV) {
             seg_mem.push_back(m);
             seg_v0.push_back(c->h_mem_off[m] + s);
-            seg_n.push_back(std::min(32, c->h_mem_n[m] - s));
+            seg_n.push_back(std::min(kSegV, c->h_mem_n[m] - s));
         }
     }
     mem_seg_off[nm] = (int)seg_mem.size();
@@ -459,6 +459,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
     a.inv_rc_w = 1.0 / rc_w; a.inv_rc_h = 1.0 / rc_h;
     a.inv_y_eq = c->bp.y_eq > 0 ? 1.0 / c->bp.y_eq : 0.0;
+    a.d_cut2 = (c->bp.d_cut * (1.0 + 1e-12)) * (c->bp.d_cut * (1.0 + 1e-12));
     a.sigma = c->bp.sigma; a.y_eq = c->bp.y_eq; a.d_cut = c->bp.d_cut; a.d_break = c->bp.d_break;
     a.kf_dt = c->bp.kf_dt; a.kr0_dt = c->bp.kr0_dt; a.beta_f = c->bp.beta_f; a.beta_r = c->bp.beta_r;
     a.seed = c->bp.seed; a.instance = c->bp.instance;

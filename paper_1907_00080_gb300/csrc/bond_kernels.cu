@@ -54,11 +54,14 @@ __device__ __forceinline__ double p_rupture(const MarkerArgs& a, double d) {
 // periodic minimum image (multiplication by 1/L: no FP64 division)
 __device__ __forceinline__ double wrapd(double d, double L, double invL) { return d - L * floor(d * invL + 0.5); }
 
-__device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, double cyp, int r) {
+__device__ __forceinline__ double lig_rec_dist2(const MarkerArgs& a, double cxp, double cyp, int r) {
     const double dx = wrapd(a.rec_xy[2 * r] - cxp, (double)a.nx, a.inv_nx);
     double dy = a.rec_xy[2 * r + 1] - cyp;
     if (!a.walls) dy = wrapd(dy, (double)a.ny, a.inv_ny);
-    return sqrt(dx * dx + dy * dy);
+    return dx * dx + dy * dy;
+}
+__device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, double cyp, int r) {
+    return sqrt(lig_rec_dist2(a, cxp, cyp, r));
 }
 
 // Last-block epilogue: every block counts itself in once it is done; the block
@@ -120,7 +123,9 @@ __global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
                     for (int p = p0 + ((lane - t) % 32 + 32) % 32; p < p1; p += 32) {
                         const int rr = a.rcell_ids[p];
                         if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
-                        const double d = lig_rec_dist(a, cxp, cyp, rr);
+                        const double d2 = lig_rec_dist2(a, cxp, cyp, rr);
+                        if (!(d2 < a.d_cut2)) continue;  // clearly beyond the cut-off
+                        const double d = sqrt(d2);
                         if (!(d < a.d_cut)) continue;
                         if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
                     }

@@ -25,7 +25,14 @@ __device__ __forceinline__ float wrap_half(float d, float L) {
 // force value to the fixed-point grid of the spread field (scaled by 2^52)
 template <typename C> __device__ __forceinline__ long long to_fix(C v);
 template <> __device__ __forceinline__ long long to_fix<float>(float v) {
-    return __float2ll_rn(v * 4503599627370496.0f);
+    // exact: t = v 2^52 is either below 2^23 in magnitude (round it with a 32-bit
+    // conversion) or an integer whose mantissa is shifted into place
+    const float t = v * 4503599627370496.0f;
+    if (fabsf(t) < 8388608.0f) return (long long)__float2int_rn(t);
+    const int bits = __float_as_int(t);
+    const int e = ((bits >> 23) & 0xff) - 150;  // t = mant 2^e with e >= 0 here
+    const long long mag = (long long)((bits & 0x7fffff) | 0x800000) << (e < 40 ? e : 40);
+    return bits < 0 ? -mag : mag;
 }
 template <> __device__ __forceinline__ long long to_fix<double>(double v) {
     return __double2ll_rn(v * kFixScale);
@@ -70,6 +77,23 @@ __device__ double block_sum(double v, double* red) {
     __syncthreads();
     if (threadIdx.x < 32) {
         double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// block-wide sum in the compute type (all threads get it)
+template <typename C>
+__device__ C block_sum_c(C v, C* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        C t = threadIdx.x < nw ? red[threadIdx.x] : C(0);
         for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
         if (threadIdx.x == 0) red[32] = t;
     }
@@ -195,7 +219,8 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
     if (repel) {
         const float Lx = float(a.nx), Ly = float(a.ny);
         const float reach = float(a.d_rep) + 2e-3f;
-        const int sown0 = a.mem_seg_off[m] + k0 / 32, sown1 = a.mem_seg_off[m] + (k0 + kn + 31) / 32;
+        const int sown0 = a.mem_seg_off[m] + k0 / kSegV;
+        const int sown1 = a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int base = 0; base < a.nseg; base += blockDim.x) {
             const int sg = base + threadIdx.x;
@@ -422,25 +447,50 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
 // ---------------------------------------------------------------- advance
 // one warp: bounding box of a 32-vertex segment, stored as FP32 with the
 // centre's x wrapped into [0, nx)
-__device__ void seg_box_warp(const MarkerArgs& a, int sg, int lane) {
-    const int v0 = a.seg_v0[sg], nb = a.seg_n[sg];
-    const int v = v0 + (lane < nb ? lane : 0);
-    const double ax = a.X[2 * v0], ay = a.X[2 * v0 + 1];
-    const double px = a.X[2 * v], py = a.X[2 * v + 1];
-    if (lane < nb) a.xoff[v] = make_float2(float(px - ax), float(py - ay));
-    double lo_x = px, hi_x = px, lo_y = py, hi_y = py;
-    for (int o = 16; o > 0; o >>= 1) {
-        lo_x = fmin(lo_x, __shfl_xor_sync(FULL, lo_x, o));
-        hi_x = fmax(hi_x, __shfl_xor_sync(FULL, hi_x, o));
-        lo_y = fmin(lo_y, __shfl_xor_sync(FULL, lo_y, o));
-        hi_y = fmax(hi_y, __shfl_xor_sync(FULL, hi_y, o));
+// One group of kSegV lanes per segment: FP32 offsets of the vertices from the
+// segment's first vertex (the anchor), their bounding box reduced within the
+// group, stored with the centre's x wrapped into [0, nx).  All 32 lanes of the
+// warp call this; `sg` is this lane group's segment or -1.
+__device__ void seg_box_group(const MarkerArgs& a, int sg, int lane) {
+    const int g = lane & (kSegV - 1);
+    int v0 = 0, nb = 0;
+    if (sg >= 0) {
+        v0 = a.seg_v0[sg];
+        nb = a.seg_n[sg];
     }
-    if (lane == 0) {
-        const double cxd = 0.5 * (lo_x + hi_x);
+    float ox = 0.f, oy = 0.f;
+    double ax = 0.0, ay = 0.0;
+    if (nb > 0) {
+        ax = a.X[2 * v0];
+        ay = a.X[2 * v0 + 1];
+        const int v = v0 + (g < nb ? g : 0);
+        ox = float(a.X[2 * v] - ax);
+        oy = float(a.X[2 * v + 1] - ay);
+        if (g < nb) a.xoff[v] = make_float2(ox, oy);
+    }
+    float lo_x = ox, hi_x = ox, lo_y = oy, hi_y = oy;
+    for (int o = kSegV / 2; o > 0; o >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(FULL, lo_x, o));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(FULL, hi_x, o));
+        lo_y = fminf(lo_y, __shfl_xor_sync(FULL, lo_y, o));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(FULL, hi_y, o));
+    }
+    if (nb > 0 && g == 0) {
+        const double cxd = ax + 0.5 * (double)(lo_x + hi_x);
         const double cxw = cxd - (double)a.nx * floor(cxd * a.inv_nx);
-        a.seg_box[sg] = make_float4(float(cxw), float(0.5 * (lo_y + hi_y)),
-                                    float(0.5 * (hi_x - lo_x)), float(0.5 * (hi_y - lo_y)));
+        a.seg_box[sg] = make_float4(float(cxw), float(ay + 0.5 * (double)(lo_y + hi_y)),
+                                    0.5f * (hi_x - lo_x), 0.5f * (hi_y - lo_y));
         a.seg_anchor[sg] = make_double2(ax, ay);
+    }
+}
+
+// boxes of segments [s0, s1) by the warps of a block, kSegV lanes per segment
+__device__ void seg_boxes_block(const MarkerArgs& a, int s0, int s1) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int per_warp = 32 / kSegV;
+    for (int base = s0 + wid * per_warp; base < s1; base += nw * per_warp) {
+        const int sg = base + lane / kSegV;
+        seg_box_group(a, sg < s1 ? sg : -1, lane);
     }
 }
 
@@ -519,18 +569,16 @@ template <typename C>
 __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
     const int m = a.au[3 * blockIdx.x], k0 = a.au[3 * blockIdx.x + 1], kn = a.au[3 * blockIdx.x + 2];
     const int off = a.mem_off[m], n = a.mem_n[m];
-    __shared__ double red[33];
+    __shared__ C cred[33];
     const long long step = *a.d_step;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (a.mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED) {
         for (int j = threadIdx.x; j < kn; j += blockDim.x) {
             interp_vertex<C>(a, off + k0 + j);
             advance_vertex<C>(a, off + k0 + j, step);
         }
         __syncthreads();
-        // boxes of the 32-vertex segments this chunk covers (chunks are 32-aligned)
-        const int s0 = a.mem_seg_off[m] + k0 / 32, s1 = a.mem_seg_off[m] + (k0 + kn + 31) / 32;
-        for (int sg = s0 + wid; sg < s1; sg += nw) seg_box_warp(a, sg, lane);
+        // boxes of the segments this chunk covers (chunks are segment-aligned)
+        seg_boxes_block(a, a.mem_seg_off[m] + k0 / kSegV, a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV);
     } else {
         C* U = static_cast<C*>(a.U);
         double* X = a.X;
@@ -548,8 +596,8 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
             sv += U[2 * v + 1];
         }
         const C inv_n = C(1) / C(n);
-        const C mx = C(block_sum((double)sx, red)) * inv_n, my = C(block_sum((double)sy, red)) * inv_n;
-        const C mu = C(block_sum((double)su, red)) * inv_n, mv = C(block_sum((double)sv, red)) * inv_n;
+        const C mx = block_sum_c<C>(sx, cred) * inv_n, my = block_sum_c<C>(sy, cred) * inv_n;
+        const C mu = block_sum_c<C>(su, cred) * inv_n, mv = block_sum_c<C>(sv, cred) * inv_n;
         C num = 0, den = 0;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int v = off + k;
@@ -557,7 +605,7 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
             num += rx * (U[2 * v + 1] - mv) - ry * (U[2 * v] - mu);
             den += rx * rx + ry * ry;
         }
-        const C om = C(block_sum((double)num, red)) / C(block_sum((double)den, red));
+        const C om = block_sum_c<C>(num, cred) / block_sum_c<C>(den, cred);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int v = off + k;
             const C rx = C(X[2 * v] - xr) - mx, ry = C(X[2 * v + 1] - yr) - my;
@@ -567,7 +615,7 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         __syncthreads();
         for (int k = threadIdx.x; k < n; k += blockDim.x) advance_vertex<C>(a, off + k, step);
         __syncthreads();
-        for (int sg = a.mem_seg_off[m] + wid; sg < a.mem_seg_off[m + 1]; sg += nw) seg_box_warp(a, sg, lane);
+        seg_boxes_block(a, a.mem_seg_off[m], a.mem_seg_off[m + 1]);
     }
     // without bond kinetics nothing later in the step reads the step counter
     if (a.bump_in_advance && arrive_last(&a.tickets[0])) {
@@ -580,9 +628,9 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
 
 // segment boxes alone (before the first step and after user-written markers)
 __global__ void k_seg_boxes(const MarkerArgs a) {
-    const int sg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (sg >= a.nseg) return;
-    seg_box_warp(a, sg, threadIdx.x & 31);
+    constexpr int per_block = (256 / 32) * (32 / kSegV);
+    const int s0 = blockIdx.x * per_block;
+    seg_boxes_block(a, s0, min(a.nseg, s0 + per_block));
 }
 
 __global__ void k_areas(const MarkerArgs a, double* areas) {
@@ -622,7 +670,8 @@ cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_
 
 cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s) {
     if (a.nseg == 0) return cudaSuccess;
-    k_seg_boxes<<<(a.nseg + 7) / 8, 256, 0, s>>>(a);
+    constexpr int per_block = (256 / 32) * (32 / kSegV);
+    k_seg_boxes<<<(a.nseg + per_block - 1) / per_block, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,10 @@ struct alignas(sizeof(S) * VEC) Pack {
 // fixed-point force value (scaled by 2^52) to the compute type
 template <typename C> __device__ __forceinline__ C from_fix(long long v);
 template <> __device__ __forceinline__ float from_fix<float>(long long v) {
-    return __ll2float_rn(v) * 2.220446049250313e-16f;
+    // two 32-bit conversions instead of a 64-bit one: hi 2^32 + lo, scaled by 2^-52
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 9.5367431640625e-07f, (float)lo * 2.220446049250313e-16f);
 }
 template <> __device__ __forceinline__ double from_fix<double>(long long v) {
     return __ll2double_rn(v) * kFixInv;

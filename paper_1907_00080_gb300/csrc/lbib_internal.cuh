@@ -151,6 +151,7 @@ struct MarkerArgs {
     int rc_nx, rc_ny;         // receptor grid
     double rc_w, rc_h, rc_y0; // cell size, y origin
     double inv_rc_w, inv_rc_h, inv_y_eq;
+    double d_cut2;            // (d_cut (1 + 1e-12))^2, a conservative pre-check
     double sigma, y_eq, d_cut, d_break, kf_dt, kr0_dt, beta_f, beta_r;
     uint64_t seed, instance;
     // tiles of the fused kernel, spreading target of this step
@@ -170,6 +171,7 @@ struct MarkerArgs {
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2 };
 
 constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of 32)
+constexpr int kSegV = 8;      // vertices per repulsion-screening segment (divides kChunkV)
 
 // ---------------------------------------------------------------- launchers
 // lb_kernels.cu
