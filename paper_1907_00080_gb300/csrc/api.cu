@@ -338,10 +338,10 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * (nm + 1)); add(4 * (nm + 1)); add(4 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1));
         add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
         add(16 * nv); add(16 * nv); add(2 * cs * nv); add(2 * cs * nv); add(9 * cs * nv); add(8 * nv);
-        add(32 * nv); add(4 * nv); add(8 * nv);
-        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
+        add(32 * nv); add(4 * nv); add(16 * nv + 16 * nr);
+        add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
         add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
-        add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
+        add(16 * nr); add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
         add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
         bytes = probe.used + 256;
@@ -365,20 +365,19 @@ static lbib_status finalize(lbib_ctx* c) {
     double* ka = ar.take<double>(nm + 1);
     double* A0 = ar.take<double>(nm + 1);
     int* lig_off = ar.take<int>(nm + 2);
-    a.X = ar.take<double>(2 * (size_t)nv);
+    a.X = ar.take<double>(2 * (size_t)nv);   // 16 bytes per vertex in either layout
     a.Xp = ar.take<double>(2 * (size_t)nv);
+    c->xy_stage = ar.take<double>(2 * (size_t)nv + 2 * (size_t)nr);
     a.F = ar.take<char>(2 * cs * nv);
     a.U = ar.take<char>(2 * cs * nv);
     a.W = ar.take<char>(9 * cs * nv);
     a.stencil = ar.take<int>(2 * (size_t)nv);
     double* rest = ar.take<double>(4 * (size_t)nv);
     int* elig = ar.take<int>(nv);
-    a.xoff = ar.take<float2>(nv);
     int* d_seg_mem = ar.take<int>(c->nseg);
     int* d_seg_v0 = ar.take<int>(c->nseg);
     int* d_seg_n = ar.take<int>(c->nseg);
     a.seg_box = ar.take<float4>(c->nseg);
-    a.seg_anchor = ar.take<double2>(c->nseg);
     int* d_mem_seg_off = ar.take<int>(nm + 1);
     int* d_lig_a = ar.take<int>(nl);
     int* d_lig_b = ar.take<int>(nl);
@@ -386,6 +385,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.cand = ar.take<int>(nl);
     a.rupt = ar.take<int>(nl);
     double* rec_xy = ar.take<double>(2 * (size_t)nr);
+    void* rec_e = ar.take<double>(2 * (size_t)nr);
     a.owner = ar.take<int>(nr);
     a.claim = ar.take<int>(nr);
     int* d_rcs = ar.take<int>(rcell_start.size());
@@ -411,8 +411,9 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(kb, c->h_kb.data(), 8 * nm));
         CK(H2D(ka, c->h_ka.data(), 8 * nm));
         CK(H2D(lig_off, mem_lig_off.data(), 4 * (nm + 1)));
-        CK(H2D(a.X, c->h_xy.data(), 16 * (size_t)nv));
-        CK(H2D(a.Xp, c->h_xy.data(), 16 * (size_t)nv));
+        CK(H2D(c->xy_stage, c->h_xy.data(), 16 * (size_t)nv));
+        CK(launch_pos_in(c->prec, c->xy_stage, a.X, nv, c->stream));
+        CK(launch_pos_in(c->prec, c->xy_stage, a.Xp, nv, c->stream));
         CK(cudaMemsetAsync(a.F, 0, 2 * cs * nv, c->stream));
         CK(cudaMemsetAsync(a.U, 0, 2 * cs * nv, c->stream));
         CK(H2D(elig, elem_lig.data(), 4 * (size_t)nv));
@@ -432,6 +433,7 @@ static lbib_status finalize(lbib_ctx* c) {
     }
     if (nr > 0) {
         CK(H2D(rec_xy, c->h_rec.data(), 16 * (size_t)nr));
+        CK(launch_pos_in(c->prec, rec_xy, rec_e, nr, c->stream));
         CK(cudaMemsetAsync(a.owner, 0xFF, 4 * nr, c->stream));
         CK(cudaMemsetAsync(a.claim, 0x7F, 4 * nr, c->stream));  // 0x7F7F7F7F: no claim
     }
@@ -455,7 +457,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
     a.nfu = (int)(fu.size() / 3); a.nau = (int)(au.size() / 3); a.fu = d_fu; a.au = d_au;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
-    a.rec_xy = rec_xy; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
+    a.rec_xy = rec_xy; a.rec_e = rec_e; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
     a.inv_rc_w = 1.0 / rc_w; a.inv_rc_h = 1.0 / rc_h;
     a.inv_y_eq = c->bp.y_eq > 0 ? 1.0 / c->bp.y_eq : 0.0;
@@ -470,7 +472,7 @@ static lbib_status finalize(lbib_ctx* c) {
 
     if (nm > 0) {
         CK(launch_rest(c->prec, a, rest, A0, c->stream));
-        CK(launch_seg_boxes(a, c->stream));
+        CK(launch_seg_boxes(c->prec, a, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));
     c->finalized = true;
@@ -512,7 +514,7 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     if ((e = launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, has_ib, l, s)) != cudaSuccess)
         return e;
     if (has_ib && (e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
-    return launch_bonds(a, s);
+    return launch_bonds(c->prec, a, s);
 }
 
 static lbib_status build_graphs(lbib_ctx* c) {
@@ -675,7 +677,8 @@ extern "C" lbib_status lbib_read_markers(lbib_ctx* c, int32_t m, double* xy) {
     if (c->nv == 0) return LBIB_OK;
     const int off = m < 0 ? 0 : c->h_mem_off[m];
     const int n = m < 0 ? c->nv : c->h_mem_n[m];
-    CK(cudaMemcpyAsync(xy, c->ma.X + 2 * (size_t)off, 16 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CK(launch_pos_out(c->prec, c->ma.X, c->xy_stage, c->nv, c->stream));
+    CK(cudaMemcpyAsync(xy, c->xy_stage + 2 * (size_t)off, 16 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBIB_OK;
 }
@@ -686,9 +689,11 @@ extern "C" lbib_status lbib_write_markers(lbib_ctx* c, const double* xy, const d
     if (st != LBIB_OK) return st;
     if (c->nv == 0) return LBIB_OK;
     const size_t b = 16 * (size_t)c->nv;
-    CK(cudaMemcpyAsync(c->ma.X, xy, b, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->ma.Xp, xy_prev ? xy_prev : xy, b, cudaMemcpyHostToDevice, c->stream));
-    CK(launch_seg_boxes(c->ma, c->stream));
+    CK(cudaMemcpyAsync(c->xy_stage, xy, b, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.X, c->nv, c->stream));
+    CK(cudaMemcpyAsync(c->xy_stage, xy_prev ? xy_prev : xy, b, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.Xp, c->nv, c->stream));
+    CK(launch_seg_boxes(c->prec, c->ma, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBIB_OK;
 }
@@ -760,7 +765,7 @@ extern "C" lbib_status lbib_diagnostics(lbib_ctx* c, double* mass, double* areas
         CK(cudaMemcpyAsync(mass, c->dscalar, 8, cudaMemcpyDeviceToHost, c->stream));
     }
     if (areas && c->nmem > 0) {
-        CK(launch_areas(c->ma, c->d_areas, c->stream));
+        CK(launch_areas(c->prec, c->ma, c->d_areas, c->stream));
         CK(cudaMemcpyAsync(areas, c->d_areas, 8 * (size_t)c->nmem, cudaMemcpyDeviceToHost, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));

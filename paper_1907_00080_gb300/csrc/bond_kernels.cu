@@ -9,6 +9,7 @@
 // as 1, 2, 3", SC'11 -- implemented here from that definition.
 #include <climits>
 
+#include "ext_real.cuh"
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -64,6 +65,101 @@ __device__ __forceinline__ double lig_rec_dist(const MarkerArgs& a, double cxp, 
     return sqrt(lig_rec_dist2(a, cxp, cyp, r));
 }
 
+// FP32 estimates used to settle clear-cut decisions without the FP64 pipe;
+// anything within kMargin of the threshold is decided again in FP64, so the
+// outcome is the FP64 decision.  The estimates are accurate to ~1e-6.
+constexpr float kMargin = 1e-5f;
+__device__ __forceinline__ float p_form_f(const MarkerArgs& a, float d) {
+    const float z = (d - float(a.y_eq)) * float(a.inv_y_eq);
+    return 1.0f - expf(-float(a.kf_dt) * expf(-float(a.beta_f) * z * z));
+}
+__device__ __forceinline__ float p_rupture_f(const MarkerArgs& a, float d) {
+    const float z = (d - float(a.y_eq)) * float(a.inv_y_eq);
+    return 1.0f - expf(-float(a.kr0_dt) * expf(float(a.beta_r) * z * z));
+}
+
+// Ligand point (element centroid) and its distance to receptor r: the cheap
+// estimate in the compute precision, and the FP64 value on demand.
+template <typename C>
+struct LigandPoint {
+    typename Ext<C>::E cx, cy;
+    double cxd, cyd;
+    bool have_d;
+    __device__ void init(const MarkerArgs& a, int l) {
+        typename Ext<C>::E xa, ya, xb, yb;
+        PosIO<C>::load(a.X, a.lig_a[l], xa, ya);
+        PosIO<C>::load(a.X, a.lig_b[l], xb, yb);
+        cx = emulc(eadd(xa, xb), C(0.5));
+        cy = emulc(eadd(ya, yb), C(0.5));
+        have_d = false;
+    }
+    __device__ bool finite() const { return isfinite(ehi(cx)) && isfinite(ehi(cy)); }
+    __device__ C dist_est(const MarkerArgs& a, int r) const {
+        typename Ext<C>::E rx, ry;
+        PosIO<C>::load(a.rec_e, r, rx, ry);
+        const C dx = etoc(ewrap(esub(rx, cx), C(a.nx), C(a.inv_nx)));
+        C dy = etoc(esub(ry, cy));
+        if (!a.walls) dy = etoc(ewrap(esub(ry, cy), C(a.ny), C(a.inv_ny)));
+        return sqrt(dx * dx + dy * dy);
+    }
+    __device__ double dist(const MarkerArgs& a, int r) {
+        if (!have_d) {
+            cxd = etod(cx);
+            cyd = etod(cy);
+            have_d = true;
+        }
+        return lig_rec_dist(a, cxd, cyd, r);
+    }
+};
+
+// Eq.-free decisions of the bond model: `below(u, P)` style tests with the FP32
+// estimate first and FP64 where the estimate cannot settle it
+template <typename C>
+__device__ bool forms(const MarkerArgs& a, LigandPoint<C>& lp, long long step, int l, int r) {
+    if (sizeof(C) == 8) {
+        const double d = lp.dist(a, r);
+        if (!(d < a.d_cut)) return false;
+        return bond_uniform(a, step, l, r, 0) < p_form(a, d);
+    }
+    const float df = float(lp.dist_est(a, r));
+    const float dc = float(a.d_cut);
+    if (!(df < dc * (1.f + kMargin))) return false;  // surely beyond the cut-off
+    double d = -1.0;
+    if (!(df < dc * (1.f - kMargin))) {
+        d = lp.dist(a, r);
+        if (!(d < a.d_cut)) return false;
+    }
+    const double u = bond_uniform(a, step, l, r, 0);
+    const float pf = p_form_f(a, df);
+    if (u < (double)(pf - kMargin)) return true;
+    if (u > (double)(pf + kMargin)) return false;
+    if (d < 0.0) d = lp.dist(a, r);
+    return u < p_form(a, d);
+}
+
+template <typename C>
+__device__ bool ruptures(const MarkerArgs& a, LigandPoint<C>& lp, long long step, int l, int r) {
+    if (sizeof(C) == 8) {
+        const double d = lp.dist(a, r);
+        if (d >= a.d_break) return true;
+        return bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+    }
+    const float df = float(lp.dist_est(a, r));
+    const float db = float(a.d_break);
+    double d = -1.0;
+    if (df >= db * (1.f + kMargin)) return true;
+    if (!(df < db * (1.f - kMargin))) {
+        d = lp.dist(a, r);
+        if (d >= a.d_break) return true;
+    }
+    const double u = bond_uniform(a, step, l, r, 1);
+    const float pr = p_rupture_f(a, df);
+    if (u < (double)(pr - kMargin)) return true;
+    if (u > (double)(pr + kMargin)) return false;
+    if (d < 0.0) d = lp.dist(a, r);
+    return u < p_rupture(a, d);
+}
+
 // Last-block epilogue: every block counts itself in once it is done; the block
 // that arrives last (it sees all other blocks' writes after the fences) runs the
 // epilogue and resets the counter.  No block ever waits for another.
@@ -86,22 +182,20 @@ __device__ bool arrive_last_b(unsigned int* counter) {
 // atomicMin so that the lowest ligand id wins.  The last block to finish applies
 // ruptures and winning claims for all ligands, clears the claims and advances
 // the step counter.
+template <typename C>
 __global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
     const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const long long step = *a.d_step;
     if (l < a.nlig) {  // warp-uniform
-        const int va = a.lig_a[l], vb = a.lig_b[l];
-        const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
-        const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
-        bool look = isfinite(cxp) && isfinite(cyp);  // non-finite positions: reported by the advance
+        LigandPoint<C> lp;
+        lp.init(a, l);
+        bool look = lp.finite();  // non-finite positions: reported by the advance
         const int r = a.bond_of_lig[l];
         if (look && r >= 0) {
             int rupture = 0;
             if (lane == 0) {
-                const double d = lig_rec_dist(a, cxp, cyp, r);
-                rupture = d >= a.d_break;
-                if (!rupture) rupture = bond_uniform(a, step, l, r, 1) < p_rupture(a, d);
+                rupture = ruptures<C>(a, lp, step, l, r);
                 if (rupture) a.rupt[l] = r;
             }
             look = __shfl_sync(0xffffffffu, rupture, 0) != 0;
@@ -109,10 +203,13 @@ __global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
         int best = INT_MAX;
         if (look) {
             // receptors within d_cut lie in the 3x3 block of grid cells around the ligand point
-            const double xw = cxp - (double)a.nx * floor(cxp * a.inv_nx);
-            int gx = (int)floor(xw * a.inv_rc_w);
+            const float cxh = float(ehi(lp.cx)), cyh = float(ehi(lp.cy));
+            const float Lx = float(a.nx);
+            const float xw = cxh - Lx * floorf(cxh / Lx);
+            int gx = (int)floorf(xw * float(a.inv_rc_w));
             gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
-            const int gy = (int)fmin(fmax(floor((cyp - a.rc_y0) * a.inv_rc_h), -4.0), (double)a.rc_ny + 4.0);
+            const int gy = (int)fminf(fmaxf(floorf((cyh - float(a.rc_y0)) * float(a.inv_rc_h)), -4.f),
+                                      float(a.rc_ny) + 4.f);
             int t = 0;  // running index over the candidate receptors
             for (int qy = gy - 1; qy <= gy + 1; ++qy) {
                 if (qy < 0 || qy >= a.rc_ny) continue;
@@ -123,11 +220,7 @@ __global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
                     for (int p = p0 + ((lane - t) % 32 + 32) % 32; p < p1; p += 32) {
                         const int rr = a.rcell_ids[p];
                         if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
-                        const double d2 = lig_rec_dist2(a, cxp, cyp, rr);
-                        if (!(d2 < a.d_cut2)) continue;  // clearly beyond the cut-off
-                        const double d = sqrt(d2);
-                        if (!(d < a.d_cut)) continue;
-                        if (bond_uniform(a, step, l, rr, 0) < p_form(a, d)) best = rr;
+                        if (forms<C>(a, lp, step, l, rr)) best = rr;
                     }
                     t += p1 - p0;
                 }
@@ -168,8 +261,11 @@ __global__ void __launch_bounds__(128) k_bonds(const MarkerArgs a) {
     }
 }
 
-cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s) {
-    if (a.nlig > 0 && a.nrec > 0) k_bonds<<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
+cudaError_t launch_bonds(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
+    if (a.nlig > 0 && a.nrec > 0) {
+        if (prec == LBIB_F64) k_bonds<double><<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
+        else k_bonds<float><<<(a.nlig + 3) / 4, 128, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -1,23 +1,23 @@
 // Lagrangian-side kernels: membrane forces (stretching, bending, enclosed
-// area, repulsion, bond springs), IB shape functions and tile binning, the
-// deterministic tile lists, and the interpolation + kinematic advance.
+// area, repulsion, bond springs), the IB shape functions and the spreading of
+// the marker forces, and the interpolation + kinematic advance.
 //
 // Paper: Coclite, arXiv 1907.00080, Sec. 2.2 (Eqs. strainFor, bendFor,
 // areaFor, repFor, adhFor; MLS exchange), Sec. 2.3 (nine Eulerian points per
 // vertex, Eq. kinematicPos).
+//
+// Precision: the compute type C is double in FP64 mode and float otherwise;
+// positions and every cancellation-prone product use the matching extended
+// type E (double, or float-float) from ext_real.cuh.
 #include <climits>
 
+#include "ext_real.cuh"
 #include "lbib_internal.cuh"
 
 namespace lbib {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// periodic minimum image, multiplying by 1/L (an FP64 division is a long
-// instruction sequence on this part)
-__device__ __forceinline__ double wrap_m(double d, double L, double invL) {
-    return d - L * floor(d * invL + 0.5);
-}
 __device__ __forceinline__ float wrap_half(float d, float L) {
     return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
 }
@@ -50,38 +50,63 @@ __device__ __forceinline__ C roma(C r) {
     return C(0);
 }
 
-// Edge products at a vertex, in FP64 with every product and sum rounded as
-// written (no contraction), so the rest shape reproduces them bit for bit:
-// squared length of e_R = x_{v+1} - x_v, cross and dot of e_L = x_v - x_{v-1}
-// with e_R.
+template <typename C>
+__device__ __forceinline__ void load_pos(const MarkerArgs& a, int v, typename Ext<C>::E& x,
+                                         typename Ext<C>::E& y) {
+    PosIO<C>::load(a.X, v, x, y);
+}
+
+// Edge products at a vertex in the extended type: squared length of
+// e_R = x_{v+1} - x_v, and the cross and dot products of e_L = x_v - x_{v-1}
+// with e_R (their rotation from the rest pair gives theta - theta_0).
+template <typename C>
 struct EdgeProducts {
-    double lsqR, cross, dot;
+    typename Ext<C>::E lsqR, cross, dot;
 };
-__device__ __forceinline__ EdgeProducts edge_products(double xL, double yL, double xv, double yv,
-                                                      double xR, double yR) {
-    const double eLx = __dsub_rn(xv, xL), eLy = __dsub_rn(yv, yL);
-    const double eRx = __dsub_rn(xR, xv), eRy = __dsub_rn(yR, yv);
-    EdgeProducts p;
-    p.lsqR = __dadd_rn(__dmul_rn(eRx, eRx), __dmul_rn(eRy, eRy));
-    p.cross = __dsub_rn(__dmul_rn(eLx, eRy), __dmul_rn(eLy, eRx));
-    p.dot = __dadd_rn(__dmul_rn(eLx, eRx), __dmul_rn(eLy, eRy));
+template <typename C>
+__device__ __forceinline__ EdgeProducts<C> edge_products(const MarkerArgs& a, int L, int v, int R) {
+    using E = typename Ext<C>::E;
+    E xL, yL, xv, yv, xR, yR;
+    load_pos<C>(a, L, xL, yL);
+    load_pos<C>(a, v, xv, yv);
+    load_pos<C>(a, R, xR, yR);
+    const E eLx = esub(xv, xL), eLy = esub(yv, yL), eRx = esub(xR, xv), eRy = esub(yR, yv);
+    EdgeProducts<C> p;
+    p.lsqR = eadd(emul(eRx, eRx), emul(eRy, eRy));
+    p.cross = esub(emul(eLx, eRy), emul(eLy, eRx));
+    p.dot = eadd(emul(eLx, eRx), emul(eLy, eRy));
     return p;
 }
 
-// block-wide FP64 sum (blockDim multiple of 32, <= 1024); all threads get it
-__device__ double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
+// Enclosed area of membrane m by the shoelace formula about vertex 0, summed by
+// warp 0 of the calling block in a fixed order (lane l takes terms l, l+32, ...,
+// then a fixed tree), so every caller gets the same bits.  The result is in
+// red[32] after the call; all threads of the block must call it.
+template <typename C>
+__device__ void ring_area(const MarkerArgs& a, int m, typename Ext<C>::E* red) {
+    using E = typename Ext<C>::E;
+    const int off = a.mem_off[m], n = a.mem_n[m];
     if (threadIdx.x < 32) {
-        double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(FULL, t, o);
-        if (threadIdx.x == 0) red[32] = t;
+        E xr, yr;
+        load_pos<C>(a, off, xr, yr);
+        E acc = ezero<E>();
+        for (int k = threadIdx.x; k < n; k += 32) {
+            const int R = k == n - 1 ? 0 : k + 1;
+            E xv, yv, xR, yR;
+            load_pos<C>(a, off + k, xv, yv);
+            load_pos<C>(a, off + R, xR, yR);
+            const E t = esub(emul(esub(xv, xr), esub(yR, yr)), emul(esub(xR, xr), esub(yv, yr)));
+            acc = eadd(acc, t);
+        }
+        red[threadIdx.x] = acc;
+        __syncwarp();
+        for (int o = 16; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] = eadd(red[threadIdx.x], red[threadIdx.x + o]);
+            __syncwarp();
+        }
+        if (threadIdx.x == 0) red[32] = emulc(red[0], C(0.5));
     }
     __syncthreads();
-    return red[32];
 }
 
 // block-wide sum in the compute type (all threads get it)
@@ -106,91 +131,90 @@ __device__ C block_sum_c(C v, C* red) {
 // (v, v+1) and the rest cross/dot products of the two edges at v (which fix the
 // rest turning angle theta_0), plus A_0 per membrane -- with the arithmetic the
 // force kernel repeats, so the rest shape gives exactly zero force.
-__global__ void k_rest(const MarkerArgs a, double* rest, double* A0) {
+template <typename C>
+__global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0) {
+    using E = typename Ext<C>::E;
     const int m = blockIdx.x;
     const int off = a.mem_off[m], n = a.mem_n[m];
-    __shared__ double red[33];
-    const double* X = a.X;
-    const double xr = X[2 * off], yr = X[2 * off + 1];
-    double ap = 0.0;
+    __shared__ E red[33];
+    Rest<C>* rest = static_cast<Rest<C>*>(rest_v);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
-        const EdgeProducts p = edge_products(X[2 * L], X[2 * L + 1], X[2 * v], X[2 * v + 1],
-                                             X[2 * R], X[2 * R + 1]);
-        rest[4 * (size_t)v + 0] = p.lsqR;
-        rest[4 * (size_t)v + 1] = sqrt(p.lsqR);
-        rest[4 * (size_t)v + 2] = p.cross;
-        rest[4 * (size_t)v + 3] = p.dot;
-        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
+        const EdgeProducts<C> p = edge_products<C>(a, L, v, R);
+        Rest<C> r;
+        r.lsq = p.lsqR;
+        r.cross = p.cross;
+        r.dot = p.dot;
+        r.l0 = sqrt(etoc(p.lsqR));
+        rest[v] = r;
     }
-    const double s = block_sum(ap, red);
-    if (threadIdx.x == 0) A0[m] = 0.5 * s;
+    ring_area<C>(a, m, red);
+    if (threadIdx.x == 0) A0[m] = etod(red[32]);
 }
 
 // ---------------------------------------------------------------- forces
+// Eq. adhFor on element e (if its ligand is bonded), half to the vertex
 template <typename C>
-__device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, double nxd, double nyd,
-                                                C& Fx, C& Fy) {
+__device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, C& Fx, C& Fy) {
+    using E = typename Ext<C>::E;
     const int l = a.elem_lig[e];
     if (l < 0) return;
     const int r = a.bond_of_lig[l];
     if (r < 0) return;
-    const int va = a.lig_a[l], vb = a.lig_b[l];
-    const double cxp = 0.5 * (a.X[2 * va] + a.X[2 * vb]);
-    const double cyp = 0.5 * (a.X[2 * va + 1] + a.X[2 * vb + 1]);
-    const double dx = wrap_m(a.rec_xy[2 * r] - cxp, nxd, a.inv_nx);
-    double dy = a.rec_xy[2 * r + 1] - cyp;
-    if (!a.walls) dy = wrap_m(dy, nyd, a.inv_ny);
-    const double d = sqrt(dx * dx + dy * dy);
-    const double c = a.sigma * (d - a.y_eq) / d;
-    Fx += C(0.5 * c * dx);
-    Fy += C(0.5 * c * dy);
+    E xa, ya, xb, yb;
+    load_pos<C>(a, a.lig_a[l], xa, ya);
+    load_pos<C>(a, a.lig_b[l], xb, yb);
+    E rx, ry;
+    PosIO<C>::load(a.rec_e, r, rx, ry);
+    // receptor minus ligand point (element centroid)
+    const E cx = emulc(eadd(xa, xb), C(0.5)), cy = emulc(eadd(ya, yb), C(0.5));
+    const C dx = etoc(ewrap(esub(rx, cx), C(a.nx), C(a.inv_nx)));
+    C dy = etoc(esub(ry, cy));
+    if (!a.walls) dy = etoc(ewrap(esub(ry, cy), C(a.ny), C(a.inv_ny)));
+    const C d = sqrt(dx * dx + dy * dy);
+    const C c = C(a.sigma) * (d - C(a.y_eq)) / d;
+    Fx += C(0.5) * c * dx;
+    Fy += C(0.5) * c * dy;
 }
 
 // One block per work unit (a chunk of up to kChunkV consecutive vertices of one
-// membrane); one thread per vertex.  The enclosed area of the whole membrane is
-// summed by every unit of that membrane in the same fixed order (so all units
-// agree bit for bit), and the bending geometry of the chunk plus one halo
-// vertex on each side is staged in shared memory.
+// membrane); one thread per vertex.  Computes F^n, the nine shape functions at
+// X^n and spreads w_j F_v into the fixed-point force field.
 template <typename C>
 __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
+    using E = typename Ext<C>::E;
     const int m = a.fu[3 * blockIdx.x], k0 = a.fu[3 * blockIdx.x + 1], kn = a.fu[3 * blockIdx.x + 2];
     const int off = a.mem_off[m], n = a.mem_n[m];
     __shared__ C s_mnx[kChunkV + 2], s_mny[kChunkV + 2], s_sL[kChunkV + 2], s_sR[kChunkV + 2];
     __shared__ C s_nx[kChunkV + 2], s_ny[kChunkV + 2];
-    __shared__ double red[33];
-    const double* X = a.X;
-    const double nxd = (double)a.nx, nyd = (double)a.ny;
-    const double xr = X[2 * off], yr = X[2 * off + 1];
+    __shared__ E red[33];
+    const Rest<C>* rest = static_cast<const Rest<C>*>(a.rest);
     const C kb = C(a.mem_kb[m]);
 
-    // shoelace area about vertex 0 over the whole ring (FP64)
-    double ap = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k, R = off + (k == n - 1 ? 0 : k + 1);
-        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
-    }
-    const double A = 0.5 * block_sum(ap, red);
-    // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
-    const C ca = C(-a.mem_ka[m] * (1.0 - A / a.mem_A0[m]) * (1.0 / 3.0));
+    // enclosed area (Eq. areaFor) with p_ref = 1/3: F_l = c_a (inward normal) l_l
+    ring_area<C>(a, m, red);
+    const C ca = C(-a.mem_ka[m] * (1.0 - etod(red[32]) / a.mem_A0[m]) * (1.0 / 3.0));
     const C ks = C(a.mem_ks[m]);
 
     // vertex geometry of local slots j = 0..kn+1 (vertex k0 - 1 + j, wrapped).
     // theta - theta_0 comes from the rotation between the rest and the current
-    // edge pair, atan2(c d0 - d c0, d d0 + c c0), free of the cancellation of
+    // edge pair, atan2(c d0 - c0 d, d d0 + c c0), free of the cancellation of
     // subtracting two nearly equal angles.
     for (int j = threadIdx.x; j < kn + 2; j += blockDim.x) {
         int k = k0 - 1 + j;
         k = k < 0 ? k + n : (k >= n ? k - n : k);
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
-        const double xL = X[2 * L], yL = X[2 * L + 1], xv = X[2 * v], yv = X[2 * v + 1];
-        const double xR = X[2 * R], yR = X[2 * R + 1];
-        const EdgeProducts p = edge_products(xL, yL, xv, yv, xR, yR);
-        const double c0 = a.rest[4 * (size_t)v + 2], d0 = a.rest[4 * (size_t)v + 3];
-        const double sn = __dsub_rn(__dmul_rn(p.cross, d0), __dmul_rn(p.dot, c0));
-        const double cs = __dadd_rn(__dmul_rn(p.dot, d0), __dmul_rn(p.cross, c0));
-        const C dth = atan2(C(sn), C(cs));
-        const C eLx = C(xv - xL), eLy = C(yv - yL), eRx = C(xR - xv), eRy = C(yR - yv);
+        const EdgeProducts<C> p = edge_products<C>(a, L, v, R);
+        const Rest<C> r0 = rest[v];
+        const E sn = esub(emul(p.cross, r0.dot), emul(r0.cross, p.dot));
+        const E cs = eadd(emul(p.dot, r0.dot), emul(p.cross, r0.cross));
+        const C dth = atan2(etoc(sn), etoc(cs));
+        E xL, yL, xv, yv, xR, yR;
+        load_pos<C>(a, L, xL, yL);
+        load_pos<C>(a, v, xv, yv);
+        load_pos<C>(a, R, xR, yR);
+        const C eLx = etoc(esub(xv, xL)), eLy = etoc(esub(yv, yL));
+        const C eRx = etoc(esub(xR, xv)), eRy = etoc(esub(yR, yv));
         const C lL = sqrt(eLx * eLx + eLy * eLy), lR = sqrt(eRx * eRx + eRy * eRy);
         // outward vertex normal: normalised sum of the outward edge normals (CCW ring)
         C nx_ = eLy / lL + eRy / lR;
@@ -216,8 +240,8 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
     __shared__ int s_ncand;
     if (threadIdx.x == 0) s_ncand = 0;
     const bool repel = a.nmem > 1;
+    const float Lxf = float(a.nx), Lyf = float(a.ny);
     if (repel) {
-        const float Lx = float(a.nx), Ly = float(a.ny);
         const float reach = float(a.d_rep) + 2e-3f;
         const int sown0 = a.mem_seg_off[m] + k0 / kSegV;
         const int sown1 = a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV;
@@ -229,9 +253,9 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
                 const float4 b = a.seg_box[sg];
                 for (int so = sown0; so < sown1 && !hit; ++so) {
                     const float4 o = a.seg_box[so];
-                    const float dx = wrap_half(b.x - o.x, Lx);
+                    const float dx = wrap_half(b.x - o.x, Lxf);
                     float dy = b.y - o.y;
-                    if (!a.walls) dy = wrap_half(dy, Ly);
+                    if (!a.walls) dy = wrap_half(dy, Lyf);
                     hit = fabsf(dx) <= b.z + o.z + reach && fabsf(dy) <= b.w + o.w + reach;
                 }
             }
@@ -264,108 +288,95 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         const int kL = k == 0 ? n - 1 : k - 1, kR = k == n - 1 ? 0 : k + 1;
         const int v = off + k, L = off + kL, R = off + kR;
         const int sj = j + 1;  // shared-memory slot of vertex k
-        const double xv = X[2 * v], yv = X[2 * v + 1];
-        const double xl = X[2 * L], yl = X[2 * L + 1], xR = X[2 * R], yR = X[2 * R + 1];
+        E xv, yv, xl, yl, xR, yR;
+        load_pos<C>(a, v, xv, yv);
+        load_pos<C>(a, L, xl, yl);
+        load_pos<C>(a, R, xR, yR);
         C Fx = C(0), Fy = C(0);
         // Eq. adhFor on the two elements sharing v, half each
         if (a.nlig > 0) {
-            bond_on_element<C>(a, L, nxd, nyd, Fx, Fy);
-            bond_on_element<C>(a, v, nxd, nyd, Fx, Fy);
+            bond_on_element<C>(a, L, Fx, Fy);
+            bond_on_element<C>(a, v, Fx, Fy);
         }
         // Eq. repFor against vertices of other membranes closer than d_rep:
-        // segment boxes are screened in FP32 (wrapped x), close pairs in FP64
-        if (repel && (ncand > 0)) {
-            const float Lx = float(a.nx), Ly = float(a.ny);
-            const float xvw = float(xv - nxd * floor(xv * a.inv_nx));
-            const float yvf = float(yv);
-            const float reach = float(a.d_rep) + 1e-3f;
+        // candidate segments, then a per-vertex box test, then exact pairs
+        if (repel && ncand > 0) {
+            const float hx = float(ehi(xv));
+            const float xvw = hx - Lxf * floorf(hx / Lxf);
+            const float yvf = float(ehi(yv));
+            const float reach = float(a.d_rep) + 2e-3f;
             const int nscan = all_segs ? a.nseg : ncand;
             for (int ci = 0; ci < nscan; ++ci) {
                 const int sg = all_segs ? ci : s_cand[ci];
                 if (a.seg_mem[sg] == m) continue;
                 const float4 bx = a.seg_box[sg];
-                const float ddx = wrap_half(xvw - bx.x, Lx);
+                const float ddx = wrap_half(xvw - bx.x, Lxf);
                 float ddy = yvf - bx.y;
-                if (!a.walls) ddy = wrap_half(ddy, Ly);
+                if (!a.walls) ddy = wrap_half(ddy, Lyf);
                 if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
                 const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
-                if (sizeof(C) == 4) {
-                    // one FP64 offset to the segment anchor, then FP32 per vertex
-                    const double2 an = a.seg_anchor[sg];
-                    const float bxo = float(wrap_m(xv - an.x, nxd, a.inv_nx));
-                    double byd = yv - an.y;
-                    if (!a.walls) byd = wrap_m(byd, nyd, a.inv_ny);
-                    const float byo = float(byd);
-                    for (int b = b0; b < b0 + nb; ++b) {
-                        const float2 o = a.xoff[b];
-                        const C dx = C(bxo - o.x), dy = C(byo - o.y);
-                        const C d = sqrt(dx * dx + dy * dy);
-                        if (d < C(a.d_rep)) {
-                            const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
-                            Fx -= mag * s_nx[sj];
-                            Fy -= mag * s_ny[sj];
-                        }
-                    }
-                } else {
-                    for (int b = b0; b < b0 + nb; ++b) {
-                        const C dx = C(wrap_m(xv - X[2 * b], nxd, a.inv_nx));
-                        double dyd = yv - X[2 * b + 1];
-                        if (!a.walls) dyd = wrap_m(dyd, nyd, a.inv_ny);
-                        const C dy = C(dyd);
-                        const C d = sqrt(dx * dx + dy * dy);
-                        if (d < C(a.d_rep)) {
-                            const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
-                            Fx -= mag * s_nx[sj];
-                            Fy -= mag * s_ny[sj];
-                        }
+                for (int b = b0; b < b0 + nb; ++b) {
+                    E xb, yb;
+                    load_pos<C>(a, b, xb, yb);
+                    const C dx = etoc(ewrap(esub(xv, xb), C(a.nx), C(a.inv_nx)));
+                    C dy = etoc(esub(yv, yb));
+                    if (!a.walls) dy = etoc(ewrap(esub(yv, yb), C(a.ny), C(a.inv_ny)));
+                    const C d = sqrt(dx * dx + dy * dy);
+                    if (d < C(a.d_rep)) {
+                        const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
+                        Fx -= mag * s_nx[sj];
+                        Fy -= mag * s_ny[sj];
                     }
                 }
             }
         }
         // Eq. strainFor on elements (v, R) and (L, v); l - l_0 is formed as
-        // (l^2 - l_0^2) / (l + l_0) with the squares in FP64
+        // (l^2 - l_0^2) / (l + l_0) with the squares in the extended type
         {
-            const double ex = __dsub_rn(xR, xv), ey = __dsub_rn(yR, yv);
-            const double lsq = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
-            const C l = sqrt(C(lsq));
-            const C c = ks * C(__dsub_rn(lsq, a.rest[4 * (size_t)v])) / ((l + C(a.rest[4 * (size_t)v + 1])) * l);
-            Fx += c * C(ex);
-            Fy += c * C(ey);
-            const double gx = __dsub_rn(xv, xl), gy = __dsub_rn(yv, yl);
-            const double lsq2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
-            const C l2 = sqrt(C(lsq2));
-            const C c2 = -ks * C(__dsub_rn(lsq2, a.rest[4 * (size_t)L])) / ((l2 + C(a.rest[4 * (size_t)L + 1])) * l2);
-            Fx += c2 * C(gx);
-            Fy += c2 * C(gy);
+            const E ex = esub(xR, xv), ey = esub(yR, yv);
+            const E lsq = eadd(emul(ex, ex), emul(ey, ey));
+            const C l = sqrt(etoc(lsq));
+            const Rest<C> rv = rest[v];
+            const C c = ks * etoc(esub(lsq, rv.lsq)) / ((l + rv.l0) * l);
+            Fx += c * etoc(ex);
+            Fy += c * etoc(ey);
+            const E gx = esub(xv, xl), gy = esub(yv, yl);
+            const E lsq2 = eadd(emul(gx, gx), emul(gy, gy));
+            const C l2 = sqrt(etoc(lsq2));
+            const Rest<C> rl = rest[L];
+            const C c2 = -ks * etoc(esub(lsq2, rl.lsq)) / ((l2 + rl.l0) * l2);
+            Fx += c2 * etoc(gx);
+            Fy += c2 * etoc(gy);
         }
         // Eq. bendFor gathered: own term plus the neighbours' shares
         Fx += -s_mnx[sj] + s_mnx[sj + 1] * s_sL[sj + 1] + s_mnx[sj - 1] * s_sR[sj - 1];
         Fy += -s_mny[sj] + s_mny[sj + 1] * s_sL[sj + 1] + s_mny[sj - 1] * s_sR[sj - 1];
         // Eq. areaFor, half of each adjacent element
-        Fx += C(0.5) * ca * C(-(yR - yl));
-        Fy += C(0.5) * ca * C(xR - xl);
+        Fx += C(0.5) * ca * (-etoc(esub(yR, yl)));
+        Fy += C(0.5) * ca * etoc(esub(xR, xl));
         F[2 * (size_t)v] = Fx;
         F[2 * (size_t)v + 1] = Fy;
 
         // ---- IB shape functions at X^n: nine nearest nodes, Roma weights,
-        // MLS (basis 1, dx, dy) re-solved where wall rows drop out
-        // clamped so that a runaway (or NaN) position still yields in-range integers;
-        // the advance kernel flags non-finite positions
-        const double fi0 = fmin(fmax(floor(xv + 0.5), -1.0e9), 1.0e9);
-        const double fj0 = fmin(fmax(floor(yv + 0.5), -1.0e6), 1.0e6);
-        const long long i0 = (long long)fi0;
+        // MLS (basis 1, dx, dy) re-solved where wall rows drop out.  Node
+        // indices are clamped so that a runaway position still stays in range;
+        // the advance kernel flags non-finite positions.
+        const C fi0 = fmin(fmax(C(efloor(eaddc(xv, C(0.5)))), C(-1.0e7)), C(1.0e7));
+        const C fj0 = fmin(fmax(C(efloor(eaddc(yv, C(0.5)))), C(-1.0e6)), C(1.0e6));
+        const int i0 = (int)fi0;
         const int j0 = (int)fj0;
         C rx[3], ry[3], wx[3], wy[3];
         bool rowok[3];
         bool all = true;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            rx[q] = C((fi0 + (q - 1)) - xv);
-            ry[q] = C((fj0 + (q - 1)) - yv);
+            // node minus marker, (i0 + q - 1) - x
+            rx[q] = -etoc(eaddc(xv, -(fi0 + C(q - 1))));
+            ry[q] = -etoc(eaddc(yv, -(fj0 + C(q - 1))));
             wx[q] = roma<C>(rx[q]);
             wy[q] = roma<C>(ry[q]);
-            const int j = j0 + q - 1;
-            rowok[q] = a.walls ? (j >= 0 && j < a.ny) : true;
+            const int jj = j0 + q - 1;
+            rowok[q] = a.walls ? (jj >= 0 && jj < a.ny) : true;
             all = all && rowok[q];
         }
         C w[9];
@@ -409,7 +420,7 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < 9; ++q) W[9 * (size_t)v + q] = w[q];
-        const int i0w = (int)(((i0 % a.nx) + a.nx) % a.nx);
+        const int i0w = ((i0 % a.nx) + a.nx) % a.nx;
         const int j0s = a.walls ? j0 : (((j0 % a.ny) + a.ny) % a.ny);
         a.stencil[2 * (size_t)v] = i0w;
         a.stencil[2 * (size_t)v + 1] = j0s;
@@ -419,22 +430,22 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
         int last_t = -1;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
-            int j = j0 + b - 1;
+            int jj = j0 + b - 1;
             if (a.walls) {
-                if (j < 0 || j >= a.ny) continue;
+                if (jj < 0 || jj >= a.ny) continue;
             } else {
-                j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
+                jj = jj < 0 ? jj + a.ny : (jj >= a.ny ? jj - a.ny : jj);
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                int i = i0w + q - 1;
-                i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
-                const size_t node = (size_t)j * a.nx + i;
+                int ii = i0w + q - 1;
+                ii = ii < 0 ? ii + a.nx : (ii >= a.nx ? ii - a.nx : ii);
+                const size_t node = (size_t)jj * a.nx + ii;
                 const C wq = w[b * 3 + q];
                 unsigned long long* gp = reinterpret_cast<unsigned long long*>(a.gsum + node);
                 atomicAdd(gp, (unsigned long long)to_fix<C>(wq * Fx));
                 atomicAdd(gp + 1, (unsigned long long)to_fix<C>(wq * Fy));
-                const int t = (j / a.tile_h) * a.tiles_x + i / a.tile_w;
+                const int t = (jj / a.tile_h) * a.tiles_x + ii / a.tile_w;
                 if (t != last_t) {
                     a.flags[t] = 1;
                     last_t = t;
@@ -444,14 +455,14 @@ __global__ void __launch_bounds__(kChunkV) k_forces(const MarkerArgs a) {
     }
 }
 
-// ---------------------------------------------------------------- advance
-// one warp: bounding box of a 32-vertex segment, stored as FP32 with the
-// centre's x wrapped into [0, nx)
-// One group of kSegV lanes per segment: FP32 offsets of the vertices from the
-// segment's first vertex (the anchor), their bounding box reduced within the
-// group, stored with the centre's x wrapped into [0, nx).  All 32 lanes of the
-// warp call this; `sg` is this lane group's segment or -1.
+// ---------------------------------------------------------------- segments
+// One group of kSegV lanes per segment: bounding box of its vertices, in FP32
+// offsets from the segment's first vertex, stored with the centre's x wrapped
+// into [0, nx).  All 32 lanes of the warp call this; `sg` is this lane group's
+// segment or -1.
+template <typename C>
 __device__ void seg_box_group(const MarkerArgs& a, int sg, int lane) {
+    using E = typename Ext<C>::E;
     const int g = lane & (kSegV - 1);
     int v0 = 0, nb = 0;
     if (sg >= 0) {
@@ -459,14 +470,13 @@ __device__ void seg_box_group(const MarkerArgs& a, int sg, int lane) {
         nb = a.seg_n[sg];
     }
     float ox = 0.f, oy = 0.f;
-    double ax = 0.0, ay = 0.0;
+    E ax = ezero<E>(), ay = ezero<E>();
     if (nb > 0) {
-        ax = a.X[2 * v0];
-        ay = a.X[2 * v0 + 1];
-        const int v = v0 + (g < nb ? g : 0);
-        ox = float(a.X[2 * v] - ax);
-        oy = float(a.X[2 * v + 1] - ay);
-        if (g < nb) a.xoff[v] = make_float2(ox, oy);
+        load_pos<C>(a, v0, ax, ay);
+        E px, py;
+        load_pos<C>(a, v0 + (g < nb ? g : 0), px, py);
+        ox = float(etoc(esub(px, ax)));
+        oy = float(etoc(esub(py, ay)));
     }
     float lo_x = ox, hi_x = ox, lo_y = oy, hi_y = oy;
     for (int o = kSegV / 2; o > 0; o >>= 1) {
@@ -476,21 +486,21 @@ __device__ void seg_box_group(const MarkerArgs& a, int sg, int lane) {
         hi_y = fmaxf(hi_y, __shfl_xor_sync(FULL, hi_y, o));
     }
     if (nb > 0 && g == 0) {
-        const double cxd = ax + 0.5 * (double)(lo_x + hi_x);
-        const double cxw = cxd - (double)a.nx * floor(cxd * a.inv_nx);
-        a.seg_box[sg] = make_float4(float(cxw), float(ay + 0.5 * (double)(lo_y + hi_y)),
+        const float Lx = float(a.nx);
+        const float cx = float(ehi(ax)) + 0.5f * (lo_x + hi_x);
+        a.seg_box[sg] = make_float4(cx - Lx * floorf(cx / Lx), float(ehi(ay)) + 0.5f * (lo_y + hi_y),
                                     0.5f * (hi_x - lo_x), 0.5f * (hi_y - lo_y));
-        a.seg_anchor[sg] = make_double2(ax, ay);
     }
 }
 
 // boxes of segments [s0, s1) by the warps of a block, kSegV lanes per segment
+template <typename C>
 __device__ void seg_boxes_block(const MarkerArgs& a, int s0, int s1) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int per_warp = 32 / kSegV;
     for (int base = s0 + wid * per_warp; base < s1; base += nw * per_warp) {
         const int sg = base + lane / kSegV;
-        seg_box_group(a, sg < s1 ? sg : -1, lane);
+        seg_box_group<C>(a, sg < s1 ? sg : -1, lane);
     }
 }
 
@@ -509,6 +519,7 @@ __device__ bool arrive_last(unsigned int* counter) {
     return last;
 }
 
+// ---------------------------------------------------------------- advance
 // interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
 template <typename C>
 __device__ __forceinline__ void interp_vertex(const MarkerArgs& a, int v) {
@@ -540,33 +551,34 @@ __device__ __forceinline__ void interp_vertex(const MarkerArgs& a, int v) {
     U[2 * v + 1] = sy;
 }
 
-// Eq. kinematicPos (BDF2); forward Euler on the very first step
+// Eq. kinematicPos (BDF2): x^{n+1} = 2/3 (2 x^n - 1/2 x^{n-1} + U dt);
+// forward Euler on the very first step
 template <typename C>
 __device__ __forceinline__ void advance_vertex(const MarkerArgs& a, int v, long long step) {
+    using E = typename Ext<C>::E;
     const C* U = static_cast<const C*>(a.U);
-    double* X = a.X;
-    double* Xp = a.Xp;
-    const double Ux = (double)U[2 * v], Uy = (double)U[2 * v + 1];
-    const double x = X[2 * v], y = X[2 * v + 1];
-    double xn, yn;
+    E x, y, xp, yp;
+    load_pos<C>(a, v, x, y);
+    PosIO<C>::load(a.Xp, v, xp, yp);
+    E xn, yn;
     if (step == 0) {
-        xn = x + Ux;
-        yn = y + Uy;
+        xn = eaddc(x, U[2 * v]);
+        yn = eaddc(y, U[2 * v + 1]);
     } else {
-        xn = (2.0 / 3.0) * (2.0 * x - 0.5 * Xp[2 * v] + Ux);
-        yn = (2.0 / 3.0) * (2.0 * y - 0.5 * Xp[2 * v + 1] + Uy);
+        const E tt = two_thirds_e<E>();
+        xn = emul(eaddc(esub(emulc(x, C(2)), emulc(xp, C(0.5))), U[2 * v]), tt);
+        yn = emul(eaddc(esub(emulc(y, C(2)), emulc(yp, C(0.5))), U[2 * v + 1]), tt);
     }
-    if (!isfinite(xn) || !isfinite(yn)) atomicOr(a.status, ST_NONFINITE);
-    Xp[2 * v] = x;
-    Xp[2 * v + 1] = y;
-    X[2 * v] = xn;
-    X[2 * v + 1] = yn;
+    if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
+    PosIO<C>::store(a.Xp, v, x, y);
+    PosIO<C>::store(a.X, v, xn, yn);
 }
 
 // One block per unit: a chunk of a kinematic membrane (independent vertices)
 // or a whole rigid-projected membrane (needs its centroid and mean rotation).
 template <typename C>
 __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
+    using E = typename Ext<C>::E;
     const int m = a.au[3 * blockIdx.x], k0 = a.au[3 * blockIdx.x + 1], kn = a.au[3 * blockIdx.x + 2];
     const int off = a.mem_off[m], n = a.mem_n[m];
     __shared__ C cred[33];
@@ -578,20 +590,22 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         }
         __syncthreads();
         // boxes of the segments this chunk covers (chunks are segment-aligned)
-        seg_boxes_block(a, a.mem_seg_off[m] + k0 / kSegV, a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV);
+        seg_boxes_block<C>(a, a.mem_seg_off[m] + k0 / kSegV, a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV);
     } else {
         C* U = static_cast<C*>(a.U);
-        double* X = a.X;
         for (int k = threadIdx.x; k < n; k += blockDim.x) interp_vertex<C>(a, off + k);
         __syncthreads();
         // least-squares rigid motion U_c + omega x (x - x_c) of the ring; the
         // sums run in the compute precision on positions taken about vertex 0
-        const double xr = X[2 * off], yr = X[2 * off + 1];
+        E xr, yr;
+        load_pos<C>(a, off, xr, yr);
         C sx = 0, sy = 0, su = 0, sv = 0;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int v = off + k;
-            sx += C(X[2 * v] - xr);
-            sy += C(X[2 * v + 1] - yr);
+            E x, y;
+            load_pos<C>(a, v, x, y);
+            sx += etoc(esub(x, xr));
+            sy += etoc(esub(y, yr));
             su += U[2 * v];
             sv += U[2 * v + 1];
         }
@@ -601,21 +615,25 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         C num = 0, den = 0;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int v = off + k;
-            const C rx = C(X[2 * v] - xr) - mx, ry = C(X[2 * v + 1] - yr) - my;
+            E x, y;
+            load_pos<C>(a, v, x, y);
+            const C rx = etoc(esub(x, xr)) - mx, ry = etoc(esub(y, yr)) - my;
             num += rx * (U[2 * v + 1] - mv) - ry * (U[2 * v] - mu);
             den += rx * rx + ry * ry;
         }
         const C om = block_sum_c<C>(num, cred) / block_sum_c<C>(den, cred);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             const int v = off + k;
-            const C rx = C(X[2 * v] - xr) - mx, ry = C(X[2 * v + 1] - yr) - my;
+            E x, y;
+            load_pos<C>(a, v, x, y);
+            const C rx = etoc(esub(x, xr)) - mx, ry = etoc(esub(y, yr)) - my;
             U[2 * v] = mu - om * ry;
             U[2 * v + 1] = mv + om * rx;
         }
         __syncthreads();
         for (int k = threadIdx.x; k < n; k += blockDim.x) advance_vertex<C>(a, off + k, step);
         __syncthreads();
-        seg_boxes_block(a, a.mem_seg_off[m], a.mem_seg_off[m + 1]);
+        seg_boxes_block<C>(a, a.mem_seg_off[m], a.mem_seg_off[m + 1]);
     }
     // without bond kinetics nothing later in the step reads the step counter
     if (a.bump_in_advance && arrive_last(&a.tickets[0])) {
@@ -627,32 +645,43 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
 }
 
 // segment boxes alone (before the first step and after user-written markers)
+template <typename C>
 __global__ void k_seg_boxes(const MarkerArgs a) {
     constexpr int per_block = (256 / 32) * (32 / kSegV);
     const int s0 = blockIdx.x * per_block;
-    seg_boxes_block(a, s0, min(a.nseg, s0 + per_block));
+    seg_boxes_block<C>(a, s0, min(a.nseg, s0 + per_block));
 }
 
+template <typename C>
 __global__ void k_areas(const MarkerArgs a, double* areas) {
-    const int m = blockIdx.x;
-    const int off = a.mem_off[m], n = a.mem_n[m];
-    __shared__ double red[33];
-    const double* X = a.X;
-    const double xr = X[2 * off], yr = X[2 * off + 1];
-    double ap = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int v = off + k, R = off + (k == n - 1 ? 0 : k + 1);
-        ap += (X[2 * v] - xr) * (X[2 * R + 1] - yr) - (X[2 * R] - xr) * (X[2 * v + 1] - yr);
-    }
-    const double s = block_sum(ap, red);
-    if (threadIdx.x == 0) areas[m] = 0.5 * s;
+    __shared__ typename Ext<C>::E red[33];
+    ring_area<C>(a, blockIdx.x, red);
+    if (threadIdx.x == 0) areas[blockIdx.x] = etod(red[32]);
+}
+
+// marker positions between doubles (x0, y0, x1, ...) and the device layout
+template <typename C>
+__global__ void k_pos_in(const double* xy, void* X, int nv) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    PosIO<C>::store(X, v, from_double_e<C>(xy[2 * v]), from_double_e<C>(xy[2 * v + 1]));
+}
+template <typename C>
+__global__ void k_pos_out(const void* X, double* xy, int nv) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    typename Ext<C>::E x, y;
+    PosIO<C>::load(X, v, x, y);
+    xy[2 * v] = etod(x);
+    xy[2 * v + 1] = etod(y);
 }
 
 // ---------------------------------------------------------------- launchers
 static bool is_f64(lbib_precision p) { return p == LBIB_F64; }
 
-cudaError_t launch_rest(lbib_precision, const MarkerArgs& a, double* rest, double* A0, cudaStream_t s) {
-    k_rest<<<a.nmem, 256, 0, s>>>(a, rest, A0);
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0, cudaStream_t s) {
+    if (is_f64(prec)) k_rest<double><<<a.nmem, 256, 0, s>>>(a, rest, A0);
+    else k_rest<float><<<a.nmem, 256, 0, s>>>(a, rest, A0);
     return cudaGetLastError();
 }
 
@@ -668,15 +697,32 @@ cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s) {
+cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
     if (a.nseg == 0) return cudaSuccess;
     constexpr int per_block = (256 / 32) * (32 / kSegV);
-    k_seg_boxes<<<(a.nseg + per_block - 1) / per_block, 256, 0, s>>>(a);
+    const int g = (a.nseg + per_block - 1) / per_block;
+    if (is_f64(prec)) k_seg_boxes<double><<<g, 256, 0, s>>>(a);
+    else k_seg_boxes<float><<<g, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_areas(const MarkerArgs& a, double* areas, cudaStream_t s) {
-    k_areas<<<a.nmem, 256, 0, s>>>(a, areas);
+cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s) {
+    if (is_f64(prec)) k_areas<double><<<a.nmem, 32, 0, s>>>(a, areas);
+    else k_areas<float><<<a.nmem, 32, 0, s>>>(a, areas);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s) {
+    if (nv == 0) return cudaSuccess;
+    if (is_f64(prec)) k_pos_in<double><<<(nv + 255) / 256, 256, 0, s>>>(xy, X, nv);
+    else k_pos_in<float><<<(nv + 255) / 256, 256, 0, s>>>(xy, X, nv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pos_out(lbib_precision prec, const void* X, double* xy, int nv, cudaStream_t s) {
+    if (nv == 0) return cudaSuccess;
+    if (is_f64(prec)) k_pos_out<double><<<(nv + 255) / 256, 256, 0, s>>>(X, xy, nv);
+    else k_pos_out<float><<<(nv + 255) / 256, 256, 0, s>>>(X, xy, nv);
     return cudaGetLastError();
 }
 

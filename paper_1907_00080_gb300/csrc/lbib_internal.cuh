@@ -111,14 +111,15 @@ struct MarkerArgs {
     const double* mem_ka;
     const double* mem_A0;
     const int* mem_lig_off;   // ligands of membrane m: [lig_off[m], lig_off[m+1])
-    double* X;                // [nv][2] current positions (unwrapped)
-    double* Xp;               // [nv][2] previous positions
+    void* X;                  // [nv] current positions (unwrapped): double (x, y) in
+                              // FP64 mode, float-float {x.hi, y.hi, x.lo, y.lo} otherwise
+    void* Xp;                 // [nv] previous positions, same layout
     void* F;                  // [nv][2] compute type
     void* U;                  // [nv][2] compute type
     void* W;                  // [nv][9] compute type
     int* stencil;             // [nv][2]
-    const double* rest;       // [nv][4] rest state: |x_{v+1}-x_v|^2, |x_{v+1}-x_v|, and the
-                              // cross and dot products of the two edges at v
+    const void* rest;         // [nv] rest records (32 bytes): |x_{v+1}-x_v|^2, the cross and
+                              // dot products of the two edges at v, |x_{v+1}-x_v|
     const int* elem_lig;      // [nv] ligand on element (v, v+1) or -1
     // repulsion
     double d_rep;
@@ -127,8 +128,6 @@ struct MarkerArgs {
     const int* seg_v0;        // [nseg] first global vertex
     const int* seg_n;         // [nseg]
     float4* seg_box;          // [nseg] centre x wrapped to [0,nx), centre y, half extents
-    double2* seg_anchor;      // [nseg] position of the segment's first vertex
-    float2* xoff;             // [nv] vertex position relative to its segment's anchor
     const int* mem_seg_off;   // segments of membrane m: [mem_seg_off[m], mem_seg_off[m+1])
     // work units: (membrane, first local vertex, vertex count); the force kernel
     // cuts every membrane into chunks of kChunkV vertices, the advance kernel
@@ -143,7 +142,8 @@ struct MarkerArgs {
     int* bond_of_lig;         // [nlig]
     int* cand;                // [nlig]
     int* rupt;                // [nlig]
-    const double* rec_xy;     // [nrec][2]
+    const double* rec_xy;     // [nrec][2] receptor positions (FP64 decisions)
+    const void* rec_e;        // [nrec] the same in the marker position layout
     int* owner;               // [nrec]
     int* claim;               // [nrec]
     const int* rcell_start;   // [ncell + 1]
@@ -186,14 +186,16 @@ cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int n
 cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
                         int n_partials, double* out, float inv_scale, cudaStream_t s);
 // ib_kernels.cu
-cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, double* rest, double* A0,
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0,
                         cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
-cudaError_t launch_seg_boxes(const MarkerArgs& a, cudaStream_t s);
-cudaError_t launch_areas(const MarkerArgs& a, double* areas, cudaStream_t s);
+cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
+cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s);
+cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);
+cudaError_t launch_pos_out(lbib_precision prec, const void* X, double* xy, int nv, cudaStream_t s);
 // bond_kernels.cu
-cudaError_t launch_bonds(const MarkerArgs& a, cudaStream_t s);
+cudaError_t launch_bonds(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 int bond_kernel_count(const MarkerArgs& a);
 
 }  // namespace lbib
@@ -246,6 +248,7 @@ struct lbib_ctx {
     longlong2* G[2] = {nullptr, nullptr};   // fixed-point IB force fields (by parity)
     int* flags[2] = {nullptr, nullptr};      // spread-touched tiles (by parity)
     double* d_areas = nullptr;
+    double* xy_stage = nullptr;             // 2*nv doubles for marker read/write
     unsigned int* tickets = nullptr;
 
     long long* d_step = nullptr;
