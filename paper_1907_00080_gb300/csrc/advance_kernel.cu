@@ -1,0 +1,181 @@
+// Interpolation, kinematic advance and bond kinetics in one kernel.
+//
+// One block per unit: a chunk of up to kChunkV vertices of a kinematic
+// membrane, or a whole rigid-projected membrane (its velocities are first
+// projected on their least-squares rigid motion).  Per vertex: interpolate
+// u^n (Sec. 2.3), advance with Eq. kinematicPos (BDF2; forward Euler on the
+// first step), refresh the repulsion boxes.  Then the ligands whose element
+// lies inside the unit are decided at X^{n+1} (bond_logic.cuh); the last
+// block to finish decides the few ligands whose element straddles two units,
+// applies ruptures and formations for all ligands and advances the step
+// counter.
+#include "marker_common.cuh"
+
+namespace lbib {
+
+constexpr int kRigidPer = 4;  // vertices per thread of a rigid unit (<= 4 * kChunkV vertices)
+
+template <typename C>
+__device__ __forceinline__ void load_pos_cg(const void* X, int v, typename Ext<C>::E& x,
+                                            typename Ext<C>::E& y);
+template <>
+__device__ __forceinline__ void load_pos_cg<double>(const void* X, int v, double& x, double& y) {
+    const double* p = static_cast<const double*>(X);
+    x = __ldcg(p + 2 * v);
+    y = __ldcg(p + 2 * v + 1);
+}
+template <>
+__device__ __forceinline__ void load_pos_cg<float>(const void* X, int v, ff& x, ff& y) {
+    const float4 q = __ldcg(static_cast<const float4*>(X) + v);
+    x = ff{q.x, q.z};
+    y = ff{q.y, q.w};
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
+    using E = typename Ext<C>::E;
+    const int u = blockIdx.x;
+    const int m = a.au[3 * u], k0 = a.au[3 * u + 1], kn = a.au[3 * u + 2];
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ E s_x[kRigidPer * kChunkV], s_y[kRigidPer * kChunkV];
+    __shared__ C cred[33];
+    __shared__ bool s_last;
+    const long long step = *a.d_step;
+    C* U = static_cast<C*>(a.U);
+
+    if (a.mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED) {
+        // ---- kinematic chunk: one vertex per thread
+        const bool valid = tid < kn;
+        const int v = off + k0 + (valid ? tid : 0);
+        E x, y, xp, yp, xn, yn;
+        load_pos<C>(a, v, x, y);
+        PosIO<C>::load(a.Xp, v, xp, yp);
+        if (valid) {
+            C Ux, Uy;
+            interp_vertex<C>(a, v, Ux, Uy);
+            U[2 * v] = Ux;
+            U[2 * v + 1] = Uy;
+            bdf2<C>(x, xp, Ux, step, xn);
+            bdf2<C>(y, yp, Uy, step, yn);
+            if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
+            PosIO<C>::store(a.Xp, v, x, y);
+            PosIO<C>::store(a.X, v, xn, yn);
+            s_x[tid] = xn;
+            s_y[tid] = yn;
+        } else {
+            xn = x;
+            yn = y;
+        }
+        // boxes of the repulsion segments of this chunk (chunks are segment-aligned)
+        const int gfirst = tid & ~(kSegV - 1);
+        const int sg = gfirst < kn ? a.mem_seg_off[m] + (k0 + gfirst) / kSegV : -1;
+        E gx, gy;
+        shfl_e(gx, xn, lane & ~(kSegV - 1));
+        shfl_e(gy, yn, lane & ~(kSegV - 1));
+        seg_box_regs<C>(a, sg, lane, valid ? xn : gx, valid ? yn : gy);
+    } else {
+        // ---- rigid-projected membrane: the whole ring in this block
+        E xr, yr;
+        load_pos<C>(a, off, xr, yr);
+        E x[kRigidPer], y[kRigidPer];
+        C Ux[kRigidPer], Uy[kRigidPer];
+        C sx = 0, sy = 0, su = 0, sv = 0;
+#pragma unroll
+        for (int i = 0; i < kRigidPer; ++i) {
+            const int k = tid + i * kChunkV;
+            if (k < n) {
+                load_pos<C>(a, off + k, x[i], y[i]);
+                interp_vertex<C>(a, off + k, Ux[i], Uy[i]);
+                sx += etoc(esub(x[i], xr));
+                sy += etoc(esub(y[i], yr));
+                su += Ux[i];
+                sv += Uy[i];
+            }
+        }
+        // least-squares rigid motion U_c + omega x (x - x_c), positions about vertex 0
+        const C inv_n = C(1) / C(n);
+        const C mx = block_sum_c<C>(sx, cred) * inv_n, my = block_sum_c<C>(sy, cred) * inv_n;
+        const C mu = block_sum_c<C>(su, cred) * inv_n, mv = block_sum_c<C>(sv, cred) * inv_n;
+        C num = 0, den = 0;
+#pragma unroll
+        for (int i = 0; i < kRigidPer; ++i) {
+            const int k = tid + i * kChunkV;
+            if (k < n) {
+                const C rx = etoc(esub(x[i], xr)) - mx, ry = etoc(esub(y[i], yr)) - my;
+                num += rx * (Uy[i] - mv) - ry * (Ux[i] - mu);
+                den += rx * rx + ry * ry;
+            }
+        }
+        const C om = block_sum_c<C>(num, cred) / block_sum_c<C>(den, cred);
+#pragma unroll
+        for (int i = 0; i < kRigidPer; ++i) {
+            const int k = tid + i * kChunkV;
+            if (k >= n) continue;
+            const int v = off + k;
+            const C rx = etoc(esub(x[i], xr)) - mx, ry = etoc(esub(y[i], yr)) - my;
+            const C px = mu - om * ry, py = mv + om * rx;
+            U[2 * v] = px;
+            U[2 * v + 1] = py;
+            E xp, yp, xn, yn;
+            PosIO<C>::load(a.Xp, v, xp, yp);
+            bdf2<C>(x[i], xp, px, step, xn);
+            bdf2<C>(y[i], yp, py, step, yn);
+            if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
+            PosIO<C>::store(a.Xp, v, x[i], y[i]);
+            PosIO<C>::store(a.X, v, xn, yn);
+            s_x[k] = xn;
+            s_y[k] = yn;
+        }
+        __syncthreads();
+        // repulsion boxes: kSegV lanes per segment
+        constexpr int per_pass = kChunkV / kSegV;
+        const int s0 = a.mem_seg_off[m], s1 = a.mem_seg_off[m + 1];
+        for (int base = 0; base < s1 - s0; base += per_pass) {
+            const int si = base + tid / kSegV;
+            const int kfirst = si * kSegV;
+            const int g = tid & (kSegV - 1);
+            const bool ok = si < s1 - s0;
+            const int kk = ok ? (kfirst + g < n ? kfirst + g : kfirst) : 0;
+            seg_box_regs<C>(a, ok ? s0 + si : -1, lane, s_x[kk], s_y[kk]);
+        }
+    }
+    __syncthreads();
+
+    // ---- bond decisions for the ligands whose element lies inside this unit
+    const int q1 = a.nrec > 0 ? a.au_lig_off[u + 1] : a.au_lig_off[u];
+    for (int q = a.au_lig_off[u] + tid; q < q1; q += blockDim.x) {
+        const int l = a.au_ligs[q];
+        const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
+        LigandPoint<C> lp;
+        lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
+        bond_decide<C>(a, l, lp, step);
+    }
+
+    // ---- epilogue of the last block: straddling ligands, apply, next step
+    if (!arrive_last(&a.tickets[0], &s_last)) return;
+    for (int q = tid; q < (a.nrec > 0 ? a.nstrad : 0); q += blockDim.x) {
+        const int l = a.strad_ligs[q];
+        E xa, ya, xb, yb;
+        load_pos_cg<C>(a.X, a.lig_a[l], xa, ya);
+        load_pos_cg<C>(a.X, a.lig_b[l], xb, yb);
+        LigandPoint<C> lp;
+        lp.init(xa, ya, xb, yb);
+        bond_decide<C>(a, l, lp, step);
+    }
+    __syncthreads();
+    if (a.nlig > 0 && a.nrec > 0) bond_apply_all(a);
+    __syncthreads();
+    if (tid == 0) {
+        *a.d_step += 1;
+        a.tickets[0] = 0;
+    }
+}
+
+cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
+    if (prec == LBIB_F64) k_advance<double><<<a.nau, kChunkV, 0, s>>>(a);
+    else k_advance<float><<<a.nau, kChunkV, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

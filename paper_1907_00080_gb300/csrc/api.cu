@@ -171,6 +171,8 @@ extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t 
     if (!xy || n < 3) return fail(c, LBIB_E_INVALID, "a membrane needs >= 3 vertices");
     if (kind != LBIB_MEMBRANE_KINEMATIC && kind != LBIB_MEMBRANE_RIGID_PROJECTED)
         return fail(c, LBIB_E_INVALID, "unknown membrane kind");
+    if (kind == LBIB_MEMBRANE_RIGID_PROJECTED && n > 4 * kChunkV)
+        return fail(c, LBIB_E_INVALID, "rigid-projected membranes are limited to 256 vertices");
     if (n_ligands < 0 || (n_ligands > 0 && !ligand_elems))
         return fail(c, LBIB_E_INVALID, "ligand list");
     for (int k = 0; k < 2 * n; ++k)
@@ -327,6 +329,25 @@ static lbib_status finalize(lbib_ctx* c) {
         }
         if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) au.insert(au.end(), {m, 0, n});
     }
+    // ligands decided inside each advance unit (both element vertices in it) and
+    // the straddling rest, decided by the kernel's last block
+    const int nau = (int)(au.size() / 3);
+    std::vector<int> au_lig_off(nau + 1, 0), au_ligs, strad;
+    {
+        std::vector<std::vector<int>> per(nau);
+        std::vector<int> unit_of(std::max(nv, 1), -1);
+        for (int q = 0; q < nau; ++q)
+            for (int k = 0; k < au[3 * q + 2]; ++k) unit_of[c->h_mem_off[au[3 * q]] + au[3 * q + 1] + k] = q;
+        for (int l = 0; l < nl; ++l) {
+            const int ua = unit_of[lig_a[l]], ub = unit_of[lig_b[l]];
+            if (ua == ub) per[ua].push_back(l);
+            else strad.push_back(l);
+        }
+        for (int q = 0; q < nau; ++q) {
+            au_lig_off[q + 1] = au_lig_off[q] + (int)per[q].size();
+            au_ligs.insert(au_ligs.end(), per[q].begin(), per[q].end());
+        }
+    }
 
     // ---- one arena for every marker / tile / bond array
     const size_t cs = c->cmp_elem;
@@ -344,6 +365,7 @@ static lbib_status finalize(lbib_ctx* c) {
         add(16 * nr); add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
         add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
+        add(4 * au_lig_off.size()); add(4 * au_ligs.size()); add(4 * strad.size());
         bytes = probe.used + 256;
     }
     lbib_status st = LBIB_OK;
@@ -396,6 +418,9 @@ static lbib_status finalize(lbib_ctx* c) {
     c->tickets = ar.take<unsigned int>(4);
     int* d_fu = ar.take<int>(fu.size());
     int* d_au = ar.take<int>(au.size());
+    int* d_au_lig_off = ar.take<int>(au_lig_off.size());
+    int* d_au_ligs = ar.take<int>(au_ligs.size());
+    int* d_strad = ar.take<int>(strad.size());
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
 
     auto H2D = [&](void* d, const void* h, size_t b) -> cudaError_t {
@@ -423,6 +448,9 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(d_mem_seg_off, mem_seg_off.data(), 4 * (nm + 1)));
         CK(H2D(d_fu, fu.data(), 4 * fu.size()));
         CK(H2D(d_au, au.data(), 4 * au.size()));
+        CK(H2D(d_au_lig_off, au_lig_off.data(), 4 * au_lig_off.size()));
+        if (!au_ligs.empty()) CK(H2D(d_au_ligs, au_ligs.data(), 4 * au_ligs.size()));
+        if (!strad.empty()) CK(H2D(d_strad, strad.data(), 4 * strad.size()));
     }
     if (nl > 0) {
         CK(H2D(d_lig_a, lig_a.data(), 4 * nl));
@@ -455,7 +483,9 @@ static lbib_status finalize(lbib_ctx* c) {
     a.rest = rest; a.elem_lig = elig;
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
-    a.nfu = (int)(fu.size() / 3); a.nau = (int)(au.size() / 3); a.fu = d_fu; a.au = d_au;
+    a.nfu = (int)(fu.size() / 3); a.nau = nau; a.fu = d_fu; a.au = d_au;
+    a.au_lig_off = d_au_lig_off; a.au_ligs = d_au_ligs;
+    a.nstrad = (int)strad.size(); a.strad_ligs = d_strad;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
     a.rec_xy = rec_xy; a.rec_e = rec_e; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
@@ -467,7 +497,12 @@ static lbib_status finalize(lbib_ctx* c) {
     a.seed = c->bp.seed; a.instance = c->bp.instance;
     a.tile_w = c->tile_w; a.tile_h = c->tile_h; a.tiles_x = c->tiles_x; a.tiles_y = c->tiles_y;
     a.d_step = c->d_step; a.status = c->d_status; a.tickets = c->tickets;
-    a.bump_in_advance = (nv > 0 && !(nl > 0 && nr > 0)) ? 1 : 0;
+    a.f.nx = (float)c->nx; a.f.ny = (float)c->ny; a.f.inv_nx = (float)a.inv_nx; a.f.inv_ny = (float)a.inv_ny;
+    a.f.sigma = (float)a.sigma; a.f.y_eq = (float)a.y_eq; a.f.inv_y_eq = (float)a.inv_y_eq;
+    a.f.d_rep = (float)a.d_rep; a.f.d_cut = (float)a.d_cut; a.f.d_break = (float)a.d_break;
+    a.f.kf_dt = (float)a.kf_dt; a.f.kr0_dt = (float)a.kr0_dt; a.f.beta_f = (float)a.beta_f;
+    a.f.beta_r = (float)a.beta_r; a.f.inv_rc_w = (float)a.inv_rc_w; a.f.inv_rc_h = (float)a.inv_rc_h;
+    a.f.rc_y0 = (float)a.rc_y0;
     a.ux = c->ux; a.uy = c->uy;
 
     if (nm > 0) {
@@ -514,7 +549,7 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     if ((e = launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, has_ib, l, s)) != cudaSuccess)
         return e;
     if (has_ib && (e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
-    return launch_bonds(c->prec, a, s);
+    return cudaSuccess;
 }
 
 static lbib_status build_graphs(lbib_ctx* c) {
@@ -592,10 +627,8 @@ extern "C" int64_t lbib_step_count(const lbib_ctx* c) { return c ? c->steps : -1
 
 extern "C" int32_t lbib_kernels_per_step(const lbib_ctx* c) {
     if (!c) return -1;
-    int k = 1;  // fused LB
-    if (c->nv > 0) k += 2;  // forces (with spreading), interpolation + advance
-    if (c->nlig > 0 && c->have_receptors && !c->h_rec.empty()) k += 1;  // bond kinetics
-    return k;
+    // forces with spreading, fused LB, interpolation + advance + bond kinetics
+    return c->nv > 0 ? 3 : 1;
 }
 
 extern "C" int32_t lbib_storage_scale_exponent(const lbib_ctx* c) { return c ? c->scale_exp : 0; }

@@ -111,6 +111,13 @@ __device__ __forceinline__ ff ewrap(ff d, float L, float invL) {
     return k == 0.f ? d : ff_addf(d, -k * L);
 }
 
+// warp shuffle of an extended value from lane l (all lanes participate)
+__device__ __forceinline__ void shfl_e(double& d, double s, int l) { d = __shfl_sync(0xffffffffu, s, l); }
+__device__ __forceinline__ void shfl_e(ff& d, ff s, int l) {
+    d.hi = __shfl_sync(0xffffffffu, s.hi, l);
+    d.lo = __shfl_sync(0xffffffffu, s.lo, l);
+}
+
 // ---- marker positions: doubles (x, y) per vertex, or float-float pairs
 // stored as float4 {x.hi, y.hi, x.lo, y.lo}
 template <typename C> struct PosIO;

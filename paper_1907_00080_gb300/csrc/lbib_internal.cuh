@@ -161,11 +161,21 @@ struct MarkerArgs {
     // step counter, status and the arrival counters of the last-block epilogues
     long long* d_step;
     int* status;
-    unsigned int* tickets;    // [2]: advance, bond decisions
-    int bump_in_advance;
+    unsigned int* tickets;    // arrival counter of the advance kernel's last-block epilogue
     // u field (compute type)
     const void* ux;
     const void* uy;
+    // FP32 copies of the scalar parameters (no double->float conversion in the kernels)
+    struct {
+        float nx, ny, inv_nx, inv_ny, sigma, y_eq, inv_y_eq, d_rep, d_cut, d_break;
+        float kf_dt, kr0_dt, beta_f, beta_r, inv_rc_w, inv_rc_h, rc_y0;
+    } f;
+    // ligands decided by each advance unit (element inside the unit, CSR), and
+    // the ligands whose element straddles two units (decided by the last block)
+    const int* au_lig_off;    // [nau + 1]
+    const int* au_ligs;
+    int nstrad;
+    const int* strad_ligs;
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2 };
@@ -194,9 +204,6 @@ cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStrea
 cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s);
 cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);
 cudaError_t launch_pos_out(lbib_precision prec, const void* X, double* xy, int nv, cudaStream_t s);
-// bond_kernels.cu
-cudaError_t launch_bonds(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
-int bond_kernel_count(const MarkerArgs& a);
 
 }  // namespace lbib
 

@@ -1,0 +1,204 @@
+// Device helpers shared by the Lagrangian kernels (forces / spreading and
+// interpolation / advance / bonds).
+#pragma once
+
+#include <climits>
+
+#include "bond_logic.cuh"
+#include "ext_real.cuh"
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float wrap_half(float d, float L) {
+    return d > 0.5f * L ? d - L : (d < -0.5f * L ? d + L : d);
+}
+
+// force value to the fixed-point grid of the spread field (scaled by 2^52)
+template <typename C> __device__ __forceinline__ long long to_fix(C v);
+template <> __device__ __forceinline__ long long to_fix<float>(float v) {
+    // exact: t = v 2^52 is either below 2^23 in magnitude (round it with a 32-bit
+    // conversion) or an integer whose mantissa is shifted into place
+    const float t = v * 4503599627370496.0f;
+    if (fabsf(t) < 8388608.0f) return (long long)__float2int_rn(t);
+    const int bits = __float_as_int(t);
+    const int e = ((bits >> 23) & 0xff) - 150;  // t = mant 2^e with e >= 0 here
+    const long long mag = (long long)((bits & 0x7fffff) | 0x800000) << (e < 40 ? e : 40);
+    return bits < 0 ? -mag : mag;
+}
+template <> __device__ __forceinline__ long long to_fix<double>(double v) {
+    return __double2ll_rn(v * kFixScale);
+}
+
+// Roma, Peskin & Berger three-point regularised delta
+template <typename C>
+__device__ __forceinline__ C roma(C r) {
+    const C a = fabs(r);
+    if (a <= C(0.5)) return (C(1) + sqrt(C(1) - C(3) * a * a)) / C(3);
+    if (a <= C(1.5)) {
+        const C b = C(1) - a;
+        return (C(5) - C(3) * a - sqrt(C(1) - C(3) * b * b)) / C(6);
+    }
+    return C(0);
+}
+
+template <typename C>
+__device__ __forceinline__ void load_pos(const MarkerArgs& a, int v, typename Ext<C>::E& x,
+                                         typename Ext<C>::E& y) {
+    PosIO<C>::load(a.X, v, x, y);
+}
+
+// Edge products at a vertex in the extended type from the positions of L, v, R:
+// squared length of e_R = x_R - x_v, and the cross and dot products of
+// e_L = x_v - x_L with e_R (their rotation from the rest pair gives theta - theta_0).
+template <typename C>
+struct EdgeProducts {
+    typename Ext<C>::E lsqR, cross, dot;
+};
+template <typename E, typename C>
+__device__ __forceinline__ EdgeProducts<C> edge_products(E xL, E yL, E xv, E yv, E xR, E yR) {
+    const E eLx = esub(xv, xL), eLy = esub(yv, yL), eRx = esub(xR, xv), eRy = esub(yR, yv);
+    EdgeProducts<C> p;
+    p.lsqR = eadd(emul(eRx, eRx), emul(eRy, eRy));
+    p.cross = esub(emul(eLx, eRy), emul(eLy, eRx));
+    p.dot = eadd(emul(eLx, eRx), emul(eLy, eRy));
+    return p;
+}
+
+// Enclosed area of membrane m by the shoelace formula about vertex 0, summed by
+// ONE warp in a fixed order (lane l takes terms l, l+32, ..., then a fixed
+// tree through `red`), so every caller gets the same bits.  Call from all 32
+// lanes of one warp; lane 0 returns the area (other lanes return garbage).
+template <typename C>
+__device__ typename Ext<C>::E ring_area_warp(const MarkerArgs& a, int m, typename Ext<C>::E* red) {
+    using E = typename Ext<C>::E;
+    const int lane = threadIdx.x & 31;
+    const int off = a.mem_off[m], n = a.mem_n[m];
+    E xr, yr;
+    load_pos<C>(a, off, xr, yr);
+    E acc = ezero<E>();
+#pragma unroll 2
+    for (int k = lane; k < n; k += 32) {
+        const int R = k == n - 1 ? 0 : k + 1;
+        E xv, yv, xR, yR;
+        load_pos<C>(a, off + k, xv, yv);
+        load_pos<C>(a, off + R, xR, yR);
+        const E t = esub(emul(esub(xv, xr), esub(yR, yr)), emul(esub(xR, xr), esub(yv, yr)));
+        acc = eadd(acc, t);
+    }
+    red[lane] = acc;
+    __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) {
+        if (lane < o) red[lane] = eadd(red[lane], red[lane + o]);
+        __syncwarp();
+    }
+    return emulc(red[0], C(0.5));
+}
+
+// block-wide sum in the compute type (all threads get it)
+template <typename C>
+__device__ C block_sum_c(C v, C* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        C t = threadIdx.x < nw ? red[threadIdx.x] : C(0);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// Last-block epilogue: every block counts itself in once it is done; the block
+// that arrives last (it sees all other blocks' writes after the fences) runs the
+// epilogue and resets the counter.  No block ever waits for another.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    const bool last = *flag;
+    if (last) __threadfence();
+    return last;
+}
+
+// Box of one segment from positions held by a group of kSegV consecutive lanes
+// (lane g of the group holds vertex v0 + g; lanes past the segment end hold a
+// copy of the first vertex).  FP32 offsets from the first vertex; centre x
+// wrapped into [0, nx).  All 32 lanes call it.
+template <typename C>
+__device__ __forceinline__ void seg_box_regs(const MarkerArgs& a, int sg, int lane, typename Ext<C>::E x,
+                                             typename Ext<C>::E y) {
+    using E = typename Ext<C>::E;
+    const int g0 = lane & ~(kSegV - 1);
+    // first vertex of the group, broadcast in its (hi, lo) parts
+    E ax, ay;
+    shfl_e(ax, x, g0);
+    shfl_e(ay, y, g0);
+    const float ox = float(etoc(esub(x, ax))), oy = float(etoc(esub(y, ay)));
+    float lo_x = ox, hi_x = ox, lo_y = oy, hi_y = oy;
+    for (int o = kSegV / 2; o > 0; o >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(kFull, lo_x, o));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(kFull, hi_x, o));
+        lo_y = fminf(lo_y, __shfl_xor_sync(kFull, lo_y, o));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(kFull, hi_y, o));
+    }
+    if (sg >= 0 && lane == g0) {
+        const float Lx = a.f.nx;
+        const float cx = float(ehi(ax)) + 0.5f * (lo_x + hi_x);
+        a.seg_box[sg] = make_float4(cx - Lx * floorf(cx * a.f.inv_nx), float(ehi(ay)) + 0.5f * (lo_y + hi_y),
+                                    0.5f * (hi_x - lo_x), 0.5f * (hi_y - lo_y));
+    }
+}
+
+// interpolation U_v = sum_j phi_v(x_j) u(x_j) with the weights of this step
+template <typename C>
+__device__ __forceinline__ void interp_vertex(const MarkerArgs& a, int v, C& Ux, C& Uy) {
+    const C* ux = static_cast<const C*>(a.ux);
+    const C* uy = static_cast<const C*>(a.uy);
+    const C* W = static_cast<const C*>(a.W);
+    const int i0 = a.stencil[2 * v], j0 = a.stencil[2 * v + 1];
+    C sx = C(0), sy = C(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        int j = j0 + b - 1;
+        if (a.walls) {
+            if (j < 0 || j >= a.ny) continue;
+        } else {
+            j = j < 0 ? j + a.ny : (j >= a.ny ? j - a.ny : j);
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            int i = i0 + q - 1;
+            i = i < 0 ? i + a.nx : (i >= a.nx ? i - a.nx : i);
+            const C w = W[9 * (size_t)v + b * 3 + q];
+            const size_t node = (size_t)j * a.nx + i;
+            sx += w * ux[node];
+            sy += w * uy[node];
+        }
+    }
+    Ux = sx;
+    Uy = sy;
+}
+
+// Eq. kinematicPos (BDF2): x^{n+1} = 2/3 (2 x^n - 1/2 x^{n-1} + U dt);
+// forward Euler on the very first step
+template <typename C>
+__device__ __forceinline__ void bdf2(typename Ext<C>::E x, typename Ext<C>::E xp, C U, long long step,
+                                     typename Ext<C>::E& xn) {
+    using E = typename Ext<C>::E;
+    if (step == 0) {
+        xn = eaddc(x, U);
+    } else {
+        xn = emul(eaddc(esub(emulc(x, C(2)), emulc(xp, C(0.5))), U), two_thirds_e<E>());
+    }
+}
+
+}  // namespace lbib
