@@ -23,7 +23,7 @@ __global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0) {
     using E = typename Ext<C>::E;
     const int m = blockIdx.x;
     const int off = a.mem_off[m], n = a.mem_n[m];
-    __shared__ E red[32];
+    __shared__ E red[32 * kAreaWarps];
     Rest<C>* rest = static_cast<Rest<C>*>(rest_v);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int v = off + k, L = off + (k == 0 ? n - 1 : k - 1), R = off + (k == n - 1 ? 0 : k + 1);
@@ -39,8 +39,8 @@ __global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0) {
         r.l0 = sqrt(etoc(p.lsqR));
         rest[v] = r;
     }
-    if (threadIdx.x < 32) {
-        const E A = ring_area_warp<C>(a, m, red);
+    if (threadIdx.x < 32 * kAreaWarps) {
+        const E A = ring_area_group<C>(a, m, 0, red, 1);
         if (threadIdx.x == 0) A0[m] = etod(A);
     }
 }
@@ -68,17 +68,19 @@ __device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, E xa
     Fy += C(0.5) * c * dy;
 }
 
-constexpr int kForceThreads = 4 * kChunkV;   // threads per force block
-constexpr int kMaxCand = 256;                 // repulsion candidate segments per block
+constexpr int kForceWarps = 10;
+constexpr int kForceThreads = 32 * kForceWarps;  // threads per force block
+constexpr int kMaxCand = 256;                     // repulsion candidate segments per block
 
 // One block per work unit (a chunk of up to kChunkV consecutive vertices of one
 // membrane).  The warps split the work of a vertex:
-//   phase 1  warps 0-2  bending geometry of the chunk plus one halo vertex each side
-//            warp  3    enclosed area of the whole membrane
-//            warps 4-5  IB shape functions (MLS / Roma) and stencil origins
-//            warp  6    repulsion candidate segments (ascending order)
+//   phase 1  warps 0-1  bending geometry of the chunk plus one halo vertex each side
+//            warps 2-3  IB shape functions (MLS / Roma) and stencil origins
+//            warps 4-7  enclosed area of the whole membrane (fixed-order sum)
+//            warp  8    repulsion candidate segments (ascending order)
 //   phase 2  warps 0-1  stretching, bending, area and bond forces per vertex
-//            warps 2-3  repulsion per vertex
+//            warps 2-9  repulsion over (candidate segment, vertex) pairs,
+//                       accumulated per vertex in fixed point (order-free)
 //   phase 3  all        spreading: (vertex, node) pairs into the fixed-point field
 template <typename C>
 __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
@@ -93,9 +95,9 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     __shared__ C s_nx[kChunkV + 2], s_ny[kChunkV + 2];
     __shared__ C s_w[kChunkV][9];
     __shared__ int s_i0[kChunkV], s_j0[kChunkV];
-    __shared__ C s_rx[kChunkV], s_ry[kChunkV];
+    __shared__ unsigned long long s_rep[kChunkV];
     __shared__ C s_F[kChunkV][2];
-    __shared__ E red[32];
+    __shared__ E red[32 * kAreaWarps];
     __shared__ C s_ca;
     __shared__ int s_cand[kMaxCand];
     __shared__ int s_ncand;
@@ -107,15 +109,16 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         k = k < 0 ? k + n : (k >= n ? k - n : k);
         load_pos<C>(a, off + k, s_x[p], s_y[p]);
     }
+    if (tid < kChunkV) s_rep[tid] = 0ull;
     __syncthreads();
 
     // ---- phase 1
-    if (wid < 3) {
+    if (wid < 2) {
         // theta - theta_0 from the rotation between the rest and the current
         // edge pair, atan2(c d0 - c0 d, d d0 + c c0): no cancellation of two
         // nearly equal angles
         const C kb = par<C>(a.mem_kb[m], float(a.mem_kb[m]));
-        for (int j = tid; j < kn + 2; j += 96) {
+        for (int j = tid; j < kn + 2; j += 64) {
             int k = k0 - 1 + j;
             k = k < 0 ? k + n : (k >= n ? k - n : k);
             const E xL = s_x[j], yL = s_y[j], xv = s_x[j + 1], yv = s_y[j + 1], xR = s_x[j + 2], yR = s_y[j + 2];
@@ -141,16 +144,12 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             s_nx[j] = nx_;
             s_ny[j] = ny_;
         }
-    } else if (wid == 3) {
-        // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
-        const E A = ring_area_warp<C>(a, m, red);
-        if (lane == 0) s_ca = C(-a.mem_ka[m] * (1.0 - etod(A) / a.mem_A0[m]) * (1.0 / 3.0));
-    } else if (wid < 6) {
+    } else if (wid < 4) {
         // IB shape functions at X^n: nine nearest nodes, Roma weights, MLS
         // (basis 1, dx, dy) re-solved where wall rows drop out.  Node indices are
         // clamped so that a runaway position still stays in range; the advance
         // kernel flags non-finite positions.
-        const int j = tid - 128;
+        const int j = tid - 64;
         if (j < kn) {
             const E xv = s_x[j + 2], yv = s_y[j + 2];
             const C fi0 = fmin(fmax(C(efloor(eaddc(xv, C(0.5)))), C(-1.0e7)), C(1.0e7));
@@ -224,27 +223,48 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             s_i0[j] = i0w;
             s_j0[j] = j0;
         }
-    } else if (wid == 6) {
+    } else if (wid < 4 + kAreaWarps) {
+        // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
+        const E A = ring_area_group<C>(a, m, 4, red, 1);
+        if (tid == 32 * 4) s_ca = C(-a.mem_ka[m] * (1.0 - etod(A) / a.mem_A0[m]) * (1.0 / 3.0));
+    } else if (wid == 8) {
         // Eq. repFor screening, once per block: segments of other membranes whose
-        // box comes within d_rep of a box of this chunk's own segments, appended
-        // in ascending segment order so the per-vertex sums are reproducible
+        // box comes within d_rep of this chunk's box (the union of its own
+        // segments' boxes), appended in ascending segment order
         int cnt = 0;
         if (a.nmem > 1) {
-            const float reach = a.f.d_rep + 2e-3f;
             const int sown0 = a.mem_seg_off[m] + k0 / kSegV;
-            const int sown1 = a.mem_seg_off[m] + (k0 + kn + kSegV - 1) / kSegV;
+            const int nown = (kn + kSegV - 1) / kSegV;  // <= kChunkV / kSegV <= 32
+            float4 o0 = a.seg_box[sown0];
+            float lo_x = 1e30f, hi_x = -1e30f, lo_y = 1e30f, hi_y = -1e30f;
+            if (lane < nown) {
+                const float4 o = a.seg_box[sown0 + lane];
+                const float dx = wrap_half(o.x - o0.x, a.f.nx);
+                float dy = o.y - o0.y;
+                if (!a.walls) dy = wrap_half(dy, a.f.ny);
+                lo_x = dx - o.z;
+                hi_x = dx + o.z;
+                lo_y = dy - o.w;
+                hi_y = dy + o.w;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                lo_x = fminf(lo_x, __shfl_xor_sync(kFull, lo_x, o));
+                hi_x = fmaxf(hi_x, __shfl_xor_sync(kFull, hi_x, o));
+                lo_y = fminf(lo_y, __shfl_xor_sync(kFull, lo_y, o));
+                hi_y = fmaxf(hi_y, __shfl_xor_sync(kFull, hi_y, o));
+            }
+            const float cbx = o0.x + 0.5f * (lo_x + hi_x), cby = o0.y + 0.5f * (lo_y + hi_y);
+            const float chx = 0.5f * (hi_x - lo_x), chy = 0.5f * (hi_y - lo_y);
+            const float reach = a.f.d_rep + 2e-3f;
             for (int base = 0; base < a.nseg; base += 32) {
                 const int sg = base + lane;
                 bool hit = false;
                 if (sg < a.nseg && a.seg_mem[sg] != m) {
                     const float4 b = a.seg_box[sg];
-                    for (int so = sown0; so < sown1 && !hit; ++so) {
-                        const float4 o = a.seg_box[so];
-                        const float dx = wrap_half(b.x - o.x, a.f.nx);
-                        float dy = b.y - o.y;
-                        if (!a.walls) dy = wrap_half(dy, a.f.ny);
-                        hit = fabsf(dx) <= b.z + o.z + reach && fabsf(dy) <= b.w + o.w + reach;
-                    }
+                    const float dx = wrap_half(b.x - cbx, a.f.nx);
+                    float dy = b.y - cby;
+                    if (!a.walls) dy = wrap_half(dy, a.f.ny);
+                    hit = fabsf(dx) <= b.z + chx + reach && fabsf(dy) <= b.w + chy + reach;
                 }
                 const unsigned bal = __ballot_sync(kFull, hit);
                 const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
@@ -300,53 +320,45 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             Fx += C(0.5) * ca * (-etoc(esub(yR, yl)));
             Fy += C(0.5) * ca * etoc(esub(xR, xl));
         }
-    } else if (wid < 4) {
-        // Eq. repFor against vertices of other membranes closer than d_rep
-        const int j = tid - 64;
-        C rx = C(0), ry = C(0);
-        if (j < kn && a.nmem > 1 && ncand > 0) {
+    } else if (a.nmem > 1 && ncand > 0) {
+        // Eq. repFor against vertices of other membranes closer than d_rep, over
+        // (candidate segment, vertex) pairs; the magnitudes of each vertex are
+        // summed in fixed point (the direction is its own inward normal)
+        const int nscan = all_segs ? a.nseg : ncand;
+        const float reach = a.f.d_rep + 2e-3f;
+        const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));
+        const C drep = par<C>(a.d_rep, a.f.d_rep);
+        for (int p = tid - 64; p < nscan * kn; p += blockDim.x - 64) {
+            const int ci = p / kn, j = p - ci * kn;
+            const int sg = all_segs ? ci : s_cand[ci];
+            if (a.seg_mem[sg] == m) continue;
             const E xv = s_x[j + 2], yv = s_y[j + 2];
-            const int sj = j + 1;
             const float hx = float(ehi(xv));
             const float xvw = hx - a.f.nx * floorf(hx * a.f.inv_nx);
-            const float yvf = float(ehi(yv));
-            const float reach = a.f.d_rep + 2e-3f;
-            const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));
-            const C drep = par<C>(a.d_rep, a.f.d_rep);
-            const int nscan = all_segs ? a.nseg : ncand;
-            for (int ci = 0; ci < nscan; ++ci) {
-                const int sg = all_segs ? ci : s_cand[ci];
-                if (a.seg_mem[sg] == m) continue;
-                const float4 bx = a.seg_box[sg];
-                const float ddx = wrap_half(xvw - bx.x, a.f.nx);
-                float ddy = yvf - bx.y;
-                if (!a.walls) ddy = wrap_half(ddy, a.f.ny);
-                if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
-                const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
-                for (int b = b0; b < b0 + nb; ++b) {
-                    E xb, yb;
-                    load_pos<C>(a, b, xb, yb);
-                    const C dx = etoc(ewrap(esub(xv, xb), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
-                    C dy = etoc(esub(yv, yb));
-                    if (!a.walls) dy = etoc(ewrap(esub(yv, yb), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
-                    const C d = sqrt(dx * dx + dy * dy);
-                    if (d < drep) {
-                        const C mag = c_rep * sqrt(C(1) / (d * d * d * d * d));
-                        rx -= mag * s_nx[sj];
-                        ry -= mag * s_ny[sj];
-                    }
-                }
+            const float4 bx = a.seg_box[sg];
+            const float ddx = wrap_half(xvw - bx.x, a.f.nx);
+            float ddy = float(ehi(yv)) - bx.y;
+            if (!a.walls) ddy = wrap_half(ddy, a.f.ny);
+            if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
+            const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
+            C mags = C(0);
+            for (int b = b0; b < b0 + nb; ++b) {
+                E xb, yb;
+                load_pos<C>(a, b, xb, yb);
+                const C dx = etoc(ewrap(esub(xv, xb), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
+                C dy = etoc(esub(yv, yb));
+                if (!a.walls) dy = etoc(ewrap(esub(yv, yb), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
+                const C d = sqrt(dx * dx + dy * dy);
+                if (d < drep) mags += c_rep * sqrt(C(1) / (d * d * d * d * d));
             }
-        }
-        if (j < kn) {
-            s_rx[j] = rx;
-            s_ry[j] = ry;
+            if (mags != C(0)) atomicAdd(&s_rep[j], (unsigned long long)to_fix60<C>(mags));
         }
     }
     __syncthreads();
     if (wid < 2 && tid < kn) {
-        Fx += s_rx[tid];
-        Fy += s_ry[tid];
+        const C mag = fix60_to_c<C>((long long)s_rep[tid]);
+        Fx -= mag * s_nx[tid + 1];
+        Fy -= mag * s_ny[tid + 1];
         C* F = static_cast<C*>(a.F);
         const int v = off + k0 + tid;
         F[2 * (size_t)v] = Fx;
@@ -400,8 +412,8 @@ __global__ void k_seg_boxes(const MarkerArgs a) {
 
 template <typename C>
 __global__ void k_areas(const MarkerArgs a, double* areas) {
-    __shared__ typename Ext<C>::E red[32];
-    const typename Ext<C>::E A = ring_area_warp<C>(a, blockIdx.x, red);
+    __shared__ typename Ext<C>::E red[32 * kAreaWarps];
+    const typename Ext<C>::E A = ring_area_group<C>(a, blockIdx.x, 0, red, 1);
     if (threadIdx.x == 0) areas[blockIdx.x] = etod(A);
 }
 
@@ -447,8 +459,8 @@ cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStrea
 }
 
 cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s) {
-    if (is_f64(prec)) k_areas<double><<<a.nmem, 32, 0, s>>>(a, areas);
-    else k_areas<float><<<a.nmem, 32, 0, s>>>(a, areas);
+    if (is_f64(prec)) k_areas<double><<<a.nmem, 32 * kAreaWarps, 0, s>>>(a, areas);
+    else k_areas<float><<<a.nmem, 32 * kAreaWarps, 0, s>>>(a, areas);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,41 @@ template <> __device__ __forceinline__ long long to_fix<double>(double v) {
     return __double2ll_rn(v * kFixScale);
 }
 
+// value scaled by 2^60 to a 64-bit integer (repulsion accumulators: magnitudes
+// stay below 8, resolution 2^-60), exact for the float case
+template <typename C> __device__ __forceinline__ long long to_fix60(C v);
+template <> __device__ __forceinline__ long long to_fix60<float>(float v) {
+    const float t = v * 1.152921504606846976e18f;  // 2^60
+    if (fabsf(t) < 8388608.0f) return (long long)__float2int_rn(t);
+    const int bits = __float_as_int(t);
+    const int e = ((bits >> 23) & 0xff) - 150;
+    const long long mag = (long long)((bits & 0x7fffff) | 0x800000) << (e < 39 ? e : 39);
+    return bits < 0 ? -mag : mag;
+}
+template <> __device__ __forceinline__ long long to_fix60<double>(double v) {
+    return __double2ll_rn(v * 1.152921504606846976e18);
+}
+template <typename C> __device__ __forceinline__ C fix60_to_c(long long v);
+template <> __device__ __forceinline__ float fix60_to_c<float>(long long v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 3.7252902984619141e-09f, (float)lo * 8.6736173798840355e-19f);
+}
+template <> __device__ __forceinline__ double fix60_to_c<double>(long long v) {
+    return __ll2double_rn(v) * 8.6736173798840355e-19;
+}
+
+// fixed-point value (scaled by 2^52) back to the compute type
+template <typename C> __device__ __forceinline__ C fix_to_c(long long v);
+template <> __device__ __forceinline__ float fix_to_c<float>(long long v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 9.5367431640625e-07f, (float)lo * 2.220446049250313e-16f);
+}
+template <> __device__ __forceinline__ double fix_to_c<double>(long long v) {
+    return __ll2double_rn(v) * kFixInv;
+}
+
 // Roma, Peskin & Berger three-point regularised delta
 template <typename C>
 __device__ __forceinline__ C roma(C r) {
@@ -67,34 +102,44 @@ __device__ __forceinline__ EdgeProducts<C> edge_products(E xL, E yL, E xv, E yv,
     return p;
 }
 
-// Enclosed area of membrane m by the shoelace formula about vertex 0, summed by
-// ONE warp in a fixed order (lane l takes terms l, l+32, ..., then a fixed
-// tree through `red`), so every caller gets the same bits.  Call from all 32
-// lanes of one warp; lane 0 returns the area (other lanes return garbage).
+// Enclosed area of membrane m by the shoelace formula about vertex 0, summed
+// by kAreaWarps warps in a fixed order (thread t of the group takes terms t,
+// t + 32 kAreaWarps, ...; each warp reduces its lanes by a fixed tree; the warp
+// partials are added in warp order), so every caller gets the same bits.  Call
+// from the kAreaWarps consecutive warps starting at `w0` (all their lanes);
+// `red` holds 32 kAreaWarps values; returns the area in every caller after the
+// named barrier `bar` (kAreaWarps * 32 threads).
+constexpr int kAreaWarps = 4;
 template <typename C>
-__device__ typename Ext<C>::E ring_area_warp(const MarkerArgs& a, int m, typename Ext<C>::E* red) {
+__device__ typename Ext<C>::E ring_area_group(const MarkerArgs& a, int m, int w0, typename Ext<C>::E* red,
+                                              int bar) {
     using E = typename Ext<C>::E;
-    const int lane = threadIdx.x & 31;
+    const int t = threadIdx.x - 32 * w0;  // 0 .. 32 kAreaWarps - 1
+    const int lane = t & 31, w = t >> 5;
     const int off = a.mem_off[m], n = a.mem_n[m];
     E xr, yr;
     load_pos<C>(a, off, xr, yr);
     E acc = ezero<E>();
-#pragma unroll 2
-    for (int k = lane; k < n; k += 32) {
+    for (int k = t; k < n; k += 32 * kAreaWarps) {
         const int R = k == n - 1 ? 0 : k + 1;
         E xv, yv, xR, yR;
         load_pos<C>(a, off + k, xv, yv);
         load_pos<C>(a, off + R, xR, yR);
-        const E t = esub(emul(esub(xv, xr), esub(yR, yr)), emul(esub(xR, xr), esub(yv, yr)));
-        acc = eadd(acc, t);
+        const E term = esub(emul(esub(xv, xr), esub(yR, yr)), emul(esub(xR, xr), esub(yv, yr)));
+        acc = eadd(acc, term);
     }
-    red[lane] = acc;
+    E* r = red + 32 * w;
+    r[lane] = acc;
     __syncwarp();
     for (int o = 16; o > 0; o >>= 1) {
-        if (lane < o) red[lane] = eadd(red[lane], red[lane + o]);
+        if (lane < o) r[lane] = eadd(r[lane], r[lane + o]);
         __syncwarp();
     }
-    return emulc(red[0], C(0.5));
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(32 * kAreaWarps) : "memory");
+    E s = red[0];
+#pragma unroll
+    for (int q = 1; q < kAreaWarps; ++q) s = eadd(s, red[32 * q]);
+    return emulc(s, C(0.5));
 }
 
 // block-wide sum in the compute type (all threads get it)
