@@ -362,7 +362,7 @@ static lbib_status finalize(lbib_ctx* c) {
         add(32 * nv); add(4 * nv); add(16 * nv + 16 * nr);
         add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
         add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
-        add(16 * nr); add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size());
+        add(16 * nr); add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size()); add(16 * nr);
         add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
         add(4 * au_lig_off.size()); add(4 * au_ligs.size()); add(4 * strad.size());
@@ -412,6 +412,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.claim = ar.take<int>(nr);
     int* d_rcs = ar.take<int>(rcell_start.size());
     int* d_rci = ar.take<int>(rcell_ids.size());
+    void* d_rcpos = ar.take<double>(2 * (size_t)nr);
     c->flags[0] = ar.take<int>(c->ntiles);
     c->flags[1] = ar.take<int>(c->ntiles);
     c->d_areas = ar.take<double>(nm + 1);
@@ -466,7 +467,18 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(cudaMemsetAsync(a.claim, 0x7F, 4 * nr, c->stream));  // 0x7F7F7F7F: no claim
     }
     CK(H2D(d_rcs, rcell_start.data(), 4 * rcell_start.size()));
-    if (!rcell_ids.empty()) CK(H2D(d_rci, rcell_ids.data(), 4 * rcell_ids.size()));
+    if (!rcell_ids.empty()) {
+        CK(H2D(d_rci, rcell_ids.data(), 4 * rcell_ids.size()));
+        // receptor positions permuted into cell order (staged through xy_stage)
+        std::vector<double> rp(2 * (size_t)nr);
+        for (int p = 0; p < nr; ++p) {
+            rp[2 * p] = c->h_rec[2 * rcell_ids[p]];
+            rp[2 * p + 1] = c->h_rec[2 * rcell_ids[p] + 1];
+        }
+        CK(H2D(c->xy_stage, rp.data(), 16 * (size_t)nr));
+        CK(launch_pos_in(c->prec, c->xy_stage, d_rcpos, nr, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // rp leaves scope
+    }
     CK(cudaMemsetAsync(c->flags[0], 0, 4 * c->ntiles, c->stream));
     CK(cudaMemsetAsync(c->flags[1], 0, 4 * c->ntiles, c->stream));
     CK(cudaMemsetAsync(c->tickets, 0, 16, c->stream));
@@ -487,7 +499,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.au_lig_off = d_au_lig_off; a.au_ligs = d_au_ligs;
     a.nstrad = (int)strad.size(); a.strad_ligs = d_strad;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
-    a.rec_xy = rec_xy; a.rec_e = rec_e; a.rcell_start = d_rcs; a.rcell_ids = d_rci;
+    a.rec_xy = rec_xy; a.rec_e = rec_e; a.rcell_start = d_rcs; a.rcell_ids = d_rci; a.rcell_pos = d_rcpos;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
     a.inv_rc_w = 1.0 / rc_w; a.inv_rc_h = 1.0 / rc_h;
     a.inv_y_eq = c->bp.y_eq > 0 ? 1.0 / c->bp.y_eq : 0.0;

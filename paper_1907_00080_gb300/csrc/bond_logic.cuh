@@ -113,6 +113,9 @@ struct LigandPoint {
     __device__ C dist_est(const MarkerArgs& a, int r) const {
         typename Ext<C>::E rx, ry;
         PosIO<C>::load(a.rec_e, r, rx, ry);
+        return dist_est_at(a, rx, ry);
+    }
+    __device__ C dist_est_at(const MarkerArgs& a, typename Ext<C>::E rx, typename Ext<C>::E ry) const {
         const C dx = etoc(ewrap(esub(rx, cx), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
         C dy = etoc(esub(ry, cy));
         if (!a.walls) dy = etoc(ewrap(esub(ry, cy), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
@@ -128,15 +131,16 @@ struct LigandPoint {
     }
 };
 
-// formation test of ligand l with receptor r (tag 0): d < d_cut and u < P_f(d)
+// formation test of ligand l with receptor r at (rx, ry) (tag 0): d < d_cut and u < P_f(d)
 template <typename C>
-__device__ __forceinline__ bool forms(const MarkerArgs& a, LigandPoint<C>& lp, long long step, int l, int r) {
+__device__ __forceinline__ bool forms(const MarkerArgs& a, LigandPoint<C>& lp, long long step, int l, int r,
+                                      typename Ext<C>::E rx, typename Ext<C>::E ry) {
     if (sizeof(C) == 8) {
         const double d = lp.dist(a, r);
         if (!(d < a.d_cut)) return false;
         return bond_uniform(a, step, l, r, 0) < p_form(a, d);
     }
-    const float df = float(lp.dist_est(a, r));
+    const float df = float(lp.dist_est_at(a, rx, ry));
     const float dc = a.f.d_cut;
     if (!(df < dc * (1.f + kMargin))) return false;  // surely beyond the cut-off
     double d = -1.0;
@@ -193,17 +197,27 @@ __device__ __forceinline__ void bond_decide(const MarkerArgs& a, int l, LigandPo
     int gx = (int)floorf(xw * a.f.inv_rc_w);
     gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
     const int gy = (int)fminf(fmaxf(floorf((cyh - a.f.rc_y0) * a.f.inv_rc_h), -4.f), float(a.rc_ny) + 4.f);
+    // the three cell rows' ranges first (independent loads), then their receptors
+    int p0[9], p1[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const int qy = gy - 1 + c / 3, qx = gx - 1 + c % 3;
+        p0[c] = p1[c] = 0;
+        if (qy >= 0 && qy < a.rc_ny) {
+            const int cell = qy * a.rc_nx + ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
+            p0[c] = a.rcell_start[cell];
+            p1[c] = a.rcell_start[cell + 1];
+        }
+    }
     int best = INT_MAX;
-    for (int qy = gy - 1; qy <= gy + 1; ++qy) {
-        if (qy < 0 || qy >= a.rc_ny) continue;
-        for (int qx = gx - 1; qx <= gx + 1; ++qx) {
-            const int cxc = ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
-            const int cell = qy * a.rc_nx + cxc;
-            for (int p = a.rcell_start[cell]; p < a.rcell_start[cell + 1]; ++p) {
-                const int rr = a.rcell_ids[p];
-                if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
-                if (forms<C>(a, lp, step, l, rr)) best = rr;
-            }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        for (int p = p0[c]; p < p1[c]; ++p) {
+            const int rr = a.rcell_ids[p];
+            typename Ext<C>::E rx, ry;
+            PosIO<C>::load(a.rcell_pos, p, rx, ry);
+            if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
+            if (forms<C>(a, lp, step, l, rr, rx, ry)) best = rr;
         }
     }
     if (best != INT_MAX) {
@@ -216,20 +230,31 @@ __device__ __forceinline__ void bond_decide(const MarkerArgs& a, int l, LigandPo
 // ruptures and the winning claims, clear the claims, advance the step counter.
 // Data written by other blocks is read past L1.
 static __device__ __forceinline__ void bond_apply_all(const MarkerArgs& a) {
-    for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
-        const int r_old = __ldcg(&a.rupt[q]);
-        if (r_old >= 0) {
-            a.owner[r_old] = -1;
-            a.bond_of_lig[q] = -1;
-            a.rupt[q] = -1;
+    constexpr int kPer = 4;  // ligands per thread per pass, loads issued together
+    for (int base = 0; base < a.nlig; base += kPer * blockDim.x) {
+        int q[kPer], r_old[kPer], c[kPer], cl[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            q[i] = base + threadIdx.x + i * blockDim.x;
+            r_old[i] = q[i] < a.nlig ? __ldcg(&a.rupt[q[i]]) : -1;
+            c[i] = q[i] < a.nlig ? __ldcg(&a.cand[q[i]]) : -1;
         }
-        const int c = __ldcg(&a.cand[q]);
-        if (c >= 0 && __ldcg(&a.claim[c]) == q) {
-            a.bond_of_lig[q] = c;
-            a.owner[c] = q;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) cl[i] = c[i] >= 0 ? __ldcg(&a.claim[c[i]]) : -1;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            if (r_old[i] >= 0) {
+                a.owner[r_old[i]] = -1;
+                a.bond_of_lig[q[i]] = -1;
+                a.rupt[q[i]] = -1;
+            }
+            if (c[i] >= 0 && cl[i] == q[i]) {
+                a.bond_of_lig[q[i]] = c[i];
+                a.owner[c[i]] = q[i];
+            }
         }
     }
-    __syncthreads();
+    __syncthreads();  // every claim has been read before any is cleared
     for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
         const int c = __ldcg(&a.cand[q]);
         if (c >= 0) {

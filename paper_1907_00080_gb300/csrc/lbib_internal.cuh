@@ -147,7 +147,8 @@ struct MarkerArgs {
     int* owner;               // [nrec]
     int* claim;               // [nrec]
     const int* rcell_start;   // [ncell + 1]
-    const int* rcell_ids;     // [nrec]
+    const int* rcell_ids;     // [nrec] receptor ids in cell order
+    const void* rcell_pos;    // [nrec] their positions, same order, marker position layout
     int rc_nx, rc_ny;         // receptor grid
     double rc_w, rc_h, rc_y0; // cell size, y origin
     double inv_rc_w, inv_rc_h, inv_y_eq;
