@@ -71,6 +71,7 @@ __device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, E xa
 constexpr int kForceWarps = 10;
 constexpr int kForceThreads = 32 * kForceWarps;  // threads per force block
 constexpr int kMaxCand = 256;                     // repulsion candidate segments per block
+constexpr int kStageSeg = 48;                     // candidate segments staged in shared memory
 
 // One block per work unit (a chunk of up to kChunkV consecutive vertices of one
 // membrane).  The warps split the work of a vertex:
@@ -101,6 +102,10 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     __shared__ C s_ca;
     __shared__ int s_cand[kMaxCand];
     __shared__ int s_ncand;
+    // staged candidate segments: box, and the positions of their vertices
+    __shared__ float4 s_cbox[kStageSeg];
+    __shared__ E s_cx[kStageSeg * kSegV], s_cy[kStageSeg * kSegV];
+    __shared__ int s_cn[kStageSeg];
     const Rest<C>* rest = static_cast<const Rest<C>*>(a.rest);
 
     // ---- phase 0: positions of the chunk and two halo vertices on each side
@@ -271,6 +276,20 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
                 if (hit && pos < kMaxCand) s_cand[pos] = sg;
                 cnt += __popc(bal);
             }
+            __syncwarp();
+            // stage the first kStageSeg candidates: box, vertex count, positions
+            const int nst = cnt < kStageSeg ? cnt : kStageSeg;
+            for (int ci = lane; ci < nst; ci += 32) {
+                const int sg = s_cand[ci];
+                s_cbox[ci] = a.seg_box[sg];
+                s_cn[ci] = a.seg_n[sg];
+            }
+            for (int e = lane; e < nst * kSegV; e += 32) {
+                const int ci = e / kSegV, g = e - ci * kSegV;
+                const int sg = s_cand[ci];
+                const int nb = a.seg_n[sg];
+                if (g < nb) load_pos<C>(a, a.seg_v0[sg] + g, s_cx[e], s_cy[e]);
+            }
         }
         if (lane == 0) s_ncand = cnt;
     }
@@ -330,21 +349,28 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         const C drep = par<C>(a.d_rep, a.f.d_rep);
         for (int p = tid - 64; p < nscan * kn; p += blockDim.x - 64) {
             const int ci = p / kn, j = p - ci * kn;
+            const bool staged = !all_segs && ci < kStageSeg;
             const int sg = all_segs ? ci : s_cand[ci];
-            if (a.seg_mem[sg] == m) continue;
+            if (all_segs && a.seg_mem[sg] == m) continue;
             const E xv = s_x[j + 2], yv = s_y[j + 2];
             const float hx = float(ehi(xv));
             const float xvw = hx - a.f.nx * floorf(hx * a.f.inv_nx);
-            const float4 bx = a.seg_box[sg];
+            const float4 bx = staged ? s_cbox[ci] : a.seg_box[sg];
             const float ddx = wrap_half(xvw - bx.x, a.f.nx);
             float ddy = float(ehi(yv)) - bx.y;
             if (!a.walls) ddy = wrap_half(ddy, a.f.ny);
             if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
-            const int b0 = a.seg_v0[sg], nb = a.seg_n[sg];
+            const int nb = staged ? s_cn[ci] : a.seg_n[sg];
+            const int b0 = staged ? 0 : a.seg_v0[sg];
             C mags = C(0);
-            for (int b = b0; b < b0 + nb; ++b) {
+            for (int g = 0; g < nb; ++g) {
                 E xb, yb;
-                load_pos<C>(a, b, xb, yb);
+                if (staged) {
+                    xb = s_cx[ci * kSegV + g];
+                    yb = s_cy[ci * kSegV + g];
+                } else {
+                    load_pos<C>(a, b0 + g, xb, yb);
+                }
                 const C dx = etoc(ewrap(esub(xv, xb), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
                 C dy = etoc(esub(yv, yb));
                 if (!a.walls) dy = etoc(ewrap(esub(yv, yb), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
