@@ -14,6 +14,21 @@
 namespace lbib {
 
 constexpr int kRigidPer = 4;  // vertices per thread of a rigid unit (<= 4 * kChunkV vertices)
+constexpr int kMaxPairs = 512;  // (ligand, receptor) formation candidates staged per block
+
+// receptor position p of the cell-ordered array
+template <typename C>
+__device__ __forceinline__ typename Ext<C>::E ehi_pos_x(const MarkerArgs& a, int p) {
+    typename Ext<C>::E x, y;
+    PosIO<C>::load(a.rcell_pos, p, x, y);
+    return x;
+}
+template <typename C>
+__device__ __forceinline__ typename Ext<C>::E ehi_pos_y(const MarkerArgs& a, int p) {
+    typename Ext<C>::E x, y;
+    PosIO<C>::load(a.rcell_pos, p, x, y);
+    return y;
+}
 
 template <typename C>
 __device__ __forceinline__ void load_pos_cg(const void* X, int v, typename Ext<C>::E& x,
@@ -142,14 +157,75 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
     }
     __syncthreads();
 
-    // ---- bond decisions for the ligands whose element lies inside this unit
-    const int q1 = a.nrec > 0 ? a.au_lig_off[u + 1] : a.au_lig_off[u];
-    for (int q = a.au_lig_off[u] + tid; q < q1; q += blockDim.x) {
-        const int l = a.au_ligs[q];
-        const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
-        LigandPoint<C> lp;
-        lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
-        bond_decide<C>(a, l, lp, step);
+    // ---- bond decisions for the ligands whose element lies inside this unit.
+    // (a) per ligand: rupture test of its bond, and the receptors of the 3x3
+    //     cells around it that were free at the start of the step, as
+    //     (ligand, receptor) pairs;
+    // (b) per pair: the formation test; each ligand keeps the lowest passing
+    //     receptor id (a minimum: independent of evaluation order);
+    // (c) per ligand that is free after (a): claim its receptor.
+    const int lq0 = a.au_lig_off[u];
+    const int nlq = a.nrec > 0 ? a.au_lig_off[u + 1] - lq0 : 0;
+    if (nlq > 0) {
+        __shared__ int s_pl[kMaxPairs], s_pr[kMaxPairs];
+        __shared__ int s_best[kRigidPer * kChunkV];
+        __shared__ int s_look[kRigidPer * kChunkV];
+        __shared__ int s_np;
+        if (tid == 0) s_np = 0;
+        __syncthreads();
+        for (int q = tid; q < nlq; q += blockDim.x) {
+            const int l = a.au_ligs[lq0 + q];
+            const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
+            LigandPoint<C> lp;
+            lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
+            s_best[q] = INT_MAX;
+            bool look = lp.finite();  // non-finite positions: reported above
+            const int r = a.bond_of_lig[l];
+            if (look && r >= 0) {
+                look = ruptures<C>(a, lp, step, l, r);
+                if (look) a.rupt[l] = r;
+            }
+            s_look[q] = look;
+            if (!look) continue;
+            int p0[9], p1[9];
+            ligand_cells<C>(a, lp, p0, p1);
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                for (int p = p0[c]; p < p1[c]; ++p) {
+                    const int rr = a.rcell_ids[p];
+                    if (a.owner[rr] >= 0) continue;  // bound at the start of the step
+                    const int slot = atomicAdd(&s_np, 1);
+                    if (slot < kMaxPairs) {
+                        s_pl[slot] = q;
+                        s_pr[slot] = p;
+                    } else if (forms<C>(a, lp, step, l, rr, ehi_pos_x<C>(a, p), ehi_pos_y<C>(a, p))) {
+                        atomicMin(&s_best[q], rr);  // list full: decide in place
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int np = s_np < kMaxPairs ? s_np : kMaxPairs;
+        for (int t = tid; t < np; t += blockDim.x) {
+            const int q = s_pl[t], p = s_pr[t];
+            const int l = a.au_ligs[lq0 + q];
+            const int rr = a.rcell_ids[p];
+            const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
+            LigandPoint<C> lp;
+            lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
+            typename Ext<C>::E rx, ry;
+            PosIO<C>::load(a.rcell_pos, p, rx, ry);
+            if (forms<C>(a, lp, step, l, rr, rx, ry)) atomicMin(&s_best[q], rr);
+        }
+        __syncthreads();
+        for (int q = tid; q < nlq; q += blockDim.x) {
+            const int best = s_best[q];
+            if (s_look[q] && best != INT_MAX) {
+                const int l = a.au_ligs[lq0 + q];
+                a.cand[l] = best;
+                atomicMin(&a.claim[best], l);
+            }
+        }
     }
 
     // ---- epilogue of the last block: straddling ligands, apply, next step

@@ -226,6 +226,27 @@ __device__ __forceinline__ void bond_decide(const MarkerArgs& a, int l, LigandPo
     }
 }
 
+// 3x3 receptor-grid cells around a ligand point: the nine [p0, p1) ranges of
+// the cell-ordered receptor arrays (empty outside the grid's rows)
+template <typename C>
+__device__ __forceinline__ void ligand_cells(const MarkerArgs& a, const LigandPoint<C>& lp, int p0[9], int p1[9]) {
+    const float cxh = float(ehi(lp.cx)), cyh = float(ehi(lp.cy));
+    const float xw = cxh - a.f.nx * floorf(cxh * a.f.inv_nx);
+    int gx = (int)floorf(xw * a.f.inv_rc_w);
+    gx = gx >= a.rc_nx ? a.rc_nx - 1 : (gx < 0 ? 0 : gx);
+    const int gy = (int)fminf(fmaxf(floorf((cyh - a.f.rc_y0) * a.f.inv_rc_h), -4.f), float(a.rc_ny) + 4.f);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const int qy = gy - 1 + c / 3, qx = gx - 1 + c % 3;
+        p0[c] = p1[c] = 0;
+        if (qy >= 0 && qy < a.rc_ny) {
+            const int cell = qy * a.rc_nx + ((qx % a.rc_nx) + a.rc_nx) % a.rc_nx;
+            p0[c] = a.rcell_start[cell];
+            p1[c] = a.rcell_start[cell + 1];
+        }
+    }
+}
+
 // Epilogue run by one block after every ligand has been decided: apply the
 // ruptures and the winning claims, clear the claims, advance the step counter.
 // Data written by other blocks is read past L1.

@@ -102,9 +102,11 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     __shared__ C s_ca;
     __shared__ int s_cand[kMaxCand];
     __shared__ int s_ncand;
-    // staged candidate segments: box, and the positions of their vertices
+    // staged candidate segments: box, anchor (first vertex) and the offsets of
+    // their vertices from the anchor in the compute type
     __shared__ float4 s_cbox[kStageSeg];
-    __shared__ E s_cx[kStageSeg * kSegV], s_cy[kStageSeg * kSegV];
+    __shared__ E s_cax[kStageSeg], s_cay[kStageSeg];
+    __shared__ C s_cox[kStageSeg * kSegV], s_coy[kStageSeg * kSegV];
     __shared__ int s_cn[kStageSeg];
     const Rest<C>* rest = static_cast<const Rest<C>*>(a.rest);
 
@@ -283,12 +285,19 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
                 const int sg = s_cand[ci];
                 s_cbox[ci] = a.seg_box[sg];
                 s_cn[ci] = a.seg_n[sg];
+                load_pos<C>(a, a.seg_v0[sg], s_cax[ci], s_cay[ci]);
             }
+            __syncwarp();
             for (int e = lane; e < nst * kSegV; e += 32) {
                 const int ci = e / kSegV, g = e - ci * kSegV;
                 const int sg = s_cand[ci];
                 const int nb = a.seg_n[sg];
-                if (g < nb) load_pos<C>(a, a.seg_v0[sg] + g, s_cx[e], s_cy[e]);
+                if (g < nb) {
+                    E xb, yb;
+                    load_pos<C>(a, a.seg_v0[sg] + g, xb, yb);
+                    s_cox[e] = etoc(esub(xb, s_cax[ci]));
+                    s_coy[e] = etoc(esub(yb, s_cay[ci]));
+                }
             }
         }
         if (lane == 0) s_ncand = cnt;
@@ -360,22 +369,29 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             float ddy = float(ehi(yv)) - bx.y;
             if (!a.walls) ddy = wrap_half(ddy, a.f.ny);
             if (fabsf(ddx) > bx.z + reach || fabsf(ddy) > bx.w + reach) continue;
-            const int nb = staged ? s_cn[ci] : a.seg_n[sg];
-            const int b0 = staged ? 0 : a.seg_v0[sg];
             C mags = C(0);
-            for (int g = 0; g < nb; ++g) {
-                E xb, yb;
-                if (staged) {
-                    xb = s_cx[ci * kSegV + g];
-                    yb = s_cy[ci * kSegV + g];
-                } else {
-                    load_pos<C>(a, b0 + g, xb, yb);
+            if (staged) {
+                // vertex relative to the segment anchor once, then plain differences
+                const int nb = s_cn[ci];
+                const C dxa = etoc(ewrap(esub(xv, s_cax[ci]), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
+                C dya = etoc(esub(yv, s_cay[ci]));
+                if (!a.walls) dya = etoc(ewrap(esub(yv, s_cay[ci]), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
+                for (int g = 0; g < nb; ++g) {
+                    const C dx = dxa - s_cox[ci * kSegV + g], dy = dya - s_coy[ci * kSegV + g];
+                    const C d = sqrt(dx * dx + dy * dy);
+                    if (d < drep) mags += c_rep * sqrt(C(1) / (d * d * d * d * d));
                 }
-                const C dx = etoc(ewrap(esub(xv, xb), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
-                C dy = etoc(esub(yv, yb));
-                if (!a.walls) dy = etoc(ewrap(esub(yv, yb), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
-                const C d = sqrt(dx * dx + dy * dy);
-                if (d < drep) mags += c_rep * sqrt(C(1) / (d * d * d * d * d));
+            } else {
+                const int nb = a.seg_n[sg], b0 = a.seg_v0[sg];
+                for (int g = 0; g < nb; ++g) {
+                    E xb, yb;
+                    load_pos<C>(a, b0 + g, xb, yb);
+                    const C dx = etoc(ewrap(esub(xv, xb), par<C>(a.nx, a.f.nx), par<C>(a.inv_nx, a.f.inv_nx)));
+                    C dy = etoc(esub(yv, yb));
+                    if (!a.walls) dy = etoc(ewrap(esub(yv, yb), par<C>(a.ny, a.f.ny), par<C>(a.inv_ny, a.f.inv_ny)));
+                    const C d = sqrt(dx * dx + dy * dy);
+                    if (d < drep) mags += c_rep * sqrt(C(1) / (d * d * d * d * d));
+                }
             }
             if (mags != C(0)) atomicAdd(&s_rep[j], (unsigned long long)to_fix60<C>(mags));
         }
