@@ -175,6 +175,30 @@ lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t* ligand_ids, int32_t* recepto
  * NULL, the enclosed area of each membrane (Eq. areaFor's Green area). */
 lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
 
+/* Allocation-free FP64 mass of a population buffer the caller owns.  The
+ * paper has no counterpart: this is a library service for callers that must not
+ * allocate device memory at the time of the call, e.g. a monitor running between
+ * steps on a thread where cudaMalloc/cudaFree would synchronise the device, or a
+ * program whose memory pool has already reserved the device memory.
+ *
+ *  f       device pointer (current device) to 9*n_nodes doubles, any order of
+ *          the values (e.g. the layout of lbib_read_populations); 8-byte aligned
+ *  n_nodes 0 .. 7,456,540 (9*n_nodes <= 2^26); 0 gives mass 0
+ *  mass    device pointer (current device) that receives sum_k f[k]
+ *  stream  cudaStream_t to enqueue on (NULL: the legacy default stream)
+ *
+ * The sum runs in a fixed order (run-to-run deterministic).  It enqueues two
+ * kernels and returns without synchronising.  Scratch: one fixed 32 KiB array
+ * per device inside the library; its address is looked up on the first call
+ * on each device (with that device current), so make that first call before
+ * any stream capture.  Calls on one device that overlap in time (other streams
+ * or host threads) race on the scratch: serialise them.
+ * Errors: LBIB_E_INVALID for NULL or misaligned pointers, a pointer that is
+ * not device memory of the current device, or n_nodes out of range (nothing is
+ * launched); LBIB_E_CUDA if the scratch lookup or a launch fails.  No message
+ * is kept (there is no context). */
+lbib_status lbib_population_mass_noalloc(const double* f, int64_t n_nodes, double* mass, void* stream);
+
 /* Tile shape of the fused kernel: vec consecutive x nodes per thread, ty rows
  * per block (vec in {1,2,4,8} dividing NX, storage-aligned; ty in 1..16).
  * Must precede the first step.  0,0 picks the default. */

@@ -70,6 +70,7 @@ _SIGS = {
     "lbib_read_marker_velocity": (_I, [_P, _DP]),
     "lbib_read_bonds": (_I, [_P, _I32P, _I32P, _I32, _I32P]),
     "lbib_diagnostics": (_I, [_P, _DP, _DP]),
+    "lbib_population_mass_noalloc": (_I, [_P, _I64, _P, _P]),
     "lbib_set_tiling": (_I, [_P, _I32, _I32]),
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
@@ -210,6 +211,14 @@ def lbib_diagnostics(ctx, n_membranes=0):
     areas = np.zeros(max(n_membranes, 1))
     _check(ctx, load().lbib_diagnostics(ctx, _dptr(mass), _dptr(areas) if n_membranes else None))
     return float(mass[0]), areas[:n_membranes]
+
+
+def lbib_population_mass_noalloc(f_dev, n_nodes, mass_dev, stream=None):
+    """Device addresses (ints) in, status out; enqueues only (no sync, no
+    allocation).  Returns the lbib_status code (no context, no message)."""
+    return load().lbib_population_mass_noalloc(ctypes.c_void_p(f_dev), int(n_nodes),
+                                               ctypes.c_void_p(mass_dev),
+                                               ctypes.c_void_p(stream) if stream else None)
 
 
 def lbib_set_tiling(ctx, vec, ty):
