@@ -323,15 +323,9 @@ def lbib_main(args):
 def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
     """Fused kernel on an 8192 x 2048 lattice (1.2 GB of FP32 populations per
     buffer, far above L2) with the capillary's marker density scaled up."""
-    from paper_1907_00080_gb300 import inputs
+    from paper_1907_00080_gb300.profile_case import probe_workload
     nx, ny = 8192, 2048
-    wl = inputs.Workload(name="probe", nx=nx, ny=ny, body_force=(inputs.body_force_for(1e-5, ny), 0.0),
-                         walls=1, init="poiseuille", precision=precision, membranes=[], receptors=None)
-    rng = np.random.Generator(np.random.PCG64(1))
-    # carriers spread over the lattice: ~1.6 % of the nodes under a stencil, like 640x160
-    for k in range(256):
-        cx, cy = rng.uniform(0, nx), rng.uniform(20, ny - 20)
-        wl.membranes.append(inputs.Membrane(xy=inputs.circle(cx, cy, 8.0, 50), ks=1e-4, kb=0.0, ka=1.0))
+    wl = probe_workload(nx, ny, precision)  # 256 soft carriers of 50 markers
     sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
     vec, ty = sim.tiling
     with torch.cuda.stream(stream):
