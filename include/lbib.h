@@ -199,9 +199,19 @@ lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
  * is kept (there is no context). */
 lbib_status lbib_population_mass_noalloc(const double* f, int64_t n_nodes, double* mass, void* stream);
 
-/* Tile shape of the fused kernel: vec consecutive x nodes per thread, ty rows
- * per block (vec in {1,2,4,8} dividing NX, storage-aligned; ty in 1..16).
- * Must precede the first step.  0,0 picks the default. */
+/* Form and tile shape of the fused collide-stream kernel.  Must precede the
+ * first step; 0,0 picks the default (for F32 and 16-bit storage the
+ * persistent form when the two population buffers exceed ~96 MB, else a
+ * row-tile shape).
+ *  ty in 1..16: row tiles, vec consecutive x nodes per thread and ty rows per
+ *    block; vec divides NX, with vec in {1,2} (F64), {1,2,4} (F32), {2,4,8}
+ *    (16-bit storage).
+ *  ty = 0: persistent bulk-copy form, one or more CTAs per SM streaming row
+ *    segments of 256*vec nodes through a 4-stage shared-memory pipeline;
+ *    vec in {1,2} (F64), {1,2,4} (F32), {2,4,8} (16-bit); NX a multiple of
+ *    16 bytes of storage (2, 4 or 8 nodes).
+ * Errors: LBIB_E_INVALID for other shapes, LBIB_E_STATE after the first step.
+ * The forms give bitwise identical results. */
 lbib_status lbib_set_tiling(lbib_ctx* ctx, int32_t vec, int32_t ty);
 lbib_status lbib_get_tiling(const lbib_ctx* ctx, int32_t* vec, int32_t* ty);
 

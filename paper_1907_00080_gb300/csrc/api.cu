@@ -61,7 +61,28 @@ bool valid_vec(lbib_precision p, int vec, int nx) {
     }
 }
 
+// persistent bulk-copy form: npt nodes per thread (segments of 256 npt nodes);
+// rows must split into whole 16-byte chunks
+bool valid_stream(lbib_precision p, int npt, int nx) {
+    if (nx % lb_stream_halo(p)) return false;
+    switch (p) {
+        case LBIB_F64: return npt == 1 || npt == 2;
+        case LBIB_F32: return npt == 1 || npt == 2 || npt == 4;
+        default: return npt == 2 || npt == 4 || npt == 8;
+    }
+}
+
 void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
+    // lattices whose two population buffers do not fit in L2 stream through the
+    // persistent bulk-copy form, which keeps enough bytes in flight for DRAM
+    // (FP64 stays on row tiles: it is bound by the FP64 pipe, not by DRAM)
+    const double two_buffers = 2.0 * 9.0 * (double)c->pop_elem * c->nx * c->ny;
+    const int npt = c->prec == LBIB_F32 ? 2 : 4;
+    if (c->prec != LBIB_F64 && two_buffers > 96e6 && valid_stream(c->prec, npt, c->nx)) {
+        *vec = npt;
+        *ty = 0;
+        return;
+    }
     int v = c->prec == LBIB_F64 ? 2 : (c->prec == LBIB_F32 ? 4 : 8);
     while (v > 1 && !valid_vec(c->prec, v, c->nx)) v /= 2;
     const long long N = (long long)c->nx * c->ny;
@@ -232,8 +253,8 @@ extern "C" lbib_status lbib_set_tiling(lbib_ctx* c, int32_t vec, int32_t ty) {
         c->vec = c->ty = 0;
         return LBIB_OK;
     }
-    if (!valid_vec(c->prec, vec, c->nx) || ty < 1 || ty > 16)
-        return fail(c, LBIB_E_INVALID, "unsupported tiling");
+    const bool ok = ty == 0 ? valid_stream(c->prec, vec, c->nx) : (valid_vec(c->prec, vec, c->nx) && ty >= 1 && ty <= 16);
+    if (!ok) return fail(c, LBIB_E_INVALID, "unsupported tiling");
     c->vec = vec;
     c->ty = ty;
     return LBIB_OK;
@@ -254,8 +275,15 @@ extern "C" lbib_status lbib_get_tiling(const lbib_ctx* c, int32_t* vec, int32_t*
 static lbib_status finalize(lbib_ctx* c) {
     if (c->finalized) return LBIB_OK;
     if (!c->vec) default_tiling(c, &c->vec, &c->ty);
-    c->tile_w = 32 * c->vec;
-    c->tile_h = c->ty;
+    if (c->ty == 0) {
+        // persistent form: one force tile per row segment
+        c->tile_w = 256 * c->vec;
+        c->tile_h = 1;
+        CK(prepare_lb_stream(c->prec, c->vec, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, &c->stream_grid));
+    } else {
+        c->tile_w = 32 * c->vec;
+        c->tile_h = c->ty;
+    }
     c->tiles_x = (c->nx + c->tile_w - 1) / c->tile_w;
     c->tiles_y = (c->ny + c->tile_h - 1) / c->tile_h;
     c->ntiles = c->tiles_x * c->tiles_y;
@@ -545,7 +573,22 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.gy = c->gy;
     l.inv_scale = c->inv_scale;
     l.fields_only = 0;
+    l.tile_w = c->tile_w;
+    l.tile_h = c->tile_h;
+    l.tiles_x = c->tiles_x;
+    l.status = c->d_status;
+    if (c->nv == 0) {
+        l.flags = nullptr;
+        l.flags_other = nullptr;
+    }
     return l;
+}
+
+// the fused collide-stream kernel in the context's form
+static cudaError_t launch_fused(const lbib_ctx* c, const LbArgs& l, cudaStream_t s) {
+    const bool walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    if (c->ty == 0) return launch_lb_stream(c->prec, c->vec, walls, c->nv > 0, c->stream_grid, l, s);
+    return launch_lb_step(c->prec, c->vec, c->ty, walls, c->nv > 0, l, s);
 }
 
 // one time step from population buffer `src`: forces + weights + spreading,
@@ -558,8 +601,7 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     const bool has_ib = c->nv > 0;
     if (has_ib && (e = launch_forces(c->prec, a, c->max_mem_n, s)) != cudaSuccess) return e;
     const LbArgs l = lb_args(c, src, src, 1);
-    if ((e = launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, has_ib, l, s)) != cudaSuccess)
-        return e;
+    if ((e = launch_fused(c, l, s)) != cudaSuccess) return e;
     if (has_ib && (e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -632,6 +674,10 @@ extern "C" lbib_status lbib_sync(lbib_ctx* c) {
         c->poisoned = true;
         return fail(c, LBIB_E_NONFINITE, "a marker position became non-finite");
     }
+    if (st & ST_TIMEOUT) {
+        c->poisoned = true;
+        return fail(c, LBIB_E_TIMEOUT, "a bulk copy of the fused kernel never completed");
+    }
     return LBIB_OK;
 }
 
@@ -672,7 +718,11 @@ extern "C" lbib_status lbib_read_fields(lbib_ctx* c, double* rho, double* ux, do
     l.ux_out = du;
     l.uy_out = dv;
     l.fields_only = 1;
-    CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
+    // the row-tile kernel serves the read-back in either form (it looks the
+    // force flags up by the context's tile geometry)
+    const int rv = c->ty != 0 ? c->vec : (c->prec == LBIB_F32_STORE_F16 || c->prec == LBIB_F32_STORE_BF16 ? 2 : 1);
+    const int rt = c->ty != 0 ? c->ty : 4;
+    CK(launch_lb_step(c->prec, rv, rt, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
     if (!on_device) {
         if (rho) CK(cudaMemcpyAsync(rho, dr, N * 8, cudaMemcpyDeviceToHost, c->stream));
         if (ux) CK(cudaMemcpyAsync(ux, du, N * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -831,8 +881,8 @@ extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_
         l.src = c->f[c->cur];
         l.dst = c->f[1 - c->cur];
         l.gsum = c->G[gpar];
-        l.flags = c->flags[gpar];
-        CK(launch_lb_step(c->prec, c->vec, c->ty, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
+        l.flags = c->nv > 0 ? c->flags[gpar] : nullptr;
+        CK(launch_fused(c, l, c->stream));
         c->cur = 1 - c->cur;
     }
     CK(cudaEventRecord(e1, c->stream));

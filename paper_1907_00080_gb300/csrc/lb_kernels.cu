@@ -6,7 +6,7 @@
 // Paper: Coclite, arXiv 1907.00080, Sec. 2.1 (Eqs. BGK, feq, GaussHermite),
 // Sec. 2.2 (Eqs. forcedBGK, ForcingTerm; momentum with the half-force),
 // Sec. 3 (periodic x, no-slip walls in y).
-#include "lbib_internal.cuh"
+#include "lb_node.cuh"
 
 namespace lbib {
 
@@ -16,18 +16,6 @@ template <typename S, int VEC>
 struct alignas(sizeof(S) * VEC) Pack {
     S v[VEC];
 };
-
-// fixed-point force value (scaled by 2^52) to the compute type
-template <typename C> __device__ __forceinline__ C from_fix(long long v);
-template <> __device__ __forceinline__ float from_fix<float>(long long v) {
-    // two 32-bit conversions instead of a 64-bit one: hi 2^32 + lo, scaled by 2^-52
-    const int hi = (int)(v >> 32);
-    const unsigned lo = (unsigned)(v & 0xffffffffll);
-    return fmaf((float)hi, 9.5367431640625e-07f, (float)lo * 2.220446049250313e-16f);
-}
-template <> __device__ __forceinline__ double from_fix<double>(long long v) {
-    return __ll2double_rn(v) * kFixInv;
-}
 
 template <typename S, int VEC>
 __device__ __forceinline__ void load_pack(const S* __restrict__ row, int x0, bool ok, float inv,
@@ -111,7 +99,9 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     }
     bool flagged = false;
     if (HAS_IB) {
-        const int t = blockIdx.y * gridDim.x + blockIdx.x;
+        // this thread's force tile (one block per tile during a step; in the
+        // fields-only read-back the tiles may be those of the other kernel form)
+        const int t = (min(y, ny - 1) / a.tile_h) * a.tiles_x + min(x0, nx - 1) / a.tile_w;
         flagged = a.flags[t] != 0;
         const bool fo = a.clear_other && a.flags_other[t] != 0;
         __syncthreads();  // every warp has read flags_other[t] before it is cleared
@@ -140,30 +130,12 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     C rho_v[VEC], ux_v[VEC], uy_v[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-        C drho = C(0), jx = C(0), jy = C(0);
+        C fk[9], ok9[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            drho += f[i][k];
-            if (cx(i) != 0) jx += C(cx(i)) * f[i][k];
-            if (cy(i) != 0) jy += C(cy(i)) * f[i][k];
-        }
-        const C rho = C(1) + drho;
-        const C rinv = C(1) / rho;
-        const C ux = (jx + C(0.5) * Gx[k]) * rinv;
-        const C uy = (jy + C(0.5) * Gy[k]) * rinv;
-        const C uu = ux * ux + uy * uy;
-        rho_v[k] = rho;
-        ux_v[k] = ux;
-        uy_v[k] = uy;
+        for (int i = 0; i < 9; ++i) fk[i] = f[i][k];
+        collide_node<C>(fk, Gx[k], Gy[k], om, pre, ok9, rho_v[k], ux_v[k], uy_v[k]);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const C eu = C(cx(i)) * ux + C(cy(i)) * uy;
-            const C deq = wgt<C>(i) * (drho + rho * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * uu));
-            const C gx = C(3) * (C(cx(i)) - ux) + C(9) * eu * C(cx(i));
-            const C gy = C(3) * (C(cy(i)) - uy) + C(9) * eu * C(cy(i));
-            const C src_i = pre * wgt<C>(i) * (gx * Gx[k] + gy * Gy[k]);
-            out[i][k] = f[i][k] - om * (f[i][k] - deq) + src_i;
-        }
+        for (int i = 0; i < 9; ++i) out[i][k] = ok9[i];
     }
 
     if (!ok) return;
@@ -178,11 +150,12 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
         return;
     }
     S* __restrict__ dst = static_cast<S*>(a.dst);
+    const float scl = 1.0f / inv;  // 2^k, exact
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         Pack<S, VEC> p;
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) p.v[k] = Storage<S>::store(out[i][k], inv);
+        for (int k = 0; k < VEC; ++k) p.v[k] = Storage<S>::store(out[i][k], scl);
         *reinterpret_cast<Pack<S, VEC>*>(dst + (size_t)i * N + node) = p;
     }
     if (HAS_IB && flagged) {
@@ -276,7 +249,7 @@ __global__ void k_stream_in(const double* __restrict__ in, S* __restrict__ dst, 
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double d = in[(size_t)i * N + n] - wgt<double>(i);
-            const auto sv = Storage<S>::store((typename Storage<S>::C)d, inv);
+            const auto sv = Storage<S>::store((typename Storage<S>::C)d, 1.0f / inv);
             int sy = y - cy(i), sx = x - cx(i);
             sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
             if (walls && (sy < 0 || sy >= ny)) {
@@ -305,7 +278,7 @@ __global__ void k_init_poiseuille(S* __restrict__ dst, int nx, int ny, double ta
             const double eu = cx(i) * u;
             const double deq = wgt<double>(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u);
             const double src = pre * wgt<double>(i) * (3.0 * (cx(i) - u) + 9.0 * eu * cx(i)) * G;
-            dst[(size_t)i * N + n] = Storage<S>::store((typename Storage<S>::C)(deq + src), inv);
+            dst[(size_t)i * N + n] = Storage<S>::store((typename Storage<S>::C)(deq + src), 1.0f / inv);
         }
     }
 }

@@ -47,7 +47,8 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagona
 
 // ---------------------------------------------------------------- storage
 // Conversion between stored values and the compute type; 16-bit forms carry a
-// power-of-two scale (d_i * 2^k).
+// power-of-two scale: stored = d_i * 2^k, so load multiplies by inv = 2^-k and
+// store by scale = 2^k (both exact).
 template <typename S> struct Storage;
 template <> struct Storage<double> {
     using C = double;
@@ -62,12 +63,12 @@ template <> struct Storage<float> {
 template <> struct Storage<__half> {
     using C = float;
     __device__ static float load(__half s, float inv) { return __half2float(s) * inv; }
-    __device__ static __half store(float d, float inv) { return __float2half_rn(d / inv); }
+    __device__ static __half store(float d, float scale) { return __float2half_rn(d * scale); }
 };
 template <> struct Storage<__nv_bfloat16> {
     using C = float;
     __device__ static float load(__nv_bfloat16 s, float inv) { return __bfloat162float(s) * inv; }
-    __device__ static __nv_bfloat16 store(float d, float inv) { return __float2bfloat16_rn(d / inv); }
+    __device__ static __nv_bfloat16 store(float d, float scale) { return __float2bfloat16_rn(d * scale); }
 };
 
 // ---------------------------------------------------------------- kernel args
@@ -97,6 +98,8 @@ struct LbArgs {
     double gx, gy;         // body force
     float inv_scale;       // 2^-k for 16-bit storage, 1 otherwise
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
+    int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags
+    int* status;           // device status word (StatusBits)
 };
 
 struct MarkerArgs {
@@ -179,7 +182,7 @@ struct MarkerArgs {
     const int* strad_ligs;
 };
 
-enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2 };
+enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
 
 constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of 32)
 constexpr int kSegV = 8;      // vertices per repulsion-screening segment (divides kChunkV)
@@ -188,6 +191,14 @@ constexpr int kSegV = 8;      // vertices per repulsion-screening segment (divid
 // lb_kernels.cu
 cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,
                            const LbArgs& a, cudaStream_t s);
+// lb_stream_kernel.cu: the persistent bulk-copy form of the fused kernel (one
+// CTA per SM slot streams row segments of 256 * npt nodes through a 4-stage
+// shared-memory pipeline); prepare_ sets its shared-memory limit and returns
+// the grid size, outside any stream capture
+int lb_stream_halo(lbib_precision prec);  // elements per 16-byte halo chunk
+cudaError_t prepare_lb_stream(lbib_precision prec, int npt, bool walls, bool has_ib, int* grid);
+cudaError_t launch_lb_stream(lbib_precision prec, int npt, bool walls, bool has_ib, int grid,
+                             const LbArgs& a, cudaStream_t s);
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
                               bool walls, float inv_scale, cudaStream_t s);
 cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
@@ -232,7 +243,8 @@ struct lbib_ctx {
     double* dscalar = nullptr; // small device scratch for results
     int n_partials = 0;
 
-    int vec = 0, ty = 0;      // tiling of the fused kernel
+    int vec = 0, ty = 0;      // tiling of the fused kernel (ty = 0: persistent bulk-copy form, vec = npt)
+    int stream_grid = 0;      // CTAs of the persistent form (SMs x resident CTAs)
     int tile_w = 0, tile_h = 0, tiles_x = 0, tiles_y = 0, ntiles = 0;
 
     // host-side membrane staging

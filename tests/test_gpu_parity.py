@@ -102,6 +102,80 @@ def test_tilings_agree_bitwise():
         assert np.array_equal(b, outs[0][4]), (vec, ty)
 
 
+# persistent bulk-copy form of the fused kernel (tiling (npt, 0))
+STREAM_FORMS = {"f64": [(1, 0), (2, 0)], "f32": [(1, 0), (2, 0), (4, 0)],
+                "f16": [(2, 0), (4, 0), (8, 0)], "bf16": [(2, 0), (4, 0), (8, 0)]}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("walls", [1, 0])
+@pytest.mark.parametrize("nx,ny", [(200, 37), (8, 5), (1032, 9), (1024, 4)])
+def test_persistent_form_matches_oracle(prec, walls, nx, ny):
+    """Row segments of 256*npt nodes: single ragged segments (200, 8), a ragged
+    last segment after whole ones (1032), whole segments only (1024)."""
+    wl = lattice_only(nx, ny, walls=walls, tau=0.8, g=(1e-5, -2e-6), precision=prec)
+    f0 = inputs.random_populations(nx, ny, W9, seed=nx * ny + walls + 7, amp=5e-2)
+    r = make_oracle(wl)
+    r.set_populations(f0)
+    r.step(3)
+    f_ref = r.populations()
+    rho0, ux0, uy0 = r.fields()
+    for tiling in STREAM_FORMS[prec]:
+        s = sim_of(wl, tiling=tiling)
+        assert s.tiling == tiling
+        s.set_populations(f0)
+        s.step(3)
+        assert dev_err(s.populations(), f_ref, W9) < TOL[prec]["pop"], tiling
+        rho, ux, uy = s.fields()
+        assert rel_err(rho - 1, rho0 - 1) < TOL[prec]["field"], tiling
+        assert rel_err(ux, ux0) < TOL[prec]["field"], tiling
+        assert rel_err(uy, uy0) < TOL[prec]["field"], tiling
+        s.close()
+
+
+@pytest.mark.parametrize("prec,rowtile", [("f64", (2, 4)), ("f32", (4, 1)), ("f16", (8, 1)), ("bf16", (4, 2))])
+def test_forms_agree_bitwise_capsule(prec, rowtile):
+    wl = inputs.capsule_128x32(precision=prec, bonds="stress")
+    outs = []
+    for tiling in [rowtile] + STREAM_FORMS[prec]:
+        s = sim_of(wl, tiling=tiling)
+        s.step(60)
+        rho, ux, uy = s.fields()
+        outs.append((tiling, s.populations(), s.markers(), s.bonds(), ux))
+        s.close()
+    for tiling, f, x, b, ux in outs[1:]:
+        assert np.array_equal(f, outs[0][1]), tiling
+        assert np.array_equal(x, outs[0][2]), tiling
+        assert np.array_equal(b, outs[0][3]), tiling
+        assert np.array_equal(ux, outs[0][4]), tiling
+
+
+def test_forms_agree_bitwise_capillary_640x160():
+    wl = inputs.coarse_capillary_640x160(precision="f32")
+    wl.bonds = dict(inputs.STRESS_BONDS)
+    outs = []
+    for tiling in [(1, 2), (2, 0), (4, 0)]:
+        s = sim_of(wl, tiling=tiling)
+        s.step(80)
+        outs.append((tiling, s.populations(), s.markers(), s.bonds()))
+        s.close()
+    for tiling, f, x, b in outs[1:]:
+        assert np.array_equal(f, outs[0][1]), tiling
+        assert np.array_equal(x, outs[0][2]), tiling
+        assert np.array_equal(b, outs[0][3]), tiling
+
+
+def test_default_form_follows_lattice_size():
+    from paper_1907_00080_gb300.profile_case import probe_workload
+    small = sim_of(inputs.capsule_128x32("f32"))
+    assert small.tiling[1] > 0
+    big = sim_of(probe_workload(2048, 1024, "f32"))
+    assert big.tiling == (2, 0)
+    big.step(2)
+    _, ux, _ = big.fields()
+    assert np.all(np.isfinite(ux))
+
+
 def test_runs_are_deterministic():
     wl = inputs.capsule_128x32(precision="f64", bonds="stress")
     a, b = sim_of(wl), sim_of(wl)
