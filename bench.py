@@ -257,24 +257,31 @@ def lbib_main(args):
     units = wl.nx * wl.ny * T * args.steps * ws
     value = units / elapsed / 1e6
 
-    # ---- roofline of the fused kernel on this workload (scratch context)
+    # ---- per-kernel rooflines on this workload (scratch context); the
+    # top-level one is the kernel with the largest share of the time step
     pk, pk_kind = peaks()
-    alg_bytes_node = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[args.precision]
+    alg = alg_bytes_per_launch(args.precision, wl)
     scratch = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
     with torch.cuda.stream(stream):
         scratch.step(4)
         scratch.sync()
-        lbib.lbib_profile_fused(scratch.ctx, 200)
-        k1_ms = lbib.lbib_profile_fused(scratch.ctx, 2000)
+        lbib.lbib_profile_kernels(scratch.ctx, 50)
+        kms = lbib.lbib_profile_kernels(scratch.ctx, 500)
     scratch.close()
-    k1_gbs = alg_bytes_node * wl.nx * wl.ny / (k1_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": k1_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": k1_gbs / pk["hbm_gbs"], "traffic": None,
-                "kernel": "k_lb_step (fused pull-stream + IB gather + Guo BGK)",
-                "algorithmic_bytes_per_launch": alg_bytes_node * wl.nx * wl.ny,
-                "ms_per_launch": k1_ms, "peak_kind": pk_kind + " (copy bandwidth)",
-                "note": "the 7.4 MB lattice stays in the 129 MB L2 across back-to-back launches, "
-                        "so this can exceed the HBM copy peak; see roofline_hbm_probe"}
+    kernels = []
+    for name, ms_k, b in zip(KERNEL_NAMES, kms, alg):
+        gbs = b / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+        kernels.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": b,
+                        "traffic": NCU_TRAFFIC.get((name, args.precision, "capillary_640x160"))})
+    top = max(kernels, key=lambda k: k["ms_per_launch"])
+    roofline = dict(top)
+    roofline["peak_kind"] = pk_kind + " (copy bandwidth, burst)"
+    roofline["share_of_kernel_time"] = top["ms_per_launch"] / sum(k["ms_per_launch"] for k in kernels)
+    roofline["note"] = ("dominant kernel of the time step, timed alone on a copy of the workload; the marker "
+                        "kernels run a few dozen blocks on 152 SMs and are bound by dependent L2 round trips, "
+                        "not by bytes; the fused kernel's lattice (7.4 MB) stays in L2 here: see "
+                        "roofline_hbm_probe for the DRAM-bound case")
 
     probe = None
     if not args.no_probe and rank == 0:
@@ -288,7 +295,7 @@ def lbib_main(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         wl64 = workload("f64")
-        sample = 60
+        sample = 600
         mlups_cpu, dt_cpu, _ = cpu_oracle_mlups(wl64, sample)
         cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d time steps of the 640x160 capillary (all 12 membranes, bonds), FP64 C oracle, one thread, %.1f s" % (sample, dt_cpu)}
@@ -305,6 +312,7 @@ def lbib_main(args):
                        "l2": "flushed (256 MB write) between timed iterations; within one the lattice is L2-resident",
                        "parallelism": "replicas x%d" % ws},
             "roofline": roofline,
+            "roofline_kernels": kernels,
             "roofline_hbm_probe": probe,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -318,6 +326,39 @@ def lbib_main(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+KERNEL_NAMES = ("k_forces (forces, IB weights, spreading)", "k_lb_step / k_lb_stream (fused collide-stream)",
+                "k_advance (interpolation, advance, bonds)")
+
+# DRAM bytes per launch (read + write) from ncu captures of the current
+# kernels (profiles/marker_kernels_capillary_640x160_f32.md and
+# profiles/k_lb_stream_probe_8192x1024.md), keyed by kernel, precision and
+# workload; absent where no capture of the current kernel exists.
+NCU_TRAFFIC = {
+    (KERNEL_NAMES[0], "f32", "capillary_640x160"): 418048,
+    (KERNEL_NAMES[2], "f32", "capillary_640x160"): 636672,
+    # 8192 x 1024 capture scaled by the nodes to the 8192 x 2048 probe
+    ("k_lb_stream", "f32", "probe_8192x2048"): 2 * (322649600 + 257857792),
+}
+
+
+def alg_bytes_per_launch(precision, wl):
+    """Algorithmic bytes per launch of the three kernels of a time step.
+    forces, per vertex: position 16, rest record (28 FP32 / 32 FP64), force
+    2 values, 9 weights, stencil origin 8, 9 fixed-point spread
+    read-modify-writes of 16 B (288).  fused, per node: 9 populations read +
+    9 written.  advance, per vertex: 9 weights + stencil 8, 9 gathered
+    velocities (2 values each), X^n and X^{n-1} read and written (64), U (2
+    values)."""
+    cs = 8 if precision == "f64" else 4
+    rest = 32 if precision == "f64" else 28
+    pop = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[precision]
+    nv = wl.n_vertices
+    forces = nv * (16 + rest + 2 * cs + 9 * cs + 8 + 9 * 32)
+    fused = pop * wl.nx * wl.ny
+    advance = nv * (9 * cs + 8 + 18 * cs + 64 + 2 * cs)
+    return forces, fused, advance
 
 
 def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
@@ -336,9 +377,10 @@ def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
     sim.close()
     alg = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[precision] * nx * ny
     gbs = alg / (ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get(("k_lb_stream", precision, "probe_8192x2048")) if ty == 0 else None
     return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / pk["hbm_gbs"], "traffic": None, "nx": nx, "ny": ny, "tiling": [vec, ty],
-            "ms_per_launch": ms, "algorithmic_bytes_per_launch": alg, "peak_kind": pk_kind,
+            "frac": gbs / pk["hbm_gbs"], "traffic": traffic, "nx": nx, "ny": ny, "tiling": [vec, ty],
+            "ms_per_launch": ms, "algorithmic_bytes_per_launch": alg, "peak_kind": pk_kind + " (copy bandwidth, burst)",
             "mlups_fused_kernel": nx * ny / (ms * 1e-3) / 1e6}
 
 

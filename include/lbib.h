@@ -223,6 +223,17 @@ lbib_status lbib_get_tiling(const lbib_ctx* ctx, int32_t* vec, int32_t* ty);
  * Errors: LBIB_E_STATE before the first step. */
 lbib_status lbib_profile_fused(lbib_ctx* ctx, int32_t reps, double* ms_per_launch);
 
+/* Profiling aid: launch each kernel of the time step `reps` times back to
+ * back on the context's stream, each series bracketed by CUDA events, and
+ * return the mean duration of one launch in ms_per_launch[0..2]:
+ * [0] forces + IB weights + spreading, [1] fused collide-stream, [2]
+ * interpolation + advance + bond kinetics (0 for the marker kernels of a
+ * context without membranes).  The repeated launches leave the state
+ * inconsistent (forces accumulate, markers and bonds move without the
+ * fluid): use it on a scratch context.  Errors: LBIB_E_STATE before the
+ * first step. */
+lbib_status lbib_profile_kernels(lbib_ctx* ctx, int32_t reps, double* ms_per_launch);
+
 /* Number of kernels one time step launches (for launch accounting). */
 int32_t lbib_kernels_per_step(const lbib_ctx* ctx);
 

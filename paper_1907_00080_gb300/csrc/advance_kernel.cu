@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
     const int off = a.mem_off[m], n = a.mem_n[m];
     const int tid = threadIdx.x, lane = tid & 31;
     __shared__ E s_x[kRigidPer * kChunkV], s_y[kRigidPer * kChunkV];
-    __shared__ C cred[33];
+    __shared__ C cred[4 * 33];
     __shared__ bool s_last;
     const long long step = *a.d_step;
     C* U = static_cast<C*>(a.U);
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         // ---- rigid-projected membrane: the whole ring in this block
         E xr, yr;
         load_pos<C>(a, off, xr, yr);
-        E x[kRigidPer], y[kRigidPer];
+        E x[kRigidPer], y[kRigidPer], xpv[kRigidPer], ypv[kRigidPer];
         C Ux[kRigidPer], Uy[kRigidPer];
         C sx = 0, sy = 0, su = 0, sv = 0;
 #pragma unroll
@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
             const int k = tid + i * kChunkV;
             if (k < n) {
                 load_pos<C>(a, off + k, x[i], y[i]);
+                PosIO<C>::load(a.Xp, off + k, xpv[i], ypv[i]);
                 interp_vertex<C>(a, off + k, Ux[i], Uy[i]);
                 sx += etoc(esub(x[i], xr));
                 sy += etoc(esub(y[i], yr));
@@ -110,8 +111,8 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         }
         // least-squares rigid motion U_c + omega x (x - x_c), positions about vertex 0
         const C inv_n = C(1) / C(n);
-        const C mx = block_sum_c<C>(sx, cred) * inv_n, my = block_sum_c<C>(sy, cred) * inv_n;
-        const C mu = block_sum_c<C>(su, cred) * inv_n, mv = block_sum_c<C>(sv, cred) * inv_n;
+        block_sum4_c<C>(sx, sy, su, sv, cred);
+        const C mx = sx * inv_n, my = sy * inv_n, mu = su * inv_n, mv = sv * inv_n;
         C num = 0, den = 0;
 #pragma unroll
         for (int i = 0; i < kRigidPer; ++i) {
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
                 den += rx * rx + ry * ry;
             }
         }
-        const C om = block_sum_c<C>(num, cred) / block_sum_c<C>(den, cred);
+        C z0 = 0, z1 = 0;
+        block_sum4_c<C>(num, den, z0, z1, cred);
+        const C om = num / den;
 #pragma unroll
         for (int i = 0; i < kRigidPer; ++i) {
             const int k = tid + i * kChunkV;
@@ -132,10 +135,9 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
             const C px = mu - om * ry, py = mv + om * rx;
             U[2 * v] = px;
             U[2 * v + 1] = py;
-            E xp, yp, xn, yn;
-            PosIO<C>::load(a.Xp, v, xp, yp);
-            bdf2<C>(x[i], xp, px, step, xn);
-            bdf2<C>(y[i], yp, py, step, yn);
+            E xn, yn;
+            bdf2<C>(x[i], xpv[i], px, step, xn);
+            bdf2<C>(y[i], ypv[i], py, step, yn);
             if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
             PosIO<C>::store(a.Xp, v, x[i], y[i]);
             PosIO<C>::store(a.X, v, xn, yn);
@@ -170,12 +172,16 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         __shared__ int s_pl[kMaxPairs], s_pr[kMaxPairs];
         __shared__ int s_best[kRigidPer * kChunkV];
         __shared__ int s_look[kRigidPer * kChunkV];
+        __shared__ int s_lig[kRigidPer * kChunkV], s_ka[kRigidPer * kChunkV], s_kb[kRigidPer * kChunkV];
         __shared__ int s_np;
         if (tid == 0) s_np = 0;
         __syncthreads();
         for (int q = tid; q < nlq; q += blockDim.x) {
             const int l = a.au_ligs[lq0 + q];
             const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
+            s_lig[q] = l;
+            s_ka[q] = ka;
+            s_kb[q] = kb;
             LigandPoint<C> lp;
             lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
             s_best[q] = INT_MAX;
@@ -189,17 +195,20 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
             if (!look) continue;
             int p0[9], p1[9];
             ligand_cells<C>(a, lp, p0, p1);
+            // every receptor of the cells becomes a pair; whether it was free at
+            // the start of the step is checked per pair, in parallel
 #pragma unroll
             for (int c = 0; c < 9; ++c) {
                 for (int p = p0[c]; p < p1[c]; ++p) {
-                    const int rr = a.rcell_ids[p];
-                    if (a.owner[rr] >= 0) continue;  // bound at the start of the step
                     const int slot = atomicAdd(&s_np, 1);
                     if (slot < kMaxPairs) {
                         s_pl[slot] = q;
                         s_pr[slot] = p;
-                    } else if (forms<C>(a, lp, step, l, rr, ehi_pos_x<C>(a, p), ehi_pos_y<C>(a, p))) {
-                        atomicMin(&s_best[q], rr);  // list full: decide in place
+                    } else {
+                        // list full: decide in place
+                        const int rr = a.rcell_ids[p];
+                        if (a.owner[rr] < 0 && forms<C>(a, lp, step, l, rr, ehi_pos_x<C>(a, p), ehi_pos_y<C>(a, p)))
+                            atomicMin(&s_best[q], rr);
                     }
                 }
             }
@@ -208,20 +217,20 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         const int np = s_np < kMaxPairs ? s_np : kMaxPairs;
         for (int t = tid; t < np; t += blockDim.x) {
             const int q = s_pl[t], p = s_pr[t];
-            const int l = a.au_ligs[lq0 + q];
             const int rr = a.rcell_ids[p];
-            const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
-            LigandPoint<C> lp;
-            lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
             typename Ext<C>::E rx, ry;
             PosIO<C>::load(a.rcell_pos, p, rx, ry);
+            if (a.owner[rr] >= 0) continue;  // bound at the start of the step
+            const int l = s_lig[q], ka = s_ka[q], kb = s_kb[q];
+            LigandPoint<C> lp;
+            lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
             if (forms<C>(a, lp, step, l, rr, rx, ry)) atomicMin(&s_best[q], rr);
         }
         __syncthreads();
         for (int q = tid; q < nlq; q += blockDim.x) {
             const int best = s_best[q];
             if (s_look[q] && best != INT_MAX) {
-                const int l = a.au_ligs[lq0 + q];
+                const int l = s_lig[q];
                 a.cand[l] = best;
                 atomicMin(&a.claim[best], l);
             }

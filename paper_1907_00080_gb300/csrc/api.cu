@@ -896,6 +896,45 @@ extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_
     return LBIB_OK;
 }
 
+extern "C" lbib_status lbib_profile_kernels(lbib_ctx* c, int32_t reps, double* ms_per_launch) {
+    if (!c || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
+    if (!c->finalized || c->steps == 0) return fail(c, LBIB_E_STATE, "profile after at least one step");
+    cudaEvent_t ev[6];
+    for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&ev[k]));
+    const bool has_ib = c->nv > 0;
+    MarkerArgs a = c->ma;
+    a.gsum = c->G[c->cur];
+    a.flags = c->flags[c->cur];
+    // forces + spreading (accumulates into the field of the current parity)
+    CK(cudaEventRecord(ev[0], c->stream));
+    for (int r = 0; r < reps && has_ib; ++r) CK(launch_forces(c->prec, a, c->max_mem_n, c->stream));
+    CK(cudaEventRecord(ev[1], c->stream));
+    // fused collide-stream, ping-pong between the buffers
+    const int gpar = 1 - c->cur;
+    LbArgs l = lb_args(c, c->cur, gpar, 0);
+    CK(cudaEventRecord(ev[2], c->stream));
+    for (int r = 0; r < reps; ++r) {
+        l.src = c->f[c->cur];
+        l.dst = c->f[1 - c->cur];
+        CK(launch_fused(c, l, c->stream));
+        c->cur = 1 - c->cur;
+    }
+    CK(cudaEventRecord(ev[3], c->stream));
+    // interpolation + advance + bond kinetics
+    CK(cudaEventRecord(ev[4], c->stream));
+    for (int r = 0; r < reps && has_ib; ++r) CK(launch_advance(c->prec, a, c->stream));
+    CK(cudaEventRecord(ev[5], c->stream));
+    CK(cudaEventSynchronize(ev[5]));
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+        ms_per_launch[k] = (k != 1 && !has_ib) ? 0.0 : (double)ms / reps;
+    }
+    for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+    c->fields_valid = false;
+    return LBIB_OK;
+}
+
 extern "C" const char* lbib_last_error(const lbib_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 extern "C" void lbib_destroy(lbib_ctx* c) {

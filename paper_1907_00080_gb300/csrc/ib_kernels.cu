@@ -72,13 +72,14 @@ constexpr int kForceWarps = 10;
 constexpr int kForceThreads = 32 * kForceWarps;  // threads per force block
 constexpr int kMaxCand = 256;                     // repulsion candidate segments per block
 constexpr int kStageSeg = 48;                     // candidate segments staged in shared memory
+constexpr int kScreenIter = 8;                    // segment boxes per lane loaded ahead of the screen
 
 // One block per work unit (a chunk of up to kChunkV consecutive vertices of one
 // membrane).  The warps split the work of a vertex:
-//   phase 1  warps 0-1  bending geometry of the chunk plus one halo vertex each side
-//            warps 2-3  IB shape functions (MLS / Roma) and stencil origins
-//            warps 4-7  enclosed area of the whole membrane (fixed-order sum)
-//            warp  8    repulsion candidate segments (ascending order)
+//   phase 1  warps 0-2  bending geometry of the chunk plus one halo vertex each side
+//            warps 3-4  IB shape functions (MLS / Roma) and stencil origins
+//            warps 5-8  enclosed area of the whole membrane (fixed-order sum)
+//            warp  9    repulsion candidate segments (ascending order)
 //   phase 2  warps 0-1  stretching, bending, area and bond forces per vertex
 //            warps 2-9  repulsion over (candidate segment, vertex) pairs,
 //                       accumulated per vertex in fixed point (order-free)
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     __shared__ float4 s_cbox[kStageSeg];
     __shared__ E s_cax[kStageSeg], s_cay[kStageSeg];
     __shared__ C s_cox[kStageSeg * kSegV], s_coy[kStageSeg * kSegV];
-    __shared__ int s_cn[kStageSeg];
+    __shared__ int s_cn[kStageSeg], s_cv0[kStageSeg];
     const Rest<C>* rest = static_cast<const Rest<C>*>(a.rest);
 
     // ---- phase 0: positions of the chunk and two halo vertices on each side
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     __syncthreads();
 
     // ---- phase 1
-    if (wid < 2) {
+    if (wid < 3) {
         // theta - theta_0 from the rotation between the rest and the current
         // edge pair, atan2(c d0 - c0 d, d d0 + c c0): no cancellation of two
         // nearly equal angles
         const C kb = par<C>(a.mem_kb[m], float(a.mem_kb[m]));
-        for (int j = tid; j < kn + 2; j += 64) {
+        for (int j = tid; j < kn + 2; j += 96) {
             int k = k0 - 1 + j;
             k = k < 0 ? k + n : (k >= n ? k - n : k);
             const E xL = s_x[j], yL = s_y[j], xv = s_x[j + 1], yv = s_y[j + 1], xR = s_x[j + 2], yR = s_y[j + 2];
@@ -137,26 +138,28 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             const C eLx = etoc(esub(xv, xL)), eLy = etoc(esub(yv, yL));
             const C eRx = etoc(esub(xR, xv)), eRy = etoc(esub(yR, yv));
             const C lL = sqrt(eLx * eLx + eLy * eLy), lR = sqrt(eRx * eRx + eRy * eRy);
+            const C iL = C(1) / lL, iR = C(1) / lR;
             // outward vertex normal: normalised sum of the outward edge normals (CCW ring)
-            C nx_ = eLy / lL + eRy / lR;
-            C ny_ = -eLx / lL - eRx / lR;
-            const C nn = sqrt(nx_ * nx_ + ny_ * ny_);
-            nx_ /= nn;
-            ny_ /= nn;
+            C nx_ = eLy * iL + eRy * iR;
+            C ny_ = -eLx * iL - eRx * iR;
+            const C inn = C(1) / sqrt(nx_ * nx_ + ny_ * ny_);
+            nx_ *= inn;
+            ny_ *= inn;
             const C mb = kb * dth;
             s_mnx[j] = mb * nx_;
             s_mny[j] = mb * ny_;
-            s_sL[j] = lL / (lL + lR);
-            s_sR[j] = lR / (lL + lR);
+            const C isum = C(1) / (lL + lR);
+            s_sL[j] = lL * isum;
+            s_sR[j] = lR * isum;
             s_nx[j] = nx_;
             s_ny[j] = ny_;
         }
-    } else if (wid < 4) {
+    } else if (wid < 5) {
         // IB shape functions at X^n: nine nearest nodes, Roma weights, MLS
         // (basis 1, dx, dy) re-solved where wall rows drop out.  Node indices are
         // clamped so that a runaway position still stays in range; the advance
         // kernel flags non-finite positions.
-        const int j = tid - 64;
+        const int j = tid - 96;
         if (j < kn) {
             const E xv = s_x[j + 2], yv = s_y[j + 2];
             const C fi0 = fmin(fmax(C(efloor(eaddc(xv, C(0.5)))), C(-1.0e7)), C(1.0e7));
@@ -230,11 +233,11 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             s_i0[j] = i0w;
             s_j0[j] = j0;
         }
-    } else if (wid < 4 + kAreaWarps) {
+    } else if (wid < 5 + kAreaWarps) {
         // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
-        const E A = ring_area_group<C>(a, m, 4, red, 1);
-        if (tid == 32 * 4) s_ca = C(-a.mem_ka[m] * (1.0 - etod(A) / a.mem_A0[m]) * (1.0 / 3.0));
-    } else if (wid == 8) {
+        const E A = ring_area_group<C>(a, m, 5, red, 1);
+        if (tid == 32 * 5) s_ca = C(-a.mem_ka[m] * (1.0 - etod(A) / a.mem_A0[m]) * (1.0 / 3.0));
+    } else if (wid == 9) {
         // Eq. repFor screening, once per block: segments of other membranes whose
         // box comes within d_rep of this chunk's box (the union of its own
         // segments' boxes), appended in ascending segment order
@@ -263,11 +266,9 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
             const float cbx = o0.x + 0.5f * (lo_x + hi_x), cby = o0.y + 0.5f * (lo_y + hi_y);
             const float chx = 0.5f * (hi_x - lo_x), chy = 0.5f * (hi_y - lo_y);
             const float reach = a.f.d_rep + 2e-3f;
-            for (int base = 0; base < a.nseg; base += 32) {
-                const int sg = base + lane;
+            auto screen = [&](int sg, int mem, const float4& b) {
                 bool hit = false;
-                if (sg < a.nseg && a.seg_mem[sg] != m) {
-                    const float4 b = a.seg_box[sg];
+                if (sg < a.nseg && mem != m) {
                     const float dx = wrap_half(b.x - cbx, a.f.nx);
                     float dy = b.y - cby;
                     if (!a.walls) dy = wrap_half(dy, a.f.ny);
@@ -277,27 +278,34 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
                 const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
                 if (hit && pos < kMaxCand) s_cand[pos] = sg;
                 cnt += __popc(bal);
+            };
+            // batches of 32 kScreenIter segments: every box and owner of a batch in
+            // flight at once, then the ordered screen
+            for (int base = 0; base < a.nseg; base += 32 * kScreenIter) {
+                float4 bx[kScreenIter];
+                int bm[kScreenIter];
+#pragma unroll
+                for (int it = 0; it < kScreenIter; ++it) {
+                    const int sg = base + 32 * it + lane;
+                    bm[it] = m;
+                    if (sg < a.nseg) {
+                        bx[it] = a.seg_box[sg];
+                        bm[it] = a.seg_mem[sg];
+                    }
+                }
+#pragma unroll
+                for (int it = 0; it < kScreenIter; ++it)
+                    if (base + 32 * it < a.nseg) screen(base + 32 * it + lane, bm[it], bx[it]);
             }
             __syncwarp();
-            // stage the first kStageSeg candidates: box, vertex count, positions
+            // the first kStageSeg candidates: box, vertex count and first vertex
+            // (their positions are staged by the repulsion warps)
             const int nst = cnt < kStageSeg ? cnt : kStageSeg;
             for (int ci = lane; ci < nst; ci += 32) {
                 const int sg = s_cand[ci];
                 s_cbox[ci] = a.seg_box[sg];
                 s_cn[ci] = a.seg_n[sg];
-                load_pos<C>(a, a.seg_v0[sg], s_cax[ci], s_cay[ci]);
-            }
-            __syncwarp();
-            for (int e = lane; e < nst * kSegV; e += 32) {
-                const int ci = e / kSegV, g = e - ci * kSegV;
-                const int sg = s_cand[ci];
-                const int nb = a.seg_n[sg];
-                if (g < nb) {
-                    E xb, yb;
-                    load_pos<C>(a, a.seg_v0[sg] + g, xb, yb);
-                    s_cox[e] = etoc(esub(xb, s_cax[ci]));
-                    s_coy[e] = etoc(esub(yb, s_cay[ci]));
-                }
+                s_cv0[ci] = a.seg_v0[sg];
             }
         }
         if (lane == 0) s_ncand = cnt;
@@ -352,6 +360,24 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         // Eq. repFor against vertices of other membranes closer than d_rep, over
         // (candidate segment, vertex) pairs; the magnitudes of each vertex are
         // summed in fixed point (the direction is its own inward normal)
+        // stage the candidates' vertices as offsets from their first vertex (the
+        // anchor), then sync the repulsion warps (named barrier 2, warps 2-9)
+        const int nst = all_segs ? 0 : (ncand < kStageSeg ? ncand : kStageSeg);
+        for (int e = tid - 64; e < nst * kSegV; e += blockDim.x - 64) {
+            const int ci = e / kSegV, g = e - ci * kSegV;
+            if (g < s_cn[ci]) {
+                E xa, ya, xb, yb;
+                load_pos<C>(a, s_cv0[ci], xa, ya);
+                load_pos<C>(a, s_cv0[ci] + g, xb, yb);
+                s_cox[e] = etoc(esub(xb, xa));
+                s_coy[e] = etoc(esub(yb, ya));
+                if (g == 0) {
+                    s_cax[ci] = xa;
+                    s_cay[ci] = ya;
+                }
+            }
+        }
+        asm volatile("bar.sync 2, %0;" ::"r"(kForceThreads - 64) : "memory");
         const int nscan = all_segs ? a.nseg : ncand;
         const float reach = a.f.d_rep + 2e-3f;
         const C c_rep = C(1e-4 / (8.0 * 1.4142135623730951));

@@ -142,21 +142,34 @@ __device__ typename Ext<C>::E ring_area_group(const MarkerArgs& a, int m, int w0
     return emulc(s, C(0.5));
 }
 
-// block-wide sum in the compute type (all threads get it)
+// four block-wide sums in the compute type at once (every thread gets all four
+// in its arguments); each by a fixed shuffle tree per warp, then over the warps
 template <typename C>
-__device__ C block_sum_c(C v, C* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+__device__ void block_sum4_c(C& v0, C& v1, C& v2, C& v3, C* red) {
+    C v[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(kFull, v[q], o);
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[w] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        C t = threadIdx.x < nw ? red[threadIdx.x] : C(0);
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
-        if (threadIdx.x == 0) red[32] = t;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[33 * q + w] = v[q];
     }
     __syncthreads();
-    return red[32];
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            C t = threadIdx.x < nw ? red[33 * q + threadIdx.x] : C(0);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+            if (threadIdx.x == 0) red[33 * q + 32] = t;
+        }
+    }
+    __syncthreads();
+    v0 = red[32];
+    v1 = red[33 + 32];
+    v2 = red[66 + 32];
+    v3 = red[99 + 32];
 }
 
 // Last-block epilogue: every block counts itself in once it is done; the block

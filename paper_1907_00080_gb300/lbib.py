@@ -74,6 +74,7 @@ _SIGS = {
     "lbib_set_tiling": (_I, [_P, _I32, _I32]),
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
+    "lbib_profile_kernels": (_I, [_P, _I32, _DP]),
     "lbib_kernels_per_step": (_I32, [_P]),
     "lbib_storage_scale_exponent": (_I32, [_P]),
     "lbib_last_error": (ctypes.c_char_p, [_P]),
@@ -235,6 +236,13 @@ def lbib_profile_fused(ctx, reps):
     ms = np.zeros(1)
     _check(ctx, load().lbib_profile_fused(ctx, int(reps), _dptr(ms)))
     return float(ms[0])
+
+
+def lbib_profile_kernels(ctx, reps):
+    """Mean ms per launch of (forces, fused collide-stream, advance)."""
+    ms = np.zeros(3)
+    _check(ctx, load().lbib_profile_kernels(ctx, int(reps), _dptr(ms)))
+    return tuple(float(v) for v in ms)
 
 
 def lbib_kernels_per_step(ctx):
