@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
     return p.parse_args()
 
 
@@ -287,6 +288,10 @@ def lbib_main(args):
     if not args.no_probe and rank == 0:
         probe = hbm_probe(lbib, torch, stream, args.precision, pk, pk_kind)
 
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream)}
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -314,6 +319,7 @@ def lbib_main(args):
             "roofline": roofline,
             "roofline_kernels": kernels,
             "roofline_hbm_probe": probe,
+            "forms": forms,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": kps * T * args.steps,
@@ -382,6 +388,96 @@ def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
             "frac": gbs / pk["hbm_gbs"], "traffic": traffic, "nx": nx, "ny": ny, "tiling": [vec, ty],
             "ms_per_launch": ms, "algorithmic_bytes_per_launch": alg, "peak_kind": pk_kind + " (copy bandwidth, burst)",
             "mlups_fused_kernel": nx * ny / (ms * 1e-3) / 1e6}
+
+
+def precision_forms(lbib, torch, stream, steps=1000, timed=2000):
+    """Precision form: the fine capillary (2000 x 667, 4 red cells x 1700 + 3 rigid
+    carriers x 210 markers) with populations stored in FP32, FP16 and BF16
+    (shifted: d_i 2^k) against the FP64 run from the same inputs.  Errors after
+    `steps` time steps: velocity L2 and Linf relative to the FP64 field, marker
+    Linf in lattice units, bond-count difference; throughput over `timed`
+    further steps (CUDA events on the stream)."""
+    from paper_1907_00080_gb300 import inputs
+    res, ref = {}, None
+    for prec in ("f64", "f32", "f16", "bf16"):
+        wl = inputs.fine_capillary_2000x667(prec)
+        sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            sim.step(steps)
+            sim.sync()
+            _, ux, uy = sim.fields()
+            x = sim.markers()
+            nb = int((sim.bonds() >= 0).sum())
+            f = sim.populations()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(timed)
+            e1.record(stream)
+            sim.sync()
+            ms = e0.elapsed_time(e1)
+        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+        r = {"mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "tiling": list(sim.tiling),
+             "storage_scale_exponent": int(lbib.lbib_storage_scale_exponent(sim.ctx)),
+             "max_abs_deviation": float(np.max(np.abs(f - w))), "bonds": nb}
+        if ref is None:
+            ref = (ux, uy, x, nb)
+        else:
+            du = np.hypot(ux - ref[0], uy - ref[1])
+            um = np.hypot(ref[0], ref[1])
+            r.update(u_err_linf=float(du.max() / um.max()),
+                     u_err_l2=float(np.sqrt((du ** 2).sum() / (um ** 2).sum())),
+                     marker_err_linf_lu=float(np.max(np.abs(x - ref[2]))), bond_count_diff=nb - ref[3])
+        res[prec] = r
+        sim.close()
+    base = res["f32"]["mlups"]
+    for prec in ("f16", "bf16"):
+        res[prec]["speedup_vs_f32"] = res[prec]["mlups"] / base
+    return {"workload": "fine capillary 2000x667 (dx = 15 nm), 4 RBC x 1700 + 3 rigid carriers x 210 markers",
+            "error_after_steps": steps, "timed_steps": timed, "results": res}
+
+
+def ensemble_form(lbib, torch, stream, n=64, steps=400):
+    """Ensemble form: n coarse capillaries of lengths 32-64 um (NX 512-1008,
+    NY 160; red cells at the 640 x 160 density, 4 carriers at random release
+    heights, Ca and sigma swept), advanced together (one graph launch per 16
+    steps) against the same instances run one after another.  MLUPS = all
+    instances' nodes x steps / time (CUDA events on the stream)."""
+    from paper_1907_00080_gb300 import inputs
+    wls = inputs.capillary_ensemble(n, seed=0, precision="f32")
+    nodes = sum(wl.nx * wl.ny for wl in wls)
+
+    def timed(run):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    with torch.cuda.stream(stream):
+        ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream)
+        ens.step(32)
+        ens.sync()
+        t_ens = timed(lambda: ens.step(steps))
+        ens.sync()
+        ens.close()
+        sims = [lbib.Simulation(wl, cuda_stream=stream.cuda_stream) for wl in wls]
+        for s in sims:
+            s.step(32)
+        torch.cuda.synchronize()
+
+        def sequential():
+            for s in sims:
+                s.step(steps)
+
+        t_seq = timed(sequential)
+        for s in sims:
+            s.close()
+    return {"workload": "%d coarse capillaries, NX %d-%d x NY 160, %d nodes, %d markers in all" % (
+                n, min(wl.nx for wl in wls), max(wl.nx for wl in wls), nodes, sum(wl.n_vertices for wl in wls)),
+            "steps": steps, "ensemble_mlups": nodes * steps / t_ens / 1e6,
+            "sequential_mlups": nodes * steps / t_seq / 1e6, "speedup_vs_sequential": t_seq / t_ens,
+            "ensemble_ms_per_step": 1e3 * t_ens / steps, "sequential_ms_per_step": 1e3 * t_seq / steps}
 
 
 def end_to_end(lbib, torch, wl, tiling, stream, T, steps):

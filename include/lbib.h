@@ -175,6 +175,36 @@ lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t* ligand_ids, int32_t* recepto
  * NULL, the enclosed area of each membrane (Eq. areaFor's Green area). */
 lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
 
+/* ---------------------------------------------------------------- ensembles
+ * A batch of independent simulations (e.g. a sweep over release positions,
+ * capillary numbers and bond strengths on channels of different lengths)
+ * advanced together: one CUDA graph per chunk of 16 steps holds every
+ * member's captured time step as an independent child graph, so the members'
+ * kernels run side by side on the GPU instead of one simulation at a time.
+ * The paper runs its cases one by one; this is a throughput form only: every
+ * member computes exactly what it computes alone (bitwise).
+ *
+ * lbib_ensemble_create: members are n distinct contexts on the current device
+ *   (their set-up calls done; they are finalised here).  The ensemble takes
+ *   ownership: lbib_ensemble_destroy destroys them; do not destroy them
+ *   yourself.  cuda_stream may be NULL (the ensemble creates its own).
+ *   Errors: LBIB_E_INVALID (NULL, duplicates, other device, poisoned member),
+ *   or a member's finalisation error.
+ * lbib_ensemble_step: enqueue n steps of every member on the ensemble's
+ *   stream (asynchronous).  Do not step the members individually afterwards.
+ * lbib_ensemble_sync: wait for the ensemble's stream and check every member's
+ *   device status; call it before reading a member (lbib_ensemble_member
+ *   returns the member's context for the lbib_read_* calls).
+ */
+typedef struct lbib_ensemble lbib_ensemble;
+lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n, void* cuda_stream, lbib_ensemble** out);
+lbib_status lbib_ensemble_step(lbib_ensemble* ens, int64_t n);
+lbib_status lbib_ensemble_sync(lbib_ensemble* ens);
+int32_t lbib_ensemble_size(const lbib_ensemble* ens);
+lbib_ctx* lbib_ensemble_member(lbib_ensemble* ens, int32_t i);
+const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
+void lbib_ensemble_destroy(lbib_ensemble* ens);
+
 /* Allocation-free FP64 mass of a population buffer the caller owns.  The
  * paper has no counterpart: this is a library service for callers that must not
  * allocate device memory at the time of the call, e.g. a monitor running between

@@ -1,7 +1,8 @@
 // C ABI of the lbib library: context set-up, device arena, captured step
-// graphs and read-backs.  Every step of the time integration runs in the CUDA
-// kernels of lb_kernels.cu, ib_kernels.cu and bond_kernels.cu; this file only
-// arranges memory, validates arguments and enqueues work.
+// graphs, ensembles and read-backs.  Every step of the time integration runs
+// in the CUDA kernels of lb_kernels.cu / lb_stream_kernel.cu, ib_kernels.cu
+// and advance_kernel.cu; this file only arranges memory, validates arguments
+// and enqueues work.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -631,7 +632,7 @@ static lbib_status build_graphs(lbib_ctx* c) {
                 return cuda_fail(c, le != cudaSuccess ? le : e, "capture step");
             }
             e = cudaGraphInstantiate(&c->graph[start][kind], g, 0);
-            cudaGraphDestroy(g);
+            c->graph_tmpl[start][kind] = g;  // an ensemble embeds it as a child graph
             if (e != cudaSuccess) {
                 cudaStreamDestroy(cap);
                 return cuda_fail(c, e, "instantiate step graph");
@@ -941,8 +942,10 @@ extern "C" void lbib_destroy(lbib_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int s = 0; s < 2; ++s)
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 2; ++k) {
             if (c->graph[s][k]) cudaGraphExecDestroy(c->graph[s][k]);
+            if (c->graph_tmpl[s][k]) cudaGraphDestroy(c->graph_tmpl[s][k]);
+        }
     for (int b = 0; b < 2; ++b)
         if (c->f[b]) cudaFree(c->f[b]);
     if (c->ux) cudaFree(c->ux);
@@ -957,4 +960,152 @@ extern "C" void lbib_destroy(lbib_ctx* c) {
         if (c->G[p]) cudaFree(c->G[p]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+// ------------------------------------------------------------------ ensembles
+// Independent contexts advanced together: one graph per chunk of steps holds
+// every member's captured step graph as a child node with no edges between
+// them, so the members' kernels run side by side on the GPU.
+struct lbib_ensemble {
+    std::vector<lbib_ctx*> m;
+    cudaStream_t stream = nullptr;
+    // [flip][kind]: members at their parity at creation (flip 0) or the other
+    // one (flip 1); kind 0 one step, kind 1 a chunk of kChunk steps
+    cudaGraphExec_t g[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int flip = 0;
+    std::vector<int> cur0;
+    bool own_stream = false;
+    std::string err;
+};
+
+namespace {
+lbib_status ens_fail(lbib_ensemble* e, lbib_status st, const std::string& msg) {
+    if (e) e->err = msg;
+    return st;
+}
+}  // namespace
+
+#define ECK(call)                                                                     \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) return ens_fail(e, LBIB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static lbib_status ensemble_build(lbib_ensemble* e) {
+    for (int flip = 0; flip < 2; ++flip) {
+        for (int kind = 0; kind < 2; ++kind) {
+            cudaGraph_t g;
+            ECK(cudaGraphCreate(&g, 0));
+            for (size_t i = 0; i < e->m.size(); ++i) {
+                lbib_ctx* c = e->m[i];
+                cudaGraphNode_t node;
+                const cudaError_t r = cudaGraphAddChildGraphNode(&node, g, nullptr, 0,
+                                                                 c->graph_tmpl[e->cur0[i] ^ flip][kind]);
+                if (r != cudaSuccess) {
+                    cudaGraphDestroy(g);
+                    return ens_fail(e, LBIB_E_CUDA, std::string("add member graph: ") + cudaGetErrorString(r));
+                }
+            }
+            const cudaError_t r = cudaGraphInstantiate(&e->g[flip][kind], g, 0);
+            cudaGraphDestroy(g);
+            if (r != cudaSuccess) return ens_fail(e, LBIB_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(r));
+        }
+    }
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n, void* cuda_stream,
+                                            lbib_ensemble** out) {
+    if (!members || n < 1 || !out) return LBIB_E_INVALID;
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return LBIB_E_INVALID;
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return LBIB_E_INVALID;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBIB_E_CUDA;
+    for (int i = 0; i < n; ++i) {
+        lbib_ctx* c = members[i];
+        if (c->device != dev || c->poisoned) return LBIB_E_INVALID;
+        lbib_status st = finalize(c);
+        if (st == LBIB_OK) st = build_graphs(c);
+        if (st != LBIB_OK) return st;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBIB_E_CUDA;
+    }
+    lbib_ensemble* e = new lbib_ensemble();
+    e->m.assign(members, members + n);
+    for (int i = 0; i < n; ++i) e->cur0.push_back(members[i]->cur);
+    if (cuda_stream) {
+        e->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete e;
+        return LBIB_E_CUDA;
+    } else {
+        e->own_stream = true;
+    }
+    e->err.clear();
+    const lbib_status st = ensemble_build(e);
+    if (st != LBIB_OK) {
+        for (int f = 0; f < 2; ++f)
+            for (int k = 0; k < 2; ++k)
+                if (e->g[f][k]) cudaGraphExecDestroy(e->g[f][k]);
+        if (e->own_stream) cudaStreamDestroy(e->stream);
+        delete e;
+        return st;
+    }
+    *out = e;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_ensemble_step(lbib_ensemble* e, int64_t n) {
+    if (!e || n < 0) return LBIB_E_INVALID;
+    for (lbib_ctx* c : e->m)
+        if (c->poisoned) return ens_fail(e, LBIB_E_STATE, "a member is poisoned by an earlier device-side failure");
+    int64_t left = n;
+    while (left >= kChunk) {
+        ECK(cudaGraphLaunch(e->g[e->flip][1], e->stream));
+        left -= kChunk;  // even: every member keeps its buffer roles
+    }
+    while (left > 0) {
+        ECK(cudaGraphLaunch(e->g[e->flip][0], e->stream));
+        e->flip ^= 1;
+        --left;
+    }
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        lbib_ctx* c = e->m[i];
+        c->cur = e->cur0[i] ^ e->flip;
+        c->steps += n;
+        if (n > 0) c->fields_valid = true;
+    }
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_ensemble_sync(lbib_ensemble* e) {
+    if (!e) return LBIB_E_INVALID;
+    ECK(cudaStreamSynchronize(e->stream));
+    for (lbib_ctx* c : e->m) {
+        const lbib_status st = lbib_sync(c);
+        if (st != LBIB_OK) return ens_fail(e, st, c->err);
+    }
+    return LBIB_OK;
+}
+
+extern "C" int32_t lbib_ensemble_size(const lbib_ensemble* e) { return e ? (int32_t)e->m.size() : -1; }
+
+extern "C" lbib_ctx* lbib_ensemble_member(lbib_ensemble* e, int32_t i) {
+    if (!e || i < 0 || i >= (int32_t)e->m.size()) return nullptr;
+    return e->m[i];
+}
+
+extern "C" const char* lbib_ensemble_last_error(const lbib_ensemble* e) { return e ? e->err.c_str() : "null ensemble"; }
+
+extern "C" void lbib_ensemble_destroy(lbib_ensemble* e) {
+    if (!e) return;
+    cudaStreamSynchronize(e->stream);
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < 2; ++k)
+            if (e->g[f][k]) cudaGraphExecDestroy(e->g[f][k]);
+    for (lbib_ctx* c : e->m) lbib_destroy(c);
+    if (e->own_stream) cudaStreamDestroy(e->stream);
+    delete e;
 }

@@ -279,6 +279,7 @@ struct lbib_ctx {
 
     // captured step graphs: [start buffer][0: one step, 1: chunk of kChunk steps]
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraph_t graph_tmpl[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // kept for ensembles
     bool graphs_ready = false;
 
     std::string err;

@@ -138,23 +138,19 @@ def _point_in_poly(px, py, poly, nx):
     # ray casting, with x taken at the periodic image closest to the polygon centre
     cx = poly[:, 0].mean()
     px = px - nx * math.floor((px - cx) / nx + 0.5)
-    inside = False
-    n = len(poly)
-    for i in range(n):
-        x1, y1 = poly[i]
-        x2, y2 = poly[(i + 1) % n]
-        if (y1 > py) != (y2 > py):
-            xin = x1 + (py - y1) * (x2 - x1) / (y2 - y1)
-            if px < xin:
-                inside = not inside
-    return inside
+    x1, y1 = poly[:, 0], poly[:, 1]
+    x2, y2 = np.roll(x1, -1), np.roll(y1, -1)
+    cross = (y1 > py) != (y2 > py)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        xin = x1 + (py - y1) * (x2 - x1) / (y2 - y1)
+    return bool(np.count_nonzero(cross & (px < xin)) % 2)
 
 
 def place_membranes(shapes, nx, ny, rng, gap=2.0, wall_gap=2.0, y_range=None, max_tries=20000):
     """Random non-overlapping placement (uniform centre, uniform orientation).
     Vertices keep >= gap from every other membrane (periodic x) and >= wall_gap
     from the walls (at y = -1/2 and ny - 1/2)."""
-    placed = []
+    placed, centres, radii = [], [], []
     for k, shape in enumerate(shapes):
         ok = False
         for _ in range(max_tries):
@@ -170,20 +166,33 @@ def place_membranes(shapes, nx, ny, rng, gap=2.0, wall_gap=2.0, y_range=None, ma
             cx = rng.uniform(0.0, nx)
             cy = rng.uniform(lo, hi)
             cand = xy + np.array([cx, cy])
+            c_n = cand.mean(axis=0)
+            r_n = np.max(np.hypot(*(cand - c_n).T))
             bad = False
-            for other in placed:
-                d = cand[:, None, :] - other[None, :, :]
-                d[..., 0] -= nx * np.floor(d[..., 0] / nx + 0.5)
-                if np.min(np.hypot(d[..., 0], d[..., 1])) < gap:
-                    bad = True
-                    break
-                c_o = other.mean(axis=0)
-                c_n = cand.mean(axis=0)
+            for other, c_o, r_o in zip(placed, centres, radii):
+                # bounding circles further apart than the gap: no contact possible
+                dxc = c_n[0] - c_o[0]
+                dxc -= nx * math.floor(dxc / nx + 0.5)
+                if math.hypot(dxc, c_n[1] - c_o[1]) > r_n + r_o + gap:
+                    continue
+                # only vertices of `other` within r_n + gap of the candidate's
+                # centre can be closer than gap to one of its vertices
+                ox = other[:, 0] - c_n[0]
+                ox -= nx * np.floor(ox / nx + 0.5)
+                near = (np.abs(ox) <= r_n + gap) & (np.abs(other[:, 1] - c_n[1]) <= r_n + gap)
+                if np.any(near):
+                    d = cand[:, None, :] - other[near][None, :, :]
+                    d[..., 0] -= nx * np.floor(d[..., 0] / nx + 0.5)
+                    if np.min(np.hypot(d[..., 0], d[..., 1])) < gap:
+                        bad = True
+                        break
                 if _point_in_poly(c_n[0], c_n[1], other, nx) or _point_in_poly(c_o[0], c_o[1], cand, nx):
                     bad = True
                     break
             if not bad:
                 placed.append(cand)
+                centres.append(c_n)
+                radii.append(r_n)
                 ok = True
                 break
         if not ok:
@@ -264,6 +273,45 @@ def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carrie
 
 def coarse_capillary_640x160(precision="f32", seed=0, steps=200000) -> Workload:
     return capillary(precision=precision, seed=seed, steps=steps, name="capillary_640x160")
+
+
+def fine_capillary_2000x667(precision="f32", sigma=1.0, carriers="rigid", seed=0, steps=20000,
+                            bonds="default") -> Workload:
+    """Fine mesh: 10 x 30 um at dx = 15 nm is a 667 x 2000 lattice; 4 red cells
+    (8 um major axis -> alpha = 266.7 lu, 1700 markers each, about 19 % 2-D
+    haematocrit), 3 carriers of 1 um diameter (radius 33.3 lu, 210 markers,
+    105 ligands), all rigid (Ca = 0) or all soft (Ca = 1e-2), receptors on both
+    walls, sigma in {0.5, 1, 2}."""
+    nx, ny = 2000, 667
+    ca = 0.0 if carriers == "rigid" else 1e-2
+    return capillary(nx=nx, ny=ny, n_rbc=4, rbc_alpha=266.7, rbc_markers=1700, n_carriers=3,
+                     carrier_radius=33.3, carrier_markers=210, ca_carrier=(ca,), sigma=sigma,
+                     seed=seed, precision=precision, steps=steps, bonds=bonds,
+                     name="fine_capillary_2000x667_%s_sigma%g" % (carriers, sigma))
+
+
+def capillary_ensemble(n=64, seed=0, precision="f32", l_min_um=32.0, l_max_um=64.0, dx_um=0.0625,
+                       ny=160) -> List[Workload]:
+    """Batched ensemble of coarse capillaries: instance i has length
+    L_i ~ U[32, 64] um (NX_i = round(L_i / dx)), NY = 160, round(8 L_i / 40)
+    red cells (the 640 x 160 density), 4 carriers released at heights drawn
+    uniformly across the admissible width, Ca_i = (0, 1e-2)[i mod 2] (rigid or
+    soft carriers), sigma_i = (0.5, 1, 2)[(i div 2) mod 3], seed_i = seed + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        L = rng.uniform(l_min_um, l_max_um)
+        nx = int(round(L / dx_um))
+        nx -= nx % 8  # whole 16-byte rows in every storage form
+        n_rbc = int(round(8 * L / 40.0))
+        r = 8.0
+        release = list(rng.uniform(-0.5 + 2.0 + r, ny - 0.5 - 2.0 - r, size=4))
+        ca = (0.0, 1e-2)[i % 2]
+        sigma = (0.5, 1.0, 2.0)[(i // 2) % 3]
+        out.append(capillary(nx=nx, ny=ny, n_rbc=n_rbc, ca_carrier=(ca,), sigma=sigma, seed=seed + i,
+                             precision=precision, release_y=release,
+                             name="capillary_%dx%d_i%d" % (nx, ny, i)))
+    return out
 
 
 def random_populations(nx, ny, base, seed=0, amp=1e-2):

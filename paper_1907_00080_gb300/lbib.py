@@ -71,6 +71,13 @@ _SIGS = {
     "lbib_read_bonds": (_I, [_P, _I32P, _I32P, _I32, _I32P]),
     "lbib_diagnostics": (_I, [_P, _DP, _DP]),
     "lbib_population_mass_noalloc": (_I, [_P, _I64, _P, _P]),
+    "lbib_ensemble_create": (_I, [ctypes.POINTER(_P), _I32, _P, ctypes.POINTER(_P)]),
+    "lbib_ensemble_step": (_I, [_P, _I64]),
+    "lbib_ensemble_sync": (_I, [_P]),
+    "lbib_ensemble_size": (_I32, [_P]),
+    "lbib_ensemble_member": (_P, [_P, _I32]),
+    "lbib_ensemble_last_error": (ctypes.c_char_p, [_P]),
+    "lbib_ensemble_destroy": (None, [_P]),
     "lbib_set_tiling": (_I, [_P, _I32, _I32]),
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
@@ -262,6 +269,49 @@ def lbib_destroy(ctx):
         load().lbib_destroy(ctx)
 
 
+def _echeck(ens, st):
+    if st != LBIB_OK:
+        msg = load().lbib_ensemble_last_error(ens).decode() if ens else ""
+        raise LbibError(st, msg)
+
+
+def lbib_ensemble_create(ctxs, cuda_stream=None):
+    arr = (_P * max(len(ctxs), 1))(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    out = _P()
+    st = load().lbib_ensemble_create(arr, len(ctxs), None if cuda_stream is None else _P(int(cuda_stream)),
+                                     ctypes.byref(out))
+    _echeck(None, st)
+    return out
+
+
+def lbib_ensemble_step(ens, n):
+    _echeck(ens, load().lbib_ensemble_step(ens, int(n)))
+
+
+def lbib_ensemble_sync(ens):
+    _echeck(ens, load().lbib_ensemble_sync(ens))
+
+
+def lbib_ensemble_size(ens):
+    return load().lbib_ensemble_size(ens)
+
+
+def lbib_ensemble_member(ens, i):
+    p = load().lbib_ensemble_member(ens, int(i))
+    if not p:
+        raise LbibError(LBIB_E_INVALID, "no member %d" % i)
+    return _P(p)
+
+
+def lbib_ensemble_last_error(ens):
+    return load().lbib_ensemble_last_error(ens).decode()
+
+
+def lbib_ensemble_destroy(ens):
+    if ens:
+        load().lbib_ensemble_destroy(ens)
+
+
 # ------------------------------------------------------------------ convenience
 class Simulation:
     """Owns one lbib context built from an ``inputs.Workload`` (marshalling only)."""
@@ -289,9 +339,9 @@ class Simulation:
             lbib_set_tiling(self.ctx, *tiling)
 
     def close(self):
-        if self.ctx:
+        if self.ctx and not getattr(self, "owned_by_ensemble", False):
             lbib_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):
         try:
@@ -354,3 +404,33 @@ class Simulation:
     @property
     def kernels_per_step(self):
         return lbib_kernels_per_step(self.ctx)
+
+
+class Ensemble:
+    """Several workloads advanced together (lbib_ensemble_*); members keep the
+    Simulation read-back methods.  Marshalling only."""
+
+    def __init__(self, workloads, precision=None, cuda_stream=None):
+        self.members = [Simulation(wl, precision=precision) for wl in workloads]
+        self.ens = lbib_ensemble_create([m.ctx for m in self.members], cuda_stream)
+        for m in self.members:
+            m.owned_by_ensemble = True
+
+    def step(self, n=1):
+        lbib_ensemble_step(self.ens, n)
+
+    def sync(self):
+        lbib_ensemble_sync(self.ens)
+
+    def close(self):
+        if self.ens:
+            lbib_ensemble_destroy(self.ens)
+            self.ens = None
+            for m in self.members:
+                m.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
