@@ -290,7 +290,8 @@ def lbib_main(args):
 
     forms = None
     if not args.no_forms and rank == 0:
-        forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream)}
+        forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream),
+                 "differentiation": differentiation_form(lbib, torch)}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -478,6 +479,29 @@ def ensemble_form(lbib, torch, stream, n=64, steps=400):
             "steps": steps, "ensemble_mlups": nodes * steps / t_ens / 1e6,
             "sequential_mlups": nodes * steps / t_seq / 1e6, "speedup_vs_sequential": t_seq / t_ens,
             "ensemble_ms_per_step": 1e3 * t_ens / steps, "sequential_ms_per_step": 1e3 * t_seq / steps}
+
+
+def differentiation_form(lbib, torch, steps=1000):
+    """Differentiation form: the 320 x 160 sensitivity case (2 red cells, a soft
+    carrier released 1 lu above the wall), FP64: dJ/dp of the carrier's final
+    height J1 and bond energy J2 with respect to (k_s, k_b, sigma, release
+    height) by four forward-mode tangent runs, timed against the plain FP64
+    solver over the same steps (host wall clock around synchronised calls)."""
+    from paper_1907_00080_gb300 import sensitivity
+    p0 = sensitivity.default_params()
+    sensitivity.run(p0, 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, _ = sensitivity.run(p0, steps)
+    t_primal = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J2, jac, bonds = sensitivity.jacobian(p0, steps)
+    t_jac = time.perf_counter() - t0
+    return {"workload": "320x160, 2 RBC x 200 + 1 soft carrier x 50 markers, FP64", "steps": steps,
+            "params": list(sensitivity.PARAMS), "J": [float(v) for v in J],
+            "dJ_dp": [[float(v) for v in row] for row in jac], "bonds_at_end": int((bonds >= 0).sum()),
+            "primal_ms_per_step": 1e3 * t_primal / steps, "jacobian_ms_per_step": 1e3 * t_jac / steps,
+            "tangent_cost_per_direction_vs_primal": t_jac / 4 / t_primal}
 
 
 def end_to_end(lbib, torch, wl, tiling, stream, T, steps):

@@ -205,6 +205,39 @@ lbib_ctx* lbib_ensemble_member(lbib_ensemble* ens, int32_t i);
 const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
 void lbib_ensemble_destroy(lbib_ensemble* ens);
 
+/* ---------------------------------------------------------------- tangent
+ * Forward-mode (tangent-linear) derivative of an FP64 trajectory.  Along one
+ * direction of the parameters -- dk_s and dk_b per membrane, dsigma (the bond
+ * stiffness sigma of Eq. adhFor in lattice units) and the derivative of the
+ * current marker positions (e.g. a release height) -- the derivative of the
+ * marker positions is carried through every step with the step itself:
+ * forces (Eqs. strainFor, bendFor, areaFor, repFor, adhFor), MLS/Roma shape
+ * functions and spreading, the Guo-forced BGK collide-stream, interpolation
+ * and BDF2.  Bond formation and rupture are events: the bonds of every step are
+ * the primal run's, held fixed (the derivative of the path with that bond
+ * history).  The paper has no derivative; this serves sensitivity studies
+ * (adhesion and margination against k_s, k_b, sigma, release position).
+ *
+ * lbib_tangent_create: ctx must be LBIB_F64 without rigid-projected
+ *   membranes (LBIB_E_INVALID otherwise); the tangent borrows the context
+ *   (destroy the tangent first).  Allocates its own device buffers.
+ * lbib_tangent_seed: set the direction: dks, dkb (nmem doubles each, host, or
+ *   NULL = 0), dsigma, dxy / dxy_prev (2*nv doubles, host, the derivatives of
+ *   X^n and X^{n-1}; NULL = 0, dxy_prev NULL = dxy); clears the derivative of
+ *   the populations.
+ * lbib_tangent_step: advance the context n steps together with the tangent
+ *   (instead of lbib_step).
+ * lbib_tangent_read: derivative of X^n (and X^{n-1}) into host arrays of
+ *   2*nv doubles (either may be NULL); synchronises.
+ */
+typedef struct lbib_tangent lbib_tangent;
+lbib_status lbib_tangent_create(lbib_ctx* ctx, lbib_tangent** out);
+lbib_status lbib_tangent_seed(lbib_tangent* t, const double* dks, const double* dkb, double dsigma,
+                              const double* dxy, const double* dxy_prev);
+lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n);
+lbib_status lbib_tangent_read(lbib_tangent* t, double* dxy, double* dxy_prev);
+void lbib_tangent_destroy(lbib_tangent* t);
+
 /* Allocation-free FP64 mass of a population buffer the caller owns.  The
  * paper has no counterpart: this is a library service for callers that must not
  * allocate device memory at the time of the call, e.g. a monitor running between

@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "lbib_internal.cuh"
+#include "tangent.cuh"
 
 using namespace lbib;
 
@@ -1108,4 +1109,140 @@ extern "C" void lbib_ensemble_destroy(lbib_ensemble* e) {
     for (lbib_ctx* c : e->m) lbib_destroy(c);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;
+}
+
+// ------------------------------------------------------------------ tangent
+// Forward-mode derivative of an FP64 context's trajectory along one direction
+// of (k_s, k_b per membrane, sigma, initial marker positions); the bond events
+// of the primal run are taken as given.
+struct lbib_tangent {
+    lbib_ctx* c = nullptr;  // primal (not owned)
+    double* fd[2] = {nullptr, nullptr};
+    double* dX[3] = {nullptr, nullptr, nullptr};  // roles rotate: X^{n-1}, X^n, X^{n+1}
+    int ip = 0, ix = 1, in = 2, cf = 0;
+    double *Gv = nullptr, *Gd = nullptr, *u = nullptr, *ud = nullptr, *Wv = nullptr, *Wd = nullptr;
+    double *Fv = nullptr, *Fd = nullptr, *A = nullptr, *Ad = nullptr, *dks = nullptr, *dkb = nullptr;
+    int* st = nullptr;
+    double dsigma = 0.0;
+    std::vector<void*> allocs;
+};
+
+extern "C" void lbib_tangent_destroy(lbib_tangent* t) {
+    if (!t) return;
+    if (t->c && t->c->stream) cudaStreamSynchronize(t->c->stream);
+    for (void* p : t->allocs) cudaFree(p);
+    delete t;
+}
+
+extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
+    if (!c || !out) return LBIB_E_INVALID;
+    if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the tangent needs an FP64 context");
+    for (int k : c->h_mem_kind)
+        if (k == LBIB_MEMBRANE_RIGID_PROJECTED)
+            return fail(c, LBIB_E_INVALID, "the tangent does not support rigid-projected membranes");
+    lbib_status st = finalize(c);
+    if (st == LBIB_OK) st = build_graphs(c);
+    if (st != LBIB_OK) return st;
+    lbib_tangent* t = new lbib_tangent();
+    t->c = c;
+    const size_t N = (size_t)c->nx * c->ny, nv = std::max(c->nv, 1), nm = std::max(c->nmem, 1);
+    auto get = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        t->allocs.push_back(p);
+        return p;
+    };
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) ok = ok && (t->fd[b] = (double*)get(9 * N * 8));
+    for (int b = 0; b < 3; ++b) ok = ok && (t->dX[b] = (double*)get(2 * nv * 8));
+    ok = ok && (t->Gv = (double*)get(2 * N * 8)) && (t->Gd = (double*)get(2 * N * 8));
+    ok = ok && (t->u = (double*)get(2 * N * 8)) && (t->ud = (double*)get(2 * N * 8));
+    ok = ok && (t->Wv = (double*)get(9 * nv * 8)) && (t->Wd = (double*)get(9 * nv * 8));
+    ok = ok && (t->Fv = (double*)get(2 * nv * 8)) && (t->Fd = (double*)get(2 * nv * 8));
+    ok = ok && (t->A = (double*)get(nm * 8)) && (t->Ad = (double*)get(nm * 8));
+    ok = ok && (t->dks = (double*)get(nm * 8)) && (t->dkb = (double*)get(nm * 8));
+    ok = ok && (t->st = (int*)get(2 * nv * 4));
+    if (!ok) {
+        lbib_tangent_destroy(t);
+        return fail(c, LBIB_E_OOM, "tangent buffers");
+    }
+    cudaMemsetAsync(t->fd[0], 0, 9 * N * 8, c->stream);
+    cudaMemsetAsync(t->fd[1], 0, 9 * N * 8, c->stream);
+    for (int b = 0; b < 3; ++b) cudaMemsetAsync(t->dX[b], 0, 2 * nv * 8, c->stream);
+    cudaMemsetAsync(t->dks, 0, nm * 8, c->stream);
+    cudaMemsetAsync(t->dkb, 0, nm * 8, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        lbib_tangent_destroy(t);
+        return fail(c, LBIB_E_CUDA, "tangent set-up");
+    }
+    *out = t;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_tangent_seed(lbib_tangent* t, const double* dks, const double* dkb, double dsigma,
+                                         const double* dxy, const double* dxy_prev) {
+    if (!t) return LBIB_E_INVALID;
+    lbib_ctx* c = t->c;
+    const size_t N = (size_t)c->nx * c->ny;
+    const size_t nv = (size_t)c->nv, nm = (size_t)c->nmem;
+    CK(cudaMemsetAsync(t->fd[t->cf], 0, 9 * N * 8, c->stream));
+    if (nm) {
+        if (dks) CK(cudaMemcpyAsync(t->dks, dks, nm * 8, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(t->dks, 0, nm * 8, c->stream));
+        if (dkb) CK(cudaMemcpyAsync(t->dkb, dkb, nm * 8, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(t->dkb, 0, nm * 8, c->stream));
+    }
+    if (nv) {
+        if (dxy) CK(cudaMemcpyAsync(t->dX[t->ix], dxy, nv * 16, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(t->dX[t->ix], 0, nv * 16, c->stream));
+        const double* pv = dxy_prev ? dxy_prev : dxy;
+        if (pv) CK(cudaMemcpyAsync(t->dX[t->ip], pv, nv * 16, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(t->dX[t->ip], 0, nv * 16, c->stream));
+    }
+    t->dsigma = dsigma;
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n) {
+    if (!t || n < 0) return LBIB_E_INVALID;
+    lbib_ctx* c = t->c;
+    if (c->poisoned) return fail(c, LBIB_E_STATE, "context poisoned by an earlier device-side failure");
+    for (int64_t k = 0; k < n; ++k) {
+        TangentArgs a{};
+        a.m = c->ma;
+        a.f = static_cast<const double*>(c->f[c->cur]);
+        a.fd_src = t->fd[t->cf];
+        a.fd_dst = t->fd[1 - t->cf];
+        a.dX = t->dX[t->ix];
+        a.dXp = t->dX[t->ip];
+        a.dXn = t->dX[t->in];
+        a.Gv = t->Gv; a.Gd = t->Gd; a.u = t->u; a.ud = t->ud; a.Wv = t->Wv; a.Wd = t->Wd;
+        a.st = t->st; a.Fv = t->Fv; a.Fd = t->Fd; a.A = t->A; a.Ad = t->Ad;
+        a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma;
+        a.omega = 1.0 / c->tau; a.gx = c->gx; a.gy = c->gy;
+        a.step = c->steps;
+        CK(launch_tangent_step(a, c->stream));
+        // the primal step (its captured one-step graph) follows on the same stream
+        CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
+        c->cur = 1 - c->cur;
+        c->steps += 1;
+        c->fields_valid = true;
+        t->cf = 1 - t->cf;
+        const int op = t->ip;
+        t->ip = t->ix;
+        t->ix = t->in;
+        t->in = op;
+    }
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_tangent_read(lbib_tangent* t, double* dxy, double* dxy_prev) {
+    if (!t) return LBIB_E_INVALID;
+    lbib_ctx* c = t->c;
+    const size_t nv = (size_t)c->nv;
+    if (dxy && nv) CK(cudaMemcpyAsync(dxy, t->dX[t->ix], nv * 16, cudaMemcpyDeviceToHost, c->stream));
+    if (dxy_prev && nv) CK(cudaMemcpyAsync(dxy_prev, t->dX[t->ip], nv * 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return lbib_sync(c);
 }

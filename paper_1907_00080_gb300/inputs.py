@@ -290,6 +290,50 @@ def fine_capillary_2000x667(precision="f32", sigma=1.0, carriers="rigid", seed=0
                      name="fine_capillary_2000x667_%s_sigma%g" % (carriers, sigma))
 
 
+def adjoint_capillary_320x160(ks=None, kb=None, sigma_lu=None, release_y=8.5, seed=0, precision="f64",
+                              bonds="default") -> Workload:
+    """Sensitivity case: 320 x 160 channel (Re = 1e-2), 2 red cells (200
+    markers) and one soft carrier of radius 8 lu (50 markers, 25 ligands)
+    whose centre starts at height release_y (8.5: its lowest vertex 1.0 lu
+    above the lower wall at y = -1/2); receptors on both walls.  ks, kb and
+    sigma_lu (lattice units) replace the carrier's stiffnesses and the bond
+    stiffness when given.  The carrier is the last membrane."""
+    nx, ny = 320, 160
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u_max = u_max_for_re(1e-2, ny)
+    ks_rbc = ks_for_ca(1e-2, u_max)
+    rbcs = place_membranes([rbc_contour(64.0, 200)] * 2, nx, ny, rng)
+    mems = [Membrane(xy=xy, ks=ks_rbc, kb=0.0, ka=1.0, kind=0) for xy in rbcs]
+    # the carrier at height release_y (its lowest vertex exactly R below the
+    # centre), at a random x at least 2 lu from the red cells
+    for _ in range(20000):
+        xy = circle(rng.uniform(0.0, nx), release_y, 8.0, 50)
+        ok = True
+        for other in rbcs:
+            d = xy[:, None, :] - other[None, :, :]
+            d[..., 0] -= nx * np.floor(d[..., 0] / nx + 0.5)
+            if np.min(np.hypot(d[..., 0], d[..., 1])) < 2.0:
+                ok = False
+                break
+        if ok:
+            break
+    ks_c = ks_for_ca(1e-2, u_max)
+    mems.append(Membrane(xy=xy, ks=ks_c, kb=0.05 * ks_c * 64.0, ka=1.0, kind=0,
+                         ligands=np.arange(0, 50, 2, dtype=np.int32)))
+    wl = Workload(name="adjoint_capillary_320x160", nx=nx, ny=ny, body_force=(body_force_for(u_max, ny), 0.0),
+                  walls=1, init="poiseuille", precision=precision, membranes=mems,
+                  receptors=wall_receptors(nx, ny), sigma_lu=sigma_lattice(1.0, ny), seed=seed, steps=5000)
+    wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
+    car = mems[-1]
+    if ks is not None:
+        car.ks = ks
+    if kb is not None:
+        car.kb = kb
+    if sigma_lu is not None:
+        wl.sigma_lu = sigma_lu
+    return wl
+
+
 def capillary_ensemble(n=64, seed=0, precision="f32", l_min_um=32.0, l_max_um=64.0, dx_um=0.0625,
                        ny=160) -> List[Workload]:
     """Batched ensemble of coarse capillaries: instance i has length

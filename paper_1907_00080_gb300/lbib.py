@@ -78,6 +78,11 @@ _SIGS = {
     "lbib_ensemble_member": (_P, [_P, _I32]),
     "lbib_ensemble_last_error": (ctypes.c_char_p, [_P]),
     "lbib_ensemble_destroy": (None, [_P]),
+    "lbib_tangent_create": (_I, [_P, ctypes.POINTER(_P)]),
+    "lbib_tangent_seed": (_I, [_P, _DP, _DP, _D, _DP, _DP]),
+    "lbib_tangent_step": (_I, [_P, _I64]),
+    "lbib_tangent_read": (_I, [_P, _DP, _DP]),
+    "lbib_tangent_destroy": (None, [_P]),
     "lbib_set_tiling": (_I, [_P, _I32, _I32]),
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
@@ -310,6 +315,39 @@ def lbib_ensemble_last_error(ens):
 def lbib_ensemble_destroy(ens):
     if ens:
         load().lbib_ensemble_destroy(ens)
+
+
+def lbib_tangent_create(ctx):
+    out = _P()
+    _check(ctx, load().lbib_tangent_create(ctx, ctypes.byref(out)))
+    return out
+
+
+def _dp_or_null(a):
+    return None if a is None else _dptr(np.ascontiguousarray(a, dtype=np.float64))
+
+
+def lbib_tangent_seed(ctx, t, dks=None, dkb=None, dsigma=0.0, dxy=None, dxy_prev=None):
+    keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+            for a in (dks, dkb, dxy, dxy_prev)]
+    ptrs = [None if a is None else _dptr(a) for a in keep]
+    _check(ctx, load().lbib_tangent_seed(t, ptrs[0], ptrs[1], float(dsigma), ptrs[2], ptrs[3]))
+
+
+def lbib_tangent_step(ctx, t, n):
+    _check(ctx, load().lbib_tangent_step(t, int(n)))
+
+
+def lbib_tangent_read(ctx, t, nv):
+    dxy = np.zeros((nv, 2))
+    dxp = np.zeros((nv, 2))
+    _check(ctx, load().lbib_tangent_read(t, _dptr(dxy), _dptr(dxp)))
+    return dxy, dxp
+
+
+def lbib_tangent_destroy(t):
+    if t:
+        load().lbib_tangent_destroy(t)
 
 
 # ------------------------------------------------------------------ convenience

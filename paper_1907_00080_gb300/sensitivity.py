@@ -1,0 +1,146 @@
+"""Derivatives of carrier observables with respect to the carrier's stiffnesses,
+the bond stiffness and its release height, through the forward-mode tangent
+of the CUDA time step (lbib_tangent_*), behind a torch.autograd.Function.
+
+Observables after T steps (lattice units):
+  J1 = final height of the carrier's centroid above the lower wall (y = -1/2),
+  J2 = elastic energy of the carrier's bonds, sum over bonds of
+       sigma (d - y_eq)^2 / 2 (Eq. adhFor's spring).
+Parameters p = (k_s, k_b, sigma, y_release) of the carrier (the last membrane
+of the workload), all in lattice units.  The bond history of the run is held
+fixed (bond events are discrete); dJ/dp is the derivative along that history.
+
+This module only marshals: the state and its derivative are advanced by the
+library's kernels; J1, J2 and their directional derivatives are short sums over
+the final markers and bonds.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_1907_00080_gb300 import inputs, lbib
+
+PARAMS = ("k_s", "k_b", "sigma", "y_release")
+
+
+def make_workload(p, steps, seed=0, bonds="default"):
+    ks, kb, sigma, y0 = (float(v) for v in p)
+    wl = inputs.adjoint_capillary_320x160(ks=ks, kb=kb, sigma_lu=sigma, release_y=y0, seed=seed, bonds=bonds)
+    wl.steps = steps
+    return wl
+
+
+def observables(wl, xy, bonds):
+    """J1, J2 and the pieces their derivatives need."""
+    off = sum(len(m.xy) for m in wl.membranes[:-1])
+    n = len(wl.membranes[-1].xy)
+    car = xy[off:off + n]
+    j1 = float(car[:, 1].mean() + 0.5)
+    j2 = 0.0
+    terms = []
+    lig = wl.membranes[-1].ligands
+    y_eq = wl.bonds["y_eq"]
+    lig_base = sum(len(m.ligands) for m in wl.membranes[:-1])
+    for q, e in enumerate(lig):
+        r = int(bonds[lig_base + q])
+        if r < 0:
+            continue
+        a, b = off + int(e), off + (int(e) + 1) % n
+        c = 0.5 * (xy[a] + xy[b])
+        d = wl.receptors[r] - c
+        d[0] -= wl.nx * np.floor(d[0] / wl.nx + 0.5)
+        dist = float(np.hypot(d[0], d[1]))
+        j2 += 0.5 * wl.sigma_lu * (dist - y_eq) ** 2
+        terms.append((a, b, d, dist))
+    return j1, j2, (off, n, terms, y_eq)
+
+
+def run(p, steps, seed=0, bonds="default"):
+    """J = (J1, J2) of the FP64 solver after `steps` steps (no derivative)."""
+    wl = make_workload(p, steps, seed, bonds)
+    sim = lbib.Simulation(wl, precision="f64")
+    sim.step(steps)
+    j1, j2, _ = observables(wl, sim.markers(), sim.bonds())
+    b = sim.bonds()
+    sim.close()
+    return np.array([j1, j2]), b
+
+
+def jacobian(p, steps, seed=0, bonds="default"):
+    """J (2,) and dJ/dp (2, 4) by four tangent runs (one per parameter)."""
+    wl = make_workload(p, steps, seed, bonds)
+    nm = len(wl.membranes)
+    nv = wl.n_vertices
+    jac = np.zeros((2, 4))
+    J = None
+    bond_hist = None
+    for k in range(4):
+        sim = lbib.Simulation(wl, precision="f64")
+        t = lbib.lbib_tangent_create(sim.ctx)
+        try:
+            dks, dkb = np.zeros(nm), np.zeros(nm)
+            dxy = np.zeros((nv, 2))
+            dsig = 0.0
+            if k == 0:
+                dks[-1] = 1.0
+            elif k == 1:
+                dkb[-1] = 1.0
+            elif k == 2:
+                dsig = 1.0
+            else:
+                dxy[nv - len(wl.membranes[-1].xy):, 1] = 1.0
+            lbib.lbib_tangent_seed(sim.ctx, t, dks, dkb, dsig, dxy, None)
+            lbib.lbib_tangent_step(sim.ctx, t, steps)
+            dX, _ = lbib.lbib_tangent_read(sim.ctx, t, nv)
+            xy, bonds_f = sim.markers(), sim.bonds()
+        finally:
+            lbib.lbib_tangent_destroy(t)
+            sim.close()
+        j1, j2, (off, n, terms, y_eq) = observables(wl, xy, bonds_f)
+        if J is None:
+            J, bond_hist = np.array([j1, j2]), bonds_f
+        dj1 = float(dX[off:off + n, 1].mean())
+        dj2 = 0.0
+        for a, b, d, dist in terms:
+            dc = 0.5 * (dX[a] + dX[b])
+            ddist = -float(np.dot(d, dc)) / dist
+            dj2 += wl.sigma_lu * (dist - y_eq) * ddist
+            if k == 2:
+                dj2 += 0.5 * (dist - y_eq) ** 2
+        jac[:, k] = (dj1, dj2)
+    return J, jac, bond_hist
+
+
+def _torch_function():
+    import torch
+
+    class CarrierObservables(torch.autograd.Function):
+        """J = (J1, J2)(p), p = (k_s, k_b, sigma, y_release) as a float64
+        tensor; backward contracts the incoming gradient with dJ/dp from the
+        forward-mode tangent of the CUDA time step."""
+
+        @staticmethod
+        def forward(ctx, p, steps, seed=0):
+            pv = p.detach().cpu().numpy().astype(np.float64)
+            J, jac, _ = jacobian(pv, int(steps), int(seed))
+            ctx.save_for_backward(torch.as_tensor(jac, dtype=torch.float64))
+            return torch.as_tensor(J, dtype=torch.float64, device=p.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (jac,) = ctx.saved_tensors
+            g = grad_out.detach().to(torch.float64).cpu() @ jac
+            return g.to(grad_out.device), None, None
+
+    return CarrierObservables
+
+
+def carrier_observables(p, steps, seed=0):
+    """torch entry point: J = carrier_observables(p, steps); J.backward(...)"""
+    return _torch_function().apply(p, steps, seed)
+
+
+def default_params(seed=0):
+    wl = inputs.adjoint_capillary_320x160(seed=seed)
+    car = wl.membranes[-1]
+    return np.array([car.ks, car.kb, wl.sigma_lu, car.xy[:, 1].mean()])
