@@ -145,6 +145,15 @@ def cpu_oracle_mlups(wl, timesteps):
     return wl.nx * wl.ny * timesteps / dt / 1e6, dt, s
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's)."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -252,9 +261,7 @@ def lbib_main(args):
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     elapsed = ms / 1e3
     if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, "cuda")
     units = wl.nx * wl.ny * T * args.steps * ws
     value = units / elapsed / 1e6
 
