@@ -1,7 +1,8 @@
 // Interpolation, kinematic advance and bond kinetics in one kernel.
 //
-// One block per unit: a chunk of up to kChunkV vertices of a kinematic
-// membrane, or a whole rigid-projected membrane (its velocities are first
+// One block of kAdvThreads threads per unit: a chunk of up to kChunkV vertices
+// of a kinematic membrane, or a whole rigid-projected membrane (one vertex per
+// thread) (its velocities are first
 // projected on their least-squares rigid motion).  Per vertex: interpolate
 // u^n (Sec. 2.3), advance with Eq. kinematicPos (BDF2; forward Euler on the
 // first step), refresh the repulsion boxes.  Then the ligands whose element
@@ -13,7 +14,7 @@
 
 namespace lbib {
 
-constexpr int kRigidPer = 4;  // vertices per thread of a rigid unit (<= 4 * kChunkV vertices)
+constexpr int kAdvThreads = 4 * kChunkV;  // threads per unit: one vertex each of a rigid ring (<= 256)
 constexpr int kMaxPairs = 512;  // (ligand, receptor) formation candidates staged per block
 
 // receptor position p of the cell-ordered array
@@ -47,13 +48,13 @@ __device__ __forceinline__ void load_pos_cg<float>(const void* X, int v, ff& x, 
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
+__global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     using E = typename Ext<C>::E;
     const int u = blockIdx.x;
     const int m = a.au[3 * u], k0 = a.au[3 * u + 1], kn = a.au[3 * u + 2];
     const int off = a.mem_off[m], n = a.mem_n[m];
     const int tid = threadIdx.x, lane = tid & 31;
-    __shared__ E s_x[kRigidPer * kChunkV], s_y[kRigidPer * kChunkV];
+    __shared__ E s_x[kAdvThreads], s_y[kAdvThreads];
     __shared__ C cred[4 * 33];
     __shared__ bool s_last;
     const long long step = *a.d_step;
@@ -93,60 +94,51 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
         // ---- rigid-projected membrane: the whole ring in this block
         E xr, yr;
         load_pos<C>(a, off, xr, yr);
-        E x[kRigidPer], y[kRigidPer], xpv[kRigidPer], ypv[kRigidPer];
-        C Ux[kRigidPer], Uy[kRigidPer];
+        const int k = tid;
+        const bool valid = k < n;
+        E x, y, xpv, ypv;
+        C Ux = 0, Uy = 0;
         C sx = 0, sy = 0, su = 0, sv = 0;
-#pragma unroll
-        for (int i = 0; i < kRigidPer; ++i) {
-            const int k = tid + i * kChunkV;
-            if (k < n) {
-                load_pos<C>(a, off + k, x[i], y[i]);
-                PosIO<C>::load(a.Xp, off + k, xpv[i], ypv[i]);
-                interp_vertex<C>(a, off + k, Ux[i], Uy[i]);
-                sx += etoc(esub(x[i], xr));
-                sy += etoc(esub(y[i], yr));
-                su += Ux[i];
-                sv += Uy[i];
-            }
+        if (valid) {
+            load_pos<C>(a, off + k, x, y);
+            PosIO<C>::load(a.Xp, off + k, xpv, ypv);
+            interp_vertex<C>(a, off + k, Ux, Uy);
+            sx = etoc(esub(x, xr));
+            sy = etoc(esub(y, yr));
+            su = Ux;
+            sv = Uy;
         }
         // least-squares rigid motion U_c + omega x (x - x_c), positions about vertex 0
         const C inv_n = C(1) / C(n);
         block_sum4_c<C>(sx, sy, su, sv, cred);
         const C mx = sx * inv_n, my = sy * inv_n, mu = su * inv_n, mv = sv * inv_n;
         C num = 0, den = 0;
-#pragma unroll
-        for (int i = 0; i < kRigidPer; ++i) {
-            const int k = tid + i * kChunkV;
-            if (k < n) {
-                const C rx = etoc(esub(x[i], xr)) - mx, ry = etoc(esub(y[i], yr)) - my;
-                num += rx * (Uy[i] - mv) - ry * (Ux[i] - mu);
-                den += rx * rx + ry * ry;
-            }
+        if (valid) {
+            const C rx = etoc(esub(x, xr)) - mx, ry = etoc(esub(y, yr)) - my;
+            num = rx * (Uy - mv) - ry * (Ux - mu);
+            den = rx * rx + ry * ry;
         }
         C z0 = 0, z1 = 0;
         block_sum4_c<C>(num, den, z0, z1, cred);
         const C om = num / den;
-#pragma unroll
-        for (int i = 0; i < kRigidPer; ++i) {
-            const int k = tid + i * kChunkV;
-            if (k >= n) continue;
+        if (valid) {
             const int v = off + k;
-            const C rx = etoc(esub(x[i], xr)) - mx, ry = etoc(esub(y[i], yr)) - my;
+            const C rx = etoc(esub(x, xr)) - mx, ry = etoc(esub(y, yr)) - my;
             const C px = mu - om * ry, py = mv + om * rx;
             U[2 * v] = px;
             U[2 * v + 1] = py;
             E xn, yn;
-            bdf2<C>(x[i], xpv[i], px, step, xn);
-            bdf2<C>(y[i], ypv[i], py, step, yn);
+            bdf2<C>(x, xpv, px, step, xn);
+            bdf2<C>(y, ypv, py, step, yn);
             if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
-            PosIO<C>::store(a.Xp, v, x[i], y[i]);
+            PosIO<C>::store(a.Xp, v, x, y);
             PosIO<C>::store(a.X, v, xn, yn);
             s_x[k] = xn;
             s_y[k] = yn;
         }
         __syncthreads();
         // repulsion boxes: kSegV lanes per segment
-        constexpr int per_pass = kChunkV / kSegV;
+        constexpr int per_pass = kAdvThreads / kSegV;
         const int s0 = a.mem_seg_off[m], s1 = a.mem_seg_off[m + 1];
         for (int base = 0; base < s1 - s0; base += per_pass) {
             const int si = base + tid / kSegV;
@@ -170,9 +162,9 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
     const int nlq = a.nrec > 0 ? a.au_lig_off[u + 1] - lq0 : 0;
     if (nlq > 0) {
         __shared__ int s_pl[kMaxPairs], s_pr[kMaxPairs];
-        __shared__ int s_best[kRigidPer * kChunkV];
-        __shared__ int s_look[kRigidPer * kChunkV];
-        __shared__ int s_lig[kRigidPer * kChunkV], s_ka[kRigidPer * kChunkV], s_kb[kRigidPer * kChunkV];
+        __shared__ int s_best[kAdvThreads];
+        __shared__ int s_look[kAdvThreads];
+        __shared__ int s_lig[kAdvThreads], s_ka[kAdvThreads], s_kb[kAdvThreads];
         __shared__ int s_np;
         if (tid == 0) s_np = 0;
         __syncthreads();
@@ -258,8 +250,8 @@ __global__ void __launch_bounds__(kChunkV) k_advance(const MarkerArgs a) {
 }
 
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
-    if (prec == LBIB_F64) k_advance<double><<<a.nau, kChunkV, 0, s>>>(a);
-    else k_advance<float><<<a.nau, kChunkV, 0, s>>>(a);
+    if (prec == LBIB_F64) k_advance<double><<<a.nau, kAdvThreads, 0, s>>>(a);
+    else k_advance<float><<<a.nau, kAdvThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -75,23 +75,25 @@ bool valid_stream(lbib_precision p, int npt, int nx) {
 }
 
 void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
-    // lattices whose two population buffers do not fit in L2 stream through the
-    // persistent bulk-copy form, which keeps enough bytes in flight for DRAM
+    // lattices whose two population buffers exceed L2 (129 MB) stream through
+    // the persistent bulk-copy form, which keeps enough bytes in flight for DRAM
     // (FP64 stays on row tiles: it is bound by the FP64 pipe, not by DRAM)
     const double two_buffers = 2.0 * 9.0 * (double)c->pop_elem * c->nx * c->ny;
     const int npt = c->prec == LBIB_F32 ? 2 : 4;
-    if (c->prec != LBIB_F64 && two_buffers > 96e6 && valid_stream(c->prec, npt, c->nx)) {
+    if (c->prec != LBIB_F64 && two_buffers > 128e6 && valid_stream(c->prec, npt, c->nx)) {
         *vec = npt;
         *ty = 0;
         return;
     }
-    int v = c->prec == LBIB_F64 ? 2 : (c->prec == LBIB_F32 ? 4 : 8);
+    int v = c->prec == LBIB_F64 ? 2 : 4;
     while (v > 1 && !valid_vec(c->prec, v, c->nx)) v /= 2;
     const long long N = (long long)c->nx * c->ny;
     // small lattices: fewer nodes per thread so that every SM has warps to switch between
     while (v > 1 && N / v < 152LL * 1024 && valid_vec(c->prec, v / 2, c->nx)) v /= 2;
     const long long tiles_x = (c->nx + 32LL * v - 1) / (32LL * v);
-    int t = 4;
+    // large lattices: one row per block (most blocks in flight); small ones:
+    // up to 4 rows while the grid still fills the GPU several times over
+    int t = N >= (1LL << 20) ? 1 : 4;
     while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 8) t /= 2;
     *vec = v;
     *ty = t;
@@ -1122,6 +1124,7 @@ struct lbib_tangent {
     int ip = 0, ix = 1, in = 2, cf = 0;
     double *Gv = nullptr, *Gd = nullptr, *u = nullptr, *ud = nullptr, *Wv = nullptr, *Wd = nullptr;
     double *Fv = nullptr, *Fd = nullptr, *A = nullptr, *Ad = nullptr, *dks = nullptr, *dkb = nullptr;
+    double* box = nullptr;
     int* st = nullptr;
     double dsigma = 0.0;
     std::vector<void*> allocs;
@@ -1159,7 +1162,7 @@ extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     ok = ok && (t->u = (double*)get(2 * N * 8)) && (t->ud = (double*)get(2 * N * 8));
     ok = ok && (t->Wv = (double*)get(9 * nv * 8)) && (t->Wd = (double*)get(9 * nv * 8));
     ok = ok && (t->Fv = (double*)get(2 * nv * 8)) && (t->Fd = (double*)get(2 * nv * 8));
-    ok = ok && (t->A = (double*)get(nm * 8)) && (t->Ad = (double*)get(nm * 8));
+    ok = ok && (t->A = (double*)get(nm * 8)) && (t->Ad = (double*)get(nm * 8)) && (t->box = (double*)get(4 * nm * 8));
     ok = ok && (t->dks = (double*)get(nm * 8)) && (t->dkb = (double*)get(nm * 8));
     ok = ok && (t->st = (int*)get(2 * nv * 4));
     if (!ok) {
@@ -1218,7 +1221,7 @@ extern "C" lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n) {
         a.dXp = t->dX[t->ip];
         a.dXn = t->dX[t->in];
         a.Gv = t->Gv; a.Gd = t->Gd; a.u = t->u; a.ud = t->ud; a.Wv = t->Wv; a.Wd = t->Wd;
-        a.st = t->st; a.Fv = t->Fv; a.Fd = t->Fd; a.A = t->A; a.Ad = t->Ad;
+        a.st = t->st; a.Fv = t->Fv; a.Fd = t->Fd; a.A = t->A; a.Ad = t->Ad; a.box = t->box;
         a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma;
         a.omega = 1.0 / c->tau; a.gx = c->gx; a.gy = c->gy;
         a.step = c->steps;

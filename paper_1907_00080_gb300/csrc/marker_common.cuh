@@ -120,13 +120,26 @@ __device__ typename Ext<C>::E ring_area_group(const MarkerArgs& a, int m, int w0
     E xr, yr;
     load_pos<C>(a, off, xr, yr);
     E acc = ezero<E>();
-    for (int k = t; k < n; k += 32 * kAreaWarps) {
-        const int R = k == n - 1 ? 0 : k + 1;
-        E xv, yv, xR, yR;
-        load_pos<C>(a, off + k, xv, yv);
-        load_pos<C>(a, off + R, xR, yR);
-        const E term = esub(emul(esub(xv, xr), esub(yR, yr)), emul(esub(xR, xr), esub(yv, yr)));
-        acc = eadd(acc, term);
+    // kBatch terms per pass with all their loads issued first (long rings:
+    // one round trip per pass instead of one per term); same summation order
+    constexpr int kBatch = 4;
+    constexpr int stride = 32 * kAreaWarps;
+    for (int k0 = t; k0 < n; k0 += kBatch * stride) {
+        E xv[kBatch], yv[kBatch], xR[kBatch], yR[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            const int k = k0 + b * stride;
+            const int kk = k < n ? k : 0;
+            const int R = kk == n - 1 ? 0 : kk + 1;
+            load_pos<C>(a, off + kk, xv[b], yv[b]);
+            load_pos<C>(a, off + R, xR[b], yR[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            if (k0 + b * stride >= n) break;
+            const E term = esub(emul(esub(xv[b], xr), esub(yR[b], yr)), emul(esub(xR[b], xr), esub(yv[b], yr)));
+            acc = eadd(acc, term);
+        }
     }
     E* r = red + 32 * w;
     r[lane] = acc;

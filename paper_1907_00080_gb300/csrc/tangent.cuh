@@ -19,6 +19,7 @@ struct TangentArgs {
     int* st;               // [nv][2] stencil origin (i0, j0), unwrapped
     double *Fv, *Fd;       // [nv][2] marker forces and tangents
     double *A, *Ad;        // [nmem] enclosed areas and tangents
+    double* box;           // [nmem][4] bounding box of X^n: x_min, x_max, y_min, y_max
     const double* dks;     // [nmem] tangent of k_s per membrane
     const double* dkb;     // [nmem] tangent of k_b per membrane
     double dsigma;         // tangent of the bond stiffness

@@ -48,11 +48,11 @@ __device__ __forceinline__ void pos(const TangentArgs& t, int v, dual& x, dual& 
 __device__ __forceinline__ int ring(int off, int n, int k) { return off + ((k % n) + n) % n; }
 
 __device__ __forceinline__ dual wrap_x(const TangentArgs& t, dual dx) {
-    dx.v -= t.m.nx * floor(dx.v / t.m.nx + 0.5);
+    dx.v -= t.m.nx * floor(dx.v * t.m.inv_nx + 0.5);
     return dx;
 }
 __device__ __forceinline__ dual wrap_y(const TangentArgs& t, dual dy) {
-    if (!t.m.walls) dy.v -= t.m.ny * floor(dy.v / t.m.ny + 0.5);
+    if (!t.m.walls) dy.v -= t.m.ny * floor(dy.v * t.m.inv_ny + 0.5);
     return dy;
 }
 
@@ -91,20 +91,39 @@ __global__ void k_t_area(const TangentArgs t) {
         pos(t, ring(off, n, k + 1), xb, yb);
         s += (xa - x0) * (yb - y0) - (xb - x0) * (ya - y0);
     }
-    __shared__ double rv[256], rd[256];
+    // bounding box of the membrane (unwrapped x), for the repulsion screen
+    double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+    const double* X = static_cast<const double*>(t.m.X);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double x = X[2 * (off + k)], y = X[2 * (off + k) + 1];
+        bx0 = fmin(bx0, x);
+        bx1 = fmax(bx1, x);
+        by0 = fmin(by0, y);
+        by1 = fmax(by1, y);
+    }
+    __shared__ double rv[256], rd[256], rb[4][256];
     rv[threadIdx.x] = s.v;
     rd[threadIdx.x] = s.d;
+    rb[0][threadIdx.x] = bx0;
+    rb[1][threadIdx.x] = bx1;
+    rb[2][threadIdx.x] = by0;
+    rb[3][threadIdx.x] = by1;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) {
             rv[threadIdx.x] += rv[threadIdx.x + o];
             rd[threadIdx.x] += rd[threadIdx.x + o];
+            rb[0][threadIdx.x] = fmin(rb[0][threadIdx.x], rb[0][threadIdx.x + o]);
+            rb[1][threadIdx.x] = fmax(rb[1][threadIdx.x], rb[1][threadIdx.x + o]);
+            rb[2][threadIdx.x] = fmin(rb[2][threadIdx.x], rb[2][threadIdx.x + o]);
+            rb[3][threadIdx.x] = fmax(rb[3][threadIdx.x], rb[3][threadIdx.x + o]);
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         t.A[m] = 0.5 * rv[0];
         t.Ad[m] = 0.5 * rd[0];
+        for (int q = 0; q < 4; ++q) t.box[4 * m + q] = rb[q][0];
     }
 }
 
@@ -145,18 +164,35 @@ __global__ void k_t_forces(const TangentArgs t) {
     }
     // Eq. repFor against every vertex of the other membranes closer than d_rep
     if (t.m.nmem > 1) {
-        const VGeo g = vgeo(t, off, n, k);
         const double c0 = 1e-4 / (8.0 * 1.4142135623730951);
-        for (int b = 0; b < t.m.nv; ++b) {
-            if (b >= off && b < off + n) continue;
-            dual xb, yb;
-            pos(t, b, xb, yb);
-            const dual dx = wrap_x(t, xv - xb), dy = wrap_y(t, yv - yb);
-            const dual d = sqrt(dx * dx + dy * dy);
-            if (d.v < t.m.d_rep) {
-                const dual mag = c0 * pow_m52(d);
-                fx -= mag * g.nx;
-                fy -= mag * g.ny;
+        const double reach = t.m.d_rep + 1e-9;
+        bool have_g = false;
+        VGeo g;
+        for (int mb = 0; mb < t.m.nmem; ++mb) {
+            if (mb == m) continue;
+            // skip membranes whose box (periodic in x) is out of reach of v
+            const double* bb = t.box + 4 * mb;
+            const double hx = 0.5 * (bb[1] - bb[0]);
+            double cxm = xv.v - 0.5 * (bb[0] + bb[1]);
+            cxm -= t.m.nx * floor(cxm * t.m.inv_nx + 0.5);
+            double cym = yv.v - 0.5 * (bb[2] + bb[3]);
+            if (!t.m.walls) cym -= t.m.ny * floor(cym * t.m.inv_ny + 0.5);
+            if (::fabs(cxm) > hx + reach || ::fabs(cym) > 0.5 * (bb[3] - bb[2]) + reach) continue;
+            if (!have_g) {
+                g = vgeo(t, off, n, k);
+                have_g = true;
+            }
+            const int o2 = t.m.mem_off[mb], n2 = t.m.mem_n[mb];
+            for (int b = o2; b < o2 + n2; ++b) {
+                dual xb, yb;
+                pos(t, b, xb, yb);
+                const dual dx = wrap_x(t, xv - xb), dy = wrap_y(t, yv - yb);
+                const dual d = sqrt(dx * dx + dy * dy);
+                if (d.v < t.m.d_rep) {
+                    const dual mag = c0 * pow_m52(d);
+                    fx -= mag * g.nx;
+                    fy -= mag * g.ny;
+                }
             }
         }
     }
@@ -342,15 +378,16 @@ cudaError_t launch_tangent_step(const TangentArgs& t, cudaStream_t s) {
     const size_t N = (size_t)t.m.nx * t.m.ny;
     if ((e = cudaMemsetAsync(t.Gv, 0, 2 * N * sizeof(double), s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(t.Gd, 0, 2 * N * sizeof(double), s)) != cudaSuccess) return e;
-    const int nvb = (t.m.nv + 127) / 128;
+    // small blocks: these FP64 kernels have one thread per vertex, spread them over the SMs
+    const int nvb = (t.m.nv + 31) / 32;
     if (t.m.nv > 0) {
         k_t_area<<<t.m.nmem, 256, 0, s>>>(t);
-        k_t_forces<<<nvb, 128, 0, s>>>(t);
-        k_t_weights_spread<<<nvb, 128, 0, s>>>(t);
+        k_t_forces<<<nvb, 32, 0, s>>>(t);
+        k_t_weights_spread<<<nvb, 32, 0, s>>>(t);
     }
     const int g = (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096);
     k_t_lb<<<g, 256, 0, s>>>(t);
-    if (t.m.nv > 0) k_t_advance<<<nvb, 128, 0, s>>>(t);
+    if (t.m.nv > 0) k_t_advance<<<nvb, 32, 0, s>>>(t);
     return cudaGetLastError();
 }
 

@@ -1,8 +1,10 @@
 """Tile shape of the fused LB kernel.
 
 The fused kernel processes tiles of (32 * vec) x ty nodes: vec consecutive x
-nodes per thread, one warp per row, ty rows per block.  Small lattices want
-small vec (more threads to hide latency); large lattices want 16-byte vectors.
+nodes per thread, one warp per row, ty rows per block; or, with ty = 0, runs
+its persistent bulk-copy form with segments of 256 * vec nodes.  Small
+lattices want small vec (more threads to hide latency); large lattices want
+16-byte vectors and, beyond L2, the persistent form.
 ``TABLE`` holds shapes measured on GB300 for the benchmarked workloads;
 anything else uses the library's default rule.  ``autotune`` times candidates
 through the C ABI.
@@ -12,10 +14,14 @@ from __future__ import annotations
 import time
 
 # (precision, nx, ny) -> (vec, ty), measured with autotune() on a GB300
-TABLE = {}
+# (whole time steps, graph-launched, 3 x 2000 steps per candidate)
+TABLE = {
+    ("f32", 640, 160): (1, 4),  # 20.89 us/step; library default (1, 2): 21.26
+}
 
 
 def candidates(precision: str, nx: int):
+    """Row tiles (vec, ty) and the persistent bulk-copy form (npt, 0)."""
     vecs = {"f64": (1, 2), "f32": (1, 2, 4), "f16": (2, 4, 8), "bf16": (2, 4, 8)}[precision]
     out = []
     for v in vecs:
@@ -23,6 +29,10 @@ def candidates(precision: str, nx: int):
             continue
         for ty in (1, 2, 4, 8):
             out.append((v, ty))
+    halo = {"f64": 2, "f32": 4, "f16": 8, "bf16": 8}[precision]
+    npts = {"f64": (1, 2), "f32": (1, 2, 4), "f16": (2, 4, 8), "bf16": (2, 4, 8)}[precision]
+    if nx % halo == 0:
+        out += [(n, 0) for n in npts]
     return out
 
 
