@@ -51,16 +51,26 @@ template <typename C>
 __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     using E = typename Ext<C>::E;
     const int u = blockIdx.x;
-    const int m = a.au[3 * u], k0 = a.au[3 * u + 1], kn = a.au[3 * u + 2];
-    const int off = a.mem_off[m], n = a.mem_n[m];
+    const int4 u0 = a.au[2 * u], u1 = a.au[2 * u + 1];
+    const int m = u0.x, k0 = u0.y, kn = u0.z, off = u0.w, n = u1.x, kind = u1.y;
     const int tid = threadIdx.x, lane = tid & 31;
     __shared__ E s_x[kAdvThreads], s_y[kAdvThreads];
     __shared__ C cred[4 * 33];
     __shared__ bool s_last;
     const long long step = *a.d_step;
     C* U = static_cast<C*>(a.U);
+    // the unit's ligand records and current bonds, fetched now so that their
+    // latency overlaps the marker advance (a unit has at most one ligand per thread)
+    const int lq0 = u1.z;
+    const int nlq = a.nrec > 0 ? u1.w : 0;
+    int4 my_rec = make_int4(-1, 0, 0, 0);
+    int my_bond = -1;
+    if (tid < nlq) {
+        my_rec = a.au_ligs[lq0 + tid];
+        my_bond = a.bond_of_lig[my_rec.x];
+    }
 
-    if (a.mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED) {
+    if (kind != LBIB_MEMBRANE_RIGID_PROJECTED) {
         // ---- kinematic chunk: one vertex per thread
         const bool valid = tid < kn;
         const int v = off + k0 + (valid ? tid : 0);
@@ -158,8 +168,6 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     // (b) per pair: the formation test; each ligand keeps the lowest passing
     //     receptor id (a minimum: independent of evaluation order);
     // (c) per ligand that is free after (a): claim its receptor.
-    const int lq0 = a.au_lig_off[u];
-    const int nlq = a.nrec > 0 ? a.au_lig_off[u + 1] - lq0 : 0;
     if (nlq > 0) {
         __shared__ int s_pl[kMaxPairs], s_pr[kMaxPairs];
         __shared__ int s_best[kAdvThreads];
@@ -169,8 +177,8 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         if (tid == 0) s_np = 0;
         __syncthreads();
         for (int q = tid; q < nlq; q += blockDim.x) {
-            const int l = a.au_ligs[lq0 + q];
-            const int ka = a.lig_a[l] - off - k0, kb = a.lig_b[l] - off - k0;
+            const int4 rec = my_rec;  // q == tid: nlq <= kAdvThreads
+            const int l = rec.x, ka = rec.y, kb = rec.z;
             s_lig[q] = l;
             s_ka[q] = ka;
             s_kb[q] = kb;
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
             lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);
             s_best[q] = INT_MAX;
             bool look = lp.finite();  // non-finite positions: reported above
-            const int r = a.bond_of_lig[l];
+            const int r = my_bond;
             if (look && r >= 0) {
                 look = ruptures<C>(a, lp, step, l, r);
                 if (look) a.rupt[l] = r;
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
                     } else {
                         // list full: decide in place
                         const int rr = a.rcell_ids[p];
-                        if (a.owner[rr] < 0 && forms<C>(a, lp, step, l, rr, ehi_pos_x<C>(a, p), ehi_pos_y<C>(a, p)))
+                        if (a.owner_cell[p] < 0 && forms<C>(a, lp, step, l, rr, ehi_pos_x<C>(a, p), ehi_pos_y<C>(a, p)))
                             atomicMin(&s_best[q], rr);
                     }
                 }
@@ -212,7 +220,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
             const int rr = a.rcell_ids[p];
             typename Ext<C>::E rx, ry;
             PosIO<C>::load(a.rcell_pos, p, rx, ry);
-            if (a.owner[rr] >= 0) continue;  // bound at the start of the step
+            if (a.owner_cell[p] >= 0) continue;  // bound at the start of the step
             const int l = s_lig[q], ka = s_ka[q], kb = s_kb[q];
             LigandPoint<C> lp;
             lp.init(s_x[ka], s_y[ka], s_x[kb], s_y[kb]);

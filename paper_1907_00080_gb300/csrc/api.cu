@@ -351,33 +351,41 @@ static lbib_status finalize(lbib_ctx* c) {
         std::vector<int> cur(cnt.begin(), cnt.end() - 1);
         for (int r = 0; r < nr; ++r) rcell_ids[cur[cell[r]]++] = r;  // ascending id within a cell
     }
+    // work units, kUnitInts ints each (one 32-byte read per block):
+    // {membrane, first local vertex, vertex count, membrane offset, membrane size,
+    //  kind, first ligand record, ligand records}
     std::vector<int> fu, au;
     for (int m = 0; m < nm; ++m) {
-        const int n = c->h_mem_n[m];
+        const int n = c->h_mem_n[m], off = c->h_mem_off[m], kind = c->h_mem_kind[m];
         for (int k0 = 0; k0 < n; k0 += kChunkV) {
-            fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0)});
-            if (c->h_mem_kind[m] != LBIB_MEMBRANE_RIGID_PROJECTED)
-                au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0)});
+            fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
+            if (kind != LBIB_MEMBRANE_RIGID_PROJECTED)
+                au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
         }
-        if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) au.insert(au.end(), {m, 0, n});
+        if (kind == LBIB_MEMBRANE_RIGID_PROJECTED) au.insert(au.end(), {m, 0, n, off, n, kind, 0, 0});
     }
-    // ligands decided inside each advance unit (both element vertices in it) and
+    // ligands decided inside each advance unit (both element vertices in it),
+    // as records {ligand, local index of its element's two vertices, 0}, and
     // the straddling rest, decided by the kernel's last block
-    const int nau = (int)(au.size() / 3);
-    std::vector<int> au_lig_off(nau + 1, 0), au_ligs, strad;
+    const int nau = (int)(au.size() / kUnitInts);
+    std::vector<int> au_ligs, strad;
     {
         std::vector<std::vector<int>> per(nau);
         std::vector<int> unit_of(std::max(nv, 1), -1);
-        for (int q = 0; q < nau; ++q)
-            for (int k = 0; k < au[3 * q + 2]; ++k) unit_of[c->h_mem_off[au[3 * q]] + au[3 * q + 1] + k] = q;
+        for (int q = 0; q < nau; ++q) {
+            const int* u = &au[kUnitInts * q];
+            for (int k = 0; k < u[2]; ++k) unit_of[u[3] + u[1] + k] = q;
+        }
         for (int l = 0; l < nl; ++l) {
             const int ua = unit_of[lig_a[l]], ub = unit_of[lig_b[l]];
             if (ua == ub) per[ua].push_back(l);
             else strad.push_back(l);
         }
         for (int q = 0; q < nau; ++q) {
-            au_lig_off[q + 1] = au_lig_off[q] + (int)per[q].size();
-            au_ligs.insert(au_ligs.end(), per[q].begin(), per[q].end());
+            int* u = &au[kUnitInts * q];
+            u[6] = (int)(au_ligs.size() / 4);
+            u[7] = (int)per[q].size();  // <= vertices of the unit <= 4 kChunkV (one per advance thread)
+            for (int l : per[q]) au_ligs.insert(au_ligs.end(), {l, lig_a[l] - u[3] - u[1], lig_b[l] - u[3] - u[1], 0});
         }
     }
 
@@ -395,9 +403,10 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
         add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl); add(4 * nl);
         add(16 * nr); add(16 * nr); add(4 * nr); add(4 * nr); add(4 * rcell_start.size()); add(4 * rcell_ids.size()); add(16 * nr);
+        add(4 * nr); add(4 * nr);
         add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
-        add(4 * au_lig_off.size()); add(4 * au_ligs.size()); add(4 * strad.size());
+        add(4 * au_ligs.size()); add(4 * strad.size());
         bytes = probe.used + 256;
     }
     lbib_status st = LBIB_OK;
@@ -441,6 +450,8 @@ static lbib_status finalize(lbib_ctx* c) {
     double* rec_xy = ar.take<double>(2 * (size_t)nr);
     void* rec_e = ar.take<double>(2 * (size_t)nr);
     a.owner = ar.take<int>(nr);
+    a.owner_cell = ar.take<int>(nr);
+    int* d_rcell_of_rec = ar.take<int>(nr);
     a.claim = ar.take<int>(nr);
     int* d_rcs = ar.take<int>(rcell_start.size());
     int* d_rci = ar.take<int>(rcell_ids.size());
@@ -451,7 +462,6 @@ static lbib_status finalize(lbib_ctx* c) {
     c->tickets = ar.take<unsigned int>(4);
     int* d_fu = ar.take<int>(fu.size());
     int* d_au = ar.take<int>(au.size());
-    int* d_au_lig_off = ar.take<int>(au_lig_off.size());
     int* d_au_ligs = ar.take<int>(au_ligs.size());
     int* d_strad = ar.take<int>(strad.size());
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
@@ -481,7 +491,6 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(d_mem_seg_off, mem_seg_off.data(), 4 * (nm + 1)));
         CK(H2D(d_fu, fu.data(), 4 * fu.size()));
         CK(H2D(d_au, au.data(), 4 * au.size()));
-        CK(H2D(d_au_lig_off, au_lig_off.data(), 4 * au_lig_off.size()));
         if (!au_ligs.empty()) CK(H2D(d_au_ligs, au_ligs.data(), 4 * au_ligs.size()));
         if (!strad.empty()) CK(H2D(d_strad, strad.data(), 4 * strad.size()));
     }
@@ -496,11 +505,15 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(rec_xy, c->h_rec.data(), 16 * (size_t)nr));
         CK(launch_pos_in(c->prec, rec_xy, rec_e, nr, c->stream));
         CK(cudaMemsetAsync(a.owner, 0xFF, 4 * nr, c->stream));
+        CK(cudaMemsetAsync(a.owner_cell, 0xFF, 4 * nr, c->stream));
         CK(cudaMemsetAsync(a.claim, 0x7F, 4 * nr, c->stream));  // 0x7F7F7F7F: no claim
     }
     CK(H2D(d_rcs, rcell_start.data(), 4 * rcell_start.size()));
     if (!rcell_ids.empty()) {
         CK(H2D(d_rci, rcell_ids.data(), 4 * rcell_ids.size()));
+        std::vector<int> rcell_of_rec(nr);
+        for (int p = 0; p < nr; ++p) rcell_of_rec[rcell_ids[p]] = p;
+        CK(H2D(d_rcell_of_rec, rcell_of_rec.data(), 4 * nr));
         // receptor positions permuted into cell order (staged through xy_stage)
         std::vector<double> rp(2 * (size_t)nr);
         for (int p = 0; p < nr; ++p) {
@@ -527,11 +540,14 @@ static lbib_status finalize(lbib_ctx* c) {
     a.rest = rest; a.elem_lig = elig;
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
-    a.nfu = (int)(fu.size() / 3); a.nau = nau; a.fu = d_fu; a.au = d_au;
-    a.au_lig_off = d_au_lig_off; a.au_ligs = d_au_ligs;
+    a.nfu = (int)(fu.size() / kUnitInts); a.nau = nau;
+    a.fu = reinterpret_cast<const int4*>(d_fu);
+    a.au = reinterpret_cast<const int4*>(d_au);
+    a.au_ligs = reinterpret_cast<const int4*>(d_au_ligs);
     a.nstrad = (int)strad.size(); a.strad_ligs = d_strad;
     a.nlig = nl; a.nrec = nr; a.lig_a = d_lig_a; a.lig_b = d_lig_b;
     a.rec_xy = rec_xy; a.rec_e = rec_e; a.rcell_start = d_rcs; a.rcell_ids = d_rci; a.rcell_pos = d_rcpos;
+    a.rcell_of_rec = d_rcell_of_rec;
     a.rc_nx = rc_nx; a.rc_ny = rc_ny; a.rc_w = rc_w; a.rc_h = rc_h; a.rc_y0 = rc_y0;
     a.inv_rc_w = 1.0 / rc_w; a.inv_rc_h = 1.0 / rc_h;
     a.inv_y_eq = c->bp.y_eq > 0 ? 1.0 / c->bp.y_eq : 0.0;

@@ -216,7 +216,7 @@ __device__ __forceinline__ void bond_decide(const MarkerArgs& a, int l, LigandPo
             const int rr = a.rcell_ids[p];
             typename Ext<C>::E rx, ry;
             PosIO<C>::load(a.rcell_pos, p, rx, ry);
-            if (rr >= best || a.owner[rr] >= 0) continue;  // bound at the start of the step
+            if (rr >= best || a.owner_cell[p] >= 0) continue;  // bound at the start of the step
             if (forms<C>(a, lp, step, l, rr, rx, ry)) best = rr;
         }
     }
@@ -251,36 +251,58 @@ __device__ __forceinline__ void ligand_cells(const MarkerArgs& a, const LigandPo
 // ruptures and the winning claims, clear the claims, advance the step counter.
 // Data written by other blocks is read past L1.
 static __device__ __forceinline__ void bond_apply_all(const MarkerArgs& a) {
+    // ruptures free their receptor, won claims bind it; owner is kept both by
+    // receptor id and in cell order (owner_cell, read by the formation tests)
     constexpr int kPer = 4;  // ligands per thread per pass, loads issued together
+    const bool one_pass = a.nlig <= kPer * (int)blockDim.x;
+    int keep_c[kPer];
     for (int base = 0; base < a.nlig; base += kPer * blockDim.x) {
-        int q[kPer], r_old[kPer], c[kPer], cl[kPer];
+        int q[kPer], r_old[kPer], c[kPer], cl[kPer], pr[kPer], pc[kPer];
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
             q[i] = base + threadIdx.x + i * blockDim.x;
             r_old[i] = q[i] < a.nlig ? __ldcg(&a.rupt[q[i]]) : -1;
             c[i] = q[i] < a.nlig ? __ldcg(&a.cand[q[i]]) : -1;
+            keep_c[i] = c[i];
         }
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) cl[i] = c[i] >= 0 ? __ldcg(&a.claim[c[i]]) : -1;
+        for (int i = 0; i < kPer; ++i) {
+            cl[i] = c[i] >= 0 ? __ldcg(&a.claim[c[i]]) : -1;
+            pc[i] = c[i] >= 0 ? a.rcell_of_rec[c[i]] : -1;
+            pr[i] = r_old[i] >= 0 ? a.rcell_of_rec[r_old[i]] : -1;
+        }
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
             if (r_old[i] >= 0) {
                 a.owner[r_old[i]] = -1;
+                a.owner_cell[pr[i]] = -1;
                 a.bond_of_lig[q[i]] = -1;
                 a.rupt[q[i]] = -1;
             }
             if (c[i] >= 0 && cl[i] == q[i]) {
                 a.bond_of_lig[q[i]] = c[i];
                 a.owner[c[i]] = q[i];
+                a.owner_cell[pc[i]] = q[i];
             }
         }
     }
     __syncthreads();  // every claim has been read before any is cleared
-    for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
-        const int c = __ldcg(&a.cand[q]);
-        if (c >= 0) {
-            a.claim[c] = INT_MAX;
-            a.cand[q] = -1;
+    if (one_pass) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int q = threadIdx.x + i * blockDim.x;
+            if (keep_c[i] >= 0) {
+                a.claim[keep_c[i]] = INT_MAX;
+                a.cand[q] = -1;
+            }
+        }
+    } else {
+        for (int q = threadIdx.x; q < a.nlig; q += blockDim.x) {
+            const int c = __ldcg(&a.cand[q]);
+            if (c >= 0) {
+                a.claim[c] = INT_MAX;
+                a.cand[q] = -1;
+            }
         }
     }
 }

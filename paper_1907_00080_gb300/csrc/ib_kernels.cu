@@ -87,8 +87,8 @@ constexpr int kScreenIter = 8;                    // segment boxes per lane load
 template <typename C>
 __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     using E = typename Ext<C>::E;
-    const int m = a.fu[3 * blockIdx.x], k0 = a.fu[3 * blockIdx.x + 1], kn = a.fu[3 * blockIdx.x + 2];
-    const int off = a.mem_off[m], n = a.mem_n[m];
+    const int4 u0 = a.fu[2 * blockIdx.x], u1 = a.fu[2 * blockIdx.x + 1];
+    const int m = u0.x, k0 = u0.y, kn = u0.z, off = u0.w, n = u1.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // positions of vertices k0-2 .. k0+kn+1 (slot p <-> vertex k0 - 2 + p)
     __shared__ E s_x[kChunkV + 4], s_y[kChunkV + 4];

@@ -136,8 +136,8 @@ struct MarkerArgs {
     // cuts every membrane into chunks of kChunkV vertices, the advance kernel
     // cuts kinematic membranes the same way and keeps rigid-projected ones whole
     int nfu, nau;
-    const int* fu;            // [nfu][3]
-    const int* au;            // [nau][3]
+    const int4* fu;           // [nfu][2]: {m, k0, kn, off} {n, kind, lig0, nlig} (see kUnitInts)
+    const int4* au;           // [nau][2], same records
     // bonds
     int nlig, nrec;
     const int* lig_a;         // [nlig] first vertex of the ligand element
@@ -148,6 +148,8 @@ struct MarkerArgs {
     const double* rec_xy;     // [nrec][2] receptor positions (FP64 decisions)
     const void* rec_e;        // [nrec] the same in the marker position layout
     int* owner;               // [nrec]
+    int* owner_cell;          // [nrec] the same in cell order (owner_cell[p] = owner[rcell_ids[p]])
+    const int* rcell_of_rec;  // [nrec] cell-order position of receptor r
     int* claim;               // [nrec]
     const int* rcell_start;   // [ncell + 1]
     const int* rcell_ids;     // [nrec] receptor ids in cell order
@@ -176,8 +178,7 @@ struct MarkerArgs {
     } f;
     // ligands decided by each advance unit (element inside the unit, CSR), and
     // the ligands whose element straddles two units (decided by the last block)
-    const int* au_lig_off;    // [nau + 1]
-    const int* au_ligs;
+    const int4* au_ligs;      // {ligand, local vertex a, local vertex b, 0} per unit ligand
     int nstrad;
     const int* strad_ligs;
 };
@@ -185,6 +186,7 @@ struct MarkerArgs {
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
 
 constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of 32)
+constexpr int kUnitInts = 8;  // ints per work-unit record (two int4)
 constexpr int kSegV = 8;      // vertices per repulsion-screening segment (divides kChunkV)
 
 // ---------------------------------------------------------------- launchers
