@@ -1,6 +1,6 @@
 // Interpolation, kinematic advance and bond kinetics in one kernel.
 //
-// One block of kAdvThreads threads per unit: a chunk of up to kChunkV vertices
+// One block of a.adv_threads (<= kAdvThreads) threads per unit: a chunk of up to kChunkV vertices
 // of a kinematic membrane, or a whole rigid-projected membrane (one vertex per
 // thread) (its velocities are first
 // projected on their least-squares rigid motion).  Per vertex: interpolate
@@ -14,7 +14,7 @@
 
 namespace lbib {
 
-constexpr int kAdvThreads = 4 * kChunkV;  // threads per unit: one vertex each of a rigid ring (<= 256)
+constexpr int kAdvThreads = 4 * kChunkV;  // most threads per unit: one vertex each of a rigid ring (<= 256)
 constexpr int kMaxPairs = 512;  // (ligand, receptor) formation candidates staged per block
 
 // receptor position p of the cell-ordered array
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         }
         __syncthreads();
         // repulsion boxes: kSegV lanes per segment
-        constexpr int per_pass = kAdvThreads / kSegV;
+        const int per_pass = blockDim.x / kSegV;
         const int s0 = a.mem_seg_off[m], s1 = a.mem_seg_off[m + 1];
         for (int base = 0; base < s1 - s0; base += per_pass) {
             const int si = base + tid / kSegV;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         if (tid == 0) s_np = 0;
         __syncthreads();
         for (int q = tid; q < nlq; q += blockDim.x) {
-            const int4 rec = my_rec;  // q == tid: nlq <= kAdvThreads
+            const int4 rec = my_rec;  // q == tid: a unit has no more ligands than threads
             const int l = rec.x, ka = rec.y, kb = rec.z;
             s_lig[q] = l;
             s_ka[q] = ka;
@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
 }
 
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
-    if (prec == LBIB_F64) k_advance<double><<<a.nau, kAdvThreads, 0, s>>>(a);
-    else k_advance<float><<<a.nau, kAdvThreads, 0, s>>>(a);
+    if (a.adv_threads < kChunkV || a.adv_threads > kAdvThreads || a.adv_threads % 32) return cudaErrorInvalidValue;
+    if (prec == LBIB_F64) k_advance<double><<<a.nau, a.adv_threads, 0, s>>>(a);
+    else k_advance<float><<<a.nau, a.adv_threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -541,6 +541,14 @@ static lbib_status finalize(lbib_ctx* c) {
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
     a.nfu = (int)(fu.size() / kUnitInts); a.nau = nau;
+    // advance blocks: one thread per vertex of the longest rigid ring, at least
+    // a chunk; small blocks leave room for other work (ensembles) on the SMs
+    {
+        int longest = kChunkV;
+        for (int m = 0; m < nm; ++m)
+            if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) longest = std::max(longest, c->h_mem_n[m]);
+        a.adv_threads = (longest + 31) / 32 * 32;
+    }
     a.fu = reinterpret_cast<const int4*>(d_fu);
     a.au = reinterpret_cast<const int4*>(d_au);
     a.au_ligs = reinterpret_cast<const int4*>(d_au_ligs);

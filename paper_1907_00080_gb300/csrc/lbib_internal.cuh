@@ -136,6 +136,7 @@ struct MarkerArgs {
     // cuts every membrane into chunks of kChunkV vertices, the advance kernel
     // cuts kinematic membranes the same way and keeps rigid-projected ones whole
     int nfu, nau;
+    int adv_threads;          // threads per advance block: 64, or the longest rigid ring rounded up to a warp
     const int4* fu;           // [nfu][2]: {m, k0, kn, off} {n, kind, lig0, nlig} (see kUnitInts)
     const int4* au;           // [nau][2], same records
     // bonds
