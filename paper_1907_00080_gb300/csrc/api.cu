@@ -353,12 +353,13 @@ static lbib_status finalize(lbib_ctx* c) {
     }
     // work units, kUnitInts ints each (one 32-byte read per block):
     // {membrane, first local vertex, vertex count, membrane offset, membrane size,
-    //  kind, first ligand record, ligand records}
+    //  kind, then for force units the membrane's first segment, for advance
+    //  units the first ligand record and the number of ligand records}
     std::vector<int> fu, au;
     for (int m = 0; m < nm; ++m) {
         const int n = c->h_mem_n[m], off = c->h_mem_off[m], kind = c->h_mem_kind[m];
         for (int k0 = 0; k0 < n; k0 += kChunkV) {
-            fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
+            fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, mem_seg_off[m], 0});
             if (kind != LBIB_MEMBRANE_RIGID_PROJECTED)
                 au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
         }
@@ -397,7 +398,7 @@ static lbib_status finalize(lbib_ctx* c) {
         probe.base = nullptr;
         auto add = [&](size_t b) { probe.used = ((probe.used + 255) & ~size_t(255)) + (b ? b : 1); };
         add(4 * (nm + 1)); add(4 * (nm + 1)); add(4 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1));
-        add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
+        add(8 * (nm + 1)); add(8 * (nm + 1)); add(8 * (nm + 1)); add(4 * (nm + 2));
         add(16 * nv); add(16 * nv); add(2 * cs * nv); add(2 * cs * nv); add(9 * cs * nv); add(8 * nv);
         add(32 * nv); add(4 * nv); add(16 * nv + 16 * nr);
         add(4 * c->nseg); add(4 * c->nseg); add(4 * c->nseg); add(16 * c->nseg); add(4 * (nm + 1));
@@ -427,6 +428,7 @@ static lbib_status finalize(lbib_ctx* c) {
     double* kb = ar.take<double>(nm + 1);
     double* ka = ar.take<double>(nm + 1);
     double* A0 = ar.take<double>(nm + 1);
+    double* qa = ar.take<double>(nm + 1);
     int* lig_off = ar.take<int>(nm + 2);
     a.X = ar.take<double>(2 * (size_t)nv);   // 16 bytes per vertex in either layout
     a.Xp = ar.take<double>(2 * (size_t)nv);
@@ -536,7 +538,7 @@ static lbib_status finalize(lbib_ctx* c) {
     }
 
     a.mem_off = mem_off; a.mem_n = mem_n; a.mem_kind = mem_kind;
-    a.mem_ks = ks; a.mem_kb = kb; a.mem_ka = ka; a.mem_A0 = A0; a.mem_lig_off = lig_off;
+    a.mem_ks = ks; a.mem_kb = kb; a.mem_ka = ka; a.mem_A0 = A0; a.mem_qa = qa; a.mem_lig_off = lig_off;
     a.rest = rest; a.elem_lig = elig;
     a.d_rep = c->d_rep; a.nseg = c->nseg;
     a.seg_mem = d_seg_mem; a.seg_v0 = d_seg_v0; a.seg_n = d_seg_n; a.mem_seg_off = d_mem_seg_off;
@@ -574,7 +576,7 @@ static lbib_status finalize(lbib_ctx* c) {
     a.ux = c->ux; a.uy = c->uy;
 
     if (nm > 0) {
-        CK(launch_rest(c->prec, a, rest, A0, c->stream));
+        CK(launch_rest(c->prec, a, rest, A0, qa, c->stream));
         CK(launch_seg_boxes(c->prec, a, c->stream));
     }
     CK(cudaStreamSynchronize(c->stream));

@@ -19,7 +19,7 @@ namespace lbib {
 // rest turning angle theta_0), plus A_0 per membrane -- with the arithmetic the
 // force kernel repeats, so the rest shape gives exactly zero force.
 template <typename C>
-__global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0) {
+__global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0, double* qa) {
     using E = typename Ext<C>::E;
     const int m = blockIdx.x;
     const int off = a.mem_off[m], n = a.mem_n[m];
@@ -41,7 +41,11 @@ __global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0) {
     }
     if (threadIdx.x < 32 * kAreaWarps) {
         const E A = ring_area_group<C>(a, m, 0, red, 1);
-        if (threadIdx.x == 0) A0[m] = etod(A);
+        if (threadIdx.x == 0) {
+            const double A0m = etod(A);
+            A0[m] = A0m;
+            qa[m] = a.mem_ka[m] * (1.0 / 3.0) / A0m;  // k_a p_ref / A_0 (p_ref = 1/3)
+        }
     }
 }
 
@@ -235,36 +239,45 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         }
     } else if (wid < 5 + kAreaWarps) {
         // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
+        // c_a = -k_a (1 - A/A_0) p_ref = q (A - A_0), q = k_a p_ref / A_0 from set-up
+        const double A0 = a.mem_A0[m], q = a.mem_qa[m];
         const E A = ring_area_group<C>(a, m, 5, red, 1);
-        if (tid == 32 * 5) s_ca = C(-a.mem_ka[m] * (1.0 - etod(A) / a.mem_A0[m]) * (1.0 / 3.0));
+        if (tid == 32 * 5) s_ca = C(q * (etod(A) - A0));
     } else if (wid == 9) {
         // Eq. repFor screening, once per block: segments of other membranes whose
         // box comes within d_rep of this chunk's box (the union of its own
         // segments' boxes), appended in ascending segment order
         int cnt = 0;
         if (a.nmem > 1) {
-            const int sown0 = a.mem_seg_off[m] + k0 / kSegV;
+            const int sown0 = u1.z + k0 / kSegV;  // the unit record carries the membrane's first segment
             const int nown = (kn + kSegV - 1) / kSegV;  // <= kChunkV / kSegV <= 32
-            float4 o0 = a.seg_box[sown0];
-            float lo_x = 1e30f, hi_x = -1e30f, lo_y = 1e30f, hi_y = -1e30f;
-            if (lane < nown) {
-                const float4 o = a.seg_box[sown0 + lane];
-                const float dx = wrap_half(o.x - o0.x, a.f.nx);
-                float dy = o.y - o0.y;
-                if (!a.walls) dy = wrap_half(dy, a.f.ny);
-                lo_x = dx - o.z;
-                hi_x = dx + o.z;
-                lo_y = dy - o.w;
-                hi_y = dy + o.w;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                lo_x = fminf(lo_x, __shfl_xor_sync(kFull, lo_x, o));
-                hi_x = fmaxf(hi_x, __shfl_xor_sync(kFull, hi_x, o));
-                lo_y = fminf(lo_y, __shfl_xor_sync(kFull, lo_y, o));
-                hi_y = fmaxf(hi_y, __shfl_xor_sync(kFull, hi_y, o));
-            }
-            const float cbx = o0.x + 0.5f * (lo_x + hi_x), cby = o0.y + 0.5f * (lo_y + hi_y);
-            const float chx = 0.5f * (hi_x - lo_x), chy = 0.5f * (hi_y - lo_y);
+            // this chunk's own boxes; the chunk box is formed once the first batch
+            // of candidate boxes is in flight as well
+            const float4 o0 = a.seg_box[sown0];
+            const float4 own = lane < nown ? a.seg_box[sown0 + lane] : o0;
+            float cbx = 0.f, cby = 0.f, chx = 0.f, chy = 0.f;
+            auto chunk_box = [&]() {
+                float lo_x = 1e30f, hi_x = -1e30f, lo_y = 1e30f, hi_y = -1e30f;
+                if (lane < nown) {
+                    const float dx = wrap_half(own.x - o0.x, a.f.nx);
+                    float dy = own.y - o0.y;
+                    if (!a.walls) dy = wrap_half(dy, a.f.ny);
+                    lo_x = dx - own.z;
+                    hi_x = dx + own.z;
+                    lo_y = dy - own.w;
+                    hi_y = dy + own.w;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo_x = fminf(lo_x, __shfl_xor_sync(kFull, lo_x, o));
+                    hi_x = fmaxf(hi_x, __shfl_xor_sync(kFull, hi_x, o));
+                    lo_y = fminf(lo_y, __shfl_xor_sync(kFull, lo_y, o));
+                    hi_y = fmaxf(hi_y, __shfl_xor_sync(kFull, hi_y, o));
+                }
+                cbx = o0.x + 0.5f * (lo_x + hi_x);
+                cby = o0.y + 0.5f * (lo_y + hi_y);
+                chx = 0.5f * (hi_x - lo_x);
+                chy = 0.5f * (hi_y - lo_y);
+            };
             const float reach = a.f.d_rep + 2e-3f;
             auto screen = [&](int sg, int mem, const float4& b) {
                 bool hit = false;
@@ -293,6 +306,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
                         bm[it] = a.seg_mem[sg];
                     }
                 }
+                if (base == 0) chunk_box();
 #pragma unroll
                 for (int it = 0; it < kScreenIter; ++it)
                     if (base + 32 * it < a.nseg) screen(base + 32 * it + lane, bm[it], bx[it]);
@@ -505,9 +519,10 @@ __global__ void k_pos_out(const void* X, double* xy, int nv) {
 // ---------------------------------------------------------------- launchers
 static bool is_f64(lbib_precision p) { return p == LBIB_F64; }
 
-cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0, cudaStream_t s) {
-    if (is_f64(prec)) k_rest<double><<<a.nmem, 256, 0, s>>>(a, rest, A0);
-    else k_rest<float><<<a.nmem, 256, 0, s>>>(a, rest, A0);
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0, double* qa,
+                        cudaStream_t s) {
+    if (is_f64(prec)) k_rest<double><<<a.nmem, 256, 0, s>>>(a, rest, A0, qa);
+    else k_rest<float><<<a.nmem, 256, 0, s>>>(a, rest, A0, qa);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,7 @@ struct MarkerArgs {
     const double* mem_kb;
     const double* mem_ka;
     const double* mem_A0;
+    const double* mem_qa;     // [nmem] k_a p_ref / A_0: the area coefficient is mem_qa (A - A_0)
     const int* mem_lig_off;   // ligands of membrane m: [lig_off[m], lig_off[m+1])
     void* X;                  // [nv] current positions (unwrapped): double (x, y) in
                               // FP64 mode, float-float {x.hi, y.hi, x.lo, y.lo} otherwise
@@ -211,7 +212,7 @@ cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int n
 cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
                         int n_partials, double* out, float inv_scale, cudaStream_t s);
 // ib_kernels.cu
-cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0,
+cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, double* A0, double* qa,
                         cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
