@@ -398,50 +398,55 @@ def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
             "mlups_fused_kernel": nx * ny / (ms * 1e-3) / 1e6}
 
 
-def precision_forms(lbib, torch, stream, steps=1000, timed=2000):
+def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
     """Precision form: the fine capillary (2000 x 667, 4 red cells x 1700 + 3 rigid
     carriers x 210 markers) with populations stored in FP32, FP16 and BF16
     (shifted: d_i 2^k) against the FP64 run from the same inputs.  Errors after
-    `steps` time steps: velocity L2 and Linf relative to the FP64 field, marker
-    Linf in lattice units, bond-count difference; throughput over `timed`
-    further steps (CUDA events on the stream)."""
+    each checkpoint (time steps): velocity L2 and Linf relative to the FP64
+    field, marker Linf in lattice units, bond-count difference; throughput over
+    `timed` further steps (CUDA events on the stream)."""
     from paper_1907_00080_gb300 import inputs
-    res, ref = {}, None
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    res, ref = {}, {}
     for prec in ("f64", "f32", "f16", "bf16"):
         wl = inputs.fine_capillary_2000x667(prec)
         sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
+        r = {"tiling": list(sim.tiling), "storage_scale_exponent": int(lbib.lbib_storage_scale_exponent(sim.ctx))}
+        done = 0
         with torch.cuda.stream(stream):
-            sim.step(steps)
-            sim.sync()
-            _, ux, uy = sim.fields()
-            x = sim.markers()
-            nb = int((sim.bonds() >= 0).sum())
-            f = sim.populations()
+            for cp in checkpoints:
+                sim.step(cp - done)
+                done = cp
+                sim.sync()
+                _, ux, uy = sim.fields()
+                x = sim.markers()
+                nb = int((sim.bonds() >= 0).sum())
+                f = sim.populations()
+                e = {"max_abs_deviation": float(np.max(np.abs(f - w))), "bonds": nb}
+                if prec == "f64":
+                    ref[cp] = (ux, uy, x, nb)
+                else:
+                    rx = ref[cp]
+                    du = np.hypot(ux - rx[0], uy - rx[1])
+                    um = np.hypot(rx[0], rx[1])
+                    e.update(u_err_linf=float(du.max() / um.max()),
+                             u_err_l2=float(np.sqrt((du ** 2).sum() / (um ** 2).sum())),
+                             marker_err_linf_lu=float(np.max(np.abs(x - rx[2]))), bond_count_diff=nb - rx[3])
+                r["after_%d_steps" % cp] = e
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             sim.step(timed)
             e1.record(stream)
             sim.sync()
             ms = e0.elapsed_time(e1)
-        w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
-        r = {"mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "tiling": list(sim.tiling),
-             "storage_scale_exponent": int(lbib.lbib_storage_scale_exponent(sim.ctx)),
-             "max_abs_deviation": float(np.max(np.abs(f - w))), "bonds": nb}
-        if ref is None:
-            ref = (ux, uy, x, nb)
-        else:
-            du = np.hypot(ux - ref[0], uy - ref[1])
-            um = np.hypot(ref[0], ref[1])
-            r.update(u_err_linf=float(du.max() / um.max()),
-                     u_err_l2=float(np.sqrt((du ** 2).sum() / (um ** 2).sum())),
-                     marker_err_linf_lu=float(np.max(np.abs(x - ref[2]))), bond_count_diff=nb - ref[3])
+        r["mlups"] = wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6
         res[prec] = r
         sim.close()
     base = res["f32"]["mlups"]
     for prec in ("f16", "bf16"):
         res[prec]["speedup_vs_f32"] = res[prec]["mlups"] / base
     return {"workload": "fine capillary 2000x667 (dx = 15 nm), 4 RBC x 1700 + 3 rigid carriers x 210 markers",
-            "error_after_steps": steps, "timed_steps": timed, "results": res}
+            "checkpoints": list(checkpoints), "timed_steps": timed, "results": res}
 
 
 def ensemble_form(lbib, torch, stream, n=64, steps=400):
@@ -488,7 +493,7 @@ def ensemble_form(lbib, torch, stream, n=64, steps=400):
             "ensemble_ms_per_step": 1e3 * t_ens / steps, "sequential_ms_per_step": 1e3 * t_seq / steps}
 
 
-def differentiation_form(lbib, torch, steps=1000):
+def differentiation_form(lbib, torch, steps=5000):
     """Differentiation form: the 320 x 160 sensitivity case (2 red cells, a soft
     carrier released 1 lu above the wall), FP64: dJ/dp of the carrier's final
     height J1 and bond energy J2 with respect to (k_s, k_b, sigma, release

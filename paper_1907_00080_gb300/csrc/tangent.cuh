@@ -28,5 +28,8 @@ struct TangentArgs {
 };
 
 cudaError_t launch_tangent_step(const TangentArgs& t, cudaStream_t s);
+// the marker part alone (areas and boxes, forces, shape functions, spreading
+// into t.Gv / t.Gd, which the caller has zeroed)
+cudaError_t launch_tangent_markers(const TangentArgs& t, cudaStream_t s);
 
 }  // namespace lbib
