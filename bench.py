@@ -493,12 +493,14 @@ def ensemble_form(lbib, torch, stream, n=64, steps=400):
             "ensemble_ms_per_step": 1e3 * t_ens / steps, "sequential_ms_per_step": 1e3 * t_seq / steps}
 
 
-def differentiation_form(lbib, torch, steps=5000):
+def differentiation_form(lbib, torch, steps=5000, checkpoint_every=250):
     """Differentiation form: the 320 x 160 sensitivity case (2 red cells, a soft
     carrier released 1 lu above the wall), FP64: dJ/dp of the carrier's final
     height J1 and bond energy J2 with respect to (k_s, k_b, sigma, release
-    height) by four forward-mode tangent runs, timed against the plain FP64
-    solver over the same steps (host wall clock around synchronised calls)."""
+    height).  Reverse mode: one recorded run (checkpoints every 250 steps) and
+    one backward sweep per observable, each giving all four derivatives.
+    Forward mode: four tangent runs.  Both timed against the plain FP64 solver
+    over the same steps (host wall clock around synchronised calls)."""
     from paper_1907_00080_gb300 import sensitivity
     p0 = sensitivity.default_params()
     sensitivity.run(p0, 10)
@@ -507,13 +509,31 @@ def differentiation_form(lbib, torch, steps=5000):
     J, _ = sensitivity.run(p0, steps)
     t_primal = time.perf_counter() - t0
     t0 = time.perf_counter()
+    rec = sensitivity.Recording(p0, steps, checkpoint_every=checkpoint_every)
+    t_rec = time.perf_counter() - t0
+    try:
+        t0 = time.perf_counter()
+        g1 = rec.gradient((1.0, 0.0))
+        t_sweep = time.perf_counter() - t0
+        g2 = rec.gradient((0.0, 1.0))
+    finally:
+        rec.close()
+    jac_a = np.stack([g1, g2])
+    t0 = time.perf_counter()
     J2, jac, bonds = sensitivity.jacobian(p0, steps)
     t_jac = time.perf_counter() - t0
+    rel = [float(np.max(np.abs(jac_a[i] - jac[i]) / np.maximum(np.abs(jac[i]), 1e-300))) for i in range(2)]
     return {"workload": "320x160, 2 RBC x 200 + 1 soft carrier x 50 markers, FP64", "steps": steps,
             "params": list(sensitivity.PARAMS), "J": [float(v) for v in J],
-            "dJ_dp": [[float(v) for v in row] for row in jac], "bonds_at_end": int((bonds >= 0).sum()),
-            "primal_ms_per_step": 1e3 * t_primal / steps, "jacobian_ms_per_step": 1e3 * t_jac / steps,
-            "tangent_cost_per_direction_vs_primal": t_jac / 4 / t_primal}
+            "dJ_dp": [[float(v) for v in row] for row in jac_a], "bonds_at_end": int((bonds >= 0).sum()),
+            "primal_ms_per_step": 1e3 * t_primal / steps,
+            "adjoint": {"checkpoint_every": checkpoint_every, "record_ms_per_step": 1e3 * t_rec / steps,
+                        "sweep_ms_per_step": 1e3 * t_sweep / steps,
+                        "gradient_cost_vs_primal": (t_rec + t_sweep) / t_primal,
+                        "max_rel_diff_vs_tangent": rel},
+            "tangent": {"jacobian_ms_per_step": 1e3 * t_jac / steps,
+                        "cost_per_direction_vs_primal": t_jac / 4 / t_primal,
+                        "gradient_cost_vs_primal": t_jac / 4 / t_primal * 4}}
 
 
 def end_to_end(lbib, torch, wl, tiling, stream, T, steps):

@@ -238,6 +238,53 @@ lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n);
 lbib_status lbib_tangent_read(lbib_tangent* t, double* dxy, double* dxy_prev);
 void lbib_tangent_destroy(lbib_tangent* t);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse-mode derivative of an FP64 trajectory: the transpose of the tangent
+ * above, with the same bond history held fixed.  For a scalar J of the final
+ * state (X^N, X^{N-1}, f^N) it returns, in one backward sweep, dJ/dk_s and
+ * dJ/dk_b of every membrane, dJ/dsigma and dJ/d(X^0, X^{-1}, f^0) -- the
+ * gradient with respect to all parameters at the cost of about one tangent
+ * direction.  The paper has no derivative; this serves the same sensitivity
+ * studies as the tangent when there are many parameters.
+ *
+ * Memory: the full step state (populations, X^n, X^{n-1}, bonds, receptor
+ * occupancy, step counter) every `checkpoint_every` steps, plus a tape of one
+ * segment (checkpoint_every copies of the populations, positions and bonds).
+ * The backward sweep re-runs each segment from its checkpoint with the
+ * context's own step (bit-identical to the recorded run) and then applies the
+ * adjoint step to the tape in reverse order.
+ *
+ * lbib_adjoint_create: ctx must be LBIB_F64, without rigid-projected
+ *   membranes and with at least 5 vertices per membrane (LBIB_E_INVALID
+ *   otherwise); checkpoint_every >= 1; LBIB_E_OOM if the tape does not fit.
+ *   The adjoint borrows the context (destroy the adjoint first).
+ * lbib_adjoint_record: advance the context n >= 1 steps (instead of
+ *   lbib_step) from its current state, keeping the checkpoints; replaces an
+ *   earlier recording; synchronises and returns the step status.
+ * lbib_adjoint_seed: dJ/dX^N and dJ/dX^{N-1} (2*nv doubles each, host, NULL =
+ *   0) and dJ/df^N (9*NY*NX doubles, host, layout of lbib_read_populations,
+ *   NULL = 0) at the end of the recording; clears the parameter gradients.
+ *   LBIB_E_STATE before a recording.
+ * lbib_adjoint_reverse: the backward sweep over the recorded steps; the
+ *   context is left in the state the recording ended in.  LBIB_E_STATE unless
+ *   seeded since the last sweep.  Synchronises.
+ * lbib_adjoint_read: dJ/dX^0, dJ/dX^{-1} (2*nv doubles), dJ/dk_s, dJ/dk_b
+ *   (nmem doubles), dJ/dsigma (1 double), dJ/df^0 (9*NY*NX doubles, layout of
+ *   lbib_read_populations) into host arrays; any pointer may be NULL.  Here 0
+ *   is the first recorded step.  Synchronises.
+ * lbib_adjoint_recorded_steps: N of the last recording (0 before, -1 for NULL).
+ */
+typedef struct lbib_adjoint lbib_adjoint;
+lbib_status lbib_adjoint_create(lbib_ctx* ctx, int32_t checkpoint_every, lbib_adjoint** out);
+lbib_status lbib_adjoint_record(lbib_adjoint* adj, int64_t n);
+lbib_status lbib_adjoint_seed(lbib_adjoint* adj, const double* xy_bar, const double* xy_prev_bar,
+                              const double* f_bar);
+lbib_status lbib_adjoint_reverse(lbib_adjoint* adj);
+lbib_status lbib_adjoint_read(lbib_adjoint* adj, double* xy_bar, double* xy_prev_bar, double* ks_bar,
+                              double* kb_bar, double* sigma_bar, double* f_bar);
+int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* adj);
+void lbib_adjoint_destroy(lbib_adjoint* adj);
+
 /* Allocation-free FP64 mass of a population buffer the caller owns.  The
  * paper has no counterpart: this is a library service for callers that must not
  * allocate device memory at the time of the call, e.g. a monitor running between

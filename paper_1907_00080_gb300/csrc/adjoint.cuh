@@ -1,0 +1,40 @@
+// Arguments of the reverse-mode (adjoint) step kernels (adjoint_kernels.cu).
+//
+// One FP64 time step maps S^n = (d*^{n-1}, X^n, X^{n-1}) to S^{n+1}; its
+// adjoint maps the adjoints of S^{n+1} to those of S^n and adds the step's
+// share of dJ/dk_s, dJ/dk_b and dJ/dsigma.  The primal quantities of step n
+// (areas, forces, shape functions, spread force) are re-evaluated from the
+// recorded state by the tangent kernels with a zero tangent; the bond set of
+// step n is the recorded one (bond events are not differentiated).
+#pragma once
+
+#include "tangent.cuh"
+
+namespace lbib {
+
+struct AdjointArgs {
+    TangentArgs t;        // primal evaluation at step n: t.f = d*^{n-1}, t.m.X = X^n, t.m.bond_of_lig
+                          // = bonds of step n; t.Gv, t.Fv, t.Wv, t.st, t.A filled by the tangent kernels
+    const double* fbar;   // [9][N] adjoint of d*^n (the deviations step n stores)
+    double* fbar_out;     // [9][N] adjoint of d*^{n-1}; every entry is written
+    double* XB;           // [nv][2] in: adjoint of X^{n+1}; out: adjoint of X^n
+    double* XPB;          // [nv][2] in: adjoint of X^n as the previous position of step n+1;
+                          //          out: adjoint of X^{n-1}
+    double* ubar;         // [N][2] adjoint of the interpolated velocity field (zero between steps)
+    double* Gbar;         // [N][2] adjoint of the spread force
+    double* Fbar;         // [nv][2] adjoint of the marker forces
+    double* Wbar;         // [nv][9] adjoint of the shape functions
+    double* Abar;         // [nmem] adjoint of the enclosed areas
+    double* ks_bar;       // [nmem] accumulated dJ/dk_s
+    double* kb_bar;       // [nmem] accumulated dJ/dk_b
+    double* sigma_bar;    // [1] accumulated dJ/dsigma
+};
+
+cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
+
+// adjoint of the stored deviations <-> adjoint of the pre-collision
+// populations in the read-back layout (f^n_i(x) = w_i + d*_i(source of (x, i)))
+cudaError_t launch_adjoint_perm(const double* in, double* out, int nx, int ny, int walls, int to_storage,
+                                cudaStream_t s);
+
+}  // namespace lbib

@@ -1,0 +1,378 @@
+// Reverse-mode (adjoint) step of the FP64 time step.
+//
+// Transposes, in reverse order, the parts of one step (Sec. 2.1 - 2.4):
+//   interpolation                                      -> k_a_interp
+//   moments + Guo-forced BGK collision and pull stream -> k_a_collide
+//   spreading, BDF2 advance (Euler on step 0)          -> k_a_spread
+//   membrane, bond and repulsion forces, MLS/Roma
+//   shape functions                                    -> k_a_forces
+//   enclosed area                                      -> k_a_area
+// The lattice part (every node, FP64) is written out by hand: the collision
+// is (1 - omega) d_i plus a function of five scalars (drho, j, G), and its
+// transpose costs about as much as the collision itself.  The per-vertex parts
+// (a few thousand vertices) take local Jacobian columns from the dual-number
+// functions of the tangent (one-hot seeds), so they share their arithmetic
+// with the forward-mode derivative.
+#include "adjoint.cuh"
+#include "lb_node.cuh"
+#include "tangent_ops.cuh"
+
+namespace lbib {
+namespace {
+
+// Transpose of collide_node<double> at one node.  d: pulled deviations, (Gx, Gy)
+// total force; yb: adjoints of the nine outputs d*_i, (ubx, uby) adjoint of the
+// velocity output.  Returns the adjoints of d and of G.  With eu_i = e_i.u and
+// eG_i = e_i.G every output is
+//   d*_i = (1 - omega) d_i + w_i [a + b eu_i + c eu_i^2 + g eG_i + h eu_i eG_i],
+//   a = omega drho - 1.5 omega rho u.u - 3 pre u.G,  b = 3 omega rho,
+//   c = 4.5 omega rho,  g = 3 pre,  h = 9 pre,
+//   u = (j + G/2) / rho,  rho = 1 + drho,  drho = sum d_i,  j = sum e_i d_i.
+__device__ __forceinline__ void collide_node_rev(const double (&d)[9], double Gx, double Gy, double om, double pre,
+                                                 const double (&yb)[9], double ubx, double uby, double (&db)[9],
+                                                 double& Gbx, double& Gby) {
+    double drho = 0.0, jx = 0.0, jy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        drho += d[i];
+        jx += cx(i) * d[i];
+        jy += cy(i) * d[i];
+    }
+    const double rho = 1.0 + drho, r = 1.0 / rho;
+    const double px = jx + 0.5 * Gx, py = jy + 0.5 * Gy;
+    const double ux = px * r, uy = py * r;
+    const double uu = ux * ux + uy * uy;
+    const double omr = om * rho;
+    const double b = 3.0 * omr, c = 4.5 * omr, g = 3.0 * pre, h = 9.0 * pre;
+    // adjoints of a, b, c and of u, G through eu_i, eG_i
+    double Sa = 0.0, Sb = 0.0, Sc = 0.0;
+    double uxb = ubx, uyb = uby;
+    Gbx = 0.0;
+    Gby = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double wy = wgt<double>(i) * yb[i];
+        const double eu = cx(i) * ux + cy(i) * uy, eG = cx(i) * Gx + cy(i) * Gy;
+        Sa += wy;
+        Sb += wy * eu;
+        Sc += wy * eu * eu;
+        const double deu = wy * (b + 2.0 * c * eu + h * eG);
+        const double deG = wy * (g + h * eu);
+        uxb += cx(i) * deu;
+        uyb += cy(i) * deu;
+        Gbx += cx(i) * deG;
+        Gby += cy(i) * deG;
+    }
+    // a, b, c -> drho, rho, u.u, u.G
+    double drhob = om * Sa;
+    double rhob = -1.5 * om * uu * Sa + 3.0 * om * Sb + 4.5 * om * Sc;
+    const double uub = -1.5 * omr * Sa, uGb = -3.0 * pre * Sa;
+    uxb += 2.0 * ux * uub + Gx * uGb;
+    uyb += 2.0 * uy * uub + Gy * uGb;
+    Gbx += ux * uGb;
+    Gby += uy * uGb;
+    // u = (j + G/2) r,  r = 1/rho,  rho = 1 + drho
+    const double jxb = r * uxb, jyb = r * uyb;
+    Gbx += 0.5 * r * uxb;
+    Gby += 0.5 * r * uyb;
+    rhob -= r * r * (px * uxb + py * uyb);
+    drhob += rhob;
+    const double omc = 1.0 - om;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) db[i] = omc * yb[i] + drhob + cx(i) * jxb + cy(i) * jyb;
+}
+
+// velocity output of the collision at `node` (the field the markers interpolate)
+__device__ __forceinline__ void node_velocity(const TangentArgs& t, size_t node, double& ux, double& uy) {
+    const int nx = t.m.nx, ny = t.m.ny;
+    double d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = t.f[t_pull_src(node, i, nx, ny, t.m.walls)];
+    double out[9], rho;
+    collide_node<double>(d, t.gx + t.Gv[2 * node], t.gy + t.Gv[2 * node + 1], t.omega, 1.0 - 0.5 * t.omega, out, rho,
+                         ux, uy);
+}
+
+// BDF2 coefficients of X^{n+1} = ca X^n + cb X^{n-1} + cu U^n (Euler on step 0)
+struct Bdf2 {
+    double ca, cb, cu;
+};
+__device__ __forceinline__ Bdf2 bdf2(long long step) {
+    return step == 0 ? Bdf2{1.0, 0.0, 1.0} : Bdf2{4.0 / 3.0, -1.0 / 3.0, 2.0 / 3.0};
+}
+
+// Adjoint of the interpolation U_v = sum_k W_vk u(x_k), with U_v-bar = cu X_v^{n+1}-bar:
+// the velocity adjoint is scattered onto the nodes, and W_vk-bar = U_v-bar . u(x_k).
+// One thread per (vertex, stencil entry k = blockIdx.y).
+__global__ void k_a_interp(const AdjointArgs a) {
+    const TangentArgs& t = a.t;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (v == 0 && k == 0)
+        for (int m = 0; m < t.m.nmem; ++m) a.Abar[m] = 0.0;
+    if (v >= t.m.nv) return;
+    const double cu = bdf2(t.step).cu;
+    const double Ubx = cu * a.XB[2 * v], Uby = cu * a.XB[2 * v + 1];
+    const int i0 = t.st[2 * v], j0 = t.st[2 * v + 1];
+    double wb = 0.0;
+    if (!(t.m.walls && (j0 + k / 3 - 1 < 0 || j0 + k / 3 - 1 >= t.m.ny))) {
+        const size_t node = t_node(t, i0, j0, k);
+        const double w = t.Wv[9 * v + k];
+        double ux, uy;
+        node_velocity(t, node, ux, uy);
+        atomicAdd(&a.ubar[2 * node], w * Ubx);
+        atomicAdd(&a.ubar[2 * node + 1], w * Uby);
+        wb = Ubx * ux + Uby * uy;
+    }
+    a.Wbar[9 * v + k] = wb;
+}
+
+// Adjoint of the collision and of the pull stream at every node.  The pull is a
+// permutation of the stored values, so each adjoint entry has exactly one
+// writer.  Also clears this step's u-bar and spread force for the next step.
+__global__ void k_a_collide(const AdjointArgs a) {
+    const TangentArgs& t = a.t;
+    const int nx = t.m.nx, ny = t.m.ny;
+    const size_t N = (size_t)nx * ny;
+    const double om = t.omega, pre = 1.0 - 0.5 * t.omega;
+    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < N;
+         node += (size_t)gridDim.x * blockDim.x) {
+        size_t src[9];
+        double d[9], yb[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            src[i] = t_pull_src(node, i, nx, ny, t.m.walls);
+            d[i] = t.f[src[i]];
+            yb[i] = a.fbar[(size_t)i * N + node];
+        }
+        const double gsx = t.Gv[2 * node], gsy = t.Gv[2 * node + 1];
+        const double ubx = a.ubar[2 * node], uby = a.ubar[2 * node + 1];
+        double db[9], Gbx, Gby;
+        collide_node_rev(d, t.gx + gsx, t.gy + gsy, om, pre, yb, ubx, uby, db, Gbx, Gby);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) a.fbar_out[src[i]] = db[i];
+        a.Gbar[2 * node] = Gbx;
+        a.Gbar[2 * node + 1] = Gby;
+        if (ubx != 0.0 || uby != 0.0) {
+            a.ubar[2 * node] = 0.0;
+            a.ubar[2 * node + 1] = 0.0;
+        }
+        if (gsx != 0.0 || gsy != 0.0) {
+            t.Gv[2 * node] = 0.0;
+            t.Gv[2 * node + 1] = 0.0;
+        }
+    }
+}
+
+// Adjoint of the spreading G(x_k) += W_vk F_v: F_v-bar and the shape
+// functions' share W_vk-bar += G-bar(x_k) . F_v.
+__global__ void k_a_spread(const AdjointArgs a) {
+    const TangentArgs& t = a.t;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= t.m.nv) return;
+    const int i0 = t.st[2 * v], j0 = t.st[2 * v + 1];
+    const double Fx = t.Fv[2 * v], Fy = t.Fv[2 * v + 1];
+    double Fbx = 0.0, Fby = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        if (t.m.walls && (j0 + k / 3 - 1 < 0 || j0 + k / 3 - 1 >= t.m.ny)) continue;
+        const size_t node = t_node(t, i0, j0, k);
+        const double w = t.Wv[9 * v + k];
+        const double gbx = a.Gbar[2 * node], gby = a.Gbar[2 * node + 1];
+        Fbx += w * gbx;
+        Fby += w * gby;
+        a.Wbar[9 * v + k] += gbx * Fx + gby * Fy;
+    }
+    a.Fbar[2 * v] = Fbx;
+    a.Fbar[2 * v + 1] = Fby;
+    // the BDF2 part of the advance adjoint: X^n-bar = X^n-slot-bar + ca X^{n+1}-bar,
+    // X^{n-1}-bar = cb X^{n+1}-bar (the interpolation share was taken above)
+    const Bdf2 q = bdf2(t.step);
+    for (int c = 0; c < 2; ++c) {
+        const double xb = a.XB[2 * v + c], xpb = a.XPB[2 * v + c];
+        a.XB[2 * v + c] = xpb + q.ca * xb;
+        a.XPB[2 * v + c] = q.cb * xb;
+    }
+}
+
+// Tasks of k_a_forces (blockIdx.y), one dual evaluation each
+enum AdjTask {
+    kTaskPos0 = 0,      // 0..9: coordinate (task & 1) of vertex v - 2 + task / 2
+    kTaskArea = 10,
+    kTaskKs = 11,
+    kTaskKb = 12,
+    kTaskSigma = 13,
+    kTaskRep = 14,      // the repulsion pairs of v
+    kTaskWx = 15,       // shape functions of v against x_v, y_v
+    kTaskWy = 16,
+    kNumTasks = 17
+};
+
+// Adjoint of the total Lagrangian force on vertex v and of its shape functions.
+// Bonds, stretching, bending and the area penalty depend on X_{v-2} .. X_{v+2},
+// the membrane's area, k_s, k_b and sigma: one dual evaluation per seed gives
+// the column dF_v/d(seed), and F_v-bar . column is added to that input's
+// adjoint.  The repulsion -sum_b c0 d_vb^{-5/2} n_v (Eq. repFor) is transposed
+// pair by pair: through d_vb into X_v and X_b, and through the vertex normal n_v
+// into X_{v-1}, X_v, X_{v+1}.  The shape functions of v depend on X_v alone
+// (two seeds).  Each (vertex, task) is one thread: the FP64 chains are long,
+// and one thread per vertex would leave most SMs idle.
+__global__ void k_a_forces(const AdjointArgs a) {
+    const TangentArgs& t = a.t;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int task = blockIdx.y;
+    if (v >= t.m.nv) return;
+    if (task == kTaskWx || task == kTaskWy) {
+        dual w[9];
+        bool in[9];
+        int si, sj;
+        const int c = task - kTaskWx;
+        t_vertex_weights(t, v, Seed{kPos, v, c, -1}, w, in, si, sj);
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k)
+            if (in[k]) acc += a.Wbar[9 * v + k] * w[k].d;
+        atomicAdd(&a.XB[2 * v + c], acc);
+        return;
+    }
+    const double Fbx = a.Fbar[2 * v], Fby = a.Fbar[2 * v + 1];
+    if (Fbx == 0.0 && Fby == 0.0) return;
+    const int m = t_mem_of(t, v);
+    const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
+    dual fx, fy;
+    if (task < kTaskArea) {
+        const int u = t_ring(off, n, k - 2 + task / 2), c = task & 1;
+        t_vertex_force(t, v, m, Seed{kPos, u, c, -1}, fx, fy, false);
+        atomicAdd(&a.XB[2 * u + c], Fbx * fx.d + Fby * fy.d);
+        return;
+    }
+    if (task == kTaskArea) {
+        t_vertex_force(t, v, m, Seed{kArea, -1, 0, m}, fx, fy, false);
+        atomicAdd(&a.Abar[m], Fbx * fx.d + Fby * fy.d);
+        return;
+    }
+    if (task == kTaskKs) {
+        t_vertex_force(t, v, m, Seed{kKs, -1, 0, m}, fx, fy, false);
+        atomicAdd(&a.ks_bar[m], Fbx * fx.d + Fby * fy.d);
+        return;
+    }
+    if (task == kTaskKb) {
+        t_vertex_force(t, v, m, Seed{kKb, -1, 0, m}, fx, fy, false);
+        atomicAdd(&a.kb_bar[m], Fbx * fx.d + Fby * fy.d);
+        return;
+    }
+    if (task == kTaskSigma) {
+        if (t.m.nlig > 0) {
+            t_vertex_force(t, v, m, Seed{kSigma, -1, 0, -1}, fx, fy, false);
+            atomicAdd(a.sigma_bar, Fbx * fx.d + Fby * fy.d);
+        }
+        return;
+    }
+    // kTaskRep
+    if (t.m.nmem < 2) return;
+    const double* X = static_cast<const double*>(t.m.X);
+    const double xv = X[2 * v], yv = X[2 * v + 1];
+    bool have_g = false;
+    VGeo g;
+    double nbx = 0.0, nby = 0.0, xvb = 0.0, yvb = 0.0;
+    for (int mb = 0; mb < t.m.nmem; ++mb) {
+        if (mb == m || !t_near_box(t, mb, xv, yv)) continue;
+        if (!have_g) {
+            g = t_vgeo(t, off, n, k, tangent_seed());
+            have_g = true;
+        }
+        const double gnx = g.nx.v, gny = g.ny.v;
+        const int o2 = t.m.mem_off[mb], n2 = t.m.mem_n[mb];
+        for (int b = o2; b < o2 + n2; ++b) {
+            if (!t_rep_candidate(t, xv, yv, b)) continue;
+            const double dxv = t_wrap_x(t, dual(xv - X[2 * b])).v;
+            const double dyv = t_wrap_y(t, dual(yv - X[2 * b + 1])).v;
+            // magnitude and its two partials with respect to (dx, dy)
+            const dual ddx = sqrt(dual(dxv, 1.0) * dual(dxv, 1.0) + dual(dyv) * dual(dyv));
+            if (ddx.v >= t.m.d_rep) continue;
+            const dual ddy = sqrt(dual(dxv) * dual(dxv) + dual(dyv, 1.0) * dual(dyv, 1.0));
+            const dual mx = kRepC0 * pow_m52(ddx), my = kRepC0 * pow_m52(ddy);
+            // F_v -= mag n_v
+            nbx -= mx.v * Fbx;
+            nby -= mx.v * Fby;
+            const double magb = -(Fbx * gnx + Fby * gny);
+            const double gx = magb * mx.d, gy = magb * my.d;
+            xvb += gx;
+            yvb += gy;
+            atomicAdd(&a.XB[2 * b], -gx);
+            atomicAdd(&a.XB[2 * b + 1], -gy);
+        }
+    }
+    if (!have_g) return;
+    atomicAdd(&a.XB[2 * v], xvb);
+    atomicAdd(&a.XB[2 * v + 1], yvb);
+    if (nbx == 0.0 && nby == 0.0) return;
+    for (int dk = -1; dk <= 1; ++dk) {
+        const int u = t_ring(off, n, k + dk);
+        for (int c = 0; c < 2; ++c) {
+            const VGeo gs = t_vgeo(t, off, n, k, Seed{kPos, u, c, -1});
+            atomicAdd(&a.XB[2 * u + c], nbx * gs.nx.d + nby * gs.ny.d);
+        }
+    }
+}
+
+// Adjoint of the enclosed area (shoelace): dA/dx_v = (y_{v+1} - y_{v-1}) / 2,
+// dA/dy_v = (x_{v-1} - x_{v+1}) / 2.
+__global__ void k_a_area(const AdjointArgs a) {
+    const TangentArgs& t = a.t;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= t.m.nv) return;
+    const int m = t_mem_of(t, v);
+    const double Ab = a.Abar[m];
+    if (Ab == 0.0) return;
+    const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
+    const double* X = static_cast<const double*>(t.m.X);
+    const int L = t_ring(off, n, k - 1), R = t_ring(off, n, k + 1);
+    atomicAdd(&a.XB[2 * v], 0.5 * Ab * (X[2 * R + 1] - X[2 * L + 1]));
+    atomicAdd(&a.XB[2 * v + 1], 0.5 * Ab * (X[2 * L] - X[2 * R]));
+}
+
+// read-back layout <-> stored deviations (a permutation; the constant w_i of the
+// read-back has no adjoint)
+__global__ void k_a_perm(const double* __restrict__ in, double* __restrict__ out, int nx, int ny, int walls,
+                         int to_storage) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t node = blockIdx.x * (size_t)blockDim.x + threadIdx.x; node < N;
+         node += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const size_t src = t_pull_src(node, i, nx, ny, walls);
+            if (to_storage) out[src] = in[(size_t)i * N + node];
+            else out[(size_t)i * N + node] = in[src];
+        }
+    }
+}
+
+int node_grid(size_t N) { return (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096); }
+
+}  // namespace
+
+cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
+    const TangentArgs& t = a.t;
+    const size_t N = (size_t)t.m.nx * t.m.ny;
+    const int nvb = (t.m.nv + 31) / 32;
+    cudaError_t e;
+    if (t.m.nv > 0) {
+        // primal areas, forces, shape functions and spread force of step n
+        if ((e = launch_tangent_markers(t, s)) != cudaSuccess) return e;
+        k_a_interp<<<dim3(nvb, 9), 32, 0, s>>>(a);
+    }
+    k_a_collide<<<node_grid(N), 256, 0, s>>>(a);
+    if (t.m.nv > 0) {
+        k_a_spread<<<nvb, 32, 0, s>>>(a);
+        k_a_forces<<<dim3(nvb, kNumTasks), 32, 0, s>>>(a);
+        k_a_area<<<nvb, 32, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_perm(const double* in, double* out, int nx, int ny, int walls, int to_storage,
+                                cudaStream_t s) {
+    k_a_perm<<<node_grid((size_t)nx * ny), 256, 0, s>>>(in, out, nx, ny, walls, to_storage);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "lbib_internal.cuh"
+#include "adjoint.cuh"
 #include "tangent.cuh"
 
 using namespace lbib;
@@ -1275,3 +1276,321 @@ extern "C" lbib_status lbib_tangent_read(lbib_tangent* t, double* dxy, double* d
     CK(cudaStreamSynchronize(c->stream));
     return lbib_sync(c);
 }
+
+// ------------------------------------------------------------------ adjoint
+// Reverse-mode derivative of an FP64 context's trajectory (the transpose of
+// the tangent above).  lbib_adjoint_record runs the primal and keeps the full
+// step state every K steps; lbib_adjoint_reverse walks the segments backwards:
+// it restores a segment's first state, re-runs the segment with the context's
+// own step graph (bit-identical to the recorded run: fixed-point spreading and
+// counter-based bond draws) while copying each step's state to a tape, then
+// applies the adjoint step to the tape in reverse order.
+namespace {
+
+// the context's full step state at a step boundary (FP64 storage)
+struct Snap {
+    void* mem = nullptr;
+    double *f = nullptr, *X = nullptr, *Xp = nullptr;
+    int *bond = nullptr, *owner = nullptr, *owner_cell = nullptr;
+    float4* seg_box = nullptr;
+    long long* d_step = nullptr;
+    long long step = 0;
+};
+
+size_t snap_bytes(const lbib_ctx* c) {
+    Arena a;
+    const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
+    a.take<double>(9 * N);
+    a.take<double>(2 * nv);
+    a.take<double>(2 * nv);
+    a.take<int>(nlig);
+    a.take<int>(nrec);
+    a.take<int>(nrec);
+    a.take<float4>(c->nseg);
+    a.take<long long>(1);
+    return a.used + 256;
+}
+
+void snap_layout(const lbib_ctx* c, Snap& s) {
+    Arena a;
+    a.base = static_cast<char*>(s.mem);
+    const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
+    s.f = a.take<double>(9 * N);
+    s.X = a.take<double>(2 * nv);
+    s.Xp = a.take<double>(2 * nv);
+    s.bond = a.take<int>(nlig);
+    s.owner = a.take<int>(nrec);
+    s.owner_cell = a.take<int>(nrec);
+    s.seg_box = a.take<float4>(c->nseg);
+    s.d_step = a.take<long long>(1);
+}
+
+// copy the state between the context and a snapshot (to_snap: context -> snapshot)
+cudaError_t snap_copy(lbib_ctx* c, Snap& s, bool to_snap) {
+    const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
+    auto cp = [&](void* snap, void* ctx, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        return cudaMemcpyAsync(to_snap ? snap : ctx, to_snap ? ctx : snap, bytes, cudaMemcpyDeviceToDevice,
+                               c->stream);
+    };
+    cudaError_t e;
+    if ((e = cp(s.f, c->f[c->cur], 9 * N * 8)) != cudaSuccess) return e;
+    if ((e = cp(s.X, c->ma.X, 16 * nv)) != cudaSuccess) return e;
+    if ((e = cp(s.Xp, c->ma.Xp, 16 * nv)) != cudaSuccess) return e;
+    if ((e = cp(s.bond, c->ma.bond_of_lig, 4 * nlig)) != cudaSuccess) return e;
+    if ((e = cp(s.owner, c->ma.owner, 4 * nrec)) != cudaSuccess) return e;
+    if ((e = cp(s.owner_cell, c->ma.owner_cell, 4 * nrec)) != cudaSuccess) return e;
+    if ((e = cp(s.seg_box, c->ma.seg_box, sizeof(float4) * c->nseg)) != cudaSuccess) return e;
+    if ((e = cp(s.d_step, c->d_step, 8)) != cudaSuccess) return e;
+    if (to_snap) s.step = c->steps;
+    else c->steps = s.step;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+struct lbib_adjoint {
+    lbib_ctx* c = nullptr;  // primal (not owned)
+    int K = 0;              // checkpoint interval (steps per segment)
+    std::vector<Snap> snaps;  // state at the first step of each recorded segment
+    Snap end;                 // state after the recorded run
+    int64_t n_rec = 0;
+    bool seeded = false, reversed = false;
+    // tape of one segment: deviations, positions and bonds of each of its steps
+    double* tape_f = nullptr;
+    double* tape_X = nullptr;
+    int* tape_bond = nullptr;
+    // adjoint state and per-step work arrays
+    double* fbar[2] = {nullptr, nullptr};
+    int cb = 0;
+    double *XB = nullptr, *XPB = nullptr, *ubar = nullptr, *Gbar = nullptr, *Fbar = nullptr, *Wbar = nullptr;
+    double *Abar = nullptr, *ksb = nullptr, *kbb = nullptr, *sgb = nullptr, *fio = nullptr;
+    // primal re-evaluation of the marker part (tangent buffers, zero tangent)
+    double *Gv = nullptr, *Gd = nullptr, *Wv = nullptr, *Wd = nullptr, *Fv = nullptr, *Fd = nullptr;
+    double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr;
+    int* st = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+void adjoint_free_snaps(lbib_adjoint* a) {
+    for (Snap& s : a->snaps) cudaFree(s.mem);
+    a->snaps.clear();
+    if (a->end.mem) cudaFree(a->end.mem);
+    a->end = Snap{};
+}
+
+}  // namespace
+
+extern "C" void lbib_adjoint_destroy(lbib_adjoint* a) {
+    if (!a) return;
+    if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
+    adjoint_free_snaps(a);
+    for (void* p : a->allocs) cudaFree(p);
+    delete a;
+}
+
+extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every, lbib_adjoint** out) {
+    if (!c || !out) return LBIB_E_INVALID;
+    *out = nullptr;
+    if (checkpoint_every < 1) return fail(c, LBIB_E_INVALID, "checkpoint interval must be at least 1");
+    if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the adjoint needs an FP64 context");
+    for (size_t m = 0; m < c->h_mem_kind.size(); ++m) {
+        if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED)
+            return fail(c, LBIB_E_INVALID, "the adjoint does not support rigid-projected membranes");
+        if (c->h_mem_n[m] < 5) return fail(c, LBIB_E_INVALID, "the adjoint needs membranes of at least 5 vertices");
+    }
+    lbib_status st = finalize(c);
+    if (st == LBIB_OK) st = build_graphs(c);
+    if (st != LBIB_OK) return st;
+    lbib_adjoint* a = new lbib_adjoint();
+    a->c = c;
+    a->K = checkpoint_every;
+    const size_t N = (size_t)c->nx * c->ny, nv = std::max(c->nv, 1), nm = std::max(c->nmem, 1);
+    const size_t nl = std::max(c->nlig, 1), K = (size_t)checkpoint_every;
+    auto get = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        a->allocs.push_back(p);
+        return p;
+    };
+    bool ok = (a->tape_f = (double*)get(K * 9 * N * 8)) && (a->tape_X = (double*)get(K * 2 * nv * 8)) &&
+              (a->tape_bond = (int*)get(K * nl * 4));
+    ok = ok && (a->fbar[0] = (double*)get(9 * N * 8)) && (a->fbar[1] = (double*)get(9 * N * 8)) &&
+         (a->fio = (double*)get(9 * N * 8));
+    ok = ok && (a->XB = (double*)get(2 * nv * 8)) && (a->XPB = (double*)get(2 * nv * 8)) &&
+         (a->Fbar = (double*)get(2 * nv * 8)) && (a->Wbar = (double*)get(9 * nv * 8));
+    ok = ok && (a->ubar = (double*)get(2 * N * 8)) && (a->Gbar = (double*)get(2 * N * 8));
+    ok = ok && (a->Abar = (double*)get(nm * 8)) && (a->ksb = (double*)get(nm * 8)) && (a->kbb = (double*)get(nm * 8)) &&
+         (a->sgb = (double*)get(8));
+    ok = ok && (a->Gv = (double*)get(2 * N * 8)) && (a->Gd = (double*)get(2 * N * 8));
+    ok = ok && (a->Wv = (double*)get(9 * nv * 8)) && (a->Wd = (double*)get(9 * nv * 8)) &&
+         (a->Fv = (double*)get(2 * nv * 8)) && (a->Fd = (double*)get(2 * nv * 8));
+    ok = ok && (a->A = (double*)get(nm * 8)) && (a->Ad = (double*)get(nm * 8)) && (a->box = (double*)get(4 * nm * 8));
+    ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->st = (int*)get(2 * nv * 4));
+    if (!ok) {
+        lbib_adjoint_destroy(a);
+        return fail(c, LBIB_E_OOM, "adjoint buffers (tape of the checkpoint interval)");
+    }
+    cudaError_t e = cudaSuccess;
+    for (double* p : {a->ubar, a->Gv, a->Gd}) e = e == cudaSuccess ? cudaMemsetAsync(p, 0, 2 * N * 8, c->stream) : e;
+    if (e == cudaSuccess) e = cudaMemsetAsync(a->zero, 0, std::max(2 * nv, nm) * 8, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        lbib_adjoint_destroy(a);
+        return cuda_fail(c, e, "adjoint set-up");
+    }
+    *out = a;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_adjoint_record(lbib_adjoint* a, int64_t n) {
+    if (!a || n < 1) return LBIB_E_INVALID;
+    lbib_ctx* c = a->c;
+    if (c->poisoned) return fail(c, LBIB_E_STATE, "context poisoned by an earlier device-side failure");
+    CK(cudaStreamSynchronize(c->stream));
+    adjoint_free_snaps(a);
+    a->n_rec = 0;
+    a->seeded = a->reversed = false;
+    const size_t bytes = snap_bytes(c);
+    const int64_t nseg = (n + a->K - 1) / a->K;
+    auto alloc_snap = [&](Snap& s) -> bool {
+        if (cudaMalloc(&s.mem, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            s.mem = nullptr;
+            return false;
+        }
+        snap_layout(c, s);
+        return true;
+    };
+    for (int64_t j = 0; j < nseg; ++j) {
+        Snap s;
+        if (!alloc_snap(s)) {
+            adjoint_free_snaps(a);
+            return fail(c, LBIB_E_OOM, "adjoint checkpoint");
+        }
+        a->snaps.push_back(s);
+        CK(snap_copy(c, a->snaps.back(), true));
+        const lbib_status st = lbib_step(c, std::min<int64_t>(a->K, n - j * a->K));
+        if (st != LBIB_OK) return st;
+    }
+    if (!alloc_snap(a->end)) {
+        adjoint_free_snaps(a);
+        return fail(c, LBIB_E_OOM, "adjoint checkpoint");
+    }
+    CK(snap_copy(c, a->end, true));
+    const lbib_status st = lbib_sync(c);
+    if (st != LBIB_OK) return st;
+    a->n_rec = n;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_adjoint_seed(lbib_adjoint* a, const double* xy_bar, const double* xy_prev_bar,
+                                         const double* f_bar) {
+    if (!a) return LBIB_E_INVALID;
+    lbib_ctx* c = a->c;
+    if (a->n_rec == 0) return fail(c, LBIB_E_STATE, "nothing recorded: call lbib_adjoint_record first");
+    const size_t N = (size_t)c->nx * c->ny, nv = (size_t)c->nv, nm = std::max(c->nmem, 1);
+    if (nv) {
+        if (xy_bar) CK(cudaMemcpyAsync(a->XB, xy_bar, 16 * nv, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(a->XB, 0, 16 * nv, c->stream));
+        if (xy_prev_bar) CK(cudaMemcpyAsync(a->XPB, xy_prev_bar, 16 * nv, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(a->XPB, 0, 16 * nv, c->stream));
+    }
+    if (f_bar) {
+        CK(cudaMemcpyAsync(a->fio, f_bar, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_adjoint_perm(a->fio, a->fbar[a->cb], c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK, 1,
+                               c->stream));
+    } else {
+        CK(cudaMemsetAsync(a->fbar[a->cb], 0, 9 * N * 8, c->stream));
+    }
+    CK(cudaMemsetAsync(a->ksb, 0, nm * 8, c->stream));
+    CK(cudaMemsetAsync(a->kbb, 0, nm * 8, c->stream));
+    CK(cudaMemsetAsync(a->sgb, 0, 8, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    a->seeded = true;
+    a->reversed = false;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
+    if (!a) return LBIB_E_INVALID;
+    lbib_ctx* c = a->c;
+    if (!a->seeded || a->reversed) return fail(c, LBIB_E_STATE, "the adjoint needs a fresh lbib_adjoint_seed");
+    if (c->poisoned) return fail(c, LBIB_E_STATE, "context poisoned by an earlier device-side failure");
+    const size_t N = (size_t)c->nx * c->ny, nv = std::max(c->nv, 1), nl = std::max(c->nlig, 1);
+    for (int64_t j = (int64_t)a->snaps.size() - 1; j >= 0; --j) {
+        Snap& s = a->snaps[j];
+        const int len = (int)std::min<int64_t>(a->K, a->n_rec - j * a->K);
+        // re-run the segment, keeping the state of each of its steps
+        CK(snap_copy(c, s, false));
+        for (int k = 0; k < len; ++k) {
+            CK(cudaMemcpyAsync(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8, cudaMemcpyDeviceToDevice,
+                               c->stream));
+            if (c->nv)
+                CK(cudaMemcpyAsync(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * (size_t)c->nv,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+            if (c->nlig)
+                CK(cudaMemcpyAsync(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+            if (k + 1 < len) {
+                CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
+                c->cur = 1 - c->cur;
+                c->steps += 1;
+            }
+        }
+        // adjoint steps, last to first
+        for (int k = len - 1; k >= 0; --k) {
+            AdjointArgs g{};
+            TangentArgs& t = g.t;
+            t.m = c->ma;
+            t.m.X = a->tape_X + (size_t)k * 2 * nv;
+            t.m.bond_of_lig = a->tape_bond + (size_t)k * nl;
+            t.f = a->tape_f + (size_t)k * 9 * N;
+            t.dX = a->zero;
+            t.dXp = a->zero;
+            t.Gv = a->Gv; t.Gd = a->Gd; t.Wv = a->Wv; t.Wd = a->Wd; t.st = a->st;
+            t.Fv = a->Fv; t.Fd = a->Fd; t.A = a->A; t.Ad = a->Ad; t.box = a->box;
+            t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0;
+            t.omega = 1.0 / c->tau; t.gx = c->gx; t.gy = c->gy;
+            t.step = s.step + k;
+            g.fbar = a->fbar[a->cb];
+            g.fbar_out = a->fbar[1 - a->cb];
+            g.XB = a->XB; g.XPB = a->XPB; g.ubar = a->ubar; g.Gbar = a->Gbar; g.Fbar = a->Fbar; g.Wbar = a->Wbar;
+            g.Abar = a->Abar; g.ks_bar = a->ksb; g.kb_bar = a->kbb; g.sigma_bar = a->sgb;
+            CK(launch_adjoint_step(g, c->stream));
+            a->cb = 1 - a->cb;
+        }
+    }
+    // leave the context as the recorded run left it
+    CK(snap_copy(c, a->end, false));
+    c->fields_valid = false;
+    a->reversed = true;
+    return lbib_sync(c);
+}
+
+extern "C" lbib_status lbib_adjoint_read(lbib_adjoint* a, double* xy_bar, double* xy_prev_bar, double* ks_bar,
+                                         double* kb_bar, double* sigma_bar, double* f_bar) {
+    if (!a) return LBIB_E_INVALID;
+    lbib_ctx* c = a->c;
+    if (!a->seeded) return fail(c, LBIB_E_STATE, "the adjoint has not been seeded");
+    const size_t N = (size_t)c->nx * c->ny, nv = (size_t)c->nv, nm = (size_t)c->nmem;
+    if (xy_bar && nv) CK(cudaMemcpyAsync(xy_bar, a->XB, 16 * nv, cudaMemcpyDeviceToHost, c->stream));
+    if (xy_prev_bar && nv) CK(cudaMemcpyAsync(xy_prev_bar, a->XPB, 16 * nv, cudaMemcpyDeviceToHost, c->stream));
+    if (ks_bar && nm) CK(cudaMemcpyAsync(ks_bar, a->ksb, 8 * nm, cudaMemcpyDeviceToHost, c->stream));
+    if (kb_bar && nm) CK(cudaMemcpyAsync(kb_bar, a->kbb, 8 * nm, cudaMemcpyDeviceToHost, c->stream));
+    if (sigma_bar) CK(cudaMemcpyAsync(sigma_bar, a->sgb, 8, cudaMemcpyDeviceToHost, c->stream));
+    if (f_bar) {
+        CK(launch_adjoint_perm(a->fbar[a->cb], a->fio, c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK, 0,
+                               c->stream));
+        CK(cudaMemcpyAsync(f_bar, a->fio, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+extern "C" int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* a) { return a ? a->n_rec : -1; }

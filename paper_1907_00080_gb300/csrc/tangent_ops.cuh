@@ -125,6 +125,17 @@ __device__ __forceinline__ bool t_near_box(const TangentArgs& t, int mb, double 
     return ::fabs(cxm) <= 0.5 * (bb[1] - bb[0]) + reach && ::fabs(cym) <= 0.5 * (bb[3] - bb[2]) + reach;
 }
 
+// plain-value pre-check of a repulsion pair: false only where the pair is
+// certainly farther apart than d_rep (the squared distance, with a margin far
+// above its rounding), so the exact test d < d_rep after the square root keeps
+// the same pairs
+__device__ __forceinline__ bool t_rep_candidate(const TangentArgs& t, double xv, double yv, int b) {
+    const double* X = static_cast<const double*>(t.m.X);
+    const double dx = t_wrap_x(t, dual(xv - X[2 * b])).v;
+    const double dy = t_wrap_y(t, dual(yv - X[2 * b + 1])).v;
+    return dx * dx + dy * dy < t.m.d_rep * t.m.d_rep * (1.0 + 1e-10);
+}
+
 // Total Lagrangian force on vertex v (membrane m, local index k) at X^n:
 // bond springs (Eq. adhFor) of the elements sharing v, repulsion (Eq. repFor)
 // from the other membranes, stretching (Eq. strainFor), bending (Eq. bendFor:
@@ -158,6 +169,7 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
             }
             const int o2 = t.m.mem_off[mb], n2 = t.m.mem_n[mb];
             for (int b = o2; b < o2 + n2; ++b) {
+                if (!t_rep_candidate(t, xv.v, yv.v, b)) continue;
                 dual xb, yb;
                 t_pos(t, b, s, xb, yb);
                 const dual dx = t_wrap_x(t, xv - xb), dy = t_wrap_y(t, yv - yb);
@@ -220,16 +232,24 @@ __device__ __forceinline__ void t_vertex_weights(const TangentArgs& t, int v, co
     t_pos(t, v, s, px, py);
     i0 = (int)floor(px.v + 0.5);
     j0 = (int)floor(py.v + 0.5);
+    // the Roma factors of the three columns and the three rows
+    dual rxa[3], rya[3], phx[3], phy[3];
+    for (int a = 0; a < 3; ++a) {
+        rxa[a] = dual((double)(i0 + a - 1)) - px;
+        rya[a] = dual((double)(j0 + a - 1)) - py;
+        phx[a] = t_roma(rxa[a]);
+        phy[a] = t_roma(rya[a]);
+    }
     dual Wr[9], rx[9], ry[9];
     int nvalid = 0;
     for (int b = -1; b <= 1; ++b)
         for (int a = -1; a <= 1; ++a) {
             const int k = (b + 1) * 3 + (a + 1);
-            rx[k] = dual((double)(i0 + a)) - px;
-            ry[k] = dual((double)(j0 + b)) - py;
+            rx[k] = rxa[a + 1];
+            ry[k] = rya[b + 1];
             const int j = j0 + b;
             in[k] = t.m.walls ? (j >= 0 && j < t.m.ny) : true;
-            Wr[k] = in[k] ? t_roma(rx[k]) * t_roma(ry[k]) : dual(0.0);
+            Wr[k] = in[k] ? phx[a + 1] * phy[b + 1] : dual(0.0);
             nvalid += in[k];
         }
     for (int k = 0; k < 9; ++k) w[k] = dual(0.0);

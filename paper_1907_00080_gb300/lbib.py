@@ -83,6 +83,13 @@ _SIGS = {
     "lbib_tangent_step": (_I, [_P, _I64]),
     "lbib_tangent_read": (_I, [_P, _DP, _DP]),
     "lbib_tangent_destroy": (None, [_P]),
+    "lbib_adjoint_create": (_I, [_P, _I32, ctypes.POINTER(_P)]),
+    "lbib_adjoint_record": (_I, [_P, _I64]),
+    "lbib_adjoint_seed": (_I, [_P, _DP, _DP, _DP]),
+    "lbib_adjoint_reverse": (_I, [_P]),
+    "lbib_adjoint_read": (_I, [_P, _DP, _DP, _DP, _DP, _DP, _DP]),
+    "lbib_adjoint_recorded_steps": (_I64, [_P]),
+    "lbib_adjoint_destroy": (None, [_P]),
     "lbib_set_tiling": (_I, [_P, _I32, _I32]),
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
@@ -348,6 +355,50 @@ def lbib_tangent_read(ctx, t, nv):
 def lbib_tangent_destroy(t):
     if t:
         load().lbib_tangent_destroy(t)
+
+
+def lbib_adjoint_create(ctx, checkpoint_every):
+    out = _P()
+    _check(ctx, load().lbib_adjoint_create(ctx, int(checkpoint_every), ctypes.byref(out)))
+    return out
+
+
+def lbib_adjoint_record(ctx, adj, n):
+    _check(ctx, load().lbib_adjoint_record(adj, int(n)))
+
+
+def lbib_adjoint_seed(ctx, adj, xy_bar=None, xy_prev_bar=None, f_bar=None):
+    keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+            for a in (xy_bar, xy_prev_bar, f_bar)]
+    ptrs = [None if a is None else _dptr(a) for a in keep]
+    _check(ctx, load().lbib_adjoint_seed(adj, ptrs[0], ptrs[1], ptrs[2]))
+
+
+def lbib_adjoint_reverse(ctx, adj):
+    _check(ctx, load().lbib_adjoint_reverse(adj))
+
+
+def lbib_adjoint_read(ctx, adj, nv, nmem, n_nodes=None):
+    """Adjoints after the reverse sweep: dict of xy, xy_prev ([nv, 2]), k_s, k_b
+    ([nmem]), sigma (float) and, when n_nodes is given, f ([9, n_nodes])."""
+    xy = np.zeros((nv, 2))
+    xyp = np.zeros((nv, 2))
+    ks = np.zeros(max(nmem, 1))
+    kb = np.zeros(max(nmem, 1))
+    sg = np.zeros(1)
+    f = None if n_nodes is None else np.zeros((9, n_nodes))
+    _check(ctx, load().lbib_adjoint_read(adj, _dptr(xy), _dptr(xyp), _dptr(ks), _dptr(kb), _dptr(sg),
+                                         None if f is None else _dptr(f)))
+    return {"xy": xy, "xy_prev": xyp, "k_s": ks[:nmem], "k_b": kb[:nmem], "sigma": float(sg[0]), "f": f}
+
+
+def lbib_adjoint_recorded_steps(adj):
+    return load().lbib_adjoint_recorded_steps(adj)
+
+
+def lbib_adjoint_destroy(adj):
+    if adj:
+        load().lbib_adjoint_destroy(adj)
 
 
 # ------------------------------------------------------------------ convenience

@@ -1,6 +1,8 @@
 """Derivatives of carrier observables with respect to the carrier's stiffnesses,
-the bond stiffness and its release height, through the forward-mode tangent
-of the CUDA time step (lbib_tangent_*), behind a torch.autograd.Function.
+the bond stiffness and its release height, through the reverse-mode adjoint
+(lbib_adjoint_*: one backward sweep for the whole gradient) or the
+forward-mode tangent (lbib_tangent_*: one run per parameter) of the CUDA time
+step, behind a torch.autograd.Function.
 
 Observables after T steps (lattice units):
   J1 = final height of the carrier's centroid above the lower wall (y = -1/2),
@@ -111,33 +113,116 @@ def jacobian(p, steps, seed=0, bonds="default"):
     return J, jac, bond_hist
 
 
+def observable_gradient(wl, xy, bonds, w):
+    """dJ/dX^N (nv, 2) of J = w[0] J1 + w[1] J2 at the final markers, and the
+    explicit dJ/dsigma of the bond energy."""
+    _, _, (off, n, terms, y_eq) = observables(wl, xy, bonds)
+    g = np.zeros((wl.n_vertices, 2))
+    g[off:off + n, 1] += w[0] / n
+    dsig = 0.0
+    for a, b, d, dist in terms:
+        gc = -w[1] * wl.sigma_lu * (dist - y_eq) / dist * d  # d J2 / d(ligand point)
+        g[a] += 0.5 * gc
+        g[b] += 0.5 * gc
+        dsig += w[1] * 0.5 * (dist - y_eq) ** 2
+    return g, dsig
+
+
+class Recording:
+    """One FP64 run of the sensitivity case, recorded for backward sweeps
+    (checkpoints every `checkpoint_every` steps)."""
+
+    def __init__(self, p, steps, checkpoint_every=250, seed=0, bonds="default"):
+        self.wl = make_workload(p, steps, seed, bonds)
+        self.sim = lbib.Simulation(self.wl, precision="f64")
+        self.adj = None
+        self.adj = lbib.lbib_adjoint_create(self.sim.ctx, checkpoint_every)
+        lbib.lbib_adjoint_record(self.sim.ctx, self.adj, steps)
+        self.xy, self.bonds = self.sim.markers(), self.sim.bonds()
+        j1, j2, _ = observables(self.wl, self.xy, self.bonds)
+        self.J = np.array([j1, j2])
+
+    def gradient(self, w):
+        """d(w . J)/dp (4,) from one backward sweep."""
+        nv, nm = self.wl.n_vertices, len(self.wl.membranes)
+        g, dsig = observable_gradient(self.wl, self.xy, self.bonds, w)
+        lbib.lbib_adjoint_seed(self.sim.ctx, self.adj, g, None, None)
+        lbib.lbib_adjoint_reverse(self.sim.ctx, self.adj)
+        r = lbib.lbib_adjoint_read(self.sim.ctx, self.adj, nv, nm)
+        nc = len(self.wl.membranes[-1].xy)
+        # the release height moves X^0 and X^{-1} of every carrier vertex
+        dy = float(r["xy"][nv - nc:, 1].sum() + r["xy_prev"][nv - nc:, 1].sum())
+        return np.array([r["k_s"][-1], r["k_b"][-1], r["sigma"] + dsig, dy])
+
+    def close(self):
+        if self.adj is not None:
+            lbib.lbib_adjoint_destroy(self.adj)
+            self.adj = None
+        if self.sim is not None:
+            self.sim.close()
+            self.sim = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adjoint_jacobian(p, steps, checkpoint_every=250, seed=0, bonds="default"):
+    """J (2,) and dJ/dp (2, 4) by one recorded run and two backward sweeps."""
+    rec = Recording(p, steps, checkpoint_every, seed, bonds)
+    try:
+        jac = np.stack([rec.gradient((1.0, 0.0)), rec.gradient((0.0, 1.0))])
+        return rec.J, jac, rec.bonds
+    finally:
+        rec.close()
+
+
 def _torch_function():
     import torch
 
     class CarrierObservables(torch.autograd.Function):
         """J = (J1, J2)(p), p = (k_s, k_b, sigma, y_release) as a float64
-        tensor; backward contracts the incoming gradient with dJ/dp from the
-        forward-mode tangent of the CUDA time step."""
+        tensor.  mode "adjoint": forward records the FP64 run, backward seeds
+        the adjoint with the incoming gradient and runs one backward sweep;
+        mode "tangent": forward builds dJ/dp from four tangent runs, backward
+        contracts the incoming gradient with it."""
 
         @staticmethod
-        def forward(ctx, p, steps, seed=0):
+        def forward(ctx, p, steps, seed=0, mode="adjoint", checkpoint_every=250):
             pv = p.detach().cpu().numpy().astype(np.float64)
-            J, jac, _ = jacobian(pv, int(steps), int(seed))
-            ctx.save_for_backward(torch.as_tensor(jac, dtype=torch.float64))
+            ctx.rec = None
+            if mode == "adjoint":
+                ctx.rec = Recording(pv, int(steps), int(checkpoint_every), int(seed))
+                J = ctx.rec.J
+            elif mode == "tangent":
+                J, jac, _ = jacobian(pv, int(steps), int(seed))
+                ctx.save_for_backward(torch.as_tensor(jac, dtype=torch.float64))
+            else:
+                raise ValueError("mode must be 'adjoint' or 'tangent'")
             return torch.as_tensor(J, dtype=torch.float64, device=p.device)
 
         @staticmethod
         def backward(ctx, grad_out):
-            (jac,) = ctx.saved_tensors
-            g = grad_out.detach().to(torch.float64).cpu() @ jac
-            return g.to(grad_out.device), None, None
+            w = grad_out.detach().to(torch.float64).cpu()
+            if ctx.rec is not None:
+                try:
+                    g = torch.as_tensor(ctx.rec.gradient(w.numpy()), dtype=torch.float64)
+                finally:
+                    ctx.rec.close()
+                    ctx.rec = None
+            else:
+                (jac,) = ctx.saved_tensors
+                g = w @ jac
+            return g.to(grad_out.device), None, None, None, None
 
     return CarrierObservables
 
 
-def carrier_observables(p, steps, seed=0):
+def carrier_observables(p, steps, seed=0, mode="adjoint", checkpoint_every=250):
     """torch entry point: J = carrier_observables(p, steps); J.backward(...)"""
-    return _torch_function().apply(p, steps, seed)
+    return _torch_function().apply(p, steps, seed, mode, checkpoint_every)
 
 
 def default_params(seed=0):

@@ -144,7 +144,7 @@ def test_autograd_function_backward(tangent):
     import torch
     p0, J, jac, _ = tangent
     p = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
-    out = sensitivity.carrier_observables(p, STEPS)
+    out = sensitivity.carrier_observables(p, STEPS, mode="tangent")
     np.testing.assert_allclose(out.detach().numpy(), J, rtol=0, atol=0)
     (out[0] + 2.0 * out[1]).backward()
     np.testing.assert_allclose(p.grad.numpy(), jac[0] + 2.0 * jac[1], rtol=1e-14, atol=0)
