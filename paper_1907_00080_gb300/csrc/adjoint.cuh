@@ -3,9 +3,10 @@
 // One FP64 time step maps S^n = (d*^{n-1}, X^n, X^{n-1}) to S^{n+1}; its
 // adjoint maps the adjoints of S^{n+1} to those of S^n and adds the step's
 // share of dJ/dk_s, dJ/dk_b and dJ/dsigma.  The primal quantities of step n
-// (areas, forces, shape functions, spread force) are re-evaluated from the
-// recorded state by the tangent kernels with a zero tangent; the bond set of
-// step n is the recorded one (bond events are not differentiated).
+// (forces, shape functions and their stencils, the spread force field) are the
+// ones the context's own step computed, copied to the tape when the segment
+// is re-run; areas and bounding boxes are re-evaluated from X^n.  The bond set
+// of step n is the recorded one (bond events are not differentiated).
 #pragma once
 
 #include "tangent.cuh"
@@ -13,8 +14,10 @@
 namespace lbib {
 
 struct AdjointArgs {
-    TangentArgs t;        // primal evaluation at step n: t.f = d*^{n-1}, t.m.X = X^n, t.m.bond_of_lig
-                          // = bonds of step n; t.Gv, t.Fv, t.Wv, t.st, t.A filled by the tangent kernels
+    TangentArgs t;        // primal state of step n: t.f = d*^{n-1}, t.m.X = X^n, t.m.bond_of_lig = bonds
+                          // of step n, t.Fv = F^n, t.Wv = shape functions, t.st = stencil origins (wrapped
+                          // i0, j0), all from the tape; t.A, t.Ad, t.box filled by the area kernel
+    const longlong2* gfix;  // [N] spread force of step n, fixed point (scaled by 2^52)
     const double* fbar;   // [9][N] adjoint of d*^n (the deviations step n stores)
     double* fbar_out;     // [9][N] adjoint of d*^{n-1}; every entry is written
     double* XB;           // [nv][2] in: adjoint of X^{n+1}; out: adjoint of X^n

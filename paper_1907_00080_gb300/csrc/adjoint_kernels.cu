@@ -13,6 +13,8 @@
 // (a few thousand vertices) take local Jacobian columns from the dual-number
 // functions of the tangent (one-hot seeds), so they share their arithmetic
 // with the forward-mode derivative.
+#include <algorithm>
+
 #include "adjoint.cuh"
 #include "lb_node.cuh"
 #include "tangent_ops.cuh"
@@ -44,24 +46,31 @@ __device__ __forceinline__ void collide_node_rev(const double (&d)[9], double Gx
     const double uu = ux * ux + uy * uy;
     const double omr = om * rho;
     const double b = 3.0 * omr, c = 4.5 * omr, g = 3.0 * pre, h = 9.0 * pre;
-    // adjoints of a, b, c and of u, G through eu_i, eG_i
-    double Sa = 0.0, Sb = 0.0, Sc = 0.0;
+    // adjoints of a, b, c and of u, G through eu_i, eG_i; opposite directions
+    // (e_o = -e_i) share eu^2 and flip eu, eG, so each pair is summed once in its
+    // even (y_i + y_o) and odd (y_i - y_o) parts
+    double Sa = wgt<double>(0) * yb[0], Sb = 0.0, Sc = 0.0;
     double uxb = ubx, uyb = uby;
     Gbx = 0.0;
     Gby = 0.0;
+    const double eus[4] = {ux, uy, ux + uy, uy - ux};
+    const double eGs[4] = {Gx, Gy, Gx + Gy, Gy - Gx};
+    constexpr int ip[4] = {1, 2, 5, 6};
+    constexpr int io[4] = {3, 4, 7, 8};
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const double wy = wgt<double>(i) * yb[i];
-        const double eu = cx(i) * ux + cy(i) * uy, eG = cx(i) * Gx + cy(i) * Gy;
-        Sa += wy;
-        Sb += wy * eu;
-        Sc += wy * eu * eu;
-        const double deu = wy * (b + 2.0 * c * eu + h * eG);
-        const double deG = wy * (g + h * eu);
-        uxb += cx(i) * deu;
-        uyb += cy(i) * deu;
-        Gbx += cx(i) * deG;
-        Gby += cy(i) * deG;
+    for (int p = 0; p < 4; ++p) {
+        const double w = wgt<double>(ip[p]);
+        const double eu = eus[p], eG = eGs[p];
+        const double yE = w * (yb[ip[p]] + yb[io[p]]), yO = w * (yb[ip[p]] - yb[io[p]]);
+        Sa += yE;
+        Sb += eu * yO;
+        Sc += eu * eu * yE;
+        const double deu = b * yO + (2.0 * c * eu + h * eG) * yE;  // along e_ip
+        const double deG = g * yO + h * eu * yE;
+        uxb += cx(ip[p]) * deu;
+        uyb += cy(ip[p]) * deu;
+        Gbx += cx(ip[p]) * deG;
+        Gby += cy(ip[p]) * deG;
     }
     // a, b, c -> drho, rho, u.u, u.G
     double drhob = om * Sa;
@@ -83,14 +92,15 @@ __device__ __forceinline__ void collide_node_rev(const double (&d)[9], double Gx
 }
 
 // velocity output of the collision at `node` (the field the markers interpolate)
-__device__ __forceinline__ void node_velocity(const TangentArgs& t, size_t node, double& ux, double& uy) {
+__device__ __forceinline__ void node_velocity(const TangentArgs& t, const longlong2 g, size_t node, double& ux,
+                                              double& uy) {
     const int nx = t.m.nx, ny = t.m.ny;
     double d[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) d[i] = t.f[t_pull_src(node, i, nx, ny, t.m.walls)];
     double out[9], rho;
-    collide_node<double>(d, t.gx + t.Gv[2 * node], t.gy + t.Gv[2 * node + 1], t.omega, 1.0 - 0.5 * t.omega, out, rho,
-                         ux, uy);
+    collide_node<double>(d, t.gx + from_fix<double>(g.x), t.gy + from_fix<double>(g.y), t.omega, 1.0 - 0.5 * t.omega,
+                         out, rho, ux, uy);
 }
 
 // BDF2 coefficients of X^{n+1} = ca X^n + cb X^{n-1} + cu U^n (Euler on step 0)
@@ -119,7 +129,7 @@ __global__ void k_a_interp(const AdjointArgs a) {
         const size_t node = t_node(t, i0, j0, k);
         const double w = t.Wv[9 * v + k];
         double ux, uy;
-        node_velocity(t, node, ux, uy);
+        node_velocity(t, a.gfix[node], node, ux, uy);
         atomicAdd(&a.ubar[2 * node], w * Ubx);
         atomicAdd(&a.ubar[2 * node + 1], w * Uby);
         wb = Ubx * ux + Uby * uy;
@@ -129,7 +139,7 @@ __global__ void k_a_interp(const AdjointArgs a) {
 
 // Adjoint of the collision and of the pull stream at every node.  The pull is a
 // permutation of the stored values, so each adjoint entry has exactly one
-// writer.  Also clears this step's u-bar and spread force for the next step.
+// writer.  Also clears this step's u-bar for the next step.
 __global__ void k_a_collide(const AdjointArgs a) {
     const TangentArgs& t = a.t;
     const int nx = t.m.nx, ny = t.m.ny;
@@ -145,10 +155,11 @@ __global__ void k_a_collide(const AdjointArgs a) {
             d[i] = t.f[src[i]];
             yb[i] = a.fbar[(size_t)i * N + node];
         }
-        const double gsx = t.Gv[2 * node], gsy = t.Gv[2 * node + 1];
+        const longlong2 gf = a.gfix[node];
         const double ubx = a.ubar[2 * node], uby = a.ubar[2 * node + 1];
         double db[9], Gbx, Gby;
-        collide_node_rev(d, t.gx + gsx, t.gy + gsy, om, pre, yb, ubx, uby, db, Gbx, Gby);
+        collide_node_rev(d, t.gx + from_fix<double>(gf.x), t.gy + from_fix<double>(gf.y), om, pre, yb, ubx, uby, db,
+                         Gbx, Gby);
 #pragma unroll
         for (int i = 0; i < 9; ++i) a.fbar_out[src[i]] = db[i];
         a.Gbar[2 * node] = Gbx;
@@ -156,10 +167,6 @@ __global__ void k_a_collide(const AdjointArgs a) {
         if (ubx != 0.0 || uby != 0.0) {
             a.ubar[2 * node] = 0.0;
             a.ubar[2 * node + 1] = 0.0;
-        }
-        if (gsx != 0.0 || gsy != 0.0) {
-            t.Gv[2 * node] = 0.0;
-            t.Gv[2 * node + 1] = 0.0;
         }
     }
 }
@@ -194,79 +201,80 @@ __global__ void k_a_spread(const AdjointArgs a) {
     }
 }
 
-// Tasks of k_a_forces (blockIdx.y), one dual evaluation each
-enum AdjTask {
-    kTaskPos0 = 0,      // 0..9: coordinate (task & 1) of vertex v - 2 + task / 2
-    kTaskArea = 10,
-    kTaskKs = 11,
-    kTaskKb = 12,
-    kTaskSigma = 13,
-    kTaskRep = 14,      // the repulsion pairs of v
-    kTaskWx = 15,       // shape functions of v against x_v, y_v
-    kTaskWy = 16,
-    kNumTasks = 17
+// Tasks of k_a_forces (blockIdx.y): one dual evaluation each, of the force
+// terms of vertex v that depend on one seed.  Position seeds X_{v+d}: the
+// bending moment at v-1 depends on d in -2..0, the one at v on -1..1, the one
+// at v+1 on 0..2; bonds, stretching and the area penalty on -1..1.
+struct AdjTask {
+    signed char kind, d, coord;  // kind: a SeedKind, or kRepTask / kWeightsTask
+    unsigned char terms;
 };
+constexpr int kRepTask = 100, kWeightsTask = 101;
+constexpr unsigned char kOther = kTermBond | kTermStretch | kTermArea;
+constexpr int kNumTasks = 33;
+__constant__ AdjTask c_tasks[kNumTasks] = {
+    // x coordinate
+    {kPos, -2, 0, kTermBendL},
+    {kPos, -1, 0, kTermBendL}, {kPos, -1, 0, kTermBendV}, {kPos, -1, 0, kOther},
+    {kPos, 0, 0, kTermBendL}, {kPos, 0, 0, kTermBendV}, {kPos, 0, 0, kTermBendR}, {kPos, 0, 0, kOther},
+    {kPos, 1, 0, kTermBendV}, {kPos, 1, 0, kTermBendR}, {kPos, 1, 0, kOther},
+    {kPos, 2, 0, kTermBendR},
+    // y coordinate
+    {kPos, -2, 1, kTermBendL},
+    {kPos, -1, 1, kTermBendL}, {kPos, -1, 1, kTermBendV}, {kPos, -1, 1, kOther},
+    {kPos, 0, 1, kTermBendL}, {kPos, 0, 1, kTermBendV}, {kPos, 0, 1, kTermBendR}, {kPos, 0, 1, kOther},
+    {kPos, 1, 1, kTermBendV}, {kPos, 1, 1, kTermBendR}, {kPos, 1, 1, kOther},
+    {kPos, 2, 1, kTermBendR},
+    // parameters and the area
+    {kArea, 0, 0, kTermArea}, {kKs, 0, 0, kTermStretch}, {kSigma, 0, 0, kTermBond},
+    {kKb, 0, 0, kTermBendL}, {kKb, 0, 0, kTermBendV}, {kKb, 0, 0, kTermBendR},
+    // repulsion pairs, shape functions against x_v and y_v
+    {kRepTask, 0, 0, 0}, {kWeightsTask, 0, 0, 0}, {kWeightsTask, 0, 1, 0}};
 
 // Adjoint of the total Lagrangian force on vertex v and of its shape functions.
 // Bonds, stretching, bending and the area penalty depend on X_{v-2} .. X_{v+2},
-// the membrane's area, k_s, k_b and sigma: one dual evaluation per seed gives
-// the column dF_v/d(seed), and F_v-bar . column is added to that input's
-// adjoint.  The repulsion -sum_b c0 d_vb^{-5/2} n_v (Eq. repFor) is transposed
-// pair by pair: through d_vb into X_v and X_b, and through the vertex normal n_v
-// into X_{v-1}, X_v, X_{v+1}.  The shape functions of v depend on X_v alone
-// (two seeds).  Each (vertex, task) is one thread: the FP64 chains are long,
-// and one thread per vertex would leave most SMs idle.
+// the membrane's area, k_s, k_b and sigma: one dual evaluation per (seed, term
+// group) gives that part of the column dF_v/d(seed), and F_v-bar . column is
+// added to the seed's adjoint.  The repulsion -sum_b c0 d_vb^{-5/2} n_v (Eq.
+// repFor) is transposed pair by pair: through d_vb into X_v and X_b, and through
+// the vertex normal n_v into X_{v-1}, X_v, X_{v+1}.  The shape functions of v
+// depend on X_v alone (two seeds).  Each (vertex, task) is one thread: the FP64
+// chains are long, and one thread per vertex would leave most SMs idle.
 __global__ void k_a_forces(const AdjointArgs a) {
     const TangentArgs& t = a.t;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const int task = blockIdx.y;
     if (v >= t.m.nv) return;
-    if (task == kTaskWx || task == kTaskWy) {
+    const AdjTask q = c_tasks[blockIdx.y];
+    if (q.kind == kWeightsTask) {
         dual w[9];
         bool in[9];
         int si, sj;
-        const int c = task - kTaskWx;
-        t_vertex_weights(t, v, Seed{kPos, v, c, -1}, w, in, si, sj);
+        t_vertex_weights(t, v, Seed{kPos, v, q.coord, -1}, w, in, si, sj);
         double acc = 0.0;
         for (int k = 0; k < 9; ++k)
             if (in[k]) acc += a.Wbar[9 * v + k] * w[k].d;
-        atomicAdd(&a.XB[2 * v + c], acc);
+        atomicAdd(&a.XB[2 * v + q.coord], acc);
         return;
     }
     const double Fbx = a.Fbar[2 * v], Fby = a.Fbar[2 * v + 1];
     if (Fbx == 0.0 && Fby == 0.0) return;
     const int m = t_mem_of(t, v);
     const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
-    dual fx, fy;
-    if (task < kTaskArea) {
-        const int u = t_ring(off, n, k - 2 + task / 2), c = task & 1;
-        t_vertex_force(t, v, m, Seed{kPos, u, c, -1}, fx, fy, false);
-        atomicAdd(&a.XB[2 * u + c], Fbx * fx.d + Fby * fy.d);
+    if (q.kind != kRepTask) {
+        if (q.kind == kSigma && t.m.nlig == 0) return;
+        const int u = q.kind == kPos ? t_ring(off, n, k + q.d) : -1;
+        dual fx, fy;
+        t_vertex_force(t, v, m, Seed{q.kind, u, q.coord, m}, fx, fy, q.terms);
+        const double g = Fbx * fx.d + Fby * fy.d;
+        double* dst = q.kind == kPos ? &a.XB[2 * u + q.coord]
+                      : q.kind == kArea ? &a.Abar[m]
+                      : q.kind == kKs   ? &a.ks_bar[m]
+                      : q.kind == kKb   ? &a.kb_bar[m]
+                                        : a.sigma_bar;
+        atomicAdd(dst, g);
         return;
     }
-    if (task == kTaskArea) {
-        t_vertex_force(t, v, m, Seed{kArea, -1, 0, m}, fx, fy, false);
-        atomicAdd(&a.Abar[m], Fbx * fx.d + Fby * fy.d);
-        return;
-    }
-    if (task == kTaskKs) {
-        t_vertex_force(t, v, m, Seed{kKs, -1, 0, m}, fx, fy, false);
-        atomicAdd(&a.ks_bar[m], Fbx * fx.d + Fby * fy.d);
-        return;
-    }
-    if (task == kTaskKb) {
-        t_vertex_force(t, v, m, Seed{kKb, -1, 0, m}, fx, fy, false);
-        atomicAdd(&a.kb_bar[m], Fbx * fx.d + Fby * fy.d);
-        return;
-    }
-    if (task == kTaskSigma) {
-        if (t.m.nlig > 0) {
-            t_vertex_force(t, v, m, Seed{kSigma, -1, 0, -1}, fx, fy, false);
-            atomicAdd(a.sigma_bar, Fbx * fx.d + Fby * fy.d);
-        }
-        return;
-    }
-    // kTaskRep
+    // the repulsion pairs of v
     if (t.m.nmem < 2) return;
     const double* X = static_cast<const double*>(t.m.X);
     const double xv = X[2 * v], yv = X[2 * v + 1];
@@ -356,11 +364,13 @@ cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
     const int nvb = (t.m.nv + 31) / 32;
     cudaError_t e;
     if (t.m.nv > 0) {
-        // primal areas, forces, shape functions and spread force of step n
-        if ((e = launch_tangent_markers(t, s)) != cudaSuccess) return e;
+        // areas and bounding boxes of X^n (forces, shape functions and the spread
+        // force come from the tape)
+        if ((e = launch_tangent_areas(t, s)) != cudaSuccess) return e;
         k_a_interp<<<dim3(nvb, 9), 32, 0, s>>>(a);
     }
-    k_a_collide<<<node_grid(N), 256, 0, s>>>(a);
+    // FP64-bound: 128-thread blocks, up to 16 per SM
+    k_a_collide<<<(int)std::min<size_t>((N + 127) / 128, 152 * 16), 128, 0, s>>>(a);
     if (t.m.nv > 0) {
         k_a_spread<<<nvb, 32, 0, s>>>(a);
         k_a_forces<<<dim3(nvb, kNumTasks), 32, 0, s>>>(a);

@@ -1152,6 +1152,7 @@ struct lbib_tangent {
     double *Gv = nullptr, *Gd = nullptr, *u = nullptr, *ud = nullptr, *Wv = nullptr, *Wd = nullptr;
     double *Fv = nullptr, *Fd = nullptr, *A = nullptr, *Ad = nullptr, *dks = nullptr, *dkb = nullptr;
     double* box = nullptr;
+    double* th0 = nullptr;
     int* st = nullptr;
     double dsigma = 0.0;
     std::vector<void*> allocs;
@@ -1191,11 +1192,12 @@ extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     ok = ok && (t->Fv = (double*)get(2 * nv * 8)) && (t->Fd = (double*)get(2 * nv * 8));
     ok = ok && (t->A = (double*)get(nm * 8)) && (t->Ad = (double*)get(nm * 8)) && (t->box = (double*)get(4 * nm * 8));
     ok = ok && (t->dks = (double*)get(nm * 8)) && (t->dkb = (double*)get(nm * 8));
-    ok = ok && (t->st = (int*)get(2 * nv * 4));
+    ok = ok && (t->st = (int*)get(2 * nv * 4)) && (t->th0 = (double*)get(nv * 8));
     if (!ok) {
         lbib_tangent_destroy(t);
         return fail(c, LBIB_E_OOM, "tangent buffers");
     }
+    launch_rest_angles(c->ma, t->th0, c->stream);
     cudaMemsetAsync(t->fd[0], 0, 9 * N * 8, c->stream);
     cudaMemsetAsync(t->fd[1], 0, 9 * N * 8, c->stream);
     for (int b = 0; b < 3; ++b) cudaMemsetAsync(t->dX[b], 0, 2 * nv * 8, c->stream);
@@ -1249,7 +1251,7 @@ extern "C" lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n) {
         a.dXn = t->dX[t->in];
         a.Gv = t->Gv; a.Gd = t->Gd; a.u = t->u; a.ud = t->ud; a.Wv = t->Wv; a.Wd = t->Wd;
         a.st = t->st; a.Fv = t->Fv; a.Fd = t->Fd; a.A = t->A; a.Ad = t->Ad; a.box = t->box;
-        a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma;
+        a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma; a.th0 = t->th0;
         a.omega = 1.0 / c->tau; a.gx = c->gx; a.gy = c->gy;
         a.step = c->steps;
         CK(launch_tangent_step(a, c->stream));
@@ -1356,19 +1358,23 @@ struct lbib_adjoint {
     Snap end;                 // state after the recorded run
     int64_t n_rec = 0;
     bool seeded = false, reversed = false;
-    // tape of one segment: deviations, positions and bonds of each of its steps
+    // tape of one segment, per step: the state it starts from (deviations,
+    // positions, bonds) and what the context's step computed from it (marker
+    // forces, shape functions, stencil origins, fixed-point spread force)
     double* tape_f = nullptr;
     double* tape_X = nullptr;
     int* tape_bond = nullptr;
+    double* tape_F = nullptr;
+    double* tape_W = nullptr;
+    int* tape_st = nullptr;
+    longlong2* tape_G = nullptr;
     // adjoint state and per-step work arrays
     double* fbar[2] = {nullptr, nullptr};
     int cb = 0;
     double *XB = nullptr, *XPB = nullptr, *ubar = nullptr, *Gbar = nullptr, *Fbar = nullptr, *Wbar = nullptr;
     double *Abar = nullptr, *ksb = nullptr, *kbb = nullptr, *sgb = nullptr, *fio = nullptr;
-    // primal re-evaluation of the marker part (tangent buffers, zero tangent)
-    double *Gv = nullptr, *Gd = nullptr, *Wv = nullptr, *Wd = nullptr, *Fv = nullptr, *Fd = nullptr;
-    double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr;
-    int* st = nullptr;
+    // areas and boxes re-evaluated per step (tangent area kernel, zero tangent)
+    double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr, *th0 = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -1420,6 +1426,8 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     };
     bool ok = (a->tape_f = (double*)get(K * 9 * N * 8)) && (a->tape_X = (double*)get(K * 2 * nv * 8)) &&
               (a->tape_bond = (int*)get(K * nl * 4));
+    ok = ok && (a->tape_F = (double*)get(K * 2 * nv * 8)) && (a->tape_W = (double*)get(K * 9 * nv * 8)) &&
+         (a->tape_st = (int*)get(K * 2 * nv * 4)) && (a->tape_G = (longlong2*)get(K * N * sizeof(longlong2)));
     ok = ok && (a->fbar[0] = (double*)get(9 * N * 8)) && (a->fbar[1] = (double*)get(9 * N * 8)) &&
          (a->fio = (double*)get(9 * N * 8));
     ok = ok && (a->XB = (double*)get(2 * nv * 8)) && (a->XPB = (double*)get(2 * nv * 8)) &&
@@ -1427,18 +1435,17 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     ok = ok && (a->ubar = (double*)get(2 * N * 8)) && (a->Gbar = (double*)get(2 * N * 8));
     ok = ok && (a->Abar = (double*)get(nm * 8)) && (a->ksb = (double*)get(nm * 8)) && (a->kbb = (double*)get(nm * 8)) &&
          (a->sgb = (double*)get(8));
-    ok = ok && (a->Gv = (double*)get(2 * N * 8)) && (a->Gd = (double*)get(2 * N * 8));
-    ok = ok && (a->Wv = (double*)get(9 * nv * 8)) && (a->Wd = (double*)get(9 * nv * 8)) &&
-         (a->Fv = (double*)get(2 * nv * 8)) && (a->Fd = (double*)get(2 * nv * 8));
     ok = ok && (a->A = (double*)get(nm * 8)) && (a->Ad = (double*)get(nm * 8)) && (a->box = (double*)get(4 * nm * 8));
-    ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->st = (int*)get(2 * nv * 4));
+    ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->th0 = (double*)get(nv * 8));
     if (!ok) {
         lbib_adjoint_destroy(a);
         return fail(c, LBIB_E_OOM, "adjoint buffers (tape of the checkpoint interval)");
     }
-    cudaError_t e = cudaSuccess;
-    for (double* p : {a->ubar, a->Gv, a->Gd}) e = e == cudaSuccess ? cudaMemsetAsync(p, 0, 2 * N * 8, c->stream) : e;
+    cudaError_t e = cudaMemsetAsync(a->ubar, 0, 2 * N * 8, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(a->zero, 0, std::max(2 * nv, nm) * 8, c->stream);
+    // without markers there is no spread force: the tape's field stays zero
+    if (e == cudaSuccess && c->nv == 0) e = cudaMemsetAsync(a->tape_G, 0, K * N * sizeof(longlong2), c->stream);
+    if (e == cudaSuccess) e = launch_rest_angles(c->ma, a->th0, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         lbib_adjoint_destroy(a);
@@ -1526,21 +1533,26 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
     for (int64_t j = (int64_t)a->snaps.size() - 1; j >= 0; --j) {
         Snap& s = a->snaps[j];
         const int len = (int)std::min<int64_t>(a->K, a->n_rec - j * a->K);
-        // re-run the segment, keeping the state of each of its steps
+        // re-run the segment, keeping each step's state and what the step
+        // computed from it (the spread field before the next step clears it)
         CK(snap_copy(c, s, false));
+        auto d2d = [&](void* dst, const void* src, size_t bytes) {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        };
+        const size_t nvr = (size_t)c->nv;
         for (int k = 0; k < len; ++k) {
-            CK(cudaMemcpyAsync(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8, cudaMemcpyDeviceToDevice,
-                               c->stream));
-            if (c->nv)
-                CK(cudaMemcpyAsync(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * (size_t)c->nv,
-                                   cudaMemcpyDeviceToDevice, c->stream));
-            if (c->nlig)
-                CK(cudaMemcpyAsync(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig,
-                                   cudaMemcpyDeviceToDevice, c->stream));
-            if (k + 1 < len) {
-                CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
-                c->cur = 1 - c->cur;
-                c->steps += 1;
+            CK(d2d(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8));
+            if (nvr) CK(d2d(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * nvr));
+            if (c->nlig) CK(d2d(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig));
+            const int src = c->cur;
+            CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
+            c->cur = 1 - c->cur;
+            c->steps += 1;
+            if (nvr) {
+                CK(d2d(a->tape_F + (size_t)k * 2 * nv, c->ma.F, 16 * nvr));
+                CK(d2d(a->tape_W + (size_t)k * 9 * nv, c->ma.W, 72 * nvr));
+                CK(d2d(a->tape_st + (size_t)k * 2 * nv, c->ma.stencil, 8 * nvr));
+                CK(d2d(a->tape_G + (size_t)k * N, c->G[src], N * sizeof(longlong2)));
             }
         }
         // adjoint steps, last to first
@@ -1553,9 +1565,12 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
             t.f = a->tape_f + (size_t)k * 9 * N;
             t.dX = a->zero;
             t.dXp = a->zero;
-            t.Gv = a->Gv; t.Gd = a->Gd; t.Wv = a->Wv; t.Wd = a->Wd; t.st = a->st;
-            t.Fv = a->Fv; t.Fd = a->Fd; t.A = a->A; t.Ad = a->Ad; t.box = a->box;
-            t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0;
+            t.Fv = a->tape_F + (size_t)k * 2 * nv;
+            t.Wv = a->tape_W + (size_t)k * 9 * nv;
+            t.st = a->tape_st + (size_t)k * 2 * nv;
+            t.A = a->A; t.Ad = a->Ad; t.box = a->box;
+            t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0; t.th0 = a->th0;
+            g.gfix = a->tape_G + (size_t)k * N;
             t.omega = 1.0 / c->tau; t.gx = c->gx; t.gy = c->gy;
             t.step = s.step + k;
             g.fbar = a->fbar[a->cb];

@@ -23,6 +23,7 @@ struct TangentArgs {
     const double* dks;     // [nmem] tangent of k_s per membrane
     const double* dkb;     // [nmem] tangent of k_b per membrane
     double dsigma;         // tangent of the bond stiffness
+    const double* th0;     // [nv] rest turning angle at each vertex (Eq. bendFor's theta_0)
     double omega, gx, gy;
     long long step;        // n (forward Euler at n = 0)
 };
@@ -31,5 +32,9 @@ cudaError_t launch_tangent_step(const TangentArgs& t, cudaStream_t s);
 // the marker part alone (areas and boxes, forces, shape functions, spreading
 // into t.Gv / t.Gd, which the caller has zeroed)
 cudaError_t launch_tangent_markers(const TangentArgs& t, cudaStream_t s);
+// enclosed areas (value and tangent) and bounding boxes of X^n alone
+cudaError_t launch_tangent_areas(const TangentArgs& t, cudaStream_t s);
+// rest turning angles theta_0 = atan2(cross, dot) of the rest records into th0[nv]
+cudaError_t launch_rest_angles(const MarkerArgs& m, double* th0, cudaStream_t s);
 
 }  // namespace lbib

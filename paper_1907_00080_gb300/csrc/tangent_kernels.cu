@@ -157,7 +157,24 @@ __global__ void k_t_advance(const TangentArgs t) {
     }
 }
 
+__global__ void k_rest_angles(const MarkerArgs m, double* th0) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= m.nv) return;
+    const Rest<double>* rest = static_cast<const Rest<double>*>(m.rest);
+    th0[v] = ::atan2(rest[v].cross, rest[v].dot);
+}
+
 }  // namespace
+
+cudaError_t launch_rest_angles(const MarkerArgs& m, double* th0, cudaStream_t s) {
+    if (m.nv > 0) k_rest_angles<<<(m.nv + 127) / 128, 128, 0, s>>>(m, th0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tangent_areas(const TangentArgs& t, cudaStream_t s) {
+    if (t.m.nv > 0) k_t_area<<<t.m.nmem, 256, 0, s>>>(t);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tangent_markers(const TangentArgs& t, cudaStream_t s) {
     // small blocks: these FP64 kernels have one thread per vertex, spread them over the SMs

@@ -141,9 +141,20 @@ __device__ __forceinline__ bool t_rep_candidate(const TangentArgs& t, double xv,
 // from the other membranes, stretching (Eq. strainFor), bending (Eq. bendFor:
 // own term and the shares of both neighbours) and the area penalty (Eq.
 // areaFor, half of each adjacent element, with the membrane's area t.A).
-// with_rep = false leaves out the repulsion (the adjoint takes it separately).
+// `terms` selects the contributions (kTerm* bits); the adjoint evaluates only
+// those that depend on its seed and takes the repulsion separately.
+enum ForceTerm : unsigned {
+    kTermBond = 1u,
+    kTermRep = 2u,
+    kTermStretch = 4u,
+    kTermBendL = 8u,   // bending moment at vertex v - 1 (depends on X_{v-2} .. X_v)
+    kTermBendV = 16u,  // at v (X_{v-1} .. X_{v+1})
+    kTermBendR = 32u,  // at v + 1 (X_v .. X_{v+2})
+    kTermArea = 64u,
+    kTermAll = 127u
+};
 __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int m, const Seed& s, dual& fx, dual& fy,
-                                               bool with_rep = true) {
+                                               unsigned terms = kTermAll) {
     const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
     const int L = t_ring(off, n, k - 1), R = t_ring(off, n, k + 1);
     const Rest<double>* rest = static_cast<const Rest<double>*>(t.m.rest);
@@ -153,11 +164,11 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
     t_pos(t, L, s, xL, yL);
     t_pos(t, v, s, xv, yv);
     t_pos(t, R, s, xR, yR);
-    if (t.m.nlig > 0) {
+    if ((terms & kTermBond) && t.m.nlig > 0) {
         t_bond_half(t, L, s, fx, fy);
         t_bond_half(t, v, s, fx, fy);
     }
-    if (with_rep && t.m.nmem > 1) {
+    if ((terms & kTermRep) && t.m.nmem > 1) {
         const double c0 = kRepC0;
         bool have_g = false;
         VGeo g;
@@ -182,8 +193,8 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
             }
         }
     }
-    const dual ks = t_ks(t, m, s);
-    {
+    if (terms & kTermStretch) {
+        const dual ks = t_ks(t, m, s);
         const dual rx = xv - xR, ry = yv - yR;
         const dual l = sqrt(rx * rx + ry * ry);
         const dual c = -ks * (l - dual(rest[v].l0)) / l;
@@ -195,17 +206,30 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
         fx -= c2 * qx;
         fy -= c2 * qy;
     }
-    const dual kb = t_kb(t, m, s);
-    {
-        const VGeo gL = t_vgeo(t, off, n, k - 1, s), gv = t_vgeo(t, off, n, k, s), gR = t_vgeo(t, off, n, k + 1, s);
-        const dual mL = kb * (gL.th - dual(atan2(rest[L].cross, rest[L].dot)));
-        const dual mv = kb * (gv.th - dual(atan2(rest[v].cross, rest[v].dot)));
-        const dual mR = kb * (gR.th - dual(atan2(rest[R].cross, rest[R].dot)));
-        const dual sR_L = gL.lR / (gL.lL + gL.lR), sL_R = gR.lL / (gR.lL + gR.lR);
-        fx += mL * sR_L * gL.nx - mv * gv.nx + mR * sL_R * gR.nx;
-        fy += mL * sR_L * gL.ny - mv * gv.ny + mR * sL_R * gR.ny;
+    if (terms & (kTermBendL | kTermBendV | kTermBendR)) {
+        const dual kb = t_kb(t, m, s);
+        if (terms & kTermBendL) {
+            const VGeo gL = t_vgeo(t, off, n, k - 1, s);
+            const dual mL = kb * (gL.th - dual(t.th0[L]));
+            const dual sR_L = gL.lR / (gL.lL + gL.lR);
+            fx += mL * sR_L * gL.nx;
+            fy += mL * sR_L * gL.ny;
+        }
+        if (terms & kTermBendV) {
+            const VGeo gv = t_vgeo(t, off, n, k, s);
+            const dual mv = kb * (gv.th - dual(t.th0[v]));
+            fx -= mv * gv.nx;
+            fy -= mv * gv.ny;
+        }
+        if (terms & kTermBendR) {
+            const VGeo gR = t_vgeo(t, off, n, k + 1, s);
+            const dual mR = kb * (gR.th - dual(t.th0[R]));
+            const dual sL_R = gR.lL / (gR.lL + gR.lR);
+            fx += mR * sL_R * gR.nx;
+            fy += mR * sL_R * gR.ny;
+        }
     }
-    {
+    if (terms & kTermArea) {
         const dual A = t_area(t, m, s);
         const dual c = -t.m.mem_ka[m] * (dual(1.0) - A / dual(t.m.mem_A0[m])) * kPrefT;
         fx += 0.5 * c * (-(yR - yv)) + 0.5 * c * (-(yv - yL));
