@@ -2,12 +2,15 @@
 
   python -m paper_1907_00080_gb300.profile_case --case probe --nx 8192 --ny 1024 --launches 3
   python -m paper_1907_00080_gb300.profile_case --case capillary --steps 40
+  python -m paper_1907_00080_gb300.profile_case --case adjoint --steps 40 --checkpoint-every 20
 
 ``probe``: a channel of nx x ny nodes with soft circular carriers spread over
 it (the coarse capillary's share of nodes under a marker stencil), stepped twice, then ``--launches``
 launches of the fused collide-stream kernel alone (``lbib_profile_fused``).
 ``capillary``: the 640 x 160 coarse capillary stepped ``--steps`` time steps
-(all kernels of the time step).  Prints one JSON line with the timings.
+(all kernels of the time step).  ``adjoint``: the 320 x 160 sensitivity case
+(FP64) recorded for ``--steps`` steps with checkpoints every
+``--checkpoint-every`` steps, then one backward sweep.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -42,13 +45,14 @@ def probe_workload(nx, ny, precision, n_carriers=None, seed=1):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--case", choices=["probe", "capillary"], default="probe")
+    p.add_argument("--case", choices=["probe", "capillary", "adjoint"], default="probe")
     p.add_argument("--nx", type=int, default=8192)
     p.add_argument("--ny", type=int, default=1024)
     p.add_argument("--precision", default="f32")
     p.add_argument("--tiling", default=None, help="vec,ty of the fused kernel")
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--checkpoint-every", type=int, default=20)
     args = p.parse_args(argv)
     build.build()
     lbib.load()
@@ -63,6 +67,17 @@ def main(argv=None):
         alg = ALG_BYTES_PER_NODE[args.precision] * wl.nx * wl.ny
         out.update(nx=wl.nx, ny=wl.ny, tiling=list(sim.tiling), launches=args.launches,
                    ms_per_launch=ms, algorithmic_bytes_per_launch=alg, gbs=alg / (ms * 1e-3) / 1e9)
+    elif args.case == "adjoint":
+        from paper_1907_00080_gb300 import sensitivity
+        rec = sensitivity.Recording(sensitivity.default_params(), args.steps, args.checkpoint_every)
+        try:
+            g = rec.gradient((1.0, 1.0))
+        finally:
+            rec.close()
+        out.update(precision="f64", steps=args.steps, checkpoint_every=args.checkpoint_every,
+                   gradient=[float(v) for v in g])
+        print(json.dumps(out))
+        return 0
     else:
         wl = inputs.coarse_capillary_640x160(args.precision)
         sim = lbib.Simulation(wl, tiling=tiling)
