@@ -88,6 +88,11 @@ _SIGS = {
     "orc_ring_forces": (None, [_I, _DP, _DP, _DP, _DP, _D, _D, _D, _D, _D, _I, _DP, _DP]),
     "orc_p_form": (_D, [_P, _D]),
     "orc_p_rupture": (_D, [_P, _D]),
+    "orc_tangent_create": (_P, [_P]),
+    "orc_tangent_destroy": (None, [_P]),
+    "orc_tangent_seed": (None, [_P, _DP, _DP, _D, _DP, _DP, _DP]),
+    "orc_tangent_step": (None, [_P, _L]),
+    "orc_tangent_get": (None, [_P, _DP, _DP, _DP]),
 }
 
 
@@ -345,3 +350,39 @@ class OracleSim:
         gx, gy = np.zeros((self.ny, self.nx)), np.zeros((self.ny, self.nx))
         lib().orc_spread(self._s, len(pts), _dp(px), _dp(py), _dp(fx), _dp(fy), _dp(gx), _dp(gy))
         return gx, gy
+
+
+# ---------------------------------------------------------------- tangent
+class OracleTangent:
+    """Forward-mode (dual-number) tangent of an OracleSim's trajectory along
+    one direction of (k_s, k_b per membrane, sigma, X^n, X^{n-1}, f^n), with the
+    primal's bond history.  ``step(n)`` advances the simulation and the
+    tangent together (use it instead of ``sim.step``)."""
+
+    def __init__(self, sim):
+        self.sim = sim
+        self._t = lib().orc_tangent_create(sim._s)
+        if not self._t:
+            raise ValueError("the oracle tangent needs kinematic membranes only")
+
+    def __del__(self):
+        t = getattr(self, "_t", None)
+        if t:
+            lib().orc_tangent_destroy(t)
+            self._t = None
+
+    def seed(self, dks=None, dkb=None, dsigma=0.0, dxy=None, dxy_prev=None, df=None):
+        keep = [None if a is None else _f64(a) for a in (dks, dkb, dxy, dxy_prev, df)]
+        ptrs = [None if a is None else _dp(a) for a in keep]
+        lib().orc_tangent_seed(self._t, ptrs[0], ptrs[1], float(dsigma), ptrs[2], ptrs[3], ptrs[4])
+
+    def step(self, n=1):
+        lib().orc_tangent_step(self._t, int(n))
+
+    def get(self):
+        """(dX^n, dX^{n-1}) as (nv, 2) arrays and df^n as (9, ny, nx)."""
+        nv = self.sim.nv
+        dxy, dxp = np.zeros((nv, 2)), np.zeros((nv, 2))
+        df = np.zeros((9, self.sim.ny, self.sim.nx))
+        lib().orc_tangent_get(self._t, _dp(dxy), _dp(dxp), _dp(df))
+        return dxy, dxp, df

@@ -27,6 +27,10 @@
  *  11. bond rupture then formation at X^{n+1}          Sec. 2.2 (wall-particle)
  *  12. diagnostics (mass, enclosed area)               Sec. 2.1, Eq. areaFor
  *
+ * The end of the file holds the forward-mode tangent of steps 1-10 in dual
+ * numbers (orc_tangent_*), differentiated line by line from the code above,
+ * with bond events (step 11) held at the primal's.
+ *
  * Readings of passages the paper leaves open (all listed in the design notes):
  *  - Eq. ForcingTerm is read as the standard Guo term
  *      F_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . G
@@ -826,3 +830,405 @@ double orc_membrane_area(const orc_sim *s, int m) {
     return orc_ring_area(s->mem_n[m], s->x + s->mem_off[m], s->y + s->mem_off[m]);
 }
 double orc_membrane_rest_area(const orc_sim *s, int m) { return s->mem_A0[m]; }
+
+/* ========================================================================= */
+/* Forward-mode tangent of the step (FP64 dual numbers v + d eps, eps^2 = 0)  */
+/*                                                                           */
+/* The derivative of steps 1-10 above along one direction of (k_s, k_b per    */
+/* membrane, sigma, X^n, X^{n-1}, f^n), each step differentiated as written   */
+/* above, with every branch (stencil origin, dropped wall rows, repulsion     */
+/* range, minimum image) taken at the primal value.  Bond events (step 11)    */
+/* are not differentiated: the tangent runs along the primal's bond history.  */
+/* Kinematic membranes only (no rigid projection).                            */
+/* ========================================================================= */
+typedef struct {
+    double v, d;
+} dn;
+
+static dn dn_make(double v, double d) {
+    dn r;
+    r.v = v;
+    r.d = d;
+    return r;
+}
+static dn dn_c(double v) { return dn_make(v, 0.0); }
+static dn dn_add(dn a, dn b) { return dn_make(a.v + b.v, a.d + b.d); }
+static dn dn_sub(dn a, dn b) { return dn_make(a.v - b.v, a.d - b.d); }
+static dn dn_neg(dn a) { return dn_make(-a.v, -a.d); }
+static dn dn_scale(double c, dn a) { return dn_make(c * a.v, c * a.d); }
+static dn dn_mul(dn a, dn b) { return dn_make(a.v * b.v, a.d * b.v + a.v * b.d); }
+/* (a/b)' = (a' - (a/b) b') / b */
+static dn dn_div(dn a, dn b) {
+    double q = a.v / b.v;
+    return dn_make(q, (a.d - q * b.d) / b.v);
+}
+/* sqrt(a)' = a' / (2 sqrt(a)) */
+static dn dn_sqrt(dn a) {
+    double r = sqrt(a.v);
+    return dn_make(r, a.d / (2.0 * r));
+}
+/* atan2(y, x)' = (x y' - y x') / (x^2 + y^2) */
+static dn dn_atan2(dn y, dn x) {
+    return dn_make(atan2(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v));
+}
+static dn dn_fabs(dn a) { return a.v < 0.0 ? dn_neg(a) : a; }
+
+typedef struct {
+    orc_sim *s;                  /* primal (not owned) */
+    long N;
+    double *df, *dftmp;          /* tangent of the pre-collision f^n, scratch */
+    double *dx, *dy, *dxp, *dyp; /* tangent of X^n and X^{n-1} */
+    double *dks, *dkb;           /* tangent of k_s, k_b per membrane */
+    double dsigma;               /* tangent of the bond stiffness */
+    dn *Fx, *Fy;                 /* [nv] force */
+    dn *W;                       /* [nv][9] shape functions */
+    long *idx;                   /* [nv][9] node of each (-1: dropped) */
+    dn *Gx, *Gy;                 /* [N] force field */
+    dn *ux, *uy;                 /* [N] velocity of the collide */
+} orc_tangent;
+
+static dn t_x(const orc_tangent *t, int v) { return dn_make(t->s->x[v], t->dx[v]); }
+static dn t_y(const orc_tangent *t, int v) { return dn_make(t->s->y[v], t->dy[v]); }
+
+/* vertex_geometry on dual positions (ring of n vertices starting at off) */
+static void t_vertex_geometry(const orc_tangent *t, int off, int n, int v, dn *theta, dn *nvx, dn *nvy,
+                              dn *lL, dn *lR) {
+    int L = off + (v + n - 1) % n, C = off + v, R = off + (v + 1) % n;
+    dn eLx = dn_sub(t_x(t, C), t_x(t, L)), eLy = dn_sub(t_y(t, C), t_y(t, L));
+    dn eRx = dn_sub(t_x(t, R), t_x(t, C)), eRy = dn_sub(t_y(t, R), t_y(t, C));
+    dn a = dn_sqrt(dn_add(dn_mul(eLx, eLx), dn_mul(eLy, eLy)));
+    dn b = dn_sqrt(dn_add(dn_mul(eRx, eRx), dn_mul(eRy, eRy)));
+    dn cr = dn_sub(dn_mul(eLx, eRy), dn_mul(eLy, eRx));
+    dn dt = dn_add(dn_mul(eLx, eRx), dn_mul(eLy, eRy));
+    *theta = dn_atan2(cr, dt);
+    dn nx_ = dn_add(dn_div(eLy, a), dn_div(eRy, b));
+    dn ny_ = dn_sub(dn_neg(dn_div(eLx, a)), dn_div(eRx, b));
+    dn nn = dn_sqrt(dn_add(dn_mul(nx_, nx_), dn_mul(ny_, ny_)));
+    *nvx = dn_div(nx_, nn);
+    *nvy = dn_div(ny_, nn);
+    *lL = a;
+    *lR = b;
+}
+
+/* shoelace area about vertex 0, on dual positions */
+static dn t_ring_area(const orc_tangent *t, int off, int n) {
+    dn s = dn_c(0.0);
+    dn xr = t_x(t, off), yr = t_y(t, off);
+    for (int v = 0; v < n; ++v) {
+        int a = off + v, b = off + (v + 1) % n;
+        s = dn_add(s, dn_sub(dn_mul(dn_sub(t_x(t, a), xr), dn_sub(t_y(t, b), yr)),
+                             dn_mul(dn_sub(t_x(t, b), xr), dn_sub(t_y(t, a), yr))));
+    }
+    return dn_scale(0.5, s);
+}
+
+/* steps 3-5 (Eqs. strainFor, bendFor, areaFor) of membrane m on duals */
+static void t_ring_forces(orc_tangent *t, int m) {
+    orc_sim *s = t->s;
+    int off = s->mem_off[m], n = s->mem_n[m];
+    dn ks = dn_make(s->mem_ks[m], t->dks[m]), kb = dn_make(s->mem_kb[m], t->dkb[m]);
+    for (int v = 0; v < n; ++v) {
+        int a = off + v, b = off + (v + 1) % n;
+        dn rx = dn_sub(t_x(t, a), t_x(t, b)), ry = dn_sub(t_y(t, a), t_y(t, b));
+        dn l = dn_sqrt(dn_add(dn_mul(rx, rx), dn_mul(ry, ry)));
+        dn c = dn_div(dn_mul(dn_neg(ks), dn_sub(l, dn_c(s->l0[a]))), l);
+        t->Fx[a] = dn_add(t->Fx[a], dn_mul(c, rx));
+        t->Fy[a] = dn_add(t->Fy[a], dn_mul(c, ry));
+        t->Fx[b] = dn_sub(t->Fx[b], dn_mul(c, rx));
+        t->Fy[b] = dn_sub(t->Fy[b], dn_mul(c, ry));
+    }
+    for (int v = 0; v < n; ++v) {
+        int L = off + (v + n - 1) % n, C = off + v, R = off + (v + 1) % n;
+        dn th, nvx, nvy, lL, lR;
+        t_vertex_geometry(t, off, n, v, &th, &nvx, &nvy, &lL, &lR);
+        dn mo = dn_mul(kb, dn_sub(th, dn_c(s->th0[C])));
+        dn sL = dn_div(lL, dn_add(lL, lR)), sR = dn_div(lR, dn_add(lL, lR));
+        t->Fx[L] = dn_add(t->Fx[L], dn_mul(dn_mul(mo, sL), nvx));
+        t->Fy[L] = dn_add(t->Fy[L], dn_mul(dn_mul(mo, sL), nvy));
+        t->Fx[C] = dn_sub(t->Fx[C], dn_mul(mo, nvx));
+        t->Fy[C] = dn_sub(t->Fy[C], dn_mul(mo, nvy));
+        t->Fx[R] = dn_add(t->Fx[R], dn_mul(dn_mul(mo, sR), nvx));
+        t->Fy[R] = dn_add(t->Fy[R], dn_mul(dn_mul(mo, sR), nvy));
+    }
+    dn A = t_ring_area(t, off, n);
+    dn c = dn_scale(s->p_ref, dn_scale(-s->mem_ka[m], dn_sub(dn_c(1.0), dn_div(A, dn_c(s->mem_A0[m])))));
+    for (int v = 0; v < n; ++v) {
+        int a = off + v, b = off + (v + 1) % n;
+        dn ex = dn_sub(t_x(t, b), t_x(t, a)), ey = dn_sub(t_y(t, b), t_y(t, a));
+        dn Fx = dn_mul(c, dn_neg(ey)), Fy = dn_mul(c, ex);
+        t->Fx[a] = dn_add(t->Fx[a], dn_scale(0.5, Fx));
+        t->Fy[a] = dn_add(t->Fy[a], dn_scale(0.5, Fy));
+        t->Fx[b] = dn_add(t->Fx[b], dn_scale(0.5, Fx));
+        t->Fy[b] = dn_add(t->Fy[b], dn_scale(0.5, Fy));
+    }
+}
+
+/* steps 1-5 on duals (orc_compute_forces differentiated) */
+static void t_compute_forces(orc_tangent *t) {
+    orc_sim *s = t->s;
+    int nv = s->nv;
+    for (int v = 0; v < nv; ++v) {
+        t->Fx[v] = dn_c(0.0);
+        t->Fy[v] = dn_c(0.0);
+    }
+    /* 1. bonds (Eq. adhFor); the minimum-image shift is a constant */
+    dn sigma = dn_make(s->sigma, t->dsigma);
+    for (int l = 0; l < s->nlig; ++l) {
+        int r = s->bond_of_lig[l];
+        if (r < 0) continue;
+        int a = s->lig_elem[l];
+        int m = s->vert_mem[a];
+        int b = s->mem_off[m] + (a - s->mem_off[m] + 1) % s->mem_n[m];
+        dn cx = dn_scale(0.5, dn_add(t_x(t, a), t_x(t, b)));
+        dn cy = dn_scale(0.5, dn_add(t_y(t, a), t_y(t, b)));
+        dn dx = dn_sub(dn_c(s->rx[r]), cx), dy = dn_sub(dn_c(s->ry[r]), cy);
+        double sx = dx.v, sy = dy.v;
+        min_image(s, &sx, &sy);
+        dx.v = sx;
+        dy.v = sy;
+        dn d = dn_sqrt(dn_add(dn_mul(dx, dx), dn_mul(dy, dy)));
+        dn c = dn_div(dn_mul(sigma, dn_sub(d, dn_c(s->y_eq))), d);
+        t->Fx[a] = dn_add(t->Fx[a], dn_scale(0.5, dn_mul(c, dx)));
+        t->Fy[a] = dn_add(t->Fy[a], dn_scale(0.5, dn_mul(c, dy)));
+        t->Fx[b] = dn_add(t->Fx[b], dn_scale(0.5, dn_mul(c, dx)));
+        t->Fy[b] = dn_add(t->Fy[b], dn_scale(0.5, dn_mul(c, dy)));
+    }
+    /* 2. repulsion (Eq. repFor), pairs within d_rep at the primal distance */
+    if (s->nmem > 1) {
+        const double c0 = 1e-4 / (8.0 * sqrt(2.0));
+        for (int a = 0; a < nv; ++a) {
+            int ma = s->vert_mem[a];
+            int off = s->mem_off[ma], n = s->mem_n[ma];
+            dn th, nvx, nvy, lL, lR;
+            t_vertex_geometry(t, off, n, a - off, &th, &nvx, &nvy, &lL, &lR);
+            for (int b = 0; b < nv; ++b) {
+                if (s->vert_mem[b] == ma) continue;
+                dn dx = dn_sub(t_x(t, a), t_x(t, b)), dy = dn_sub(t_y(t, a), t_y(t, b));
+                double sx = dx.v, sy = dy.v;
+                min_image(s, &sx, &sy);
+                dx.v = sx;
+                dy.v = sy;
+                dn d = dn_sqrt(dn_add(dn_mul(dx, dx), dn_mul(dy, dy)));
+                if (d.v < s->d_rep) {
+                    dn d5 = dn_mul(dn_mul(dn_mul(dn_mul(d, d), d), d), d);
+                    dn mag = dn_scale(c0, dn_sqrt(dn_div(dn_c(1.0), d5)));
+                    t->Fx[a] = dn_sub(t->Fx[a], dn_mul(mag, nvx));
+                    t->Fy[a] = dn_sub(t->Fy[a], dn_mul(mag, nvy));
+                }
+            }
+        }
+    }
+    /* 3-5 */
+    for (int m = 0; m < s->nmem; ++m) t_ring_forces(t, m);
+}
+
+/* Roma kernel on a dual argument */
+static dn t_roma(dn r) {
+    dn a = dn_fabs(r);
+    if (a.v <= 0.5) return dn_scale(1.0 / 3.0, dn_add(dn_c(1.0), dn_sqrt(dn_sub(dn_c(1.0), dn_scale(3.0, dn_mul(a, a))))));
+    if (a.v <= 1.5) {
+        dn b = dn_sub(dn_c(1.0), a);
+        dn q = dn_sqrt(dn_sub(dn_c(1.0), dn_scale(3.0, dn_mul(b, b))));
+        return dn_div(dn_sub(dn_sub(dn_c(5.0), dn_scale(3.0, a)), q), dn_c(6.0));
+    }
+    return dn_c(0.0);
+}
+
+/* orc_ib_weights on a dual point (same stencil, same dropped rows) */
+static void t_ib_weights(const orc_sim *s, dn px, dn py, dn w[9], long idx[9]) {
+    long i0 = (long)floor(px.v + 0.5), j0 = (long)floor(py.v + 0.5);
+    dn Wr[9], rx[9], ry[9];
+    int nvalid = 0;
+    for (int b = -1; b <= 1; ++b) {
+        for (int a = -1; a <= 1; ++a) {
+            int k = (b + 1) * 3 + (a + 1);
+            long i = i0 + a, j = j0 + b;
+            rx[k] = dn_sub(dn_c((double)i), px);
+            ry[k] = dn_sub(dn_c((double)j), py);
+            int inside = s->walls ? (j >= 0 && j < s->ny) : 1;
+            if (inside) {
+                Wr[k] = dn_mul(t_roma(rx[k]), t_roma(ry[k]));
+                idx[k] = imod(j, s->ny) * s->nx + imod(i, s->nx);
+                ++nvalid;
+            } else {
+                Wr[k] = dn_c(0.0);
+                idx[k] = -1;
+            }
+        }
+    }
+    if (nvalid == 9) {
+        for (int k = 0; k < 9; ++k) w[k] = Wr[k];
+        return;
+    }
+    dn A[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) A[r][c] = dn_c(0.0);
+    dn sumW = dn_c(0.0);
+    for (int k = 0; k < 9; ++k) {
+        dn p[3] = {dn_c(1.0), rx[k], ry[k]};
+        sumW = dn_add(sumW, Wr[k]);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[r][c] = dn_add(A[r][c], dn_mul(dn_mul(Wr[k], p[r]), p[c]));
+    }
+    dn c00 = dn_sub(dn_mul(A[1][1], A[2][2]), dn_mul(A[1][2], A[2][1]));
+    dn c10 = dn_neg(dn_sub(dn_mul(A[1][0], A[2][2]), dn_mul(A[1][2], A[2][0])));
+    dn c20 = dn_sub(dn_mul(A[1][0], A[2][1]), dn_mul(A[1][1], A[2][0]));
+    dn det = dn_add(dn_add(dn_mul(A[0][0], c00), dn_mul(A[0][1], c10)), dn_mul(A[0][2], c20));
+    if (det.v > 1e-10) {
+        dn cv[3] = {dn_div(c00, det), dn_div(c10, det), dn_div(c20, det)};
+        for (int k = 0; k < 9; ++k)
+            w[k] = dn_mul(Wr[k], dn_add(dn_add(cv[0], dn_mul(cv[1], rx[k])), dn_mul(cv[2], ry[k])));
+    } else if (sumW.v > 0.0) {
+        for (int k = 0; k < 9; ++k) w[k] = dn_div(Wr[k], sumW);
+    } else {
+        for (int k = 0; k < 9; ++k) w[k] = dn_c(0.0);
+    }
+}
+
+/* steps 6-10 and the tangent of the populations, on duals; then the primal
+ * step.  Reads the primal state of step n before step_once replaces it. */
+static void t_step_once(orc_tangent *t) {
+    orc_sim *s = t->s;
+    long N = t->N;
+    int nv = s->nv;
+    t_compute_forces(t);
+    /* 6. weights at X^n; 7. spread */
+    for (int v = 0; v < nv; ++v) t_ib_weights(s, t_x(t, v), t_y(t, v), t->W + 9 * v, t->idx + 9 * v);
+    for (long n = 0; n < N; ++n) {
+        t->Gx[n] = dn_c(s->gx);
+        t->Gy[n] = dn_c(s->gy);
+    }
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < 9; ++k) {
+            long j = t->idx[9 * v + k];
+            if (j < 0) continue;
+            t->Gx[j] = dn_add(t->Gx[j], dn_mul(t->W[9 * v + k], t->Fx[v]));
+            t->Gy[j] = dn_add(t->Gy[j], dn_mul(t->W[9 * v + k], t->Fy[v]));
+        }
+    /* 8. collide (Eqs. feq, forcedBGK, ForcingTerm with rho u = sum f e + G/2) */
+    double pre = 1.0 - 1.0 / (2.0 * s->tau);
+    for (long n = 0; n < N; ++n) {
+        dn f[9];
+        for (int i = 0; i < 9; ++i) f[i] = dn_make(s->f[i * N + n], t->df[i * N + n]);
+        dn r = dn_c(0.0), jx = dn_c(0.0), jy = dn_c(0.0);
+        for (int i = 0; i < 9; ++i) {
+            r = dn_add(r, f[i]);
+            jx = dn_add(jx, dn_scale((double)EX[i], f[i]));
+            jy = dn_add(jy, dn_scale((double)EY[i], f[i]));
+        }
+        dn gx = t->Gx[n], gy = t->Gy[n];
+        jx = dn_add(jx, dn_scale(0.5, gx));
+        jy = dn_add(jy, dn_scale(0.5, gy));
+        dn ux = dn_div(jx, r), uy = dn_div(jy, r);
+        t->ux[n] = ux;
+        t->uy[n] = uy;
+        dn uu = dn_add(dn_mul(ux, ux), dn_mul(uy, uy));
+        for (int i = 0; i < 9; ++i) {
+            dn eu = dn_add(dn_scale((double)EX[i], ux), dn_scale((double)EY[i], uy));
+            dn feq = dn_scale(W9[i], dn_mul(r, dn_sub(dn_add(dn_add(dn_c(1.0), dn_scale(3.0, eu)),
+                                                             dn_scale(4.5, dn_mul(eu, eu))),
+                                                      dn_scale(1.5, uu))));
+            dn cx = dn_add(dn_scale(3.0, dn_sub(dn_c((double)EX[i]), ux)), dn_scale(9.0 * EX[i], eu));
+            dn cy = dn_add(dn_scale(3.0, dn_sub(dn_c((double)EY[i]), uy)), dn_scale(9.0 * EY[i], eu));
+            dn F = dn_scale(pre * W9[i], dn_add(dn_mul(cx, gx), dn_mul(cy, gy)));
+            dn out = dn_add(dn_sub(f[i], dn_scale(1.0 / s->tau, dn_sub(f[i], feq))), F);
+            t->dftmp[i * N + n] = out.d;
+        }
+    }
+    /* streaming of the tangent: the same permutation as the populations */
+    orc_stream(s, t->dftmp, t->df);
+    /* 9. interpolation; 10. BDF2 (Euler on step 0) */
+    for (int v = 0; v < nv; ++v) {
+        dn a = dn_c(0.0), b = dn_c(0.0);
+        for (int k = 0; k < 9; ++k) {
+            long j = t->idx[9 * v + k];
+            if (j < 0) continue;
+            a = dn_add(a, dn_mul(t->W[9 * v + k], t->ux[j]));
+            b = dn_add(b, dn_mul(t->W[9 * v + k], t->uy[j]));
+        }
+        double nx_, ny_;
+        if (s->step == 0) {
+            nx_ = t->dx[v] + a.d;
+            ny_ = t->dy[v] + b.d;
+        } else {
+            nx_ = (2.0 / 3.0) * (2.0 * t->dx[v] - 0.5 * t->dxp[v] + a.d);
+            ny_ = (2.0 / 3.0) * (2.0 * t->dy[v] - 0.5 * t->dyp[v] + b.d);
+        }
+        t->dxp[v] = t->dx[v];
+        t->dyp[v] = t->dy[v];
+        t->dx[v] = nx_;
+        t->dy[v] = ny_;
+    }
+    step_once(s);
+}
+
+/* Tangent object.  Returns NULL if a membrane is rigid-projected. */
+orc_tangent *orc_tangent_create(orc_sim *s) {
+    for (int m = 0; m < s->nmem; ++m)
+        if (s->mem_kind[m] == 1) return NULL;
+    orc_tangent *t = (orc_tangent *)calloc(1, sizeof(orc_tangent));
+    long N = (long)s->nx * s->ny;
+    int nv = s->nv > 0 ? s->nv : 1, nm = s->nmem > 0 ? s->nmem : 1;
+    t->s = s;
+    t->N = N;
+    t->df = (double *)calloc(9 * N, sizeof(double));
+    t->dftmp = (double *)calloc(9 * N, sizeof(double));
+    t->dx = (double *)calloc(nv, sizeof(double));
+    t->dy = (double *)calloc(nv, sizeof(double));
+    t->dxp = (double *)calloc(nv, sizeof(double));
+    t->dyp = (double *)calloc(nv, sizeof(double));
+    t->dks = (double *)calloc(nm, sizeof(double));
+    t->dkb = (double *)calloc(nm, sizeof(double));
+    t->Fx = (dn *)calloc(nv, sizeof(dn));
+    t->Fy = (dn *)calloc(nv, sizeof(dn));
+    t->W = (dn *)calloc(9 * (size_t)nv, sizeof(dn));
+    t->idx = (long *)calloc(9 * (size_t)nv, sizeof(long));
+    t->Gx = (dn *)calloc(N, sizeof(dn));
+    t->Gy = (dn *)calloc(N, sizeof(dn));
+    t->ux = (dn *)calloc(N, sizeof(dn));
+    t->uy = (dn *)calloc(N, sizeof(dn));
+    return t;
+}
+
+void orc_tangent_destroy(orc_tangent *t) {
+    if (!t) return;
+    free(t->df); free(t->dftmp); free(t->dx); free(t->dy); free(t->dxp); free(t->dyp);
+    free(t->dks); free(t->dkb); free(t->Fx); free(t->Fy); free(t->W); free(t->idx);
+    free(t->Gx); free(t->Gy); free(t->ux); free(t->uy);
+    free(t);
+}
+
+/* direction: dks, dkb [nmem] (NULL = 0), dsigma, dxy / dxy_prev [nv][2]
+ * (NULL = 0; dxy_prev NULL = dxy), df [9][ny][nx] of the pre-collision
+ * populations (NULL = 0) */
+void orc_tangent_seed(orc_tangent *t, const double *dks, const double *dkb, double dsigma, const double *dxy,
+                      const double *dxy_prev, const double *df) {
+    orc_sim *s = t->s;
+    for (int m = 0; m < s->nmem; ++m) {
+        t->dks[m] = dks ? dks[m] : 0.0;
+        t->dkb[m] = dkb ? dkb[m] : 0.0;
+    }
+    t->dsigma = dsigma;
+    const double *pv = dxy_prev ? dxy_prev : dxy;
+    for (int v = 0; v < s->nv; ++v) {
+        t->dx[v] = dxy ? dxy[2 * v] : 0.0;
+        t->dy[v] = dxy ? dxy[2 * v + 1] : 0.0;
+        t->dxp[v] = pv ? pv[2 * v] : 0.0;
+        t->dyp[v] = pv ? pv[2 * v + 1] : 0.0;
+    }
+    for (long k = 0; k < 9 * t->N; ++k) t->df[k] = df ? df[k] : 0.0;
+}
+
+/* n primal steps with their tangent */
+void orc_tangent_step(orc_tangent *t, long n) {
+    for (long k = 0; k < n; ++k) t_step_once(t);
+}
+
+void orc_tangent_get(const orc_tangent *t, double *dxy, double *dxy_prev, double *df) {
+    const orc_sim *s = t->s;
+    for (int v = 0; v < s->nv; ++v) {
+        if (dxy) { dxy[2 * v] = t->dx[v]; dxy[2 * v + 1] = t->dy[v]; }
+        if (dxy_prev) { dxy_prev[2 * v] = t->dxp[v]; dxy_prev[2 * v + 1] = t->dyp[v]; }
+    }
+    if (df) memcpy(df, t->df, sizeof(double) * 9 * t->N);
+}

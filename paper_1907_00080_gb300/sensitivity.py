@@ -98,19 +98,25 @@ def jacobian(p, steps, seed=0, bonds="default"):
         finally:
             lbib.lbib_tangent_destroy(t)
             sim.close()
-        j1, j2, (off, n, terms, y_eq) = observables(wl, xy, bonds_f)
+        j1, j2, _ = observables(wl, xy, bonds_f)
         if J is None:
             J, bond_hist = np.array([j1, j2]), bonds_f
-        dj1 = float(dX[off:off + n, 1].mean())
-        dj2 = 0.0
-        for a, b, d, dist in terms:
-            dc = 0.5 * (dX[a] + dX[b])
-            ddist = -float(np.dot(d, dc)) / dist
-            dj2 += wl.sigma_lu * (dist - y_eq) * ddist
-            if k == 2:
-                dj2 += 0.5 * (dist - y_eq) ** 2
-        jac[:, k] = (dj1, dj2)
+        jac[:, k] = observable_directional(wl, xy, bonds_f, dX, dsig)
     return J, jac, bond_hist
+
+
+def observable_directional(wl, xy, bonds, dX, dsigma):
+    """(dJ1, dJ2) along a direction that moves the final markers by dX and
+    the bond stiffness by dsigma."""
+    _, _, (off, n, terms, y_eq) = observables(wl, xy, bonds)
+    dj1 = float(dX[off:off + n, 1].mean())
+    dj2 = 0.0
+    for a, b, d, dist in terms:
+        dc = 0.5 * (dX[a] + dX[b])
+        ddist = -float(np.dot(d, dc)) / dist
+        dj2 += wl.sigma_lu * (dist - y_eq) * ddist
+        dj2 += dsigma * 0.5 * (dist - y_eq) ** 2
+    return dj1, dj2
 
 
 def observable_gradient(wl, xy, bonds, w):

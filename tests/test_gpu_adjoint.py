@@ -298,3 +298,57 @@ def test_error_paths():
             L.lbib_adjoint_destroy(adj)
     finally:
         sim.close()
+
+
+def test_derivatives_match_the_oracle_tangent():
+    """The oracle's own forward-mode tangent (dual numbers in the plain C
+    oracle, pinned to the oracle's central differences in
+    test_oracle_tangent.py) on the sensitivity case: the GPU tangent's marker
+    derivatives along a random direction of every parameter and marker, and
+    the adjoint's dJ/dp for the four carrier parameters."""
+    import oracle
+    from helpers import make_oracle
+    L = lb()
+    steps = 60
+    p0 = sensitivity.default_params()
+    wl = sensitivity.make_workload(p0, steps)
+    nm, nv = len(wl.membranes), wl.n_vertices
+    nc = len(wl.membranes[-1].xy)
+
+    def oracle_run(dks, dkb, dsig, dxy):
+        s = make_oracle(wl)
+        t = oracle.OracleTangent(s)
+        t.seed(dks, dkb, dsig, dxy, None)
+        t.step(steps)
+        dX, _, _ = t.get()
+        return dX, s.markers(), s.bonds()
+
+    rng = np.random.default_rng(21)
+    dks, dkb = rng.standard_normal(nm) * 1e-3, rng.standard_normal(nm) * 1e-3
+    dsig = float(rng.standard_normal()) * 1e-4
+    dxy = rng.standard_normal((nv, 2))
+    dX_o, _, bonds_o = oracle_run(dks, dkb, dsig, dxy)
+    dX_g, _ = tangent_run(wl, steps, dks, dkb, dsig, dxy)
+    assert np.abs(dX_g - dX_o).max() <= 1e-8 * np.abs(dX_o).max(), np.abs(dX_g - dX_o).max()
+
+    jac_o = np.zeros((2, 4))
+    for k in range(4):
+        a, b = np.zeros(nm), np.zeros(nm)
+        s_ = 0.0
+        d = np.zeros((nv, 2))
+        if k == 0:
+            a[-1] = 1.0
+        elif k == 1:
+            b[-1] = 1.0
+        elif k == 2:
+            s_ = 1.0
+        else:
+            d[nv - nc:, 1] = 1.0
+        dX, xy, bo = oracle_run(a, b, s_, d)
+        jac_o[:, k] = sensitivity.observable_directional(wl, xy, bo, dX, s_)
+    J, jac_a, bonds = sensitivity.adjoint_jacobian(p0, steps, checkpoint_every=16)
+    np.testing.assert_array_equal(bonds, bonds_o)
+    for i in range(2):
+        for k in range(4):
+            assert abs(jac_a[i, k] - jac_o[i, k]) <= 1e-8 * abs(jac_o[i, k]) + 1e-11 * np.abs(jac_o[i]).max(), \
+                (i, sensitivity.PARAMS[k], jac_a[i, k], jac_o[i, k])
