@@ -498,7 +498,8 @@ def differentiation_form(lbib, torch, steps=5000, checkpoint_every=250):
     carrier released 1 lu above the wall), FP64: dJ/dp of the carrier's final
     height J1 and bond energy J2 with respect to (k_s, k_b, sigma, release
     height).  Reverse mode: one recorded run (checkpoints every 250 steps) and
-    one backward sweep per observable, each giving all four derivatives.
+    one backward sweep per observable, each giving all four derivatives; from
+    an FP64 forward run and from an FP32 one (FP64 adjoint in both).
     Forward mode: four tangent runs.  Both timed against the plain FP64 solver
     over the same steps (host wall clock around synchronised calls)."""
     from paper_1907_00080_gb300 import sensitivity
@@ -519,6 +520,27 @@ def differentiation_form(lbib, torch, steps=5000, checkpoint_every=250):
     finally:
         rec.close()
     jac_a = np.stack([g1, g2])
+    # the same gradient from an FP32 forward run (FP64 adjoint and accumulation)
+    sim32 = lbib.Simulation(sensitivity.make_workload(p0, steps, precision="f32"), precision="f32")
+    sim32.step(10)
+    sim32.sync()
+    t0 = time.perf_counter()
+    sim32.step(steps)
+    sim32.sync()
+    t_primal32 = time.perf_counter() - t0
+    sim32.close()
+    t0 = time.perf_counter()
+    rec32 = sensitivity.Recording(p0, steps, checkpoint_every=checkpoint_every, precision="f32")
+    t_rec32 = time.perf_counter() - t0
+    try:
+        t0 = time.perf_counter()
+        h1 = rec32.gradient((1.0, 0.0))
+        t_sweep32 = time.perf_counter() - t0
+        h2 = rec32.gradient((0.0, 1.0))
+    finally:
+        rec32.close()
+    jac32 = np.stack([h1, h2])
+    rel32 = [float(np.max(np.abs(jac32[i] - jac_a[i]) / np.maximum(np.abs(jac_a[i]), 1e-300))) for i in range(2)]
     t0 = time.perf_counter()
     J2, jac, bonds = sensitivity.jacobian(p0, steps)
     t_jac = time.perf_counter() - t0
@@ -531,6 +553,11 @@ def differentiation_form(lbib, torch, steps=5000, checkpoint_every=250):
                         "sweep_ms_per_step": 1e3 * t_sweep / steps,
                         "gradient_cost_vs_primal": (t_rec + t_sweep) / t_primal,
                         "max_rel_diff_vs_tangent": rel},
+            "adjoint_fp32_forward": {"primal_ms_per_step": 1e3 * t_primal32 / steps,
+                                     "record_ms_per_step": 1e3 * t_rec32 / steps,
+                                     "sweep_ms_per_step": 1e3 * t_sweep32 / steps,
+                                     "gradient_cost_vs_fp32_primal": (t_rec32 + t_sweep32) / t_primal32,
+                                     "max_rel_diff_vs_fp64_adjoint": rel32},
             "tangent": {"jacobian_ms_per_step": 1e3 * t_jac / steps,
                         "cost_per_direction_vs_primal": t_jac / 4 / t_primal,
                         "gradient_cost_vs_primal": t_jac / 4 / t_primal * 4}}

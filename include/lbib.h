@@ -254,10 +254,15 @@ void lbib_tangent_destroy(lbib_tangent* t);
  * context's own step (bit-identical to the recorded run) and then applies the
  * adjoint step to the tape in reverse order.
  *
- * lbib_adjoint_create: ctx must be LBIB_F64, without rigid-projected
- *   membranes and with at least 5 vertices per membrane (LBIB_E_INVALID
- *   otherwise); checkpoint_every >= 1; LBIB_E_OOM if the tape does not fit.
- *   The adjoint borrows the context (destroy the adjoint first).
+ * Precision: the recorded run is the context's own, in any precision (e.g.
+ * an FP32 forward run); the tape holds FP64 copies of its states, and the
+ * adjoint arithmetic and every gradient are FP64.  The result is then the
+ * derivative of the exact-arithmetic step along that trajectory.
+ *
+ * lbib_adjoint_create: ctx without rigid-projected membranes and with at
+ *   least 5 vertices per membrane (LBIB_E_INVALID otherwise);
+ *   checkpoint_every >= 1; LBIB_E_OOM if the tape does not fit.  The adjoint
+ *   borrows the context (destroy the adjoint first).
  * lbib_adjoint_record: advance the context n >= 1 steps (instead of
  *   lbib_step) from its current state, keeping the checkpoints; replaces an
  *   earlier recording; synchronises and returns the step status.

@@ -35,6 +35,12 @@ struct AdjointArgs {
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
 
+// FP64 copies for the tape of a context of another precision: stored
+// populations (deviations, scaled storage undone) and compute-type arrays
+cudaError_t launch_widen_storage(lbib_precision prec, const void* src, double* dst, size_t n, float inv_scale,
+                                 cudaStream_t s);
+cudaError_t launch_widen_compute(lbib_precision prec, const void* src, double* dst, size_t n, cudaStream_t s);
+
 // adjoint of the stored deviations <-> adjoint of the pre-collision
 // populations in the read-back layout (f^n_i(x) = w_i + d*_i(source of (x, i)))
 cudaError_t launch_adjoint_perm(const double* in, double* out, int nx, int ny, int walls, int to_storage,

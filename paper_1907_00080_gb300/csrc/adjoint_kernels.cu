@@ -354,6 +354,18 @@ __global__ void k_a_perm(const double* __restrict__ in, double* __restrict__ out
     }
 }
 
+template <typename S>
+__global__ void k_widen_storage(const S* __restrict__ src, double* __restrict__ dst, size_t n, float inv) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (double)Storage<S>::load(src[k], inv);
+}
+
+template <typename C>
+__global__ void k_widen_compute(const C* __restrict__ src, double* __restrict__ dst, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = (double)src[k];
+}
+
 int node_grid(size_t N) { return (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096); }
 
 }  // namespace
@@ -376,6 +388,31 @@ cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
         k_a_forces<<<dim3(nvb, kNumTasks), 32, 0, s>>>(a);
         k_a_area<<<nvb, 32, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_storage(lbib_precision prec, const void* src, double* dst, size_t n, float inv_scale,
+                                 cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int g = node_grid(n);
+    switch (prec) {
+        case LBIB_F64: k_widen_storage<double><<<g, 256, 0, s>>>(static_cast<const double*>(src), dst, n, inv_scale); break;
+        case LBIB_F32: k_widen_storage<float><<<g, 256, 0, s>>>(static_cast<const float*>(src), dst, n, inv_scale); break;
+        case LBIB_F32_STORE_F16:
+            k_widen_storage<__half><<<g, 256, 0, s>>>(static_cast<const __half*>(src), dst, n, inv_scale);
+            break;
+        default:
+            k_widen_storage<__nv_bfloat16><<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(src), dst, n,
+                                                             inv_scale);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_widen_compute(lbib_precision prec, const void* src, double* dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int g = node_grid(n);
+    if (prec == LBIB_F64) k_widen_compute<double><<<g, 256, 0, s>>>(static_cast<const double*>(src), dst, n);
+    else k_widen_compute<float><<<g, 256, 0, s>>>(static_cast<const float*>(src), dst, n);
     return cudaGetLastError();
 }
 

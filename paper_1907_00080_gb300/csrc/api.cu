@@ -1153,6 +1153,7 @@ struct lbib_tangent {
     double *Fv = nullptr, *Fd = nullptr, *A = nullptr, *Ad = nullptr, *dks = nullptr, *dkb = nullptr;
     double* box = nullptr;
     double* th0 = nullptr;
+    double* l0 = nullptr;
     int* st = nullptr;
     double dsigma = 0.0;
     std::vector<void*> allocs;
@@ -1192,12 +1193,12 @@ extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     ok = ok && (t->Fv = (double*)get(2 * nv * 8)) && (t->Fd = (double*)get(2 * nv * 8));
     ok = ok && (t->A = (double*)get(nm * 8)) && (t->Ad = (double*)get(nm * 8)) && (t->box = (double*)get(4 * nm * 8));
     ok = ok && (t->dks = (double*)get(nm * 8)) && (t->dkb = (double*)get(nm * 8));
-    ok = ok && (t->st = (int*)get(2 * nv * 4)) && (t->th0 = (double*)get(nv * 8));
+    ok = ok && (t->st = (int*)get(2 * nv * 4)) && (t->th0 = (double*)get(nv * 8)) && (t->l0 = (double*)get(nv * 8));
     if (!ok) {
         lbib_tangent_destroy(t);
         return fail(c, LBIB_E_OOM, "tangent buffers");
     }
-    launch_rest_angles(c->ma, t->th0, c->stream);
+    launch_rest_fp64(c->prec, c->ma, t->l0, t->th0, c->stream);
     cudaMemsetAsync(t->fd[0], 0, 9 * N * 8, c->stream);
     cudaMemsetAsync(t->fd[1], 0, 9 * N * 8, c->stream);
     for (int b = 0; b < 3; ++b) cudaMemsetAsync(t->dX[b], 0, 2 * nv * 8, c->stream);
@@ -1251,7 +1252,7 @@ extern "C" lbib_status lbib_tangent_step(lbib_tangent* t, int64_t n) {
         a.dXn = t->dX[t->in];
         a.Gv = t->Gv; a.Gd = t->Gd; a.u = t->u; a.ud = t->ud; a.Wv = t->Wv; a.Wd = t->Wd;
         a.st = t->st; a.Fv = t->Fv; a.Fd = t->Fd; a.A = t->A; a.Ad = t->Ad; a.box = t->box;
-        a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma; a.th0 = t->th0;
+        a.dks = t->dks; a.dkb = t->dkb; a.dsigma = t->dsigma; a.th0 = t->th0; a.l0 = t->l0;
         a.omega = 1.0 / c->tau; a.gx = c->gx; a.gy = c->gy;
         a.step = c->steps;
         CK(launch_tangent_step(a, c->stream));
@@ -1289,10 +1290,12 @@ extern "C" lbib_status lbib_tangent_read(lbib_tangent* t, double* dxy, double* d
 // applies the adjoint step to the tape in reverse order.
 namespace {
 
-// the context's full step state at a step boundary (FP64 storage)
+// the context's full step state at a step boundary (in the context's own
+// storage and position layouts)
 struct Snap {
     void* mem = nullptr;
-    double *f = nullptr, *X = nullptr, *Xp = nullptr;
+    void* f = nullptr;
+    double *X = nullptr, *Xp = nullptr;
     int *bond = nullptr, *owner = nullptr, *owner_cell = nullptr;
     float4* seg_box = nullptr;
     long long* d_step = nullptr;
@@ -1302,7 +1305,7 @@ struct Snap {
 size_t snap_bytes(const lbib_ctx* c) {
     Arena a;
     const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
-    a.take<double>(9 * N);
+    a.take<char>(9 * N * c->pop_elem);
     a.take<double>(2 * nv);
     a.take<double>(2 * nv);
     a.take<int>(nlig);
@@ -1317,7 +1320,7 @@ void snap_layout(const lbib_ctx* c, Snap& s) {
     Arena a;
     a.base = static_cast<char*>(s.mem);
     const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
-    s.f = a.take<double>(9 * N);
+    s.f = a.take<char>(9 * N * c->pop_elem);
     s.X = a.take<double>(2 * nv);
     s.Xp = a.take<double>(2 * nv);
     s.bond = a.take<int>(nlig);
@@ -1336,7 +1339,7 @@ cudaError_t snap_copy(lbib_ctx* c, Snap& s, bool to_snap) {
                                c->stream);
     };
     cudaError_t e;
-    if ((e = cp(s.f, c->f[c->cur], 9 * N * 8)) != cudaSuccess) return e;
+    if ((e = cp(s.f, c->f[c->cur], 9 * N * c->pop_elem)) != cudaSuccess) return e;
     if ((e = cp(s.X, c->ma.X, 16 * nv)) != cudaSuccess) return e;
     if ((e = cp(s.Xp, c->ma.Xp, 16 * nv)) != cudaSuccess) return e;
     if ((e = cp(s.bond, c->ma.bond_of_lig, 4 * nlig)) != cudaSuccess) return e;
@@ -1374,7 +1377,7 @@ struct lbib_adjoint {
     double *XB = nullptr, *XPB = nullptr, *ubar = nullptr, *Gbar = nullptr, *Fbar = nullptr, *Wbar = nullptr;
     double *Abar = nullptr, *ksb = nullptr, *kbb = nullptr, *sgb = nullptr, *fio = nullptr;
     // areas and boxes re-evaluated per step (tangent area kernel, zero tangent)
-    double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr, *th0 = nullptr;
+    double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr, *th0 = nullptr, *l0 = nullptr;
     std::vector<void*> allocs;
 };
 
@@ -1401,7 +1404,6 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     if (!c || !out) return LBIB_E_INVALID;
     *out = nullptr;
     if (checkpoint_every < 1) return fail(c, LBIB_E_INVALID, "checkpoint interval must be at least 1");
-    if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the adjoint needs an FP64 context");
     for (size_t m = 0; m < c->h_mem_kind.size(); ++m) {
         if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED)
             return fail(c, LBIB_E_INVALID, "the adjoint does not support rigid-projected membranes");
@@ -1436,7 +1438,8 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     ok = ok && (a->Abar = (double*)get(nm * 8)) && (a->ksb = (double*)get(nm * 8)) && (a->kbb = (double*)get(nm * 8)) &&
          (a->sgb = (double*)get(8));
     ok = ok && (a->A = (double*)get(nm * 8)) && (a->Ad = (double*)get(nm * 8)) && (a->box = (double*)get(4 * nm * 8));
-    ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->th0 = (double*)get(nv * 8));
+    ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->th0 = (double*)get(nv * 8)) &&
+         (a->l0 = (double*)get(nv * 8));
     if (!ok) {
         lbib_adjoint_destroy(a);
         return fail(c, LBIB_E_OOM, "adjoint buffers (tape of the checkpoint interval)");
@@ -1445,7 +1448,7 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     if (e == cudaSuccess) e = cudaMemsetAsync(a->zero, 0, std::max(2 * nv, nm) * 8, c->stream);
     // without markers there is no spread force: the tape's field stays zero
     if (e == cudaSuccess && c->nv == 0) e = cudaMemsetAsync(a->tape_G, 0, K * N * sizeof(longlong2), c->stream);
-    if (e == cudaSuccess) e = launch_rest_angles(c->ma, a->th0, c->stream);
+    if (e == cudaSuccess) e = launch_rest_fp64(c->prec, c->ma, a->l0, a->th0, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         lbib_adjoint_destroy(a);
@@ -1540,17 +1543,26 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
             return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
         };
         const size_t nvr = (size_t)c->nv;
+        const bool f64 = c->prec == LBIB_F64;  // other precisions: FP64 copies on the tape
         for (int k = 0; k < len; ++k) {
-            CK(d2d(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8));
-            if (nvr) CK(d2d(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * nvr));
+            if (f64) CK(d2d(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8));
+            else CK(launch_widen_storage(c->prec, c->f[c->cur], a->tape_f + (size_t)k * 9 * N, 9 * N, c->inv_scale,
+                                         c->stream));
+            if (nvr && f64) CK(d2d(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * nvr));
+            if (nvr && !f64) CK(launch_pos_out(c->prec, c->ma.X, a->tape_X + (size_t)k * 2 * nv, c->nv, c->stream));
             if (c->nlig) CK(d2d(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig));
             const int src = c->cur;
             CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
             c->cur = 1 - c->cur;
             c->steps += 1;
-            if (nvr) {
+            if (nvr && f64) {
                 CK(d2d(a->tape_F + (size_t)k * 2 * nv, c->ma.F, 16 * nvr));
                 CK(d2d(a->tape_W + (size_t)k * 9 * nv, c->ma.W, 72 * nvr));
+            } else if (nvr) {
+                CK(launch_widen_compute(c->prec, c->ma.F, a->tape_F + (size_t)k * 2 * nv, 2 * nvr, c->stream));
+                CK(launch_widen_compute(c->prec, c->ma.W, a->tape_W + (size_t)k * 9 * nv, 9 * nvr, c->stream));
+            }
+            if (nvr) {
                 CK(d2d(a->tape_st + (size_t)k * 2 * nv, c->ma.stencil, 8 * nvr));
                 CK(d2d(a->tape_G + (size_t)k * N, c->G[src], N * sizeof(longlong2)));
             }
@@ -1569,7 +1581,7 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
             t.Wv = a->tape_W + (size_t)k * 9 * nv;
             t.st = a->tape_st + (size_t)k * 2 * nv;
             t.A = a->A; t.Ad = a->Ad; t.box = a->box;
-            t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0; t.th0 = a->th0;
+            t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0; t.th0 = a->th0; t.l0 = a->l0;
             g.gfix = a->tape_G + (size_t)k * N;
             t.omega = 1.0 / c->tau; t.gx = c->gx; t.gy = c->gy;
             t.step = s.step + k;

@@ -24,6 +24,7 @@ struct TangentArgs {
     const double* dkb;     // [nmem] tangent of k_b per membrane
     double dsigma;         // tangent of the bond stiffness
     const double* th0;     // [nv] rest turning angle at each vertex (Eq. bendFor's theta_0)
+    const double* l0;      // [nv] rest length of element (v, v+1) (Eq. strainFor's l_0)
     double omega, gx, gy;
     long long step;        // n (forward Euler at n = 0)
 };
@@ -34,7 +35,8 @@ cudaError_t launch_tangent_step(const TangentArgs& t, cudaStream_t s);
 cudaError_t launch_tangent_markers(const TangentArgs& t, cudaStream_t s);
 // enclosed areas (value and tangent) and bounding boxes of X^n alone
 cudaError_t launch_tangent_areas(const TangentArgs& t, cudaStream_t s);
-// rest turning angles theta_0 = atan2(cross, dot) of the rest records into th0[nv]
-cudaError_t launch_rest_angles(const MarkerArgs& m, double* th0, cudaStream_t s);
+// rest lengths l0[nv] and turning angles th0[nv] = atan2(cross, dot) of the
+// context's rest records, in FP64 whatever the context's precision
+cudaError_t launch_rest_fp64(lbib_precision prec, const MarkerArgs& m, double* l0, double* th0, cudaStream_t s);
 
 }  // namespace lbib

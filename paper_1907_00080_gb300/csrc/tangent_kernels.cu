@@ -157,17 +157,22 @@ __global__ void k_t_advance(const TangentArgs t) {
     }
 }
 
-__global__ void k_rest_angles(const MarkerArgs m, double* th0) {
+template <typename C>
+__global__ void k_rest_fp64(const MarkerArgs m, double* l0, double* th0) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.nv) return;
-    const Rest<double>* rest = static_cast<const Rest<double>*>(m.rest);
-    th0[v] = ::atan2(rest[v].cross, rest[v].dot);
+    const Rest<C>* rest = static_cast<const Rest<C>*>(m.rest);
+    l0[v] = (double)rest[v].l0;
+    th0[v] = ::atan2(etod(rest[v].cross), etod(rest[v].dot));
 }
 
 }  // namespace
 
-cudaError_t launch_rest_angles(const MarkerArgs& m, double* th0, cudaStream_t s) {
-    if (m.nv > 0) k_rest_angles<<<(m.nv + 127) / 128, 128, 0, s>>>(m, th0);
+cudaError_t launch_rest_fp64(lbib_precision prec, const MarkerArgs& m, double* l0, double* th0, cudaStream_t s) {
+    if (m.nv == 0) return cudaSuccess;
+    const int g = (m.nv + 127) / 128;
+    if (prec == LBIB_F64) k_rest_fp64<double><<<g, 128, 0, s>>>(m, l0, th0);
+    else k_rest_fp64<float><<<g, 128, 0, s>>>(m, l0, th0);
     return cudaGetLastError();
 }
 

@@ -157,7 +157,6 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
                                                unsigned terms = kTermAll) {
     const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
     const int L = t_ring(off, n, k - 1), R = t_ring(off, n, k + 1);
-    const Rest<double>* rest = static_cast<const Rest<double>*>(t.m.rest);
     fx = dual(0.0);
     fy = dual(0.0);
     dual xL, yL, xv, yv, xR, yR;
@@ -197,12 +196,12 @@ __device__ __forceinline__ void t_vertex_force(const TangentArgs& t, int v, int 
         const dual ks = t_ks(t, m, s);
         const dual rx = xv - xR, ry = yv - yR;
         const dual l = sqrt(rx * rx + ry * ry);
-        const dual c = -ks * (l - dual(rest[v].l0)) / l;
+        const dual c = -ks * (l - dual(t.l0[v])) / l;
         fx += c * rx;
         fy += c * ry;
         const dual qx = xL - xv, qy = yL - yv;
         const dual l2 = sqrt(qx * qx + qy * qy);
-        const dual c2 = -ks * (l2 - dual(rest[L].l0)) / l2;
+        const dual c2 = -ks * (l2 - dual(t.l0[L])) / l2;
         fx -= c2 * qx;
         fy -= c2 * qy;
     }

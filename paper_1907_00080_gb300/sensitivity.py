@@ -25,9 +25,10 @@ from paper_1907_00080_gb300 import inputs, lbib
 PARAMS = ("k_s", "k_b", "sigma", "y_release")
 
 
-def make_workload(p, steps, seed=0, bonds="default"):
+def make_workload(p, steps, seed=0, bonds="default", precision="f64"):
     ks, kb, sigma, y0 = (float(v) for v in p)
-    wl = inputs.adjoint_capillary_320x160(ks=ks, kb=kb, sigma_lu=sigma, release_y=y0, seed=seed, bonds=bonds)
+    wl = inputs.adjoint_capillary_320x160(ks=ks, kb=kb, sigma_lu=sigma, release_y=y0, seed=seed, bonds=bonds,
+                                          precision=precision)
     wl.steps = steps
     return wl
 
@@ -135,12 +136,14 @@ def observable_gradient(wl, xy, bonds, w):
 
 
 class Recording:
-    """One FP64 run of the sensitivity case, recorded for backward sweeps
-    (checkpoints every `checkpoint_every` steps)."""
+    """One run of the sensitivity case, recorded for backward sweeps
+    (checkpoints every `checkpoint_every` steps).  precision: the forward
+    run's ("f64", or "f32" / "f16" / "bf16" storage with FP32 arithmetic); the
+    adjoint and the gradients are FP64 in every case."""
 
-    def __init__(self, p, steps, checkpoint_every=250, seed=0, bonds="default"):
-        self.wl = make_workload(p, steps, seed, bonds)
-        self.sim = lbib.Simulation(self.wl, precision="f64")
+    def __init__(self, p, steps, checkpoint_every=250, seed=0, bonds="default", precision="f64"):
+        self.wl = make_workload(p, steps, seed, bonds, precision)
+        self.sim = lbib.Simulation(self.wl, precision=precision)
         self.adj = None
         self.adj = lbib.lbib_adjoint_create(self.sim.ctx, checkpoint_every)
         lbib.lbib_adjoint_record(self.sim.ctx, self.adj, steps)
@@ -175,9 +178,9 @@ class Recording:
             pass
 
 
-def adjoint_jacobian(p, steps, checkpoint_every=250, seed=0, bonds="default"):
+def adjoint_jacobian(p, steps, checkpoint_every=250, seed=0, bonds="default", precision="f64"):
     """J (2,) and dJ/dp (2, 4) by one recorded run and two backward sweeps."""
-    rec = Recording(p, steps, checkpoint_every, seed, bonds)
+    rec = Recording(p, steps, checkpoint_every, seed, bonds, precision)
     try:
         jac = np.stack([rec.gradient((1.0, 0.0)), rec.gradient((0.0, 1.0))])
         return rec.J, jac, rec.bonds
@@ -196,11 +199,11 @@ def _torch_function():
         contracts the incoming gradient with it."""
 
         @staticmethod
-        def forward(ctx, p, steps, seed=0, mode="adjoint", checkpoint_every=250):
+        def forward(ctx, p, steps, seed=0, mode="adjoint", checkpoint_every=250, precision="f64"):
             pv = p.detach().cpu().numpy().astype(np.float64)
             ctx.rec = None
             if mode == "adjoint":
-                ctx.rec = Recording(pv, int(steps), int(checkpoint_every), int(seed))
+                ctx.rec = Recording(pv, int(steps), int(checkpoint_every), int(seed), precision=precision)
                 J = ctx.rec.J
             elif mode == "tangent":
                 J, jac, _ = jacobian(pv, int(steps), int(seed))
@@ -221,14 +224,16 @@ def _torch_function():
             else:
                 (jac,) = ctx.saved_tensors
                 g = w @ jac
-            return g.to(grad_out.device), None, None, None, None
+            return g.to(grad_out.device), None, None, None, None, None
 
     return CarrierObservables
 
 
-def carrier_observables(p, steps, seed=0, mode="adjoint", checkpoint_every=250):
-    """torch entry point: J = carrier_observables(p, steps); J.backward(...)"""
-    return _torch_function().apply(p, steps, seed, mode, checkpoint_every)
+def carrier_observables(p, steps, seed=0, mode="adjoint", checkpoint_every=250, precision="f64"):
+    """torch entry point: J = carrier_observables(p, steps); J.backward(...).
+    precision selects the forward run of the adjoint mode (the tangent mode is
+    FP64)."""
+    return _torch_function().apply(p, steps, seed, mode, checkpoint_every, precision)
 
 
 def default_params(seed=0):
