@@ -70,8 +70,12 @@ typedef enum {
 
 typedef enum {
     LBIB_INIT_REST = 0,        /* f_i = w_i (rho = 1, u = 0)                        */
-    LBIB_INIT_POISEUILLE = 1   /* tau = 1 discrete Poiseuille fixed point of the
+    LBIB_INIT_POISEUILLE = 1,  /* tau = 1 discrete Poiseuille fixed point of the
                                   body force along x (needs bounce-back walls)   */
+    LBIB_INIT_COUETTE = 2      /* planar Couette flow between the walls moving at
+                                  the velocities of lbib_set_wall_velocity (rest
+                                  until they are set); the discrete fixed point
+                                  at tau = 1 (needs bounce-back walls)            */
 } lbib_init;
 
 typedef enum {
@@ -126,6 +130,20 @@ lbib_status lbib_add_membrane(lbib_ctx* ctx, const double* xy, int32_t n, double
  * cleared.  Must precede the first lbib_step.  Errors: LBIB_E_INVALID, LBIB_E_STATE. */
 lbib_status lbib_set_receptors(lbib_ctx* ctx, const double* xy, int32_t n,
                                const lbib_bond_params* params);
+
+/* Walls moving along x (the planar Couette flow of the cell-free-layer
+ * adhesion study, Sec. 4): u_bottom, u_top are the x velocities of the walls
+ * at y = -1/2 and y = NY - 1/2 (default 0).  A population bounced back at a
+ * moving wall gains 2 w_i rho_w (e_i . u_w) / c_s^2 with rho_w = 1 (the
+ * moving-wall bounce-back of Ladd 1994); with tau = 1 the linear profile
+ * u(y) = u_bottom + (u_top - u_bottom)(y + 1/2)/NY is the discrete steady state.
+ * Must precede the first lbib_step; it re-initialises the populations to the
+ * context's initial state (with LBIB_INIT_COUETTE, the Couette flow of these
+ * velocities) and, for FP16 storage, chooses the storage scale again.  The
+ * tangent and the adjoint need resting walls.
+ * Errors: LBIB_E_INVALID (no bounce-back walls, non-finite), LBIB_E_STATE
+ * (after the first step). */
+lbib_status lbib_set_wall_velocity(lbib_ctx* ctx, double u_bottom, double u_top);
 
 /* Cut-off distance of the inter-membrane repulsion, Eq. repFor (default 2). */
 lbib_status lbib_set_repulsion(lbib_ctx* ctx, double d_rep);

@@ -54,6 +54,8 @@ _SIGS = {
     "orc_get_fields": (None, [_P, _DP, _DP, _DP]),
     "orc_get_force_field": (None, [_P, _DP, _DP]),
     "orc_init_poiseuille": (None, [_P]),
+    "orc_set_wall_velocity": (None, [_P, _D, _D]),
+    "orc_init_couette": (None, [_P]),
     "orc_add_membrane": (_I, [_P, _DP, _I, _D, _D, _D, _I, _IP, _I]),
     "orc_set_receptors": (None, [_P, _DP, _I, _D, _D, _D, _D, _D, _D, _D, _D, _U64, _U64]),
     "orc_set_repulsion": (None, [_P, _D]),
@@ -177,15 +179,18 @@ def ring_forces(xy, l0, th0, A0, ks, kb, ka, p_ref=1.0 / 3.0, which=7):
 class OracleSim:
     """One oracle simulation (FP64, CPU).  walls=1: bounce-back walls in y."""
 
-    def __init__(self, nx, ny, tau=1.0, body_force=(0.0, 0.0), walls=1, init="rest"):
+    def __init__(self, nx, ny, tau=1.0, body_force=(0.0, 0.0), walls=1, init="rest", wall_velocity=(0.0, 0.0)):
         self.nx, self.ny = int(nx), int(ny)
         self.walls = int(walls)
         self._s = lib().orc_create(self.nx, self.ny, float(tau), float(body_force[0]),
                                    float(body_force[1]), self.walls)
         self.nmem = 0
         self.mem_sizes = []
+        lib().orc_set_wall_velocity(self._s, float(wall_velocity[0]), float(wall_velocity[1]))
         if init == "poiseuille":
             lib().orc_init_poiseuille(self._s)
+        elif init == "couette":
+            lib().orc_init_couette(self._s)
         elif init != "rest":
             raise ValueError(init)
 

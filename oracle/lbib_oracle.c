@@ -121,6 +121,7 @@ typedef struct {
     uint64_t seed, instance;
 
     double d_rep, p_ref;
+    double uw_bot, uw_top;     /* x velocities of the walls y = -1/2 and y = NY - 1/2 */
     long step;
 } orc_sim;
 
@@ -202,7 +203,10 @@ static void moments_at(const double *f, long N, long node, double gx, double gy,
 
 /* streaming of a post-collision field fstar into fout (Eq. BGK left-hand side):
  * f_i(x, t+1) = f*_i(x - e_i); periodic in x; in y periodic (walls = 0) or
- * half-way bounce-back f_i(x, t+1) = f*_opp(i)(x) when x - e_i is a wall. */
+ * half-way bounce-back f_i(x, t+1) = f*_opp(i)(x) when x - e_i is a wall.  A
+ * wall moving along x with velocity u_w (the Couette set-up of Sec. 4) adds the
+ * momentum it imparts, 2 w_i rho_w (e_i . u_w) / c_s^2 with rho_w = 1 (the
+ * bounce-back rule for moving walls of Ladd, J. Fluid Mech. 271, 1994). */
 void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
     long nx = s->nx, ny = s->ny, N = nx * ny;
     for (int i = 0; i < 9; ++i) {
@@ -213,7 +217,8 @@ void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
                 long sx = imod(x - EX[i], nx);
                 double v;
                 if (s->walls && (sy < 0 || sy >= ny)) {
-                    v = fstar[o * N + y * nx + x];
+                    double uw = sy < 0 ? s->uw_bot : s->uw_top;
+                    v = fstar[o * N + y * nx + x] + 6.0 * W9[i] * (EX[i] * uw);
                 } else {
                     sy = imod(sy, ny);
                     v = fstar[i * N + sy * nx + sx];
@@ -523,6 +528,30 @@ void orc_init_poiseuille(orc_sim *s) {
         orc_guo_source(s->tau, u, 0.0, s->gx, s->gy, F);
         for (long x = 0; x < nx; ++x)
             for (int i = 0; i < 9; ++i) s->ftmp[i * N + y * nx + x] = feq[i] + F[i];
+    }
+    orc_stream(s, s->ftmp, s->f);
+}
+
+/* x velocities of the two walls (Couette set-up, Sec. 4: planar Couette flow
+ * in the cell-free layer) */
+void orc_set_wall_velocity(orc_sim *s, double u_bottom, double u_top) {
+    s->uw_bot = u_bottom;
+    s->uw_top = u_top;
+}
+
+/* tau = 1 planar Couette state between the walls: post-collision f* =
+ * feq(1, u(y)) with u(y) = u_bot + (u_top - u_bot) (y + 1/2) / NY, streamed.
+ * With tau = 1 this is the discrete steady state: the pulled populations have
+ * density 1 and velocity u(y) (the quadratic terms of feq cancel for a linear
+ * profile), and the moving-wall bounce-back reproduces the half-way walls. */
+void orc_init_couette(orc_sim *s) {
+    long nx = s->nx, ny = s->ny, N = nx * ny;
+    double feq[9];
+    for (long y = 0; y < ny; ++y) {
+        double u = s->uw_bot + (s->uw_top - s->uw_bot) * ((double)y + 0.5) / (double)ny;
+        orc_equilibrium(1.0, u, 0.0, feq);
+        for (long x = 0; x < nx; ++x)
+            for (int i = 0; i < 9; ++i) s->ftmp[i * N + y * nx + x] = feq[i];
     }
     orc_stream(s, s->ftmp, s->f);
 }

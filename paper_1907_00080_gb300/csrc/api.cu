@@ -103,6 +103,42 @@ void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
 }  // namespace
 
 // ------------------------------------------------------------------ create
+// FP16 storage: scale the deviations so that the expected peak (a few times
+// the Poiseuille peak deviation w_1 * 3 u_max, or the largest wall velocity's)
+// sits near 2^12
+void choose_scale(lbib_ctx* c) {
+    if (c->prec != LBIB_F32_STORE_F16) return;
+    const double nu = (c->tau - 0.5) / 3.0;
+    const double umax = std::max(1e-12, std::fabs(c->gx) * (double)c->ny * c->ny / (8.0 * nu) +
+                                             std::fabs(c->gy) * (double)c->nx * c->nx / (8.0 * nu) +
+                                             std::max(std::fabs(c->uw_bot), std::fabs(c->uw_top)));
+    const double dmax = std::max(umax / 3.0, 1e-9);
+    int k = (int)std::floor(std::log2(4096.0 / dmax));
+    k = std::max(0, std::min(k, 40));
+    c->scale_exp = k;
+    c->inv_scale = std::ldexp(1.0f, -k);
+}
+
+double bb_term(double u_wall);
+
+// the initial state in f[0]: rest (pre-collision f_i = w_i), or the
+// post-collision state of the Poiseuille or Couette fixed point
+cudaError_t init_populations(lbib_ctx* c) {
+    const size_t N = (size_t)c->nx * c->ny;
+    cudaError_t e = cudaMemsetAsync(c->f[0], 0, 9 * N * c->pop_elem, c->stream);
+    if (e == cudaSuccess && c->init == LBIB_INIT_REST && (c->uw_bot != 0.0 || c->uw_top != 0.0))
+        e = launch_init_rest_walls(c->prec, c->f[0], c->nx, c->ny, bb_term(c->uw_bot), bb_term(c->uw_top),
+                                   c->inv_scale, c->stream);
+    if (e == cudaSuccess && c->init == LBIB_INIT_POISEUILLE)
+        e = launch_init_poiseuille(c->prec, c->f[0], c->nx, c->ny, c->tau, c->gx, c->inv_scale, c->stream);
+    if (e == cudaSuccess && c->init == LBIB_INIT_COUETTE)
+        e = launch_init_couette(c->prec, c->f[0], c->nx, c->ny, c->uw_bot, c->uw_top, c->inv_scale, c->stream);
+    return e;
+}
+
+// momentum a moving wall gives a bounced-back diagonal population: 6 w_d u_w
+double bb_term(double u_wall) { return 6.0 * (1.0 / 36.0) * u_wall; }
+
 extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const double body_force[2],
                                    lbib_walls walls, void* cuda_stream, lbib_ctx** out) {
     if (!lat || !out) return LBIB_E_INVALID;
@@ -113,6 +149,8 @@ extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const do
     if (walls != LBIB_WALLS_NONE && walls != LBIB_WALLS_Y_BOUNCEBACK) return LBIB_E_INVALID;
     if (lat->init == LBIB_INIT_POISEUILLE && (walls != LBIB_WALLS_Y_BOUNCEBACK || tau != 1.0))
         return LBIB_E_INVALID;
+    if (lat->init == LBIB_INIT_COUETTE && walls != LBIB_WALLS_Y_BOUNCEBACK) return LBIB_E_INVALID;
+    if (lat->init < LBIB_INIT_REST || lat->init > LBIB_INIT_COUETTE) return LBIB_E_INVALID;
     if (lat->prec != LBIB_F64 && lat->prec != LBIB_F32 && (lat->nx % 2)) return LBIB_E_INVALID;
     lbib_ctx* c = new lbib_ctx();
     c->nx = lat->nx;
@@ -138,18 +176,7 @@ extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const do
         }
         c->own_stream = true;
     }
-    if (c->prec == LBIB_F32_STORE_F16) {
-        // scale the deviations so that the expected peak (a few times the
-        // Poiseuille peak deviation w_1 * 3 u_max) sits near 2^12 in FP16
-        const double nu = (tau - 0.5) / 3.0;
-        const double umax = std::max(1e-12, std::fabs(c->gx) * (double)c->ny * c->ny / (8.0 * nu) +
-                                                 std::fabs(c->gy) * (double)c->nx * c->nx / (8.0 * nu));
-        const double dmax = std::max(umax / 3.0, 1e-9);
-        int k = (int)std::floor(std::log2(4096.0 / dmax));
-        k = std::max(0, std::min(k, 40));
-        c->scale_exp = k;
-        c->inv_scale = std::ldexp(1.0f, -k);
-    }
+    choose_scale(c);
     const size_t N = (size_t)c->nx * c->ny;
     cudaError_t e;
     for (int b = 0; b < 2; ++b) {
@@ -174,10 +201,7 @@ extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const do
     if (e == cudaSuccess) e = cudaMemsetAsync(c->uy, 0, N * c->cmp_elem, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_step, 0, sizeof(long long), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
-    // rest: all deviations zero; Poiseuille: the fixed point's post-collision state
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, 9 * N * c->pop_elem, c->stream);
-    if (e == cudaSuccess && c->init == LBIB_INIT_POISEUILLE)
-        e = launch_init_poiseuille(c->prec, c->f[0], c->nx, c->ny, tau, c->gx, c->inv_scale, c->stream);
+    if (e == cudaSuccess) e = init_populations(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         lbib_destroy(c);
@@ -248,6 +272,21 @@ extern "C" lbib_status lbib_set_receptors(lbib_ctx* c, const double* xy, int32_t
 extern "C" lbib_status lbib_set_repulsion(lbib_ctx* c, double d_rep) {
     if (!c || !(d_rep >= 0.0)) return LBIB_E_INVALID;
     c->d_rep = d_rep;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_set_wall_velocity(lbib_ctx* c, double u_bottom, double u_top) {
+    if (!c) return LBIB_E_INVALID;
+    if (c->walls != LBIB_WALLS_Y_BOUNCEBACK) return fail(c, LBIB_E_INVALID, "moving walls need bounce-back walls");
+    if (!std::isfinite(u_bottom) || !std::isfinite(u_top)) return fail(c, LBIB_E_INVALID, "non-finite wall velocity");
+    if (c->graphs_ready || c->steps > 0) return fail(c, LBIB_E_STATE, "wall velocities are fixed at the first step");
+    c->uw_bot = u_bottom;
+    c->uw_top = u_top;
+    choose_scale(c);
+    c->cur = 0;
+    CK(init_populations(c));
+    CK(cudaStreamSynchronize(c->stream));
+    c->fields_valid = false;
     return LBIB_OK;
 }
 
@@ -603,6 +642,8 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.gx = c->gx;
     l.gy = c->gy;
     l.inv_scale = c->inv_scale;
+    l.bb_bot = bb_term(c->uw_bot);
+    l.bb_top = bb_term(c->uw_top);
     l.fields_only = 0;
     l.tile_w = c->tile_w;
     l.tile_h = c->tile_h;
@@ -773,7 +814,7 @@ extern "C" lbib_status lbib_read_populations(lbib_ctx* c, double* f, int on_devi
         out = c->stage;
     }
     CK(launch_stream_out(c->prec, c->f[c->cur], out, c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
-                         c->inv_scale, c->stream));
+                         c->inv_scale, bb_term(c->uw_bot), bb_term(c->uw_top), c->stream));
     if (!on_device) CK(cudaMemcpyAsync(f, out, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBIB_OK;
@@ -790,7 +831,7 @@ extern "C" lbib_status lbib_write_populations(lbib_ctx* c, const double* f, int 
         in = c->stage;
     }
     CK(launch_stream_in(c->prec, in, c->f[c->cur], c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
-                        c->inv_scale, c->stream));
+                        c->inv_scale, bb_term(c->uw_bot), bb_term(c->uw_top), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->fields_valid = false;
     return LBIB_OK;
@@ -1169,6 +1210,7 @@ extern "C" void lbib_tangent_destroy(lbib_tangent* t) {
 extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     if (!c || !out) return LBIB_E_INVALID;
     if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the tangent needs an FP64 context");
+    if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the tangent needs resting walls");
     for (int k : c->h_mem_kind)
         if (k == LBIB_MEMBRANE_RIGID_PROJECTED)
             return fail(c, LBIB_E_INVALID, "the tangent does not support rigid-projected membranes");
@@ -1404,6 +1446,7 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     if (!c || !out) return LBIB_E_INVALID;
     *out = nullptr;
     if (checkpoint_every < 1) return fail(c, LBIB_E_INVALID, "checkpoint interval must be at least 1");
+    if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the adjoint needs resting walls");
     for (size_t m = 0; m < c->h_mem_kind.size(); ++m) {
         if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED)
             return fail(c, LBIB_E_INVALID, "the adjoint does not support rigid-projected membranes");

@@ -59,9 +59,15 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
             sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         }
         if (bb) {
-            // the population that left this node toward the wall comes back reversed
+            // the population that left this node toward the wall comes back
+            // reversed, plus the momentum of a moving wall (diagonals only)
             const S* row = src + (size_t)opp(i) * N + (size_t)y * nx;
             load_pack<S, VEC>(row, x0, ok, inv, f[i]);
+            if (cx(i) != 0) {
+                const C t = C(cx(i)) * C(sy < 0 ? a.bb_bot : a.bb_top);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) f[i][k] += t;
+            }
             continue;
         }
         const S* row = src + (size_t)i * N + (size_t)sy * nx;
@@ -217,7 +223,7 @@ cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, boo
 // pre-collision populations the next step starts from, as doubles.
 template <typename S>
 __global__ void k_stream_out(const S* __restrict__ src, double* __restrict__ out, int nx, int ny,
-                             int walls, float inv) {
+                             int walls, float inv, double bb_bot, double bb_top) {
     const size_t N = (size_t)nx * ny;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
@@ -228,7 +234,8 @@ __global__ void k_stream_out(const S* __restrict__ src, double* __restrict__ out
             sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
             double d;
             if (walls && (sy < 0 || sy >= ny)) {
-                d = (double)Storage<S>::load(src[(size_t)opp(i) * N + n], inv);
+                d = (double)Storage<S>::load(src[(size_t)opp(i) * N + n], inv) +
+                    (double)cx(i) * (sy < 0 ? bb_bot : bb_top);
             } else {
                 sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
                 d = (double)Storage<S>::load(src[(size_t)i * N + (size_t)sy * nx + sx], inv);
@@ -241,7 +248,7 @@ __global__ void k_stream_out(const S* __restrict__ src, double* __restrict__ out
 // inverse of k_stream_out: scatter f^n back to the post-collision slots it came from
 template <typename S>
 __global__ void k_stream_in(const double* __restrict__ in, S* __restrict__ dst, int nx, int ny,
-                            int walls, float inv) {
+                            int walls, float inv, double bb_bot, double bb_top) {
     const size_t N = (size_t)nx * ny;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
@@ -253,7 +260,9 @@ __global__ void k_stream_in(const double* __restrict__ in, S* __restrict__ dst, 
             int sy = y - cy(i), sx = x - cx(i);
             sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
             if (walls && (sy < 0 || sy >= ny)) {
-                dst[(size_t)opp(i) * N + n] = sv;
+                // a moving wall's momentum is not stored
+                const double dw = d - (double)cx(i) * (sy < 0 ? bb_bot : bb_top);
+                dst[(size_t)opp(i) * N + n] = Storage<S>::store((typename Storage<S>::C)dw, 1.0f / inv);
             } else {
                 sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
                 dst[(size_t)i * N + (size_t)sy * nx + sx] = sv;
@@ -279,6 +288,41 @@ __global__ void k_init_poiseuille(S* __restrict__ dst, int nx, int ny, double ta
             const double deq = wgt<double>(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u);
             const double src = pre * wgt<double>(i) * (3.0 * (cx(i) - u) + 9.0 * eu * cx(i)) * G;
             dst[(size_t)i * N + n] = Storage<S>::store((typename Storage<S>::C)(deq + src), 1.0f / inv);
+        }
+    }
+}
+
+// tau = 1 planar Couette state (Sec. 4, cell-free layer): post-collision
+// deviations feq(1, u(y)) - w with u(y) = u_bot + (u_top - u_bot)(y + 1/2)/NY
+template <typename S>
+__global__ void k_init_couette(S* __restrict__ dst, int nx, int ny, double u_bot, double u_top, float inv) {
+    const size_t N = (size_t)nx * ny;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const double y = (double)(n / nx);
+        const double u = u_bot + (u_top - u_bot) * (y + 0.5) / (double)ny;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double eu = cx(i) * u;
+            const double deq = wgt<double>(i) * (3.0 * eu + 4.5 * eu * eu - 1.5 * u * u);
+            dst[(size_t)i * N + n] = Storage<S>::store((typename Storage<S>::C)deq, 1.0f / inv);
+        }
+    }
+}
+
+// rest state f_i = w_i beside moving walls: the stored deviations are zero
+// except in the slots that the wall rows pull back from the walls, which hold
+// minus the wall's momentum term (so that the pulled populations are w_i)
+template <typename S>
+__global__ void k_init_rest_walls(S* __restrict__ dst, int nx, int ny, double bb_bot, double bb_top, float inv) {
+    const size_t N = (size_t)nx * ny;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 5; i < 9; ++i) {
+            const bool from_bottom = cy(i) > 0;  // 5, 6 leave the lower wall; 7, 8 the upper
+            const size_t node = from_bottom ? (size_t)x : (size_t)(ny - 1) * nx + x;
+            const double t = (double)cx(i) * (from_bottom ? bb_bot : bb_top);
+            dst[(size_t)opp(i) * N + node] = Storage<S>::store((typename Storage<S>::C)(-t), 1.0f / inv);
         }
     }
 }
@@ -331,18 +375,34 @@ static int grid_for(size_t n, int block) {
     }
 
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
-                              bool walls, float inv_scale, cudaStream_t s) {
+                              bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s) {
     const int g = grid_for((size_t)nx * ny, 256);
     LBIB_DISPATCH_S(prec, (k_stream_out<S><<<g, 256, 0, s>>>(static_cast<const S*>(src), out, nx,
-                                                              ny, walls ? 1 : 0, inv_scale)));
+                                                              ny, walls ? 1 : 0, inv_scale, bb_bot, bb_top)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
-                             bool walls, float inv_scale, cudaStream_t s) {
+                             bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s) {
     const int g = grid_for((size_t)nx * ny, 256);
     LBIB_DISPATCH_S(prec, (k_stream_in<S><<<g, 256, 0, s>>>(in, static_cast<S*>(dst), nx, ny,
-                                                             walls ? 1 : 0, inv_scale)));
+                                                             walls ? 1 : 0, inv_scale, bb_bot, bb_top)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_rest_walls(lbib_precision prec, void* dst, int nx, int ny, double bb_bot, double bb_top,
+                                   float inv_scale, cudaStream_t s) {
+    const int g = grid_for((size_t)nx, 256);
+    LBIB_DISPATCH_S(prec, (k_init_rest_walls<S><<<g, 256, 0, s>>>(static_cast<S*>(dst), nx, ny, bb_bot, bb_top,
+                                                                   inv_scale)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_couette(lbib_precision prec, void* dst, int nx, int ny, double u_bot, double u_top,
+                                float inv_scale, cudaStream_t s) {
+    const int g = grid_for((size_t)nx * ny, 256);
+    LBIB_DISPATCH_S(prec, (k_init_couette<S><<<g, 256, 0, s>>>(static_cast<S*>(dst), nx, ny, u_bot, u_top,
+                                                                inv_scale)));
     return cudaGetLastError();
 }
 

@@ -256,6 +256,12 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
                     if (bb || cx(i) == 0) {
 #pragma unroll
                         for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
+                        if (bb && cx(i) != 0) {
+                            // the momentum of a moving wall (diagonals only)
+                            const C t = C(cx(i)) * C(y - cy(i) < 0 ? a.bb_bot : a.bb_top);
+#pragma unroll
+                            for (int q = 0; q < NPT; ++q) f[i][q] += t;
+                        }
                     } else if (cx(i) == 1) {
                         f[i][0] = Storage<S>::load(rp[-1], inv);
 #pragma unroll
@@ -437,6 +443,12 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
                 if (bb || cx(i) == 0) {
 #pragma unroll
                     for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
+                    if (bb && cx(i) != 0) {
+                        // the momentum of a moving wall (diagonals only)
+                        const C t = C(cx(i)) * C(y - cy(i) < 0 ? a.bb_bot : a.bb_top);
+#pragma unroll
+                        for (int q = 0; q < NPT; ++q) f[i][q] += t;
+                    }
                 } else if (cx(i) == 1) {
                     f[i][0] = Storage<S>::load(rp[-1], inv);
 #pragma unroll

@@ -97,6 +97,8 @@ struct LbArgs {
     double omega;          // 1/tau
     double gx, gy;         // body force
     float inv_scale;       // 2^-k for 16-bit storage, 1 otherwise
+    double bb_bot, bb_top; // moving walls: 6 w_d u_w (w_d = 1/36) of the lower / upper wall; a
+                           // diagonal population bounced back there gains cx(i) times it
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
     int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags
     int* status;           // device status word (StatusBits)
@@ -204,9 +206,13 @@ cudaError_t prepare_lb_stream(lbib_precision prec, int npt, bool walls, bool has
 cudaError_t launch_lb_stream(lbib_precision prec, int npt, bool walls, bool has_ib, int grid,
                              const LbArgs& a, cudaStream_t s);
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
-                              bool walls, float inv_scale, cudaStream_t s);
+                              bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s);
 cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
-                             bool walls, float inv_scale, cudaStream_t s);
+                             bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s);
+cudaError_t launch_init_rest_walls(lbib_precision prec, void* dst, int nx, int ny, double bb_bot, double bb_top,
+                                   float inv_scale, cudaStream_t s);
+cudaError_t launch_init_couette(lbib_precision prec, void* dst, int nx, int ny, double u_bot, double u_top,
+                                float inv_scale, cudaStream_t s);
 cudaError_t launch_init_poiseuille(lbib_precision prec, void* dst, int nx, int ny, double tau,
                                    double gx, float inv_scale, cudaStream_t s);
 cudaError_t launch_mass(lbib_precision prec, const void* src, long long n_elems, double* partials,
@@ -237,6 +243,7 @@ struct lbib_ctx {
     size_t cmp_elem = 4;      // bytes per compute-type value
     int scale_exp = 0;        // 16-bit storage scale 2^k
     float inv_scale = 1.0f;
+    double uw_bot = 0.0, uw_top = 0.0;  // x velocities of the lower and upper walls
 
     void* f[2] = {nullptr, nullptr};
     int cur = 0;              // buffer holding d*^{n-1}

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "liblbib.so")
 LBIB_OK, LBIB_E_INVALID, LBIB_E_CUDA, LBIB_E_OOM, LBIB_E_TIMEOUT, LBIB_E_NONFINITE, LBIB_E_STATE = range(7)
 LBIB_F64, LBIB_F32, LBIB_F32_STORE_F16, LBIB_F32_STORE_BF16 = range(4)
 LBIB_WALLS_NONE, LBIB_WALLS_Y_BOUNCEBACK = 0, 1
-LBIB_INIT_REST, LBIB_INIT_POISEUILLE = 0, 1
+LBIB_INIT_REST, LBIB_INIT_POISEUILLE, LBIB_INIT_COUETTE = 0, 1, 2
 LBIB_MEMBRANE_KINEMATIC, LBIB_MEMBRANE_RIGID_PROJECTED = 0, 1
 
 PRECISIONS = {"f64": LBIB_F64, "f32": LBIB_F32, "f16": LBIB_F32_STORE_F16, "bf16": LBIB_F32_STORE_BF16}
@@ -58,6 +58,7 @@ _SIGS = {
     "lbib_add_membrane": (_I, [_P, _DP, _I32, _D, _D, _D, _I, _I32P, _I32, _I32P]),
     "lbib_set_receptors": (_I, [_P, _DP, _I32, ctypes.POINTER(lbib_bond_params)]),
     "lbib_set_repulsion": (_I, [_P, _D]),
+    "lbib_set_wall_velocity": (_I, [_P, _D, _D]),
     "lbib_step": (_I, [_P, _I64]),
     "lbib_sync": (_I, [_P]),
     "lbib_step_count": (_I64, [_P]),
@@ -172,6 +173,10 @@ def lbib_set_receptors(ctx, xy, d_cut=1.5, y_eq=0.75, sigma=0.0, kf_dt=1e-2, kr0
 
 def lbib_set_repulsion(ctx, d_rep):
     _check(ctx, load().lbib_set_repulsion(ctx, float(d_rep)))
+
+
+def lbib_set_wall_velocity(ctx, u_bottom, u_top):
+    _check(ctx, load().lbib_set_wall_velocity(ctx, float(u_bottom), float(u_top)))
 
 
 def lbib_step(ctx, n):
@@ -407,7 +412,7 @@ class Simulation:
 
     def __init__(self, wl, precision=None, tiling=None, cuda_stream=None):
         prec = PRECISIONS[precision or wl.precision]
-        init = LBIB_INIT_POISEUILLE if wl.init == "poiseuille" else LBIB_INIT_REST
+        init = {"poiseuille": LBIB_INIT_POISEUILLE, "couette": LBIB_INIT_COUETTE}.get(wl.init, LBIB_INIT_REST)
         self.wl = wl
         self.nx, self.ny = wl.nx, wl.ny
         self.ctx = lbib_create(wl.nx, wl.ny, prec, init, wl.tau, wl.body_force, wl.walls, cuda_stream)
@@ -424,6 +429,8 @@ class Simulation:
                                beta_f=b["beta_f"], beta_r=b["beta_r"], d_break=b["d_break"],
                                seed=wl.seed, instance=wl.instance)
         lbib_set_repulsion(self.ctx, wl.d_rep)
+        if any(u != 0.0 for u in wl.wall_velocity):
+            lbib_set_wall_velocity(self.ctx, *wl.wall_velocity)
         if tiling is not None:
             lbib_set_tiling(self.ctx, *tiling)
 

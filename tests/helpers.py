@@ -5,7 +5,8 @@ import oracle
 
 
 def make_oracle(wl):
-    s = oracle.OracleSim(wl.nx, wl.ny, wl.tau, wl.body_force, wl.walls, init=wl.init)
+    s = oracle.OracleSim(wl.nx, wl.ny, wl.tau, wl.body_force, wl.walls, init=wl.init,
+                         wall_velocity=wl.wall_velocity)
     for m in wl.membranes:
         s.add_membrane(m.xy, m.ks, m.kb, m.ka, m.kind, m.ligands)
     if wl.receptors is not None and len(wl.receptors):

@@ -226,3 +226,54 @@ def test_momentum_budget_periodic_box():
     # with a single external point force the budget must see it exactly
     gx, gy = s.force_field()
     np.testing.assert_allclose([gx.sum(), gy.sum()], budget, rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- moving walls
+def couette_profile(ny, u_bot, u_top):
+    """planar Couette flow between walls at y = -1/2 and y = NY - 1/2"""
+    y = np.arange(ny, dtype=np.float64)
+    return u_bot + (u_top - u_bot) * (y + 0.5) / ny
+
+
+def test_couette_state_is_the_tau1_fixed_point():
+    """tau = 1: the Couette initial state (post-collision feq of the linear
+    profile) is reproduced by every step (moving-wall bounce-back at both
+    walls), with rho = 1 and u = the closed-form profile."""
+    import oracle
+    nx, ny = 12, 8
+    s = oracle.OracleSim(nx, ny, tau=1.0, walls=1, init="couette", wall_velocity=(-0.004, 0.01))
+    f0 = s.populations()
+    s.step(200)
+    np.testing.assert_allclose(s.populations(), f0, rtol=0, atol=1e-15)
+    rho, ux, uy = s.fields()
+    np.testing.assert_allclose(rho, 1.0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(ux, np.broadcast_to(couette_profile(ny, -0.004, 0.01)[:, None], (ny, nx)),
+                               rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy, 0.0, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.3])
+def test_couette_from_rest_reaches_the_linear_profile(tau):
+    """From rest, the flow driven by the moving walls relaxes to the linear
+    profile with the walls exactly half-way (exact for a linear profile at any
+    tau with this bounce-back)."""
+    import oracle
+    nx, ny = 4, 6
+    s = oracle.OracleSim(nx, ny, tau=tau, walls=1, init="rest", wall_velocity=(-0.005, 0.01))
+    m0 = s.mass()
+    s.step(20000)
+    rho, ux, uy = s.fields()
+    np.testing.assert_allclose(ux, np.broadcast_to(couette_profile(ny, -0.005, 0.01)[:, None], (ny, nx)),
+                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(uy, 0.0, rtol=0, atol=1e-14)
+    assert abs(s.mass() - m0) <= 1e-12 * m0
+
+
+def test_walls_moving_together_carry_the_fluid_along():
+    """Both walls at the same velocity U: the fluid reaches the uniform flow U
+    (a Galilean check of the momentum term's sign and size)."""
+    import oracle
+    s = oracle.OracleSim(4, 5, tau=1.0, walls=1, init="rest", wall_velocity=(0.02, 0.02))
+    s.step(5000)
+    rho, ux, uy = s.fields()
+    np.testing.assert_allclose(ux, 0.02, rtol=0, atol=1e-12)
