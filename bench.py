@@ -298,7 +298,8 @@ def lbib_main(args):
     forms = None
     if not args.no_forms and rank == 0:
         forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream),
-                 "differentiation": differentiation_form(lbib, torch)}
+                 "differentiation": differentiation_form(lbib, torch),
+                 "couette_cell_free_layer": couette_form(lbib, torch, stream)}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -447,6 +448,36 @@ def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
         res[prec]["speedup_vs_f32"] = res[prec]["mlups"] / base
     return {"workload": "fine capillary 2000x667 (dx = 15 nm), 4 RBC x 1700 + 3 rigid carriers x 210 markers",
             "checkpoints": list(checkpoints), "timed_steps": timed, "results": res}
+
+
+def couette_form(lbib, torch, stream, warm=2000, timed=4000):
+    """The adhesion set-up of the cell-free layer (600 x 200 planar Couette
+    flow, Re = 0.003, upper wall moving, receptors on the lower wall, one 1 um
+    carrier released 1 lu above it), FP32 storage, rigid and soft carriers,
+    sigma in {0.5, 1, 2}: throughput over `timed` steps after `warm` (CUDA
+    events on the stream), bonds and carrier height at the end."""
+    from paper_1907_00080_gb300 import inputs
+    res = {}
+    for carrier in ("rigid", "soft"):
+        for sigma in (0.5, 1.0, 2.0):
+            wl = inputs.couette_cfl_600x200("f32", sigma=sigma, carrier=carrier)
+            sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                sim.step(warm)
+                sim.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(timed)
+                e1.record(stream)
+                sim.sync()
+                ms = e0.elapsed_time(e1)
+            x = sim.markers()
+            res["%s_sigma%g" % (carrier, sigma)] = {
+                "mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "bonds": int((sim.bonds() >= 0).sum()),
+                "carrier_min_height_lu": float(x[:, 1].min() + 0.5), "tiling": list(sim.tiling)}
+            sim.close()
+    return {"workload": "Couette 600x200 (dx = 15 nm, H_CFL = 3 um), Re = 0.003, one 1 um carrier x 210 markers, "
+                        "FP32", "steps": warm + timed, "results": res}
 
 
 def ensemble_form(lbib, torch, stream, n=64, steps=400):
