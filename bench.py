@@ -455,7 +455,9 @@ def couette_form(lbib, torch, stream, warm=2000, timed=4000):
     flow, Re = 0.003, upper wall moving, receptors on the lower wall, one 1 um
     carrier released 1 lu above it), FP32 storage, rigid and soft carriers,
     sigma in {0.5, 1, 2}: throughput over `timed` steps after `warm` (CUDA
-    events on the stream), bonds and carrier height at the end."""
+    events on the stream); at the end, from lbib_membrane_observables, the
+    bonds n_L (and their ratio to the count after the warm-up), the rolling
+    velocity over the wall speed, the lowest marker height and the region."""
     from paper_1907_00080_gb300 import inputs
     res = {}
     for carrier in ("rigid", "soft"):
@@ -465,16 +467,19 @@ def couette_form(lbib, torch, stream, warm=2000, timed=4000):
             with torch.cuda.stream(stream):
                 sim.step(warm)
                 sim.sync()
+                o0 = sim.observables()[0]
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 sim.step(timed)
                 e1.record(stream)
                 sim.sync()
                 ms = e0.elapsed_time(e1)
-            x = sim.markers()
+            o = sim.observables()[0]
             res["%s_sigma%g" % (carrier, sigma)] = {
-                "mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "bonds": int((sim.bonds() >= 0).sum()),
-                "carrier_min_height_lu": float(x[:, 1].min() + 0.5), "tiling": list(sim.tiling)}
+                "mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "bonds": int(o[5]),
+                "n_L_over_n_L_after_warm": float(o[5] / o0[5]) if o0[5] > 0 else None,
+                "u_roll_over_u_wall": float(o[2] / wl.wall_velocity[1]),
+                "carrier_min_height_lu": float(o[6]), "region": int(o[4]), "tiling": list(sim.tiling)}
             sim.close()
     return {"workload": "Couette 600x200 (dx = 15 nm, H_CFL = 3 um), Re = 0.003, one 1 um carrier x 210 markers, "
                         "FP32", "steps": warm + timed, "results": res}

@@ -308,6 +308,21 @@ lbib_status lbib_adjoint_read(lbib_adjoint* adj, double* xy_bar, double* xy_prev
 int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* adj);
 void lbib_adjoint_destroy(lbib_adjoint* adj);
 
+/* Observables of the margination and adhesion studies (Sec. 4) for every
+ * membrane, reduced on the device in FP64 over the current markers.  out
+ * receives 8 doubles per membrane (host memory, nmem * 8):
+ *   [0], [1]  centroid (x, y) of the vertices (x unwrapped)
+ *   [2], [3]  centroid velocity, mean of X^n - X^{n-1} (lattice units per
+ *             step): [2] is the rolling / translation velocity u_roll of an
+ *             adhering carrier, [3] the lateral velocity
+ *   [4]       region of the centroid height h = (y + 1/2)/NY above the lower
+ *             wall: 0 bulk (0.3 <= h <= 0.7), 1 intermediate (0.2 <= h < 0.3
+ *             or 0.7 < h <= 0.8), 2 cell-free layer (h < 0.2 or h > 0.8)
+ *   [5]       bonds held by the membrane's ligands (n_L)
+ *   [6], [7]  lowest and highest vertex height above the lower wall (y + 1/2)
+ * Synchronises.  Allocates a small device buffer on the first call. */
+lbib_status lbib_membrane_observables(lbib_ctx* ctx, double* out);
+
 /* Allocation-free FP64 mass of a population buffer the caller owns.  The
  * paper has no counterpart: this is a library service for callers that must not
  * allocate device memory at the time of the call, e.g. a monitor running between

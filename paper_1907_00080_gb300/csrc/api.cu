@@ -939,6 +939,18 @@ extern "C" lbib_status lbib_diagnostics(lbib_ctx* c, double* mass, double* areas
     return LBIB_OK;
 }
 
+extern "C" lbib_status lbib_membrane_observables(lbib_ctx* c, double* out) {
+    if (!c || !out) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (c->nmem == 0) return LBIB_OK;
+    if (!c->d_obs) CK(cudaMalloc(&c->d_obs, 8 * sizeof(double) * (size_t)c->nmem));
+    CK(launch_observables(c->prec, c->ma, c->d_obs, c->stream));
+    CK(cudaMemcpyAsync(out, c->d_obs, 8 * sizeof(double) * (size_t)c->nmem, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
 extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_per_launch) {
     if (!c || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
     if (!c->finalized || c->steps == 0) return fail(c, LBIB_E_STATE, "profile after at least one step");
@@ -1027,6 +1039,7 @@ extern "C" void lbib_destroy(lbib_ctx* c) {
     if (c->d_step) cudaFree(c->d_step);
     if (c->d_status) cudaFree(c->d_status);
     if (c->dmem) cudaFree(c->dmem);
+    if (c->d_obs) cudaFree(c->d_obs);
     for (int p = 0; p < 2; ++p)
         if (c->G[p]) cudaFree(c->G[p]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -224,6 +224,8 @@ cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, c
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s);
+// observables.cu: 8 doubles per membrane (see lbib_membrane_observables)
+cudaError_t launch_observables(lbib_precision prec, const MarkerArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);
 cudaError_t launch_pos_out(lbib_precision prec, const void* X, double* xy, int nv, cudaStream_t s);
 
@@ -280,6 +282,7 @@ struct lbib_ctx {
     int* flags[2] = {nullptr, nullptr};      // spread-touched tiles (by parity)
     double* d_areas = nullptr;
     double* xy_stage = nullptr;             // 2*nv doubles for marker read/write
+    double* d_obs = nullptr;                // 8*nmem doubles of membrane observables (lazy)
     unsigned int* tickets = nullptr;
 
     long long* d_step = nullptr;

@@ -59,6 +59,7 @@ _SIGS = {
     "lbib_set_receptors": (_I, [_P, _DP, _I32, ctypes.POINTER(lbib_bond_params)]),
     "lbib_set_repulsion": (_I, [_P, _D]),
     "lbib_set_wall_velocity": (_I, [_P, _D, _D]),
+    "lbib_membrane_observables": (_I, [_P, _DP]),
     "lbib_step": (_I, [_P, _I64]),
     "lbib_sync": (_I, [_P]),
     "lbib_step_count": (_I64, [_P]),
@@ -177,6 +178,16 @@ def lbib_set_repulsion(ctx, d_rep):
 
 def lbib_set_wall_velocity(ctx, u_bottom, u_top):
     _check(ctx, load().lbib_set_wall_velocity(ctx, float(u_bottom), float(u_top)))
+
+
+OBSERVABLES = ("x_c", "y_c", "u_c", "v_c", "region", "bonds", "y_min", "y_max")
+
+
+def lbib_membrane_observables(ctx, nmem):
+    """(nmem, 8) array; columns as in OBSERVABLES"""
+    out = np.zeros((max(nmem, 1), 8))
+    _check(ctx, load().lbib_membrane_observables(ctx, _dptr(out)))
+    return out[:nmem]
 
 
 def lbib_step(ctx, n):
@@ -492,6 +503,10 @@ class Simulation:
 
     def diagnostics(self):
         return lbib_diagnostics(self.ctx, len(self.mem_sizes))
+
+    def observables(self):
+        """per-membrane observables (lbib_membrane_observables), (nmem, 8)"""
+        return lbib_membrane_observables(self.ctx, len(self.mem_sizes))
 
     @property
     def tiling(self):
