@@ -20,12 +20,12 @@ struct AdjointArgs {
     const longlong2* gfix;  // [N] spread force of step n, fixed point (scaled by 2^52)
     const double* fbar;   // [9][N] adjoint of d*^n (the deviations step n stores)
     double* fbar_out;     // [9][N] adjoint of d*^{n-1}; every entry is written
-    double* XB;           // [nv][2] in: adjoint of X^{n+1}; out: adjoint of X^n
+    const double* XB;     // [nv][2] adjoint of X^{n+1}
+    double* XB_out;       // [nv][2] adjoint of X^n (written by k_a_interp, then accumulated)
     double* XPB;          // [nv][2] in: adjoint of X^n as the previous position of step n+1;
                           //          out: adjoint of X^{n-1}
     double* ubar;         // [N][2] adjoint of the interpolated velocity field (zero between steps)
     double* Gbar;         // [N][2] adjoint of the spread force
-    double* Fbar;         // [nv][2] adjoint of the marker forces
     double* Wbar;         // [nv][9] adjoint of the shape functions
     double* Abar;         // [nmem] adjoint of the enclosed areas
     double* ks_bar;       // [nmem] accumulated dJ/dk_s
@@ -34,6 +34,21 @@ struct AdjointArgs {
 };
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
+
+// enclosed areas A[k][nmem] and bounding boxes box[k][nmem][4] of the taped
+// positions X_k = tape_X + k * 2 nv of steps k = 0 .. len-1, in one launch
+cudaError_t launch_tape_areas(const MarkerArgs& m, const double* tape_X, int len, double* A, double* box,
+                              cudaStream_t s);
+
+// Up to four device-to-device copies of whole 4-byte words in one launch (the
+// tape of a step: fewer calls per reverse step than one copy each)
+struct CopyList {
+    const void* src[4];
+    void* dst[4];
+    size_t words[4];
+    int n;
+};
+cudaError_t launch_copy_words(const CopyList& l, cudaStream_t s);
 
 // FP64 copies for the tape of a context of another precision: stored
 // populations (deviations, scaled storage undone) and compute-type arrays

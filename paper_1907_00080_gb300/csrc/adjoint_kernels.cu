@@ -1,12 +1,13 @@
 // Reverse-mode (adjoint) step of the FP64 time step.
 //
 // Transposes, in reverse order, the parts of one step (Sec. 2.1 - 2.4):
-//   interpolation                                      -> k_a_interp
+//   BDF2 advance (Euler on step 0), interpolation      -> k_a_interp
 //   moments + Guo-forced BGK collision and pull stream -> k_a_collide
-//   spreading, BDF2 advance (Euler on step 0)          -> k_a_spread
-//   membrane, bond and repulsion forces, MLS/Roma
-//   shape functions                                    -> k_a_forces
+//   spreading, membrane, bond and repulsion forces,
+//   MLS/Roma shape functions                           -> k_a_forces
 //   enclosed area                                      -> k_a_area
+// (the areas and bounding boxes the force terms use are evaluated for a whole
+// taped segment at once, k_tape_areas)
 // The lattice part (every node, FP64) is written out by hand: the collision
 // is (1 - omega) d_i plus a function of five scalars (drho, j, G), and its
 // transpose costs about as much as the collision itself.  The per-vertex parts
@@ -111,9 +112,10 @@ __device__ __forceinline__ Bdf2 bdf2(long long step) {
     return step == 0 ? Bdf2{1.0, 0.0, 1.0} : Bdf2{4.0 / 3.0, -1.0 / 3.0, 2.0 / 3.0};
 }
 
-// Adjoint of the interpolation U_v = sum_k W_vk u(x_k), with U_v-bar = cu X_v^{n+1}-bar:
-// the velocity adjoint is scattered onto the nodes, and W_vk-bar = U_v-bar . u(x_k).
-// One thread per (vertex, stencil entry k = blockIdx.y).
+// Adjoint of the advance X^{n+1} = ca X^n + cb X^{n-1} + cu U^n and of the
+// interpolation U_v = sum_k W_vk u(x_k): the velocity adjoint cu X_v^{n+1}-bar is
+// scattered onto the nodes, and W_vk-bar = U_v-bar . u(x_k).  One thread per
+// (vertex, stencil entry k = blockIdx.y); the k = 0 thread also starts X^n-bar.
 __global__ void k_a_interp(const AdjointArgs a) {
     const TangentArgs& t = a.t;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,8 +123,16 @@ __global__ void k_a_interp(const AdjointArgs a) {
     if (v == 0 && k == 0)
         for (int m = 0; m < t.m.nmem; ++m) a.Abar[m] = 0.0;
     if (v >= t.m.nv) return;
-    const double cu = bdf2(t.step).cu;
-    const double Ubx = cu * a.XB[2 * v], Uby = cu * a.XB[2 * v + 1];
+    const Bdf2 q = bdf2(t.step);
+    const double Ubx = q.cu * a.XB[2 * v], Uby = q.cu * a.XB[2 * v + 1];
+    if (k == 0) {
+        // the BDF2 part: X^n-bar = X^n-slot-bar + ca X^{n+1}-bar, X^{n-1}-bar = cb X^{n+1}-bar
+        for (int c = 0; c < 2; ++c) {
+            const double xb = a.XB[2 * v + c];
+            a.XB_out[2 * v + c] = a.XPB[2 * v + c] + q.ca * xb;
+            a.XPB[2 * v + c] = q.cb * xb;
+        }
+    }
     const int i0 = t.st[2 * v], j0 = t.st[2 * v + 1];
     double wb = 0.0;
     if (!(t.m.walls && (j0 + k / 3 - 1 < 0 || j0 + k / 3 - 1 >= t.m.ny))) {
@@ -171,36 +181,6 @@ __global__ void k_a_collide(const AdjointArgs a) {
     }
 }
 
-// Adjoint of the spreading G(x_k) += W_vk F_v: F_v-bar and the shape
-// functions' share W_vk-bar += G-bar(x_k) . F_v.
-__global__ void k_a_spread(const AdjointArgs a) {
-    const TangentArgs& t = a.t;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= t.m.nv) return;
-    const int i0 = t.st[2 * v], j0 = t.st[2 * v + 1];
-    const double Fx = t.Fv[2 * v], Fy = t.Fv[2 * v + 1];
-    double Fbx = 0.0, Fby = 0.0;
-    for (int k = 0; k < 9; ++k) {
-        if (t.m.walls && (j0 + k / 3 - 1 < 0 || j0 + k / 3 - 1 >= t.m.ny)) continue;
-        const size_t node = t_node(t, i0, j0, k);
-        const double w = t.Wv[9 * v + k];
-        const double gbx = a.Gbar[2 * node], gby = a.Gbar[2 * node + 1];
-        Fbx += w * gbx;
-        Fby += w * gby;
-        a.Wbar[9 * v + k] += gbx * Fx + gby * Fy;
-    }
-    a.Fbar[2 * v] = Fbx;
-    a.Fbar[2 * v + 1] = Fby;
-    // the BDF2 part of the advance adjoint: X^n-bar = X^n-slot-bar + ca X^{n+1}-bar,
-    // X^{n-1}-bar = cb X^{n+1}-bar (the interpolation share was taken above)
-    const Bdf2 q = bdf2(t.step);
-    for (int c = 0; c < 2; ++c) {
-        const double xb = a.XB[2 * v + c], xpb = a.XPB[2 * v + c];
-        a.XB[2 * v + c] = xpb + q.ca * xb;
-        a.XPB[2 * v + c] = q.cb * xb;
-    }
-}
-
 // Tasks of k_a_forces (blockIdx.y): one dual evaluation each, of the force
 // terms of vertex v that depend on one seed.  Position seeds X_{v+d}: the
 // bending moment at v-1 depends on d in -2..0, the one at v on -1..1, the one
@@ -245,6 +225,22 @@ __global__ void k_a_forces(const AdjointArgs a) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= t.m.nv) return;
     const AdjTask q = c_tasks[blockIdx.y];
+    // the spreading G(x_k) += W_vk F_v transposed: F_v-bar = sum_k W_vk G-bar(x_k),
+    // and the shape functions' share G-bar(x_k) . F_v
+    const int i0 = t.st[2 * v], j0 = t.st[2 * v + 1];
+    const double Fx = t.Fv[2 * v], Fy = t.Fv[2 * v + 1];
+    double Fbx = 0.0, Fby = 0.0, gF[9];
+    for (int k = 0; k < 9; ++k) {
+        gF[k] = 0.0;
+        if (t.m.walls && (j0 + k / 3 - 1 < 0 || j0 + k / 3 - 1 >= t.m.ny)) continue;
+        const size_t node = t_node(t, i0, j0, k);
+        const double w = t.Wv[9 * v + k];
+        const double gbx = a.Gbar[2 * node], gby = a.Gbar[2 * node + 1];
+        Fbx += w * gbx;
+        Fby += w * gby;
+        gF[k] = gbx * Fx + gby * Fy;
+    }
+    double* XB = a.XB_out;
     if (q.kind == kWeightsTask) {
         dual w[9];
         bool in[9];
@@ -252,11 +248,10 @@ __global__ void k_a_forces(const AdjointArgs a) {
         t_vertex_weights(t, v, Seed{kPos, v, q.coord, -1}, w, in, si, sj);
         double acc = 0.0;
         for (int k = 0; k < 9; ++k)
-            if (in[k]) acc += a.Wbar[9 * v + k] * w[k].d;
-        atomicAdd(&a.XB[2 * v + q.coord], acc);
+            if (in[k]) acc += (a.Wbar[9 * v + k] + gF[k]) * w[k].d;
+        atomicAdd(&XB[2 * v + q.coord], acc);
         return;
     }
-    const double Fbx = a.Fbar[2 * v], Fby = a.Fbar[2 * v + 1];
     if (Fbx == 0.0 && Fby == 0.0) return;
     const int m = t_mem_of(t, v);
     const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
@@ -266,7 +261,7 @@ __global__ void k_a_forces(const AdjointArgs a) {
         dual fx, fy;
         t_vertex_force(t, v, m, Seed{q.kind, u, q.coord, m}, fx, fy, q.terms);
         const double g = Fbx * fx.d + Fby * fy.d;
-        double* dst = q.kind == kPos ? &a.XB[2 * u + q.coord]
+        double* dst = q.kind == kPos ? &XB[2 * u + q.coord]
                       : q.kind == kArea ? &a.Abar[m]
                       : q.kind == kKs   ? &a.ks_bar[m]
                       : q.kind == kKb   ? &a.kb_bar[m]
@@ -305,19 +300,19 @@ __global__ void k_a_forces(const AdjointArgs a) {
             const double gx = magb * mx.d, gy = magb * my.d;
             xvb += gx;
             yvb += gy;
-            atomicAdd(&a.XB[2 * b], -gx);
-            atomicAdd(&a.XB[2 * b + 1], -gy);
+            atomicAdd(&XB[2 * b], -gx);
+            atomicAdd(&XB[2 * b + 1], -gy);
         }
     }
     if (!have_g) return;
-    atomicAdd(&a.XB[2 * v], xvb);
-    atomicAdd(&a.XB[2 * v + 1], yvb);
+    atomicAdd(&XB[2 * v], xvb);
+    atomicAdd(&XB[2 * v + 1], yvb);
     if (nbx == 0.0 && nby == 0.0) return;
     for (int dk = -1; dk <= 1; ++dk) {
         const int u = t_ring(off, n, k + dk);
         for (int c = 0; c < 2; ++c) {
             const VGeo gs = t_vgeo(t, off, n, k, Seed{kPos, u, c, -1});
-            atomicAdd(&a.XB[2 * u + c], nbx * gs.nx.d + nby * gs.ny.d);
+            atomicAdd(&XB[2 * u + c], nbx * gs.nx.d + nby * gs.ny.d);
         }
     }
 }
@@ -334,8 +329,48 @@ __global__ void k_a_area(const AdjointArgs a) {
     const int off = t.m.mem_off[m], n = t.m.mem_n[m], k = v - off;
     const double* X = static_cast<const double*>(t.m.X);
     const int L = t_ring(off, n, k - 1), R = t_ring(off, n, k + 1);
-    atomicAdd(&a.XB[2 * v], 0.5 * Ab * (X[2 * R + 1] - X[2 * L + 1]));
-    atomicAdd(&a.XB[2 * v + 1], 0.5 * Ab * (X[2 * L] - X[2 * R]));
+    atomicAdd(&a.XB_out[2 * v], 0.5 * Ab * (X[2 * R + 1] - X[2 * L + 1]));
+    atomicAdd(&a.XB_out[2 * v + 1], 0.5 * Ab * (X[2 * L] - X[2 * R]));
+}
+
+// areas (shoelace about vertex 0) and bounding boxes of the taped positions of
+// step k = blockIdx.y, membrane m = blockIdx.x
+__global__ void k_tape_areas(const MarkerArgs mg, const double* __restrict__ tape_X, double* A, double* box) {
+    const int m = blockIdx.x, k = blockIdx.y;
+    const int off = mg.mem_off[m], n = mg.mem_n[m];
+    const double* X = tape_X + (size_t)k * 2 * (size_t)(mg.nv > 0 ? mg.nv : 1);
+    const double x0 = X[2 * off], y0 = X[2 * off + 1];
+    double s = 0.0, bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int a = off + j, b = off + (j + 1) % n;
+        s += (X[2 * a] - x0) * (X[2 * b + 1] - y0) - (X[2 * b] - x0) * (X[2 * a + 1] - y0);
+        bx0 = fmin(bx0, X[2 * a]);
+        bx1 = fmax(bx1, X[2 * a]);
+        by0 = fmin(by0, X[2 * a + 1]);
+        by1 = fmax(by1, X[2 * a + 1]);
+    }
+    __shared__ double r[5][256];
+    r[0][threadIdx.x] = s;
+    r[1][threadIdx.x] = bx0;
+    r[2][threadIdx.x] = bx1;
+    r[3][threadIdx.x] = by0;
+    r[4][threadIdx.x] = by1;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            r[0][threadIdx.x] += r[0][threadIdx.x + o];
+            r[1][threadIdx.x] = fmin(r[1][threadIdx.x], r[1][threadIdx.x + o]);
+            r[2][threadIdx.x] = fmax(r[2][threadIdx.x], r[2][threadIdx.x + o]);
+            r[3][threadIdx.x] = fmin(r[3][threadIdx.x], r[3][threadIdx.x + o]);
+            r[4][threadIdx.x] = fmax(r[4][threadIdx.x], r[4][threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const size_t q = (size_t)k * mg.nmem + m;
+        A[q] = 0.5 * r[0][0];
+        for (int c = 0; c < 4; ++c) box[4 * q + c] = r[1 + c][0];
+    }
 }
 
 // read-back layout <-> stored deviations (a permutation; the constant w_i of the
@@ -366,6 +401,15 @@ __global__ void k_widen_compute(const C* __restrict__ src, double* __restrict__ 
         dst[k] = (double)src[k];
 }
 
+__global__ void k_copy_words(const CopyList l) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int c = 0; c < l.n; ++c) {
+        const uint32_t* __restrict__ src = static_cast<const uint32_t*>(l.src[c]);
+        uint32_t* __restrict__ dst = static_cast<uint32_t*>(l.dst[c]);
+        for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < l.words[c]; k += stride) dst[k] = src[k];
+    }
+}
+
 int node_grid(size_t N) { return (int)((N + 255) / 256 < 4096 ? (N + 255) / 256 : 4096); }
 
 }  // namespace
@@ -375,19 +419,21 @@ cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
     const size_t N = (size_t)t.m.nx * t.m.ny;
     const int nvb = (t.m.nv + 31) / 32;
     cudaError_t e;
-    if (t.m.nv > 0) {
-        // areas and bounding boxes of X^n (forces, shape functions and the spread
-        // force come from the tape)
-        if ((e = launch_tangent_areas(t, s)) != cudaSuccess) return e;
-        k_a_interp<<<dim3(nvb, 9), 32, 0, s>>>(a);
-    }
+    if (t.m.nv > 0) k_a_interp<<<dim3(nvb, 9), 32, 0, s>>>(a);
     // FP64-bound: 128-thread blocks, up to 16 per SM
     k_a_collide<<<(int)std::min<size_t>((N + 127) / 128, 152 * 16), 128, 0, s>>>(a);
     if (t.m.nv > 0) {
-        k_a_spread<<<nvb, 32, 0, s>>>(a);
         k_a_forces<<<dim3(nvb, kNumTasks), 32, 0, s>>>(a);
         k_a_area<<<nvb, 32, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_words(const CopyList& l, cudaStream_t s) {
+    size_t most = 0;
+    for (int c = 0; c < l.n; ++c) most = l.words[c] > most ? l.words[c] : most;
+    if (most == 0) return cudaSuccess;
+    k_copy_words<<<std::min<size_t>((most + 255) / 256, 152 * 8), 256, 0, s>>>(l);
     return cudaGetLastError();
 }
 
@@ -413,6 +459,13 @@ cudaError_t launch_widen_compute(lbib_precision prec, const void* src, double* d
     const int g = node_grid(n);
     if (prec == LBIB_F64) k_widen_compute<double><<<g, 256, 0, s>>>(static_cast<const double*>(src), dst, n);
     else k_widen_compute<float><<<g, 256, 0, s>>>(static_cast<const float*>(src), dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tape_areas(const MarkerArgs& m, const double* tape_X, int len, double* A, double* box,
+                              cudaStream_t s) {
+    if (m.nv == 0 || len == 0) return cudaSuccess;
+    k_tape_areas<<<dim3(m.nmem, len), 256, 0, s>>>(m, tape_X, A, box);
     return cudaGetLastError();
 }
 

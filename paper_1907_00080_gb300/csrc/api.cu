@@ -1429,7 +1429,9 @@ struct lbib_adjoint {
     // adjoint state and per-step work arrays
     double* fbar[2] = {nullptr, nullptr};
     int cb = 0;
-    double *XB = nullptr, *XPB = nullptr, *ubar = nullptr, *Gbar = nullptr, *Fbar = nullptr, *Wbar = nullptr;
+    double* XB[2] = {nullptr, nullptr};  // adjoint of the current positions (roles alternate per step)
+    int xb = 0;
+    double *XPB = nullptr, *ubar = nullptr, *Gbar = nullptr, *Wbar = nullptr;
     double *Abar = nullptr, *ksb = nullptr, *kbb = nullptr, *sgb = nullptr, *fio = nullptr;
     // areas and boxes re-evaluated per step (tangent area kernel, zero tangent)
     double *A = nullptr, *Ad = nullptr, *box = nullptr, *zero = nullptr, *th0 = nullptr, *l0 = nullptr;
@@ -1488,12 +1490,14 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
          (a->tape_st = (int*)get(K * 2 * nv * 4)) && (a->tape_G = (longlong2*)get(K * N * sizeof(longlong2)));
     ok = ok && (a->fbar[0] = (double*)get(9 * N * 8)) && (a->fbar[1] = (double*)get(9 * N * 8)) &&
          (a->fio = (double*)get(9 * N * 8));
-    ok = ok && (a->XB = (double*)get(2 * nv * 8)) && (a->XPB = (double*)get(2 * nv * 8)) &&
-         (a->Fbar = (double*)get(2 * nv * 8)) && (a->Wbar = (double*)get(9 * nv * 8));
+    ok = ok && (a->XB[0] = (double*)get(2 * nv * 8)) && (a->XB[1] = (double*)get(2 * nv * 8)) &&
+         (a->XPB = (double*)get(2 * nv * 8)) && (a->Wbar = (double*)get(9 * nv * 8));
     ok = ok && (a->ubar = (double*)get(2 * N * 8)) && (a->Gbar = (double*)get(2 * N * 8));
     ok = ok && (a->Abar = (double*)get(nm * 8)) && (a->ksb = (double*)get(nm * 8)) && (a->kbb = (double*)get(nm * 8)) &&
          (a->sgb = (double*)get(8));
-    ok = ok && (a->A = (double*)get(nm * 8)) && (a->Ad = (double*)get(nm * 8)) && (a->box = (double*)get(4 * nm * 8));
+    // areas and boxes of every taped step (one launch per segment)
+    ok = ok && (a->A = (double*)get(K * nm * 8)) && (a->Ad = (double*)get(nm * 8)) &&
+         (a->box = (double*)get(K * 4 * nm * 8));
     ok = ok && (a->zero = (double*)get(std::max(2 * nv, nm) * 8)) && (a->th0 = (double*)get(nv * 8)) &&
          (a->l0 = (double*)get(nv * 8));
     if (!ok) {
@@ -1562,8 +1566,8 @@ extern "C" lbib_status lbib_adjoint_seed(lbib_adjoint* a, const double* xy_bar, 
     if (a->n_rec == 0) return fail(c, LBIB_E_STATE, "nothing recorded: call lbib_adjoint_record first");
     const size_t N = (size_t)c->nx * c->ny, nv = (size_t)c->nv, nm = std::max(c->nmem, 1);
     if (nv) {
-        if (xy_bar) CK(cudaMemcpyAsync(a->XB, xy_bar, 16 * nv, cudaMemcpyHostToDevice, c->stream));
-        else CK(cudaMemsetAsync(a->XB, 0, 16 * nv, c->stream));
+        if (xy_bar) CK(cudaMemcpyAsync(a->XB[a->xb], xy_bar, 16 * nv, cudaMemcpyHostToDevice, c->stream));
+        else CK(cudaMemsetAsync(a->XB[a->xb], 0, 16 * nv, c->stream));
         if (xy_prev_bar) CK(cudaMemcpyAsync(a->XPB, xy_prev_bar, 16 * nv, cudaMemcpyHostToDevice, c->stream));
         else CK(cudaMemsetAsync(a->XPB, 0, 16 * nv, c->stream));
     }
@@ -1601,29 +1605,44 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
         const size_t nvr = (size_t)c->nv;
         const bool f64 = c->prec == LBIB_F64;  // other precisions: FP64 copies on the tape
         for (int k = 0; k < len; ++k) {
-            if (f64) CK(d2d(a->tape_f + (size_t)k * 9 * N, c->f[c->cur], 9 * N * 8));
-            else CK(launch_widen_storage(c->prec, c->f[c->cur], a->tape_f + (size_t)k * 9 * N, 9 * N, c->inv_scale,
-                                         c->stream));
-            if (nvr && f64) CK(d2d(a->tape_X + (size_t)k * 2 * nv, c->ma.X, 16 * nvr));
-            if (nvr && !f64) CK(launch_pos_out(c->prec, c->ma.X, a->tape_X + (size_t)k * 2 * nv, c->nv, c->stream));
-            if (c->nlig) CK(d2d(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig));
+            if (f64) {
+                // the state the step starts from, in one launch
+                CopyList l{};
+                l.src[0] = c->f[c->cur]; l.dst[0] = a->tape_f + (size_t)k * 9 * N; l.words[0] = 18 * N;
+                l.src[1] = c->ma.X; l.dst[1] = a->tape_X + (size_t)k * 2 * nv; l.words[1] = 4 * nvr;
+                l.src[2] = c->ma.bond_of_lig; l.dst[2] = a->tape_bond + (size_t)k * nl; l.words[2] = (size_t)c->nlig;
+                l.n = 3;
+                CK(launch_copy_words(l, c->stream));
+            } else {
+                CK(launch_widen_storage(c->prec, c->f[c->cur], a->tape_f + (size_t)k * 9 * N, 9 * N, c->inv_scale,
+                                        c->stream));
+                if (nvr) CK(launch_pos_out(c->prec, c->ma.X, a->tape_X + (size_t)k * 2 * nv, c->nv, c->stream));
+                if (c->nlig) CK(d2d(a->tape_bond + (size_t)k * nl, c->ma.bond_of_lig, 4 * (size_t)c->nlig));
+            }
             const int src = c->cur;
             CK(cudaGraphLaunch(c->graph[c->cur][0], c->stream));
             c->cur = 1 - c->cur;
             c->steps += 1;
             if (nvr && f64) {
-                CK(d2d(a->tape_F + (size_t)k * 2 * nv, c->ma.F, 16 * nvr));
-                CK(d2d(a->tape_W + (size_t)k * 9 * nv, c->ma.W, 72 * nvr));
+                // what the step computed, in one launch
+                CopyList l{};
+                l.src[0] = c->ma.F; l.dst[0] = a->tape_F + (size_t)k * 2 * nv; l.words[0] = 4 * nvr;
+                l.src[1] = c->ma.W; l.dst[1] = a->tape_W + (size_t)k * 9 * nv; l.words[1] = 18 * nvr;
+                l.src[2] = c->ma.stencil; l.dst[2] = a->tape_st + (size_t)k * 2 * nv; l.words[2] = 2 * nvr;
+                l.src[3] = c->G[src]; l.dst[3] = a->tape_G + (size_t)k * N; l.words[3] = 4 * N;
+                l.n = 4;
+                CK(launch_copy_words(l, c->stream));
             } else if (nvr) {
                 CK(launch_widen_compute(c->prec, c->ma.F, a->tape_F + (size_t)k * 2 * nv, 2 * nvr, c->stream));
                 CK(launch_widen_compute(c->prec, c->ma.W, a->tape_W + (size_t)k * 9 * nv, 9 * nvr, c->stream));
-            }
-            if (nvr) {
                 CK(d2d(a->tape_st + (size_t)k * 2 * nv, c->ma.stencil, 8 * nvr));
                 CK(d2d(a->tape_G + (size_t)k * N, c->G[src], N * sizeof(longlong2)));
             }
         }
+        // areas and bounding boxes of the segment's taped positions
+        CK(launch_tape_areas(c->ma, a->tape_X, len, a->A, a->box, c->stream));
         // adjoint steps, last to first
+        const size_t nm = std::max(c->nmem, 1);
         for (int k = len - 1; k >= 0; --k) {
             AdjointArgs g{};
             TangentArgs& t = g.t;
@@ -1636,17 +1655,19 @@ extern "C" lbib_status lbib_adjoint_reverse(lbib_adjoint* a) {
             t.Fv = a->tape_F + (size_t)k * 2 * nv;
             t.Wv = a->tape_W + (size_t)k * 9 * nv;
             t.st = a->tape_st + (size_t)k * 2 * nv;
-            t.A = a->A; t.Ad = a->Ad; t.box = a->box;
+            t.A = a->A + (size_t)k * nm; t.Ad = a->zero; t.box = a->box + (size_t)k * 4 * nm;
             t.dks = a->zero; t.dkb = a->zero; t.dsigma = 0.0; t.th0 = a->th0; t.l0 = a->l0;
             g.gfix = a->tape_G + (size_t)k * N;
             t.omega = 1.0 / c->tau; t.gx = c->gx; t.gy = c->gy;
             t.step = s.step + k;
             g.fbar = a->fbar[a->cb];
             g.fbar_out = a->fbar[1 - a->cb];
-            g.XB = a->XB; g.XPB = a->XPB; g.ubar = a->ubar; g.Gbar = a->Gbar; g.Fbar = a->Fbar; g.Wbar = a->Wbar;
+            g.XB = a->XB[a->xb]; g.XB_out = a->XB[1 - a->xb];
+            g.XPB = a->XPB; g.ubar = a->ubar; g.Gbar = a->Gbar; g.Wbar = a->Wbar;
             g.Abar = a->Abar; g.ks_bar = a->ksb; g.kb_bar = a->kbb; g.sigma_bar = a->sgb;
             CK(launch_adjoint_step(g, c->stream));
             a->cb = 1 - a->cb;
+            a->xb = 1 - a->xb;
         }
     }
     // leave the context as the recorded run left it
@@ -1662,7 +1683,7 @@ extern "C" lbib_status lbib_adjoint_read(lbib_adjoint* a, double* xy_bar, double
     lbib_ctx* c = a->c;
     if (!a->seeded) return fail(c, LBIB_E_STATE, "the adjoint has not been seeded");
     const size_t N = (size_t)c->nx * c->ny, nv = (size_t)c->nv, nm = (size_t)c->nmem;
-    if (xy_bar && nv) CK(cudaMemcpyAsync(xy_bar, a->XB, 16 * nv, cudaMemcpyDeviceToHost, c->stream));
+    if (xy_bar && nv) CK(cudaMemcpyAsync(xy_bar, a->XB[a->xb], 16 * nv, cudaMemcpyDeviceToHost, c->stream));
     if (xy_prev_bar && nv) CK(cudaMemcpyAsync(xy_prev_bar, a->XPB, 16 * nv, cudaMemcpyDeviceToHost, c->stream));
     if (ks_bar && nm) CK(cudaMemcpyAsync(ks_bar, a->ksb, 8 * nm, cudaMemcpyDeviceToHost, c->stream));
     if (kb_bar && nm) CK(cudaMemcpyAsync(kb_bar, a->kbb, 8 * nm, cudaMemcpyDeviceToHost, c->stream));
