@@ -478,7 +478,8 @@ def couette_form(lbib, torch, stream, warm=2000, timed=4000):
             res["%s_sigma%g" % (carrier, sigma)] = {
                 "mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "bonds": int(o[5]),
                 "n_L_over_n_L_after_warm": float(o[5] / o0[5]) if o0[5] > 0 else None,
-                "u_roll_over_u_wall": float(o[2] / wl.wall_velocity[1]),
+                # mean centroid speed over the timed steps, over the wall speed
+                "u_roll_over_u_wall": float((o[0] - o0[0]) / timed / wl.wall_velocity[1]),
                 "carrier_min_height_lu": float(o[6]), "region": int(o[4]), "tiling": list(sim.tiling)}
             sim.close()
     return {"workload": "Couette 600x200 (dx = 15 nm, H_CFL = 3 um), Re = 0.003, one 1 um carrier x 210 markers, "

@@ -644,6 +644,8 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.inv_scale = c->inv_scale;
     l.bb_bot = bb_term(c->uw_bot);
     l.bb_top = bb_term(c->uw_top);
+    l.bbf_bot = (float)l.bb_bot;
+    l.bbf_top = (float)l.bb_top;
     l.fields_only = 0;
     l.tile_w = c->tile_w;
     l.tile_h = c->tile_h;

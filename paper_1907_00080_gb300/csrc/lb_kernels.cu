@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
             const S* row = src + (size_t)opp(i) * N + (size_t)y * nx;
             load_pack<S, VEC>(row, x0, ok, inv, f[i]);
             if (cx(i) != 0) {
-                const C t = C(cx(i)) * C(sy < 0 ? a.bb_bot : a.bb_top);
+                const C t = C(cx(i)) * wall_term<C>(a, cy(i) > 0);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) f[i][k] += t;
             }

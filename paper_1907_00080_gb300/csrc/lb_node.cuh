@@ -24,6 +24,15 @@ template <> __device__ __forceinline__ double from_fix<double>(long long v) {
     return __ll2double_rn(v) * kFixInv;
 }
 
+// momentum term of the lower (bottom = true) or upper moving wall in the compute type
+template <typename C> __device__ __forceinline__ C wall_term(const LbArgs& a, bool bottom);
+template <> __device__ __forceinline__ float wall_term<float>(const LbArgs& a, bool bottom) {
+    return bottom ? a.bbf_bot : a.bbf_top;
+}
+template <> __device__ __forceinline__ double wall_term<double>(const LbArgs& a, bool bottom) {
+    return bottom ? a.bb_bot : a.bb_top;
+}
+
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }  // = 1.0f / x, correctly rounded
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
                         for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
                         if (bb && cx(i) != 0) {
                             // the momentum of a moving wall (diagonals only)
-                            const C t = C(cx(i)) * C(y - cy(i) < 0 ? a.bb_bot : a.bb_top);
+                            const C t = C(cx(i)) * wall_term<C>(a, cy(i) > 0);
 #pragma unroll
                             for (int q = 0; q < NPT; ++q) f[i][q] += t;
                         }
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
                     for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
                     if (bb && cx(i) != 0) {
                         // the momentum of a moving wall (diagonals only)
-                        const C t = C(cx(i)) * C(y - cy(i) < 0 ? a.bb_bot : a.bb_top);
+                        const C t = C(cx(i)) * wall_term<C>(a, cy(i) > 0);
 #pragma unroll
                         for (int q = 0; q < NPT; ++q) f[i][q] += t;
                     }

@@ -99,6 +99,7 @@ struct LbArgs {
     float inv_scale;       // 2^-k for 16-bit storage, 1 otherwise
     double bb_bot, bb_top; // moving walls: 6 w_d u_w (w_d = 1/36) of the lower / upper wall; a
                            // diagonal population bounced back there gains cx(i) times it
+    float bbf_bot, bbf_top;  // the same rounded to FP32 (no FP64 conversion in the FP32 kernels)
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
     int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags
     int* status;           // device status word (StatusBits)
