@@ -119,3 +119,27 @@ def test_repulsion_pushes_close_membranes_apart():
     assert abs(F[ia, 0]) >= c0 * d ** -2.5 * 0.99
     far = np.hypot(a[:, 0] - 25.0, a[:, 1] - 16.0) > 4.0
     assert np.all(F[:24][far] == 0.0)
+
+
+def test_whole_step_carries_a_relaxed_capsule_with_a_uniform_flow():
+    """A closed-form check of the whole step's orchestration (forces ->
+    spreading -> collision -> interpolation -> BDF2): both walls moving at U
+    keep the fluid uniform (tau = 1 Couette state of equal wall speeds), the
+    capsule at its rest shape feels no force, the interpolated velocity of a
+    uniform field is U (partition of unity of the shape functions, near the
+    walls too), and Euler then BDF2 give X^n = X^0 + n U exactly."""
+    import oracle
+    U = 0.013
+    s = oracle.OracleSim(64, 16, tau=1.0, walls=1, init="couette", wall_velocity=(U, U))
+    ring = np.stack([20.0 + 3.0 * np.cos(2 * np.pi * (np.arange(24) + 0.5) / 24),
+                     2.2 + 3.0 * np.sin(2 * np.pi * (np.arange(24) + 0.5) / 24)], axis=1)
+    s.add_membrane(ring, 0.05, 0.005, 0.1)
+    x0 = s.markers()
+    s.step(40)
+    x = s.markers()
+    np.testing.assert_allclose(x[:, 0], x0[:, 0] + 40 * U, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(x[:, 1], x0[:, 1], rtol=0, atol=1e-13)
+    rho, ux, uy = s.fields()
+    np.testing.assert_allclose(ux, U, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(uy, 0.0, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(s.forces(), 0.0, rtol=0, atol=1e-13)  # the rest shape, translated
