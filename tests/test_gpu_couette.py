@@ -185,3 +185,22 @@ def test_wall_velocity_errors():
         L.lbib_set_wall_velocity(s.ctx, 0.0, 0.02)
     assert ei.value.status == L.LBIB_E_STATE
     s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-6)])
+def test_relaxed_capsule_translates_with_a_uniform_flow(prec, tol):
+    """The closed form of the oracle pin on the GPU path: walls moving together
+    at U, a capsule at its rest shape next to the wall; every marker moves by
+    exactly U per step."""
+    U = 0.013
+    ring = inputs.circle(20.0, 3.3, 3.0, 24)  # lowest marker 0.8 lu from the wall: MLS re-solve
+    wl = inputs.Workload(name="uniform", nx=64, ny=16, tau=1.0, body_force=(0.0, 0.0), walls=1, init="couette",
+                         precision=prec, membranes=[inputs.Membrane(xy=ring, ks=0.05, kb=0.005, ka=0.1)],
+                         receptors=None, wall_velocity=(U, U))
+    s = lb().Simulation(wl)
+    x0 = s.markers()
+    s.step(40)
+    x = s.markers()
+    assert np.max(np.abs(x[:, 0] - (x0[:, 0] + 40 * U))) <= tol
+    assert np.max(np.abs(x[:, 1] - x0[:, 1])) <= tol
+    s.close()

@@ -132,7 +132,7 @@ def test_whole_step_carries_a_relaxed_capsule_with_a_uniform_flow():
     U = 0.013
     s = oracle.OracleSim(64, 16, tau=1.0, walls=1, init="couette", wall_velocity=(U, U))
     ring = np.stack([20.0 + 3.0 * np.cos(2 * np.pi * (np.arange(24) + 0.5) / 24),
-                     2.2 + 3.0 * np.sin(2 * np.pi * (np.arange(24) + 0.5) / 24)], axis=1)
+                     3.3 + 3.0 * np.sin(2 * np.pi * (np.arange(24) + 0.5) / 24)], axis=1)
     s.add_membrane(ring, 0.05, 0.005, 0.1)
     x0 = s.markers()
     s.step(40)
