@@ -354,7 +354,7 @@ NCU_TRAFFIC = {
     (KERNEL_NAMES[0], "f32", "capillary_640x160"): 422912,
     (KERNEL_NAMES[2], "f32", "capillary_640x160"): 633600,
     # 8192 x 1024 capture scaled by the nodes to the 8192 x 2048 probe
-    ("k_lb_stream", "f32", "probe_8192x2048"): 2 * (322649600 + 257857792),
+    ("k_lb_stream", "f32", "probe_8192x2048"): 2 * (322732800 + 257833728),
 }
 
 
