@@ -18,6 +18,7 @@ using namespace lbib;
 namespace {
 
 constexpr int kChunk = 16;  // steps per captured chunk graph (even)
+constexpr int kMaxGridY = 65535;  // largest y extent of a launch grid
 
 lbib_status fail(lbib_ctx* c, lbib_status st, const std::string& msg) {
     if (c) c->err = msg;
@@ -96,6 +97,8 @@ void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
     // up to 4 rows while the grid still fills the GPU several times over
     int t = N >= (1LL << 20) ? 1 : 4;
     while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 8) t /= 2;
+    // the grid's y extent (rows / t) is limited to 65535 blocks
+    while (t < 16 && (c->ny + t - 1) / t > kMaxGridY) t *= 2;
     *vec = v;
     *ty = t;
 }
@@ -297,7 +300,8 @@ extern "C" lbib_status lbib_set_tiling(lbib_ctx* c, int32_t vec, int32_t ty) {
         c->vec = c->ty = 0;
         return LBIB_OK;
     }
-    const bool ok = ty == 0 ? valid_stream(c->prec, vec, c->nx) : (valid_vec(c->prec, vec, c->nx) && ty >= 1 && ty <= 16);
+    const bool ok = ty == 0 ? valid_stream(c->prec, vec, c->nx)
+                            : (valid_vec(c->prec, vec, c->nx) && ty >= 1 && ty <= 16 && (c->ny + ty - 1) / ty <= kMaxGridY);
     if (!ok) return fail(c, LBIB_E_INVALID, "unsupported tiling");
     c->vec = vec;
     c->ty = ty;
@@ -325,6 +329,8 @@ static lbib_status finalize(lbib_ctx* c) {
         c->tile_h = 1;
         CK(prepare_lb_stream(c->prec, c->vec, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, &c->stream_grid));
     } else {
+        if ((c->ny + c->ty - 1) / c->ty > kMaxGridY)
+            return fail(c, LBIB_E_INVALID, "lattice too tall for the row-tile form: more than 65535 x 16 rows");
         c->tile_w = 32 * c->vec;
         c->tile_h = c->ty;
     }
@@ -795,7 +801,8 @@ extern "C" lbib_status lbib_read_fields(lbib_ctx* c, double* rho, double* ux, do
     // the row-tile kernel serves the read-back in either form (it looks the
     // force flags up by the context's tile geometry)
     const int rv = c->ty != 0 ? c->vec : (c->prec == LBIB_F32_STORE_F16 || c->prec == LBIB_F32_STORE_BF16 ? 2 : 1);
-    const int rt = c->ty != 0 ? c->ty : 4;
+    int rt = c->ty != 0 ? c->ty : 4;
+    while (rt < 16 && (c->ny + rt - 1) / rt > kMaxGridY) rt *= 2;
     CK(launch_lb_step(c->prec, rv, rt, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
     if (!on_device) {
         if (rho) CK(cudaMemcpyAsync(rho, dr, N * 8, cudaMemcpyDeviceToHost, c->stream));
