@@ -308,6 +308,29 @@ lbib_status lbib_adjoint_read(lbib_adjoint* adj, double* xy_bar, double* xy_prev
 int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* adj);
 void lbib_adjoint_destroy(lbib_adjoint* adj);
 
+/* Save and restore the full step state of a context (checkpoint / resume).
+ * lbib_save writes to the file at `path`:
+ *  - a header identifying the set-up;
+ *  - the populations in the context's storage format;
+ *  - X^n and X^{n-1};
+ *  - the bonds and the receptor occupancy;
+ *  - the repulsion boxes;
+ *  - the step counter.
+ * The file is in host byte order.
+ * lbib_load restores such a file into a context built with the same set-up
+ * (same lattice, precision, walls and wall velocities, body force, tau,
+ * membranes, ligands, receptors and repulsion range; LBIB_E_INVALID
+ * otherwise, with the context untouched).  It resets the per-step scratch.
+ * It also clears a poisoned context: after LBIB_E_NONFINITE or
+ * LBIB_E_TIMEOUT, loading a saved state lets lbib_step run again.  Stepping
+ * on from a loaded state reproduces the original run bit for bit.  Both
+ * synchronise the context's stream.
+ * Errors: LBIB_E_INVALID (NULL, unreadable or unwritable file, not a saved
+ * state, truncated, other set-up), LBIB_E_STATE (lbib_save on a poisoned
+ * context), LBIB_E_CUDA. */
+lbib_status lbib_save(lbib_ctx* ctx, const char* path);
+lbib_status lbib_load(lbib_ctx* ctx, const char* path);
+
 /* Observables of the margination and adhesion studies (Sec. 4) for every
  * membrane, reduced on the device in FP64 over the current markers.  out
  * receives 8 doubles per membrane (host memory, nmem * 8):

@@ -1707,3 +1707,131 @@ extern "C" lbib_status lbib_adjoint_read(lbib_adjoint* a, double* xy_bar, double
 }
 
 extern "C" int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* a) { return a ? a->n_rec : -1; }
+
+// ------------------------------------------------------------------ save / load
+// The full step state of a context in a binary file: a header that identifies
+// the set-up, then the stored populations of the current buffer (storage
+// format), X^n, X^{n-1}, the bonds, the receptor occupancy (both orders), the
+// repulsion segment boxes and the step counter.  Host byte order.
+namespace {
+
+constexpr char kSaveMagic[8] = {'L', 'B', 'I', 'B', 'S', 'A', 'V', '1'};
+
+struct SaveHeader {
+    char magic[8];
+    int32_t version, nx, ny, prec, walls, nmem, nv, nlig, nrec, nseg, scale_exp, pad;
+    double tau, gx, gy, uw_bot, uw_top, d_rep;
+    int64_t steps;
+};
+
+SaveHeader header_of(const lbib_ctx* c) {
+    SaveHeader h{};
+    std::memcpy(h.magic, kSaveMagic, 8);
+    h.version = 1;
+    h.nx = c->nx; h.ny = c->ny; h.prec = (int32_t)c->prec; h.walls = (int32_t)c->walls;
+    h.nmem = c->nmem; h.nv = c->nv; h.nlig = c->nlig; h.nrec = c->ma.nrec; h.nseg = c->nseg;
+    h.scale_exp = c->scale_exp;
+    h.tau = c->tau; h.gx = c->gx; h.gy = c->gy; h.uw_bot = c->uw_bot; h.uw_top = c->uw_top; h.d_rep = c->d_rep;
+    h.steps = c->steps;
+    return h;
+}
+
+// the device arrays of the state, with their sizes in bytes
+struct StatePart {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<StatePart> state_parts(lbib_ctx* c) {
+    const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
+    return {{c->f[c->cur], 9 * N * c->pop_elem}, {c->ma.X, 16 * nv},          {c->ma.Xp, 16 * nv},
+            {c->ma.bond_of_lig, 4 * nlig},       {c->ma.owner, 4 * nrec},     {c->ma.owner_cell, 4 * nrec},
+            {c->ma.seg_box, sizeof(float4) * (size_t)c->nseg},              {c->d_step, 8}};
+}
+
+}  // namespace
+
+extern "C" lbib_status lbib_save(lbib_ctx* c, const char* path) {
+    if (!c || !path) return LBIB_E_INVALID;
+    if (c->poisoned) return fail(c, LBIB_E_STATE, "context poisoned by an earlier device-side failure");
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, LBIB_E_INVALID, std::string("cannot open for writing: ") + path);
+    const SaveHeader h = header_of(c);
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1;
+    std::vector<char> buf;
+    for (const StatePart& p : state_parts(c)) {
+        if (!ok || p.bytes == 0) continue;
+        buf.resize(p.bytes);
+        const cudaError_t e = cudaMemcpy(buf.data(), p.dev, p.bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(fp);
+            return cuda_fail(c, e, "save: read-back");
+        }
+        ok = std::fwrite(buf.data(), 1, p.bytes, fp) == p.bytes;
+    }
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(c, LBIB_E_INVALID, std::string("cannot write: ") + path);
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_load(lbib_ctx* c, const char* path) {
+    if (!c || !path) return LBIB_E_INVALID;
+    lbib_status st = finalize(c);
+    if (st == LBIB_OK) st = build_graphs(c);
+    if (st != LBIB_OK) return st;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, LBIB_E_INVALID, std::string("cannot open for reading: ") + path);
+    SaveHeader h{};
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kSaveMagic, 8) != 0 || h.version != 1) {
+        std::fclose(fp);
+        return fail(c, LBIB_E_INVALID, "not a saved lbib state");
+    }
+    const SaveHeader mine = header_of(c);
+    const bool same = h.nx == mine.nx && h.ny == mine.ny && h.prec == mine.prec && h.walls == mine.walls &&
+                      h.nmem == mine.nmem && h.nv == mine.nv && h.nlig == mine.nlig && h.nrec == mine.nrec &&
+                      h.nseg == mine.nseg && h.scale_exp == mine.scale_exp && h.tau == mine.tau &&
+                      h.gx == mine.gx && h.gy == mine.gy && h.uw_bot == mine.uw_bot && h.uw_top == mine.uw_top &&
+                      h.d_rep == mine.d_rep;
+    if (!same) {
+        std::fclose(fp);
+        return fail(c, LBIB_E_INVALID, "the saved state belongs to another set-up (lattice, precision, membranes, "
+                                       "receptors or parameters differ)");
+    }
+    // read everything before touching the context, so that a short file leaves it as it was
+    std::vector<StatePart> parts = state_parts(c);
+    std::vector<std::vector<char>> data(parts.size());
+    for (size_t k = 0; k < parts.size(); ++k) {
+        data[k].resize(parts[k].bytes);
+        if (parts[k].bytes && std::fread(data[k].data(), 1, parts[k].bytes, fp) != parts[k].bytes) {
+            std::fclose(fp);
+            return fail(c, LBIB_E_INVALID, "the saved state is truncated");
+        }
+    }
+    std::fclose(fp);
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < parts.size(); ++k)
+        if (parts[k].bytes)
+            CK(cudaMemcpyAsync(parts[k].dev, data[k].data(), parts[k].bytes, cudaMemcpyHostToDevice, c->stream));
+    // the per-step scratch back to its idle values: no spread force, no flagged
+    // tiles, no bond candidates, ruptures or claims, no status
+    const size_t N = (size_t)c->nx * c->ny;
+    for (int p = 0; p < 2; ++p) {
+        if (c->G[p]) CK(cudaMemsetAsync(c->G[p], 0, sizeof(longlong2) * N, c->stream));
+        if (c->flags[p]) CK(cudaMemsetAsync(c->flags[p], 0, 4 * (size_t)c->ntiles, c->stream));
+    }
+    CK(cudaMemsetAsync(c->tickets, 0, 16, c->stream));
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    if (c->nlig > 0) {
+        CK(cudaMemsetAsync(c->ma.cand, 0xFF, 4 * (size_t)c->nlig, c->stream));
+        CK(cudaMemsetAsync(c->ma.rupt, 0xFF, 4 * (size_t)c->nlig, c->stream));
+    }
+    if (c->ma.nrec > 0) CK(cudaMemsetAsync(c->ma.claim, 0x7F, 4 * (size_t)c->ma.nrec, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->steps = h.steps;
+    c->poisoned = false;
+    c->fields_valid = false;
+    return LBIB_OK;
+}

@@ -60,6 +60,8 @@ _SIGS = {
     "lbib_set_repulsion": (_I, [_P, _D]),
     "lbib_set_wall_velocity": (_I, [_P, _D, _D]),
     "lbib_membrane_observables": (_I, [_P, _DP]),
+    "lbib_save": (_I, [_P, ctypes.c_char_p]),
+    "lbib_load": (_I, [_P, ctypes.c_char_p]),
     "lbib_step": (_I, [_P, _I64]),
     "lbib_sync": (_I, [_P]),
     "lbib_step_count": (_I64, [_P]),
@@ -178,6 +180,14 @@ def lbib_set_repulsion(ctx, d_rep):
 
 def lbib_set_wall_velocity(ctx, u_bottom, u_top):
     _check(ctx, load().lbib_set_wall_velocity(ctx, float(u_bottom), float(u_top)))
+
+
+def lbib_save(ctx, path):
+    _check(ctx, load().lbib_save(ctx, os.fsencode(path)))
+
+
+def lbib_load(ctx, path):
+    _check(ctx, load().lbib_load(ctx, os.fsencode(path)))
 
 
 OBSERVABLES = ("x_c", "y_c", "u_c", "v_c", "region", "bonds", "y_min", "y_max")
@@ -503,6 +513,12 @@ class Simulation:
 
     def diagnostics(self):
         return lbib_diagnostics(self.ctx, len(self.mem_sizes))
+
+    def save(self, path):
+        lbib_save(self.ctx, path)
+
+    def load_state(self, path):
+        lbib_load(self.ctx, path)
 
     def observables(self):
         """per-membrane observables (lbib_membrane_observables), (nmem, 8)"""
