@@ -440,7 +440,15 @@ def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
             e1.record(stream)
             sim.sync()
             ms = e0.elapsed_time(e1)
+            # the fused kernel alone on this lattice (the three kernels timed
+            # back to back, lbib_profile_kernels): its share of the roofline
+            kms = lbib.lbib_profile_kernels(sim.ctx, 100)
         r["mlups"] = wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6
+        alg = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[prec] * wl.nx * wl.ny
+        r["fused_kernel"] = {"ms_per_launch": kms[1], "algorithmic_bytes": alg,
+                             "achieved_gbs": alg / (kms[1] * 1e-3) / 1e9,
+                             "frac_of_hbm": alg / (kms[1] * 1e-3) / 1e9 / peaks()[0]["hbm_gbs"],
+                             "note": "two buffers of this lattice partly fit in the 129 MB L2"}
         res[prec] = r
         sim.close()
     base = res["f32"]["mlups"]

@@ -371,9 +371,10 @@ lbib_status lbib_membrane_observables(lbib_ctx* ctx, double* out);
 lbib_status lbib_population_mass_noalloc(const double* f, int64_t n_nodes, double* mass, void* stream);
 
 /* Form and tile shape of the fused collide-stream kernel.  Must precede the
- * first step; 0,0 picks the default (for F32 and 16-bit storage the
- * persistent form when the two population buffers exceed 128 MB, else a
- * row-tile shape).
+ * first step; 0,0 picks the default: for F32 and 16-bit storage the
+ * persistent form when the two population buffers exceed 128 MB, for 16-bit
+ * storage also from 2^20 nodes on (segments of 512 nodes), else a row-tile
+ * shape.
  *  ty in 1..16: row tiles, vec consecutive x nodes per thread and ty rows per
  *    block; vec divides NX, with vec in {1,2} (F64), {1,2,4} (F32), {2,4,8}
  *    (16-bit storage).

@@ -87,15 +87,26 @@ void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
         *ty = 0;
         return;
     }
+    const long long nodes = (long long)c->nx * c->ny;
+    // 16-bit storage from a million nodes on: the row tiles' occupancy is capped
+    // by registers and they wait on their loads, while the persistent form's
+    // bulk copies keep the bytes in flight (512-node segments for L2-sized lattices)
+    const bool half = c->prec == LBIB_F32_STORE_F16 || c->prec == LBIB_F32_STORE_BF16;
+    if (half && nodes >= (1LL << 20) && valid_stream(c->prec, 2, c->nx)) {
+        *vec = 2;
+        *ty = 0;
+        return;
+    }
     int v = c->prec == LBIB_F64 ? 2 : 4;
     while (v > 1 && !valid_vec(c->prec, v, c->nx)) v /= 2;
     const long long N = (long long)c->nx * c->ny;
     // small lattices: fewer nodes per thread so that every SM has warps to switch between
     while (v > 1 && N / v < 152LL * 1024 && valid_vec(c->prec, v / 2, c->nx)) v /= 2;
     const long long tiles_x = (c->nx + 32LL * v - 1) / (32LL * v);
-    // large lattices: one row per block (most blocks in flight); small ones:
-    // up to 4 rows while the grid still fills the GPU several times over
-    int t = N >= (1LL << 20) ? 1 : 4;
+    // large lattices: two rows per block (one-warp blocks would hit the limit of
+    // 32 resident blocks per SM); small ones: up to 4 rows while the grid still
+    // fills the GPU several times over
+    int t = N >= (1LL << 20) ? 2 : 4;
     while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 8) t /= 2;
     // the grid's y extent (rows / t) is limited to 65535 blocks
     while (t < 16 && (c->ny + t - 1) / t > kMaxGridY) t *= 2;

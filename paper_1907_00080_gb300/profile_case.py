@@ -3,6 +3,7 @@
   python -m paper_1907_00080_gb300.profile_case --case probe --nx 8192 --ny 1024 --launches 3
   python -m paper_1907_00080_gb300.profile_case --case capillary --steps 40
   python -m paper_1907_00080_gb300.profile_case --case adjoint --steps 40 --checkpoint-every 20
+  python -m paper_1907_00080_gb300.profile_case --case fine --precision f16 --steps 20
 
 ``probe``: a channel of nx x ny nodes with soft circular carriers spread over
 it (the coarse capillary's share of nodes under a marker stencil), stepped twice, then ``--launches``
@@ -10,7 +11,8 @@ launches of the fused collide-stream kernel alone (``lbib_profile_fused``).
 ``capillary``: the 640 x 160 coarse capillary stepped ``--steps`` time steps
 (all kernels of the time step).  ``adjoint``: the 320 x 160 sensitivity case
 (FP64) recorded for ``--steps`` steps with checkpoints every
-``--checkpoint-every`` steps, then one backward sweep.  Prints one JSON line.
+``--checkpoint-every`` steps, then one backward sweep.  ``fine``: the 2000 x 667
+fine capillary stepped ``--steps`` time steps.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ def probe_workload(nx, ny, precision, n_carriers=None, seed=1):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--case", choices=["probe", "capillary", "adjoint"], default="probe")
+    p.add_argument("--case", choices=["probe", "capillary", "adjoint", "fine"], default="probe")
     p.add_argument("--nx", type=int, default=8192)
     p.add_argument("--ny", type=int, default=1024)
     p.add_argument("--precision", default="f32")
@@ -79,7 +81,10 @@ def main(argv=None):
         print(json.dumps(out))
         return 0
     else:
-        wl = inputs.coarse_capillary_640x160(args.precision)
+        if args.case == "fine":
+            wl = inputs.fine_capillary_2000x667(args.precision)
+        else:
+            wl = inputs.coarse_capillary_640x160(args.precision)
         sim = lbib.Simulation(wl, tiling=tiling)
         sim.step(args.steps)
         sim.sync()
