@@ -105,9 +105,9 @@ void default_tiling(const lbib_ctx* c, int* vec, int* ty) {
     const long long tiles_x = (c->nx + 32LL * v - 1) / (32LL * v);
     // large lattices: two rows per block (one-warp blocks would hit the limit of
     // 32 resident blocks per SM); small ones: up to 4 rows while the grid still
-    // fills the GPU several times over
+    // has four blocks per SM (the 640 x 160 capillary measured fastest at 4 rows)
     int t = N >= (1LL << 20) ? 2 : 4;
-    while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 8) t /= 2;
+    while (t > 1 && tiles_x * ((c->ny + t - 1) / t) < 152LL * 4) t /= 2;
     // the grid's y extent (rows / t) is limited to 65535 blocks
     while (t < 16 && (c->ny + t - 1) / t > kMaxGridY) t *= 2;
     *vec = v;
