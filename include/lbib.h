@@ -308,6 +308,39 @@ lbib_status lbib_adjoint_read(lbib_adjoint* adj, double* xy_bar, double* xy_prev
 int64_t lbib_adjoint_recorded_steps(const lbib_adjoint* adj);
 void lbib_adjoint_destroy(lbib_adjoint* adj);
 
+/* ---------------------------------------------------------------- x-slabs
+ * One lattice decomposed into x-slabs (the domain decomposition a multi-GPU
+ * run of a single lattice would use; here the slabs share one GPU).  Slab k
+ * is an ordinary context of width W_k + 2 on the same rows: its columns 1 ..
+ * W_k are the lattice's columns X_k .. X_k + W_k - 1 (X_0 = 0, X_{k+1} = X_k +
+ * W_k), and columns 0 and W_k + 1 are ghost columns.  After each step the
+ * ghost columns receive from the neighbouring slabs (a ring: x stays
+ * periodic) the post-collision populations that stream into the slab, so that
+ * every interior column evolves exactly as in the undivided lattice.  Ghost
+ * columns hold no meaningful populations of their own: read-backs and
+ * diagnostics of a slab include them, so use the interior columns only.
+ *
+ * lbib_slabs_create: 2 .. 16 contexts in order of x, with the same NY,
+ *   precision, walls, wall velocities, tau, body force and CUDA stream, no
+ *   membranes, all at the same step; the slabs object borrows them (destroy it
+ *   first).  Initialise each slab's populations with those of the lattice's
+ *   columns X_k - 1 .. X_k + W_k (periodic) before creating the object, or use
+ *   an x-uniform initial state.  Exchanges the ghost columns once.  (FP16
+ *   storage: each context picks its storage scale at creation from the body
+ *   force, whose y component counts the width; the slabs match the undivided
+ *   lattice bit for bit when their scale equals its scale, e.g. with a body
+ *   force along x.)
+ * lbib_slabs_step: n times, one step of every slab and the exchange (enqueued).
+ * lbib_slabs_sync: synchronise and report the slabs' device-side status.
+ * Errors: LBIB_E_INVALID (sizes, mismatched slabs, membranes), LBIB_E_STATE
+ * (slabs at different steps, a poisoned slab), LBIB_E_CUDA. */
+typedef struct lbib_slabs lbib_slabs;
+lbib_status lbib_slabs_create(lbib_ctx* const* slabs, int32_t n, lbib_slabs** out);
+lbib_status lbib_slabs_step(lbib_slabs* group, int64_t n);
+lbib_status lbib_slabs_sync(lbib_slabs* group);
+const char* lbib_slabs_last_error(const lbib_slabs* group);
+void lbib_slabs_destroy(lbib_slabs* group);
+
 /* Save and restore the full step state of a context (checkpoint / resume).
  * lbib_save writes to the file at `path`:
  *  - a header identifying the set-up;

@@ -11,6 +11,7 @@
 
 #include "lbib_internal.cuh"
 #include "adjoint.cuh"
+#include "slabs.cuh"
 #include "tangent.cuh"
 
 using namespace lbib;
@@ -1845,4 +1846,103 @@ extern "C" lbib_status lbib_load(lbib_ctx* c, const char* path) {
     c->poisoned = false;
     c->fields_valid = false;
     return LBIB_OK;
+}
+
+// ------------------------------------------------------------------ x-slabs
+// One lattice decomposed into x-slabs, each a context with two ghost columns
+// (slabs.cu); one step of the group steps every slab and exchanges the ghost
+// columns.
+struct lbib_slabs {
+    std::vector<lbib_ctx*> s;  // not owned
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+lbib_status slabs_fail(lbib_slabs* g, lbib_status st, const std::string& msg) {
+    if (g) g->err = msg;
+    return st;
+}
+
+cudaError_t slabs_exchange(lbib_slabs* g) {
+    SlabTable t{};
+    t.n = (int)g->s.size();
+    t.ny = g->s[0]->ny;
+    for (int k = 0; k < t.n; ++k) {
+        t.f[k] = g->s[k]->f[g->s[k]->cur];
+        t.width[k] = g->s[k]->nx;
+    }
+    return launch_halo_exchange(t, g->s[0]->pop_elem, g->stream);
+}
+
+}  // namespace
+
+extern "C" lbib_status lbib_slabs_create(lbib_ctx* const* slabs, int32_t n, lbib_slabs** out) {
+    if (!slabs || !out || n < 2 || n > kMaxSlabs) return LBIB_E_INVALID;
+    *out = nullptr;
+    lbib_ctx* c0 = slabs[0];
+    for (int k = 0; k < n; ++k) {
+        lbib_ctx* c = slabs[k];
+        if (!c) return LBIB_E_INVALID;
+        for (int j = 0; j < k; ++j)
+            if (slabs[j] == c) return fail(c, LBIB_E_INVALID, "a context appears twice among the slabs");
+        const bool same = c->ny == c0->ny && c->prec == c0->prec && c->walls == c0->walls && c->tau == c0->tau &&
+                          c->gx == c0->gx && c->gy == c0->gy && c->uw_bot == c0->uw_bot && c->uw_top == c0->uw_top &&
+                          c->scale_exp == c0->scale_exp && c->stream == c0->stream;
+        if (!same) return fail(c, LBIB_E_INVALID, "slabs need the same rows, precision, walls, tau, forcing and stream");
+        if (c->nmem > 0) return fail(c, LBIB_E_INVALID, "slabs carry the lattice only (no membranes)");
+        if (c->poisoned) return fail(c, LBIB_E_STATE, "a slab is poisoned by an earlier device-side failure");
+        if (c->cur != c0->cur || c->steps != c0->steps)
+            return fail(c, LBIB_E_STATE, "the slabs must be at the same step");
+        lbib_status st = finalize(c);
+        if (st == LBIB_OK) st = build_graphs(c);
+        if (st != LBIB_OK) return st;
+    }
+    lbib_slabs* g = new lbib_slabs();
+    g->s.assign(slabs, slabs + n);
+    g->stream = c0->stream;
+    cudaError_t e = slabs_exchange(g);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(c0, e, "slab halo exchange");
+    }
+    *out = g;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_slabs_step(lbib_slabs* g, int64_t n) {
+    if (!g || n < 0) return LBIB_E_INVALID;
+    for (lbib_ctx* c : g->s)
+        if (c->poisoned) return slabs_fail(g, LBIB_E_STATE, "a slab is poisoned by an earlier device-side failure");
+    for (int64_t k = 0; k < n; ++k) {
+        for (lbib_ctx* c : g->s) {
+            const cudaError_t e = cudaGraphLaunch(c->graph[c->cur][0], c->stream);
+            if (e != cudaSuccess) return slabs_fail(g, LBIB_E_CUDA, std::string("slab step: ") + cudaGetErrorString(e));
+            c->cur = 1 - c->cur;
+            c->steps += 1;
+            c->fields_valid = true;
+        }
+        const cudaError_t e = slabs_exchange(g);
+        if (e != cudaSuccess) return slabs_fail(g, LBIB_E_CUDA, std::string("halo exchange: ") + cudaGetErrorString(e));
+    }
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_slabs_sync(lbib_slabs* g) {
+    if (!g) return LBIB_E_INVALID;
+    for (lbib_ctx* c : g->s) {
+        const lbib_status st = lbib_sync(c);
+        if (st != LBIB_OK) return slabs_fail(g, st, c->err);
+    }
+    return LBIB_OK;
+}
+
+extern "C" const char* lbib_slabs_last_error(const lbib_slabs* g) { return g ? g->err.c_str() : "null slabs"; }
+
+extern "C" void lbib_slabs_destroy(lbib_slabs* g) {
+    if (!g) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    delete g;
 }

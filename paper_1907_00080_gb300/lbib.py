@@ -82,6 +82,11 @@ _SIGS = {
     "lbib_ensemble_member": (_P, [_P, _I32]),
     "lbib_ensemble_last_error": (ctypes.c_char_p, [_P]),
     "lbib_ensemble_destroy": (None, [_P]),
+    "lbib_slabs_create": (_I, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P)]),
+    "lbib_slabs_step": (_I, [_P, _I64]),
+    "lbib_slabs_sync": (_I, [_P]),
+    "lbib_slabs_last_error": (ctypes.c_char_p, [_P]),
+    "lbib_slabs_destroy": (None, [_P]),
     "lbib_tangent_create": (_I, [_P, ctypes.POINTER(_P)]),
     "lbib_tangent_seed": (_I, [_P, _DP, _DP, _D, _DP, _DP]),
     "lbib_tangent_step": (_I, [_P, _I64]),
@@ -350,6 +355,34 @@ def lbib_ensemble_destroy(ens):
         load().lbib_ensemble_destroy(ens)
 
 
+def lbib_slabs_create(ctxs):
+    arr = (_P * max(len(ctxs), 1))(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    out = _P()
+    st = load().lbib_slabs_create(arr, len(ctxs), ctypes.byref(out))
+    if st != LBIB_OK:
+        msg = load().lbib_last_error(ctxs[0]).decode() if ctxs else ""
+        raise LbibError(st, msg)
+    return out
+
+
+def _scheck(group, st):
+    if st != LBIB_OK:
+        raise LbibError(st, load().lbib_slabs_last_error(group).decode())
+
+
+def lbib_slabs_step(group, n):
+    _scheck(group, load().lbib_slabs_step(group, int(n)))
+
+
+def lbib_slabs_sync(group):
+    _scheck(group, load().lbib_slabs_sync(group))
+
+
+def lbib_slabs_destroy(group):
+    if group:
+        load().lbib_slabs_destroy(group)
+
+
 def lbib_tangent_create(ctx):
     out = _P()
     _check(ctx, load().lbib_tangent_create(ctx, ctypes.byref(out)))
@@ -555,6 +588,63 @@ class Ensemble:
             self.ens = None
             for m in self.members:
                 m.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Slabs:
+    """A lattice-only workload split into x-slabs of the given interior widths
+    (sum = NX), each a context with two ghost columns, advanced together with
+    the halo exchange (lbib_slabs_*) on one shared CUDA stream.  f0 (9, NY, NX),
+    optional, is the lattice's initial pre-collision state.  Marshalling only."""
+
+    def __init__(self, wl, widths, precision=None, tiling=None, f0=None):
+        import dataclasses
+
+        import torch
+        if wl.membranes:
+            raise ValueError("slabs carry the lattice only")
+        if sum(widths) != wl.nx:
+            raise ValueError("the slab widths must add up to NX")
+        self.widths = list(widths)
+        self.stream = torch.cuda.Stream()
+        self.sims = []
+        x0 = 0
+        for w in self.widths:
+            sub = dataclasses.replace(wl, nx=w + 2, name="%s_slab%d" % (wl.name, len(self.sims)))
+            sim = Simulation(sub, precision=precision, tiling=tiling, cuda_stream=self.stream.cuda_stream)
+            if f0 is not None:
+                cols = [(x0 - 1 + j) % wl.nx for j in range(w + 2)]
+                sim.set_populations(np.asarray(f0)[:, :, cols])
+            self.sims.append(sim)
+            x0 += w
+        self.group = lbib_slabs_create([s.ctx for s in self.sims])
+
+    def step(self, n=1):
+        lbib_slabs_step(self.group, n)
+
+    def sync(self):
+        lbib_slabs_sync(self.group)
+
+    def populations(self):
+        """(9, NY, NX): the interior columns of the slabs"""
+        return np.concatenate([s.populations()[:, :, 1:-1] for s in self.sims], axis=2)
+
+    def fields(self):
+        parts = [s.fields() for s in self.sims]
+        return tuple(np.concatenate([p[q][:, 1:-1] for p in parts], axis=1) for q in range(3))
+
+    def close(self):
+        if self.group:
+            lbib_slabs_destroy(self.group)
+            self.group = None
+        for s in self.sims:
+            s.close()
+        self.sims = []
 
     def __del__(self):
         try:
