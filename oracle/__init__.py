@@ -90,6 +90,22 @@ _SIGS = {
     "orc_ring_forces": (None, [_I, _DP, _DP, _DP, _DP, _D, _D, _D, _D, _D, _I, _DP, _DP]),
     "orc_p_form": (_D, [_P, _D]),
     "orc_p_rupture": (_D, [_P, _D]),
+    "orc_ring_mass_properties": (None, [_I, _DP, _DP, _DP, _DP, _DP, _DP]),
+    "orc_mls_shape": (None, [_P, _D, _D, _DP, _LP]),
+    "orc_mls_fit": (None, [_P, _D, _D, _DP, _DP]),
+    "orc_hydro_element_forces": (None, [_P, _I, _DP]),
+    "orc_compute_step_forces": (None, [_P]),
+    "orc_particle_advance": (None, [_P, _L]),
+    "orc_set_membrane_density": (None, [_P, _I, _D]),
+    "orc_membrane_mass": (_D, [_P, _I]),
+    "orc_membrane_inertia": (_D, [_P, _I]),
+    "orc_set_forces": (None, [_P, _DP]),
+    "orc_set_marker_velocity": (None, [_P, _DP]),
+    "orc_get_particle_velocity": (None, [_P, _DP]),
+    "orc_set_particle_velocity": (None, [_P, _DP]),
+    "orc_get_hydro_forces": (None, [_P, _DP]),
+    "orc_get_ib_forces": (None, [_P, _DP]),
+    "orc_get_rigid_state": (None, [_P, _I, _DP]),
     "orc_tangent_create": (_P, [_P]),
     "orc_tangent_destroy": (None, [_P]),
     "orc_tangent_seed": (None, [_P, _DP, _DP, _D, _DP, _DP, _DP]),
@@ -173,6 +189,15 @@ def ring_forces(xy, l0, th0, A0, ks, kb, ka, p_ref=1.0 / 3.0, which=7):
     lib().orc_ring_forces(n, _dp(x), _dp(y), _dp(_f64(l0)), _dp(_f64(th0)), A0, ks, kb, ka,
                           p_ref, which, _dp(fx), _dp(fy))
     return np.stack([fx, fy], axis=1)
+
+
+def ring_mass_properties(xy):
+    """(area, centroid relative to vertex 0, polar moment about the centroid)"""
+    xy = _f64(xy).reshape(-1, 2)
+    x, y = _f64(xy[:, 0]), _f64(xy[:, 1])
+    o = np.zeros(4)
+    lib().orc_ring_mass_properties(len(x), _dp(x), _dp(y), _dp(o[0:]), _dp(o[1:]), _dp(o[2:]), _dp(o[3:]))
+    return float(o[0]), (float(o[1]), float(o[2])), float(o[3])
 
 
 # ---------------------------------------------------------------- simulation
@@ -332,6 +357,69 @@ class OracleSim:
     def p_rupture(self, d):
         return lib().orc_p_rupture(self._s, float(d))
 
+    # dynamic particles (kinds 2 and 3)
+    def set_density(self, m, rho_p):
+        lib().orc_set_membrane_density(self._s, int(m), float(rho_p))
+
+    def mass_of(self, m):
+        return lib().orc_membrane_mass(self._s, int(m))
+
+    def inertia_of(self, m):
+        return lib().orc_membrane_inertia(self._s, int(m))
+
+    def mls_shape(self, x, y):
+        phi = np.zeros((3, 9))
+        idx = np.zeros(9, dtype=np.int64)
+        lib().orc_mls_shape(self._s, float(x), float(y), _dp(phi), idx.ctypes.data_as(_LP))
+        return phi, idx
+
+    def mls_fit(self, x, y, g):
+        g = _f64(g).reshape(self.ny, self.nx)
+        out = np.zeros(3)
+        lib().orc_mls_fit(self._s, float(x), float(y), _dp(g), _dp(out))
+        return out
+
+    def hydro_element_forces(self, m):
+        fe = np.zeros((self.mem_sizes[m], 2))
+        lib().orc_hydro_element_forces(self._s, int(m), _dp(fe))
+        return fe
+
+    def compute_step_forces(self):
+        lib().orc_compute_step_forces(self._s)
+
+    def particle_advance(self, step):
+        lib().orc_particle_advance(self._s, int(step))
+
+    def set_forces(self, fxy):
+        lib().orc_set_forces(self._s, _dp(_f64(fxy).reshape(-1, 2)))
+
+    def set_marker_velocity(self, uxy):
+        lib().orc_set_marker_velocity(self._s, _dp(_f64(uxy).reshape(-1, 2)))
+
+    def particle_velocity(self):
+        v = np.zeros((self.nv, 2))
+        lib().orc_get_particle_velocity(self._s, _dp(v))
+        return v
+
+    def set_particle_velocity(self, vxy):
+        lib().orc_set_particle_velocity(self._s, _dp(_f64(vxy).reshape(-1, 2)))
+
+    def hydro_forces(self):
+        f = np.zeros((self.nv, 2))
+        lib().orc_get_hydro_forces(self._s, _dp(f))
+        return f
+
+    def ib_forces(self):
+        f = np.zeros((self.nv, 2))
+        lib().orc_get_ib_forces(self._s, _dp(f))
+        return f
+
+    def rigid_state(self, m):
+        """(u, v, u_prev, v_prev, omega, omega_prev) of a rigid dynamic membrane"""
+        o = np.zeros(6)
+        lib().orc_get_rigid_state(self._s, int(m), _dp(o))
+        return o
+
     # IB primitives on this lattice
     def ib_weights(self, x, y):
         w = np.zeros(9)
@@ -368,7 +456,7 @@ class OracleTangent:
         self.sim = sim
         self._t = lib().orc_tangent_create(sim._s)
         if not self._t:
-            raise ValueError("the oracle tangent needs kinematic membranes only")
+            raise ValueError("the oracle tangent needs kinematic membranes only (kind 0)")
 
     def __del__(self):
         t = getattr(self, "_t", None)

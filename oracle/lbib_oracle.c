@@ -24,6 +24,10 @@
  *                                                        ForcingTerm; Sec. 3
  *   9. interpolation U_v = sum_j phi_v(x_j) u(x_j)     Sec. 2.3 (blood cells)
  *  10. kinematic marker advance (BDF2)                 Eq. kinematicPos
+ *      or, for dynamic particles, Newton's law under    Sec. 2.4: Eqs. hydroForP,
+ *      internal and hydrodynamic forces, with the         hydroForNu, newtonSoft,
+ *      fluid driven toward the particle velocity          verletPos, verletVel,
+ *                                                         linearVelRig, angularVelRig
  *  11. bond rupture then formation at X^{n+1}          Sec. 2.2 (wall-particle)
  *  12. diagnostics (mass, enclosed area)               Sec. 2.1, Eq. areaFor
  *
@@ -48,6 +52,12 @@
  *  - bond force is along ligand->receptor; bond kinetics are Dembo-type forward
  *    and reverse probabilities (the paper defers their form to a citation).
  *  - first step advances with forward Euler (BDF2 needs two past positions).
+ *  - dynamic particles: the fluid side of the coupling ("weak coupling",
+ *    Sec. 2.4) is direct forcing, F^ib = 2 dV (u_particle - U~) spread with
+ *    the IB shape functions; the stresses are evaluated on the flow at the
+ *    start of the step; viscous stress rho_0 nu (grad u + grad u^T); vertex
+ *    mass rho_P A_0 / n; rigid bodies turn about their area centroid; the
+ *    particles start at rest.
  *  - random numbers: Philox4x64-10 (Salmon et al., SC'11), counter
  *    (step, ligand, receptor, tag), key (seed, instance); u = (x0 >> 11) 2^-53.
  *
@@ -123,6 +133,14 @@ typedef struct {
     double d_rep, p_ref;
     double uw_bot, uw_top;     /* x velocities of the walls y = -1/2 and y = NY - 1/2 */
     long step;
+
+    /* dynamic particles (kinds 2 and 3, Sec. 2.4) */
+    double *mem_rhop;          /* particle density over fluid density        */
+    double *mem_J0;            /* polar second moment of area of the rest shape about its centroid */
+    double *mem_rb;            /* rigid state per membrane: u, v, u_prev, v_prev, omega, omega_prev */
+    double *vx, *vy;           /* particle velocity of each vertex, u_v^n    */
+    double *hx, *hy;           /* hydrodynamic force on each vertex, last step */
+    double *ibx, *iby;         /* force spread into the fluid for each dynamic vertex, last step */
 } orc_sim;
 
 /* ------------------------------------------------------------------------- */
@@ -461,6 +479,301 @@ void orc_ring_forces(int n, const double *x, const double *y, const double *l0,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Dynamic IB for particles (Sec. 2.4)                                        */
+/*                                                                           */
+/* Particles of kind 2 (deformable) and 3 (rigid) move by Newton's law        */
+/* under their internal forces and the hydrodynamic stresses of Eqs.          */
+/* hydroForP / hydroForNu, instead of with the fluid.  The fluid feels them   */
+/* through a forcing term that drives its velocity at the vertices toward the */
+/* particle's (the paper's "effective forcing term", read as direct forcing:  */
+/* Uhlmann, J. Comput. Phys. 209, 2005; with the MLS transfer of Vanella &    */
+/* Balaras, J. Comput. Phys. 228, 2009).                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Area, area centroid and polar second moment about the centroid of a closed
+ * CCW polygon, summed over the triangles (vertex 0, v, v+1): with a, b their
+ * corners relative to vertex 0 and c = a x b, the triangle has area c/2,
+ * centroid (a + b)/3 and polar moment c (|a|^2 + a.b + |b|^2) / 12 about
+ * vertex 0; the parallel-axis theorem moves the sum to the centroid.  The
+ * centroid is returned relative to vertex 0. */
+void orc_ring_mass_properties(int n, const double *x, const double *y, double *A, double *cx,
+                              double *cy, double *J) {
+    double s2 = 0.0, sx = 0.0, sy = 0.0, sj = 0.0;
+    for (int v = 0; v < n; ++v) {
+        int w = (v + 1) % n;
+        double ax = x[v] - x[0], ay = y[v] - y[0];
+        double bx = x[w] - x[0], by = y[w] - y[0];
+        double c = ax * by - ay * bx;
+        s2 += c;
+        sx += c * (ax + bx);
+        sy += c * (ay + by);
+        sj += c * ((ax * ax + ay * ay) + (ax * bx + ay * by) + (bx * bx + by * by));
+    }
+    double area = 0.5 * s2;
+    double gx = sx / (3.0 * s2), gy = sy / (3.0 * s2);
+    *A = area;
+    *cx = gx;
+    *cy = gy;
+    *J = sj / 12.0 - area * (gx * gx + gy * gy);
+}
+
+/* MLS fit at a point q (Sec. 2.2: the moving-least-squares transfer; the
+ * probe derivatives of Eqs. hydroForP / hydroForNu): over the 3x3 nodes
+ * nearest to q that lie in the fluid, with Roma weights W_j and the linear
+ * basis p_j = [1, x_j - q_x, y_j - q_y], A = sum_j W_j p_j p_j^T and a field g
+ * is fitted by a = A^{-1} sum_j W_j p_j g_j: a_0 is its value at q, a_1 and
+ * a_2 its x and y derivatives.  phi[r][k] = W_k (A^{-1} p_k)_r, so that
+ * a_r = sum_k phi[r][k] g(idx[k]).  When A is singular (q too far outside the
+ * fluid) the value falls back to the normalised weights and the gradient to
+ * zero. */
+void orc_mls_shape(const orc_sim *s, double qx, double qy, double phi[3][9], long idx[9]) {
+    long i0 = (long)floor(qx + 0.5), j0 = (long)floor(qy + 0.5);
+    double Wr[9], rx[9], ry[9];
+    for (int b = -1; b <= 1; ++b) {
+        for (int a = -1; a <= 1; ++a) {
+            int k = (b + 1) * 3 + (a + 1);
+            long i = i0 + a, j = j0 + b;
+            rx[k] = (double)i - qx;
+            ry[k] = (double)j - qy;
+            int inside = s->walls ? (j >= 0 && j < s->ny) : 1;
+            if (inside) {
+                Wr[k] = orc_roma(rx[k]) * orc_roma(ry[k]);
+                idx[k] = imod(j, s->ny) * s->nx + imod(i, s->nx);
+            } else {
+                Wr[k] = 0.0;
+                idx[k] = -1;
+            }
+        }
+    }
+    double A[3][3] = {{0}};
+    double sumW = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        double p[3] = {1.0, rx[k], ry[k]};
+        sumW += Wr[k];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) A[r][c] += Wr[k] * p[r] * p[c];
+    }
+    /* inverse by the adjugate (A is symmetric, so is its cofactor matrix) */
+    double cof[3][3];
+    cof[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    cof[0][1] = -(A[1][0] * A[2][2] - A[1][2] * A[2][0]);
+    cof[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    cof[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    cof[1][2] = -(A[0][0] * A[2][1] - A[0][1] * A[2][0]);
+    cof[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    cof[1][0] = cof[0][1];
+    cof[2][0] = cof[0][2];
+    cof[2][1] = cof[1][2];
+    double det = A[0][0] * cof[0][0] + A[0][1] * cof[0][1] + A[0][2] * cof[0][2];
+    for (int k = 0; k < 9; ++k) {
+        if (det > 1e-10) {
+            for (int r = 0; r < 3; ++r)
+                phi[r][k] = Wr[k] * (cof[r][0] + cof[r][1] * rx[k] + cof[r][2] * ry[k]) / det;
+        } else {
+            phi[0][k] = sumW > 0.0 ? Wr[k] / sumW : 0.0;
+            phi[1][k] = 0.0;
+            phi[2][k] = 0.0;
+        }
+    }
+}
+
+/* value and gradient of a node field at q by the MLS fit */
+void orc_mls_fit(const orc_sim *s, double qx, double qy, const double *g, double out[3]) {
+    double phi[3][9];
+    long idx[9];
+    orc_mls_shape(s, qx, qy, phi, idx);
+    for (int r = 0; r < 3; ++r) {
+        double a = 0.0;
+        for (int k = 0; k < 9; ++k)
+            if (idx[k] >= 0) a += phi[r][k] * g[idx[k]];
+        out[r] = a;
+    }
+}
+
+/* the flow seen by the particles at the start of a step: rho and
+ * u = (sum f e + G_body/2) / rho of the pre-collision populations f^n (the
+ * IB forces of the step are not yet known), and the pressure relative to
+ * the reference state, p = c_s^2 (rho - 1) with c_s^2 = 1/3 (Sec. 2.1) */
+static void flow_at(const orc_sim *s, long node, double *p, double *ux, double *uy) {
+    long N = (long)s->nx * s->ny;
+    double rho;
+    moments_at(s->f, N, node, s->gx, s->gy, &rho, ux, uy);
+    *p = (rho - 1.0) / 3.0;
+}
+
+/* Eqs. hydroForP and hydroForNu on every element l = (v, v+1) of membrane m:
+ * F_l = (-p n_l + tau . n_l) l_l with n_l the outward unit normal of the CCW
+ * element, p and the velocity gradient taken from the MLS fit at the probe
+ * point c_l + 1.2 n_l (c_l the element centroid), and the viscous stress
+ * tau = rho_0 nu (grad u + grad u^T), rho_0 = 1, nu = (tau_LB - 1/2) / 3.
+ * fe receives 2 n values (x, y per element). */
+void orc_hydro_element_forces(const orc_sim *s, int m, double *fe) {
+    int off = s->mem_off[m], n = s->mem_n[m];
+    double nu = (s->tau - 0.5) / 3.0;
+    for (int l = 0; l < n; ++l) {
+        int v = off + l, w = off + (l + 1) % n;
+        double ex = s->x[w] - s->x[v], ey = s->y[w] - s->y[v];
+        double len = sqrt(ex * ex + ey * ey);
+        double nx = ey / len, ny = -ex / len;
+        double qx = 0.5 * (s->x[v] + s->x[w]) + 1.2 * nx;
+        double qy = 0.5 * (s->y[v] + s->y[w]) + 1.2 * ny;
+        double phi[3][9];
+        long idx[9];
+        orc_mls_shape(s, qx, qy, phi, idx);
+        double p = 0.0, dux = 0.0, duy = 0.0, dvx = 0.0, dvy = 0.0;
+        for (int k = 0; k < 9; ++k) {
+            if (idx[k] < 0) continue;
+            double pk, uk, vk;
+            flow_at(s, idx[k], &pk, &uk, &vk);
+            p += phi[0][k] * pk;
+            dux += phi[1][k] * uk;
+            duy += phi[2][k] * uk;
+            dvx += phi[1][k] * vk;
+            dvy += phi[2][k] * vk;
+        }
+        double txx = 2.0 * nu * dux, tyy = 2.0 * nu * dvy, txy = nu * (duy + dvx);
+        fe[2 * l] = (-p * nx + (txx * nx + txy * ny)) * len;
+        fe[2 * l + 1] = (-p * ny + (txy * nx + tyy * ny)) * len;
+    }
+}
+
+static int is_dynamic(int kind) { return kind == 2 || kind == 3; }
+
+/* For every dynamic membrane at X^n: the hydrodynamic force on each vertex
+ * (half of each adjacent element's force, as the element forces of Eq. areaFor
+ * are shared) is added to its total force F_v of Eq. newtonSoft, and the
+ * force the vertex exerts on the fluid is
+ *   F^ib_v = 2 dV_v (u_v - U~_v),
+ * with u_v the particle velocity at the vertex, U~_v the interpolation of
+ * the flow at the start of the step (same shape functions as the
+ * kinematic markers), and dV_v = (l_L + l_R) / 2 the vertex's share of the
+ * contour times Delta x = 1.  With Guo forcing a node's velocity carries half
+ * the force it receives (rho u = sum f e + G/2, rho ~ 1): the factor 2 makes
+ * F^ib the force that would bring the local velocity to u_v in one step. */
+static void dynamic_coupling(orc_sim *s) {
+    for (int m = 0; m < s->nmem; ++m) {
+        if (!is_dynamic(s->mem_kind[m])) continue;
+        int off = s->mem_off[m], n = s->mem_n[m];
+        double *fe = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+        orc_hydro_element_forces(s, m, fe);
+        for (int k = 0; k < n; ++k) {
+            int v = off + k, L = off + (k + n - 1) % n, R = off + (k + 1) % n;
+            int kl = (k + n - 1) % n;
+            double hx = 0.5 * (fe[2 * kl] + fe[2 * k]);
+            double hy = 0.5 * (fe[2 * kl + 1] + fe[2 * k + 1]);
+            s->hx[v] = hx;
+            s->hy[v] = hy;
+            s->fx[v] += hx;
+            s->fy[v] += hy;
+            double w[9];
+            long idx[9];
+            orc_ib_weights(s, s->x[v], s->y[v], w, idx);
+            double Ux = 0.0, Uy = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                if (idx[q] < 0) continue;
+                double pq, uq, vq;
+                flow_at(s, idx[q], &pq, &uq, &vq);
+                Ux += w[q] * uq;
+                Uy += w[q] * vq;
+            }
+            double aLx = s->x[v] - s->x[L], aLy = s->y[v] - s->y[L];
+            double aRx = s->x[R] - s->x[v], aRy = s->y[R] - s->y[v];
+            double dV = 0.5 * (sqrt(aLx * aLx + aLy * aLy) + sqrt(aRx * aRx + aRy * aRy));
+            s->ibx[v] = 2.0 * dV * (s->vx[v] - Ux);
+            s->iby[v] = 2.0 * dV * (s->vy[v] - Uy);
+        }
+        free(fe);
+    }
+}
+
+/* Eqs. verletPos and verletVel for a deformable particle: each vertex moves
+ * by the interpolated fluid velocity U_v (the first tentative velocity) plus
+ * half its acceleration F_v / m_v, m_v = rho_P A_0 / n (the particle's mass
+ * spread evenly over its vertices); its velocity is the second-order backward
+ * difference 3/2 x^{n+1} - 2 x^n + 1/2 x^{n-1}, written as
+ * 3/2 (x^{n+1} - x^n) - 1/2 (x^n - x^{n-1}) (first-order on the first step). */
+static void soft_advance(orc_sim *s, int m, long step) {
+    int off = s->mem_off[m], n = s->mem_n[m];
+    double mv = s->mem_rhop[m] * s->mem_A0[m] / n;
+    for (int v = off; v < off + n; ++v) {
+        double xn = s->x[v] + (s->Ux[v] + 0.5 * s->fx[v] / mv);
+        double yn = s->y[v] + (s->Uy[v] + 0.5 * s->fy[v] / mv);
+        if (step == 0) {
+            s->vx[v] = xn - s->x[v];
+            s->vy[v] = yn - s->y[v];
+        } else {
+            s->vx[v] = 1.5 * (xn - s->x[v]) - 0.5 * (s->x[v] - s->xp[v]);
+            s->vy[v] = 1.5 * (yn - s->y[v]) - 0.5 * (s->y[v] - s->yp[v]);
+        }
+        s->xp[v] = s->x[v];
+        s->yp[v] = s->y[v];
+        s->x[v] = xn;
+        s->y[v] = yn;
+    }
+}
+
+/* Eqs. linearVelRig and angularVelRig for a rigid particle: the total force F
+ * and its moment M about the area centroid give du/dt = F/m and
+ * domega/dt = M/I (m = rho_P A_0, I = rho_P J_0); u and omega advance by the
+ * printed second-order form (forward Euler on the first step).  The body then
+ * translates by u Delta t and turns by omega Delta t about its centroid, and
+ * each vertex takes the rigid velocity u + omega x r.  cos(omega) - 1 is
+ * formed as -2 sin^2(omega/2) (no cancellation for small turns). */
+static void rigid_advance(orc_sim *s, int m, long step) {
+    int off = s->mem_off[m], n = s->mem_n[m];
+    double A, cx, cy, J;
+    orc_ring_mass_properties(n, s->x + off, s->y + off, &A, &cx, &cy, &J);
+    double x0 = s->x[off], y0 = s->y[off];
+    double Fx = 0.0, Fy = 0.0, M = 0.0;
+    for (int v = off; v < off + n; ++v) {
+        double rx = (s->x[v] - x0) - cx, ry = (s->y[v] - y0) - cy;
+        Fx += s->fx[v];
+        Fy += s->fy[v];
+        M += rx * s->fy[v] - ry * s->fx[v];
+    }
+    double mass = s->mem_rhop[m] * s->mem_A0[m], inertia = s->mem_rhop[m] * s->mem_J0[m];
+    double ax = Fx / mass, ay = Fy / mass, al = M / inertia;
+    double *rb = s->mem_rb + 6 * m;
+    double un, vn, wn;
+    if (step == 0) {
+        un = rb[0] + ax;
+        vn = rb[1] + ay;
+        wn = rb[4] + al;
+    } else {
+        un = (2.0 / 3.0) * (2.0 * rb[0] - 0.5 * rb[2] + ax);
+        vn = (2.0 / 3.0) * (2.0 * rb[1] - 0.5 * rb[3] + ay);
+        wn = (2.0 / 3.0) * (2.0 * rb[4] - 0.5 * rb[5] + al);
+    }
+    rb[2] = rb[0]; rb[3] = rb[1]; rb[5] = rb[4];
+    rb[0] = un; rb[1] = vn; rb[4] = wn;
+    double h = sin(0.5 * wn);
+    double c1 = -2.0 * h * h, sn = sin(wn);
+    for (int v = off; v < off + n; ++v) {
+        double rx = (s->x[v] - x0) - cx, ry = (s->y[v] - y0) - cy;
+        double drx = c1 * rx - sn * ry, dry = sn * rx + c1 * ry;
+        s->vx[v] = un - wn * (ry + dry);
+        s->vy[v] = vn + wn * (rx + drx);
+        s->xp[v] = s->x[v];
+        s->yp[v] = s->y[v];
+        s->x[v] = s->x[v] + (un + drx);
+        s->y[v] = s->y[v] + (vn + dry);
+    }
+}
+
+/* advance of every dynamic membrane from the total forces F_v and the
+ * interpolated velocities U_v held in the state (step 10 for kinds 2, 3) */
+void orc_particle_advance(orc_sim *s, long step) {
+    for (int m = 0; m < s->nmem; ++m) {
+        if (s->mem_kind[m] == 2) soft_advance(s, m, step);
+        else if (s->mem_kind[m] == 3) rigid_advance(s, m, step);
+    }
+}
+
+void orc_set_membrane_density(orc_sim *s, int m, double rho_p) { s->mem_rhop[m] = rho_p; }
+double orc_membrane_inertia(const orc_sim *s, int m) { return s->mem_rhop[m] * s->mem_J0[m]; }
+double orc_membrane_mass(const orc_sim *s, int m) { return s->mem_rhop[m] * s->mem_A0[m]; }
+
+/* ------------------------------------------------------------------------- */
 /* Simulation object                                                          */
 /* ------------------------------------------------------------------------- */
 
@@ -492,6 +805,8 @@ void orc_destroy(orc_sim *s) {
     free(s->x); free(s->y); free(s->xp); free(s->yp); free(s->fx); free(s->fy);
     free(s->l0); free(s->th0); free(s->wgt); free(s->widx); free(s->Ux); free(s->Uy);
     free(s->lig_elem); free(s->rx); free(s->ry); free(s->bond_of_lig); free(s->owner_of_rec);
+    free(s->mem_rhop); free(s->mem_J0); free(s->mem_rb);
+    free(s->vx); free(s->vy); free(s->hx); free(s->hy); free(s->ibx); free(s->iby);
     free(s);
 }
 
@@ -560,7 +875,9 @@ static void *grow(void *p, size_t n, size_t sz) { return realloc(p, n * sz); }
 
 /* add a closed CCW ring of n vertices, rest shape = given positions.
  * kind 0: kinematic (Eq. kinematicPos); kind 1: velocities projected on a rigid
- * motion before the advance. ligand_elems are local element ids. */
+ * motion before the advance; kind 2: dynamic deformable particle (Eqs.
+ * newtonSoft, verletPos, verletVel); kind 3: dynamic rigid particle (Eqs.
+ * linearVelRig, angularVelRig). ligand_elems are local element ids. */
 int orc_add_membrane(orc_sim *s, const double *xy, int n, double ks, double kb, double ka,
                      int kind, const int *ligand_elems, int nlig) {
     int m = s->nmem++;
@@ -581,6 +898,12 @@ int orc_add_membrane(orc_sim *s, const double *xy, int n, double ks, double kb, 
     s->Ux = grow(s->Ux, nv, sizeof(double)); s->Uy = grow(s->Uy, nv, sizeof(double));
     s->wgt = grow(s->wgt, (size_t)nv * 9, sizeof(double));
     s->widx = grow(s->widx, (size_t)nv * 9, sizeof(long));
+    s->mem_rhop = grow(s->mem_rhop, s->nmem, sizeof(double));
+    s->mem_J0 = grow(s->mem_J0, s->nmem, sizeof(double));
+    s->mem_rb = grow(s->mem_rb, (size_t)s->nmem * 6, sizeof(double));
+    s->vx = grow(s->vx, nv, sizeof(double)); s->vy = grow(s->vy, nv, sizeof(double));
+    s->hx = grow(s->hx, nv, sizeof(double)); s->hy = grow(s->hy, nv, sizeof(double));
+    s->ibx = grow(s->ibx, nv, sizeof(double)); s->iby = grow(s->iby, nv, sizeof(double));
     s->mem_off[m] = off; s->mem_n[m] = n; s->mem_kind[m] = kind;
     s->mem_ks[m] = ks; s->mem_kb[m] = kb; s->mem_ka[m] = ka;
     for (int v = 0; v < n; ++v) {
@@ -590,9 +913,18 @@ int orc_add_membrane(orc_sim *s, const double *xy, int n, double ks, double kb, 
         s->yp[off + v] = xy[2 * v + 1];
         s->fx[off + v] = 0.0; s->fy[off + v] = 0.0;
         s->Ux[off + v] = 0.0; s->Uy[off + v] = 0.0;
+        s->vx[off + v] = 0.0; s->vy[off + v] = 0.0;  /* particles start at rest (Sec. 3) */
+        s->hx[off + v] = 0.0; s->hy[off + v] = 0.0;
+        s->ibx[off + v] = 0.0; s->iby[off + v] = 0.0;
         s->vert_mem[off + v] = m;
     }
     orc_ring_rest(n, s->x + off, s->y + off, s->l0 + off, s->th0 + off, &s->mem_A0[m]);
+    for (int k = 0; k < 6; ++k) s->mem_rb[6 * m + k] = 0.0;
+    {
+        double A, cx, cy;
+        orc_ring_mass_properties(n, s->x + off, s->y + off, &A, &cx, &cy, &s->mem_J0[m]);
+    }
+    s->mem_rhop[m] = 1.1;  /* rho_P / rho = 1.1 (Sec. 3) */
     s->nv = nv;
     if (nlig > 0) {
         s->lig_elem = grow(s->lig_elem, s->nlig + nlig, sizeof(int));
@@ -747,22 +1079,33 @@ void orc_bonds_update(orc_sim *s, long step) {
     free(claimed);
 }
 
+/* steps 1-5 and, for dynamic membranes, their hydrodynamic forces and the
+ * forces they exert on the fluid */
+void orc_compute_step_forces(orc_sim *s) {
+    orc_compute_forces(s);
+    dynamic_coupling(s);
+}
+
 /* one full step n -> n+1 */
 static void step_once(orc_sim *s) {
     long N = (long)s->nx * s->ny;
     int nv = s->nv;
-    orc_compute_forces(s);
+    orc_compute_step_forces(s);
     /* 6. weights at X^n */
     for (int v = 0; v < nv; ++v) orc_ib_weights(s, s->x[v], s->y[v], s->wgt + 9 * v, s->widx + 9 * v);
-    /* 7. spread */
+    /* 7. spread: the membrane forces of kinematic membranes, the forcing
+     * term F^ib of dynamic ones */
     for (long n = 0; n < N; ++n) { s->Gx[n] = s->gx; s->Gy[n] = s->gy; }
-    for (int v = 0; v < nv; ++v)
+    for (int v = 0; v < nv; ++v) {
+        int dyn = is_dynamic(s->mem_kind[s->vert_mem[v]]);
+        double Fx = dyn ? s->ibx[v] : s->fx[v], Fy = dyn ? s->iby[v] : s->fy[v];
         for (int k = 0; k < 9; ++k) {
             long j = s->widx[9 * v + k];
             if (j < 0) continue;
-            s->Gx[j] += s->wgt[9 * v + k] * s->fx[v];
-            s->Gy[j] += s->wgt[9 * v + k] * s->fy[v];
+            s->Gx[j] += s->wgt[9 * v + k] * Fx;
+            s->Gy[j] += s->wgt[9 * v + k] * Fy;
         }
+    }
     /* 8. collide + stream */
     collide_and_stream(s);
     /* 9. interpolate u^n at X^n */
@@ -777,9 +1120,11 @@ static void step_once(orc_sim *s) {
         s->Ux[v] = a;
         s->Uy[v] = b;
     }
-    /* 10. advance (rigid projection first for kind 1) */
+    /* 10. advance (rigid projection first for kind 1; Newton for kinds 2, 3) */
+    orc_particle_advance(s, s->step);
     for (int m = 0; m < s->nmem; ++m) {
         int off = s->mem_off[m], n = s->mem_n[m];
+        if (is_dynamic(s->mem_kind[m])) continue;
         if (s->mem_kind[m] == 1) {
             double xc = 0, yc = 0, uc = 0, vc = 0;
             for (int v = off; v < off + n; ++v) { xc += s->x[v]; yc += s->y[v]; uc += s->Ux[v]; vc += s->Uy[v]; }
@@ -840,6 +1185,27 @@ void orc_get_forces(const orc_sim *s, double *fxy) {
 }
 void orc_get_marker_velocity(const orc_sim *s, double *uxy) {
     for (int v = 0; v < s->nv; ++v) { uxy[2 * v] = s->Ux[v]; uxy[2 * v + 1] = s->Uy[v]; }
+}
+void orc_set_forces(orc_sim *s, const double *fxy) {
+    for (int v = 0; v < s->nv; ++v) { s->fx[v] = fxy[2 * v]; s->fy[v] = fxy[2 * v + 1]; }
+}
+void orc_set_marker_velocity(orc_sim *s, const double *uxy) {
+    for (int v = 0; v < s->nv; ++v) { s->Ux[v] = uxy[2 * v]; s->Uy[v] = uxy[2 * v + 1]; }
+}
+void orc_get_particle_velocity(const orc_sim *s, double *vxy) {
+    for (int v = 0; v < s->nv; ++v) { vxy[2 * v] = s->vx[v]; vxy[2 * v + 1] = s->vy[v]; }
+}
+void orc_set_particle_velocity(orc_sim *s, const double *vxy) {
+    for (int v = 0; v < s->nv; ++v) { s->vx[v] = vxy[2 * v]; s->vy[v] = vxy[2 * v + 1]; }
+}
+void orc_get_hydro_forces(const orc_sim *s, double *fxy) {
+    for (int v = 0; v < s->nv; ++v) { fxy[2 * v] = s->hx[v]; fxy[2 * v + 1] = s->hy[v]; }
+}
+void orc_get_ib_forces(const orc_sim *s, double *fxy) {
+    for (int v = 0; v < s->nv; ++v) { fxy[2 * v] = s->ibx[v]; fxy[2 * v + 1] = s->iby[v]; }
+}
+void orc_get_rigid_state(const orc_sim *s, int m, double *out) {
+    for (int k = 0; k < 6; ++k) out[k] = s->mem_rb[6 * m + k];
 }
 void orc_get_bonds(const orc_sim *s, int *bond_of_lig) {
     for (int l = 0; l < s->nlig; ++l) bond_of_lig[l] = s->bond_of_lig[l];
@@ -1194,7 +1560,7 @@ static void t_step_once(orc_tangent *t) {
 /* Tangent object.  Returns NULL if a membrane is rigid-projected. */
 orc_tangent *orc_tangent_create(orc_sim *s) {
     for (int m = 0; m < s->nmem; ++m)
-        if (s->mem_kind[m] == 1) return NULL;
+        if (s->mem_kind[m] != 0) return NULL;
     orc_tangent *t = (orc_tangent *)calloc(1, sizeof(orc_tangent));
     long N = (long)s->nx * s->ny;
     int nv = s->nv > 0 ? s->nv : 1, nm = s->nmem > 0 ? s->nmem : 1;
