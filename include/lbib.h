@@ -80,8 +80,12 @@ typedef enum {
 
 typedef enum {
     LBIB_MEMBRANE_KINEMATIC = 0,       /* Eq. kinematicPos with the interpolated velocity */
-    LBIB_MEMBRANE_RIGID_PROJECTED = 1  /* same, velocity first projected on the
+    LBIB_MEMBRANE_RIGID_PROJECTED = 1, /* same, velocity first projected on the
                                           least-squares rigid motion of the ring  */
+    LBIB_MEMBRANE_DYNAMIC = 2,         /* dynamic IB, deformable particle (Sec. 2.4):
+                                          Eqs. newtonSoft, verletPos, verletVel  */
+    LBIB_MEMBRANE_DYNAMIC_RIGID = 3    /* dynamic IB, rigid particle (Sec. 2.4):
+                                          Eqs. linearVelRig, angularVelRig      */
 } lbib_kind;
 
 typedef struct {
@@ -124,6 +128,39 @@ lbib_status lbib_create(const lbib_lattice* lattice, double tau, const double bo
 lbib_status lbib_add_membrane(lbib_ctx* ctx, const double* xy, int32_t n, double k_s, double k_b,
                               double k_area, lbib_kind kind, const int32_t* ligand_elems,
                               int32_t n_ligands, int32_t* membrane_id_out);
+
+/* Dynamic particles (kinds LBIB_MEMBRANE_DYNAMIC and LBIB_MEMBRANE_DYNAMIC_RIGID,
+ * Sec. 2.4).  Per step, at X^n, from the populations f^n at the start of the
+ * step (rho, u = (sum f e + G_body/2)/rho, p = (rho - 1)/3):
+ *  - Eqs. hydroForP / hydroForNu on each element: (-p n + tau.n) l, with n the
+ *    outward normal, p and grad u fitted by MLS (linear basis, Roma weights,
+ *    3x3 nearest nodes in the fluid) at the probe c + 1.2 n, tau =
+ *    nu (grad u + grad u^T), nu = (tau_LB - 1/2)/3; half to each end vertex;
+ *  - the total vertex force is the membrane force plus this hydrodynamic force;
+ *  - the fluid receives, instead of the membrane forces, the forcing term
+ *    2 dV (u_p - U~) per vertex (direct forcing: u_p the particle velocity at
+ *    the vertex, U~ the interpolated flow, dV half the two adjacent element
+ *    lengths), spread with the IB shape functions.
+ * After the collision the deformable particle moves each vertex by the
+ * interpolated velocity plus F / (2 m_v) (m_v = rho_P A_0 / n) and takes the
+ * second-order backward-difference velocity; the rigid one advances its
+ * velocity and spin by the printed second-order update of F/m and M/I (m =
+ * rho_P A_0, I = rho_P J_0 about the area centroid), translates and turns about
+ * its area centroid.  Particles start at rest.  A dynamic membrane has at most
+ * 256 vertices.  The tangent, the adjoint and the slab decomposition refuse
+ * contexts that hold one. */
+
+/* Particle density over fluid density rho_P / rho of a dynamic membrane
+ * (default 1.1, Sec. 3).  Must precede the first lbib_step.
+ * Errors: LBIB_E_INVALID (not a dynamic membrane, rho_ratio <= 0 or not
+ * finite), LBIB_E_STATE (after the first step). */
+lbib_status lbib_set_particle_density(lbib_ctx* ctx, int32_t membrane_id, double rho_ratio);
+
+/* Particle velocity u_p^n of each vertex of one dynamic membrane (2 doubles
+ * per vertex, host memory): the backward-difference velocity of a deformable
+ * particle, u + omega x r of a rigid one; zero before the first step.
+ * Errors: LBIB_E_INVALID (not a dynamic membrane), LBIB_E_STATE (not finalised). */
+lbib_status lbib_read_particle_velocity(lbib_ctx* ctx, int32_t membrane_id, double* uv);
 
 /* Receptors: xy holds 2n doubles (fixed positions, typically one per wall
  * node at y = -1/2 or NY - 1/2).  Replaces any earlier set; all bonds are

@@ -1,9 +1,10 @@
 // Interpolation, kinematic advance and bond kinetics in one kernel.
 //
 // One block of a.adv_threads (<= kAdvThreads) threads per unit: a chunk of up to kChunkV vertices
-// of a kinematic membrane, or a whole rigid-projected membrane (one vertex per
-// thread) (its velocities are first
-// projected on their least-squares rigid motion).  Per vertex: interpolate
+// of a kinematic membrane or a deformable dynamic particle, or a whole
+// rigid-projected membrane or rigid dynamic particle (one vertex per thread;
+// the velocities of the former are first projected on their least-squares
+// rigid motion, the latter follows Newton-Euler).  Per vertex: interpolate
 // u^n (Sec. 2.3), advance with Eq. kinematicPos (BDF2; forward Euler on the
 // first step), refresh the repulsion boxes.  Then the ligands whose element
 // lies inside the unit are decided at X^{n+1} (bond_logic.cuh); the last
@@ -47,6 +48,47 @@ __device__ __forceinline__ void load_pos_cg<float>(const void* X, int v, ff& x, 
     y = ff{q.y, q.w};
 }
 
+// Eqs. verletPos / verletVel of a deformable dynamic particle: the vertex moves
+// by the interpolated velocity (the first tentative velocity) plus F / (2 m_v)
+// (F the total force of this step, m_v = rho_P A_0 / n); its velocity is the
+// backward difference 3/2 (x^{n+1} - x^n) - 1/2 (x^n - x^{n-1}) (first-order on
+// the first step)
+template <typename C>
+__device__ __forceinline__ void verlet(const MarkerArgs& a, int m, int v, typename Ext<C>::E x,
+                                       typename Ext<C>::E y, typename Ext<C>::E xp, typename Ext<C>::E yp,
+                                       C Ux, C Uy, long long step, typename Ext<C>::E& xn,
+                                       typename Ext<C>::E& yn) {
+    const C* F = static_cast<const C*>(a.F);
+    C* V = static_cast<C*>(a.V);
+    const C mv = C(a.mem_dyn[3 * m + 2]);
+    xn = eaddc(x, Ux + (C(0.5) * F[2 * (size_t)v]) / mv);
+    yn = eaddc(y, Uy + (C(0.5) * F[2 * (size_t)v + 1]) / mv);
+    if (step == 0) {
+        V[2 * (size_t)v] = etoc(esub(xn, x));
+        V[2 * (size_t)v + 1] = etoc(esub(yn, y));
+    } else {
+        V[2 * (size_t)v] = C(1.5) * etoc(esub(xn, x)) - C(0.5) * etoc(esub(x, xp));
+        V[2 * (size_t)v + 1] = C(1.5) * etoc(esub(yn, y)) - C(0.5) * etoc(esub(y, yp));
+    }
+}
+
+// repulsion boxes of a whole ring whose new positions are in shared memory:
+// kSegV lanes per segment
+template <typename C>
+__device__ __forceinline__ void ring_boxes(const MarkerArgs& a, int m, int n, int tid, int lane,
+                                           const typename Ext<C>::E* s_x, const typename Ext<C>::E* s_y) {
+    const int per_pass = blockDim.x / kSegV;
+    const int s0 = a.mem_seg_off[m], s1 = a.mem_seg_off[m + 1];
+    for (int base = 0; base < s1 - s0; base += per_pass) {
+        const int si = base + tid / kSegV;
+        const int kfirst = si * kSegV;
+        const int g = tid & (kSegV - 1);
+        const bool ok = si < s1 - s0;
+        const int kk = ok ? (kfirst + g < n ? kfirst + g : kfirst) : 0;
+        seg_box_regs<C>(a, ok ? s0 + si : -1, lane, s_x[kk], s_y[kk]);
+    }
+}
+
 template <typename C>
 __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     using E = typename Ext<C>::E;
@@ -70,8 +112,8 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         my_bond = a.bond_of_lig[my_rec.x];
     }
 
-    if (kind != LBIB_MEMBRANE_RIGID_PROJECTED) {
-        // ---- kinematic chunk: one vertex per thread
+    if (kind == LBIB_MEMBRANE_KINEMATIC || kind == LBIB_MEMBRANE_DYNAMIC) {
+        // ---- kinematic or deformable dynamic chunk: one vertex per thread
         const bool valid = tid < kn;
         const int v = off + k0 + (valid ? tid : 0);
         E x, y, xp, yp, xn, yn;
@@ -82,8 +124,12 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
             interp_vertex<C>(a, v, Ux, Uy);
             U[2 * v] = Ux;
             U[2 * v + 1] = Uy;
-            bdf2<C>(x, xp, Ux, step, xn);
-            bdf2<C>(y, yp, Uy, step, yn);
+            if (kind == LBIB_MEMBRANE_DYNAMIC) {
+                verlet<C>(a, m, v, x, y, xp, yp, Ux, Uy, step, xn, yn);
+            } else {
+                bdf2<C>(x, xp, Ux, step, xn);
+                bdf2<C>(y, yp, Uy, step, yn);
+            }
             if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
             PosIO<C>::store(a.Xp, v, x, y);
             PosIO<C>::store(a.X, v, xn, yn);
@@ -100,6 +146,80 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         shfl_e(gx, xn, lane & ~(kSegV - 1));
         shfl_e(gy, yn, lane & ~(kSegV - 1));
         seg_box_regs<C>(a, sg, lane, valid ? xn : gx, valid ? yn : gy);
+    } else if (kind == LBIB_MEMBRANE_DYNAMIC_RIGID) {
+        // ---- rigid dynamic particle, the whole ring in this block: Eqs.
+        // linearVelRig / angularVelRig.  F and its moment M about the area
+        // centroid give du/dt = F/m, domega/dt = M/I; the body translates by u
+        // and turns by omega about its centroid (cos omega - 1 = -2 sin^2(omega/2))
+        E xr, yr;
+        load_pos<C>(a, off, xr, yr);
+        const int k = tid;
+        const bool valid = k < n;
+        const C* F = static_cast<const C*>(a.F);
+        E x, y;
+        C Ux = 0, Uy = 0, ax = 0, ay = 0, bx = 0, by = 0, fx = 0, fy = 0;
+        if (valid) {
+            E xq, yq;
+            load_pos<C>(a, off + k, x, y);
+            load_pos<C>(a, off + (k + 1 == n ? 0 : k + 1), xq, yq);
+            interp_vertex<C>(a, off + k, Ux, Uy);
+            ax = etoc(esub(x, xr));
+            ay = etoc(esub(y, yr));
+            bx = etoc(esub(xq, xr));
+            by = etoc(esub(yq, yr));
+            fx = F[2 * (size_t)(off + k)];
+            fy = F[2 * (size_t)(off + k) + 1];
+        }
+        // area centroid relative to vertex 0 from the triangles (vertex 0, k, k+1)
+        const C cr = ax * by - ay * bx;
+        C s2 = cr, gsx = cr * (ax + bx), gsy = cr * (ay + by), z0 = 0;
+        block_sum4_c<C>(s2, gsx, gsy, z0, cred);
+        const C gx = gsx / (C(3) * s2), gy = gsy / (C(3) * s2);
+        const C rx = ax - gx, ry = ay - gy;
+        // the rigid state is read by every thread before thread 0 rewrites it
+        double* rb = a.rb + 6 * m;
+        const double u0 = rb[0], v0 = rb[1], up = rb[2], vp = rb[3], w0 = rb[4], wp = rb[5];
+        C Fx = fx, Fy = fy, Mz = valid ? rx * fy - ry * fx : C(0), z1 = 0;
+        block_sum4_c<C>(Fx, Fy, Mz, z1, cred);
+        const double mass = a.mem_dyn[3 * m], inertia = a.mem_dyn[3 * m + 1];
+        const double axd = double(Fx) / mass, ayd = double(Fy) / mass, ald = double(Mz) / inertia;
+        double un, vn, wn;
+        if (step == 0) {
+            un = u0 + axd;
+            vn = v0 + ayd;
+            wn = w0 + ald;
+        } else {
+            un = (2.0 / 3.0) * (2.0 * u0 - 0.5 * up + axd);
+            vn = (2.0 / 3.0) * (2.0 * v0 - 0.5 * vp + ayd);
+            wn = (2.0 / 3.0) * (2.0 * w0 - 0.5 * wp + ald);
+        }
+        if (tid == 0) {
+            rb[2] = u0;
+            rb[3] = v0;
+            rb[5] = w0;
+            rb[0] = un;
+            rb[1] = vn;
+            rb[4] = wn;
+        }
+        const C hs = sin(C(0.5) * C(wn));
+        const C c1 = C(-2) * hs * hs, sn = sin(C(wn));
+        if (valid) {
+            const int v = off + k;
+            const C drx = c1 * rx - sn * ry, dry = sn * rx + c1 * ry;
+            C* V = static_cast<C*>(a.V);
+            V[2 * (size_t)v] = C(un) - C(wn) * (ry + dry);
+            V[2 * (size_t)v + 1] = C(vn) + C(wn) * (rx + drx);
+            U[2 * v] = Ux;
+            U[2 * v + 1] = Uy;
+            const E xn = eaddc(x, C(un) + drx), yn = eaddc(y, C(vn) + dry);
+            if (!isfinite(ehi(xn)) || !isfinite(ehi(yn))) atomicOr(a.status, ST_NONFINITE);
+            PosIO<C>::store(a.Xp, v, x, y);
+            PosIO<C>::store(a.X, v, xn, yn);
+            s_x[k] = xn;
+            s_y[k] = yn;
+        }
+        __syncthreads();
+        ring_boxes<C>(a, m, n, tid, lane, s_x, s_y);
     } else {
         // ---- rigid-projected membrane: the whole ring in this block
         E xr, yr;
@@ -147,17 +267,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
             s_y[k] = yn;
         }
         __syncthreads();
-        // repulsion boxes: kSegV lanes per segment
-        const int per_pass = blockDim.x / kSegV;
-        const int s0 = a.mem_seg_off[m], s1 = a.mem_seg_off[m + 1];
-        for (int base = 0; base < s1 - s0; base += per_pass) {
-            const int si = base + tid / kSegV;
-            const int kfirst = si * kSegV;
-            const int g = tid & (kSegV - 1);
-            const bool ok = si < s1 - s0;
-            const int kk = ok ? (kfirst + g < n ? kfirst + g : kfirst) : 0;
-            seg_box_regs<C>(a, ok ? s0 + si : -1, lane, s_x[kk], s_y[kk]);
-        }
+        ring_boxes<C>(a, m, n, tid, lane, s_x, s_y);
     }
     __syncthreads();
 

@@ -45,6 +45,36 @@ size_t elem_size(lbib_precision p) {
     }
 }
 
+bool is_dynamic(int kind) { return kind == LBIB_MEMBRANE_DYNAMIC || kind == LBIB_MEMBRANE_DYNAMIC_RIGID; }
+// membranes advanced by one block over the whole ring (their sums span it)
+bool whole_ring(int kind) { return kind == LBIB_MEMBRANE_RIGID_PROJECTED || kind == LBIB_MEMBRANE_DYNAMIC_RIGID; }
+
+// Area A_0 and polar second moment J_0 about the area centroid of a rest
+// polygon (CCW, xy interleaved), summed over the triangles (vertex 0, v, v+1):
+// with a, b their corners relative to vertex 0 and c = a x b, the triangle has
+// area c/2, centroid (a + b)/3 and polar moment c (|a|^2 + a.b + |b|^2)/12
+// about vertex 0; the parallel-axis theorem moves the sum to the centroid.
+// A_0 is the shoelace sum about vertex 0 the rest of the library uses.
+void rest_mass_properties(int n, const double* xy, double* A0, double* J0) {
+    double sa = 0.0, s2 = 0.0, sx = 0.0, sy = 0.0, sj = 0.0;
+    const double xr = xy[0], yr = xy[1];
+    for (int v = 0; v < n; ++v) {
+        const int w = (v + 1) % n;
+        const double ax = xy[2 * v] - xr, ay = xy[2 * v + 1] - yr;
+        const double bx = xy[2 * w] - xr, by = xy[2 * w + 1] - yr;
+        sa += ax * by - bx * ay;
+        const double c = ax * by - ay * bx;
+        s2 += c;
+        sx += c * (ax + bx);
+        sy += c * (ay + by);
+        sj += c * ((ax * ax + ay * ay) + (ax * bx + ay * by) + (bx * bx + by * by));
+    }
+    const double area = 0.5 * s2;
+    const double gx = sx / (3.0 * s2), gy = sy / (3.0 * s2);
+    *A0 = 0.5 * sa;
+    *J0 = sj / 12.0 - area * (gx * gx + gy * gy);
+}
+
 struct Arena {
     char* base = nullptr;
     size_t used = 0;
@@ -234,10 +264,11 @@ extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t 
     if (!c) return LBIB_E_INVALID;
     if (c->finalized) return fail(c, LBIB_E_STATE, "membranes must be added before the first step");
     if (!xy || n < 3) return fail(c, LBIB_E_INVALID, "a membrane needs >= 3 vertices");
-    if (kind != LBIB_MEMBRANE_KINEMATIC && kind != LBIB_MEMBRANE_RIGID_PROJECTED)
+    if (kind != LBIB_MEMBRANE_KINEMATIC && kind != LBIB_MEMBRANE_RIGID_PROJECTED &&
+        kind != LBIB_MEMBRANE_DYNAMIC && kind != LBIB_MEMBRANE_DYNAMIC_RIGID)
         return fail(c, LBIB_E_INVALID, "unknown membrane kind");
-    if (kind == LBIB_MEMBRANE_RIGID_PROJECTED && n > 4 * kChunkV)
-        return fail(c, LBIB_E_INVALID, "rigid-projected membranes are limited to 256 vertices");
+    if (kind != LBIB_MEMBRANE_KINEMATIC && n > 4 * kChunkV)
+        return fail(c, LBIB_E_INVALID, "rigid-projected and dynamic membranes are limited to 256 vertices");
     if (n_ligands < 0 || (n_ligands > 0 && !ligand_elems))
         return fail(c, LBIB_E_INVALID, "ligand list");
     for (int k = 0; k < 2 * n; ++k)
@@ -255,6 +286,8 @@ extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t 
     c->h_ks.push_back(k_s);
     c->h_kb.push_back(k_b);
     c->h_ka.push_back(k_area);
+    c->h_rhop.push_back(1.1);  // rho_P / rho of the particles (Sec. 3)
+    if (kind == LBIB_MEMBRANE_DYNAMIC || kind == LBIB_MEMBRANE_DYNAMIC_RIGID) c->ndyn += 1;
     c->h_xy.insert(c->h_xy.end(), xy, xy + 2 * n);
     if (c->h_mem_lig_off.empty()) c->h_mem_lig_off.push_back(0);
     for (int k = 0; k < n_ligands; ++k) c->h_lig_elem_local.push_back(c->nv + ligand_elems[k]);
@@ -418,10 +451,9 @@ static lbib_status finalize(lbib_ctx* c) {
         const int n = c->h_mem_n[m], off = c->h_mem_off[m], kind = c->h_mem_kind[m];
         for (int k0 = 0; k0 < n; k0 += kChunkV) {
             fu.insert(fu.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, mem_seg_off[m], 0});
-            if (kind != LBIB_MEMBRANE_RIGID_PROJECTED)
-                au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
+            if (!whole_ring(kind)) au.insert(au.end(), {m, k0, std::min(kChunkV, n - k0), off, n, kind, 0, 0});
         }
-        if (kind == LBIB_MEMBRANE_RIGID_PROJECTED) au.insert(au.end(), {m, 0, n, off, n, kind, 0, 0});
+        if (whole_ring(kind)) au.insert(au.end(), {m, 0, n, off, n, kind, 0, 0});
     }
     // ligands decided inside each advance unit (both element vertices in it),
     // as records {ligand, local index of its element's two vertices, 0}, and
@@ -448,6 +480,22 @@ static lbib_status finalize(lbib_ctx* c) {
         }
     }
 
+    // dynamic particles: mass rho_P A_0, inertia rho_P J_0 (J_0 the polar moment
+    // of the rest polygon about its area centroid) and vertex mass per membrane
+    std::vector<double> dyn_consts(3 * (size_t)std::max(nm, 1), 0.0);
+    std::vector<int> dyn_ids;
+    for (int m = 0; m < nm; ++m) {
+        if (!is_dynamic(c->h_mem_kind[m])) continue;
+        dyn_ids.push_back(m);
+        const int n = c->h_mem_n[m];
+        const double* p = c->h_xy.data() + 2 * (size_t)c->h_mem_off[m];
+        double A0, J0;
+        rest_mass_properties(n, p, &A0, &J0);
+        dyn_consts[3 * m] = c->h_rhop[m] * A0;
+        dyn_consts[3 * m + 1] = c->h_rhop[m] * J0;
+        dyn_consts[3 * m + 2] = c->h_rhop[m] * A0 / n;
+    }
+
     // ---- one arena for every marker / tile / bond array
     const size_t cs = c->cmp_elem;
     size_t bytes = 0;
@@ -466,6 +514,8 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * c->ntiles); add(4 * c->ntiles); add(8 * (nm + 1)); add(16);
         add(4 * fu.size()); add(4 * au.size());
         add(4 * au_ligs.size()); add(4 * strad.size());
+        add(2 * cs * nv); add(2 * cs * nv); add(2 * cs * nv); add(48 * (nm + 1)); add(24 * (nm + 1));
+        add(4 * (c->ndyn + 1));
         bytes = probe.used + 256;
     }
     lbib_status st = LBIB_OK;
@@ -524,6 +574,12 @@ static lbib_status finalize(lbib_ctx* c) {
     int* d_au = ar.take<int>(au.size());
     int* d_au_ligs = ar.take<int>(au_ligs.size());
     int* d_strad = ar.take<int>(strad.size());
+    void* V = ar.take<char>(2 * cs * nv);
+    void* Hf = ar.take<char>(2 * cs * nv);
+    void* Dib = ar.take<char>(2 * cs * nv);
+    double* rb = ar.take<double>(6 * (size_t)(nm + 1));
+    double* mem_dyn = ar.take<double>(3 * (size_t)(nm + 1));
+    int* d_dyn_mem = ar.take<int>(c->ndyn + 1);
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
 
     auto H2D = [&](void* d, const void* h, size_t b) -> cudaError_t {
@@ -553,6 +609,13 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(H2D(d_au, au.data(), 4 * au.size()));
         if (!au_ligs.empty()) CK(H2D(d_au_ligs, au_ligs.data(), 4 * au_ligs.size()));
         if (!strad.empty()) CK(H2D(d_strad, strad.data(), 4 * strad.size()));
+        CK(cudaMemsetAsync(V, 0, 2 * cs * nv, c->stream));
+        CK(cudaMemsetAsync(Hf, 0, 2 * cs * nv, c->stream));
+        CK(cudaMemsetAsync(Dib, 0, 2 * cs * nv, c->stream));
+        CK(cudaMemsetAsync(rb, 0, 48 * (size_t)nm, c->stream));
+        CK(H2D(mem_dyn, dyn_consts.data(), 24 * (size_t)nm));
+        if (!dyn_ids.empty()) CK(H2D(d_dyn_mem, dyn_ids.data(), 4 * dyn_ids.size()));
+        CK(cudaStreamSynchronize(c->stream));  // dyn_consts, dyn_ids leave scope
     }
     if (nl > 0) {
         CK(H2D(d_lig_a, lig_a.data(), 4 * nl));
@@ -606,9 +669,15 @@ static lbib_status finalize(lbib_ctx* c) {
     {
         int longest = kChunkV;
         for (int m = 0; m < nm; ++m)
-            if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED) longest = std::max(longest, c->h_mem_n[m]);
+            if (whole_ring(c->h_mem_kind[m])) longest = std::max(longest, c->h_mem_n[m]);
         a.adv_threads = (longest + 31) / 32 * 32;
     }
+    // dynamic particles: states at rest, the ids for the hydrodynamic kernel
+    a.V = V; a.Hf = Hf; a.Dib = Dib; a.rb = rb; a.mem_dyn = mem_dyn;
+    c->d_dyn_mem = d_dyn_mem;
+    c->dyn_threads = 32;
+    for (int m = 0; m < nm; ++m)
+        if (is_dynamic(c->h_mem_kind[m])) c->dyn_threads = std::max(c->dyn_threads, (c->h_mem_n[m] + 31) / 32 * 32);
     a.fu = reinterpret_cast<const int4*>(d_fu);
     a.au = reinterpret_cast<const int4*>(d_au);
     a.au_ligs = reinterpret_cast<const int4*>(d_au_ligs);
@@ -676,6 +745,24 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     return l;
 }
 
+// the hydrodynamic-stress kernel's view of the populations in buffer `src`
+static HydroArgs hydro_args(const lbib_ctx* c, int src) {
+    HydroArgs h{};
+    h.src = c->f[src];
+    h.inv_scale = c->inv_scale;
+    h.bb_bot = bb_term(c->uw_bot);
+    h.bb_top = bb_term(c->uw_top);
+    h.bbf_bot = (float)h.bb_bot;
+    h.bbf_top = (float)h.bb_top;
+    h.gx = c->gx;
+    h.gy = c->gy;
+    h.nu = (c->tau - 0.5) / 3.0;
+    h.ndyn = c->ndyn;
+    h.dyn_mem = c->d_dyn_mem;
+    h.threads = c->dyn_threads;
+    return h;
+}
+
 // the fused collide-stream kernel in the context's form
 static cudaError_t launch_fused(const lbib_ctx* c, const LbArgs& l, cudaStream_t s) {
     const bool walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK;
@@ -691,6 +778,7 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     a.flags = c->flags[src];
     cudaError_t e;
     const bool has_ib = c->nv > 0;
+    if (c->ndyn > 0 && (e = launch_hydro(c->prec, a, hydro_args(c, src), s)) != cudaSuccess) return e;
     if (has_ib && (e = launch_forces(c->prec, a, c->max_mem_n, s)) != cudaSuccess) return e;
     const LbArgs l = lb_args(c, src, src, 1);
     if ((e = launch_fused(c, l, s)) != cudaSuccess) return e;
@@ -913,6 +1001,28 @@ extern "C" lbib_status lbib_read_marker_forces(lbib_ctx* c, double* fxy) {
     return read_cvec(c, c->ma.F, fxy);
 }
 
+extern "C" lbib_status lbib_set_particle_density(lbib_ctx* c, int32_t m, double rho_ratio) {
+    if (!c) return LBIB_E_INVALID;
+    if (c->finalized) return fail(c, LBIB_E_STATE, "particle densities must be set before the first step");
+    if (m < 0 || m >= c->nmem || !is_dynamic(c->h_mem_kind[m]))
+        return fail(c, LBIB_E_INVALID, "not a dynamic membrane");
+    if (!(rho_ratio > 0.0) || !std::isfinite(rho_ratio)) return fail(c, LBIB_E_INVALID, "density ratio");
+    c->h_rhop[m] = rho_ratio;
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_particle_velocity(lbib_ctx* c, int32_t m, double* uv) {
+    if (!c || !uv) return LBIB_E_INVALID;
+    if (m < 0 || m >= c->nmem || !is_dynamic(c->h_mem_kind[m]))
+        return fail(c, LBIB_E_INVALID, "not a dynamic membrane");
+    std::vector<double> all(2 * (size_t)c->nv);
+    lbib_status st = read_cvec(c, c->ma.V, all.data());
+    if (st != LBIB_OK) return st;
+    std::copy(all.begin() + 2 * (size_t)c->h_mem_off[m],
+              all.begin() + 2 * (size_t)(c->h_mem_off[m] + c->h_mem_n[m]), uv);
+    return LBIB_OK;
+}
+
 extern "C" lbib_status lbib_read_marker_velocity(lbib_ctx* c, double* uxy) {
     if (!c) return LBIB_E_INVALID;
     lbib_status st = finalize(c);
@@ -1010,9 +1120,13 @@ extern "C" lbib_status lbib_profile_kernels(lbib_ctx* c, int32_t reps, double* m
     MarkerArgs a = c->ma;
     a.gsum = c->G[c->cur];
     a.flags = c->flags[c->cur];
-    // forces + spreading (accumulates into the field of the current parity)
+    // forces + spreading (accumulates into the field of the current parity),
+    // with the hydrodynamic stresses of dynamic particles
     CK(cudaEventRecord(ev[0], c->stream));
-    for (int r = 0; r < reps && has_ib; ++r) CK(launch_forces(c->prec, a, c->max_mem_n, c->stream));
+    for (int r = 0; r < reps && has_ib; ++r) {
+        if (c->ndyn > 0) CK(launch_hydro(c->prec, a, hydro_args(c, c->cur), c->stream));
+        CK(launch_forces(c->prec, a, c->max_mem_n, c->stream));
+    }
     CK(cudaEventRecord(ev[1], c->stream));
     // fused collide-stream, ping-pong between the buffers
     const int gpar = 1 - c->cur;
@@ -1246,8 +1360,8 @@ extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the tangent needs an FP64 context");
     if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the tangent needs resting walls");
     for (int k : c->h_mem_kind)
-        if (k == LBIB_MEMBRANE_RIGID_PROJECTED)
-            return fail(c, LBIB_E_INVALID, "the tangent does not support rigid-projected membranes");
+        if (k != LBIB_MEMBRANE_KINEMATIC)
+            return fail(c, LBIB_E_INVALID, "the tangent supports kinematic membranes only");
     lbib_status st = finalize(c);
     if (st == LBIB_OK) st = build_graphs(c);
     if (st != LBIB_OK) return st;
@@ -1484,8 +1598,8 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     if (checkpoint_every < 1) return fail(c, LBIB_E_INVALID, "checkpoint interval must be at least 1");
     if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the adjoint needs resting walls");
     for (size_t m = 0; m < c->h_mem_kind.size(); ++m) {
-        if (c->h_mem_kind[m] == LBIB_MEMBRANE_RIGID_PROJECTED)
-            return fail(c, LBIB_E_INVALID, "the adjoint does not support rigid-projected membranes");
+        if (c->h_mem_kind[m] != LBIB_MEMBRANE_KINEMATIC)
+            return fail(c, LBIB_E_INVALID, "the adjoint supports kinematic membranes only");
         if (c->h_mem_n[m] < 5) return fail(c, LBIB_E_INVALID, "the adjoint needs membranes of at least 5 vertices");
     }
     lbib_status st = finalize(c);
@@ -1731,7 +1845,7 @@ constexpr char kSaveMagic[8] = {'L', 'B', 'I', 'B', 'S', 'A', 'V', '1'};
 
 struct SaveHeader {
     char magic[8];
-    int32_t version, nx, ny, prec, walls, nmem, nv, nlig, nrec, nseg, scale_exp, pad;
+    int32_t version, nx, ny, prec, walls, nmem, nv, nlig, nrec, nseg, scale_exp, ndyn;
     double tau, gx, gy, uw_bot, uw_top, d_rep;
     int64_t steps;
 };
@@ -1743,6 +1857,7 @@ SaveHeader header_of(const lbib_ctx* c) {
     h.nx = c->nx; h.ny = c->ny; h.prec = (int32_t)c->prec; h.walls = (int32_t)c->walls;
     h.nmem = c->nmem; h.nv = c->nv; h.nlig = c->nlig; h.nrec = c->ma.nrec; h.nseg = c->nseg;
     h.scale_exp = c->scale_exp;
+    h.ndyn = c->ndyn;
     h.tau = c->tau; h.gx = c->gx; h.gy = c->gy; h.uw_bot = c->uw_bot; h.uw_top = c->uw_top; h.d_rep = c->d_rep;
     h.steps = c->steps;
     return h;
@@ -1758,7 +1873,10 @@ std::vector<StatePart> state_parts(lbib_ctx* c) {
     const size_t N = (size_t)c->nx * c->ny, nv = c->nv, nlig = c->nlig, nrec = c->ma.nrec;
     return {{c->f[c->cur], 9 * N * c->pop_elem}, {c->ma.X, 16 * nv},          {c->ma.Xp, 16 * nv},
             {c->ma.bond_of_lig, 4 * nlig},       {c->ma.owner, 4 * nrec},     {c->ma.owner_cell, 4 * nrec},
-            {c->ma.seg_box, sizeof(float4) * (size_t)c->nseg},              {c->d_step, 8}};
+            {c->ma.seg_box, sizeof(float4) * (size_t)c->nseg},              {c->d_step, 8},
+            // dynamic particles: vertex velocities and rigid states
+            {c->ma.V, c->ndyn > 0 ? 2 * c->cmp_elem * nv : 0},
+            {c->ma.rb, c->ndyn > 0 ? 6 * sizeof(double) * (size_t)c->nmem : 0}};
 }
 
 }  // namespace

@@ -88,6 +88,7 @@ constexpr int kScreenIter = 8;                    // segment boxes per lane load
 //            warps 2-9  repulsion over (candidate segment, vertex) pairs,
 //                       accumulated per vertex in fixed point (order-free)
 //   phase 3  all        spreading: (vertex, node) pairs into the fixed-point field
+//                       (of a dynamic particle: its forcing term, see dynamic_kernels.cu)
 template <typename C>
 __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     using E = typename Ext<C>::E;
@@ -443,10 +444,21 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         Fy -= mag * s_ny[tid + 1];
         C* F = static_cast<C*>(a.F);
         const int v = off + k0 + tid;
+        C Sx = Fx, Sy = Fy;
+        if (u1.y >= LBIB_MEMBRANE_DYNAMIC) {
+            // dynamic particle (Sec. 2.4): the total force of Eq. newtonSoft adds
+            // the hydrodynamic force; the fluid receives the forcing term instead
+            const C* Hf = static_cast<const C*>(a.Hf);
+            const C* D = static_cast<const C*>(a.Dib);
+            Fx += Hf[2 * (size_t)v];
+            Fy += Hf[2 * (size_t)v + 1];
+            Sx = D[2 * (size_t)v];
+            Sy = D[2 * (size_t)v + 1];
+        }
         F[2 * (size_t)v] = Fx;
         F[2 * (size_t)v + 1] = Fy;
-        s_F[tid][0] = Fx;
-        s_F[tid][1] = Fy;
+        s_F[tid][0] = Sx;
+        s_F[tid][1] = Sy;
     }
     __syncthreads();
 

@@ -186,6 +186,27 @@ struct MarkerArgs {
     const int4* au_ligs;      // {ligand, local vertex a, local vertex b, 0} per unit ligand
     int nstrad;
     const int* strad_ligs;
+    // dynamic particles (Sec. 2.4): compute-type [nv][2] arrays, meaningful on
+    // the vertices of dynamic membranes only
+    void* V;                  // particle velocity u_p^n
+    void* Hf;                 // hydrodynamic force of this step (k_hydro)
+    void* Dib;                // forcing term spread into the fluid (k_hydro)
+    double* rb;               // [nmem][6] rigid state: u, v, u_prev, v_prev, omega, omega_prev
+    const double* mem_dyn;    // [nmem][3] mass rho_P A_0, inertia rho_P J_0, vertex mass m / n
+};
+
+// Arguments of the hydrodynamic-stress kernel: the populations the step
+// starts from and what turns them into p and u
+struct HydroArgs {
+    const void* src;          // post-collision deviations d* of step n-1 (f^n = w + pulled d*)
+    float inv_scale;
+    double bb_bot, bb_top;    // moving-wall terms of the bounce-back (as in LbArgs)
+    float bbf_bot, bbf_top;
+    double gx, gy;            // body force (u = (sum f e + G_body / 2) / rho)
+    double nu;                // (tau - 1/2) / 3
+    int ndyn;                 // dynamic membranes, one block each
+    const int* dyn_mem;       // [ndyn] their ids
+    int threads;              // block size: the longest dynamic ring rounded up to a warp
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
@@ -225,6 +246,9 @@ cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, c
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s);
+// dynamic_kernels.cu: hydrodynamic stresses and forcing terms of the dynamic
+// particles at the start of a step (before launch_forces)
+cudaError_t launch_hydro(lbib_precision prec, const MarkerArgs& a, const HydroArgs& h, cudaStream_t s);
 // observables.cu: 8 doubles per membrane (see lbib_membrane_observables)
 cudaError_t launch_observables(lbib_precision prec, const MarkerArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);
@@ -265,7 +289,11 @@ struct lbib_ctx {
     std::vector<double> h_xy;
     std::vector<int> h_mem_off, h_mem_n, h_mem_kind, h_lig_elem_local, h_mem_lig_off;
     std::vector<double> h_ks, h_kb, h_ka;
+    std::vector<double> h_rhop;   // rho_P / rho of each membrane (dynamic ones)
     int nmem = 0, nv = 0, nlig = 0;
+    int ndyn = 0;                 // dynamic membranes
+    int* d_dyn_mem = nullptr;     // their ids (in the arena)
+    int dyn_threads = 0;
     // receptors
     std::vector<double> h_rec;
     lbib_bond_params bp{};

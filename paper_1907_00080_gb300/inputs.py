@@ -37,8 +37,9 @@ class Membrane:
     ks: float
     kb: float
     ka: float
-    kind: int = 0             # 0 kinematic, 1 rigid-projected
+    kind: int = 0             # 0 kinematic, 1 rigid-projected, 2 dynamic, 3 dynamic rigid
     ligands: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+    rho_p: float = 1.1        # particle / fluid density of a dynamic membrane (Sec. 3)
 
 
 @dataclass
@@ -230,15 +231,43 @@ def capsule_128x32(precision="f64", bonds="default") -> Workload:
     return wl
 
 
+def dynamic_carriers_128x48(precision="f64", bonds="stress") -> Workload:
+    """Dynamic-IB case (Sec. 2.4): 128x48 channel, u_max = 0.02; a rigid
+    dynamic carrier (radius 5, 32 markers, a ligand on every element) whose
+    lowest vertex sits 1.27 lu above the lower wall, so that its probes and
+    bonds reach the wall; a deformable dynamic carrier (radius 5, 32 markers,
+    k_s = 5e-3, k_b = 5e-4) across the channel centre; a kinematic capsule
+    (radius 4, 24 markers) between them; receptors on every lower-wall node."""
+    nx, ny = 128, 48
+    g = body_force_for(0.02, ny)
+    mems = [
+        Membrane(xy=circle(30.0, 5.75, 5.0, 32), ks=0.05, kb=0.005, ka=1.0, kind=3,
+                 ligands=np.arange(32, dtype=np.int32)),
+        Membrane(xy=circle(70.0, 24.3, 5.0, 32), ks=5e-3, kb=5e-4, ka=1.0, kind=2),
+        Membrane(xy=circle(50.0, 14.0, 4.0, 24), ks=0.02, kb=0.002, ka=0.1, kind=0),
+    ]
+    wl = Workload(name="dynamic_carriers_128x48", nx=nx, ny=ny, body_force=(g, 0.0), walls=1,
+                  init="poiseuille", precision=precision, membranes=mems,
+                  receptors=wall_receptors(nx, ny, lower=True, upper=False),
+                  sigma_lu=sigma_lattice(1.0, ny), seed=0, steps=1000)
+    wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
+    return wl
+
+
 def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carriers=4,
               carrier_radius=8.0, carrier_markers=50, ca_carrier=(0.0, 1e-2), sigma=1.0,
               re=1e-2, seed=0, precision="f32", steps=200000, name=None,
-              bonds="default", release_y=None) -> Workload:
+              bonds="default", release_y=None, carrier_model="kinematic") -> Workload:
     """Coarse capillary: 10x40 um at dx = 62.5 nm is a 160x640 lattice; 8
     biconcave red cells (8 um major axis -> alpha = 64 lu, 200 markers each),
     4 carriers of 1 um diameter (radius 8 lu, 50 markers), alternating rigid
-    (Ca = 0, rigid-projected) and soft (Ca = 1e-2) carriers, ligand density
-    0.5 (every other element), receptors on both walls, sigma = 1."""
+    (Ca = 0) and soft (Ca = 1e-2) carriers, ligand density 0.5 (every other
+    element), receptors on both walls, sigma = 1.  carrier_model "kinematic":
+    rigid carriers rigid-projected, soft ones kinematic; "dynamic": the
+    dynamic IB of Sec. 2.4 (rigid and deformable particles, rho_P / rho = 1.1)."""
+    if carrier_model not in ("kinematic", "dynamic"):
+        raise ValueError(carrier_model)
+    dyn = carrier_model == "dynamic"
     rng = np.random.Generator(np.random.PCG64(seed))
     u_max = u_max_for_re(re, ny)
     g = body_force_for(u_max, ny)
@@ -258,10 +287,10 @@ def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carrie
         ca = ca_carrier[c % len(ca_carrier)]
         if ca == 0.0:
             ks = ks_rbc
-            kind = 1
+            kind = 3 if dyn else 1
         else:
             ks = ks_for_ca(ca, u_max)
-            kind = 0
+            kind = 2 if dyn else 0
         kb = 0.05 * ks * carrier_radius ** 2
         mems.append(Membrane(xy=placed[n_rbc + c], ks=ks, kb=kb, ka=1.0, kind=kind, ligands=lig.copy()))
     wl = Workload(name=name or "capillary_%dx%d" % (nx, ny), nx=nx, ny=ny, body_force=(g, 0.0),
@@ -272,8 +301,9 @@ def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carrie
     return wl
 
 
-def coarse_capillary_640x160(precision="f32", seed=0, steps=200000) -> Workload:
-    return capillary(precision=precision, seed=seed, steps=steps, name="capillary_640x160")
+def coarse_capillary_640x160(precision="f32", seed=0, steps=200000, carrier_model="kinematic") -> Workload:
+    name = "capillary_640x160" + ("_dynamic" if carrier_model == "dynamic" else "")
+    return capillary(precision=precision, seed=seed, steps=steps, name=name, carrier_model=carrier_model)
 
 
 def fine_capillary_2000x667(precision="f32", sigma=1.0, carriers="rigid", seed=0, steps=20000,

@@ -21,6 +21,7 @@ LBIB_F64, LBIB_F32, LBIB_F32_STORE_F16, LBIB_F32_STORE_BF16 = range(4)
 LBIB_WALLS_NONE, LBIB_WALLS_Y_BOUNCEBACK = 0, 1
 LBIB_INIT_REST, LBIB_INIT_POISEUILLE, LBIB_INIT_COUETTE = 0, 1, 2
 LBIB_MEMBRANE_KINEMATIC, LBIB_MEMBRANE_RIGID_PROJECTED = 0, 1
+LBIB_MEMBRANE_DYNAMIC, LBIB_MEMBRANE_DYNAMIC_RIGID = 2, 3
 
 PRECISIONS = {"f64": LBIB_F64, "f32": LBIB_F32, "f16": LBIB_F32_STORE_F16, "bf16": LBIB_F32_STORE_BF16}
 STATUS_NAMES = {0: "LBIB_OK", 1: "LBIB_E_INVALID", 2: "LBIB_E_CUDA", 3: "LBIB_E_OOM",
@@ -72,6 +73,8 @@ _SIGS = {
     "lbib_write_markers": (_I, [_P, _DP, _DP]),
     "lbib_read_marker_forces": (_I, [_P, _DP]),
     "lbib_read_marker_velocity": (_I, [_P, _DP]),
+    "lbib_set_particle_density": (_I, [_P, _I32, _D]),
+    "lbib_read_particle_velocity": (_I, [_P, _I32, _DP]),
     "lbib_read_bonds": (_I, [_P, _I32P, _I32P, _I32, _I32P]),
     "lbib_diagnostics": (_I, [_P, _DP, _DP]),
     "lbib_population_mass_noalloc": (_I, [_P, _I64, _P, _P]),
@@ -245,6 +248,14 @@ def lbib_read_marker_forces(ctx, fxy):
 
 def lbib_read_marker_velocity(ctx, uxy):
     _check(ctx, load().lbib_read_marker_velocity(ctx, _dptr(uxy)))
+
+
+def lbib_set_particle_density(ctx, membrane_id, rho_ratio):
+    _check(ctx, load().lbib_set_particle_density(ctx, int(membrane_id), float(rho_ratio)))
+
+
+def lbib_read_particle_velocity(ctx, membrane_id, uv):
+    _check(ctx, load().lbib_read_particle_velocity(ctx, int(membrane_id), _dptr(uv)))
 
 
 def lbib_read_bonds(ctx, cap):
@@ -471,8 +482,10 @@ class Simulation:
         self.nx, self.ny = wl.nx, wl.ny
         self.ctx = lbib_create(wl.nx, wl.ny, prec, init, wl.tau, wl.body_force, wl.walls, cuda_stream)
         self.mem_sizes = []
-        for m in wl.membranes:
+        for k, m in enumerate(wl.membranes):
             lbib_add_membrane(self.ctx, m.xy, m.ks, m.kb, m.ka, m.kind, m.ligands)
+            if m.kind in (LBIB_MEMBRANE_DYNAMIC, LBIB_MEMBRANE_DYNAMIC_RIGID):
+                lbib_set_particle_density(self.ctx, k, m.rho_p)
             self.mem_sizes.append(len(m.xy))
         self.nv = sum(self.mem_sizes)
         self.nlig = wl.n_ligands
@@ -536,6 +549,20 @@ class Simulation:
         if self.nv:
             lbib_read_marker_velocity(self.ctx, u)
         return u
+
+    def particle_velocity(self):
+        """particle velocity of every vertex (zero on non-dynamic membranes),
+        like the oracle's"""
+        v = np.zeros((self.nv, 2))
+        off = 0
+        for k, m in enumerate(self.wl.membranes):
+            n = len(m.xy)
+            if m.kind in (LBIB_MEMBRANE_DYNAMIC, LBIB_MEMBRANE_DYNAMIC_RIGID):
+                part = np.zeros((n, 2))
+                lbib_read_particle_velocity(self.ctx, k, part)
+                v[off:off + n] = part
+            off += n
+        return v
 
     def bonds(self):
         """bond_of_ligand array (-1 = free), like the oracle's"""

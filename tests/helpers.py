@@ -8,7 +8,9 @@ def make_oracle(wl):
     s = oracle.OracleSim(wl.nx, wl.ny, wl.tau, wl.body_force, wl.walls, init=wl.init,
                          wall_velocity=wl.wall_velocity)
     for m in wl.membranes:
-        s.add_membrane(m.xy, m.ks, m.kb, m.ka, m.kind, m.ligands)
+        k = s.add_membrane(m.xy, m.ks, m.kb, m.ka, m.kind, m.ligands)
+        if m.kind in (2, 3):
+            s.set_density(k, m.rho_p)
     if wl.receptors is not None and len(wl.receptors):
         b = wl.bonds
         s.set_receptors(wl.receptors, d_cut=b["d_cut"], y_eq=b["y_eq"], sigma=wl.sigma_lu,
