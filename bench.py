@@ -299,7 +299,8 @@ def lbib_main(args):
     if not args.no_forms and rank == 0:
         forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream),
                  "differentiation": differentiation_form(lbib, torch),
-                 "couette_cell_free_layer": couette_form(lbib, torch, stream)}
+                 "couette_cell_free_layer": couette_form(lbib, torch, stream),
+                 "dynamic_carriers": dynamic_form(lbib, torch, stream)}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -492,6 +493,61 @@ def couette_form(lbib, torch, stream, warm=2000, timed=4000):
             sim.close()
     return {"workload": "Couette 600x200 (dx = 15 nm, H_CFL = 3 um), Re = 0.003, one 1 um carrier x 210 markers, "
                         "FP32", "steps": warm + timed, "results": res}
+
+
+def dynamic_form(lbib, torch, stream, warm=200, timed=4000, couette_warm=2000, couette_timed=4000):
+    """The dynamic IB of Sec. 2.4 for the carriers (rigid: Newton-Euler; soft:
+    Verlet; probe tractions and direct forcing) against their kinematic
+    reading on the same workloads: the coarse 640 x 160 capillary in FP32 and
+    FP64 (MLUPS over `timed` steps after `warm`, CUDA events on the stream, and
+    the hydrodynamic-stress kernel's own time per launch), and the Couette
+    cell-free-layer carrier at sigma = 1 (rolling velocity and bonds)."""
+    from paper_1907_00080_gb300 import inputs, tuning
+    cap = {}
+    for prec in ("f32", "f64"):
+        for model in ("kinematic", "dynamic"):
+            wl = inputs.coarse_capillary_640x160(prec, carrier_model=model)
+            sim = lbib.Simulation(wl, tiling=tuning.bench_tiling(wl), cuda_stream=stream.cuda_stream)
+            with torch.cuda.stream(stream):
+                sim.step(warm)
+                sim.sync()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(timed)
+                e1.record(stream)
+                sim.sync()
+                ms = e0.elapsed_time(e1)
+                entry = {"mlups": wl.nx * wl.ny * timed / (ms * 1e-3) / 1e6, "us_per_step": 1e3 * ms / timed,
+                         "kernels_per_step": sim.kernels_per_step}
+                if model == "dynamic":
+                    lbib.lbib_profile_hydro(sim.ctx, 20)
+                    entry["k_hydro_us_per_launch"] = 1e3 * lbib.lbib_profile_hydro(sim.ctx, 500)
+            cap["%s_%s" % (model, prec)] = entry
+            sim.close()
+    for prec in ("f32", "f64"):
+        d, k = cap["dynamic_" + prec], cap["kinematic_" + prec]
+        d["step_time_over_kinematic"] = d["us_per_step"] / k["us_per_step"]
+    couette = {}
+    for carrier in ("rigid", "soft"):
+        wl = inputs.couette_cfl_600x200("f32", sigma=1.0, carrier=carrier, carrier_model="dynamic")
+        sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            sim.step(couette_warm)
+            sim.sync()
+            o0 = sim.observables()[0]
+            sim.step(couette_timed)
+            sim.sync()
+        o = sim.observables()[0]
+        couette["dynamic_%s_sigma1" % carrier] = {
+            "bonds": int(o[5]), "n_L_over_n_L_after_warm": float(o[5] / o0[5]) if o0[5] > 0 else None,
+            "u_roll_over_u_wall": float((o[0] - o0[0]) / couette_timed / wl.wall_velocity[1]),
+            "carrier_min_height_lu": float(o[6])}
+        sim.close()
+    return {"workload": "capillary 640x160 (8 red cells, 4 carriers, 1 280 receptors), carriers kinematic "
+                        "(rigid-projected / kinematic) vs dynamic (Newton-Euler / Verlet, rho_P/rho = 1.1); "
+                        "Couette 600x200 one 1 um dynamic carrier, FP32",
+            "capillary": cap, "couette_cell_free_layer": couette,
+            "steps": {"capillary": warm + timed, "couette": couette_warm + couette_timed}}
 
 
 def ensemble_form(lbib, torch, stream, n=64, steps=400):

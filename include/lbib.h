@@ -146,8 +146,8 @@ lbib_status lbib_add_membrane(lbib_ctx* ctx, const double* xy, int32_t n, double
  * second-order backward-difference velocity; the rigid one advances its
  * velocity and spin by the printed second-order update of F/m and M/I (m =
  * rho_P A_0, I = rho_P J_0 about the area centroid), translates and turns about
- * its area centroid.  Particles start at rest.  A dynamic membrane has at most
- * 256 vertices.  The tangent, the adjoint and the slab decomposition refuse
+ * its area centroid.  Particles start at rest.  A rigid dynamic membrane has
+ * at most 256 vertices.  The tangent, the adjoint and the slab decomposition refuse
  * contexts that hold one. */
 
 /* Particle density over fluid density rho_P / rho of a dynamic membrane
@@ -475,6 +475,13 @@ lbib_status lbib_profile_fused(lbib_ctx* ctx, int32_t reps, double* ms_per_launc
  * fluid): use it on a scratch context.  Errors: LBIB_E_STATE before the
  * first step. */
 lbib_status lbib_profile_kernels(lbib_ctx* ctx, int32_t reps, double* ms_per_launch);
+
+/* Profiling aid: the hydrodynamic-stress kernel of the dynamic particles
+ * launched `reps` times back to back on the context's stream (it only reads
+ * the state and rewrites its own outputs); mean duration of one launch in
+ * *ms_per_launch, 0 for a context without dynamic membranes.
+ * Errors: LBIB_E_STATE before the first step. */
+lbib_status lbib_profile_hydro(lbib_ctx* ctx, int32_t reps, double* ms_per_launch);
 
 /* Number of kernels one time step launches (for launch accounting). */
 int32_t lbib_kernels_per_step(const lbib_ctx* ctx);

@@ -267,8 +267,8 @@ extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t 
     if (kind != LBIB_MEMBRANE_KINEMATIC && kind != LBIB_MEMBRANE_RIGID_PROJECTED &&
         kind != LBIB_MEMBRANE_DYNAMIC && kind != LBIB_MEMBRANE_DYNAMIC_RIGID)
         return fail(c, LBIB_E_INVALID, "unknown membrane kind");
-    if (kind != LBIB_MEMBRANE_KINEMATIC && n > 4 * kChunkV)
-        return fail(c, LBIB_E_INVALID, "rigid-projected and dynamic membranes are limited to 256 vertices");
+    if (whole_ring(kind) && n > 4 * kChunkV)
+        return fail(c, LBIB_E_INVALID, "rigid-projected and rigid dynamic membranes are limited to 256 vertices");
     if (n_ligands < 0 || (n_ligands > 0 && !ligand_elems))
         return fail(c, LBIB_E_INVALID, "ligand list");
     for (int k = 0; k < 2 * n; ++k)
@@ -482,12 +482,14 @@ static lbib_status finalize(lbib_ctx* c) {
 
     // dynamic particles: mass rho_P A_0, inertia rho_P J_0 (J_0 the polar moment
     // of the rest polygon about its area centroid) and vertex mass per membrane
+    // and the blocks of the hydrodynamic kernel, {membrane, k0, count, 0}
     std::vector<double> dyn_consts(3 * (size_t)std::max(nm, 1), 0.0);
-    std::vector<int> dyn_ids;
+    std::vector<int> hydro_units;
     for (int m = 0; m < nm; ++m) {
         if (!is_dynamic(c->h_mem_kind[m])) continue;
-        dyn_ids.push_back(m);
         const int n = c->h_mem_n[m];
+        for (int k0 = 0; k0 < n; k0 += hydro_chunk())
+            hydro_units.insert(hydro_units.end(), {m, k0, std::min(hydro_chunk(), n - k0), 0});
         const double* p = c->h_xy.data() + 2 * (size_t)c->h_mem_off[m];
         double A0, J0;
         rest_mass_properties(n, p, &A0, &J0);
@@ -515,7 +517,7 @@ static lbib_status finalize(lbib_ctx* c) {
         add(4 * fu.size()); add(4 * au.size());
         add(4 * au_ligs.size()); add(4 * strad.size());
         add(2 * cs * nv); add(2 * cs * nv); add(2 * cs * nv); add(48 * (nm + 1)); add(24 * (nm + 1));
-        add(4 * (c->ndyn + 1));
+        add(4 * hydro_units.size());
         bytes = probe.used + 256;
     }
     lbib_status st = LBIB_OK;
@@ -579,7 +581,7 @@ static lbib_status finalize(lbib_ctx* c) {
     void* Dib = ar.take<char>(2 * cs * nv);
     double* rb = ar.take<double>(6 * (size_t)(nm + 1));
     double* mem_dyn = ar.take<double>(3 * (size_t)(nm + 1));
-    int* d_dyn_mem = ar.take<int>(c->ndyn + 1);
+    int* d_hydro_units = ar.take<int>(hydro_units.size());
     if (ar.used > bytes) return fail(c, LBIB_E_STATE, "internal arena sizing error");
 
     auto H2D = [&](void* d, const void* h, size_t b) -> cudaError_t {
@@ -614,8 +616,8 @@ static lbib_status finalize(lbib_ctx* c) {
         CK(cudaMemsetAsync(Dib, 0, 2 * cs * nv, c->stream));
         CK(cudaMemsetAsync(rb, 0, 48 * (size_t)nm, c->stream));
         CK(H2D(mem_dyn, dyn_consts.data(), 24 * (size_t)nm));
-        if (!dyn_ids.empty()) CK(H2D(d_dyn_mem, dyn_ids.data(), 4 * dyn_ids.size()));
-        CK(cudaStreamSynchronize(c->stream));  // dyn_consts, dyn_ids leave scope
+        if (!hydro_units.empty()) CK(H2D(d_hydro_units, hydro_units.data(), 4 * hydro_units.size()));
+        CK(cudaStreamSynchronize(c->stream));  // dyn_consts, hydro_units leave scope
     }
     if (nl > 0) {
         CK(H2D(d_lig_a, lig_a.data(), 4 * nl));
@@ -674,10 +676,8 @@ static lbib_status finalize(lbib_ctx* c) {
     }
     // dynamic particles: states at rest, the ids for the hydrodynamic kernel
     a.V = V; a.Hf = Hf; a.Dib = Dib; a.rb = rb; a.mem_dyn = mem_dyn;
-    c->d_dyn_mem = d_dyn_mem;
-    c->dyn_threads = 32;
-    for (int m = 0; m < nm; ++m)
-        if (is_dynamic(c->h_mem_kind[m])) c->dyn_threads = std::max(c->dyn_threads, (c->h_mem_n[m] + 31) / 32 * 32);
+    c->d_hydro_units = reinterpret_cast<int4*>(d_hydro_units);
+    c->n_hydro_units = (int)(hydro_units.size() / 4);
     a.fu = reinterpret_cast<const int4*>(d_fu);
     a.au = reinterpret_cast<const int4*>(d_au);
     a.au_ligs = reinterpret_cast<const int4*>(d_au_ligs);
@@ -757,9 +757,8 @@ static HydroArgs hydro_args(const lbib_ctx* c, int src) {
     h.gx = c->gx;
     h.gy = c->gy;
     h.nu = (c->tau - 0.5) / 3.0;
-    h.ndyn = c->ndyn;
-    h.dyn_mem = c->d_dyn_mem;
-    h.threads = c->dyn_threads;
+    h.nunits = c->n_hydro_units;
+    h.units = c->d_hydro_units;
     return h;
 }
 
@@ -865,8 +864,9 @@ extern "C" int64_t lbib_step_count(const lbib_ctx* c) { return c ? c->steps : -1
 
 extern "C" int32_t lbib_kernels_per_step(const lbib_ctx* c) {
     if (!c) return -1;
-    // forces with spreading, fused LB, interpolation + advance + bond kinetics
-    return c->nv > 0 ? 3 : 1;
+    // forces with spreading, fused LB, interpolation + advance + bond kinetics,
+    // and the hydrodynamic stresses when there are dynamic particles
+    return c->nv > 0 ? (c->ndyn > 0 ? 4 : 3) : 1;
 }
 
 extern "C" int32_t lbib_storage_scale_exponent(const lbib_ctx* c) { return c ? c->scale_exp : 0; }
@@ -1111,6 +1111,24 @@ extern "C" lbib_status lbib_profile_fused(lbib_ctx* c, int32_t reps, double* ms_
     return LBIB_OK;
 }
 
+extern "C" lbib_status lbib_profile_hydro(lbib_ctx* c, int32_t reps, double* ms_per_launch) {
+    if (!c || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
+    if (!c->finalized || c->steps == 0) return fail(c, LBIB_E_STATE, "profile after at least one step");
+    *ms_per_launch = 0.0;
+    if (c->ndyn == 0) return LBIB_OK;
+    cudaEvent_t ev[2];
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ev[k]));
+    CK(cudaEventRecord(ev[0], c->stream));
+    for (int r = 0; r < reps; ++r) CK(launch_hydro(c->prec, c->ma, hydro_args(c, c->cur), c->stream));
+    CK(cudaEventRecord(ev[1], c->stream));
+    CK(cudaEventSynchronize(ev[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    *ms_per_launch = (double)ms / reps;
+    for (int k = 0; k < 2; ++k) cudaEventDestroy(ev[k]);
+    return LBIB_OK;
+}
+
 extern "C" lbib_status lbib_profile_kernels(lbib_ctx* c, int32_t reps, double* ms_per_launch) {
     if (!c || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
     if (!c->finalized || c->steps == 0) return fail(c, LBIB_E_STATE, "profile after at least one step");
@@ -1120,13 +1138,9 @@ extern "C" lbib_status lbib_profile_kernels(lbib_ctx* c, int32_t reps, double* m
     MarkerArgs a = c->ma;
     a.gsum = c->G[c->cur];
     a.flags = c->flags[c->cur];
-    // forces + spreading (accumulates into the field of the current parity),
-    // with the hydrodynamic stresses of dynamic particles
+    // forces + spreading (accumulates into the field of the current parity)
     CK(cudaEventRecord(ev[0], c->stream));
-    for (int r = 0; r < reps && has_ib; ++r) {
-        if (c->ndyn > 0) CK(launch_hydro(c->prec, a, hydro_args(c, c->cur), c->stream));
-        CK(launch_forces(c->prec, a, c->max_mem_n, c->stream));
-    }
+    for (int r = 0; r < reps && has_ib; ++r) CK(launch_forces(c->prec, a, c->max_mem_n, c->stream));
     CK(cudaEventRecord(ev[1], c->stream));
     // fused collide-stream, ping-pong between the buffers
     const int gpar = 1 - c->cur;

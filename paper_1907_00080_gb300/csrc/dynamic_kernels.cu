@@ -17,15 +17,14 @@
 // element lengths, and the factor 2 accounts for the half force a node's
 // velocity carries under Guo forcing.
 //
-// One block per dynamic membrane, one thread per vertex (<= 256 vertices).
+// One block per chunk of kHydroV vertices of a dynamic membrane, one thread
+// per (fit, stencil node) pair.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "marker_common.cuh"
 
 namespace lbib {
-
-constexpr int kHydroThreads = 4 * kChunkV;  // most vertices of a dynamic membrane
 
 template <typename C> __device__ __forceinline__ C hydro_wall(const HydroArgs& h, bool bottom);
 template <> __device__ __forceinline__ float hydro_wall<float>(const HydroArgs& h, bool bottom) {
@@ -103,6 +102,31 @@ __device__ __forceinline__ Stencil<C> stencil_at(const MarkerArgs& a, E px, E py
     return st;
 }
 
+// the stencil's values at row b, column q, picked with unrolled selects (no
+// run-time indexing of the register arrays)
+template <typename C>
+struct NodeOf {
+    C rx, ry, wx, wy;
+    bool rowok;
+};
+template <typename C>
+__device__ __forceinline__ NodeOf<C> node_of(const Stencil<C>& st, int b, int q) {
+    NodeOf<C> o{C(0), C(0), C(0), C(0), false};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k == q) {
+            o.rx = st.rx[k];
+            o.wx = st.wx[k];
+        }
+        if (k == b) {
+            o.ry = st.ry[k];
+            o.wy = st.wy[k];
+            o.rowok = st.rowok[k];
+        }
+    }
+    return o;
+}
+
 template <typename C>
 __device__ __forceinline__ void stencil_node(const MarkerArgs& a, const Stencil<C>& st, int b, int q, int& i,
                                              int& j) {
@@ -111,177 +135,204 @@ __device__ __forceinline__ void stencil_node(const MarkerArgs& a, const Stencil<
     i = ((st.i0 + q - 1) % a.nx + a.nx) % a.nx;
 }
 
-// MLS fit at the probe: value of p and the gradient of (u, v)
+// The work of a block: a chunk of up to kHydroV consecutive vertices of one
+// dynamic membrane.  Its fits are the probes of the kv + 1 elements k0 - 1 ..
+// k0 + kv - 1 (each vertex needs the elements on both sides) and the kv
+// vertices; each (fit, stencil node) pair is one thread, so that the nine
+// node flows of a fit are read in parallel and the fit's sums are formed
+// afterwards in the fixed node order.
+constexpr int kHydroV = 16;
+constexpr int kHydroFits = 2 * kHydroV + 1;
+constexpr int kHydroThreads = 320;  // >= 9 kHydroFits = 297, a whole number of warps
+static_assert(9 * kHydroFits <= kHydroThreads, "one thread per (fit, node)");
+
+// node-flow products of one (fit, node) pair: a probe's MLS rows times (p, u, u, v, v)
+// (value of p, x and y derivatives of u and of v), or a vertex's shape
+// function times (u, v)
 template <typename S, typename E>
-__device__ void probe_fit(const MarkerArgs& a, const HydroArgs& h, E qx, E qy, typename Storage<S>::C& p,
-                          typename Storage<S>::C& dux, typename Storage<S>::C& duy,
-                          typename Storage<S>::C& dvx, typename Storage<S>::C& dvy) {
+__device__ __forceinline__ void probe_part(const MarkerArgs& a, const HydroArgs& h, E qx, E qy, int b, int q,
+                                           typename Storage<S>::C (&part)[5]) {
     using C = typename Storage<S>::C;
     const Stencil<C> st = stencil_at<C, E>(a, qx, qy);
     C M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+    for (int bb = 0; bb < 3; ++bb)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const C w = st.rowok[b] ? st.wx[q] * st.wy[b] : C(0);
+        for (int qq = 0; qq < 3; ++qq) {
+            const C w = st.rowok[bb] ? st.wx[qq] * st.wy[bb] : C(0);
             M00 += w;
-            M01 += w * st.rx[q];
-            M02 += w * st.ry[b];
-            M11 += w * st.rx[q] * st.rx[q];
-            M12 += w * st.rx[q] * st.ry[b];
-            M22 += w * st.ry[b] * st.ry[b];
+            M01 += w * st.rx[qq];
+            M02 += w * st.ry[bb];
+            M11 += w * st.rx[qq] * st.rx[qq];
+            M12 += w * st.rx[qq] * st.ry[bb];
+            M22 += w * st.ry[bb] * st.ry[bb];
         }
-    // inverse of the symmetric moment matrix by its adjugate
+#pragma unroll
+    for (int r = 0; r < 5; ++r) part[r] = C(0);
+    const NodeOf<C> nd = node_of<C>(st, b, q);
+    if (!nd.rowok) return;
+    int i, j;
+    stencil_node<C>(a, st, b, q, i, j);
+    C pk, uk, vk;
+    node_flow<S>(a, h, i, j, pk, uk, vk);
+    const C w = nd.wx * nd.wy;
+    // inverse of the symmetric moment matrix by its adjugate; with one fluid
+    // row (or none) the y derivative is undetermined: the value falls back to
+    // the normalised weights, the gradient to zero
     const C c00 = M11 * M22 - M12 * M12;
     const C c01 = -(M01 * M22 - M12 * M02);
     const C c02 = M01 * M12 - M11 * M02;
-    const C c11 = M00 * M22 - M02 * M02;
-    const C c12 = -(M00 * M12 - M01 * M02);
-    const C c22 = M00 * M11 - M01 * M01;
     const C det = M00 * c00 + M01 * c01 + M02 * c02;
-    // one fluid row (or none) leaves the y derivative undetermined: the value
-    // falls back to the normalised weights, the gradient to zero
-    const bool solve = st.nrow >= 2 && det > C(1e-10);
-    p = dux = duy = dvx = dvy = C(0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        if (!st.rowok[b]) continue;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            int i, j;
-            stencil_node<C>(a, st, b, q, i, j);
-            C pk, uk, vk;
-            node_flow<S>(a, h, i, j, pk, uk, vk);
-            const C w = st.wx[q] * st.wy[b];
-            if (solve) {
-                const C f0 = w * (c00 + c01 * st.rx[q] + c02 * st.ry[b]) / det;
-                const C f1 = w * (c01 + c11 * st.rx[q] + c12 * st.ry[b]) / det;
-                const C f2 = w * (c02 + c12 * st.rx[q] + c22 * st.ry[b]) / det;
-                p += f0 * pk;
-                dux += f1 * uk;
-                duy += f2 * uk;
-                dvx += f1 * vk;
-                dvy += f2 * vk;
-            } else {
-                p += (M00 > C(0) ? w / M00 : C(0)) * pk;
-            }
-        }
+    if (st.nrow >= 2 && det > C(1e-10)) {
+        const C c11 = M00 * M22 - M02 * M02;
+        const C c12 = -(M00 * M12 - M01 * M02);
+        const C c22 = M00 * M11 - M01 * M01;
+        const C f0 = w * (c00 + c01 * nd.rx + c02 * nd.ry) / det;
+        const C f1 = w * (c01 + c11 * nd.rx + c12 * nd.ry) / det;
+        const C f2 = w * (c02 + c12 * nd.rx + c22 * nd.ry) / det;
+        part[0] = f0 * pk;
+        part[1] = f1 * uk;
+        part[2] = f2 * uk;
+        part[3] = f1 * vk;
+        part[4] = f2 * vk;
+    } else {
+        part[0] = (M00 > C(0) ? w / M00 : C(0)) * pk;
     }
 }
 
-// the flow interpolated at a vertex with the IB shape functions (Roma weights
-// on the full stencil; near a wall the MLS value row, as in the force kernel)
+// the IB shape function of a vertex at one stencil node (Roma weights on the
+// full stencil; near a wall the MLS value row, as in the force kernel) times
+// the node's (u, v)
 template <typename S, typename E>
-__device__ void vertex_flow(const MarkerArgs& a, const HydroArgs& h, E xv, E yv, typename Storage<S>::C& Ux,
-                            typename Storage<S>::C& Uy) {
+__device__ __forceinline__ void vertex_part(const MarkerArgs& a, const HydroArgs& h, E xv, E yv, int b, int q,
+                                            typename Storage<S>::C (&part)[5]) {
     using C = typename Storage<S>::C;
     const Stencil<C> st = stencil_at<C, E>(a, xv, yv);
-    C w[9];
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) w[b * 3 + q] = st.rowok[b] ? st.wx[q] * st.wy[b] : C(0);
+    for (int r = 0; r < 5; ++r) part[r] = C(0);
+    const NodeOf<C> nd = node_of<C>(st, b, q);
+    if (!nd.rowok) return;
+    C w = nd.wx * nd.wy;
     if (st.nrow < 3) {
         C M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0, sw = 0;
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
+        for (int bb = 0; bb < 3; ++bb)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const C ww = w[b * 3 + q];
+            for (int qq = 0; qq < 3; ++qq) {
+                const C ww = st.rowok[bb] ? st.wx[qq] * st.wy[bb] : C(0);
                 sw += ww;
                 M00 += ww;
-                M01 += ww * st.rx[q];
-                M02 += ww * st.ry[b];
-                M11 += ww * st.rx[q] * st.rx[q];
-                M12 += ww * st.rx[q] * st.ry[b];
-                M22 += ww * st.ry[b] * st.ry[b];
+                M01 += ww * st.rx[qq];
+                M02 += ww * st.ry[bb];
+                M11 += ww * st.rx[qq] * st.rx[qq];
+                M12 += ww * st.rx[qq] * st.ry[bb];
+                M22 += ww * st.ry[bb] * st.ry[bb];
             }
         const C c0 = M11 * M22 - M12 * M12;
         const C c1 = -(M01 * M22 - M12 * M02);
         const C c2 = M01 * M12 - M11 * M02;
         const C det = M00 * c0 + M01 * c1 + M02 * c2;
-        if (det > C(1e-10)) {
-#pragma unroll
-            for (int b = 0; b < 3; ++b)
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    w[b * 3 + q] = w[b * 3 + q] * (c0 + c1 * st.rx[q] + c2 * st.ry[b]) / det;
-        } else if (sw > C(0)) {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) w[q] = w[q] / sw;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) w[q] = C(0);
-        }
+        if (det > C(1e-10)) w = w * (c0 + c1 * nd.rx + c2 * nd.ry) / det;
+        else w = sw > C(0) ? w / sw : C(0);
     }
-    Ux = Uy = C(0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-        if (!st.rowok[b]) continue;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            int i, j;
-            stencil_node<C>(a, st, b, q, i, j);
-            C pk, uk, vk;
-            node_flow<S>(a, h, i, j, pk, uk, vk);
-            Ux += w[b * 3 + q] * uk;
-            Uy += w[b * 3 + q] * vk;
-        }
-    }
+    int i, j;
+    stencil_node<C>(a, st, b, q, i, j);
+    C pk, uk, vk;
+    node_flow<S>(a, h, i, j, pk, uk, vk);
+    part[0] = w * uk;
+    part[1] = w * vk;
 }
 
 template <typename S>
 __global__ void __launch_bounds__(kHydroThreads) k_hydro(const MarkerArgs a, const HydroArgs h) {
     using C = typename Storage<S>::C;
     using E = typename Ext<C>::E;
-    const int m = h.dyn_mem[blockIdx.x];
+    const int4 u = h.units[blockIdx.x];
+    const int m = u.x, k0 = u.y, kv = u.z;
     const int off = a.mem_off[m], n = a.mem_n[m];
-    const int k = threadIdx.x;
-    const bool valid = k < n;
-    __shared__ C s_fx[kHydroThreads], s_fy[kHydroThreads], s_len[kHydroThreads];
-    E x, y;
-    if (valid) {
-        E xr, yr;
-        load_pos<C>(a, off + k, x, y);
-        load_pos<C>(a, off + (k + 1 == n ? 0 : k + 1), xr, yr);
-        const C ex = etoc(esub(xr, x)), ey = etoc(esub(yr, y));
-        const C len = sqrt(ex * ex + ey * ey);
-        const C nx = ey / len, ny = -ex / len;
-        // probe c_l + 1.2 n_l
-        const E qx = eaddc(emulc(eadd(x, xr), C(0.5)), C(1.2) * nx);
-        const E qy = eaddc(emulc(eadd(y, yr), C(0.5)), C(1.2) * ny);
-        C p, dux, duy, dvx, dvy;
-        probe_fit<S, E>(a, h, qx, qy, p, dux, duy, dvx, dvy);
-        const C nu = C(h.nu);
-        const C txx = C(2) * nu * dux, tyy = C(2) * nu * dvy, txy = nu * (duy + dvx);
-        s_fx[k] = (-p * nx + (txx * nx + txy * ny)) * len;
-        s_fy[k] = (-p * ny + (txy * nx + tyy * ny)) * len;
-        s_len[k] = len;
+    const int nel = kv + 1, nfit = 2 * kv + 1;
+    __shared__ C s_part[kHydroFits][9][5];
+    __shared__ C s_nx[kHydroV + 1], s_ny[kHydroV + 1], s_len[kHydroV + 1];
+    __shared__ C s_fx[kHydroV + 1], s_fy[kHydroV + 1], s_ux[kHydroV], s_uy[kHydroV];
+    const int t = threadIdx.x;
+    const int fit = t / 9, node = t - 9 * (t / 9);
+    const int b = node / 3, q = node - 3 * (node / 3);
+
+    // ---- one (fit, node) pair per thread
+    if (fit < nfit) {
+        C part[5];
+        if (fit < nel) {
+            // element e = (k0 - 1 + fit) mod n between vertices e and e + 1:
+            // outward normal, length, probe c_e + 1.2 n_e
+            int e = k0 - 1 + fit;
+            e = e < 0 ? e + n : (e >= n ? e - n : e);
+            E x0, y0, x1, y1;
+            load_pos<C>(a, off + e, x0, y0);
+            load_pos<C>(a, off + (e + 1 == n ? 0 : e + 1), x1, y1);
+            const C ex = etoc(esub(x1, x0)), ey = etoc(esub(y1, y0));
+            const C len = sqrt(ex * ex + ey * ey);
+            const C nx = ey / len, ny = -ex / len;
+            const E qx = eaddc(emulc(eadd(x0, x1), C(0.5)), C(1.2) * nx);
+            const E qy = eaddc(emulc(eadd(y0, y1), C(0.5)), C(1.2) * ny);
+            probe_part<S, E>(a, h, qx, qy, b, q, part);
+            if (node == 0) {
+                s_nx[fit] = nx;
+                s_ny[fit] = ny;
+                s_len[fit] = len;
+            }
+        } else {
+            E xv, yv;
+            load_pos<C>(a, off + k0 + fit - nel, xv, yv);
+            vertex_part<S, E>(a, h, xv, yv, b, q, part);
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r) s_part[fit][node][r] = part[r];
     }
     __syncthreads();
-    if (!valid) return;
-    const int kl = k == 0 ? n - 1 : k - 1;
-    const int v = off + k;
-    C* H = static_cast<C*>(a.Hf);
-    C* D = static_cast<C*>(a.Dib);
-    const C* V = static_cast<const C*>(a.V);
-    H[2 * (size_t)v] = C(0.5) * (s_fx[kl] + s_fx[k]);
-    H[2 * (size_t)v + 1] = C(0.5) * (s_fy[kl] + s_fy[k]);
-    C Ux, Uy;
-    vertex_flow<S, E>(a, h, x, y, Ux, Uy);
-    const C dV = C(0.5) * (s_len[kl] + s_len[k]);
-    D[2 * (size_t)v] = C(2) * dV * (V[2 * (size_t)v] - Ux);
-    D[2 * (size_t)v + 1] = C(2) * dV * (V[2 * (size_t)v + 1] - Uy);
+
+    // ---- per fit: the sums over the nine nodes in node order
+    if (t < nfit) {
+        C sum[5] = {C(0), C(0), C(0), C(0), C(0)};
+        for (int k = 0; k < 9; ++k)
+#pragma unroll
+            for (int r = 0; r < 5; ++r) sum[r] += s_part[t][k][r];
+        if (t < nel) {
+            // Eqs. hydroForP / hydroForNu: (-p n + tau . n) l, tau = nu (grad u + grad u^T)
+            const C p = sum[0], dux = sum[1], duy = sum[2], dvx = sum[3], dvy = sum[4];
+            const C nu = C(h.nu), nx = s_nx[t], ny = s_ny[t], len = s_len[t];
+            const C txx = C(2) * nu * dux, tyy = C(2) * nu * dvy, txy = nu * (duy + dvx);
+            s_fx[t] = (-p * nx + (txx * nx + txy * ny)) * len;
+            s_fy[t] = (-p * ny + (txy * nx + tyy * ny)) * len;
+        } else {
+            s_ux[t - nel] = sum[0];
+            s_uy[t - nel] = sum[1];
+        }
+    }
+    __syncthreads();
+
+    // ---- per vertex: half of both adjacent element forces, and the forcing term
+    if (t < kv) {
+        const int v = off + k0 + t;  // elements k0 + t - 1 and k0 + t are fits t and t + 1
+        C* H = static_cast<C*>(a.Hf);
+        C* D = static_cast<C*>(a.Dib);
+        const C* V = static_cast<const C*>(a.V);
+        H[2 * (size_t)v] = C(0.5) * (s_fx[t] + s_fx[t + 1]);
+        H[2 * (size_t)v + 1] = C(0.5) * (s_fy[t] + s_fy[t + 1]);
+        const C dV = C(0.5) * (s_len[t] + s_len[t + 1]);
+        D[2 * (size_t)v] = C(2) * dV * (V[2 * (size_t)v] - s_ux[t]);
+        D[2 * (size_t)v + 1] = C(2) * dV * (V[2 * (size_t)v + 1] - s_uy[t]);
+    }
 }
 
+int hydro_chunk() { return kHydroV; }
+
 cudaError_t launch_hydro(lbib_precision prec, const MarkerArgs& a, const HydroArgs& h, cudaStream_t s) {
-    if (h.ndyn == 0) return cudaSuccess;
-    if (h.threads < 32 || h.threads > kHydroThreads || h.threads % 32) return cudaErrorInvalidValue;
+    if (h.nunits == 0) return cudaSuccess;
     switch (prec) {
-        case LBIB_F64: k_hydro<double><<<h.ndyn, h.threads, 0, s>>>(a, h); break;
-        case LBIB_F32: k_hydro<float><<<h.ndyn, h.threads, 0, s>>>(a, h); break;
-        case LBIB_F32_STORE_F16: k_hydro<__half><<<h.ndyn, h.threads, 0, s>>>(a, h); break;
-        case LBIB_F32_STORE_BF16: k_hydro<__nv_bfloat16><<<h.ndyn, h.threads, 0, s>>>(a, h); break;
+        case LBIB_F64: k_hydro<double><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
+        case LBIB_F32: k_hydro<float><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
+        case LBIB_F32_STORE_F16: k_hydro<__half><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
+        case LBIB_F32_STORE_BF16: k_hydro<__nv_bfloat16><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

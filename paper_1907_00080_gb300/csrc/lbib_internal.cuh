@@ -204,9 +204,8 @@ struct HydroArgs {
     float bbf_bot, bbf_top;
     double gx, gy;            // body force (u = (sum f e + G_body / 2) / rho)
     double nu;                // (tau - 1/2) / 3
-    int ndyn;                 // dynamic membranes, one block each
-    const int* dyn_mem;       // [ndyn] their ids
-    int threads;              // block size: the longest dynamic ring rounded up to a warp
+    int nunits;               // blocks: chunks of hydro_chunk() vertices of the dynamic membranes
+    const int4* units;        // [nunits] {membrane, first local vertex, vertex count, 0}
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
@@ -249,6 +248,7 @@ cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas
 // dynamic_kernels.cu: hydrodynamic stresses and forcing terms of the dynamic
 // particles at the start of a step (before launch_forces)
 cudaError_t launch_hydro(lbib_precision prec, const MarkerArgs& a, const HydroArgs& h, cudaStream_t s);
+int hydro_chunk();  // vertices per block of the hydrodynamic kernel
 // observables.cu: 8 doubles per membrane (see lbib_membrane_observables)
 cudaError_t launch_observables(lbib_precision prec, const MarkerArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);
@@ -292,8 +292,8 @@ struct lbib_ctx {
     std::vector<double> h_rhop;   // rho_P / rho of each membrane (dynamic ones)
     int nmem = 0, nv = 0, nlig = 0;
     int ndyn = 0;                 // dynamic membranes
-    int* d_dyn_mem = nullptr;     // their ids (in the arena)
-    int dyn_threads = 0;
+    int4* d_hydro_units = nullptr; // chunks of their vertices (in the arena)
+    int n_hydro_units = 0;
     // receptors
     std::vector<double> h_rec;
     lbib_bond_params bp{};

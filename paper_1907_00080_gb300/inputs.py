@@ -365,7 +365,8 @@ def adjoint_capillary_320x160(ks=None, kb=None, sigma_lu=None, release_y=8.5, se
     return wl
 
 
-def couette_cfl_600x200(precision="f32", sigma=1.0, carrier="rigid", gap=1.0, seed=0, steps=20000) -> Workload:
+def couette_cfl_600x200(precision="f32", sigma=1.0, carrier="rigid", gap=1.0, seed=0, steps=20000,
+                        carrier_model="kinematic") -> Workload:
     """Adhesion in the cell-free layer (Sec. 4): planar Couette flow at
     Re = H_CFL u_w / nu = 0.003 in a channel of H_CFL = 3 um = 200 lu
     (dx = 15 nm) and length 3 H_CFL, periodic in x, the upper wall moving at
@@ -373,21 +374,27 @@ def couette_cfl_600x200(precision="f32", sigma=1.0, carrier="rigid", gap=1.0, se
     One 1 um carrier (radius 33.3 lu, 210 markers, a ligand on every other
     element) starts with its lowest marker `gap` lu above the lower wall at a
     random x; rigid (Ca = 0, rigid-projected) or soft (Ca = 1e-2 on the wall
-    speed).  Bonds use the physical cut-off y_cr = 25 nm = 1.67 lu and
-    y_eq = y_cr / 2 (Sec. 2.2); sigma in units rho nu^2 / H_CFL."""
+    speed); with carrier_model "dynamic" the carrier follows the dynamic IB of
+    Sec. 2.4 instead (rigid or deformable, rho_P / rho = 1.1).  Bonds use the
+    physical cut-off y_cr = 25 nm = 1.67 lu and y_eq = y_cr / 2 (Sec. 2.2);
+    sigma in units rho nu^2 / H_CFL."""
+    if carrier_model not in ("kinematic", "dynamic"):
+        raise ValueError(carrier_model)
     nx, ny = 600, 200
     rng = np.random.Generator(np.random.PCG64(seed))
     u_w = u_max_for_re(0.003, ny)
     r = 33.3
     xy = circle(rng.uniform(0.0, nx), -0.5 + gap + r, r, 210)
     xy[:, 1] += (-0.5 + gap) - xy[:, 1].min()
+    dyn = carrier_model == "dynamic"
     if carrier == "rigid":
-        ks, kind = ks_for_ca(1e-2, u_w), 1
+        ks, kind = ks_for_ca(1e-2, u_w), 3 if dyn else 1
     else:
-        ks, kind = ks_for_ca(1e-2, u_w), 0
+        ks, kind = ks_for_ca(1e-2, u_w), 2 if dyn else 0
     mem = Membrane(xy=xy, ks=ks, kb=0.05 * ks * r * r, ka=1.0, kind=kind,
                    ligands=np.arange(0, 210, 2, dtype=np.int32))
-    wl = Workload(name="couette_cfl_600x200_%s_sigma%g" % (carrier, sigma), nx=nx, ny=ny, body_force=(0.0, 0.0),
+    name = "couette_cfl_600x200_%s%s_sigma%g" % ("dynamic_" if dyn else "", carrier, sigma)
+    wl = Workload(name=name, nx=nx, ny=ny, body_force=(0.0, 0.0),
                   walls=1, init="couette", precision=precision, membranes=[mem],
                   receptors=wall_receptors(nx, ny, lower=True, upper=False),
                   sigma_lu=sigma_lattice(sigma, ny), seed=seed, steps=steps, wall_velocity=(0.0, u_w))

@@ -106,6 +106,7 @@ _SIGS = {
     "lbib_get_tiling": (_I, [_P, _I32P, _I32P]),
     "lbib_profile_fused": (_I, [_P, _I32, _DP]),
     "lbib_profile_kernels": (_I, [_P, _I32, _DP]),
+    "lbib_profile_hydro": (_I, [_P, _I32, _DP]),
     "lbib_kernels_per_step": (_I32, [_P]),
     "lbib_storage_scale_exponent": (_I32, [_P]),
     "lbib_last_error": (ctypes.c_char_p, [_P]),
@@ -296,6 +297,12 @@ def lbib_get_tiling(ctx):
 def lbib_profile_fused(ctx, reps):
     ms = np.zeros(1)
     _check(ctx, load().lbib_profile_fused(ctx, int(reps), _dptr(ms)))
+    return float(ms[0])
+
+
+def lbib_profile_hydro(ctx, reps):
+    ms = np.zeros(1)
+    _check(ctx, load().lbib_profile_hydro(ctx, int(reps), _dptr(ms)))
     return float(ms[0])
 
 

@@ -4,6 +4,7 @@
   python -m paper_1907_00080_gb300.profile_case --case capillary --steps 40
   python -m paper_1907_00080_gb300.profile_case --case adjoint --steps 40 --checkpoint-every 20
   python -m paper_1907_00080_gb300.profile_case --case fine --precision f16 --steps 20
+  python -m paper_1907_00080_gb300.profile_case --case dynamic --steps 40
 
 ``probe``: a channel of nx x ny nodes with soft circular carriers spread over
 it (the coarse capillary's share of nodes under a marker stencil), stepped twice, then ``--launches``
@@ -12,7 +13,9 @@ launches of the fused collide-stream kernel alone (``lbib_profile_fused``).
 (all kernels of the time step).  ``adjoint``: the 320 x 160 sensitivity case
 (FP64) recorded for ``--steps`` steps with checkpoints every
 ``--checkpoint-every`` steps, then one backward sweep.  ``fine``: the 2000 x 667
-fine capillary stepped ``--steps`` time steps.  Prints one JSON line.
+fine capillary stepped ``--steps`` time steps.  ``dynamic``: the 640 x 160
+capillary with dynamic carriers (Sec. 2.4) stepped ``--steps`` time steps.
+Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -47,7 +50,7 @@ def probe_workload(nx, ny, precision, n_carriers=None, seed=1):
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--case", choices=["probe", "capillary", "adjoint", "fine"], default="probe")
+    p.add_argument("--case", choices=["probe", "capillary", "adjoint", "fine", "dynamic"], default="probe")
     p.add_argument("--nx", type=int, default=8192)
     p.add_argument("--ny", type=int, default=1024)
     p.add_argument("--precision", default="f32")
@@ -83,6 +86,8 @@ def main(argv=None):
     else:
         if args.case == "fine":
             wl = inputs.fine_capillary_2000x667(args.precision)
+        elif args.case == "dynamic":
+            wl = inputs.coarse_capillary_640x160(args.precision, carrier_model="dynamic")
         else:
             wl = inputs.coarse_capillary_640x160(args.precision)
         sim = lbib.Simulation(wl, tiling=tiling)

@@ -71,6 +71,25 @@ def test_dynamic_carriers_match_the_oracle(prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_coarse_capillary_with_dynamic_carriers(prec):
+    """The 640 x 160 capillary (8 red cells, 2 rigid and 2 deformable dynamic
+    carriers, receptors on both walls, stress kinetics) in the tiling the
+    benchmark uses, 100 steps against the oracle."""
+    from paper_1907_00080_gb300 import tuning
+    wl = inputs.coarse_capillary_640x160(precision=prec, carrier_model="dynamic")
+    wl.bonds = dict(inputs.STRESS_BONDS)
+    s = lb().Simulation(wl, tiling=tuning.bench_tiling(wl))
+    r = make_oracle(wl)
+    for _ in range(2):
+        s.step(50)
+        r.step(50)
+        compare(s, r, prec, "step %d" % r.step_count)
+        if prec == "f64":
+            np.testing.assert_array_equal(s.bonds(), r.bonds())
+    s.close()
+
+
 def test_probes_outside_the_fluid():
     """A rigid carrier 0.35 lu above the wall and a deformable one near the
     upper wall: probes of their outer elements have one fluid row or none
@@ -172,7 +191,23 @@ def test_refusals():
     s.close()
     big = inputs.Workload(name="big", nx=64, ny=64, init="rest", precision="f64",
                           membranes=[inputs.Membrane(xy=inputs.circle(32.0, 32.0, 20.0, 300), ks=1e-3, kb=0.0,
-                                                     ka=1.0, kind=2)])
+                                                     ka=1.0, kind=3)])
     with pytest.raises(L.LbibError) as ei:
-        L.Simulation(big)
+        L.Simulation(big)  # a rigid dynamic ring is advanced by one block
     assert ei.value.status == L.LBIB_E_INVALID
+
+
+def test_large_deformable_particle_matches_the_oracle():
+    """A deformable dynamic particle of 300 vertices (19 blocks of the
+    hydrodynamic kernel, the last one ragged) in a periodic box."""
+    wl = inputs.Workload(name="big_soft", nx=96, ny=80, init="rest", walls=0, body_force=(1e-6, 0.0),
+                         precision="f64",
+                         membranes=[inputs.Membrane(xy=inputs.circle(40.0, 40.0, 30.0, 300), ks=1e-3, kb=1e-4,
+                                                    ka=1.0, kind=2)])
+    s = lb().Simulation(wl)
+    r = make_oracle(wl)
+    for k in (1, 20):
+        s.step(k)
+        r.step(k)
+        compare(s, r, "f64", "step %d" % r.step_count)
+    s.close()
