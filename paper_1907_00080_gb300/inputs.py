@@ -297,8 +297,22 @@ def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carrie
                   walls=1, init="poiseuille", precision=precision, membranes=mems,
                   receptors=wall_receptors(nx, ny), sigma_lu=sigma_lattice(sigma, ny),
                   seed=seed, steps=steps)
-    wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
+    if bonds == "physical":
+        wl.bonds = physical_bonds(dx_nm=10000.0 / ny)
+    else:
+        wl.bonds = dict(STRESS_BONDS if bonds == "stress" else DEFAULT_BONDS)
     return wl
+
+
+def physical_bonds(dx_nm: float) -> dict:
+    """The paper's own cut-off y_cr = 25 nm (Sec. 2.2) in lattice units, with
+    y_eq = y_cr / 2 and the default kinetics; only meaningful where the mesh
+    resolves it (dx = 15 nm: 1.67 lu).  At dx = 62.5 nm it would be 0.4 lu,
+    below the IB resolution, which is why the coarse mesh keeps 1.5 lu."""
+    y_cr = 25.0 / dx_nm
+    if y_cr < 1.0:
+        raise ValueError("y_cr = 25 nm is %.2f lu on this mesh: below the IB resolution" % y_cr)
+    return dict(DEFAULT_BONDS, d_cut=y_cr, y_eq=0.5 * y_cr, d_break=2.0 * y_cr)
 
 
 def coarse_capillary_640x160(precision="f32", seed=0, steps=200000, carrier_model="kinematic") -> Workload:
@@ -312,7 +326,8 @@ def fine_capillary_2000x667(precision="f32", sigma=1.0, carriers="rigid", seed=0
     (8 um major axis -> alpha = 266.7 lu, 1700 markers each, about 19 % 2-D
     haematocrit), 3 carriers of 1 um diameter (radius 33.3 lu, 210 markers,
     105 ligands), all rigid (Ca = 0) or all soft (Ca = 1e-2), receptors on both
-    walls, sigma in {0.5, 1, 2}."""
+    walls, sigma in {0.5, 1, 2}.  bonds="physical" uses the paper's cut-off
+    y_cr = 25 nm = 1.67 lu, which this mesh resolves."""
     nx, ny = 2000, 667
     ca = 0.0 if carriers == "rigid" else 1e-2
     return capillary(nx=nx, ny=ny, n_rbc=4, rbc_alpha=266.7, rbc_markers=1700, n_carriers=3,

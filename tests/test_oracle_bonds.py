@@ -163,3 +163,18 @@ def test_just_ruptured_receptor_is_not_rebound_in_the_same_step():
     assert list(s.bonds()) == [-1, -1]
     s.bonds_update(1)
     assert (s.bonds() >= 0).sum() <= 1
+
+
+def test_physical_cutoff_where_the_mesh_resolves_it():
+    """The paper's y_cr = 25 nm (Sec. 2.2) in lattice units: 1.67 lu at
+    dx = 15 nm (fine mesh), refused at dx = 62.5 nm (0.4 lu, below the IB
+    resolution); y_eq = y_cr / 2."""
+    from paper_1907_00080_gb300 import inputs
+    b = inputs.physical_bonds(15.0)
+    assert b["d_cut"] == pytest.approx(25.0 / 15.0, rel=1e-15)
+    assert b["y_eq"] == pytest.approx(12.5 / 15.0, rel=1e-15)
+    assert b["d_break"] == pytest.approx(50.0 / 15.0, rel=1e-15)
+    with pytest.raises(ValueError):
+        inputs.physical_bonds(62.5)
+    wl = inputs.fine_capillary_2000x667("f32", bonds="physical")
+    assert wl.bonds["d_cut"] == pytest.approx(25.0 / (10000.0 / 667), rel=1e-12)  # dx = 10 um / 667
