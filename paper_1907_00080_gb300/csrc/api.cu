@@ -734,6 +734,8 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.bbf_bot = (float)l.bb_bot;
     l.bbf_top = (float)l.bb_top;
     l.fields_only = 0;
+    // the two population buffers and the force field well inside the 129 MB L2
+    l.g_prefetch = (size_t)c->nx * c->ny * (2 * 9 * c->pop_elem + sizeof(longlong2)) <= (size_t)64 << 20;
     l.tile_w = c->tile_w;
     l.tile_h = c->tile_h;
     l.tiles_x = c->tiles_x;

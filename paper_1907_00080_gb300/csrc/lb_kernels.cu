@@ -47,6 +47,17 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     const S* __restrict__ src = static_cast<const S*>(a.src);
     const float inv = a.inv_scale;
 
+    // ---- on lattices that stay in L2, the spread force of every node is read
+    // up front (the field is zero outside the tiles this step's spreading
+    // touched), so that its latency overlaps the population loads instead of
+    // following the tile flag
+    longlong2 gpre[VEC];
+    const bool pre_g = HAS_IB && a.g_prefetch && ok;
+    if (pre_g) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) gpre[k] = a.gsum[(size_t)y * nx + x0 + k];
+    }
+
     // ---- pull streaming (Eq. BGK left side) with half-way bounce-back
     C f[9][VEC];
 #pragma unroll
@@ -115,7 +126,7 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
         if (flagged && ok) {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-                const longlong2 g = a.gsum[node + k];
+                const longlong2 g = pre_g ? gpre[k] : a.gsum[node + k];
                 Gx[k] += from_fix<C>(g.x);
                 Gy[k] += from_fix<C>(g.y);
             }

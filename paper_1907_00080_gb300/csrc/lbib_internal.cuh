@@ -101,6 +101,7 @@ struct LbArgs {
                            // diagonal population bounced back there gains cx(i) times it
     float bbf_bot, bbf_top;  // the same rounded to FP32 (no FP64 conversion in the FP32 kernels)
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
+    int g_prefetch;        // row tiles: read the spread force of every node up front (L2-resident lattices)
     int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags
     int* status;           // device status word (StatusBits)
 };
