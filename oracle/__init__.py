@@ -106,6 +106,7 @@ _SIGS = {
     "orc_get_hydro_forces": (None, [_P, _DP]),
     "orc_get_ib_forces": (None, [_P, _DP]),
     "orc_get_rigid_state": (None, [_P, _I, _DP]),
+    "orc_set_rigid_state": (None, [_P, _I, _DP]),
     "orc_tangent_create": (_P, [_P]),
     "orc_tangent_destroy": (None, [_P]),
     "orc_tangent_seed": (None, [_P, _DP, _DP, _D, _DP, _DP, _DP]),
@@ -413,6 +414,10 @@ class OracleSim:
         f = np.zeros((self.nv, 2))
         lib().orc_get_ib_forces(self._s, _dp(f))
         return f
+
+    def set_rigid_state(self, m, state):
+        """(u, v, u_prev, v_prev, omega, omega_prev); vertex velocities follow"""
+        lib().orc_set_rigid_state(self._s, int(m), _dp(_f64(state)))
 
     def rigid_state(self, m):
         """(u, v, u_prev, v_prev, omega, omega_prev) of a rigid dynamic membrane"""

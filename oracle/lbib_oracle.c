@@ -1207,6 +1207,20 @@ void orc_get_ib_forces(const orc_sim *s, double *fxy) {
 void orc_get_rigid_state(const orc_sim *s, int m, double *out) {
     for (int k = 0; k < 6; ++k) out[k] = s->mem_rb[6 * m + k];
 }
+/* set the rigid state (u, v, u_prev, v_prev, omega, omega_prev) of a rigid
+ * dynamic membrane and the matching vertex velocities u + omega x r (r from
+ * the area centroid) */
+void orc_set_rigid_state(orc_sim *s, int m, const double *in) {
+    int off = s->mem_off[m], n = s->mem_n[m];
+    for (int k = 0; k < 6; ++k) s->mem_rb[6 * m + k] = in[k];
+    double A, cx, cy, J;
+    orc_ring_mass_properties(n, s->x + off, s->y + off, &A, &cx, &cy, &J);
+    for (int v = off; v < off + n; ++v) {
+        double rx = (s->x[v] - s->x[off]) - cx, ry = (s->y[v] - s->y[off]) - cy;
+        s->vx[v] = in[0] - in[4] * ry;
+        s->vy[v] = in[1] + in[4] * rx;
+    }
+}
 void orc_get_bonds(const orc_sim *s, int *bond_of_lig) {
     for (int l = 0; l < s->nlig; ++l) bond_of_lig[l] = s->bond_of_lig[l];
 }

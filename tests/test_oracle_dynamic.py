@@ -300,3 +300,28 @@ def test_soft_velocity_is_exact_for_quadratic_paths():
         want = h if k == 0 else c * (k + 0.5) + h
         np.testing.assert_allclose(V, np.tile(want, (nv, 1)), rtol=1e-9, atol=1e-17)
     np.testing.assert_allclose(s.markers() - xy, np.tile(c * K * (K - 1) / 2 + h * K, (nv, 1)), rtol=1e-10)
+
+
+@pytest.mark.parametrize("walls", [0, 1])
+def test_drag_opposes_the_motion_of_a_rigid_particle(walls):
+    """In a fluid at rest the probe tractions and the forcing term must slow a
+    rigid particle down.  Its spin decays monotonically and does not reverse.
+    Its translation stays below the initial speed and does not reverse: the
+    fluid only ever receives energy from the particle.  It need not decay
+    monotonically, since the fluid first entrained by the forcing term pushes
+    back."""
+    s, m, xy = dynamic_ring(nx=64, ny=64, walls=walls, R=8.0, n=50, kind=3)
+    s.set_rigid_state(m, [0.0, 0.0, 0.0, 0.0, 1e-4, 1e-4])
+    last = 1e-4
+    for _ in range(6):
+        s.step(50)
+        om = s.rigid_state(m)[4]
+        assert 0.0 < om < last
+        last = om
+    s, m, xy = dynamic_ring(nx=64, ny=64, walls=walls, R=8.0, n=50, kind=3)
+    s.set_rigid_state(m, [1e-3, 0.0, 1e-3, 0.0, 0.0, 0.0])
+    for _ in range(8):
+        s.step(25)
+        u = s.rigid_state(m)[0]
+        assert 0.0 < u < 1e-3
+    assert u < 0.5e-3
