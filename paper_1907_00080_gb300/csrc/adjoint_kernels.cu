@@ -427,7 +427,6 @@ cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
     const TangentArgs& t = a.t;
     const size_t N = (size_t)t.m.nx * t.m.ny;
     const int nvb = (t.m.nv + 31) / 32;
-    cudaError_t e;
     if (t.m.nv > 0) k_a_interp<<<dim3(nvb, 9), 32, 0, s>>>(a);
     // FP64-bound: 128-thread blocks, up to 16 per SM
     k_a_collide<<<(int)std::min<size_t>((N + 127) / 128, 152 * 16), 128, 0, s>>>(a);

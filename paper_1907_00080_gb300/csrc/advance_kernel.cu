@@ -89,7 +89,9 @@ __device__ __forceinline__ void ring_boxes(const MarkerArgs& a, int m, int n, in
     }
 }
 
-template <typename C>
+// DYN: the context holds dynamic particles (without them their paths are not
+// compiled into the kernel, which keeps its code small)
+template <typename C, bool DYN>
 __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     using E = typename Ext<C>::E;
     const int u = blockIdx.x;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         my_bond = a.bond_of_lig[my_rec.x];
     }
 
-    if (kind == LBIB_MEMBRANE_KINEMATIC || kind == LBIB_MEMBRANE_DYNAMIC) {
+    if (kind == LBIB_MEMBRANE_KINEMATIC || (DYN && kind == LBIB_MEMBRANE_DYNAMIC)) {
         // ---- kinematic or deformable dynamic chunk: one vertex per thread
         const bool valid = tid < kn;
         const int v = off + k0 + (valid ? tid : 0);
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
             interp_vertex<C>(a, v, Ux, Uy);
             U[2 * v] = Ux;
             U[2 * v + 1] = Uy;
-            if (kind == LBIB_MEMBRANE_DYNAMIC) {
+            if (DYN && kind == LBIB_MEMBRANE_DYNAMIC) {
                 verlet<C>(a, m, v, x, y, xp, yp, Ux, Uy, step, xn, yn);
             } else {
                 bdf2<C>(x, xp, Ux, step, xn);
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
         shfl_e(gx, xn, lane & ~(kSegV - 1));
         shfl_e(gy, yn, lane & ~(kSegV - 1));
         seg_box_regs<C>(a, sg, lane, valid ? xn : gx, valid ? yn : gy);
-    } else if (kind == LBIB_MEMBRANE_DYNAMIC_RIGID) {
+    } else if (DYN && kind == LBIB_MEMBRANE_DYNAMIC_RIGID) {
         // ---- rigid dynamic particle, the whole ring in this block: Eqs.
         // linearVelRig / angularVelRig.  F and its moment M about the area
         // centroid give du/dt = F/m, domega/dt = M/I; the body translates by u
@@ -369,8 +371,13 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
 
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
     if (a.adv_threads < kChunkV || a.adv_threads > kAdvThreads || a.adv_threads % 32) return cudaErrorInvalidValue;
-    if (prec == LBIB_F64) k_advance<double><<<a.nau, a.adv_threads, 0, s>>>(a);
-    else k_advance<float><<<a.nau, a.adv_threads, 0, s>>>(a);
+    if (prec == LBIB_F64) {
+        if (a.has_dyn) k_advance<double, true><<<a.nau, a.adv_threads, 0, s>>>(a);
+        else k_advance<double, false><<<a.nau, a.adv_threads, 0, s>>>(a);
+    } else {
+        if (a.has_dyn) k_advance<float, true><<<a.nau, a.adv_threads, 0, s>>>(a);
+        else k_advance<float, false><<<a.nau, a.adv_threads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

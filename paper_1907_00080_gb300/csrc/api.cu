@@ -675,7 +675,7 @@ static lbib_status finalize(lbib_ctx* c) {
         a.adv_threads = (longest + 31) / 32 * 32;
     }
     // dynamic particles: states at rest, the ids for the hydrodynamic kernel
-    a.V = V; a.Hf = Hf; a.Dib = Dib; a.rb = rb; a.mem_dyn = mem_dyn;
+    a.V = V; a.Hf = Hf; a.Dib = Dib; a.rb = rb; a.mem_dyn = mem_dyn; a.has_dyn = c->ndyn > 0 ? 1 : 0;
     c->d_hydro_units = reinterpret_cast<int4*>(d_hydro_units);
     c->n_hydro_units = (int)(hydro_units.size() / 4);
     a.fu = reinterpret_cast<const int4*>(d_fu);
@@ -735,7 +735,10 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.bbf_top = (float)l.bb_top;
     l.fields_only = 0;
     // the two population buffers and the force field well inside the 129 MB L2
-    l.g_prefetch = (size_t)c->nx * c->ny * (2 * 9 * c->pop_elem + sizeof(longlong2)) <= (size_t)64 << 20;
+    // (not for ensemble members: together they leave L2, and the extra reads
+    // cost DRAM bandwidth)
+    l.g_prefetch = !c->no_g_prefetch &&
+                   (size_t)c->nx * c->ny * (2 * 9 * c->pop_elem + sizeof(longlong2)) <= (size_t)64 << 20;
     l.tile_w = c->tile_w;
     l.tile_h = c->tile_h;
     l.tiles_x = c->tiles_x;
@@ -785,6 +788,18 @@ static cudaError_t enqueue_step(lbib_ctx* c, int src, cudaStream_t s) {
     if ((e = launch_fused(c, l, s)) != cudaSuccess) return e;
     if (has_ib && (e = launch_advance(c->prec, a, s)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// discard the captured step graphs (they are captured again on next use)
+static void drop_graphs(lbib_ctx* c) {
+    for (int s = 0; s < 2; ++s)
+        for (int k = 0; k < 2; ++k) {
+            if (c->graph[s][k]) cudaGraphExecDestroy(c->graph[s][k]);
+            if (c->graph_tmpl[s][k]) cudaGraphDestroy(c->graph_tmpl[s][k]);
+            c->graph[s][k] = nullptr;
+            c->graph_tmpl[s][k] = nullptr;
+        }
+    c->graphs_ready = false;
 }
 
 static lbib_status build_graphs(lbib_ctx* c) {
@@ -1263,6 +1278,12 @@ extern "C" lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n,
         lbib_ctx* c = members[i];
         if (c->device != dev || c->poisoned) return LBIB_E_INVALID;
         lbib_status st = finalize(c);
+        if (st == LBIB_OK && !c->no_g_prefetch) {
+            // the members' row tiles read the force field only in flagged tiles
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBIB_E_CUDA;
+            c->no_g_prefetch = true;
+            drop_graphs(c);
+        }
         if (st == LBIB_OK) st = build_graphs(c);
         if (st != LBIB_OK) return st;
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBIB_E_CUDA;

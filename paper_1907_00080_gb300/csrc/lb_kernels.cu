@@ -35,8 +35,11 @@ __device__ __forceinline__ void load_pack(const S* __restrict__ row, int x0, boo
 // 32*VEC consecutive x of one row, so every row predicate is warp-uniform; the
 // x-shifted pulls load aligned vectors and take the single off-vector element
 // from the neighbouring lane (or, at the warp edge, with one scalar load).
-template <typename S, int VEC, bool WALLS, bool HAS_IB>
+// IB: 0 no markers; 1 the spread force read in the tiles the spreading
+// flagged; 2 the same, with every node's force read up front (see below)
+template <typename S, int VEC, bool WALLS, int IB>
 __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
+    constexpr bool HAS_IB = IB > 0;
     using C = typename Storage<S>::C;
     const int lane = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     // touched), so that its latency overlaps the population loads instead of
     // following the tile flag
     longlong2 gpre[VEC];
-    const bool pre_g = HAS_IB && a.g_prefetch && ok;
+    const bool pre_g = IB == 2 && a.g_prefetch && ok;
     if (pre_g) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) gpre[k] = a.gsum[(size_t)y * nx + x0 + k];
@@ -192,12 +195,17 @@ template <typename S, int VEC>
 static cudaError_t launch_lb_t(int ty, bool walls, bool has_ib, const LbArgs& a, cudaStream_t s) {
     dim3 block(32, ty);
     dim3 grid((a.nx + 32 * VEC - 1) / (32 * VEC), (a.ny + ty - 1) / ty);
+    // the up-front force read is its own instantiation: its registers would
+    // lower the occupancy of the plain form, which DRAM-bound runs need
+    const int ib = has_ib ? (a.g_prefetch ? 2 : 1) : 0;
     if (walls) {
-        if (has_ib) k_lb_step<S, VEC, true, true><<<grid, block, 0, s>>>(a);
-        else k_lb_step<S, VEC, true, false><<<grid, block, 0, s>>>(a);
+        if (ib == 2) k_lb_step<S, VEC, true, 2><<<grid, block, 0, s>>>(a);
+        else if (ib == 1) k_lb_step<S, VEC, true, 1><<<grid, block, 0, s>>>(a);
+        else k_lb_step<S, VEC, true, 0><<<grid, block, 0, s>>>(a);
     } else {
-        if (has_ib) k_lb_step<S, VEC, false, true><<<grid, block, 0, s>>>(a);
-        else k_lb_step<S, VEC, false, false><<<grid, block, 0, s>>>(a);
+        if (ib == 2) k_lb_step<S, VEC, false, 2><<<grid, block, 0, s>>>(a);
+        else if (ib == 1) k_lb_step<S, VEC, false, 1><<<grid, block, 0, s>>>(a);
+        else k_lb_step<S, VEC, false, 0><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -194,6 +194,7 @@ struct MarkerArgs {
     void* Dib;                // forcing term spread into the fluid (k_hydro)
     double* rb;               // [nmem][6] rigid state: u, v, u_prev, v_prev, omega, omega_prev
     const double* mem_dyn;    // [nmem][3] mass rho_P A_0, inertia rho_P J_0, vertex mass m / n
+    int has_dyn;              // 1 if any membrane is dynamic
 };
 
 // Arguments of the hydrodynamic-stress kernel: the populations the step
@@ -325,6 +326,7 @@ struct lbib_ctx {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraph_t graph_tmpl[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // kept for ensembles
     bool graphs_ready = false;
+    bool no_g_prefetch = false;  // set for ensemble members (see lb_args)
 
     std::string err;
 };
