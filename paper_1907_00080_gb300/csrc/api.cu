@@ -482,14 +482,14 @@ static lbib_status finalize(lbib_ctx* c) {
 
     // dynamic particles: mass rho_P A_0, inertia rho_P J_0 (J_0 the polar moment
     // of the rest polygon about its area centroid) and vertex mass per membrane
-    // and the blocks of the hydrodynamic kernel, {membrane, k0, count, 0}
+    // and the blocks of the hydrodynamic kernel, {k0, count, membrane offset, membrane size}
     std::vector<double> dyn_consts(3 * (size_t)std::max(nm, 1), 0.0);
     std::vector<int> hydro_units;
     for (int m = 0; m < nm; ++m) {
         if (!is_dynamic(c->h_mem_kind[m])) continue;
         const int n = c->h_mem_n[m];
         for (int k0 = 0; k0 < n; k0 += hydro_chunk())
-            hydro_units.insert(hydro_units.end(), {m, k0, std::min(hydro_chunk(), n - k0), 0});
+            hydro_units.insert(hydro_units.end(), {k0, std::min(hydro_chunk(), n - k0), c->h_mem_off[m], n});
         const double* p = c->h_xy.data() + 2 * (size_t)c->h_mem_off[m];
         double A0, J0;
         rest_mass_properties(n, p, &A0, &J0);

@@ -247,10 +247,18 @@ template <typename S>
 __global__ void __launch_bounds__(kHydroThreads) k_hydro(const MarkerArgs a, const HydroArgs h) {
     using C = typename Storage<S>::C;
     using E = typename Ext<C>::E;
+    // the unit record carries the membrane's offset and size, so that no block
+    // waits on a second table before its first position load
     const int4 u = h.units[blockIdx.x];
-    const int m = u.x, k0 = u.y, kv = u.z;
-    const int off = a.mem_off[m], n = a.mem_n[m];
+    const int k0 = u.x, kv = u.y, off = u.z, n = u.w;
     const int nel = kv + 1, nfit = 2 * kv + 1;
+    // the particle velocities of the chunk, fetched now for the last stage
+    C vpx = C(0), vpy = C(0);
+    if (threadIdx.x < kv) {
+        const C* V = static_cast<const C*>(a.V);
+        vpx = V[2 * (size_t)(off + k0 + threadIdx.x)];
+        vpy = V[2 * (size_t)(off + k0 + threadIdx.x) + 1];
+    }
     __shared__ C s_part[kHydroFits][9][5];
     __shared__ C s_nx[kHydroV + 1], s_ny[kHydroV + 1], s_len[kHydroV + 1];
     __shared__ C s_fx[kHydroV + 1], s_fy[kHydroV + 1], s_ux[kHydroV], s_uy[kHydroV];
@@ -315,12 +323,11 @@ __global__ void __launch_bounds__(kHydroThreads) k_hydro(const MarkerArgs a, con
         const int v = off + k0 + t;  // elements k0 + t - 1 and k0 + t are fits t and t + 1
         C* H = static_cast<C*>(a.Hf);
         C* D = static_cast<C*>(a.Dib);
-        const C* V = static_cast<const C*>(a.V);
         H[2 * (size_t)v] = C(0.5) * (s_fx[t] + s_fx[t + 1]);
         H[2 * (size_t)v + 1] = C(0.5) * (s_fy[t] + s_fy[t + 1]);
         const C dV = C(0.5) * (s_len[t] + s_len[t + 1]);
-        D[2 * (size_t)v] = C(2) * dV * (V[2 * (size_t)v] - s_ux[t]);
-        D[2 * (size_t)v + 1] = C(2) * dV * (V[2 * (size_t)v + 1] - s_uy[t]);
+        D[2 * (size_t)v] = C(2) * dV * (vpx - s_ux[t]);
+        D[2 * (size_t)v + 1] = C(2) * dV * (vpy - s_uy[t]);
     }
 }
 

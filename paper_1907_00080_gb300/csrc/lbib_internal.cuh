@@ -207,7 +207,7 @@ struct HydroArgs {
     double gx, gy;            // body force (u = (sum f e + G_body / 2) / rho)
     double nu;                // (tau - 1/2) / 3
     int nunits;               // blocks: chunks of hydro_chunk() vertices of the dynamic membranes
-    const int4* units;        // [nunits] {membrane, first local vertex, vertex count, 0}
+    const int4* units;        // [nunits] {first local vertex, vertex count, membrane offset, membrane size}
 };
 
 enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
