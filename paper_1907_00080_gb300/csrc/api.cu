@@ -488,8 +488,9 @@ static lbib_status finalize(lbib_ctx* c) {
     for (int m = 0; m < nm; ++m) {
         if (!is_dynamic(c->h_mem_kind[m])) continue;
         const int n = c->h_mem_n[m];
-        for (int k0 = 0; k0 < n; k0 += hydro_chunk())
-            hydro_units.insert(hydro_units.end(), {k0, std::min(hydro_chunk(), n - k0), c->h_mem_off[m], n});
+        const int hc = hydro_chunk(c->prec);
+        for (int k0 = 0; k0 < n; k0 += hc)
+            hydro_units.insert(hydro_units.end(), {k0, std::min(hc, n - k0), c->h_mem_off[m], n});
         const double* p = c->h_xy.data() + 2 * (size_t)c->h_mem_off[m];
         double A0, J0;
         rest_mass_properties(n, p, &A0, &J0);

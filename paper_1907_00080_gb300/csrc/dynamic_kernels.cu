@@ -17,8 +17,8 @@
 // element lengths, and the factor 2 accounts for the half force a node's
 // velocity carries under Guo forcing.
 //
-// One block per chunk of kHydroV vertices of a dynamic membrane, one thread
-// per (fit, stencil node) pair.
+// One block per chunk of 16 (FP32) or 4 (FP64) vertices of a dynamic
+// membrane, one thread per (fit, stencil node) pair.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -135,16 +135,21 @@ __device__ __forceinline__ void stencil_node(const MarkerArgs& a, const Stencil<
     i = ((st.i0 + q - 1) % a.nx + a.nx) % a.nx;
 }
 
-// The work of a block: a chunk of up to kHydroV consecutive vertices of one
+// The work of a block: a chunk of up to V consecutive vertices of one
 // dynamic membrane.  Its fits are the probes of the kv + 1 elements k0 - 1 ..
 // k0 + kv - 1 (each vertex needs the elements on both sides) and the kv
 // vertices; each (fit, stencil node) pair is one thread, so that the nine
 // node flows of a fit are read in parallel and the fit's sums are formed
 // afterwards in the fixed node order.
-constexpr int kHydroV = 16;
-constexpr int kHydroFits = 2 * kHydroV + 1;
-constexpr int kHydroThreads = 320;  // >= 9 kHydroFits = 297, a whole number of warps
-static_assert(9 * kHydroFits <= kHydroThreads, "one thread per (fit, node)");
+// Chunk sizes: 16 vertices (320 threads) in FP32; 4 vertices (96 threads) in
+// FP64, where the work is bound by the FP64 pipe of the SMs it runs on, so
+// more, smaller blocks spread it over more SMs.
+template <int V>
+struct HydroShape {
+    static constexpr int fits = 2 * V + 1;
+    static constexpr int threads = (9 * fits + 31) / 32 * 32;  // one thread per (fit, node)
+};
+constexpr int kHydroV32 = 16, kHydroV64 = 4;
 
 // node-flow products of one (fit, node) pair: a probe's MLS rows times (p, u, u, v, v)
 // (value of p, x and y derivatives of u and of v), or a vertex's shape
@@ -243,8 +248,9 @@ __device__ __forceinline__ void vertex_part(const MarkerArgs& a, const HydroArgs
     part[1] = w * vk;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kHydroThreads) k_hydro(const MarkerArgs a, const HydroArgs h) {
+template <typename S, int kHydroV>
+__global__ void __launch_bounds__(HydroShape<kHydroV>::threads) k_hydro(const MarkerArgs a, const HydroArgs h) {
+    constexpr int kHydroFits = HydroShape<kHydroV>::fits;
     using C = typename Storage<S>::C;
     using E = typename Ext<C>::E;
     // the unit record carries the membrane's offset and size, so that no block
@@ -331,15 +337,23 @@ __global__ void __launch_bounds__(kHydroThreads) k_hydro(const MarkerArgs a, con
     }
 }
 
-int hydro_chunk() { return kHydroV; }
+int hydro_chunk(lbib_precision prec) { return prec == LBIB_F64 ? kHydroV64 : kHydroV32; }
 
 cudaError_t launch_hydro(lbib_precision prec, const MarkerArgs& a, const HydroArgs& h, cudaStream_t s) {
     if (h.nunits == 0) return cudaSuccess;
     switch (prec) {
-        case LBIB_F64: k_hydro<double><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
-        case LBIB_F32: k_hydro<float><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
-        case LBIB_F32_STORE_F16: k_hydro<__half><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
-        case LBIB_F32_STORE_BF16: k_hydro<__nv_bfloat16><<<h.nunits, kHydroThreads, 0, s>>>(a, h); break;
+        case LBIB_F64:
+            k_hydro<double, kHydroV64><<<h.nunits, HydroShape<kHydroV64>::threads, 0, s>>>(a, h);
+            break;
+        case LBIB_F32:
+            k_hydro<float, kHydroV32><<<h.nunits, HydroShape<kHydroV32>::threads, 0, s>>>(a, h);
+            break;
+        case LBIB_F32_STORE_F16:
+            k_hydro<__half, kHydroV32><<<h.nunits, HydroShape<kHydroV32>::threads, 0, s>>>(a, h);
+            break;
+        case LBIB_F32_STORE_BF16:
+            k_hydro<__nv_bfloat16, kHydroV32><<<h.nunits, HydroShape<kHydroV32>::threads, 0, s>>>(a, h);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -250,7 +250,7 @@ cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas
 // dynamic_kernels.cu: hydrodynamic stresses and forcing terms of the dynamic
 // particles at the start of a step (before launch_forces)
 cudaError_t launch_hydro(lbib_precision prec, const MarkerArgs& a, const HydroArgs& h, cudaStream_t s);
-int hydro_chunk();  // vertices per block of the hydrodynamic kernel
+int hydro_chunk(lbib_precision prec);  // vertices per block of the hydrodynamic kernel
 // observables.cu: 8 doubles per membrane (see lbib_membrane_observables)
 cudaError_t launch_observables(lbib_precision prec, const MarkerArgs& a, double* out, cudaStream_t s);
 cudaError_t launch_pos_in(lbib_precision prec, const double* xy, void* X, int nv, cudaStream_t s);

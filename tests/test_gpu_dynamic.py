@@ -198,11 +198,12 @@ def test_refusals():
 
 
 def test_large_deformable_particle_matches_the_oracle():
-    """A deformable dynamic particle of 300 vertices (19 blocks of the
-    hydrodynamic kernel, the last one ragged) in a periodic box."""
+    """A deformable dynamic particle of 302 vertices (76 blocks of 4
+    vertices of the FP64 hydrodynamic kernel, the last one ragged) in a
+    periodic box."""
     wl = inputs.Workload(name="big_soft", nx=96, ny=80, init="rest", walls=0, body_force=(1e-6, 0.0),
                          precision="f64",
-                         membranes=[inputs.Membrane(xy=inputs.circle(40.0, 40.0, 30.0, 300), ks=1e-3, kb=1e-4,
+                         membranes=[inputs.Membrane(xy=inputs.circle(40.0, 40.0, 30.0, 302), ks=1e-3, kb=1e-4,
                                                     ka=1.0, kind=2)])
     s = lb().Simulation(wl)
     r = make_oracle(wl)
