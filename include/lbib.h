@@ -213,7 +213,8 @@ lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, int on_device
 lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t membrane_id, double* xy);
 
 /* Overwrite X^n and X^{n-1} of all membranes (2*nv doubles each, host memory);
- * xy_prev may be NULL (then X^{n-1} = X^n). */
+ * xy_prev may be NULL (then X^{n-1} = X^n).  The particle velocities and rigid
+ * states of dynamic membranes are left as they are. */
 lbib_status lbib_write_markers(lbib_ctx* ctx, const double* xy, const double* xy_prev);
 
 /* Total Lagrangian force F^n and interpolated velocity U^n used by the last
