@@ -34,6 +34,27 @@ template <> __device__ __forceinline__ double hydro_wall<double>(const HydroArgs
     return bottom ? h.bb_bot : h.bb_top;
 }
 
+// Division and square root of the FP32 path through the hardware's fast
+// approximations (a few ulp: far inside the FP32 path's 1e-5 bar, and the
+// kernel is bound by its dependent chain of these operations); the FP64 path
+// keeps the correctly rounded ones.
+__device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double hdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float hsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double hsqrt(double x) { return sqrt(x); }
+
+// Roma, Peskin & Berger three-point regularised delta with those operations
+template <typename C>
+__device__ __forceinline__ C roma_h(C r) {
+    const C a = fabs(r);
+    if (a <= C(0.5)) return hdiv(C(1) + hsqrt(C(1) - C(3) * a * a), C(3));
+    if (a <= C(1.5)) {
+        const C b = C(1) - a;
+        return hdiv(C(5) - C(3) * a - hsqrt(C(1) - C(3) * b * b), C(6));
+    }
+    return C(0);
+}
+
 // p, u, v of node (i, j) (i in [0, nx), j a fluid row) from the pre-collision
 // populations: the pull of the post-collision deviations, with the half-way
 // bounce-back (plus the moving-wall term) where the source lies behind a wall
@@ -64,9 +85,9 @@ __device__ __forceinline__ void node_flow(const MarkerArgs& a, const HydroArgs& 
     const C jx = (d[1] - d[3]) + ((d[5] - d[7]) + (d[8] - d[6]));
     const C jy = (d[2] - d[4]) + ((d[5] - d[7]) + (d[6] - d[8]));
     const C rho = C(1) + drho;
-    u = (jx + C(0.5) * C(h.gx)) / rho;
-    v = (jy + C(0.5) * C(h.gy)) / rho;
-    p = drho / C(3);
+    u = hdiv(jx + C(0.5) * C(h.gx), rho);
+    v = hdiv(jy + C(0.5) * C(h.gy), rho);
+    p = hdiv(drho, C(3));
 }
 
 // nearest-node stencil of a point: origin, node-minus-point offsets, Roma
@@ -93,8 +114,8 @@ __device__ __forceinline__ Stencil<C> stencil_at(const MarkerArgs& a, E px, E py
     for (int q = 0; q < 3; ++q) {
         st.rx[q] = -etoc(eaddc(px, -(fi0 + C(q - 1))));
         st.ry[q] = -etoc(eaddc(py, -(fj0 + C(q - 1))));
-        st.wx[q] = roma<C>(st.rx[q]);
-        st.wy[q] = roma<C>(st.ry[q]);
+        st.wx[q] = roma_h<C>(st.rx[q]);
+        st.wy[q] = roma_h<C>(st.ry[q]);
         const int jj = st.j0 + q - 1;
         st.rowok[q] = a.walls ? (jj >= 0 && jj < a.ny) : true;
         st.nrow += st.rowok[q] ? 1 : 0;
@@ -192,16 +213,16 @@ __device__ __forceinline__ void probe_part(const MarkerArgs& a, const HydroArgs&
         const C c11 = M00 * M22 - M02 * M02;
         const C c12 = -(M00 * M12 - M01 * M02);
         const C c22 = M00 * M11 - M01 * M01;
-        const C f0 = w * (c00 + c01 * nd.rx + c02 * nd.ry) / det;
-        const C f1 = w * (c01 + c11 * nd.rx + c12 * nd.ry) / det;
-        const C f2 = w * (c02 + c12 * nd.rx + c22 * nd.ry) / det;
+        const C f0 = hdiv(w * (c00 + c01 * nd.rx + c02 * nd.ry), det);
+        const C f1 = hdiv(w * (c01 + c11 * nd.rx + c12 * nd.ry), det);
+        const C f2 = hdiv(w * (c02 + c12 * nd.rx + c22 * nd.ry), det);
         part[0] = f0 * pk;
         part[1] = f1 * uk;
         part[2] = f2 * uk;
         part[3] = f1 * vk;
         part[4] = f2 * vk;
     } else {
-        part[0] = (M00 > C(0) ? w / M00 : C(0)) * pk;
+        part[0] = (M00 > C(0) ? hdiv(w, M00) : C(0)) * pk;
     }
 }
 
@@ -237,8 +258,8 @@ __device__ __forceinline__ void vertex_part(const MarkerArgs& a, const HydroArgs
         const C c1 = -(M01 * M22 - M12 * M02);
         const C c2 = M01 * M12 - M11 * M02;
         const C det = M00 * c0 + M01 * c1 + M02 * c2;
-        if (det > C(1e-10)) w = w * (c0 + c1 * nd.rx + c2 * nd.ry) / det;
-        else w = sw > C(0) ? w / sw : C(0);
+        if (det > C(1e-10)) w = hdiv(w * (c0 + c1 * nd.rx + c2 * nd.ry), det);
+        else w = sw > C(0) ? hdiv(w, sw) : C(0);
     }
     int i, j;
     stencil_node<C>(a, st, b, q, i, j);
@@ -284,8 +305,8 @@ __global__ void __launch_bounds__(HydroShape<kHydroV>::threads) k_hydro(const Ma
             load_pos<C>(a, off + e, x0, y0);
             load_pos<C>(a, off + (e + 1 == n ? 0 : e + 1), x1, y1);
             const C ex = etoc(esub(x1, x0)), ey = etoc(esub(y1, y0));
-            const C len = sqrt(ex * ex + ey * ey);
-            const C nx = ey / len, ny = -ex / len;
+            const C len = hsqrt(ex * ex + ey * ey);
+            const C nx = hdiv(ey, len), ny = hdiv(-ex, len);
             const E qx = eaddc(emulc(eadd(x0, x1), C(0.5)), C(1.2) * nx);
             const E qy = eaddc(emulc(eadd(y0, y1), C(0.5)), C(1.2) * ny);
             probe_part<S, E>(a, h, qx, qy, b, q, part);
