@@ -21,6 +21,12 @@ LIB = os.path.join(PKG, "liblbib.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# The marker kernels are latency-bound chains of FP32 divisions and square
+# roots: in these units FP32 division and square root use the hardware's fast
+# approximations (a few ulp; the FP32 path is held to 1e-5, and the bond
+# decisions fall back to FP64 within a 1e-5 guard band).  FP64 is unaffected.
+FAST_FP32 = {"ib_kernels.cu", "advance_kernel.cu"}
+FAST_FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 
 def _nvcc():
@@ -54,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        fast = FAST_FP32_FLAGS if os.path.basename(src) in FAST_FP32 else []
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *fast, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
