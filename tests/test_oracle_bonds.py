@@ -178,3 +178,66 @@ def test_physical_cutoff_where_the_mesh_resolves_it():
         inputs.physical_bonds(62.5)
     wl = inputs.fine_capillary_2000x667("f32", bonds="physical")
     assert wl.bonds["d_cut"] == pytest.approx(25.0 / (10000.0 / 667), rel=1e-12)  # dx = 10 um / 667
+
+
+def _kinetics(y_eq=0.75, kf_dt=0.01, kr0_dt=0.004, beta_f=0.5, beta_r=2.0):
+    s = oracle.OracleSim(16, 8, walls=1)
+    s.add_membrane(_strip(2), ks=0.0, kb=0.0, ka=0.0, ligand_elems=[0])
+    s.set_receptors(np.array([[1.0, -0.5]]), y_eq=y_eq, d_cut=2 * y_eq, kf_dt=kf_dt, kr0_dt=kr0_dt,
+                    beta_f=beta_f, beta_r=beta_r)
+    return s
+
+
+def test_bond_probabilities_at_the_equilibrium_length():
+    """Sec. 2.2 (wall-particle interaction): at the equilibrium bond length the
+    spring is unloaded, so formation and rupture run at their unloaded rates:
+    per step P_f = 1 - exp(-k_f dt) and P_r = 1 - exp(-k_r0 dt) (a Poisson event
+    at that rate within one step)."""
+    for y_eq, kf, kr in ((0.75, 0.01, 0.01 / 8.5e3), (0.8333, 0.05, 0.01), (1.3, 0.3, 0.2)):
+        s = _kinetics(y_eq=y_eq, kf_dt=kf, kr0_dt=kr)
+        assert s.p_form(y_eq) == pytest.approx(-math.expm1(-kf), rel=1e-14)
+        assert s.p_rupture(y_eq) == pytest.approx(-math.expm1(-kr), rel=1e-14)
+    # the paper's only number: k_f / k_r0 = 8.5e3 gives that ratio of the
+    # unloaded per-step probabilities in the small-rate limit
+    s = _kinetics(kf_dt=1e-6, kr0_dt=1e-6 / 8.5e3)
+    assert s.p_form(0.75) / s.p_rupture(0.75) == pytest.approx(8.5e3, rel=1e-5)
+
+
+def test_bond_probabilities_symmetric_and_monotone_in_the_stretch():
+    """Formation slows and rupture speeds up as the bond is stretched or
+    compressed away from y_eq, symmetrically in d - y_eq."""
+    y_eq = 0.75
+    s = _kinetics(y_eq=y_eq, kf_dt=0.05, kr0_dt=0.01)
+    dev = np.linspace(0.0, 0.7, 36)
+    pf_plus = np.array([s.p_form(y_eq + e) for e in dev])
+    pf_minus = np.array([s.p_form(y_eq - e) for e in dev])
+    pr_plus = np.array([s.p_rupture(y_eq + e) for e in dev])
+    pr_minus = np.array([s.p_rupture(y_eq - e) for e in dev])
+    np.testing.assert_allclose(pf_plus, pf_minus, rtol=1e-13)
+    np.testing.assert_allclose(pr_plus, pr_minus, rtol=1e-13)
+    assert np.all(np.diff(pf_plus) < 0) and np.all(np.diff(pr_plus) > 0)
+    assert np.all((pf_plus > 0) & (pf_plus < 1) & (pr_plus > 0) & (pr_plus < 1))
+
+
+def test_bond_probabilities_scale_with_the_relative_stretch():
+    """The rates depend on the stretch only through z = (d - y_eq) / y_eq with
+    a Gaussian factor: -log(1 - P) = k dt exp(-+beta z^2).  Fitting a
+    parabola in z to log(-log(1 - P)) recovers log(k dt) as its constant and
+    -beta_f (formation) or +beta_r (rupture) as its curvature, for two
+    different y_eq; the two lengths give the same P at the same z."""
+    kf, kr, bf, br = 0.05, 0.01, 0.5, 2.0
+    z = np.linspace(-0.9, 0.9, 41)
+    curves = []
+    for y_eq in (0.75, 1.9):
+        s = _kinetics(y_eq=y_eq, kf_dt=kf, kr0_dt=kr, beta_f=bf, beta_r=br)
+        pf = np.array([s.p_form(y_eq * (1 + q)) for q in z])
+        pr = np.array([s.p_rupture(y_eq * (1 + q)) for q in z])
+        cf = np.polyfit(z, np.log(-np.log1p(-pf)), 2)
+        cr = np.polyfit(z, np.log(-np.log1p(-pr)), 2)
+        assert cf[0] == pytest.approx(-bf, rel=1e-9) and abs(cf[1]) < 1e-9
+        assert cf[2] == pytest.approx(math.log(kf), rel=1e-9)
+        assert cr[0] == pytest.approx(br, rel=1e-9) and abs(cr[1]) < 1e-9
+        assert cr[2] == pytest.approx(math.log(kr), rel=1e-9)
+        curves.append((pf, pr))
+    np.testing.assert_allclose(curves[0][0], curves[1][0], rtol=1e-12)
+    np.testing.assert_allclose(curves[0][1], curves[1][1], rtol=1e-12)

@@ -148,3 +148,50 @@ def test_rbc_contour_matches_eq_rbcshape():
     for p in xy[::7]:
         assert np.min(np.hypot(curve[:, 0] - p[0], curve[:, 1] - p[1])) < 2e-3
     assert inputs._signed_area(xy) > 0
+
+
+def test_bending_regular_ngon_against_flat_rest_angles():
+    """Eq. bendFor on a regular N-gon with rest angles 0 (a straight rest
+    shape): every vertex turns by theta = 2 pi / N.  Vertex v gets
+    -k_b theta n_v from its own term and k_b theta / 2 n_{v -+ 1} from each
+    neighbour's (equal elements), and n_{v -+ 1} is n_v turned by -+ 2 pi / N,
+    so F_v = k_b theta (cos(2 pi / N) - 1) n_v, whatever the radius."""
+    kb = 0.013
+    for N in (7, 12, 50):
+        for R in (3.0, 11.5):
+            xy = inputs.circle(2.0, -1.0, R, N)
+            l0, _, A0 = oracle.ring_rest(xy)
+            F = oracle.ring_forces(xy, l0, np.zeros(N), A0, ks=0.0, kb=kb, ka=0.0, which=2)
+            theta = 2 * math.pi / N
+            # outward vertex normal of a regular polygon: the radial direction
+            n = (xy - np.array([2.0, -1.0])) / R
+            expect = kb * theta * (math.cos(theta) - 1.0) * n
+            np.testing.assert_allclose(F, expect, rtol=0, atol=1e-14 * kb)
+
+
+def test_bending_split_follows_unequal_element_lengths():
+    """One bent vertex between elements of unequal length (l_L = 1, l_R = 3),
+    every other vertex at its rest angle: the vertex gets -k_b (theta -
+    theta_0) n_v, its left neighbour l_L / (l_L + l_R) of the opposite and the
+    right one l_R / (l_L + l_R).  n_v is the unit vector normal to the sum of
+    the two unit edge vectors, pointing out of the ring."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [1.0 + 3.0 * math.cos(0.4), 3.0 * math.sin(0.4)],
+                   [-0.5, 3.5]])
+    n = len(xy)
+    l0, th0, A0 = oracle.ring_rest(xy)
+    v, dth, kb = 1, 0.05, 0.02
+    th0 = th0.copy()
+    th0[v] -= dth  # only vertex 1 is away from its rest angle, by dth
+    F = oracle.ring_forces(xy, l0, th0, A0, ks=0.0, kb=kb, ka=0.0, which=2)
+    eL = xy[1] - xy[0]
+    eR = xy[2] - xy[1]
+    lL, lR = np.linalg.norm(eL), np.linalg.norm(eR)
+    assert (lL, lR) == pytest.approx((1.0, 3.0), rel=1e-15)
+    t = eL / lL + eR / lR
+    nv = np.array([t[1], -t[0]]) / np.linalg.norm(t)
+    assert nv @ (xy[1] - xy.mean(axis=0)) > 0  # outward
+    np.testing.assert_allclose(F[1], -kb * dth * nv, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(F[0], kb * dth * lL / (lL + lR) * nv, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(F[2], kb * dth * lR / (lL + lR) * nv, rtol=0, atol=1e-16)
+    assert np.all(F[3] == 0.0)
+    assert np.linalg.norm(F[2]) / np.linalg.norm(F[0]) == pytest.approx(3.0, rel=1e-13)
