@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     // ---- moments, Guo-corrected velocity, BGK collision with Guo source
     const C om = C(a.omega);
     const C pre = C(1) - C(0.5) * om;
+    const C om3 = C(3.0 * a.omega);
     C out[9][VEC];
     C rho_v[VEC], ux_v[VEC], uy_v[VEC];
 #pragma unroll
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
         C fk[9], ok9[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fk[i] = f[i][k];
-        collide_node<C>(fk, Gx[k], Gy[k], om, pre, ok9, rho_v[k], ux_v[k], uy_v[k]);
+        collide<S>(fk, Gx[k], Gy[k], om, pre, om3, ok9, rho_v[k], ux_v[k], uy_v[k]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i][k] = ok9[i];
     }

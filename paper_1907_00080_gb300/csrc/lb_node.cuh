@@ -8,6 +8,8 @@
 // Sec. 2.2 (Eqs. forcedBGK, ForcingTerm; rho u = sum f e + G/2).
 #pragma once
 
+#include <type_traits>
+
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -80,6 +82,97 @@ __device__ __forceinline__ void collide_node(const C (&f)[9], C Gx, C Gy, C om, 
         const C odd = b * eu + g * eG;
         out[ip[p]] = omc * f[ip[p]] + w * (even + odd);
         out[io[p]] = omc * f[io[p]] + w * (even - odd);
+    }
+}
+
+// The same collision for FP32 storage, arranged so that the momentum it hands
+// on carries no systematic rounding error.  In FP32 the per-node rounding of
+// the momentum (about 1e-9 of populations near 0.01) is coherent across a
+// slowly varying flow: with every operation rounded to nearest, double
+// roundings (a sum rounded to one grid, then added to a term and rounded to a
+// coarser one) leave a bias of a fraction of an ulp per node and step.  The
+// flow integrates such a bias over its viscous time like a spurious body force
+// (2.2e-4 lu of marker drift over 1000 steps of the 128x32 capsule at
+// u_max = 0.02).  Three changes remove it:
+//  * the momentum sums are exact: every pulled deviation is split into a part
+//    on the 2^-20 grid (d + 12 - 12, exact for |d| < 4) and a remainder below
+//    2^-21; the grid parts add without rounding, the remainders with errors
+//    below 2^-42;
+//  * the odd part of each direction pair, 3 omega (e.t) + 3 pre (e.G) with
+//    t = rho u = j + G/2, is formed from those two parts by fused
+//    multiply-adds with one final rounding (instead of from a rounded rho and
+//    u, whose product re-rounds rho u);
+//  * the weights are k/36 with k = 16, 4, 1 (exact multiples), and the
+//    product by 1/36 is compensated: x/36 = x hi + x lo with hi + lo = 1/36
+//    to 2^-48, so the weights carry no common relative error (the nearest
+//    floats to 1/9, 1/36 and 4/9 are all 7.45e-9 too large, which would scale
+//    the momentum of every collision by 1 + 7.45e-9).
+// The remaining per-node momentum error is unbiased rounding: about 1e-11 of
+// mean against 3e-10 of scatter at u = 0.015 (it was 7e-10 of mean).  At
+// tau = 1 (omega = 1) every constant is exact.  At other tau, 3 omega and
+// 1 - omega are rounded separately, which leaves a relative mismatch of at
+// most 2^-24 between the odd moments and the relaxation.
+// Mass (the even parts) keeps the plain arithmetic.
+__device__ __forceinline__ void collide_node_exactj(const float (&f)[9], float Gx, float Gy, float om, float pre,
+                                                    float om3, float (&out)[9], float& rho_o, float& ux_o,
+                                                    float& uy_o) {
+    const float drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    float hi[9], lo[9];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        hi[i] = __fadd_rn(__fadd_rn(f[i], 12.0f), -12.0f);  // f[i] rounded to the 2^-20 grid
+        lo[i] = __fadd_rn(f[i], -hi[i]);                     // exact remainder
+    }
+    const float Jxh = __fadd_rn(__fadd_rn(hi[1], -hi[3]), __fadd_rn(__fadd_rn(hi[5], -hi[7]), __fadd_rn(hi[8], -hi[6])));
+    const float Jyh = __fadd_rn(__fadd_rn(hi[2], -hi[4]), __fadd_rn(__fadd_rn(hi[5], -hi[7]), __fadd_rn(hi[6], -hi[8])));
+    const float Jxl = (lo[1] - lo[3]) + ((lo[5] - lo[7]) + (lo[8] - lo[6]));
+    const float Jyl = (lo[2] - lo[4]) + ((lo[5] - lo[7]) + (lo[6] - lo[8]));
+    const float Txl = fmaf(0.5f, Gx, Jxl), Tyl = fmaf(0.5f, Gy, Jyl);  // t = j + G/2 = (Jh) + (Tl)
+    const float tx = Jxh + Txl, ty = Jyh + Tyl;
+    const float rho = 1.0f + drho;
+    const float rinv = recip(rho);
+    const float ux = tx * rinv, uy = ty * rinv;
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+    const float tu = tx * ux + ty * uy;  // rho u^2
+    const float uG = ux * Gx + uy * Gy;
+    const float a = om * drho - 1.5f * om * tu - 3.0f * pre * uG;
+    const float c45 = 4.5f * om, g = 3.0f * pre, h = 9.0f * pre;
+    const float omc = 1.0f - om;
+    constexpr float whi = 1.0f / 36.0f;
+    constexpr float wlo = (float)(1.0 / 36.0 - (double)(1.0f / 36.0f));
+    // k x / 36 + base with one final rounding of the weighted part; k is a
+    // power of two, so k whi and k wlo are exact and x (k whi) = (k x) whi
+    auto wmul = [&](float k, float x, float base) { return fmaf(x, k * whi, fmaf(x, k * wlo, base)); };
+    out[0] = wmul(16.0f, a, omc * f[0]);
+    const float eus[4] = {ux, uy, ux + uy, uy - ux};
+    const float ets[4] = {tx, ty, tx + ty, ty - tx};
+    const float eGs[4] = {Gx, Gy, Gx + Gy, Gy - Gx};
+    const float eth[4] = {Jxh, Jyh, __fadd_rn(Jxh, Jyh), __fadd_rn(Jyh, -Jxh)};  // exact on the 2^-20 grid
+    const float etl[4] = {Txl, Tyl, Txl + Tyl, Tyl - Txl};
+    constexpr int ip[4] = {1, 2, 5, 6};
+    constexpr int io[4] = {3, 4, 7, 8};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float k = p < 2 ? 4.0f : 1.0f;
+        const float even = a + eus[p] * (c45 * ets[p] + h * eGs[p]);
+        const float odd = fmaf(om3, eth[p], fmaf(om3, etl[p], g * eGs[p]));
+        out[ip[p]] = wmul(k, even + odd, omc * f[ip[p]]);
+        out[io[p]] = wmul(k, even - odd, omc * f[io[p]]);
+    }
+}
+
+// the collision of storage type S: the exact-momentum form for FP32 storage,
+// the plain form otherwise (FP64; 16-bit storage, whose own rounding is far
+// coarser)
+template <typename S, typename C>
+__device__ __forceinline__ void collide(const C (&f)[9], C Gx, C Gy, C om, C pre, C om3, C (&out)[9], C& rho_o,
+                                        C& ux_o, C& uy_o) {
+    if constexpr (std::is_same<S, float>::value) {
+        collide_node_exactj(f, Gx, Gy, om, pre, om3, out, rho_o, ux_o, uy_o);
+    } else {
+        collide_node<C>(f, Gx, Gy, om, pre, out, rho_o, ux_o, uy_o);
     }
 }
 

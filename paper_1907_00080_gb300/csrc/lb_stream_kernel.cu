@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
         // ---- consumers
         const C om = C(a.omega);
         const C pre = C(1) - C(0.5) * om;
+        const C om3 = C(3.0 * a.omega);
         const float inv = a.inv_scale;
         const float scl = 1.0f / inv;  // 2^k, exact
         C* __restrict__ uxf = static_cast<C*>(a.ux);
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
                     C fq[9], out[9], rho;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
-                    collide_node<C>(fq, Gx, Gy, om, pre, out, rho, pu.v[q], pv.v[q]);
+                    collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
                 }
@@ -412,6 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
 
     const C om = C(a.omega);
     const C pre = C(1) - C(0.5) * om;
+    const C om3 = C(3.0 * a.omega);
     const float inv = a.inv_scale;
     const float scl = 1.0f / inv;  // 2^k, exact
     C* __restrict__ uxf = static_cast<C*>(a.ux);
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
                 C fq[9], out[9], rho;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
-                collide_node<C>(fq, Gx, Gy, om, pre, out, rho, pu.v[q], pv.v[q]);
+                collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
             }

@@ -286,28 +286,43 @@ def test_capsule_128x32_fp64_1000_steps(bonds):
 
 def test_capsule_128x32_fp32_against_fp64_oracle():
     """FP32 storage and arithmetic against the FP64 oracle on the stiff capsule
-    (k_s = 0.05, u_max = 0.02): within 1e-5 (fields, relative to the speed
-    scale) and 1e-5 lattice units (markers) over 100 steps; bond sets bit-exact
-    over 1000 steps.  Beyond that the FP32 velocity error that the capsule's
-    motion integrates grows (measured 2.6e-5 fields, 1.5e-4 lu markers at 1000
-    steps); the 1000-step check holds that measured envelope."""
+    (k_s = 0.05, u_max = 0.02, stress kinetics): within 1e-5 (fields, relative
+    to the speed scale) and 1e-5 lattice units (markers) after 100 and after
+    1000 steps; bond sets bit-exact every 100 steps.  The FP32 collision
+    carries the momentum without systematic rounding error; with the plain
+    FP32 arithmetic the capsule drifted by 2e-4 lu over the 1000 steps."""
     wl = inputs.capsule_128x32(precision="f32", bonds="stress")
     s, r = sim_of(wl), make_oracle(wl)
-    s.step(100)
-    r.step(100)
-    rho, ux, uy = s.fields()
-    rho0, ux0, uy0 = r.fields()
-    assert vel_err(ux, uy, ux0, uy0) < 1e-5
-    assert rel_err(rho, rho0) < 1e-5
-    assert np.max(np.abs(s.markers() - r.markers())) < 1e-5
-    for _ in range(9):
+    for k in range(10):
         s.step(100)
         r.step(100)
         assert np.array_equal(s.bonds(), r.bonds())
-    _, ux, uy = s.fields()
-    _, ux0, uy0 = r.fields()
-    assert vel_err(ux, uy, ux0, uy0) < 5e-5
-    assert np.max(np.abs(s.markers() - r.markers())) < 5e-4
+        if k in (0, 9):
+            rho, ux, uy = s.fields()
+            rho0, ux0, uy0 = r.fields()
+            assert vel_err(ux, uy, ux0, uy0) < TOL["f32"]["field"]
+            assert rel_err(rho, rho0) < TOL["f32"]["field"]
+            assert np.max(np.abs(s.markers() - r.markers())) < TOL["f32"]["marker_abs"]
+
+
+def test_coarse_capillary_640x160_fp32_1000_steps():
+    """The coarse capillary in FP32 over 1000 steps against the oracle (stress
+    kinetics on both walls): fields within 1e-5 of the speed scale, markers
+    within 1e-5 lu, bond sets bit-exact every 100 steps."""
+    from paper_1907_00080_gb300 import tuning
+    wl = inputs.coarse_capillary_640x160(precision="f32")
+    wl.bonds = dict(inputs.STRESS_BONDS)
+    s = sim_of(wl, tiling=tuning.bench_tiling(wl))
+    r = make_oracle(wl)
+    for _ in range(10):
+        s.step(100)
+        r.step(100)
+        assert np.array_equal(s.bonds(), r.bonds())
+    rho, ux, uy = s.fields()
+    rho0, ux0, uy0 = r.fields()
+    assert vel_err(ux, uy, ux0, uy0) < TOL["f32"]["field"]
+    assert rel_err(rho, rho0) < TOL["f32"]["field"]
+    assert np.max(np.abs(s.markers() - r.markers())) < TOL["f32"]["marker_abs"]
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
