@@ -49,7 +49,11 @@ typedef enum {
     LBIB_E_CUDA = 2,      /* a CUDA runtime call failed                       */
     LBIB_E_OOM = 3,       /* device allocation failed                         */
     LBIB_E_TIMEOUT = 4,   /* a bounded device-side wait gave up               */
-    LBIB_E_NONFINITE = 5, /* a marker position became NaN/Inf                 */
+    LBIB_E_NONFINITE = 5, /* a marker position became NaN/Inf, or a spread
+                             force (|w F| >= 64 lu per vertex and node) or a
+                             repulsion magnitude (>= 1 per vertex and segment,
+                             i.e. overlapping membranes) left the range of its
+                             fixed-point accumulator (the value was clamped) */
     LBIB_E_STATE = 6      /* call not valid in the current state              */
 } lbib_status;
 

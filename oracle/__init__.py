@@ -25,15 +25,32 @@ _lib = None
 CFLAGS = ["-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction) if stale; return the path."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+_LIB_OMP = os.path.join(_HERE, "liblbib_oracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) if stale; return the
+    path.  openmp=True builds the OpenMP variant (the same source with its
+    loop pragmas enabled; the loops it splits write disjoint elements, so it
+    gives the same bits)."""
+    out = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", *CFLAGS, *(["-fopenmp"] if openmp else []), _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def use_threads(n: int) -> int:
+    """Switch this process to the OpenMP build with n threads (n <= 1: back to
+    the plain build).  Call before creating simulations: a simulation must be
+    driven by the build that created it.  Returns the thread count in use."""
+    global _lib
+    with _lock:
+        _lib = _load(build(openmp=n > 1))
+    return int(_lib.orc_set_threads(int(n)))
 
 
 _D = ctypes.c_double
@@ -112,7 +129,17 @@ _SIGS = {
     "orc_tangent_seed": (None, [_P, _DP, _DP, _D, _DP, _DP, _DP]),
     "orc_tangent_step": (None, [_P, _L]),
     "orc_tangent_get": (None, [_P, _DP, _DP, _DP]),
+    "orc_set_threads": (_I, [_I]),
 }
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
 
 
 def lib():
@@ -120,13 +147,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            for name, (res, args) in _SIGS.items():
-                fn = getattr(L, name)
-                fn.restype = res
-                fn.argtypes = args
-            _lib = L
+            _lib = _load(build())
     return _lib
 
 

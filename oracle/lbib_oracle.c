@@ -229,6 +229,7 @@ void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
     long nx = s->nx, ny = s->ny, N = nx * ny;
     for (int i = 0; i < 9; ++i) {
         int o = opposite(i);
+#pragma omp parallel for schedule(static)
         for (long y = 0; y < ny; ++y) {
             for (long x = 0; x < nx; ++x) {
                 long sy = y - EY[i];
@@ -257,8 +258,9 @@ void orc_moments(const orc_sim *s, const double *f, const double *Gx, const doub
 /* Eq. forcedBGK with Delta t = 1, then streaming; stores rho, u */
 static void collide_and_stream(orc_sim *s) {
     long N = (long)s->nx * s->ny;
-    double feq[9], F[9];
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
+        double feq[9], F[9];
         double rho, ux, uy;
         double gx = s->Gx[n], gy = s->Gy[n];
         moments_at(s->f, N, n, gx, gy, &rho, &ux, &uy);
@@ -1012,6 +1014,7 @@ void orc_compute_forces(orc_sim *s) {
     /* 2. repulsion, Eq. repFor (Delta x = 1), along the vertex's inward normal */
     if (s->nmem > 1) {
         const double c0 = 1e-4 / (8.0 * sqrt(2.0));
+#pragma omp parallel for schedule(dynamic, 16)
         for (int a = 0; a < nv; ++a) {
             int ma = s->vert_mem[a];
             int off = s->mem_off[ma], n = s->mem_n[ma];
@@ -1092,9 +1095,11 @@ static void step_once(orc_sim *s) {
     int nv = s->nv;
     orc_compute_step_forces(s);
     /* 6. weights at X^n */
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < nv; ++v) orc_ib_weights(s, s->x[v], s->y[v], s->wgt + 9 * v, s->widx + 9 * v);
     /* 7. spread: the membrane forces of kinematic membranes, the forcing
      * term F^ib of dynamic ones */
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) { s->Gx[n] = s->gx; s->Gy[n] = s->gy; }
     for (int v = 0; v < nv; ++v) {
         int dyn = is_dynamic(s->mem_kind[s->vert_mem[v]]);
@@ -1109,6 +1114,7 @@ static void step_once(orc_sim *s) {
     /* 8. collide + stream */
     collide_and_stream(s);
     /* 9. interpolate u^n at X^n */
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < nv; ++v) {
         double a = 0.0, b = 0.0;
         for (int k = 0; k < 9; ++k) {
@@ -1163,6 +1169,15 @@ static void step_once(orc_sim *s) {
 void orc_step(orc_sim *s, long nsteps) {
     for (long k = 0; k < nsteps; ++k) step_once(s);
 }
+
+/* threads of the OpenMP build (the plain build ignores the pragmas above,
+ * whose loops write disjoint elements, so both builds give the same bits) */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_set_threads(int n) { if (n > 0) omp_set_num_threads(n); return omp_get_max_threads(); }
+#else
+int orc_set_threads(int n) { (void)n; return 1; }
+#endif
 
 /* accessors */
 int orc_num_vertices(const orc_sim *s) { return s->nv; }

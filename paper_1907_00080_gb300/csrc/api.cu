@@ -871,6 +871,12 @@ extern "C" lbib_status lbib_sync(lbib_ctx* c) {
         c->poisoned = true;
         return fail(c, LBIB_E_NONFINITE, "a marker position became non-finite");
     }
+    if (st & ST_FIXRANGE) {
+        c->poisoned = true;
+        return fail(c, LBIB_E_NONFINITE,
+                    "a spread marker force (|w F| >= 64 lu per node) or a repulsion magnitude (>= 1, membranes "
+                    "overlapping) left its fixed-point range or was not finite");
+    }
     if (st & ST_TIMEOUT) {
         c->poisoned = true;
         return fail(c, LBIB_E_TIMEOUT, "a bulk copy of the fused kernel never completed");
@@ -1886,18 +1892,63 @@ struct SaveHeader {
     int32_t version, nx, ny, prec, walls, nmem, nv, nlig, nrec, nseg, scale_exp, ndyn;
     double tau, gx, gy, uw_bot, uw_top, d_rep;
     int64_t steps;
+    uint64_t setup_hash;  // of the membranes, ligands, receptors and bond parameters
 };
+constexpr int32_t kSaveVersion = 2;
+
+// FNV-1a over the bytes of the set-up that the header's sizes do not pin:
+// rest shapes, stiffnesses, kinds, densities, ligand elements, receptor
+// positions and bond parameters
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void bytes(const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t k = 0; k < n; ++k) h = (h ^ b[k]) * 1099511628211ull;
+    }
+    template <typename T>
+    void vec(const std::vector<T>& v) {
+        const uint64_t n = v.size();
+        bytes(&n, sizeof(n));
+        if (n) bytes(v.data(), n * sizeof(T));
+    }
+    template <typename T>
+    void val(T x) { bytes(&x, sizeof(x)); }
+};
+
+uint64_t setup_hash(const lbib_ctx* c) {
+    Fnv f;
+    f.vec(c->h_xy);
+    f.vec(c->h_mem_off);
+    f.vec(c->h_mem_n);
+    f.vec(c->h_mem_kind);
+    f.vec(c->h_lig_elem_local);
+    f.vec(c->h_mem_lig_off);
+    f.vec(c->h_ks);
+    f.vec(c->h_kb);
+    f.vec(c->h_ka);
+    f.vec(c->h_rhop);
+    f.val<int>(c->have_receptors ? 1 : 0);
+    if (c->have_receptors) {
+        f.vec(c->h_rec);
+        const lbib_bond_params& b = c->bp;
+        for (double v : {b.d_cut, b.y_eq, b.sigma, b.kf_dt, b.kr0_dt, b.beta_f, b.beta_r, b.d_break}) f.val(v);
+        f.val(b.seed);
+        f.val(b.instance);
+    }
+    return f.h;
+}
 
 SaveHeader header_of(const lbib_ctx* c) {
     SaveHeader h{};
     std::memcpy(h.magic, kSaveMagic, 8);
-    h.version = 1;
+    h.version = kSaveVersion;
     h.nx = c->nx; h.ny = c->ny; h.prec = (int32_t)c->prec; h.walls = (int32_t)c->walls;
     h.nmem = c->nmem; h.nv = c->nv; h.nlig = c->nlig; h.nrec = c->ma.nrec; h.nseg = c->nseg;
     h.scale_exp = c->scale_exp;
     h.ndyn = c->ndyn;
     h.tau = c->tau; h.gx = c->gx; h.gy = c->gy; h.uw_bot = c->uw_bot; h.uw_top = c->uw_top; h.d_rep = c->d_rep;
     h.steps = c->steps;
+    h.setup_hash = setup_hash(c);
     return h;
 }
 
@@ -1953,7 +2004,7 @@ extern "C" lbib_status lbib_load(lbib_ctx* c, const char* path) {
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return fail(c, LBIB_E_INVALID, std::string("cannot open for reading: ") + path);
     SaveHeader h{};
-    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kSaveMagic, 8) != 0 || h.version != 1) {
+    if (std::fread(&h, sizeof(h), 1, fp) != 1 || std::memcmp(h.magic, kSaveMagic, 8) != 0 || h.version != kSaveVersion) {
         std::fclose(fp);
         return fail(c, LBIB_E_INVALID, "not a saved lbib state");
     }
@@ -1962,7 +2013,7 @@ extern "C" lbib_status lbib_load(lbib_ctx* c, const char* path) {
                       h.nmem == mine.nmem && h.nv == mine.nv && h.nlig == mine.nlig && h.nrec == mine.nrec &&
                       h.nseg == mine.nseg && h.scale_exp == mine.scale_exp && h.tau == mine.tau &&
                       h.gx == mine.gx && h.gy == mine.gy && h.uw_bot == mine.uw_bot && h.uw_top == mine.uw_top &&
-                      h.d_rep == mine.d_rep;
+                      h.d_rep == mine.d_rep && h.ndyn == mine.ndyn && h.setup_hash == mine.setup_hash;
     if (!same) {
         std::fclose(fp);
         return fail(c, LBIB_E_INVALID, "the saved state belongs to another set-up (lattice, precision, membranes, "
@@ -1978,7 +2029,9 @@ extern "C" lbib_status lbib_load(lbib_ctx* c, const char* path) {
             return fail(c, LBIB_E_INVALID, "the saved state is truncated");
         }
     }
+    const bool at_end = std::fgetc(fp) == EOF;
     std::fclose(fp);
+    if (!at_end) return fail(c, LBIB_E_INVALID, "the saved state has bytes beyond its last part");
     CK(cudaStreamSynchronize(c->stream));
     for (size_t k = 0; k < parts.size(); ++k)
         if (parts[k].bytes)

@@ -434,7 +434,12 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
                     if (d < drep) mags += c_rep * sqrt(C(1) / (d * d * d * d * d));
                 }
             }
-            if (mags != C(0)) atomicAdd(&s_rep[j], (unsigned long long)to_fix60<C>(mags));
+            if (mags != C(0)) {
+                bool bad = false;
+                mags = clamp_fix(mags, C(kFix60Limit), bad);
+                if (bad) atomicOr(a.status, ST_FIXRANGE);
+                atomicAdd(&s_rep[j], (unsigned long long)to_fix60<C>(mags));
+            }
         }
     }
     __syncthreads();
@@ -477,9 +482,13 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
         ii = ii < 0 ? ii + a.nx : (ii >= a.nx ? ii - a.nx : ii);
         const size_t node = (size_t)jj * a.nx + ii;
         const C wq = s_w[j][q9];
+        bool bad = false;
+        const C gx = clamp_fix(wq * s_F[j][0], C(kFixLimit), bad);
+        const C gy = clamp_fix(wq * s_F[j][1], C(kFixLimit), bad);
+        if (bad) atomicOr(a.status, ST_FIXRANGE);
         unsigned long long* gp = reinterpret_cast<unsigned long long*>(a.gsum + node);
-        atomicAdd(gp, (unsigned long long)to_fix<C>(wq * s_F[j][0]));
-        atomicAdd(gp + 1, (unsigned long long)to_fix<C>(wq * s_F[j][1]));
+        atomicAdd(gp, (unsigned long long)to_fix<C>(gx));
+        atomicAdd(gp + 1, (unsigned long long)to_fix<C>(gy));
         a.flags[(jj / a.tile_h) * a.tiles_x + ii / a.tile_w] = 1;
     }
 }

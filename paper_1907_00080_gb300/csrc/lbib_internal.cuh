@@ -210,7 +210,9 @@ struct HydroArgs {
     const int4* units;        // [nunits] {first local vertex, vertex count, membrane offset, membrane size}
 };
 
-enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4 };
+// ST_FIXRANGE: a spread force or a repulsion magnitude left the range of its
+// fixed-point accumulator (see clamp_fix)
+enum StatusBits { ST_NONFINITE = 1, ST_TILE_OVERFLOW = 2, ST_TIMEOUT = 4, ST_FIXRANGE = 8 };
 
 constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of 32)
 constexpr int kUnitInts = 8;  // ints per work-unit record (two int4)

@@ -32,6 +32,24 @@ template <> __device__ __forceinline__ long long to_fix<double>(double v) {
     return __double2ll_rn(v * kFixScale);
 }
 
+// Range of the fixed-point conversions.  The spread field holds w F per
+// (vertex, node) scaled by 2^52, the repulsion accumulators one magnitude per
+// (vertex, segment) scaled by 2^60, in signed 64-bit integers.  A value at or
+// beyond its bound, or not finite, is clamped to the bound (NaN to 0) and
+// `bad` is set; the kernel then raises ST_FIXRANGE, which the host reads as
+// LBIB_E_NONFINITE.  Bounds: 64 lu of force per (vertex, node), 2^58 in the
+// field, so 32 such terms fit in one node's int64; repulsion 1 per
+// (vertex, segment), 2^60 in an accumulator that holds 8 (Eq. repFor reaches
+// 1 at d = 9.4e-3 lu, i.e. membranes that overlap).
+constexpr double kFixLimit = 64.0;
+constexpr double kFix60Limit = 1.0;
+template <typename C>
+__device__ __forceinline__ C clamp_fix(C v, C lim, bool& bad) {
+    if (fabs(v) < lim) return v;  // false for NaN
+    bad = true;
+    return v > C(0) ? lim : (v < C(0) ? -lim : C(0));
+}
+
 // value scaled by 2^60 to a 64-bit integer (repulsion accumulators: magnitudes
 // stay below 8, resolution 2^-60), exact for the float case
 template <typename C> __device__ __forceinline__ long long to_fix60(C v);

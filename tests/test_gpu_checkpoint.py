@@ -108,3 +108,53 @@ def test_other_set_ups_and_bad_files_are_refused(tmp_path):
         s.save(str(tmp_path / "no_such_dir" / "s.lbib"))
     assert ei.value.status == L.LBIB_E_INVALID
     s.close()
+
+
+def test_same_sizes_other_parameters_are_refused(tmp_path):
+    """A state only loads into the set-up that saved it: the same lattice and
+    the same numbers of membranes, vertices, ligands and receptors, but another
+    k_s, k_b, ligand element, receptor position, sigma, density or membrane
+    kind is refused, and so is a file with bytes after its last part."""
+    import dataclasses
+    L = lb()
+    path = str(tmp_path / "s.lbib")
+    base = inputs.capsule_128x32("f64", bonds="stress")
+    s = L.Simulation(base)
+    s.step(5)
+    s.save(path)
+
+    def variant(**kw):
+        wl = dataclasses.replace(base)
+        mem = dataclasses.replace(base.membranes[0], **{k: v for k, v in kw.items() if k in ("ks", "kb", "kind", "ligands", "rho_p")})
+        wl.membranes = [mem]
+        if "receptors" in kw:
+            wl.receptors = kw["receptors"]
+        if "sigma_lu" in kw:
+            wl.sigma_lu = kw["sigma_lu"]
+        return wl
+
+    rec = base.receptors.copy()
+    rec[3, 0] += 0.25
+    lig = base.membranes[0].ligands.copy()
+    lig[-1] = 0
+    lig[0] = 31
+    for wl in (variant(ks=0.051), variant(kb=0.004), variant(receptors=rec), variant(ligands=lig),
+               variant(sigma_lu=2 * base.sigma_lu), variant(kind=1)):
+        o = L.Simulation(wl)
+        with pytest.raises(L.LbibError) as ei:
+            o.load_state(path)
+        assert ei.value.status == L.LBIB_E_INVALID
+        o.close()
+    # the set-up that saved it loads it
+    o = L.Simulation(base)
+    o.load_state(path)
+    np.testing.assert_array_equal(o.markers(), s.markers())
+    o.close()
+    # a trailing byte is refused
+    longer = str(tmp_path / "long.lbib")
+    with open(path, "rb") as fh, open(longer, "wb") as out:
+        out.write(fh.read() + b"\0")
+    with pytest.raises(L.LbibError) as ei:
+        s.load_state(longer)
+    assert ei.value.status == L.LBIB_E_INVALID
+    s.close()
