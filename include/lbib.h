@@ -238,11 +238,35 @@ lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
 /* ---------------------------------------------------------------- ensembles
  * A batch of independent simulations (e.g. a sweep over release positions,
  * capillary numbers and bond strengths on channels of different lengths)
- * advanced together: one CUDA graph per chunk of 16 steps holds every
- * member's captured time step as an independent child graph, so the members'
- * kernels run side by side on the GPU instead of one simulation at a time.
- * The paper runs its cases one by one; this is a throughput form only: every
- * member computes exactly what it computes alone (bitwise).
+ * advanced together, one CUDA graph launch per chunk of 16 steps.  The paper
+ * runs its cases one by one; this is a throughput form only: every member
+ * computes exactly what it computes alone with the same tiling (bitwise).
+ * Two forms, chosen at creation:
+ *  - batched (lbib_ensemble_form = 1): when all members share the precision,
+ *    the walls and the form and shape of the fused kernel (lbib_set_tiling:
+ *    the same row tiles (vec, ty), or the persistent form (npt, 0) with the
+ *    same npt), and all have membranes but no dynamic particles, each time
+ *    step is three launches for all members together: the force kernel over
+ *    every member's force units, the fused kernel over every member's tiles
+ *    (row tiles) or row segments (persistent form) and the advance kernel
+ *    over every member's advance units (work lists over (member, unit) with
+ *    per-member arguments in the launch parameters or in device memory);
+ *  - graph of member graphs (form 0), for any other set of members: each
+ *    member's captured time step is an independent child graph.
+ *
+ *   In the batched form the members are split into groups of at most 64
+ *   (contiguous, about equal nodes); each group's launches form an
+ *   independent branch of the chunk graph, so groups overlap on the GPU.
+ *
+ * lbib_ensemble_form: 1 batched, 0 graph of member graphs, -1 for NULL.
+ * lbib_ensemble_set_groups: regroup a batched ensemble into `groups` groups
+ *   (ceil(n / 64) <= groups <= n; ceil(n / 64) at creation) and recapture its
+ *   graphs; waits for the ensemble's stream.  LBIB_E_STATE if not batched,
+ *   LBIB_E_INVALID out of range.  Results do not depend on the grouping.
+ * lbib_ensemble_groups: the groups in use (0 if not batched, -1 for NULL).
+ * lbib_ensemble_launches_per_step: kernel launches per time step of the
+ *   whole ensemble (3 per group in the batched form, the members' sum
+ *   otherwise).
  *
  * lbib_ensemble_create: members are n distinct contexts on the current device
  *   (their set-up calls done; they are finalised here).  The ensemble takes
@@ -261,6 +285,10 @@ lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n, void* cuda
 lbib_status lbib_ensemble_step(lbib_ensemble* ens, int64_t n);
 lbib_status lbib_ensemble_sync(lbib_ensemble* ens);
 int32_t lbib_ensemble_size(const lbib_ensemble* ens);
+int32_t lbib_ensemble_form(const lbib_ensemble* ens);
+lbib_status lbib_ensemble_set_groups(lbib_ensemble* ens, int32_t groups);
+int32_t lbib_ensemble_groups(const lbib_ensemble* ens);
+int32_t lbib_ensemble_launches_per_step(const lbib_ensemble* ens);
 lbib_ctx* lbib_ensemble_member(lbib_ensemble* ens, int32_t i);
 const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
 void lbib_ensemble_destroy(lbib_ensemble* ens);

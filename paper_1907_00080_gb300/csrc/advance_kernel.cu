@@ -91,10 +91,14 @@ __device__ __forceinline__ void ring_boxes(const MarkerArgs& a, int m, int n, in
 
 // DYN: the context holds dynamic particles (without them their paths are not
 // compiled into the kernel, which keeps its code small)
+//
+// advance_unit is the body for advance unit `u` of the context `a`, whose
+// advance launch has `nblocks` blocks in all (the last of them to finish runs
+// the epilogue): the single-context kernel runs unit blockIdx.x of gridDim.x,
+// the batched kernel (ensembles) one unit of one member per block.
 template <typename C, bool DYN>
-__global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
+__device__ __forceinline__ void advance_unit(const MarkerArgs& a, int u, unsigned nblocks) {
     using E = typename Ext<C>::E;
-    const int u = blockIdx.x;
     const int4 u0 = a.au[2 * u], u1 = a.au[2 * u + 1];
     const int m = u0.x, k0 = u0.y, kn = u0.z, off = u0.w, n = u1.x, kind = u1.y;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     }
 
     // ---- epilogue of the last block: straddling ligands, apply, next step
-    if (!arrive_last(&a.tickets[0], &s_last)) return;
+    if (!arrive_last(&a.tickets[0], &s_last, nblocks)) return;
     for (int q = tid; q < (a.nrec > 0 ? a.nstrad : 0); q += blockDim.x) {
         const int l = a.strad_ligs[q];
         E xa, ya, xb, yb;
@@ -369,6 +373,23 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
     }
 }
 
+template <typename C, bool DYN>
+__global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
+    advance_unit<C, DYN>(a, blockIdx.x, gridDim.x);
+}
+
+// Batched form: the advance units of up to kBatchMax contexts (ensemble
+// members) in one launch, one block per (member, unit); each member's last
+// block runs its epilogue.  Blocks have the threads of the widest member (idle
+// threads beyond a unit's vertices, as in the single-context kernel).
+template <typename C, bool DYN>
+__global__ void __launch_bounds__(kAdvThreads) k_advance_batch(const __grid_constant__ MarkerBatch b) {
+    __shared__ MarkerArgs s_a;
+    const int m = batch_member(b.off, b.n, blockIdx.x);
+    stage_args(&s_a, b.args + m);
+    advance_unit<C, DYN>(s_a, blockIdx.x - b.off[m], (unsigned)s_a.nau);
+}
+
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s) {
     if (a.adv_threads < kChunkV || a.adv_threads > kAdvThreads || a.adv_threads % 32) return cudaErrorInvalidValue;
     if (prec == LBIB_F64) {
@@ -377,6 +398,21 @@ cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_
     } else {
         if (a.has_dyn) k_advance<float, true><<<a.nau, a.adv_threads, 0, s>>>(a);
         else k_advance<float, false><<<a.nau, a.adv_threads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_batch(lbib_precision prec, bool dyn, const MarkerBatch& b, int threads, cudaStream_t s) {
+    if (b.n < 1 || b.n > kBatchMax) return cudaErrorInvalidValue;
+    const int nunits = b.off[b.n];
+    if (nunits <= 0) return cudaSuccess;
+    if (threads < kChunkV || threads > kAdvThreads || threads % 32) return cudaErrorInvalidValue;
+    if (prec == LBIB_F64) {
+        if (dyn) k_advance_batch<double, true><<<nunits, threads, 0, s>>>(b);
+        else k_advance_batch<double, false><<<nunits, threads, 0, s>>>(b);
+    } else {
+        if (dyn) k_advance_batch<float, true><<<nunits, threads, 0, s>>>(b);
+        else k_advance_batch<float, false><<<nunits, threads, 0, s>>>(b);
     }
     return cudaGetLastError();
 }

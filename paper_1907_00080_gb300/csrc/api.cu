@@ -369,16 +369,17 @@ static lbib_status finalize(lbib_ctx* c) {
     if (c->finalized) return LBIB_OK;
     if (!c->vec) default_tiling(c, &c->vec, &c->ty);
     if (c->ty == 0) {
-        // persistent form: one force tile per row segment
-        c->tile_w = 256 * c->vec;
-        c->tile_h = 1;
         CK(prepare_lb_stream(c->prec, c->vec, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, &c->stream_grid));
     } else {
         if ((c->ny + c->ty - 1) / c->ty > kMaxGridY)
             return fail(c, LBIB_E_INVALID, "lattice too tall for the row-tile form: more than 65535 x 16 rows");
-        c->tile_w = 32 * c->vec;
-        c->tile_h = c->ty;
     }
+    // force flags per 32 nodes of a row, in both kernel forms: a flagged tile
+    // reads and later clears the spread force and writes u only there (with
+    // tiles of a whole block or segment, red cells that cross most of them
+    // made nearly every node pay those 40 bytes)
+    c->tile_w = 32;
+    c->tile_h = 1;
     c->tiles_x = (c->nx + c->tile_w - 1) / c->tile_w;
     c->tiles_y = (c->ny + c->tile_h - 1) / c->tile_h;
     c->ntiles = c->tiles_x * c->tiles_y;
@@ -1223,6 +1224,19 @@ extern "C" void lbib_destroy(lbib_ctx* c) {
 // Independent contexts advanced together: one graph per chunk of steps holds
 // every member's captured step graph as a child node with no edges between
 // them, so the members' kernels run side by side on the GPU.
+//
+// Members that share a precision, walls and the form and shape of the fused
+// kernel (row tiles (vec, ty), or the persistent form with npt = vec) and have
+// markers but no dynamic particles are advanced in the batched form: per time
+// step one launch of each kernel covers every member of a group (one block per
+// (member, force unit) and per (member, advance unit); the fused kernel one
+// block per (member, tile), or persistent CTAs walking all members'
+// segments), with the members' arguments in the launch parameters or in
+// device memory.  Groups (at most kBatchMax members each,
+// contiguous, balanced by nodes) are independent branches of the captured
+// chunk graph, so one group's latency-bound marker kernels can run beside
+// another group's bandwidth-bound fused kernel.  Any other set of members
+// runs as a graph of the members' own step graphs.
 struct lbib_ensemble {
     std::vector<lbib_ctx*> m;
     cudaStream_t stream = nullptr;
@@ -1233,6 +1247,14 @@ struct lbib_ensemble {
     std::vector<int> cur0;
     bool own_stream = false;
     std::string err;
+    // batched form
+    bool batched = false;
+    lbib::MarkerArgs* margs = nullptr;             // [2][n] in device memory: [phase][member]
+    std::vector<int> gstart;                       // group g: members [gstart[g], gstart[g + 1])
+    std::vector<lbib::LbBatch> lbb[2];             // [phase][group]
+    std::vector<lbib::MarkerBatch> fbb[2], abb[2];  // [phase][group]
+    int adv_threads = 0;
+    int stream_grid = 0;                           // CTAs of the batched persistent form
 };
 
 namespace {
@@ -1248,7 +1270,169 @@ lbib_status ens_fail(lbib_ensemble* e, lbib_status st, const std::string& msg) {
         if (e_ != cudaSuccess) return ens_fail(e, LBIB_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// whether the members can run in the batched form (see lbib_ensemble)
+static bool batchable(const std::vector<lbib_ctx*>& m) {
+    const lbib_ctx* c0 = m[0];
+    for (const lbib_ctx* c : m) {
+        if (c->prec != c0->prec || c->walls != c0->walls || c->vec != c0->vec || c->ty != c0->ty || c->nv == 0 ||
+            c->ndyn > 0 || c->ma.nfu == 0 || c->ma.nau == 0)
+            return false;
+    }
+    return true;
+}
+
+static void drop_ensemble_graphs(lbib_ensemble* e) {
+    for (int f = 0; f < 2; ++f)
+        for (int k = 0; k < 2; ++k) {
+            if (e->g[f][k]) cudaGraphExecDestroy(e->g[f][k]);
+            e->g[f][k] = nullptr;
+        }
+}
+
+// group boundaries: ngroups contiguous ranges with about equal nodes, none
+// above kBatchMax members (ceil(n / kBatchMax) <= ngroups <= n)
+static std::vector<int> ensemble_groups(const lbib_ensemble* e, int ngroups) {
+    const int n = (int)e->m.size();
+    std::vector<double> cum(n + 1, 0.0);  // nodes of members [0, i)
+    for (int i = 0; i < n; ++i) cum[i + 1] = cum[i] + (double)e->m[i]->nx * e->m[i]->ny;
+    std::vector<int> start{0};
+    for (int g = 1; g < ngroups; ++g) {
+        const int lo = std::max(start.back() + 1, n - (ngroups - g) * kBatchMax);
+        const int hi = std::min(n - (ngroups - g), start.back() + kBatchMax);
+        int b = hi;
+        for (int i = lo; i <= hi; ++i)
+            if (cum[i] >= cum[n] * g / ngroups) {
+                b = i;
+                break;
+            }
+        start.push_back(b);
+    }
+    start.push_back(n);
+    return start;
+}
+
+// the parameter blocks of the batched launches and the device table of the
+// members' marker arguments, for `ngroups` groups
+static lbib_status ensemble_batch_tables(lbib_ensemble* e, int ngroups) {
+    const size_t n = e->m.size();
+    if (!e->margs) {
+        std::vector<MarkerArgs> ma(2 * n);
+        for (size_t i = 0; i < n; ++i) {
+            lbib_ctx* c = e->m[i];
+            for (int p = 0; p < 2; ++p) {
+                const int src = e->cur0[i] ^ p;
+                MarkerArgs a = c->ma;
+                a.gsum = c->G[src];
+                a.flags = c->flags[src];
+                ma[p * n + i] = a;
+            }
+        }
+        ECK(cudaMalloc(&e->margs, sizeof(MarkerArgs) * 2 * n));
+        ECK(cudaMemcpy(e->margs, ma.data(), sizeof(MarkerArgs) * 2 * n, cudaMemcpyHostToDevice));
+    }
+    e->gstart = ensemble_groups(e, ngroups);
+    const int G = (int)e->gstart.size() - 1;
+    e->adv_threads = 0;
+    for (int p = 0; p < 2; ++p) {
+        e->lbb[p].assign(G, LbBatch{});
+        e->fbb[p].assign(G, MarkerBatch{});
+        e->abb[p].assign(G, MarkerBatch{});
+        for (int g = 0; g < G; ++g) {
+            LbBatch& lb = e->lbb[p][g];
+            MarkerBatch& fb = e->fbb[p][g];
+            MarkerBatch& ab = e->abb[p][g];
+            const int i0 = e->gstart[g], i1 = e->gstart[g + 1];
+            lb.n = fb.n = ab.n = i1 - i0;
+            fb.args = ab.args = e->margs + p * n + i0;
+            int kb = 0, fu = 0, au = 0;
+            for (int i = i0; i < i1; ++i) {
+                lbib_ctx* c = e->m[i];
+                const int k = i - i0, src = e->cur0[i] ^ p;
+                // row tiles: blocks of (32 vec) x ty nodes; persistent form: segments of 256 vec nodes
+                const int gx = c->ty > 0 ? (c->nx + 32 * c->vec - 1) / (32 * c->vec)
+                                         : (c->nx + 256 * c->vec - 1) / (256 * c->vec);
+                const int gy = c->ty > 0 ? (c->ny + c->ty - 1) / c->ty : c->ny;
+                lb.off[k] = kb;
+                lb.tiles_x[k] = gx;
+                lb.a[k] = lb_args(c, src, src, 1);
+                fb.off[k] = fu;
+                ab.off[k] = au;
+                kb += gx * gy;
+                fu += c->ma.nfu;
+                au += c->ma.nau;
+                e->adv_threads = std::max(e->adv_threads, c->ma.adv_threads);
+            }
+            lb.off[lb.n] = kb;
+            fb.off[fb.n] = fu;
+            ab.off[ab.n] = au;
+        }
+    }
+    const lbib_ctx* c0 = e->m[0];
+    if (c0->ty == 0)
+        ECK(prepare_lb_stream_batch(c0->prec, c0->vec, c0->walls == LBIB_WALLS_Y_BOUNCEBACK, &e->stream_grid));
+    return LBIB_OK;
+}
+
+// one time step of every member of group g in the batched form, at phase p
+static cudaError_t ensemble_batch_step(const lbib_ensemble* e, int g, int p, cudaStream_t s) {
+    const lbib_ctx* c0 = e->m[0];
+    const bool walls = c0->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    cudaError_t r = launch_forces_batch(c0->prec, e->fbb[p][g], s);
+    if (r == cudaSuccess)
+        r = c0->ty > 0 ? launch_lb_batch(c0->prec, c0->vec, c0->ty, walls, e->lbb[p][g], s)
+                       : launch_lb_stream_batch(c0->prec, c0->vec, walls, e->stream_grid, e->lbb[p][g], s);
+    if (r == cudaSuccess) r = launch_advance_batch(c0->prec, false, e->abb[p][g], e->adv_threads, s);
+    return r;
+}
+
+// capture the batched chunk graphs: each group's steps on a stream of its own,
+// forked from and joined to the capturing stream
+static lbib_status ensemble_build_batched(lbib_ensemble* e, int ngroups) {
+    lbib_status st = ensemble_batch_tables(e, ngroups);
+    if (st != LBIB_OK) return st;
+    const int G = (int)e->gstart.size() - 1;
+    std::vector<cudaStream_t> gs(G, nullptr);
+    std::vector<cudaEvent_t> ev(G + 1, nullptr);
+    cudaStream_t cap = nullptr;
+    cudaError_t r = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    for (int g = 0; g < G && r == cudaSuccess; ++g) r = cudaStreamCreateWithFlags(&gs[g], cudaStreamNonBlocking);
+    for (int k = 0; k <= G && r == cudaSuccess; ++k) r = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    for (int flip = 0; flip < 2 && r == cudaSuccess; ++flip) {
+        for (int kind = 0; kind < 2 && r == cudaSuccess; ++kind) {
+            const int nsteps = kind == 0 ? 1 : kChunk;
+            cudaGraph_t gr = nullptr;
+            r = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (r != cudaSuccess) break;
+            cudaError_t le = cudaEventRecord(ev[G], cap);
+            for (int g = 0; g < G && le == cudaSuccess; ++g) {
+                cudaStream_t s = G == 1 ? cap : gs[g];
+                if (G > 1) le = cudaStreamWaitEvent(s, ev[G], 0);
+                for (int k = 0; k < nsteps && le == cudaSuccess; ++k) le = ensemble_batch_step(e, g, flip ^ (k & 1), s);
+                if (G > 1 && le == cudaSuccess) le = cudaEventRecord(ev[g], s);
+                if (G > 1 && le == cudaSuccess) le = cudaStreamWaitEvent(cap, ev[g], 0);
+            }
+            r = cudaStreamEndCapture(cap, &gr);
+            if (r == cudaSuccess) r = le;
+            if (r == cudaSuccess) r = cudaGraphInstantiate(&e->g[flip][kind], gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    for (cudaStream_t x : gs)
+        if (x) cudaStreamDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+    if (r != cudaSuccess) {
+        drop_ensemble_graphs(e);
+        return ens_fail(e, LBIB_E_CUDA, std::string("capture batched step: ") + cudaGetErrorString(r));
+    }
+    e->batched = true;
+    return LBIB_OK;
+}
+
 static lbib_status ensemble_build(lbib_ensemble* e) {
+    if (batchable(e->m))
+        return ensemble_build_batched(e, ((int)e->m.size() + kBatchMax - 1) / kBatchMax);
     for (int flip = 0; flip < 2; ++flip) {
         for (int kind = 0; kind < 2; ++kind) {
             cudaGraph_t g;
@@ -1312,6 +1496,7 @@ extern "C" lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n,
         for (int f = 0; f < 2; ++f)
             for (int k = 0; k < 2; ++k)
                 if (e->g[f][k]) cudaGraphExecDestroy(e->g[f][k]);
+        if (e->margs) cudaFree(e->margs);
         if (e->own_stream) cudaStreamDestroy(e->stream);
         delete e;
         return st;
@@ -1355,6 +1540,31 @@ extern "C" lbib_status lbib_ensemble_sync(lbib_ensemble* e) {
 
 extern "C" int32_t lbib_ensemble_size(const lbib_ensemble* e) { return e ? (int32_t)e->m.size() : -1; }
 
+extern "C" int32_t lbib_ensemble_form(const lbib_ensemble* e) { return e ? (e->batched ? 1 : 0) : -1; }
+
+extern "C" lbib_status lbib_ensemble_set_groups(lbib_ensemble* e, int32_t groups) {
+    if (!e) return LBIB_E_INVALID;
+    if (!e->batched) return ens_fail(e, LBIB_E_STATE, "groups apply to the batched form only");
+    const int n = (int)e->m.size();
+    if (groups < (n + kBatchMax - 1) / kBatchMax || groups > n)
+        return ens_fail(e, LBIB_E_INVALID, "groups must lie in [ceil(n / 64), n]");
+    ECK(cudaStreamSynchronize(e->stream));
+    drop_ensemble_graphs(e);
+    return ensemble_build_batched(e, groups);
+}
+
+extern "C" int32_t lbib_ensemble_groups(const lbib_ensemble* e) {
+    return e ? (e->batched ? (int32_t)e->gstart.size() - 1 : 0) : -1;
+}
+
+extern "C" int32_t lbib_ensemble_launches_per_step(const lbib_ensemble* e) {
+    if (!e) return -1;
+    if (e->batched) return 3 * ((int32_t)e->gstart.size() - 1);
+    int k = 0;
+    for (const lbib_ctx* c : e->m) k += lbib_kernels_per_step(c);
+    return k;
+}
+
 extern "C" lbib_ctx* lbib_ensemble_member(lbib_ensemble* e, int32_t i) {
     if (!e || i < 0 || i >= (int32_t)e->m.size()) return nullptr;
     return e->m[i];
@@ -1368,6 +1578,7 @@ extern "C" void lbib_ensemble_destroy(lbib_ensemble* e) {
     for (int f = 0; f < 2; ++f)
         for (int k = 0; k < 2; ++k)
             if (e->g[f][k]) cudaGraphExecDestroy(e->g[f][k]);
+    if (e->margs) cudaFree(e->margs);
     for (lbib_ctx* c : e->m) lbib_destroy(c);
     if (e->own_stream) cudaStreamDestroy(e->stream);
     delete e;

@@ -89,10 +89,14 @@ constexpr int kScreenIter = 8;                    // segment boxes per lane load
 //                       accumulated per vertex in fixed point (order-free)
 //   phase 3  all        spreading: (vertex, node) pairs into the fixed-point field
 //                       (of a dynamic particle: its forcing term, see dynamic_kernels.cu)
+//
+// forces_unit is the body for force unit `unit` of the context `a`: the
+// single-context kernel runs unit blockIdx.x, the batched kernel (ensembles)
+// one unit of one member per block.
 template <typename C>
-__global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
+__device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
     using E = typename Ext<C>::E;
-    const int4 u0 = a.fu[2 * blockIdx.x], u1 = a.fu[2 * blockIdx.x + 1];
+    const int4 u0 = a.fu[2 * unit], u1 = a.fu[2 * unit + 1];
     const int m = u0.x, k0 = u0.y, kn = u0.z, off = u0.w, n = u1.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // positions of vertices k0-2 .. k0+kn+1 (slot p <-> vertex k0 - 2 + p)
@@ -493,6 +497,24 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
     }
 }
 
+template <typename C>
+__global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
+    forces_unit<C>(a, blockIdx.x);
+}
+
+// Batched form: the force units of up to kBatchMax contexts (ensemble
+// members) in one launch, one block per (member, unit).  The member's
+// arguments are staged in shared memory.
+// (three blocks per SM: the batch's thousands of blocks are limited by how
+// many fit, not by one block's latency)
+template <typename C>
+__global__ void __launch_bounds__(kForceThreads, 3) k_forces_batch(const __grid_constant__ MarkerBatch b) {
+    __shared__ MarkerArgs s_a;
+    const int m = batch_member(b.off, b.n, blockIdx.x);
+    stage_args(&s_a, b.args + m);
+    forces_unit<C>(s_a, blockIdx.x - b.off[m]);
+}
+
 // ---------------------------------------------------------------- segments
 // segment boxes alone (before the first step and after user-written markers):
 // one group of kSegV lanes per segment
@@ -550,6 +572,15 @@ cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, do
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int, cudaStream_t s) {
     if (is_f64(prec)) k_forces<double><<<a.nfu, kForceThreads, 0, s>>>(a);
     else k_forces<float><<<a.nfu, kForceThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces_batch(lbib_precision prec, const MarkerBatch& b, cudaStream_t s) {
+    if (b.n < 1 || b.n > kBatchMax) return cudaErrorInvalidValue;
+    const int nunits = b.off[b.n];
+    if (nunits <= 0) return cudaSuccess;
+    if (is_f64(prec)) k_forces_batch<double><<<nunits, kForceThreads, 0, s>>>(b);
+    else k_forces_batch<float><<<nunits, kForceThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -37,14 +37,16 @@ __device__ __forceinline__ void load_pack(const S* __restrict__ row, int x0, boo
 // from the neighbouring lane (or, at the warp edge, with one scalar load).
 // IB: 0 no markers; 1 the spread force read in the tiles the spreading
 // flagged; 2 the same, with every node's force read up front (see below)
+// The tile (bx, by) of the lattice `a`: the body of the single-lattice kernel
+// (bx, by = blockIdx) and of the batched kernel (one block per (lattice, tile)).
 template <typename S, int VEC, bool WALLS, int IB>
-__global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
+__device__ __forceinline__ void lb_tile(const LbArgs& a, int bx, int by) {
     constexpr bool HAS_IB = IB > 0;
     using C = typename Storage<S>::C;
     const int lane = threadIdx.x;
     const int nx = a.nx, ny = a.ny;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int x0 = (blockIdx.x * 32 + lane) * VEC;
+    const int y = by * blockDim.y + threadIdx.y;
+    const int x0 = (bx * 32 + lane) * VEC;
     const bool ok = (y < ny) && (x0 < nx);
     const size_t N = (size_t)nx * ny;
     const S* __restrict__ src = static_cast<const S*>(a.src);
@@ -59,6 +61,18 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     if (pre_g) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) gpre[k] = a.gsum[(size_t)y * nx + x0 + k];
+    }
+    // this thread's force tile and its flags, read before the populations so
+    // that the flag (an L2 hit) is back while the population loads are still
+    // in flight and the force load that depends on it overlaps them: during a
+    // step the row-tile form flags segments of 32 nodes of one row (tile_w =
+    // 32, tile_h = 1), so the threads that share a flag are lanes of one warp;
+    // in the fields-only read-back the tiles may be those of the persistent form
+    int t = 0, flag = 0, flag_o = 0;
+    if (HAS_IB) {
+        t = (min(y, ny - 1) / a.tile_h) * a.tiles_x + min(x0, nx - 1) / a.tile_w;
+        flag = a.flags[t];
+        if (a.clear_other) flag_o = a.flags_other[t];
     }
 
     // ---- pull streaming (Eq. BGK left side) with half-way bounce-back
@@ -119,12 +133,11 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     }
     bool flagged = false;
     if (HAS_IB) {
-        // this thread's force tile (one block per tile during a step; in the
-        // fields-only read-back the tiles may be those of the other kernel form)
-        const int t = (min(y, ny - 1) / a.tile_h) * a.tiles_x + min(x0, nx - 1) / a.tile_w;
-        flagged = a.flags[t] != 0;
-        const bool fo = a.clear_other && a.flags_other[t] != 0;
-        __syncthreads();  // every warp has read flags_other[t] before it is cleared
+        flagged = flag != 0;
+        const bool fo = flag_o != 0;
+        // every thread has read flags_other[t] before it is cleared
+        if (a.tile_h == 1 && a.tile_w <= 32 * VEC && 32 % a.tile_w == 0) __syncwarp();
+        else __syncthreads();
         const size_t node = (size_t)y * nx + x0;
         if (flagged && ok) {
 #pragma unroll
@@ -139,7 +152,8 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) a.gclear[node + k] = make_longlong2(0, 0);
             }
-            if (threadIdx.x == 0 && threadIdx.y == 0) a.flags_other[t] = 0;
+            // one thread per flag: the one at the tile's first node
+            if (ok && x0 % a.tile_w == 0 && y % a.tile_h == 0) a.flags_other[t] = 0;
         }
     }
 
@@ -192,6 +206,25 @@ __global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
     }
 }
 
+template <typename S, int VEC, bool WALLS, int IB>
+__global__ void __launch_bounds__(512) k_lb_step(const LbArgs a) {
+    lb_tile<S, VEC, WALLS, IB>(a, blockIdx.x, blockIdx.y);
+}
+
+// Batched form: the tiles of up to kBatchMax lattices (ensemble members, each
+// with its own arguments and the same tile shape) in one launch, one block per
+// (lattice, tile), the tiles of a member row by row.  The member's arguments
+// come from the launch parameters into shared memory; the tile then computes
+// exactly what the single-lattice kernel computes.
+template <typename S, int VEC, bool WALLS>
+__global__ void __launch_bounds__(512) k_lb_step_batch(const __grid_constant__ LbBatch b) {
+    __shared__ LbArgs s_a;
+    const int m = batch_member(b.off, b.n, blockIdx.x);
+    const int local = blockIdx.x - b.off[m], tx = b.tiles_x[m];
+    stage_args(&s_a, &b.a[m]);
+    lb_tile<S, VEC, WALLS, 1>(s_a, local % tx, local / tx);
+}
+
 template <typename S, int VEC>
 static cudaError_t launch_lb_t(int ty, bool walls, bool has_ib, const LbArgs& a, cudaStream_t s) {
     dim3 block(32, ty);
@@ -209,6 +242,42 @@ static cudaError_t launch_lb_t(int ty, bool walls, bool has_ib, const LbArgs& a,
         else k_lb_step<S, VEC, false, 0><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
+}
+
+template <typename S, int VEC>
+static cudaError_t launch_lb_batch_t(int ty, bool walls, const LbBatch& b, cudaStream_t s) {
+    const int nblocks = b.off[b.n];
+    if (nblocks <= 0) return cudaSuccess;
+    dim3 block(32, ty);
+    if (walls) k_lb_step_batch<S, VEC, true><<<nblocks, block, 0, s>>>(b);
+    else k_lb_step_batch<S, VEC, false><<<nblocks, block, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lb_batch(lbib_precision prec, int vec, int ty, bool walls, const LbBatch& b, cudaStream_t s) {
+    if (b.n < 1 || b.n > kBatchMax) return cudaErrorInvalidValue;
+    switch (prec) {
+        case LBIB_F64:
+            if (vec == 1) return launch_lb_batch_t<double, 1>(ty, walls, b, s);
+            if (vec == 2) return launch_lb_batch_t<double, 2>(ty, walls, b, s);
+            break;
+        case LBIB_F32:
+            if (vec == 1) return launch_lb_batch_t<float, 1>(ty, walls, b, s);
+            if (vec == 2) return launch_lb_batch_t<float, 2>(ty, walls, b, s);
+            if (vec == 4) return launch_lb_batch_t<float, 4>(ty, walls, b, s);
+            break;
+        case LBIB_F32_STORE_F16:
+            if (vec == 2) return launch_lb_batch_t<__half, 2>(ty, walls, b, s);
+            if (vec == 4) return launch_lb_batch_t<__half, 4>(ty, walls, b, s);
+            if (vec == 8) return launch_lb_batch_t<__half, 8>(ty, walls, b, s);
+            break;
+        case LBIB_F32_STORE_BF16:
+            if (vec == 2) return launch_lb_batch_t<__nv_bfloat16, 2>(ty, walls, b, s);
+            if (vec == 4) return launch_lb_batch_t<__nv_bfloat16, 4>(ty, walls, b, s);
+            if (vec == 8) return launch_lb_batch_t<__nv_bfloat16, 8>(ty, walls, b, s);
+            break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,

@@ -11,7 +11,9 @@
 // thread takes NPT consecutive nodes: one vector shared-memory load per
 // direction (plus one element for the x-shifted directions) and one vector
 // global store per direction.  The spread IB force is read straight from
-// global memory in the few segments whose tile holds markers.
+// global memory where the segment's 32-node force tiles hold markers (their
+// flags are fetched kStages segments ahead by one warp and kept in shared
+// memory with the stage).
 //
 // Staged row of direction i (HALO = one 16-byte chunk on each side):
 //   [x0 - HALO, x0 + W + HALO) of plane i, row y - e_iy   (interior rows)
@@ -19,7 +21,11 @@
 // The periodic x neighbours at the ends of a row come from separate 16-byte
 // copies of the other end of the row.  The arithmetic per node is
 // collide_node(), the same as the row-tile kernel's, so both forms give the
-// same bits.  The force-tile geometry is one tile per segment (W x 1).
+// same bits.  The force tiles are 32 nodes of one row, as in the row-tile
+// form.  The same bodies serve one lattice (arguments in the kernel's
+// parameters) and a batch of lattices (ensemble members: the work list runs
+// over all members' segments, and the member's arguments are copied into the
+// stage's slot of shared memory when its segment is staged).
 //
 // Paper: Coclite, arXiv 1907.00080, Sec. 2.1 (Eqs. BGK, feq, GaussHermite),
 // Sec. 2.2 (Eqs. forcedBGK, ForcingTerm), Sec. 3 (periodic x, walls in y).
@@ -104,33 +110,236 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned
                  : "memory");
 }
 
+
+// ---------------------------------------------------------------- work lists
+// Where the items (row segments) of the work list lie, and the arguments of
+// the lattice each belongs to.  locate() is valid at any time; staged(st)
+// is the copy the staging thread made into stage st (for one lattice, the
+// kernel's own parameters).
+struct ItemRef {
+    int y, x0;
+};
+
+template <typename S, int NPT>
+struct OneLattice {
+    static constexpr int W = Geom<S, NPT>::W;
+    const LbArgs& a;
+    int nseg;
+    __device__ explicit OneLattice(const LbArgs& a_) : a(a_), nseg((a_.nx + W - 1) / W) {}
+    __device__ long long count() const { return (long long)a.ny * nseg; }
+    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
+        p = {(int)(item / nseg), (int)(item % nseg) * W};
+        return a;
+    }
+    // the staging warp (all lanes) prepares stage st for `item`: nothing to copy
+    __device__ void stage_args(long long, int, int) const {}
+    __device__ const LbArgs& staged(int) const { return a; }
+    __device__ ItemRef staged_pos(long long item, int) const { return {(int)(item / nseg), (int)(item % nseg) * W}; }
+};
+
+// b.off: first item of each member; b.tiles_x: segments per row of each member
+template <typename S, int NPT>
+struct ManyLattices {
+    static constexpr int W = Geom<S, NPT>::W;
+    const LbBatch& b;
+    LbArgs* s_args;  // [kStages] in shared memory
+    ItemRef* s_pos;  // [kStages]
+    __device__ long long count() const { return b.off[b.n]; }
+    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
+        const int m = batch_member(b.off, b.n, (int)item);
+        const int l = (int)item - b.off[m], ns = b.tiles_x[m];
+        p = {l / ns, (l % ns) * W};
+        return b.a[m];
+    }
+    // the staging warp (all lanes) copies the member's arguments, 8-byte
+    // words, and lane 0 the item's position, into stage st's slots
+    __device__ void stage_args(long long item, int st, int lane) const {
+        ItemRef p;
+        const LbArgs& A = locate(item, p);
+        constexpr int NW = (int)(sizeof(LbArgs) / 8);
+        for (int w = lane; w < NW; w += 32)
+            reinterpret_cast<long long*>(&s_args[st])[w] = reinterpret_cast<const long long*>(&A)[w];
+        if (lane == 0) s_pos[st] = p;
+    }
+    __device__ const LbArgs& staged(int st) const { return s_args[st]; }
+    __device__ ItemRef staged_pos(long long, int st) const { return s_pos[st]; }
+};
+
+// Force-tile flags of one item (segment): W / 32 tiles of 32 nodes, lane q of
+// the fetching warp taking tiles q and q + 32.  Fetched kStages items ahead into
+// registers, stored into the stage's shared slot once that stage is free.
+struct FlagRegs {
+    int f[2], o[2];
+};
+template <int W, typename Items>
+__device__ __forceinline__ void fetch_flags(const Items& it, long long item, int lane, FlagRegs& r) {
+    constexpr int NF = W / 32;
+    r.f[0] = r.f[1] = r.o[0] = r.o[1] = 0;
+    ItemRef p;
+    const LbArgs& A = it.locate(item, p);
+    if (A.flags == nullptr) return;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = lane + 32 * h;
+        if (q < NF && p.x0 + 32 * q < A.nx) {
+            const long long t = (long long)p.y * A.tiles_x + (p.x0 >> 5) + q;
+            r.f[h] = A.flags[t];
+            r.o[h] = A.clear_other ? A.flags_other[t] : 0;
+        }
+    }
+}
+template <int W>
+__device__ __forceinline__ void keep_flags(const FlagRegs& r, int lane, int* fl, int* fo) {
+    constexpr int NF = W / 32;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = lane + 32 * h;
+        if (q < NF) {
+            fl[q] = r.f[h];
+            fo[q] = r.o[h];
+        }
+    }
+}
+
+// Stage the nine source rows of `item` (plane i row y - e_iy, or plane opp(i)
+// row y at a wall; W nodes and a 16-byte halo each side, the periodic ends by
+// separate copies) into stage `st`: lane ln of the issuing group copies the
+// rows i = ln, ln + nl, ...; the caller has set the stage's expected bytes
+template <typename S, int NPT, bool WALLS>
+__device__ __forceinline__ void stage_rows(const LbArgs& A, ItemRef p, uint32_t base, uint32_t bar, int ln, int nl) {
+    using Gm = Geom<S, NPT>;
+    constexpr int H = Gm::H, W = Gm::W;
+    const int nx = A.nx, ny = A.ny;
+    const size_t N = (size_t)nx * ny;
+    const S* __restrict__ src = static_cast<const S*>(A.src);
+    const int wlen = min(W, nx - p.x0);
+    const unsigned row_bytes = (unsigned)((wlen + 2 * H) * sizeof(S));
+    const bool interior = p.x0 >= H && p.x0 + wlen + H <= nx;
+    for (int i = ln; i < 9; i += nl) {
+        int sy = p.y - cy(i), plane = i;
+        if (WALLS) {
+            if (sy < 0 || sy >= ny) {
+                plane = opp(i);
+                sy = p.y;
+            }
+        } else {
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        }
+        const S* row = src + (size_t)plane * N + (size_t)sy * nx;
+        const uint32_t d = base + i * Gm::ROW_BYTES;
+        if (interior) {
+            bulk_g2s(d, row + (p.x0 - H), row_bytes, bar);
+        } else {
+            bulk_g2s(d, row + (p.x0 == 0 ? nx - H : p.x0 - H), 16u, bar);
+            bulk_g2s(d + 16u, row + p.x0, (unsigned)(wlen * sizeof(S)), bar);
+            bulk_g2s(d + 16u + (unsigned)(wlen * sizeof(S)), row + (p.x0 + wlen == nx ? 0 : p.x0 + wlen), 16u, bar);
+        }
+    }
+}
+template <typename S, int NPT>
+__device__ __forceinline__ unsigned stage_bytes(const LbArgs& A, ItemRef p) {
+    using Gm = Geom<S, NPT>;
+    const int wlen = min(Gm::W, A.nx - p.x0);
+    return 9u * (unsigned)((wlen + 2 * Gm::H) * sizeof(S));
+}
+
+// One thread's NPT nodes of a staged segment: pull from the stage, add the
+// spread force where its tile is flagged, collide, store; write u where
+// flagged; clear the other parity's force where its tile was flagged (and the
+// flag, by the thread at the tile's first node).
+template <typename S, int NPT, bool WALLS>
+__device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp, int j0, int flag, int flag_o) {
+    using C = typename Storage<S>::C;
+    using Gm = Geom<S, NPT>;
+    constexpr int H = Gm::H;
+    const int nx = A.nx, ny = A.ny, y = p.y;
+    const size_t N = (size_t)nx * ny;
+    S* __restrict__ dst = static_cast<S*>(A.dst);
+    const C om = C(A.omega);
+    const C pre = C(1) - C(0.5) * om;
+    const C om3 = C(3.0 * A.omega);
+    const float inv = A.inv_scale;
+    const float scl = 1.0f / inv;  // 2^k, exact
+    // pull: f_i(x) = d*_i(x - e_i), or d*_opp(i)(x) where x - e_i is outside the walls
+    C f[9][NPT];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool bb = WALLS && (y - cy(i) < 0 || y - cy(i) >= ny);
+        const S* rp = sp + i * Gm::ROW + H + j0;
+        const Vec<S, NPT> v = *reinterpret_cast<const Vec<S, NPT>*>(rp);
+        if (bb || cx(i) == 0) {
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
+            if (bb && cx(i) != 0) {
+                // the momentum of a moving wall (diagonals only)
+                const C t = C(cx(i)) * wall_term<C>(A, cy(i) > 0);
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) f[i][q] += t;
+            }
+        } else if (cx(i) == 1) {
+            f[i][0] = Storage<S>::load(rp[-1], inv);
+#pragma unroll
+            for (int q = 1; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q - 1], inv);
+        } else {
+#pragma unroll
+            for (int q = 0; q < NPT - 1; ++q) f[i][q] = Storage<S>::load(v.v[q + 1], inv);
+            f[i][NPT - 1] = Storage<S>::load(rp[NPT], inv);
+        }
+    }
+    const size_t node0 = (size_t)y * nx + p.x0 + j0;
+    Vec<S, NPT> o[9];
+    Vec<C, NPT> pu, pv;
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+        C Gx = C(A.gx), Gy = C(A.gy);
+        if (flag) {
+            const longlong2 g = A.gsum[node0 + q];
+            Gx += from_fix<C>(g.x);
+            Gy += from_fix<C>(g.y);
+        }
+        C fq[9], out[9], rho;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
+        collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];
+    if (flag) {
+        // velocity for the interpolation to the markers (Sec. 2.3)
+        *reinterpret_cast<Vec<C, NPT>*>(static_cast<C*>(A.ux) + node0) = pu;
+        *reinterpret_cast<Vec<C, NPT>*>(static_cast<C*>(A.uy) + node0) = pv;
+    }
+    if (flag_o) {
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) A.gclear[node0 + q] = make_longlong2(0, 0);
+        // the tile's flag was fetched kStages segments ago; nothing reads it again
+        if (((p.x0 + j0) & 31) == 0) A.flags_other[(long long)y * A.tiles_x + ((p.x0 + j0) >> 5)] = 0;
+    }
+}
+
 // Producer-warp schedule (16-bit storage): 288 threads.  Warps 0-7 consume
 // (collide the staged segment; they leave each segment together through named
 // barrier 1), warp 8 produces: lane 0 waits for the stage's "empty" barrier
-// (one arrival once the consumers have passed the segment), then lanes 0-8
+// (one arrival once the consumers have passed the segment), the lanes store
+// the segment's tile flags, lane 0 sets the expected bytes, then lanes 0-8
 // each issue the copies of one direction.  Stage s also has a "full" barrier
 // (the producer's expect-tx plus the copies' bytes).  Issuing from nine lanes
 // instead of one thread keeps the producer ahead of the short 16-bit segments.
-template <typename S, int NPT, bool WALLS>
-__global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
-    using C = typename Storage<S>::C;
+template <typename S, int NPT, bool WALLS, typename Items>
+__device__ __forceinline__ void stream_ws(const Items& it) {
     using Gm = Geom<S, NPT>;
-    constexpr int H = Gm::H, W = Gm::W;
+    constexpr int W = Gm::W, NF = W / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kStages];
     __shared__ __align__(8) unsigned long long empty[kStages];
-    __shared__ int s_meta[kStages];
+    __shared__ int s_fl[kStages][NF], s_fo[kStages][NF];
     __shared__ int s_last_issued[kStages];
     __shared__ volatile int s_abort;
 
     const int tid = threadIdx.x;
-    const int nx = a.nx, ny = a.ny;
-    const int nseg = (nx + W - 1) / W;
-    const long long n_items = (long long)ny * nseg;
-    const size_t N = (size_t)nx * ny;
-    const S* __restrict__ src = static_cast<const S*>(a.src);
-    S* __restrict__ dst = static_cast<S*>(a.dst);
-    const bool has_ib = a.flags != nullptr;
+    const long long n_items = it.count();
     const long long first = blockIdx.x, stride = gridDim.x;
     const int my_n = first < n_items ? (int)((n_items - 1 - first) / stride + 1) : 0;
     const uint32_t smem0 = smem_addr(smem);
@@ -146,162 +355,55 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
     }
     __syncthreads();
 
-    // producer warp: stage the rows of the k-th item of this CTA into stage
-    // k % kStages; lane 0 sets the expected bytes, then lane i < 9 copies the
-    // source row of direction i
-    auto issue = [&](int k, int flagged, int fo, int ln) {
-        const long long item = first + (long long)k * stride;
-        const int stage = k % kStages;
-        const int y = (int)(item / nseg);
-        const int x0 = (int)(item % nseg) * W;
-        const int wlen = min(W, nx - x0);
-        const uint32_t bar = smem_addr(&bars[stage]);
-        const uint32_t base = smem0 + stage * Gm::STAGE_BYTES;
-        const unsigned row_bytes = (unsigned)((wlen + 2 * H) * sizeof(S));
-        if (ln == 0) {
-            s_meta[stage] = flagged | (fo << 1);
-            mbar_expect_tx(bar, 9u * row_bytes);
-        }
-        __syncwarp();
-        if (ln < 9) {
-            const int i = ln;
-            int sy = y - cy(i), plane = i;
-            if (WALLS) {
-                if (sy < 0 || sy >= ny) {
-                    plane = opp(i);
-                    sy = y;
-                }
-            } else {
-                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-            }
-            const S* row = src + (size_t)plane * N + (size_t)sy * nx;
-            const uint32_t d = base + i * Gm::ROW_BYTES;
-            if (x0 >= H && x0 + wlen + H <= nx) {
-                bulk_g2s(d, row + (x0 - H), row_bytes, bar);
-            } else {
-                bulk_g2s(d, row + (x0 == 0 ? nx - H : x0 - H), 16u, bar);
-                bulk_g2s(d + 16u, row + x0, (unsigned)(wlen * sizeof(S)), bar);
-                bulk_g2s(d + 16u + (unsigned)(wlen * sizeof(S)), row + (x0 + wlen == nx ? 0 : x0 + wlen), 16u, bar);
-            }
-        }
-    };
-    auto item_flags = [&](int k, int& flagged, int& fo) {
-        const long long item = first + (long long)k * stride;
-        flagged = has_ib && a.flags[item] != 0;
-        fo = (has_ib && a.clear_other && a.flags_other[item] != 0) ? 1 : 0;
-    };
-
     const int warp = tid >> 5, lane = tid & 31;
     if (warp == kConsumerWarps) {
         // ---- producer: stage segment k once the consumers have left the
-        // segment k - kStages that used the same stage; tile flags fetched three
-        // segments ahead by lane 0 (their latency stays off the producer's path)
-        int fl = 0, fo = 0, f1 = 0, o1 = 0, f2 = 0, o2 = 0;
-        if (lane == 0) {
-            if (my_n > 0) item_flags(0, fl, fo);
-            if (my_n > 1) item_flags(1, f1, o1);
-            if (my_n > 2) item_flags(2, f2, o2);
-        }
+        // segment k - kStages that used the same stage; its tile flags were
+        // fetched three segments ahead (their latency stays off the producer's path)
+        FlagRegs r0, r1, r2;
+        r0 = r1 = r2 = FlagRegs{{0, 0}, {0, 0}};
+        if (my_n > 0) fetch_flags<W>(it, first, lane, r0);
+        if (my_n > 1) fetch_flags<W>(it, first + stride, lane, r1);
+        if (my_n > 2) fetch_flags<W>(it, first + 2 * stride, lane, r2);
         for (int k = 0; k < my_n; ++k) {
             const int stage = k % kStages;
+            const long long item = first + (long long)k * stride;
             int stop = 0;
             if (lane == 0) {
-                if (k >= kStages &&
-                    !mbar_wait(smem_addr(&empty[stage]), (uint32_t)(((k / kStages) - 1) & 1)))
+                if (k >= kStages && !mbar_wait(smem_addr(&empty[stage]), (uint32_t)(((k / kStages) - 1) & 1)))
                     s_abort = 1;
                 stop = s_abort;
-                // the previous parity's flag of this tile is read here and only here
-                if (!stop && fo) a.flags_other[first + (long long)k * stride] = 0;
             }
             stop = __shfl_sync(0xffffffffu, stop, 0);
             if (stop) break;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const int flb = __shfl_sync(0xffffffffu, fl, 0), fob = __shfl_sync(0xffffffffu, fo, 0);
-            issue(k, flb, fob, lane);
-            if (lane == 0) {
-                s_last_issued[stage] = k;
-                fl = f1;
-                fo = o1;
-                f1 = f2;
-                o1 = o2;
-                if (k + 3 < my_n) item_flags(k + 3, f2, o2);
-            }
+            keep_flags<W>(r0, lane, s_fl[stage], s_fo[stage]);
+            it.stage_args(item, stage, lane);
+            __syncwarp();
+            const LbArgs& A = it.staged(stage);
+            const ItemRef p = it.staged_pos(item, stage);
+            const uint32_t bar = smem_addr(&bars[stage]);
+            if (lane == 0) mbar_expect_tx(bar, stage_bytes<S, NPT>(A, p));
+            __syncwarp();
+            if (lane < 9) stage_rows<S, NPT, WALLS>(A, p, smem0 + stage * Gm::STAGE_BYTES, bar, lane, 9);
+            if (lane == 0) s_last_issued[stage] = k;
+            r0 = r1;
+            r1 = r2;
+            if (k + 3 < my_n) fetch_flags<W>(it, first + (long long)(k + 3) * stride, lane, r2);
         }
     } else {
         // ---- consumers
-        const C om = C(a.omega);
-        const C pre = C(1) - C(0.5) * om;
-        const C om3 = C(3.0 * a.omega);
-        const float inv = a.inv_scale;
-        const float scl = 1.0f / inv;  // 2^k, exact
-        C* __restrict__ uxf = static_cast<C*>(a.ux);
-        C* __restrict__ uyf = static_cast<C*>(a.uy);
         for (int k = 0; k < my_n; ++k) {
             const int stage = k % kStages;
             const bool ok = mbar_wait_sleep(smem_addr(&bars[stage]), (uint32_t)((k / kStages) & 1));
             const long long item = first + (long long)k * stride;
-            const int y = (int)(item / nseg);
-            const int x0 = (int)(item % nseg) * W;
-            const int wlen = min(W, nx - x0);
-            const int meta = s_meta[stage];
-            const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
+            const LbArgs& A = it.staged(stage);
+            const ItemRef p = it.staged_pos(item, stage);
+            const int wlen = min(W, A.nx - p.x0);
             const int j0 = tid * NPT;
             if (ok && j0 < wlen) {
-                // pull: f_i(x) = d*_i(x - e_i), or d*_opp(i)(x) where x - e_i is outside the walls
-                C f[9][NPT];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const bool bb = WALLS && (y - cy(i) < 0 || y - cy(i) >= ny);
-                    const S* rp = sp + i * Gm::ROW + H + j0;
-                    const Vec<S, NPT> v = *reinterpret_cast<const Vec<S, NPT>*>(rp);
-                    if (bb || cx(i) == 0) {
-#pragma unroll
-                        for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
-                        if (bb && cx(i) != 0) {
-                            // the momentum of a moving wall (diagonals only)
-                            const C t = C(cx(i)) * wall_term<C>(a, cy(i) > 0);
-#pragma unroll
-                            for (int q = 0; q < NPT; ++q) f[i][q] += t;
-                        }
-                    } else if (cx(i) == 1) {
-                        f[i][0] = Storage<S>::load(rp[-1], inv);
-#pragma unroll
-                        for (int q = 1; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q - 1], inv);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < NPT - 1; ++q) f[i][q] = Storage<S>::load(v.v[q + 1], inv);
-                        f[i][NPT - 1] = Storage<S>::load(rp[NPT], inv);
-                    }
-                }
-                const size_t node0 = (size_t)y * nx + x0 + j0;
-                Vec<S, NPT> o[9];
-                Vec<C, NPT> pu, pv;
-#pragma unroll
-                for (int q = 0; q < NPT; ++q) {
-                    C Gx = C(a.gx), Gy = C(a.gy);
-                    if (meta & 1) {
-                        const longlong2 g = a.gsum[node0 + q];
-                        Gx += from_fix<C>(g.x);
-                        Gy += from_fix<C>(g.y);
-                    }
-                    C fq[9], out[9], rho;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
-                    collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
-                }
-#pragma unroll
-                for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];
-                if (meta & 1) {
-                    // velocity for the interpolation to the markers (Sec. 2.3)
-                    *reinterpret_cast<Vec<C, NPT>*>(uxf + node0) = pu;
-                    *reinterpret_cast<Vec<C, NPT>*>(uyf + node0) = pv;
-                }
-                if (meta & 2) {
-#pragma unroll
-                    for (int q = 0; q < NPT; ++q) a.gclear[node0 + q] = make_longlong2(0, 0);
-                }
+                const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
+                consume<S, NPT, WALLS>(A, p, sp, j0, s_fl[stage][j0 >> 5], s_fo[stage][j0 >> 5]);
             }
             // the consumer warps leave the segment together (named barrier 1):
             // their stores go out as one burst per segment; one arrival frees the stage
@@ -324,7 +426,8 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
         // a wait gave up: report it, then wait (bounded) for the copies still in
         // flight (the last segment staged into each stage) before the shared
         // memory is released
-        atomicOr(a.status, ST_TIMEOUT);
+        ItemRef p0;
+        atomicOr(it.locate(first, p0).status, ST_TIMEOUT);
         for (int st = 0; st < kStages; ++st) {
             const int m = s_last_issued[st];
             if (m >= 0) mbar_wait(smem_addr(&bars[st]), (uint32_t)((m / kStages) & 1));
@@ -332,26 +435,20 @@ __global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
     }
 }
 
-// Barrier schedule (FP32, FP64): 256 threads; a CTA barrier ends each segment
-// and thread 0 then refills the stage that segment used with the segment
-// kStages ahead (its expected bytes and the nine row copies).
-template <typename S, int NPT, bool WALLS>
-__global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
-    using C = typename Storage<S>::C;
+// Barrier schedule (FP32, FP64): 256 threads; a CTA barrier ends each segment;
+// then warp 0 refills the stage with the segment kStages ahead: the tile flags
+// it fetched at the start of this one, the arguments (batches), the expected
+// bytes and the nine row copies (lanes 0-8, one direction each).
+template <typename S, int NPT, bool WALLS, typename Items>
+__device__ __forceinline__ void stream_bar(const Items& it) {
     using Gm = Geom<S, NPT>;
-    constexpr int H = Gm::H, W = Gm::W;
+    constexpr int W = Gm::W, NF = W / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kStages];
-    __shared__ int s_meta[kStages];
+    __shared__ int s_fl[kStages][NF], s_fo[kStages][NF];
 
-    const int tid = threadIdx.x;
-    const int nx = a.nx, ny = a.ny;
-    const int nseg = (nx + W - 1) / W;
-    const long long n_items = (long long)ny * nseg;
-    const size_t N = (size_t)nx * ny;
-    const S* __restrict__ src = static_cast<const S*>(a.src);
-    S* __restrict__ dst = static_cast<S*>(a.dst);
-    const bool has_ib = a.flags != nullptr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long n_items = it.count();
     const long long first = blockIdx.x, stride = gridDim.x;
     const int my_n = first < n_items ? (int)((n_items - 1 - first) / stride + 1) : 0;
     const uint32_t smem0 = smem_addr(smem);
@@ -362,153 +459,91 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
     }
     __syncthreads();
 
-    // thread 0: stage the rows of the k-th item of this CTA into stage k % kStages
-    auto issue = [&](int k, int flagged, int fo) {
+    // warp 0 (all lanes): stage the k-th item of this CTA into stage k % kStages
+    // (its arguments and position, then lane 0 the expected bytes, then lanes
+    // 0-8 the copies of one direction each)
+    auto issue = [&](int k) {
         const long long item = first + (long long)k * stride;
         const int stage = k % kStages;
-        const int y = (int)(item / nseg);
-        const int x0 = (int)(item % nseg) * W;
-        const int wlen = min(W, nx - x0);
+        it.stage_args(item, stage, lane);
+        __syncwarp();
+        const LbArgs& A = it.staged(stage);
+        const ItemRef p = it.staged_pos(item, stage);
         const uint32_t bar = smem_addr(&bars[stage]);
-        const uint32_t base = smem0 + stage * Gm::STAGE_BYTES;
-        s_meta[stage] = flagged | (fo << 1);
-        const unsigned row_bytes = (unsigned)((wlen + 2 * H) * sizeof(S));
-        mbar_expect_tx(bar, 9u * row_bytes);
-        const bool interior = x0 >= H && x0 + wlen + H <= nx;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            int sy = y - cy(i), plane = i;
-            if (WALLS) {
-                if (sy < 0 || sy >= ny) {
-                    plane = opp(i);
-                    sy = y;
-                }
-            } else {
-                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-            }
-            const S* row = src + (size_t)plane * N + (size_t)sy * nx;
-            const uint32_t d = base + i * Gm::ROW_BYTES;
-            if (interior) {
-                bulk_g2s(d, row + (x0 - H), row_bytes, bar);
-            } else {
-                bulk_g2s(d, row + (x0 == 0 ? nx - H : x0 - H), 16u, bar);
-                bulk_g2s(d + 16u, row + x0, (unsigned)(wlen * sizeof(S)), bar);
-                bulk_g2s(d + 16u + (unsigned)(wlen * sizeof(S)), row + (x0 + wlen == nx ? 0 : x0 + wlen), 16u, bar);
-            }
-        }
-    };
-    auto item_flags = [&](int k, int& flagged, int& fo) {
-        const long long item = first + (long long)k * stride;
-        flagged = has_ib && a.flags[item] != 0;
-        fo = (has_ib && a.clear_other && a.flags_other[item] != 0) ? 1 : 0;
+        if (lane == 0) mbar_expect_tx(bar, stage_bytes<S, NPT>(A, p));
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane < 9) stage_rows<S, NPT, WALLS>(A, p, smem0 + stage * Gm::STAGE_BYTES, bar, lane, 9);
     };
 
-    if (tid == 0) {
+    if (warp == 0) {
         for (int k = 0; k < kStages && k < my_n; ++k) {
-            int fl, fo;
-            item_flags(k, fl, fo);
-            issue(k, fl, fo);
+            FlagRegs r;
+            fetch_flags<W>(it, first + (long long)k * stride, lane, r);
+            keep_flags<W>(r, lane, s_fl[k], s_fo[k]);
+            issue(k);
         }
     }
+    __syncthreads();
 
-    const C om = C(a.omega);
-    const C pre = C(1) - C(0.5) * om;
-    const C om3 = C(3.0 * a.omega);
-    const float inv = a.inv_scale;
-    const float scl = 1.0f / inv;  // 2^k, exact
-    C* __restrict__ uxf = static_cast<C*>(a.ux);
-    C* __restrict__ uyf = static_cast<C*>(a.uy);
     bool bad = false;
     int k = 0;
     for (; k < my_n; ++k) {
         const int stage = k % kStages;
-        // thread 0 fetches the flags of the item it stages at the end of this one
-        int nfl = 0, nfo = 0;
-        if (tid == 0 && k + kStages < my_n) item_flags(k + kStages, nfl, nfo);
+        // warp 0 fetches the flags of the item it stages at the end of this one
+        FlagRegs nf{{0, 0}, {0, 0}};
+        if (warp == 0 && k + kStages < my_n) fetch_flags<W>(it, first + (long long)(k + kStages) * stride, lane, nf);
 
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((k / kStages) & 1));
         const long long item = first + (long long)k * stride;
-        const int y = (int)(item / nseg);
-        const int x0 = (int)(item % nseg) * W;
-        const int wlen = min(W, nx - x0);
-        const int meta = s_meta[stage];
-        const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
+        const LbArgs& A = it.staged(stage);
+        const ItemRef p = it.staged_pos(item, stage);
+        const int wlen = min(W, A.nx - p.x0);
         const int j0 = tid * NPT;
         if (j0 < wlen) {
-            // pull: f_i(x) = d*_i(x - e_i), or d*_opp(i)(x) where x - e_i is outside the walls
-            C f[9][NPT];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const bool bb = WALLS && (y - cy(i) < 0 || y - cy(i) >= ny);
-                const S* rp = sp + i * Gm::ROW + H + j0;
-                const Vec<S, NPT> v = *reinterpret_cast<const Vec<S, NPT>*>(rp);
-                if (bb || cx(i) == 0) {
-#pragma unroll
-                    for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
-                    if (bb && cx(i) != 0) {
-                        // the momentum of a moving wall (diagonals only)
-                        const C t = C(cx(i)) * wall_term<C>(a, cy(i) > 0);
-#pragma unroll
-                        for (int q = 0; q < NPT; ++q) f[i][q] += t;
-                    }
-                } else if (cx(i) == 1) {
-                    f[i][0] = Storage<S>::load(rp[-1], inv);
-#pragma unroll
-                    for (int q = 1; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q - 1], inv);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < NPT - 1; ++q) f[i][q] = Storage<S>::load(v.v[q + 1], inv);
-                    f[i][NPT - 1] = Storage<S>::load(rp[NPT], inv);
-                }
-            }
-            const size_t node0 = (size_t)y * nx + x0 + j0;
-            Vec<S, NPT> o[9];
-            Vec<C, NPT> pu, pv;
-#pragma unroll
-            for (int q = 0; q < NPT; ++q) {
-                C Gx = C(a.gx), Gy = C(a.gy);
-                if (meta & 1) {
-                    const longlong2 g = a.gsum[node0 + q];
-                    Gx += from_fix<C>(g.x);
-                    Gy += from_fix<C>(g.y);
-                }
-                C fq[9], out[9], rho;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
-                collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
-            }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];
-            if (meta & 1) {
-                // velocity for the interpolation to the markers (Sec. 2.3)
-                *reinterpret_cast<Vec<C, NPT>*>(uxf + node0) = pu;
-                *reinterpret_cast<Vec<C, NPT>*>(uyf + node0) = pv;
-            }
-            if (meta & 2) {
-#pragma unroll
-                for (int q = 0; q < NPT; ++q) a.gclear[node0 + q] = make_longlong2(0, 0);
-            }
+            const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
+            consume<S, NPT, WALLS>(A, p, sp, j0, s_fl[stage][j0 >> 5], s_fo[stage][j0 >> 5]);
         }
         // every thread is done with this stage (and every wait ended) before it is refilled
         bad = __syncthreads_or(!ok) != 0;
         if (bad) break;
-        if (tid == 0) {
-            if (meta & 2) a.flags_other[item] = 0;
-            if (k + kStages < my_n) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(k + kStages, nfl, nfo);
-            }
+        if (warp == 0 && k + kStages < my_n) {
+            keep_flags<W>(nf, lane, s_fl[stage], s_fo[stage]);
+            issue(k + kStages);
         }
     }
     if (bad && tid == 0) {
         // a copy never completed: report it, then wait (bounded) for the copies
         // this CTA still has in flight before its shared memory is released
-        atomicOr(a.status, ST_TIMEOUT);
+        ItemRef p0;
+        atomicOr(it.locate(first + (long long)k * stride, p0).status, ST_TIMEOUT);
         for (int m = k; m < my_n && m < k + kStages; ++m)
             mbar_wait(smem_addr(&bars[m % kStages]), (uint32_t)((m / kStages) & 1));
     }
+}
+
+// ---------------------------------------------------------------- kernels
+template <typename S, int NPT, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
+    stream_ws<S, NPT, WALLS>(OneLattice<S, NPT>(a));
+}
+template <typename S, int NPT, bool WALLS>
+__global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
+    stream_bar<S, NPT, WALLS>(OneLattice<S, NPT>(a));
+}
+// batched: the segments of up to kBatchMax lattices (b.off: first item of each
+// member, b.tiles_x: its segments per row)
+template <typename S, int NPT, bool WALLS>
+__global__ void __launch_bounds__(kBlock) k_lb_stream_ws_batch(const __grid_constant__ LbBatch b) {
+    __shared__ LbArgs s_args[kStages];
+    __shared__ ItemRef s_pos[kStages];
+    stream_ws<S, NPT, WALLS>(ManyLattices<S, NPT>{b, s_args, s_pos});
+}
+template <typename S, int NPT, bool WALLS>
+__global__ void __launch_bounds__(kThreads) k_lb_stream_bar_batch(const __grid_constant__ LbBatch b) {
+    __shared__ LbArgs s_args[kStages];
+    __shared__ ItemRef s_pos[kStages];
+    stream_bar<S, NPT, WALLS>(ManyLattices<S, NPT>{b, s_args, s_pos});
 }
 
 // the producer-warp schedule for 16-bit storage, the barrier schedule otherwise
@@ -516,19 +551,29 @@ __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
 // 158 us vs 138 us)
 template <typename S>
 constexpr bool kWarpSpecialised = sizeof(S) == 2;
+// batches: the staging of a segment also copies its member's arguments, which
+// keeps the producer warp off the consumers' path in every storage type
+template <typename S>
+constexpr bool kBatchWarpSpecialised = true;
 
-template <typename S, int NPT, bool WALLS>
+template <typename S, int NPT, bool WALLS, bool BATCH>
 constexpr auto stream_kernel() {
-    if constexpr (kWarpSpecialised<S>) return k_lb_stream_ws<S, NPT, WALLS>;
-    else return k_lb_stream_bar<S, NPT, WALLS>;
+    if constexpr (BATCH) {
+        if constexpr (kBatchWarpSpecialised<S>) return k_lb_stream_ws_batch<S, NPT, WALLS>;
+        else return k_lb_stream_bar_batch<S, NPT, WALLS>;
+    } else {
+        if constexpr (kWarpSpecialised<S>) return k_lb_stream_ws<S, NPT, WALLS>;
+        else return k_lb_stream_bar<S, NPT, WALLS>;
+    }
 }
 
-template <typename S, int NPT, bool WALLS>
+template <typename S, int NPT, bool WALLS, bool BATCH>
 cudaError_t prepare_t(int* grid) {
-    auto kern = stream_kernel<S, NPT, WALLS>();
+    auto kern = stream_kernel<S, NPT, WALLS, BATCH>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Geom<S, NPT>::SMEM);
     if (e != cudaSuccess) return e;
-    const int threads = kWarpSpecialised<S> ? kBlock : kThreads;
+    const bool ws = BATCH ? kBatchWarpSpecialised<S> : kWarpSpecialised<S>;
+    const int threads = ws ? kBlock : kThreads;
     int occ = 0, dev = 0, nsm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, Geom<S, NPT>::SMEM)) != cudaSuccess)
         return e;
@@ -539,41 +584,58 @@ cudaError_t prepare_t(int* grid) {
     return cudaSuccess;
 }
 
+// one entry for the four uses: prepare (grid_out) or launch, one lattice (a)
+// or a batch (b)
 template <typename S, int NPT>
-cudaError_t dispatch(bool prepare, bool walls, int grid, int* grid_out, const LbArgs* a, cudaStream_t s) {
-    if (prepare) return walls ? prepare_t<S, NPT, true>(grid_out) : prepare_t<S, NPT, false>(grid_out);
-    const int threads = kWarpSpecialised<S> ? kBlock : kThreads;
-    const int nseg = (a->nx + Geom<S, NPT>::W - 1) / Geom<S, NPT>::W;
-    const long long items = (long long)a->ny * nseg;
+cudaError_t dispatch(bool prepare, bool walls, int grid, int* grid_out, const LbArgs* a, const LbBatch* b,
+                     cudaStream_t s) {
+    const bool batch = b != nullptr;
+    if (prepare) {
+        if (batch) return walls ? prepare_t<S, NPT, true, true>(grid_out) : prepare_t<S, NPT, false, true>(grid_out);
+        return walls ? prepare_t<S, NPT, true, false>(grid_out) : prepare_t<S, NPT, false, false>(grid_out);
+    }
+    const int threads = (batch ? kBatchWarpSpecialised<S> : kWarpSpecialised<S>) ? kBlock : kThreads;
+    long long items;
+    if (batch) {
+        if (b->n < 1 || b->n > kBatchMax) return cudaErrorInvalidValue;
+        items = b->off[b->n];
+    } else {
+        items = (long long)a->ny * ((a->nx + Geom<S, NPT>::W - 1) / Geom<S, NPT>::W);
+    }
     const int g = (int)(items < grid ? items : grid);
-    if (walls)
-        stream_kernel<S, NPT, true>()<<<g, threads, Geom<S, NPT>::SMEM, s>>>(*a);
-    else
-        stream_kernel<S, NPT, false>()<<<g, threads, Geom<S, NPT>::SMEM, s>>>(*a);
+    if (g <= 0) return cudaSuccess;
+    constexpr int SM = Geom<S, NPT>::SMEM;
+    if (batch) {
+        if (walls) stream_kernel<S, NPT, true, true>()<<<g, threads, SM, s>>>(*b);
+        else stream_kernel<S, NPT, false, true>()<<<g, threads, SM, s>>>(*b);
+    } else {
+        if (walls) stream_kernel<S, NPT, true, false>()<<<g, threads, SM, s>>>(*a);
+        else stream_kernel<S, NPT, false, false>()<<<g, threads, SM, s>>>(*a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t dispatch_all(lbib_precision prec, int npt, bool prepare, bool walls, int grid, int* grid_out,
-                         const LbArgs* a, cudaStream_t s) {
+                         const LbArgs* a, const LbBatch* b, cudaStream_t s) {
     switch (prec) {
         case LBIB_F64:
-            if (npt == 1) return dispatch<double, 1>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 2) return dispatch<double, 2>(prepare, walls, grid, grid_out, a, s);
+            if (npt == 1) return dispatch<double, 1>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 2) return dispatch<double, 2>(prepare, walls, grid, grid_out, a, b, s);
             break;
         case LBIB_F32:
-            if (npt == 1) return dispatch<float, 1>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 2) return dispatch<float, 2>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 4) return dispatch<float, 4>(prepare, walls, grid, grid_out, a, s);
+            if (npt == 1) return dispatch<float, 1>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 2) return dispatch<float, 2>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 4) return dispatch<float, 4>(prepare, walls, grid, grid_out, a, b, s);
             break;
         case LBIB_F32_STORE_F16:
-            if (npt == 2) return dispatch<__half, 2>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 4) return dispatch<__half, 4>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 8) return dispatch<__half, 8>(prepare, walls, grid, grid_out, a, s);
+            if (npt == 2) return dispatch<__half, 2>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 4) return dispatch<__half, 4>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 8) return dispatch<__half, 8>(prepare, walls, grid, grid_out, a, b, s);
             break;
         case LBIB_F32_STORE_BF16:
-            if (npt == 2) return dispatch<__nv_bfloat16, 2>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 4) return dispatch<__nv_bfloat16, 4>(prepare, walls, grid, grid_out, a, s);
-            if (npt == 8) return dispatch<__nv_bfloat16, 8>(prepare, walls, grid, grid_out, a, s);
+            if (npt == 2) return dispatch<__nv_bfloat16, 2>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 4) return dispatch<__nv_bfloat16, 4>(prepare, walls, grid, grid_out, a, b, s);
+            if (npt == 8) return dispatch<__nv_bfloat16, 8>(prepare, walls, grid, grid_out, a, b, s);
             break;
     }
     return cudaErrorInvalidValue;
@@ -586,12 +648,23 @@ int lb_stream_halo(lbib_precision prec) {
 }
 
 cudaError_t prepare_lb_stream(lbib_precision prec, int npt, bool walls, bool, int* grid) {
-    return dispatch_all(prec, npt, true, walls, 0, grid, nullptr, nullptr);
+    return dispatch_all(prec, npt, true, walls, 0, grid, nullptr, nullptr, nullptr);
 }
 
 cudaError_t launch_lb_stream(lbib_precision prec, int npt, bool walls, bool, int grid, const LbArgs& a,
                              cudaStream_t s) {
-    return dispatch_all(prec, npt, false, walls, grid, nullptr, &a, s);
+    return dispatch_all(prec, npt, false, walls, grid, nullptr, &a, nullptr, s);
+}
+
+cudaError_t prepare_lb_stream_batch(lbib_precision prec, int npt, bool walls, int* grid) {
+    LbBatch dummy;
+    dummy.n = 0;
+    return dispatch_all(prec, npt, true, walls, 0, grid, nullptr, &dummy, nullptr);
+}
+
+cudaError_t launch_lb_stream_batch(lbib_precision prec, int npt, bool walls, int grid, const LbBatch& b,
+                                   cudaStream_t s) {
+    return dispatch_all(prec, npt, false, walls, grid, nullptr, nullptr, &b, s);
 }
 
 }  // namespace lbib

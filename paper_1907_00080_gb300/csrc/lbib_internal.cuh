@@ -90,7 +90,7 @@ struct LbArgs {
     double* uy_out;
     const longlong2* gsum; // [N] fixed-point IB force of this step (flagged tiles)
     longlong2* gclear;     // [N] the other parity's field, zeroed in its flagged tiles
-    const int* flags;      // [ntiles] tiles this step's spreading touched
+    const int* flags;      // [ntiles] force tiles (32 nodes of a row) this step's spreading touched
     int* flags_other;      // [ntiles] tiles the previous step's spreading touched
     int clear_other;       // 1 during a step, 0 for read-backs and profiling
     int nx, ny;
@@ -102,7 +102,7 @@ struct LbArgs {
     float bbf_bot, bbf_top;  // the same rounded to FP32 (no FP64 conversion in the FP32 kernels)
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
     int g_prefetch;        // row tiles: read the spread force of every node up front (L2-resident lattices)
-    int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags
+    int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags (32 x 1 nodes; tiles_x = ceil(nx / 32))
     int* status;           // device status word (StatusBits)
 };
 
@@ -218,10 +218,56 @@ constexpr int kChunkV = 64;   // vertices per marker-kernel block (a multiple of
 constexpr int kUnitInts = 8;  // ints per work-unit record (two int4)
 constexpr int kSegV = 8;      // vertices per repulsion-screening segment (divides kChunkV)
 
+// Copy kernel arguments (a struct of the library's argument types) into
+// shared memory, all threads of the block taking 8-byte words; ends with a
+// block barrier.  Batched kernels stage the arguments of the member a block
+// works for this way, from global memory or (generic pointer) from the
+// launch's own parameters.
+template <typename T>
+__device__ __forceinline__ void stage_args(T* dst, const T* src) {
+    static_assert(sizeof(T) % 8 == 0 && alignof(T) >= 8, "argument structs are 8-byte words");
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int k = tid; k < (int)(sizeof(T) / 8); k += nt)
+        reinterpret_cast<long long*>(dst)[k] = reinterpret_cast<const long long*>(src)[k];
+    __syncthreads();
+}
+
+// Batched launches (ensembles): up to kBatchMax members per launch.  The block
+// of a launch that a member's work starts at is off[member]; a block finds its
+// member by a binary search over these offsets, which travel in the launch's
+// parameters (no memory round trip before the first data load).
+constexpr int kBatchMax = 64;
+__device__ __forceinline__ int batch_member(const int* off, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+// fused kernel: the members' arguments themselves are parameters (192 B each)
+struct LbBatch {
+    int n;
+    int off[kBatchMax + 1];     // row tiles: first block of each member; persistent form: first segment
+    int tiles_x[kBatchMax];     // row tiles: tiles per row; persistent form: segments per row
+    LbArgs a[kBatchMax];
+};
+// marker kernels: the members' arguments (744 B each) stay in global memory
+struct MarkerBatch {
+    int n;
+    int off[kBatchMax + 1];     // first block of each member's units
+    const MarkerArgs* args;     // [n]
+};
+
 // ---------------------------------------------------------------- launchers
 // lb_kernels.cu
 cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, bool has_ib,
                            const LbArgs& a, cudaStream_t s);
+// batched row tiles of up to kBatchMax lattices with markers, all with the
+// tile shape (vec, ty); b.off[b.n] blocks
+cudaError_t launch_lb_batch(lbib_precision prec, int vec, int ty, bool walls, const LbBatch& b, cudaStream_t s);
 // lb_stream_kernel.cu: the persistent bulk-copy form of the fused kernel (one
 // CTA per SM slot streams row segments of 256 * npt nodes through a 4-stage
 // shared-memory pipeline); prepare_ sets its shared-memory limit and returns
@@ -230,6 +276,11 @@ int lb_stream_halo(lbib_precision prec);  // elements per 16-byte halo chunk
 cudaError_t prepare_lb_stream(lbib_precision prec, int npt, bool walls, bool has_ib, int* grid);
 cudaError_t launch_lb_stream(lbib_precision prec, int npt, bool walls, bool has_ib, int grid,
                              const LbArgs& a, cudaStream_t s);
+// the persistent form over the segments of up to kBatchMax lattices (b.off:
+// first segment of each member, b.tiles_x: its segments per row)
+cudaError_t prepare_lb_stream_batch(lbib_precision prec, int npt, bool walls, int* grid);
+cudaError_t launch_lb_stream_batch(lbib_precision prec, int npt, bool walls, int grid, const LbBatch& b,
+                                   cudaStream_t s);
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
                               bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s);
 cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
@@ -247,6 +298,10 @@ cudaError_t launch_rest(lbib_precision prec, const MarkerArgs& a, void* rest, do
                         cudaStream_t s);
 cudaError_t launch_forces(lbib_precision prec, const MarkerArgs& a, int max_n, cudaStream_t s);
 cudaError_t launch_advance(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
+// batched marker kernels of up to kBatchMax contexts (b.off[b.n] blocks); the
+// advance blocks have `threads` threads (the widest member's)
+cudaError_t launch_forces_batch(lbib_precision prec, const MarkerBatch& b, cudaStream_t s);
+cudaError_t launch_advance_batch(lbib_precision prec, bool dyn, const MarkerBatch& b, int threads, cudaStream_t s);
 cudaError_t launch_seg_boxes(lbib_precision prec, const MarkerArgs& a, cudaStream_t s);
 cudaError_t launch_areas(lbib_precision prec, const MarkerArgs& a, double* areas, cudaStream_t s);
 // dynamic_kernels.cu: hydrodynamic stresses and forcing terms of the dynamic

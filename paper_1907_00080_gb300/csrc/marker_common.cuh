@@ -203,14 +203,15 @@ __device__ void block_sum4_c(C& v0, C& v1, C& v2, C& v3, C* red) {
     v3 = red[99 + 32];
 }
 
-// Last-block epilogue: every block counts itself in once it is done; the block
-// that arrives last (it sees all other blocks' writes after the fences) runs the
-// epilogue and resets the counter.  No block ever waits for another.
-__device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* flag) {
+// Last-block epilogue: every block of a context's launch counts itself in once
+// it is done; the block that arrives last (it sees all other blocks' writes
+// after the fences) runs the epilogue and resets the counter.  No block ever
+// waits for another.  nblocks: the context's blocks in the launch.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, bool* flag, unsigned nblocks) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        *flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+        *flag = atomicAdd(counter, 1u) == nblocks - 1;
     }
     __syncthreads();
     const bool last = *flag;

@@ -82,6 +82,10 @@ _SIGS = {
     "lbib_ensemble_step": (_I, [_P, _I64]),
     "lbib_ensemble_sync": (_I, [_P]),
     "lbib_ensemble_size": (_I32, [_P]),
+    "lbib_ensemble_form": (_I32, [_P]),
+    "lbib_ensemble_set_groups": (ctypes.c_int, [_P, _I32]),
+    "lbib_ensemble_groups": (_I32, [_P]),
+    "lbib_ensemble_launches_per_step": (_I32, [_P]),
     "lbib_ensemble_member": (_P, [_P, _I32]),
     "lbib_ensemble_last_error": (ctypes.c_char_p, [_P]),
     "lbib_ensemble_destroy": (None, [_P]),
@@ -357,6 +361,22 @@ def lbib_ensemble_size(ens):
     return load().lbib_ensemble_size(ens)
 
 
+def lbib_ensemble_form(ens):
+    return load().lbib_ensemble_form(ens)
+
+
+def lbib_ensemble_set_groups(ens, groups):
+    _echeck(ens, load().lbib_ensemble_set_groups(ens, int(groups)))
+
+
+def lbib_ensemble_groups(ens):
+    return load().lbib_ensemble_groups(ens)
+
+
+def lbib_ensemble_launches_per_step(ens):
+    return load().lbib_ensemble_launches_per_step(ens)
+
+
 def lbib_ensemble_member(ens, i):
     p = load().lbib_ensemble_member(ens, int(i))
     if not p:
@@ -604,11 +624,29 @@ class Ensemble:
     """Several workloads advanced together (lbib_ensemble_*); members keep the
     Simulation read-back methods.  Marshalling only."""
 
-    def __init__(self, workloads, precision=None, cuda_stream=None):
-        self.members = [Simulation(wl, precision=precision) for wl in workloads]
+    def __init__(self, workloads, precision=None, cuda_stream=None, tiling=None):
+        """tiling: (vec, ty) of the fused kernel for every member (row tiles,
+        ty > 0, give the batched form); None keeps each member's default."""
+        self.members = [Simulation(wl, precision=precision, tiling=tiling) for wl in workloads]
         self.ens = lbib_ensemble_create([m.ctx for m in self.members], cuda_stream)
         for m in self.members:
             m.owned_by_ensemble = True
+
+    @property
+    def form(self):
+        """1: batched kernels over all members; 0: graph of member graphs"""
+        return lbib_ensemble_form(self.ens)
+
+    @property
+    def launches_per_step(self):
+        return lbib_ensemble_launches_per_step(self.ens)
+
+    @property
+    def groups(self):
+        return lbib_ensemble_groups(self.ens)
+
+    def set_groups(self, groups):
+        lbib_ensemble_set_groups(self.ens, groups)
 
     def step(self, n=1):
         lbib_ensemble_step(self.ens, n)

@@ -76,3 +76,94 @@ def test_ensemble_rejects_bad_members():
     with pytest.raises(lbib.LbibError):
         lbib.lbib_ensemble_create([])
     a.close()
+
+
+@pytest.mark.parametrize("precision,tiling,groups", [("f32", (1, 4), 1), ("f64", (1, 2), 2), ("f16", (2, 2), 1),
+                                                    ("f32", (4, 1), 3), ("f32", (2, 2), 5),
+                                                    ("f32", (2, 0), 1), ("f32", (1, 0), 2), ("f64", (1, 0), 1),
+                                                    ("f16", (4, 0), 2), ("bf16", (2, 0), 1)])
+def test_batched_ensemble_matches_single_runs_bitwise(precision, tiling, groups):
+    """Members sharing the precision and the fused kernel's form and shape
+    (row tiles (vec, ty), or the persistent form (npt, 0)) run in the batched
+    form (three launches per time step for each group of members); each member
+    still computes bit for bit what it computes alone with that tiling, over
+    chunks of 16 steps and single steps, with stress kinetics (bonds form and
+    break), whatever the grouping."""
+    from paper_1907_00080_gb300 import lbib
+    wls = small_ensemble(5, precision, seed=11)
+    assert len({wl.nx for wl in wls}) > 1
+    ens = lbib.Ensemble(wls, tiling=tiling)
+    assert ens.form == 1
+    assert ens.groups == 1 and ens.launches_per_step == 3
+    ens.set_groups(groups)
+    assert ens.groups == groups and ens.launches_per_step == 3 * groups
+    ens.step(35)
+    ens.step(16)
+    ens.sync()
+    for wl, m in zip(wls, ens.members):
+        s = lbib.Simulation(wl, tiling=tiling)
+        s.step(51)
+        assert np.array_equal(m.populations(), s.populations()), wl.name
+        assert np.array_equal(m.markers(), s.markers()), wl.name
+        assert np.array_equal(m.bonds(), s.bonds()), wl.name
+        _, ux, _ = m.fields()
+        _, ux1, _ = s.fields()
+        assert np.array_equal(ux, ux1)
+        assert lbib.lbib_step_count(m.ctx) == 51
+        s.close()
+    ens.close()
+
+
+def test_batched_ensemble_member_matches_oracle_and_other_forms_fall_back():
+    """A batched member against the oracle (FP64, 40 steps); members with
+    different tile shapes run as a graph of member graphs, with the same
+    results."""
+    from paper_1907_00080_gb300 import lbib
+    wls = small_ensemble(3, "f64", seed=7)
+    ens = lbib.Ensemble(wls, tiling=(1, 4))
+    assert ens.form == 1
+    ens.step(40)
+    ens.sync()
+    wl, m = wls[1], ens.members[1]
+    r = make_oracle(wl)
+    r.step(40)
+    _, ux, uy = m.fields()
+    _, ux0, uy0 = r.fields()
+    assert vel_err(ux, uy, ux0, uy0) < f64_field_tol(np.max(np.abs(ux0)))
+    assert rel_err(m.markers(), r.markers()) < 1e-12
+    assert np.array_equal(m.bonds(), r.bonds())
+    # mixed tilings: graph of member graphs, same bits as the batched run
+    members = [lbib.Simulation(w, tiling=t) for w, t in zip(wls, [(1, 4), (1, 2), (1, 4)])]
+    e2 = lbib.lbib_ensemble_create([s.ctx for s in members])
+    for s in members:
+        s.owned_by_ensemble = True
+    assert lbib.lbib_ensemble_form(e2) == 0
+    lbib.lbib_ensemble_step(e2, 40)
+    lbib.lbib_ensemble_sync(e2)
+    for k in (0, 2):
+        assert np.array_equal(members[k].markers(), ens.members[k].markers())
+        assert np.array_equal(members[k].populations(), ens.members[k].populations())
+    lbib.lbib_ensemble_destroy(e2)
+    for s in members:
+        s.ctx = None
+    ens.close()
+
+
+def test_ensemble_groups_are_refused_outside_their_range():
+    from paper_1907_00080_gb300 import lbib
+    wls = small_ensemble(3, "f32", seed=2)
+    ens = lbib.Ensemble(wls, tiling=(1, 4))
+    for bad in (0, 4):
+        with pytest.raises(lbib.LbibError):
+            ens.set_groups(bad)
+    ens.close()
+    members = [lbib.Simulation(w, tiling=t) for w, t in zip(wls, [(1, 4), (1, 2), (1, 4)])]
+    e2 = lbib.lbib_ensemble_create([s.ctx for s in members])
+    for s in members:
+        s.owned_by_ensemble = True
+    with pytest.raises(lbib.LbibError):
+        lbib.lbib_ensemble_set_groups(e2, 1)
+    assert lbib.lbib_ensemble_groups(e2) == 0
+    lbib.lbib_ensemble_destroy(e2)
+    for s in members:
+        s.ctx = None

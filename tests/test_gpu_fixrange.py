@@ -79,11 +79,12 @@ def test_close_membranes_inside_the_range_match_the_oracle(prec):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_spread_force_beyond_the_range_is_reported(prec):
-    # a ring stretched by 10 % with k_s = 1e4: about 600 lu per vertex, so
-    # w F reaches a few hundred lu at the nearest nodes
+    # a ring of 32 vertices stretched by 10 % with k_s = 1e6: each element
+    # pulls with k_s dl = 7.8e4 lu, about 1.5e4 lu of net force per vertex,
+    # so w F reaches thousands of lu at the nearest nodes
     xy = inputs.circle(32.0, 16.0, 4.0, 32)
     wl = inputs.Workload(name="stiff", nx=64, ny=32, init="rest", precision=prec,
-                         membranes=[inputs.Membrane(xy=xy, ks=1e4, kb=0.0, ka=0.0)])
+                         membranes=[inputs.Membrane(xy=xy, ks=1e6, kb=0.0, ka=0.0)])
     from paper_1907_00080_gb300 import lbib
     s = lbib.Simulation(wl)
     lbib.lbib_write_markers(s.ctx, 1.1 * (xy - [32.0, 16.0]) + [32.0, 16.0])
