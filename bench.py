@@ -1,19 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark of the LB-IB hot path on GB300.
 
-Workload: the coarse capillary -- 10 x 40 um at dx = 62.5 nm (640 x 160
-lattice), 8 biconcave red cells (200 markers each), 4 adhesive 1 um carriers
-(50 markers, alternating rigid and soft), receptors on both walls, FP32 --
-synthetic, seeded inputs.  One benchmark "step" is one call that advances the
-simulation by T time steps (each time step: forces, IB weights and tile lists,
-fused collide-stream with the IB spreading, interpolation + advance, bonds).
-Metric: MLUPS including IB and adhesion (lattice nodes x time steps / s).
+Workload (the largest single-GPU configuration): an ensemble of 64 coarse
+capillaries -- 10 um wide, 32-64 um long at dx = 62.5 nm (NX 512-1008 x NY
+160, 8.03 M nodes in all), red cells at 20 % of the 10 x 40 um capillary's
+count per length (200 markers each), 4 adhesive 1 um carriers each (50
+markers; rigid or soft, sigma swept), receptors on both walls, FP32 --
+synthetic, seeded inputs -- advanced in the batched form (three launches per
+time step for all members, shape from the autotuner).  One benchmark "step"
+advances every member by T time steps (each: forces, IB weights and
+spreading, fused collide-stream, interpolation + advance, bonds).  Metric:
+MLUPS including IB and adhesion (lattice nodes x time steps / s).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbib|reference]
+  python bench.py --profile-case probe|capillary|ensemble|fine|adjoint|dynamic ...
 
-N > 1 runs under torchrun, one independent replica per GPU (weak scaling,
+N > 1 runs under torchrun, one independent ensemble per GPU (weak scaling,
 different seeds, no collective on the data path).  ``--impl reference`` times
-the FP64 CPU oracle on the same workload (a bounded sample per step).
+the FP64 CPU oracle on all host cores on one member of the same ensemble (a
+bounded sample per step).  ``--profile-case`` runs one small fixed case for a
+profiler (ncu) and prints one JSON line.
 """
 from __future__ import annotations
 
@@ -33,8 +39,11 @@ import numpy as np  # noqa: E402
 
 METRIC = "MLUPS incl. IB+adhesion"
 UNIT = "MLUPS"
-WORKLOAD = "coarse capillary 640x160 FP32: 8 RBC x 200 markers, 4 carriers x 50 markers, receptors on both walls"
+WORKLOAD = ("ensemble of 64 coarse capillaries (10 um x 32-64 um at dx = 62.5 nm: NX 512-1008 x NY 160, "
+            "8.03 M nodes, 138,600 markers, 4 carriers each, receptors on both walls), batched form")
+C2_WORKLOAD = "coarse capillary 640x160: 8 RBC x 200 markers, 4 carriers x 50 markers, receptors on both walls"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+ENSEMBLE_N = 64
 
 
 def parse():
@@ -43,12 +52,23 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
-    p.add_argument("--timesteps-per-step", type=int, default=1000)
+    p.add_argument("--timesteps-per-step", type=int, default=200)
     p.add_argument("--precision", default="f32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-probe", action="store_true")
     p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--no-c2", action="store_true", help="skip the 640 x 160 capillary line")
+    # one small fixed case for a profiler
+    p.add_argument("--profile-case", default=None,
+                   choices=["probe", "capillary", "ensemble", "fine", "adjoint", "dynamic"])
+    p.add_argument("--nx", type=int, default=8192)
+    p.add_argument("--ny", type=int, default=1024)
+    p.add_argument("--tiling", default=None, help="vec,ty of the fused kernel")
+    p.add_argument("--groups", type=int, default=1)
+    p.add_argument("--launches", type=int, default=3)
+    p.add_argument("--case-steps", type=int, default=40)
+    p.add_argument("--checkpoint-every", type=int, default=20)
     return p.parse_args()
 
 
@@ -69,8 +89,53 @@ def peaks():
 
 
 def workload(precision, seed=0):
+    """the 640 x 160 coarse capillary"""
     from paper_1907_00080_gb300 import inputs
     return inputs.capillary(precision=precision, seed=seed, steps=200000, name="capillary_640x160")
+
+
+def ensemble_workloads(precision, seed=0):
+    """the 64-member ensemble (member i seeded seed + i)"""
+    from paper_1907_00080_gb300 import inputs
+    return inputs.capillary_ensemble(ENSEMBLE_N, seed=seed, precision=precision)
+
+
+def cpu_model():
+    """the host CPU's model name (lscpu, else /proc/cpuinfo)"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch (read + write) of the current kernels, from the
+    ncu summaries under profiles/: lines `traffic_per_launch: <key> <bytes>`"""
+    out = {}
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return out
+    for name in sorted(os.listdir(d)):
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(d, name)) as fh:
+            for ln in fh:
+                if ln.startswith("traffic_per_launch:"):
+                    parts = ln.split()
+                    if len(parts) >= 3:
+                        out[parts[1]] = int(float(parts[2]))
+    return out
 
 
 # ------------------------------------------------------------------ clocks
@@ -134,15 +199,39 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ reference arm
-def cpu_oracle_mlups(wl, timesteps):
-    """Time the FP64 CPU oracle (as it stands, one thread) for `timesteps` steps."""
+def cpu_oracle_mlups(wl, timesteps, threads=1):
+    """Time the FP64 CPU oracle (as it stands) for `timesteps` steps, on one
+    thread or, threads > 1, its OpenMP build with that many threads."""
     import oracle
-    oracle.build()
-    s = _oracle_sim(wl)
-    t0 = time.perf_counter()
-    s.step(timesteps)
-    dt = time.perf_counter() - t0
-    return wl.nx * wl.ny * timesteps / dt / 1e6, dt, s
+    used = oracle.use_threads(threads)
+    try:
+        s = _oracle_sim(wl)
+        s.step(1)
+        t0 = time.perf_counter()
+        s.step(timesteps)
+        dt = time.perf_counter() - t0
+        del s
+    finally:
+        oracle.use_threads(1)
+    return wl.nx * wl.ny * timesteps / dt / 1e6, dt, used
+
+
+def cpu_baseline(precision_note="FP64 C oracle"):
+    """The oracle on member 0 of the ensemble: one thread (300 steps) and its
+    OpenMP build on every host core (1500 steps); `value` is the all-core
+    figure."""
+    wl = ensemble_workloads("f64")[0]
+    n1, n_all = 300, 1500
+    m1, d1, _ = cpu_oracle_mlups(wl, n1, 1)
+    cores = os.cpu_count() or 1
+    ma, da, used = cpu_oracle_mlups(wl, n_all, cores)
+    return {"value": ma, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": "%d time steps of ensemble member 0 (%dx%d, %d membranes, bonds), %s, OpenMP over nodes, "
+                      "rows and vertices on %d threads, %.1f s" % (n_all, wl.nx, wl.ny, len(wl.membranes),
+                                                                    precision_note, used, da),
+            "cpu_model": cpu_model(), "flags": "gcc -O2 -ffp-contract=off -fopenmp",
+            "single_thread": {"value": m1, "unit": UNIT, "cores": 1,
+                              "sample": "%d time steps of the same member, one thread, %.1f s" % (n1, d1)}}
 
 
 def max_over_ranks(x, dist, device):
@@ -156,6 +245,8 @@ def max_over_ranks(x, dist, device):
 
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case_main(args)
     if args.impl == "reference":
         return reference_main(args)
     return lbib_main(args)
@@ -171,25 +262,30 @@ def reference_main(args):
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-    wl = workload("f64")
-    sample = 20
     import oracle
-    oracle.build()
+    wl = ensemble_workloads("f64")[0]
+    sample = 20
+    cores = os.cpu_count() or 1
+    used = oracle.use_threads(cores)
     s = _oracle_sim(wl)
     s.step(sample * args.warmup)
     t0 = time.perf_counter()
     s.step(sample * args.steps)
     dt = time.perf_counter() - t0
+    del s
+    oracle.use_threads(1)
     mlups = wl.nx * wl.ny * sample * args.steps / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("FP32", "FP64 oracle"), "nx": wl.nx, "ny": wl.ny,
-                   "timesteps_per_step": sample},
-        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d time steps per benchmark step of the 640x160 capillary, FP64 C oracle, one thread" % sample},
+        "config": {"workload": WORKLOAD + "; FP64 CPU oracle on member 0 (%dx%d)" % (wl.nx, wl.ny),
+                   "nx": wl.nx, "ny": wl.ny, "timesteps_per_step": sample},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": "%d time steps per benchmark step of ensemble member 0, FP64 C oracle, OpenMP "
+                                   "on %d threads" % (sample, used),
+                         "cpu_model": cpu_model()},
         "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -228,19 +324,21 @@ def lbib_main(args):
     lbib.load()
 
     T = args.timesteps_per_step
-    wl = workload(args.precision, seed=rank)
+    wls = ensemble_workloads(args.precision, seed=ENSEMBLE_N * rank)
+    nodes = sum(wl.nx * wl.ny for wl in wls)
+    markers = sum(wl.n_vertices for wl in wls)
     stream = torch.cuda.Stream()
-    tiling = tuning.bench_tiling(wl)
-    sim = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
-    vec, ty = sim.tiling
-    kps = sim.kernels_per_step
-    # L2 flush buffer (> 129 MB L2), written between timed iterations
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    (tiling, groups), tuned = tuning.ensemble_shape(wls, cuda_stream=stream)
+    ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream, tiling=tiling)
+    if ens.form != 1:
+        raise RuntimeError("the benchmark ensemble did not take the batched form")
+    ens.set_groups(groups)
+    lps = ens.launches_per_step
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            sim.step(T)
-        sim.sync()
+            ens.step(T)
+        ens.sync()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         if dist is not None:
@@ -250,54 +348,45 @@ def lbib_main(args):
         clk.start()
         wall0 = time.perf_counter()
         for k in range(args.steps):
-            flush.fill_(float(k))
             starts[k].record(stream)
-            sim.step(T)
+            ens.step(T)
             ends[k].record(stream)
-        sim.sync()
+        ens.sync()
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         clocks = clk.stop()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     elapsed = ms / 1e3
     if dist is not None:
         elapsed = max_over_ranks(elapsed, dist, "cuda")
-    units = wl.nx * wl.ny * T * args.steps * ws
-    value = units / elapsed / 1e6
+    value = nodes * T * args.steps * ws / elapsed / 1e6
+    ens.close()
 
-    # ---- per-kernel rooflines on this workload (scratch context); the
-    # top-level one is the kernel with the largest share of the time step
+    # ---- the batched kernels timed alone on a scratch copy of the ensemble;
+    # the top-level roofline is the kernel with the largest share
     pk, pk_kind = peaks()
-    alg = alg_bytes_per_launch(args.precision, wl)
-    scratch = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
-    with torch.cuda.stream(stream):
-        scratch.step(4)
-        scratch.sync()
-        lbib.lbib_profile_kernels(scratch.ctx, 50)
-        kms = lbib.lbib_profile_kernels(scratch.ctx, 500)
-    scratch.close()
-    kernels = []
-    for name, ms_k, b in zip(KERNEL_NAMES, kms, alg):
-        gbs = b / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
-        kernels.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": b,
-                        "traffic": NCU_TRAFFIC.get((name, args.precision, "capillary_640x160"))})
+    traffic = ncu_traffic()
+    kernels = ensemble_kernels(lbib, torch, stream, wls, tiling, groups, args.precision, pk, traffic)
     top = max(kernels, key=lambda k: k["ms_per_launch"])
     roofline = dict(top)
     roofline["peak_kind"] = pk_kind + " (copy bandwidth, burst)"
     roofline["share_of_kernel_time"] = top["ms_per_launch"] / sum(k["ms_per_launch"] for k in kernels)
-    roofline["note"] = ("dominant kernel of the time step, timed alone on a copy of the workload; the marker "
-                        "kernels run a few dozen blocks on 152 SMs and are bound by dependent L2 round trips, "
-                        "not by bytes; the fused kernel's lattice (7.4 MB) stays in L2 here: see "
-                        "roofline_hbm_probe for the DRAM-bound case")
+    roofline["note"] = ("dominant kernel of the ensemble's time step (all 64 members in one launch), timed alone "
+                        "with CUDA events on a scratch copy; algorithmic bytes = 9 populations read + 9 written "
+                        "per node; traffic from the ncu summary of the same kernel under profiles/")
 
     probe = None
     if not args.no_probe and rank == 0:
-        probe = hbm_probe(lbib, torch, stream, args.precision, pk, pk_kind)
+        probe = hbm_probe(lbib, torch, stream, args.precision, pk, pk_kind, traffic)
+
+    c2 = None
+    if not args.no_c2 and rank == 0:
+        c2 = capillary_line(lbib, torch, stream, args.precision, pk, traffic)
 
     forms = None
     if not args.no_forms and rank == 0:
-        forms = {"precision": precision_forms(lbib, torch, stream), "ensemble": ensemble_form(lbib, torch, stream),
+        forms = {"ensemble": ensemble_form(lbib, torch, stream, wls, tiling, groups),
+                 "precision": precision_forms(lbib, torch, stream),
                  "differentiation": differentiation_form(lbib, torch),
                  "couette_cell_free_layer": couette_form(lbib, torch, stream),
                  "dynamic_carriers": dynamic_form(lbib, torch, stream)}
@@ -305,15 +394,11 @@ def lbib_main(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(lbib, torch, wl, tiling, stream, T, max(2, min(args.steps, 5)))
+        e2e = ensemble_e2e(lbib, torch, wls, tiling, groups, stream, T, max(2, min(args.steps, 4)))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        wl64 = workload("f64")
-        sample = 600
-        mlups_cpu, dt_cpu, _ = cpu_oracle_mlups(wl64, sample)
-        cpu = {"value": mlups_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d time steps of the 640x160 capillary (all 12 membranes, bonds), FP64 C oracle, one thread, %.1f s" % (sample, dt_cpu)}
+        cpu = cpu_baseline()
 
     if rank == 0:
         line = {
@@ -321,24 +406,27 @@ def lbib_main(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": wl.nx, "ny": wl.ny, "markers": wl.n_vertices,
-                       "ligands": wl.n_ligands, "receptors": int(len(wl.receptors)),
-                       "timesteps_per_step": T, "tiling": [vec, ty],
-                       "l2": "flushed (256 MB write) between timed iterations; within one the lattice is L2-resident",
-                       "parallelism": "replicas x%d" % ws},
+            "config": {"workload": WORKLOAD, "members": len(wls), "nodes": nodes, "markers": markers,
+                       "nx_range": [min(wl.nx for wl in wls), max(wl.nx for wl in wls)], "ny": wls[0].ny,
+                       "timesteps_per_step": T, "tiling": list(tiling), "groups": groups,
+                       "shape_from": "autotuner table" if tuned is None else "autotuned on this run",
+                       "l2": "inputs larger than L2: 2 x 578 MB of populations (129 MB L2); no flush",
+                       "parallelism": "one ensemble per GPU x%d" % ws},
             "roofline": roofline,
             "roofline_kernels": kernels,
             "roofline_hbm_probe": probe,
+            "capillary_640x160": c2,
             "forms": forms,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": kps * T * args.steps,
-            "kernels_per_timestep": kps,
+            "gpu_launches": lps * T * args.steps,
+            "kernels_per_timestep": lps,
             "clocks": clocks,
             "wall_s_timed_region": wall,
         }
+        if tuned is not None:
+            line["config"]["autotune_ms_per_step"] = {"%s/%d" % (t, g): v for (t, g), v in tuned.items()}
         print(json.dumps(line))
-    sim.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -346,18 +434,127 @@ def lbib_main(args):
 
 KERNEL_NAMES = ("k_forces (forces, IB weights, spreading)", "k_lb_step / k_lb_stream (fused collide-stream)",
                 "k_advance (interpolation, advance, bonds)")
+ENSEMBLE_KERNEL_NAMES = ("k_forces_batch (forces, IB weights, spreading; all members)",
+                         "k_lb_stream_ws_batch / k_lb_step_batch (fused collide-stream; all members)",
+                         "k_advance_batch (interpolation, advance, bonds; all members)")
 
-# DRAM bytes per launch (read + write) from ncu captures of the current
-# kernels (profiles/marker_kernels_capillary_640x160_f32.md and
-# profiles/k_lb_stream_probe_8192x1024.md), keyed by kernel, precision and
-# workload; absent where no capture of the current kernel exists.
-NCU_TRAFFIC = {
-    (KERNEL_NAMES[0], "f32", "capillary_640x160"): 412160,
-    (KERNEL_NAMES[1], "f32", "capillary_640x160"): 5344512,
-    (KERNEL_NAMES[2], "f32", "capillary_640x160"): 628992,
-    # 8192 x 1024 capture scaled by the nodes to the 8192 x 2048 probe
-    ("k_lb_stream", "f32", "probe_8192x2048"): 2 * (322732800 + 257833728),
-}
+
+def ensemble_kernels(lbib, torch, stream, wls, tiling, groups, precision, pk, traffic):
+    """The three batched kernels of the ensemble timed alone (200 back-to-back
+    launches each, CUDA events on the stream; lbib_ensemble_profile_kernels on
+    a scratch copy), with their algorithmic bytes per launch (the members'
+    sums, as in alg_bytes_per_launch)."""
+    scratch = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream, tiling=tiling)
+    scratch.set_groups(groups)
+    with torch.cuda.stream(stream):
+        scratch.step(4)
+        scratch.sync()
+        kms = lbib.lbib_ensemble_profile_kernels(scratch.ens, 200)
+    scratch.close()
+    alg = [0, 0, 0]
+    for wl in wls:
+        for k, b in enumerate(alg_bytes_per_launch(precision, wl)):
+            alg[k] += b
+    key = {0: "k_forces_batch", 1: "fused_batch", 2: "k_advance_batch"}
+    out = []
+    for k, (name, ms_k, b) in enumerate(zip(ENSEMBLE_KERNEL_NAMES, kms, alg)):
+        gbs = b / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+        out.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": b,
+                    "traffic": traffic.get("%s:ensemble64_%s:%d,%d" % (key[k], precision, tiling[0], tiling[1]))})
+    return out
+
+
+def capillary_line(lbib, torch, stream, precision, pk, traffic, T=1000, steps=5, warmup=3):
+    """The 640 x 160 coarse capillary alone (L2-resident, latency-bound): MLUPS
+    over `steps` calls of T time steps (CUDA events; L2 flushed between
+    calls) and its three kernels timed alone."""
+    from paper_1907_00080_gb300 import tuning
+    wl = workload(precision)
+    tiling = tuning.bench_tiling(wl)
+    sim = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            sim.step(T)
+        sim.sync()
+        ms = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(T)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+    vec, ty = sim.tiling
+    sim.close()
+    del flush
+    scratch = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        scratch.step(4)
+        scratch.sync()
+        lbib.lbib_profile_kernels(scratch.ctx, 50)
+        kms = lbib.lbib_profile_kernels(scratch.ctx, 500)
+    scratch.close()
+    alg = alg_bytes_per_launch(precision, wl)
+    key = {0: "k_forces", 1: "fused", 2: "k_advance"}
+    kernels = []
+    for k, (name, ms_k, b) in enumerate(zip(KERNEL_NAMES, kms, alg)):
+        gbs = b / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+        kernels.append({"kernel": name, "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": b,
+                        "achieved_gbs": gbs, "frac": gbs / pk["hbm_gbs"],
+                        "traffic": traffic.get("%s:capillary_640x160_%s" % (key[k], precision))})
+    return {"workload": C2_WORKLOAD, "mlups": wl.nx * wl.ny * T * steps / (ms * 1e-3) / 1e6,
+            "us_per_timestep": 1e3 * ms / (T * steps), "tiling": [vec, ty], "timesteps": T * steps,
+            "l2": "flushed (256 MB write) between calls; within one the lattice (7.4 MB) is L2-resident",
+            "kernels": kernels}
+
+
+def ensemble_e2e(lbib, torch, wls, tiling, groups, stream, T, steps):
+    """End to end through the public API with host buffers: per step, every
+    member's populations (FP64) and markers go up from pinned host memory, the
+    ensemble advances T time steps, every member's markers come back (host
+    wall clock)."""
+    ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream, tiling=tiling)
+    ens.set_groups(groups)
+    with torch.cuda.stream(stream):
+        ens.step(2)
+        ens.sync()
+        f_host, x_host, x_out = [], [], []
+        for wl, m in zip(wls, ens.members):
+            f = torch.empty((9, wl.ny, wl.nx), dtype=torch.float64, pin_memory=True).numpy()
+            f[:] = m.populations()
+            x = torch.empty((m.nv, 2), dtype=torch.float64, pin_memory=True).numpy()
+            x[:] = m.markers()
+            f_host.append(f)
+            x_host.append(x)
+            x_out.append(torch.empty((m.nv, 2), dtype=torch.float64, pin_memory=True).numpy())
+
+        def one():
+            for m, f, x in zip(ens.members, f_host, x_host):
+                lbib.lbib_write_populations(m.ctx, f)
+                lbib.lbib_write_markers(m.ctx, x, x)
+            ens.step(T)
+            ens.sync()
+            for m, xo in zip(ens.members, x_out):
+                lbib.lbib_read_markers(m.ctx, -1, xo)
+
+        one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    ens.close()
+    nodes = sum(wl.nx * wl.ny for wl in wls)
+    h2d = sum(f.nbytes for f in f_host) + 2 * sum(x.nbytes for x in x_host)
+    d2h = sum(x.nbytes for x in x_out)
+    return {"value": nodes * T * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps,
+            "note": "host wall clock; each step uploads every member's populations + markers, advances %d time "
+                    "steps, reads every member's markers back" % T}
 
 
 def alg_bytes_per_launch(precision, wl):
@@ -378,12 +575,12 @@ def alg_bytes_per_launch(precision, wl):
     return forces, fused, advance
 
 
-def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
+def hbm_probe(lbib, torch, stream, precision, pk, pk_kind, traffic):
     """Fused kernel on an 8192 x 2048 lattice (1.2 GB of FP32 populations per
     buffer, far above L2) with the capillary's marker density scaled up."""
-    from paper_1907_00080_gb300.profile_case import probe_workload
+    from paper_1907_00080_gb300 import inputs
     nx, ny = 8192, 2048
-    wl = probe_workload(nx, ny, precision)  # 256 soft carriers of 50 markers
+    wl = inputs.probe_lattice(nx, ny, precision)  # 256 soft carriers of 50 markers
     sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
     vec, ty = sim.tiling
     with torch.cuda.stream(stream):
@@ -394,11 +591,12 @@ def hbm_probe(lbib, torch, stream, precision, pk, pk_kind):
     sim.close()
     alg = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[precision] * nx * ny
     gbs = alg / (ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get(("k_lb_stream", precision, "probe_8192x2048")) if ty == 0 else None
+    # the 8192 x 1024 capture scaled by the nodes (traffic grows in proportion)
+    t = traffic.get("fused:probe_8192x1024_%s:%d,%d" % (precision, vec, ty))
     return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / pk["hbm_gbs"], "traffic": traffic, "nx": nx, "ny": ny, "tiling": [vec, ty],
-            "ms_per_launch": ms, "algorithmic_bytes_per_launch": alg, "peak_kind": pk_kind + " (copy bandwidth, burst)",
-            "mlups_fused_kernel": nx * ny / (ms * 1e-3) / 1e6}
+            "frac": gbs / pk["hbm_gbs"], "traffic": 2 * t if t else None, "nx": nx, "ny": ny,
+            "tiling": [vec, ty], "ms_per_launch": ms, "algorithmic_bytes_per_launch": alg,
+            "peak_kind": pk_kind + " (copy bandwidth, burst)", "mlups_fused_kernel": nx * ny / (ms * 1e-3) / 1e6}
 
 
 def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
@@ -551,14 +749,12 @@ def dynamic_form(lbib, torch, stream, warm=200, timed=4000, couette_warm=2000, c
             "steps": {"capillary": warm + timed, "couette": couette_warm + couette_timed}}
 
 
-def ensemble_form(lbib, torch, stream, n=64, steps=400):
-    """Ensemble form: n coarse capillaries of lengths 32-64 um (NX 512-1008,
-    NY 160; red cells at the 640 x 160 density, 4 carriers at random release
-    heights, Ca and sigma swept), advanced together (one graph launch per 16
-    steps) against the same instances run one after another.  MLUPS = all
-    instances' nodes x steps / time (CUDA events on the stream)."""
-    from paper_1907_00080_gb300 import inputs
-    wls = inputs.capillary_ensemble(n, seed=0, precision="f32")
+def ensemble_form(lbib, torch, stream, wls, tiling, groups, steps=5000):
+    """Ensemble form: the 64 coarse capillaries of the headline in the batched
+    form (autotuned shape) against the same instances run one after another
+    as plain single runs (each at its own default tiling), over `steps` time
+    steps each.  MLUPS = all instances' nodes x steps / time (CUDA events on
+    the stream)."""
     nodes = sum(wl.nx * wl.ny for wl in wls)
 
     def timed(run):
@@ -570,26 +766,29 @@ def ensemble_form(lbib, torch, stream, n=64, steps=400):
         return e0.elapsed_time(e1) * 1e-3
 
     with torch.cuda.stream(stream):
-        ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream)
+        ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream, tiling=tiling)
+        ens.set_groups(groups)
         ens.step(32)
         ens.sync()
         t_ens = timed(lambda: ens.step(steps))
         ens.sync()
         ens.close()
         sims = [lbib.Simulation(wl, cuda_stream=stream.cuda_stream) for wl in wls]
-        for s in sims:
-            s.step(32)
+        for s_ in sims:
+            s_.step(32)
         torch.cuda.synchronize()
 
         def sequential():
-            for s in sims:
-                s.step(steps)
+            for s_ in sims:
+                s_.step(steps)
 
         t_seq = timed(sequential)
-        for s in sims:
-            s.close()
+        for s_ in sims:
+            s_.close()
     return {"workload": "%d coarse capillaries, NX %d-%d x NY 160, %d nodes, %d markers in all" % (
-                n, min(wl.nx for wl in wls), max(wl.nx for wl in wls), nodes, sum(wl.n_vertices for wl in wls)),
+                len(wls), min(wl.nx for wl in wls), max(wl.nx for wl in wls), nodes,
+                sum(wl.n_vertices for wl in wls)),
+            "tiling": list(tiling), "groups": groups,
             "steps": steps, "ensemble_mlups": nodes * steps / t_ens / 1e6,
             "sequential_mlups": nodes * steps / t_seq / 1e6, "speedup_vs_sequential": t_seq / t_ens,
             "ensemble_ms_per_step": 1e3 * t_ens / steps, "sequential_ms_per_step": 1e3 * t_seq / steps}
@@ -665,40 +864,69 @@ def differentiation_form(lbib, torch, steps=5000, checkpoint_every=250):
                         "gradient_cost_vs_primal": t_jac / 4 / t_primal * 4}}
 
 
-def end_to_end(lbib, torch, wl, tiling, stream, T, steps):
-    """Per step: upload the state from pinned host memory (populations and
-    markers), advance T time steps, read rho/u and the markers back."""
-    sim = lbib.Simulation(wl, tiling=tiling, cuda_stream=stream.cuda_stream)
-    with torch.cuda.stream(stream):
+# ------------------------------------------------------------------ profiler cases
+ALG_BYTES_PER_NODE = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+
+
+def profile_case_main(args):
+    """One small, fixed case for a profiler (ncu) or a quick timing; prints
+    one JSON line.  probe: an nx x ny channel with soft carriers spread over
+    it (inputs.probe_lattice), stepped twice, then --launches launches of the
+    fused kernel alone (lbib_profile_fused).  capillary / fine / dynamic: the
+    640 x 160 capillary, the 2000 x 667 fine capillary, or the capillary with
+    dynamic carriers, stepped --case-steps time steps.  ensemble: the 64-member
+    ensemble in the batched form (--tiling, --groups) stepped --case-steps
+    time steps.  adjoint: the 320 x 160 sensitivity case (FP64) recorded for
+    --case-steps steps with checkpoints every --checkpoint-every, then one
+    backward sweep."""
+    from paper_1907_00080_gb300 import build, inputs, lbib
+    build.build()
+    lbib.load()
+    tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+    out = {"case": args.profile_case, "precision": args.precision}
+    if args.profile_case == "probe":
+        wl = inputs.probe_lattice(args.nx, args.ny, args.precision)
+        sim = lbib.Simulation(wl, tiling=tiling)
         sim.step(2)
         sim.sync()
-        f_host = torch.empty((9, wl.ny, wl.nx), dtype=torch.float64, pin_memory=True).numpy()
-        f_host[:] = sim.populations()
-        x_host = torch.empty((sim.nv, 2), dtype=torch.float64, pin_memory=True).numpy()
-        x_host[:] = sim.markers()
-        fields = [torch.empty((wl.ny, wl.nx), dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
-        xout = torch.empty((sim.nv, 2), dtype=torch.float64, pin_memory=True).numpy()
-
-        def one():
-            lbib.lbib_write_populations(sim.ctx, f_host)
-            lbib.lbib_write_markers(sim.ctx, x_host, x_host)
-            sim.step(T)
-            lbib.lbib_read_fields(sim.ctx, fields[0], fields[1], fields[2])
-            lbib.lbib_read_markers(sim.ctx, -1, xout)
-
-        one()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            one()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-    sim.close()
-    h2d = f_host.nbytes + 2 * x_host.nbytes
-    d2h = sum(a.nbytes for a in fields) + xout.nbytes
-    return {"value": wl.nx * wl.ny * T * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps,
-            "note": "host wall clock; each step uploads populations + markers, advances %d time steps, reads rho/u + markers" % T}
+        ms = lbib.lbib_profile_fused(sim.ctx, args.launches)
+        alg = ALG_BYTES_PER_NODE[args.precision] * wl.nx * wl.ny
+        out.update(nx=wl.nx, ny=wl.ny, tiling=list(sim.tiling), launches=args.launches,
+                   ms_per_launch=ms, algorithmic_bytes_per_launch=alg, gbs=alg / (ms * 1e-3) / 1e9)
+        sim.close()
+    elif args.profile_case == "ensemble":
+        wls = ensemble_workloads(args.precision)
+        ens = lbib.Ensemble(wls, tiling=tiling)
+        if ens.form == 1:
+            ens.set_groups(args.groups)
+        ens.step(args.case_steps)
+        ens.sync()
+        out.update(members=len(wls), form=ens.form, groups=ens.groups, steps=args.case_steps,
+                   tiling=list(tiling) if tiling else None)
+        ens.close()
+    elif args.profile_case == "adjoint":
+        from paper_1907_00080_gb300 import sensitivity
+        rec = sensitivity.Recording(sensitivity.default_params(), args.case_steps, args.checkpoint_every)
+        try:
+            g = rec.gradient((1.0, 1.0))
+        finally:
+            rec.close()
+        out.update(precision="f64", steps=args.case_steps, checkpoint_every=args.checkpoint_every,
+                   gradient=[float(v) for v in g])
+    else:
+        if args.profile_case == "fine":
+            wl = inputs.fine_capillary_2000x667(args.precision)
+        elif args.profile_case == "dynamic":
+            wl = inputs.coarse_capillary_640x160(args.precision, carrier_model="dynamic")
+        else:
+            wl = inputs.coarse_capillary_640x160(args.precision)
+        sim = lbib.Simulation(wl, tiling=tiling)
+        sim.step(args.case_steps)
+        sim.sync()
+        out.update(nx=wl.nx, ny=wl.ny, steps=args.case_steps, tiling=list(sim.tiling))
+        sim.close()
+    print(json.dumps(out))
+    return 0
 
 
 if __name__ == "__main__":

@@ -264,6 +264,13 @@ lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
  *   graphs; waits for the ensemble's stream.  LBIB_E_STATE if not batched,
  *   LBIB_E_INVALID out of range.  Results do not depend on the grouping.
  * lbib_ensemble_groups: the groups in use (0 if not batched, -1 for NULL).
+ * lbib_ensemble_profile_kernels: time the batched kernels alone, `reps`
+ *   back-to-back launches of each kind over all groups, and return the mean
+ *   ms per launch (a time step of the whole ensemble) of the force kernel,
+ *   the fused kernel and the advance kernel in ms_per_launch[0..2] (CUDA
+ *   events on the ensemble's stream).  The launches do not form time steps,
+ *   so the members are left poisoned: profile a scratch ensemble.
+ *   LBIB_E_STATE if not batched.
  * lbib_ensemble_launches_per_step: kernel launches per time step of the
  *   whole ensemble (3 per group in the batched form, the members' sum
  *   otherwise).
@@ -288,6 +295,7 @@ int32_t lbib_ensemble_size(const lbib_ensemble* ens);
 int32_t lbib_ensemble_form(const lbib_ensemble* ens);
 lbib_status lbib_ensemble_set_groups(lbib_ensemble* ens, int32_t groups);
 int32_t lbib_ensemble_groups(const lbib_ensemble* ens);
+lbib_status lbib_ensemble_profile_kernels(lbib_ensemble* ens, int32_t reps, double* ms_per_launch);
 int32_t lbib_ensemble_launches_per_step(const lbib_ensemble* ens);
 lbib_ctx* lbib_ensemble_member(lbib_ensemble* ens, int32_t i);
 const char* lbib_ensemble_last_error(const lbib_ensemble* ens);

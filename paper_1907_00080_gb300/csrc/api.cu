@@ -1553,6 +1553,41 @@ extern "C" lbib_status lbib_ensemble_set_groups(lbib_ensemble* e, int32_t groups
     return ensemble_build_batched(e, groups);
 }
 
+extern "C" lbib_status lbib_ensemble_profile_kernels(lbib_ensemble* e, int32_t reps, double* ms_per_launch) {
+    if (!e || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
+    if (!e->batched) return ens_fail(e, LBIB_E_STATE, "kernel times apply to the batched form only");
+    const lbib_ctx* c0 = e->m[0];
+    const bool walls = c0->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    const int G = (int)e->gstart.size() - 1;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) ECK(cudaEventCreate(&ev[k]));
+    ECK(cudaEventRecord(ev[0], e->stream));
+    for (int r = 0; r < reps; ++r)
+        for (int g = 0; g < G; ++g) ECK(launch_forces_batch(c0->prec, e->fbb[e->flip][g], e->stream));
+    ECK(cudaEventRecord(ev[1], e->stream));
+    for (int r = 0; r < reps; ++r)
+        for (int g = 0; g < G; ++g) {
+            const int p = e->flip ^ (r & 1);
+            ECK(c0->ty > 0 ? launch_lb_batch(c0->prec, c0->vec, c0->ty, walls, e->lbb[p][g], e->stream)
+                           : launch_lb_stream_batch(c0->prec, c0->vec, walls, e->stream_grid, e->lbb[p][g], e->stream));
+        }
+    ECK(cudaEventRecord(ev[2], e->stream));
+    for (int r = 0; r < reps; ++r)
+        for (int g = 0; g < G; ++g)
+            ECK(launch_advance_batch(c0->prec, false, e->abb[e->flip][g], e->adv_threads, e->stream));
+    ECK(cudaEventRecord(ev[3], e->stream));
+    ECK(cudaEventSynchronize(ev[3]));
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        ECK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+        ms_per_launch[k] = ms / reps;
+    }
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    // the members' state is no longer a time step's: the ensemble is spent
+    for (lbib_ctx* c : e->m) c->poisoned = true;
+    return LBIB_OK;
+}
+
 extern "C" int32_t lbib_ensemble_groups(const lbib_ensemble* e) {
     return e ? (e->batched ? (int32_t)e->gstart.size() - 1 : 0) : -1;
 }

@@ -448,3 +448,20 @@ def random_populations(nx, ny, base, seed=0, amp=1e-2):
     rng = np.random.Generator(np.random.PCG64(seed))
     base = np.asarray(base, dtype=np.float64).reshape(9, 1, 1)
     return base * (1.0 + amp * rng.uniform(-1.0, 1.0, size=(9, ny, nx)))
+
+
+def probe_lattice(nx, ny, precision="f32", n_carriers=None, seed=1) -> Workload:
+    """Roofline probe of the fused kernel: an nx x ny channel (Poiseuille start
+    at u_max = 1e-5) with soft circular carriers (R = 8, 50 markers) at seeded
+    random positions, as many as give the 640 x 160 capillary's share of nodes
+    under a marker stencil (256 on 8192 x 2048)."""
+    wl = Workload(name="probe_%dx%d" % (nx, ny), nx=nx, ny=ny,
+                  body_force=(body_force_for(1e-5, ny), 0.0), walls=1,
+                  init="poiseuille", precision=precision, membranes=[], receptors=None)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if n_carriers is None:
+        n_carriers = max(1, int(round(256 * nx * ny / (8192 * 2048))))
+    for _ in range(n_carriers):
+        cx, cy = rng.uniform(0, nx), rng.uniform(20, ny - 20)
+        wl.membranes.append(Membrane(xy=circle(cx, cy, 8.0, 50), ks=1e-4, kb=0.0, ka=1.0))
+    return wl

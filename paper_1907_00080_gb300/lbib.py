@@ -85,6 +85,7 @@ _SIGS = {
     "lbib_ensemble_form": (_I32, [_P]),
     "lbib_ensemble_set_groups": (ctypes.c_int, [_P, _I32]),
     "lbib_ensemble_groups": (_I32, [_P]),
+    "lbib_ensemble_profile_kernels": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_D)]),
     "lbib_ensemble_launches_per_step": (_I32, [_P]),
     "lbib_ensemble_member": (_P, [_P, _I32]),
     "lbib_ensemble_last_error": (ctypes.c_char_p, [_P]),
@@ -371,6 +372,14 @@ def lbib_ensemble_set_groups(ens, groups):
 
 def lbib_ensemble_groups(ens):
     return load().lbib_ensemble_groups(ens)
+
+
+def lbib_ensemble_profile_kernels(ens, reps):
+    """mean ms per launch of the batched force, fused and advance kernels
+    (spends the ensemble: profile a scratch one)"""
+    out = (_D * 3)()
+    _echeck(ens, load().lbib_ensemble_profile_kernels(ens, int(reps), out))
+    return list(out)
 
 
 def lbib_ensemble_launches_per_step(ens):

@@ -167,3 +167,26 @@ def test_ensemble_groups_are_refused_outside_their_range():
     lbib.lbib_ensemble_destroy(e2)
     for s in members:
         s.ctx = None
+
+
+def test_benchmark_ensemble_takes_its_tuned_shape():
+    """The 64-member ensemble of the benchmark: the shape stored by the
+    autotuner (or tuned on the spot) gives the batched form, and the ensemble
+    steps with it."""
+    from paper_1907_00080_gb300 import lbib, tuning
+    wls = inputs.capillary_ensemble(64, seed=0, precision="f32")
+    (tiling, groups), tuned = tuning.ensemble_shape(wls)
+    if tuned is None:
+        assert tuning.ENSEMBLE_TABLE[tuning.ensemble_key(wls)] == (tiling, groups)
+    else:
+        assert (tiling, groups) == min(tuned, key=tuned.get)
+    ens = lbib.Ensemble(wls, tiling=tiling)
+    assert ens.form == 1
+    ens.set_groups(groups)
+    assert ens.groups == groups and ens.launches_per_step == 3 * groups
+    ens.step(20)
+    ens.sync()
+    for m in ens.members[:3]:
+        assert lbib.lbib_step_count(m.ctx) == 20
+        assert lbib.lbib_get_tiling(m.ctx) == tuple(tiling)
+    ens.close()
