@@ -35,12 +35,15 @@
  * numbers (orc_tangent_*), differentiated line by line from the code above,
  * with bond events (step 11) held at the primal's.
  *
- * Readings of passages the paper leaves open (all listed in the design notes):
+ * Readings of passages the paper leaves open:
  *  - Eq. ForcingTerm is read as the standard Guo term
  *      F_i = (1 - 1/(2 tau)) w_i [3 (e_i - u) + 9 (e_i.u) e_i] . G
  *    and the momentum as rho u = sum_i f_i e_i + G/2 (Sec. 2.2, the "f_lb" in
  *    the text being the same body force).
- *  - walls are half-way bounce-back at y = -1/2 and y = NY - 1/2.
+ *  - walls are half-way bounce-back at y = -1/2 and y = NY - 1/2; or (walls =
+ *    2) Zou and He's known-velocity condition on the wall rows y = 0 and
+ *    y = NY - 1, with the populations' momentum the wall velocity less the
+ *    Guo half-force of the node.
  *  - the MLS weight is the Roma 3-point kernel on the nine nearest nodes; where
  *    all nine nodes are fluid the MLS shape function equals the Roma weight
  *    exactly and is taken as such; near walls the out-of-fluid nodes are dropped
@@ -103,7 +106,8 @@ typedef struct {
     int nx, ny;
     double tau;
     double gx, gy;    /* uniform body force G_body (Sec. 3 drive)        */
-    int walls;        /* 0: periodic in y too; 1: bounce-back walls in y */
+    int walls;        /* 0: periodic in y too; 1: half-way bounce-back walls in y;
+                         2: Zou-He known-velocity walls on the rows y = 0, NY - 1 */
     double *f;        /* f^n, [9][ny][nx], pre-collision                 */
     double *rho, *ux, *uy; /* moments of the last collide                */
     double *Gx, *Gy;  /* force field used by the last collide           */
@@ -131,7 +135,7 @@ typedef struct {
     uint64_t seed, instance;
 
     double d_rep, p_ref;
-    double uw_bot, uw_top;     /* x velocities of the walls y = -1/2 and y = NY - 1/2 */
+    double uw_bot, uw_top;     /* x velocities of the lower and upper walls */
     long step;
 
     /* dynamic particles (kinds 2 and 3, Sec. 2.4) */
@@ -225,6 +229,40 @@ static void moments_at(const double *f, long N, long node, double gx, double gy,
  * wall moving along x with velocity u_w (the Couette set-up of Sec. 4) adds the
  * momentum it imparts, 2 w_i rho_w (e_i . u_w) / c_s^2 with rho_w = 1 (the
  * bounce-back rule for moving walls of Ladd, J. Fluid Mech. 271, 1994). */
+/* Zou and He's known-velocity condition (Sec. 2.1; Zou & He, Phys. Fluids 9,
+ * 1997) on a wall row (wet nodes: y = 0 is the lower wall, y = NY - 1 the
+ * upper one).  After streaming, the three populations that would come from
+ * outside the fluid are unknown: at the lower wall f_2, f_5, f_6, at the upper
+ * f_4, f_7, f_8.  With the wall's velocity (u_w, 0) and the known populations,
+ * density and momentum fix them: rho = f_0 + f_1 + f_3 + 2 (the three known
+ * populations leaving toward the wall's outside) + j_y (j_y signed toward the
+ * inside), and the unknown normal population is its opposite plus 2/3 j_y,
+ * the two unknown diagonals their opposites -+ (f_1 - f_3)/2 +- j_x/2 + j_y/6.
+ * The momentum the populations carry is the known velocity less the Guo
+ * half-force of the node (rho u = sum f e + G/2, Sec. 2.2):
+ * j = rho (u_w, 0) - G/2, so that the collision sees u = (u_w, 0). */
+static void zou_he_node(const orc_sim *s, double *f, long N, long node, int lower, double gx, double gy) {
+    double uw = lower ? s->uw_bot : s->uw_top;
+    double f0 = f[0 * N + node], f1 = f[1 * N + node], f3 = f[3 * N + node];
+    if (lower) {
+        double f4 = f[4 * N + node], f7 = f[7 * N + node], f8 = f[8 * N + node];
+        double jy = -0.5 * gy;                      /* toward the inside: +y */
+        double rho = f0 + f1 + f3 + 2.0 * (f4 + f7 + f8) + jy;
+        double jx = rho * uw - 0.5 * gx;
+        f[2 * N + node] = f4 + (2.0 / 3.0) * jy;
+        f[5 * N + node] = f7 - 0.5 * (f1 - f3) + 0.5 * jx + (1.0 / 6.0) * jy;
+        f[6 * N + node] = f8 + 0.5 * (f1 - f3) - 0.5 * jx + (1.0 / 6.0) * jy;
+    } else {
+        double f2 = f[2 * N + node], f5 = f[5 * N + node], f6 = f[6 * N + node];
+        double jy = -0.5 * gy;                      /* y momentum the populations carry */
+        double rho = f0 + f1 + f3 + 2.0 * (f2 + f5 + f6) - jy;
+        double jx = rho * uw - 0.5 * gx;
+        f[4 * N + node] = f2 - (2.0 / 3.0) * jy;
+        f[7 * N + node] = f5 + 0.5 * (f1 - f3) - 0.5 * jx - (1.0 / 6.0) * jy;
+        f[8 * N + node] = f6 - 0.5 * (f1 - f3) + 0.5 * jx - (1.0 / 6.0) * jy;
+    }
+}
+
 void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
     long nx = s->nx, ny = s->ny, N = nx * ny;
     for (int i = 0; i < 9; ++i) {
@@ -235,7 +273,9 @@ void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
                 long sy = y - EY[i];
                 long sx = imod(x - EX[i], nx);
                 double v;
-                if (s->walls && (sy < 0 || sy >= ny)) {
+                if (s->walls == 2 && (sy < 0 || sy >= ny)) {
+                    v = 0.0;  /* unknown: Zou-He below */
+                } else if (s->walls && (sy < 0 || sy >= ny)) {
                     double uw = sy < 0 ? s->uw_bot : s->uw_top;
                     v = fstar[o * N + y * nx + x] + 6.0 * W9[i] * (EX[i] * uw);
                 } else {
@@ -244,6 +284,14 @@ void orc_stream(const orc_sim *s, const double *fstar, double *fout) {
                 }
                 fout[i * N + y * nx + x] = v;
             }
+        }
+    }
+    /* Zou-He walls: the unknown populations of the wall rows as the known
+     * velocity fixes them; the collision redoes this with the node's force */
+    if (s->walls == 2) {
+        for (long x = 0; x < nx; ++x) {
+            zou_he_node(s, fout, N, x, 1, 0.0, 0.0);
+            zou_he_node(s, fout, N, (ny - 1) * nx + x, 0, 0.0, 0.0);
         }
     }
 }
@@ -263,6 +311,8 @@ static void collide_and_stream(orc_sim *s) {
         double feq[9], F[9];
         double rho, ux, uy;
         double gx = s->Gx[n], gy = s->Gy[n];
+        if (s->walls == 2 && (n < s->nx || n >= N - s->nx))
+            zou_he_node(s, s->f, N, n, n < s->nx, gx, gy);
         moments_at(s->f, N, n, gx, gy, &rho, &ux, &uy);
         s->rho[n] = rho; s->ux[n] = ux; s->uy[n] = uy;
         orc_equilibrium(rho, ux, uy, feq);

@@ -277,3 +277,55 @@ def test_walls_moving_together_carry_the_fluid_along():
     s.step(5000)
     rho, ux, uy = s.fields()
     np.testing.assert_allclose(ux, 0.02, rtol=0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Zou-He walls
+@pytest.mark.parametrize("tau", [0.8, 1.0, 1.3])
+def test_zou_he_couette_from_rest_is_the_linear_profile(tau):
+    """Sec. 2.1 (Zou and He's known-velocity walls on the wall rows y = 0 and
+    y = NY - 1): planar Couette flow between walls moving at u_b and u_t,
+    started from rest, reaches u(y) = u_b + (u_t - u_b) y / (NY - 1) with
+    rho = 1 at any tau (the linear profile is the scheme's exact steady
+    state)."""
+    nx, ny, ub, ut = 8, 17, -0.01, 0.02
+    s = oracle.OracleSim(nx, ny, tau=tau, walls=2, init="rest", wall_velocity=(ub, ut))
+    s.step(20000)
+    rho, ux, uy = s.fields()
+    u = ub + (ut - ub) * np.arange(ny) / (ny - 1)
+    assert np.max(np.abs(ux - u[:, None])) < 1e-13
+    assert np.max(np.abs(uy)) < 1e-14
+    assert np.max(np.abs(rho - 1.0)) < 1e-11
+
+
+@pytest.mark.parametrize("tau", [1.0, 1.3])
+def test_zou_he_poiseuille_from_rest_is_the_parabola(tau):
+    """A uniform body force G between resting Zou-He walls (the channel of
+    height H = NY - 1 between the wall rows) reaches the plane Poiseuille
+    profile u(y) = G y (H - y) / (2 nu), zero on the wall rows: the known
+    velocity includes the Guo half-force, so the wall rows carry no slip."""
+    nx, ny, G = 4, 17, 1e-6
+    nu = (tau - 0.5) / 3.0
+    s = oracle.OracleSim(nx, ny, tau=tau, body_force=(G, 0.0), walls=2, init="rest")
+    s.step(30000)
+    _, ux, _ = s.fields()
+    y = np.arange(ny)
+    u = G / (2 * nu) * y * (ny - 1 - y)
+    assert np.max(np.abs(ux - u[:, None])) / u.max() < 1e-9
+    assert np.max(np.abs(ux[[0, -1]])) < 1e-15
+
+
+def test_zou_he_rows_take_the_wall_velocity_every_step():
+    """From a random state with a force field, every collision on the wall rows
+    sees exactly the wall velocity (the condition's definition), while mass
+    elsewhere is untouched by it."""
+    nx, ny = 12, 9
+    s = oracle.OracleSim(nx, ny, tau=0.9, body_force=(3e-5, -2e-5), walls=2, init="rest",
+                         wall_velocity=(0.004, -0.007))
+    rng = np.random.default_rng(3)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    s.set_populations(w[:, None, None] * (1 + 0.05 * rng.uniform(-1, 1, (9, ny, nx))))
+    for _ in range(3):
+        s.step(1)
+        _, ux, uy = s.fields()
+        assert np.max(np.abs(ux[0] - 0.004)) < 1e-15 and np.max(np.abs(ux[-1] + 0.007)) < 1e-15
+        assert np.max(np.abs(uy[[0, -1]])) < 1e-16
