@@ -18,7 +18,15 @@
  * Units: lattice units throughout (dx = dt = 1, rho_0 = 1).  The lattice has
  * NX nodes along the periodic x axis and NY fluid rows y = 0..NY-1; with
  * LBIB_WALLS_Y_BOUNCEBACK the walls sit half a node outside, at y = -1/2 and
- * y = NY - 1/2 (half-way bounce-back), otherwise y is periodic as well.
+ * y = NY - 1/2 (half-way bounce-back); with LBIB_WALLS_ZOU_HE they are the
+ * rows y = 0 and y = NY - 1 themselves (wet nodes: after streaming, the three
+ * populations that would come from outside are rebuilt by Zou and He's
+ * known-velocity condition from the wall's velocity, lbib_set_wall_velocity,
+ * and the known ones; the populations' momentum is the wall velocity less the
+ * node's Guo half-force, so the collision sees the wall velocity); with
+ * LBIB_WALLS_NONE y is periodic as well.  Zou-He walls start from rest
+ * (LBIB_INIT_REST) or from written populations, and take kinematic and
+ * rigid-projected membranes only; the derivative forms refuse them.
  *
  * Conventions for every call:
  *  - every call returns an lbib_status; lbib_last_error() gives a message;
@@ -69,7 +77,9 @@ typedef enum {
 
 typedef enum {
     LBIB_WALLS_NONE = 0,          /* periodic in x and y (e.g. shear-wave tests) */
-    LBIB_WALLS_Y_BOUNCEBACK = 1   /* half-way bounce-back walls in y            */
+    LBIB_WALLS_Y_BOUNCEBACK = 1,  /* half-way bounce-back walls in y            */
+    LBIB_WALLS_ZOU_HE = 2         /* Zou-He known-velocity walls on the rows y = 0
+                                     and y = NY - 1 (Sec. 2.1); see below      */
 } lbib_walls;
 
 typedef enum {

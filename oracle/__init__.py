@@ -224,7 +224,8 @@ def ring_mass_properties(xy):
 
 # ---------------------------------------------------------------- simulation
 class OracleSim:
-    """One oracle simulation (FP64, CPU).  walls=1: bounce-back walls in y."""
+    """One oracle simulation (FP64, CPU).  walls=1: half-way bounce-back walls in
+    y; walls=2: Zou-He known-velocity walls on the rows y = 0 and NY - 1."""
 
     def __init__(self, nx, ny, tau=1.0, body_force=(0.0, 0.0), walls=1, init="rest", wall_velocity=(0.0, 0.0)):
         self.nx, self.ny = int(nx), int(ny)

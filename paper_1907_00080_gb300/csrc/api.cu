@@ -171,7 +171,8 @@ double bb_term(double u_wall);
 cudaError_t init_populations(lbib_ctx* c) {
     const size_t N = (size_t)c->nx * c->ny;
     cudaError_t e = cudaMemsetAsync(c->f[0], 0, 9 * N * c->pop_elem, c->stream);
-    if (e == cudaSuccess && c->init == LBIB_INIT_REST && (c->uw_bot != 0.0 || c->uw_top != 0.0))
+    if (e == cudaSuccess && c->init == LBIB_INIT_REST && c->walls == LBIB_WALLS_Y_BOUNCEBACK &&
+        (c->uw_bot != 0.0 || c->uw_top != 0.0))
         e = launch_init_rest_walls(c->prec, c->f[0], c->nx, c->ny, bb_term(c->uw_bot), bb_term(c->uw_top),
                                    c->inv_scale, c->stream);
     if (e == cudaSuccess && c->init == LBIB_INIT_POISEUILLE)
@@ -191,7 +192,8 @@ extern "C" lbib_status lbib_create(const lbib_lattice* lat, double tau, const do
     if (lat->nx < 4 || lat->ny < 4) return LBIB_E_INVALID;
     if (!(tau > 0.5)) return LBIB_E_INVALID;
     if (lat->prec < LBIB_F64 || lat->prec > LBIB_F32_STORE_BF16) return LBIB_E_INVALID;
-    if (walls != LBIB_WALLS_NONE && walls != LBIB_WALLS_Y_BOUNCEBACK) return LBIB_E_INVALID;
+    if (walls != LBIB_WALLS_NONE && walls != LBIB_WALLS_Y_BOUNCEBACK && walls != LBIB_WALLS_ZOU_HE)
+        return LBIB_E_INVALID;
     if (lat->init == LBIB_INIT_POISEUILLE && (walls != LBIB_WALLS_Y_BOUNCEBACK || tau != 1.0))
         return LBIB_E_INVALID;
     if (lat->init == LBIB_INIT_COUETTE && walls != LBIB_WALLS_Y_BOUNCEBACK) return LBIB_E_INVALID;
@@ -269,6 +271,8 @@ extern "C" lbib_status lbib_add_membrane(lbib_ctx* c, const double* xy, int32_t 
         return fail(c, LBIB_E_INVALID, "unknown membrane kind");
     if (whole_ring(kind) && n > 4 * kChunkV)
         return fail(c, LBIB_E_INVALID, "rigid-projected and rigid dynamic membranes are limited to 256 vertices");
+    if (is_dynamic(kind) && c->walls == LBIB_WALLS_ZOU_HE)
+        return fail(c, LBIB_E_INVALID, "dynamic particles need half-way or no walls");
     if (n_ligands < 0 || (n_ligands > 0 && !ligand_elems))
         return fail(c, LBIB_E_INVALID, "ligand list");
     for (int k = 0; k < 2 * n; ++k)
@@ -305,8 +309,7 @@ extern "C" lbib_status lbib_set_receptors(lbib_ctx* c, const double* xy, int32_t
     if (!c) return LBIB_E_INVALID;
     if (c->finalized) return fail(c, LBIB_E_STATE, "receptors must be set before the first step");
     if (n < 0 || (n > 0 && !xy) || !p) return fail(c, LBIB_E_INVALID, "receptor arguments");
-    if (n > 0 && c->walls != LBIB_WALLS_Y_BOUNCEBACK)
-        return fail(c, LBIB_E_INVALID, "receptors need bounce-back walls");
+    if (n > 0 && c->walls == LBIB_WALLS_NONE) return fail(c, LBIB_E_INVALID, "receptors need walls");
     if (!(p->d_cut > 0.0) || !(p->y_eq > 0.0) || !(p->d_break > 0.0))
         return fail(c, LBIB_E_INVALID, "bond lengths must be positive");
     for (int k = 0; k < 2 * n; ++k)
@@ -325,7 +328,7 @@ extern "C" lbib_status lbib_set_repulsion(lbib_ctx* c, double d_rep) {
 
 extern "C" lbib_status lbib_set_wall_velocity(lbib_ctx* c, double u_bottom, double u_top) {
     if (!c) return LBIB_E_INVALID;
-    if (c->walls != LBIB_WALLS_Y_BOUNCEBACK) return fail(c, LBIB_E_INVALID, "moving walls need bounce-back walls");
+    if (c->walls == LBIB_WALLS_NONE) return fail(c, LBIB_E_INVALID, "moving walls need walls");
     if (!std::isfinite(u_bottom) || !std::isfinite(u_top)) return fail(c, LBIB_E_INVALID, "non-finite wall velocity");
     if (c->graphs_ready || c->steps > 0) return fail(c, LBIB_E_STATE, "wall velocities are fixed at the first step");
     c->uw_bot = u_bottom;
@@ -369,7 +372,7 @@ static lbib_status finalize(lbib_ctx* c) {
     if (c->finalized) return LBIB_OK;
     if (!c->vec) default_tiling(c, &c->vec, &c->ty);
     if (c->ty == 0) {
-        CK(prepare_lb_stream(c->prec, c->vec, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, &c->stream_grid));
+        CK(prepare_lb_stream(c->prec, c->vec, c->walls != LBIB_WALLS_NONE, c->nv > 0, &c->stream_grid));
     } else {
         if ((c->ny + c->ty - 1) / c->ty > kMaxGridY)
             return fail(c, LBIB_E_INVALID, "lattice too tall for the row-tile form: more than 65535 x 16 rows");
@@ -530,7 +533,7 @@ static lbib_status finalize(lbib_ctx* c) {
     ar.base = static_cast<char*>(c->dmem);
     MarkerArgs& a = c->ma;
     a = MarkerArgs{};
-    a.nx = c->nx; a.ny = c->ny; a.walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK ? 1 : 0;
+    a.nx = c->nx; a.ny = c->ny; a.walls = c->walls != LBIB_WALLS_NONE ? 1 : 0;
     a.inv_nx = 1.0 / c->nx; a.inv_ny = 1.0 / c->ny;
     a.nmem = nm; a.nv = nv;
     int* mem_off = ar.take<int>(nm + 1);
@@ -731,10 +734,18 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.gx = c->gx;
     l.gy = c->gy;
     l.inv_scale = c->inv_scale;
-    l.bb_bot = bb_term(c->uw_bot);
-    l.bb_top = bb_term(c->uw_top);
+    // half-way walls: the moving-wall term of the bounced-back diagonals;
+    // Zou-He wall rows: the wall velocities themselves
+    const bool zh = c->walls == LBIB_WALLS_ZOU_HE;
+    l.bb_bot = zh ? 0.0 : bb_term(c->uw_bot);
+    l.bb_top = zh ? 0.0 : bb_term(c->uw_top);
     l.bbf_bot = (float)l.bb_bot;
     l.bbf_top = (float)l.bb_top;
+    l.zou_he = zh ? 1 : 0;
+    l.uw_bot = zh ? c->uw_bot : 0.0;
+    l.uw_top = zh ? c->uw_top : 0.0;
+    l.uwf_bot = (float)l.uw_bot;
+    l.uwf_top = (float)l.uw_top;
     l.fields_only = 0;
     // the two population buffers and the force field well inside the 129 MB L2
     // (not for ensemble members: together they leave L2, and the extra reads
@@ -771,7 +782,7 @@ static HydroArgs hydro_args(const lbib_ctx* c, int src) {
 
 // the fused collide-stream kernel in the context's form
 static cudaError_t launch_fused(const lbib_ctx* c, const LbArgs& l, cudaStream_t s) {
-    const bool walls = c->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    const bool walls = c->walls != LBIB_WALLS_NONE;
     if (c->ty == 0) return launch_lb_stream(c->prec, c->vec, walls, c->nv > 0, c->stream_grid, l, s);
     return launch_lb_step(c->prec, c->vec, c->ty, walls, c->nv > 0, l, s);
 }
@@ -928,7 +939,7 @@ extern "C" lbib_status lbib_read_fields(lbib_ctx* c, double* rho, double* ux, do
     const int rv = c->ty != 0 ? c->vec : (c->prec == LBIB_F32_STORE_F16 || c->prec == LBIB_F32_STORE_BF16 ? 2 : 1);
     int rt = c->ty != 0 ? c->ty : 4;
     while (rt < 16 && (c->ny + rt - 1) / rt > kMaxGridY) rt *= 2;
-    CK(launch_lb_step(c->prec, rv, rt, c->walls == LBIB_WALLS_Y_BOUNCEBACK, c->nv > 0, l, c->stream));
+    CK(launch_lb_step(c->prec, rv, rt, c->walls != LBIB_WALLS_NONE, c->nv > 0, l, c->stream));
     if (!on_device) {
         if (rho) CK(cudaMemcpyAsync(rho, dr, N * 8, cudaMemcpyDeviceToHost, c->stream));
         if (ux) CK(cudaMemcpyAsync(ux, du, N * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -947,8 +958,10 @@ extern "C" lbib_status lbib_read_populations(lbib_ctx* c, double* f, int on_devi
         if ((st = ensure_stage(c)) != LBIB_OK) return st;
         out = c->stage;
     }
-    CK(launch_stream_out(c->prec, c->f[c->cur], out, c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
-                         c->inv_scale, bb_term(c->uw_bot), bb_term(c->uw_top), c->stream));
+    const bool zh = c->walls == LBIB_WALLS_ZOU_HE;
+    CK(launch_stream_out(c->prec, c->f[c->cur], out, c->nx, c->ny, (int)c->walls, c->inv_scale,
+                         zh ? 0.0 : bb_term(c->uw_bot), zh ? 0.0 : bb_term(c->uw_top), c->uw_bot, c->uw_top,
+                         c->stream));
     if (!on_device) CK(cudaMemcpyAsync(f, out, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBIB_OK;
@@ -964,8 +977,11 @@ extern "C" lbib_status lbib_write_populations(lbib_ctx* c, const double* f, int 
         CK(cudaMemcpyAsync(c->stage, f, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
         in = c->stage;
     }
-    CK(launch_stream_in(c->prec, in, c->f[c->cur], c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK,
-                        c->inv_scale, bb_term(c->uw_bot), bb_term(c->uw_top), c->stream));
+    // Zou-He walls: the slots the wall rows would stream out through are
+    // never pulled; the bounce-back inverse fills them harmlessly
+    const bool zh = c->walls == LBIB_WALLS_ZOU_HE;
+    CK(launch_stream_in(c->prec, in, c->f[c->cur], c->nx, c->ny, c->walls != LBIB_WALLS_NONE, c->inv_scale,
+                        zh ? 0.0 : bb_term(c->uw_bot), zh ? 0.0 : bb_term(c->uw_top), c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->fields_valid = false;
     return LBIB_OK;
@@ -1369,14 +1385,14 @@ static lbib_status ensemble_batch_tables(lbib_ensemble* e, int ngroups) {
     }
     const lbib_ctx* c0 = e->m[0];
     if (c0->ty == 0)
-        ECK(prepare_lb_stream_batch(c0->prec, c0->vec, c0->walls == LBIB_WALLS_Y_BOUNCEBACK, &e->stream_grid));
+        ECK(prepare_lb_stream_batch(c0->prec, c0->vec, c0->walls != LBIB_WALLS_NONE, &e->stream_grid));
     return LBIB_OK;
 }
 
 // one time step of every member of group g in the batched form, at phase p
 static cudaError_t ensemble_batch_step(const lbib_ensemble* e, int g, int p, cudaStream_t s) {
     const lbib_ctx* c0 = e->m[0];
-    const bool walls = c0->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    const bool walls = c0->walls != LBIB_WALLS_NONE;
     cudaError_t r = launch_forces_batch(c0->prec, e->fbb[p][g], s);
     if (r == cudaSuccess)
         r = c0->ty > 0 ? launch_lb_batch(c0->prec, c0->vec, c0->ty, walls, e->lbb[p][g], s)
@@ -1557,7 +1573,7 @@ extern "C" lbib_status lbib_ensemble_profile_kernels(lbib_ensemble* e, int32_t r
     if (!e || reps < 1 || !ms_per_launch) return LBIB_E_INVALID;
     if (!e->batched) return ens_fail(e, LBIB_E_STATE, "kernel times apply to the batched form only");
     const lbib_ctx* c0 = e->m[0];
-    const bool walls = c0->walls == LBIB_WALLS_Y_BOUNCEBACK;
+    const bool walls = c0->walls != LBIB_WALLS_NONE;
     const int G = (int)e->gstart.size() - 1;
     cudaEvent_t ev[4];
     for (int k = 0; k < 4; ++k) ECK(cudaEventCreate(&ev[k]));
@@ -1649,6 +1665,7 @@ extern "C" lbib_status lbib_tangent_create(lbib_ctx* c, lbib_tangent** out) {
     if (!c || !out) return LBIB_E_INVALID;
     if (c->prec != LBIB_F64) return fail(c, LBIB_E_INVALID, "the tangent needs an FP64 context");
     if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the tangent needs resting walls");
+    if (c->walls == LBIB_WALLS_ZOU_HE) return fail(c, LBIB_E_INVALID, "the tangent needs half-way or no walls");
     for (int k : c->h_mem_kind)
         if (k != LBIB_MEMBRANE_KINEMATIC)
             return fail(c, LBIB_E_INVALID, "the tangent supports kinematic membranes only");
@@ -1887,6 +1904,7 @@ extern "C" lbib_status lbib_adjoint_create(lbib_ctx* c, int32_t checkpoint_every
     *out = nullptr;
     if (checkpoint_every < 1) return fail(c, LBIB_E_INVALID, "checkpoint interval must be at least 1");
     if (c->uw_bot != 0.0 || c->uw_top != 0.0) return fail(c, LBIB_E_INVALID, "the adjoint needs resting walls");
+    if (c->walls == LBIB_WALLS_ZOU_HE) return fail(c, LBIB_E_INVALID, "the adjoint needs half-way or no walls");
     for (size_t m = 0; m < c->h_mem_kind.size(); ++m) {
         if (c->h_mem_kind[m] != LBIB_MEMBRANE_KINEMATIC)
             return fail(c, LBIB_E_INVALID, "the adjoint supports kinematic membranes only");
@@ -1998,7 +2016,7 @@ extern "C" lbib_status lbib_adjoint_seed(lbib_adjoint* a, const double* xy_bar, 
     }
     if (f_bar) {
         CK(cudaMemcpyAsync(a->fio, f_bar, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
-        CK(launch_adjoint_perm(a->fio, a->fbar[a->cb], c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK, 1,
+        CK(launch_adjoint_perm(a->fio, a->fbar[a->cb], c->nx, c->ny, c->walls != LBIB_WALLS_NONE, 1,
                                c->stream));
     } else {
         CK(cudaMemsetAsync(a->fbar[a->cb], 0, 9 * N * 8, c->stream));
@@ -2114,7 +2132,7 @@ extern "C" lbib_status lbib_adjoint_read(lbib_adjoint* a, double* xy_bar, double
     if (kb_bar && nm) CK(cudaMemcpyAsync(kb_bar, a->kbb, 8 * nm, cudaMemcpyDeviceToHost, c->stream));
     if (sigma_bar) CK(cudaMemcpyAsync(sigma_bar, a->sgb, 8, cudaMemcpyDeviceToHost, c->stream));
     if (f_bar) {
-        CK(launch_adjoint_perm(a->fbar[a->cb], a->fio, c->nx, c->ny, c->walls == LBIB_WALLS_Y_BOUNCEBACK, 0,
+        CK(launch_adjoint_perm(a->fbar[a->cb], a->fio, c->nx, c->ny, c->walls != LBIB_WALLS_NONE, 0,
                                c->stream));
         CK(cudaMemcpyAsync(f_bar, a->fio, 9 * N * 8, cudaMemcpyDeviceToHost, c->stream));
     }

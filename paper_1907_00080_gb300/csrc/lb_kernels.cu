@@ -161,6 +161,8 @@ __device__ __forceinline__ void lb_tile(const LbArgs& a, int bx, int by) {
     const C om = C(a.omega);
     const C pre = C(1) - C(0.5) * om;
     const C om3 = C(3.0 * a.omega);
+    // Zou-He wall rows: the populations from outside rebuilt (warp-uniform: one row per warp)
+    const bool zh = WALLS && a.zou_he && (y == 0 || y == ny - 1);
     C out[9][VEC];
     C rho_v[VEC], ux_v[VEC], uy_v[VEC];
 #pragma unroll
@@ -168,6 +170,7 @@ __device__ __forceinline__ void lb_tile(const LbArgs& a, int bx, int by) {
         C fk[9], ok9[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) fk[i] = f[i][k];
+        if (zh) zou_he<C>(fk, Gx[k], Gy[k], zh_wall_u<C>(a, y == 0), y == 0);
         collide<S>(fk, Gx[k], Gy[k], om, pre, om3, ok9, rho_v[k], ux_v[k], uy_v[k]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i][k] = ok9[i];
@@ -312,25 +315,27 @@ cudaError_t launch_lb_step(lbib_precision prec, int vec, int ty, bool walls, boo
 // pre-collision populations the next step starts from, as doubles.
 template <typename S>
 __global__ void k_stream_out(const S* __restrict__ src, double* __restrict__ out, int nx, int ny,
-                             int walls, float inv, double bb_bot, double bb_top) {
+                             int walls, float inv, double bb_bot, double bb_top, double uw_bot, double uw_top) {
     const size_t N = (size_t)nx * ny;
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         const int y = (int)(n / nx), x = (int)(n % nx);
+        double d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             int sy = y - cy(i), sx = x - cx(i);
             sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-            double d;
             if (walls && (sy < 0 || sy >= ny)) {
-                d = (double)Storage<S>::load(src[(size_t)opp(i) * N + n], inv) +
-                    (double)cx(i) * (sy < 0 ? bb_bot : bb_top);
+                d[i] = (double)Storage<S>::load(src[(size_t)opp(i) * N + n], inv) +
+                       (double)cx(i) * (sy < 0 ? bb_bot : bb_top);
             } else {
                 sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-                d = (double)Storage<S>::load(src[(size_t)i * N + (size_t)sy * nx + sx], inv);
+                d[i] = (double)Storage<S>::load(src[(size_t)i * N + (size_t)sy * nx + sx], inv);
             }
-            out[(size_t)i * N + n] = wgt<double>(i) + d;
         }
+        if (walls == 2 && (y == 0 || y == ny - 1)) zou_he<double>(d, 0.0, 0.0, y == 0 ? uw_bot : uw_top, y == 0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[(size_t)i * N + n] = wgt<double>(i) + d[i];
     }
 }
 
@@ -464,10 +469,11 @@ static int grid_for(size_t n, int block) {
     }
 
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
-                              bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s) {
+                              int walls, float inv_scale, double bb_bot, double bb_top, double uw_bot,
+                              double uw_top, cudaStream_t s) {
     const int g = grid_for((size_t)nx * ny, 256);
-    LBIB_DISPATCH_S(prec, (k_stream_out<S><<<g, 256, 0, s>>>(static_cast<const S*>(src), out, nx,
-                                                              ny, walls ? 1 : 0, inv_scale, bb_bot, bb_top)));
+    LBIB_DISPATCH_S(prec, (k_stream_out<S><<<g, 256, 0, s>>>(static_cast<const S*>(src), out, nx, ny, walls,
+                                                              inv_scale, bb_bot, bb_top, uw_bot, uw_top)));
     return cudaGetLastError();
 }
 

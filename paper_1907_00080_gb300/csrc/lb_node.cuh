@@ -35,6 +35,38 @@ template <> __device__ __forceinline__ double wall_term<double>(const LbArgs& a,
     return bottom ? a.bb_bot : a.bb_top;
 }
 
+// Zou and He's known-velocity condition (Sec. 2.1) on a wall row, in the
+// deviations d_i = f_i - w_i (the weights cancel): lower = true rebuilds
+// d_2, d_5, d_6 of the row y = 0, else d_4, d_7, d_8 of the row y = NY - 1, from
+// the known ones and the wall's velocity (uw, 0).  The populations' momentum
+// is the wall velocity less the node's Guo half-force, j = rho (uw, 0) - G/2,
+// so that the collision's velocity (sum f e + G/2) / rho is (uw, 0).
+template <typename C>
+__device__ __forceinline__ void zou_he(C (&d)[9], C Gx, C Gy, C uw, bool lower) {
+    const C jy = C(-0.5) * Gy;
+    const C s13 = d[1] - d[3];
+    if (lower) {
+        const C rho = C(1) + (d[0] + d[1] + d[3]) + C(2) * (d[4] + d[7] + d[8]) + jy;
+        const C jx = rho * uw - C(0.5) * Gx;
+        d[2] = d[4] + C(2.0 / 3.0) * jy;
+        d[5] = d[7] - C(0.5) * s13 + C(0.5) * jx + C(1.0 / 6.0) * jy;
+        d[6] = d[8] + C(0.5) * s13 - C(0.5) * jx + C(1.0 / 6.0) * jy;
+    } else {
+        const C rho = C(1) + (d[0] + d[1] + d[3]) + C(2) * (d[2] + d[5] + d[6]) - jy;
+        const C jx = rho * uw - C(0.5) * Gx;
+        d[4] = d[2] - C(2.0 / 3.0) * jy;
+        d[7] = d[5] + C(0.5) * s13 - C(0.5) * jx - C(1.0 / 6.0) * jy;
+        d[8] = d[6] - C(0.5) * s13 + C(0.5) * jx - C(1.0 / 6.0) * jy;
+    }
+}
+template <typename C> __device__ __forceinline__ C zh_wall_u(const LbArgs& a, bool lower);
+template <> __device__ __forceinline__ float zh_wall_u<float>(const LbArgs& a, bool lower) {
+    return lower ? a.uwf_bot : a.uwf_top;
+}
+template <> __device__ __forceinline__ double zh_wall_u<double>(const LbArgs& a, bool lower) {
+    return lower ? a.uw_bot : a.uw_top;
+}
+
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }  // = 1.0f / x, correctly rounded
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 

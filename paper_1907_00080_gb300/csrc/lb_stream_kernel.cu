@@ -300,6 +300,8 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
         C fq[9], out[9], rho;
 #pragma unroll
         for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
+        // Zou-He wall rows: the populations from outside rebuilt
+        if (WALLS && A.zou_he && (y == 0 || y == ny - 1)) zou_he<C>(fq, Gx, Gy, zh_wall_u<C>(A, y == 0), y == 0);
         collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);

@@ -100,6 +100,9 @@ struct LbArgs {
     double bb_bot, bb_top; // moving walls: 6 w_d u_w (w_d = 1/36) of the lower / upper wall; a
                            // diagonal population bounced back there gains cx(i) times it
     float bbf_bot, bbf_top;  // the same rounded to FP32 (no FP64 conversion in the FP32 kernels)
+    int zou_he;            // 1: the walls are Zou-He wall rows y = 0, NY - 1 (bb_* are 0)
+    double uw_bot, uw_top; // Zou-He: x velocities of the lower and upper wall rows
+    float uwf_bot, uwf_top;
     int fields_only;       // 1: write rho/ux/uy doubles, skip populations
     int g_prefetch;        // row tiles: read the spread force of every node up front (L2-resident lattices)
     int tile_w, tile_h, tiles_x;  // force-tile geometry of the flags (32 x 1 nodes; tiles_x = ceil(nx / 32))
@@ -281,8 +284,11 @@ cudaError_t launch_lb_stream(lbib_precision prec, int npt, bool walls, bool has_
 cudaError_t prepare_lb_stream_batch(lbib_precision prec, int npt, bool walls, int* grid);
 cudaError_t launch_lb_stream_batch(lbib_precision prec, int npt, bool walls, int grid, const LbBatch& b,
                                    cudaStream_t s);
+// walls: 0 periodic, 1 bounce-back (bb_* the moving-wall terms), 2 Zou-He (uw_* the wall
+// velocities; the unknown populations of the wall rows rebuilt without a force)
 cudaError_t launch_stream_out(lbib_precision prec, const void* src, double* out, int nx, int ny,
-                              bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s);
+                              int walls, float inv_scale, double bb_bot, double bb_top, double uw_bot,
+                              double uw_top, cudaStream_t s);
 cudaError_t launch_stream_in(lbib_precision prec, const double* in, void* dst, int nx, int ny,
                              bool walls, float inv_scale, double bb_bot, double bb_top, cudaStream_t s);
 cudaError_t launch_init_rest_walls(lbib_precision prec, void* dst, int nx, int ny, double bb_bot, double bb_top,

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "liblbib.so")
 # enums (mirror include/lbib.h)
 LBIB_OK, LBIB_E_INVALID, LBIB_E_CUDA, LBIB_E_OOM, LBIB_E_TIMEOUT, LBIB_E_NONFINITE, LBIB_E_STATE = range(7)
 LBIB_F64, LBIB_F32, LBIB_F32_STORE_F16, LBIB_F32_STORE_BF16 = range(4)
-LBIB_WALLS_NONE, LBIB_WALLS_Y_BOUNCEBACK = 0, 1
+LBIB_WALLS_NONE, LBIB_WALLS_Y_BOUNCEBACK, LBIB_WALLS_ZOU_HE = 0, 1, 2
 LBIB_INIT_REST, LBIB_INIT_POISEUILLE, LBIB_INIT_COUETTE = 0, 1, 2
 LBIB_MEMBRANE_KINEMATIC, LBIB_MEMBRANE_RIGID_PROJECTED = 0, 1
 LBIB_MEMBRANE_DYNAMIC, LBIB_MEMBRANE_DYNAMIC_RIGID = 2, 3

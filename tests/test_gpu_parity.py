@@ -166,10 +166,9 @@ def test_forms_agree_bitwise_capillary_640x160():
 
 
 def test_default_form_follows_lattice_size():
-    from paper_1907_00080_gb300.profile_case import probe_workload
     small = sim_of(inputs.capsule_128x32("f32"))
     assert small.tiling[1] > 0
-    big = sim_of(probe_workload(2048, 1024, "f32"))
+    big = sim_of(inputs.probe_lattice(2048, 1024, "f32"))
     assert big.tiling == (2, 0)
     big.step(2)
     _, ux, _ = big.fields()
