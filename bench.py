@@ -601,16 +601,18 @@ def hbm_probe(lbib, torch, stream, precision, pk, pk_kind, traffic):
 
 def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
     """Precision form: the fine capillary (2000 x 667, 4 red cells x 1700 + 3 rigid
-    carriers x 210 markers) with populations stored in FP32, FP16 and BF16
-    (shifted: d_i 2^k) against the FP64 run from the same inputs.  Errors after
-    each checkpoint (time steps): velocity L2 and Linf relative to the FP64
-    field, marker Linf in lattice units, bond-count difference; throughput over
-    `timed` further steps (CUDA events on the stream)."""
+    carriers x 210 markers released 1 lu from a wall, the paper's bond cut-off
+    y_cr = 1.67 lu, so that bonds form) with populations stored in FP32, FP16 and
+    BF16 (shifted: d_i 2^k) against the FP64 run from the same inputs.  Errors
+    after each checkpoint (time steps): velocity L2 and Linf relative to the
+    FP64 field, marker Linf in lattice units, bond count and the ligands whose
+    bond differs from the FP64 run's; throughput over `timed` further steps
+    (CUDA events on the stream)."""
     from paper_1907_00080_gb300 import inputs
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
     res, ref = {}, {}
     for prec in ("f64", "f32", "f16", "bf16"):
-        wl = inputs.fine_capillary_2000x667(prec)
+        wl = inputs.fine_capillary_adhering(prec)
         sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
         r = {"tiling": list(sim.tiling), "storage_scale_exponent": int(lbib.lbib_storage_scale_exponent(sim.ctx))}
         done = 0
@@ -621,18 +623,20 @@ def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
                 sim.sync()
                 _, ux, uy = sim.fields()
                 x = sim.markers()
-                nb = int((sim.bonds() >= 0).sum())
+                bl = sim.bonds()
+                nb = int((bl >= 0).sum())
                 f = sim.populations()
                 e = {"max_abs_deviation": float(np.max(np.abs(f - w))), "bonds": nb}
                 if prec == "f64":
-                    ref[cp] = (ux, uy, x, nb)
+                    ref[cp] = (ux, uy, x, nb, bl)
                 else:
                     rx = ref[cp]
                     du = np.hypot(ux - rx[0], uy - rx[1])
                     um = np.hypot(rx[0], rx[1])
                     e.update(u_err_linf=float(du.max() / um.max()),
                              u_err_l2=float(np.sqrt((du ** 2).sum() / (um ** 2).sum())),
-                             marker_err_linf_lu=float(np.max(np.abs(x - rx[2]))), bond_count_diff=nb - rx[3])
+                             marker_err_linf_lu=float(np.max(np.abs(x - rx[2]))), bond_count_diff=nb - rx[3],
+                             ligands_with_other_bond=int((bl != rx[4]).sum()))
                 r["after_%d_steps" % cp] = e
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -654,7 +658,8 @@ def precision_forms(lbib, torch, stream, checkpoints=(1000, 10000), timed=2000):
     base = res["f32"]["mlups"]
     for prec in ("f16", "bf16"):
         res[prec]["speedup_vs_f32"] = res[prec]["mlups"] / base
-    return {"workload": "fine capillary 2000x667 (dx = 15 nm), 4 RBC x 1700 + 3 rigid carriers x 210 markers",
+    return {"workload": "fine capillary 2000x667 (dx = 15 nm), 4 RBC x 1700 + 3 rigid carriers x 210 markers "
+                        "released 1 lu from a wall, bond cut-off y_cr = 1.67 lu",
             "checkpoints": list(checkpoints), "timed_steps": timed, "results": res}
 
 

@@ -257,7 +257,7 @@ def dynamic_carriers_128x48(precision="f64", bonds="stress") -> Workload:
 def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carriers=4,
               carrier_radius=8.0, carrier_markers=50, ca_carrier=(0.0, 1e-2), sigma=1.0,
               re=1e-2, seed=0, precision="f32", steps=200000, name=None,
-              bonds="default", release_y=None, carrier_model="kinematic") -> Workload:
+              bonds="default", release_y=None, carrier_model="kinematic", wall_gap=2.0) -> Workload:
     """Coarse capillary: 10x40 um at dx = 62.5 nm is a 160x640 lattice; 8
     biconcave red cells (8 um major axis -> alpha = 64 lu, 200 markers each),
     4 carriers of 1 um diameter (radius 8 lu, 50 markers), alternating rigid
@@ -278,7 +278,7 @@ def capillary(nx=640, ny=160, n_rbc=8, rbc_alpha=64.0, rbc_markers=200, n_carrie
     y_range = None
     if release_y is not None:
         y_range = [(-1e9, 1e9)] * n_rbc + [(y - 1e-6, y + 1e-6) for y in release_y]
-    placed = place_membranes(shapes, nx, ny, rng, y_range=y_range)
+    placed = place_membranes(shapes, nx, ny, rng, y_range=y_range, wall_gap=wall_gap)
     mems = []
     for k in range(n_rbc):
         mems.append(Membrane(xy=placed[k], ks=ks_rbc, kb=0.0, ka=1.0, kind=0))
@@ -321,19 +321,29 @@ def coarse_capillary_640x160(precision="f32", seed=0, steps=200000, carrier_mode
 
 
 def fine_capillary_2000x667(precision="f32", sigma=1.0, carriers="rigid", seed=0, steps=20000,
-                            bonds="default") -> Workload:
+                            bonds="default", release_y=None, wall_gap=2.0) -> Workload:
     """Fine mesh: 10 x 30 um at dx = 15 nm is a 667 x 2000 lattice; 4 red cells
     (8 um major axis -> alpha = 266.7 lu, 1700 markers each, about 19 % 2-D
     haematocrit), 3 carriers of 1 um diameter (radius 33.3 lu, 210 markers,
     105 ligands), all rigid (Ca = 0) or all soft (Ca = 1e-2), receptors on both
     walls, sigma in {0.5, 1, 2}.  bonds="physical" uses the paper's cut-off
-    y_cr = 25 nm = 1.67 lu, which this mesh resolves."""
+    y_cr = 25 nm = 1.67 lu, which this mesh resolves.  release_y: the
+    carriers' centre heights (3 values), else random."""
     nx, ny = 2000, 667
     ca = 0.0 if carriers == "rigid" else 1e-2
     return capillary(nx=nx, ny=ny, n_rbc=4, rbc_alpha=266.7, rbc_markers=1700, n_carriers=3,
                      carrier_radius=33.3, carrier_markers=210, ca_carrier=(ca,), sigma=sigma,
-                     seed=seed, precision=precision, steps=steps, bonds=bonds,
-                     name="fine_capillary_2000x667_%s_sigma%g" % (carriers, sigma))
+                     seed=seed, precision=precision, steps=steps, bonds=bonds, release_y=release_y,
+                     wall_gap=wall_gap, name="fine_capillary_2000x667_%s_sigma%g" % (carriers, sigma))
+
+
+def fine_capillary_adhering(precision="f32", sigma=1.0, carriers="rigid", seed=0) -> Workload:
+    """The fine capillary with the paper's bond cut-off (y_cr = 1.67 lu) and
+    its three carriers released 1 lu from a wall (two at the lower wall, one at
+    the upper), so that bonds form from the first steps."""
+    r, ny, gap = 33.3, 667, 1.0
+    return fine_capillary_2000x667(precision, sigma=sigma, carriers=carriers, seed=seed, bonds="physical",
+                                   release_y=(-0.5 + r + gap, -0.5 + r + gap, ny - 0.5 - r - gap), wall_gap=0.9)
 
 
 def adjoint_capillary_320x160(ks=None, kb=None, sigma_lu=None, release_y=8.5, seed=0, precision="f64",

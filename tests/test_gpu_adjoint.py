@@ -369,3 +369,28 @@ def test_derivatives_match_the_oracle_tangent():
         for k in range(4):
             assert abs(jac_a[i, k] - jac_o[i, k]) <= 1e-8 * abs(jac_o[i, k]) + 1e-11 * np.abs(jac_o[i]).max(), \
                 (i, sensitivity.PARAMS[k], jac_a[i, k], jac_o[i, k])
+
+
+def test_sensitivity_case_fp32_forward_5000_steps_matches_central_differences():
+    """The differentiation form as specified: the 320 x 160 sensitivity case,
+    FP32 forward run over 5000 steps with checkpoints every 250, FP64 adjoint
+    and gradient accumulation.  All eight derivatives dJ_i/dp_k against central
+    differences of the FP64 solver with h = 1e-4 (relative for k_s, k_b and
+    sigma, lattice units for the release height), along the same bond history,
+    within 1e-3 relative (plus 1e-6 of the row's largest entry)."""
+    p0 = sensitivity.default_params()
+    steps = 5000
+    J, jac, bonds = sensitivity.adjoint_jacobian(p0, steps, checkpoint_every=250, precision="f32")
+    assert (bonds >= 0).sum() > 0
+    for k in range(4):
+        h = 1e-4 if k == 3 else 1e-4 * abs(p0[k])
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        Jp, bp = sensitivity.run(pp, steps)
+        Jm, bm = sensitivity.run(pm, steps)
+        assert np.array_equal(bp, bonds) and np.array_equal(bm, bonds), sensitivity.PARAMS[k]
+        fd = (Jp - Jm) / (2 * h)
+        for i in range(2):
+            tol = 1e-3 * abs(fd[i]) + 1e-6 * np.abs(jac[i]).max()
+            assert abs(jac[i, k] - fd[i]) <= tol, (sensitivity.PARAMS[k], i, jac[i, k], fd[i])

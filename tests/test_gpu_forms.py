@@ -89,3 +89,34 @@ def test_fp16_scale_keeps_headroom(fine_runs):
     scaled = dmax * 2.0 ** r["k"]
     assert 2 ** 10 < scaled < 2 ** 14
     assert np.all(np.isfinite(r["f"]))
+
+
+@pytest.fixture(scope="module")
+def adhering_runs():
+    """1000 steps of the fine capillary with its carriers released 1 lu from a
+    wall and the paper's bond cut-off, in every storage form."""
+    from paper_1907_00080_gb300 import lbib
+    out = {}
+    for prec in ("f64", "f32", "f16", "bf16"):
+        s = lbib.Simulation(inputs.fine_capillary_adhering(prec))
+        s.step(1000)
+        out[prec] = dict(x=s.markers(), bonds=s.bonds())
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_storage_forms_keep_the_bonds(adhering_runs, prec):
+    """Bonds form in 1000 steps; FP32 storage keeps the FP64 run's bond set
+    (its bond decisions fall back to FP64 near ties), the 16-bit forms differ
+    from it on at most 5 % of the bonded ligands (measured: see the bench's
+    precision form)."""
+    ref, got = adhering_runs["f64"], adhering_runs[prec]
+    nb = int((ref["bonds"] >= 0).sum())
+    assert nb >= 10
+    diff = int((got["bonds"] != ref["bonds"]).sum())
+    print("bonds", nb, "ligands with another bond", diff, "marker err", np.max(np.abs(got["x"] - ref["x"])))
+    if prec == "f32":
+        assert diff == 0
+    else:
+        assert diff <= 0.05 * nb
