@@ -54,6 +54,7 @@ struct Geom {
     static constexpr int SMEM = kStages * STAGE_BYTES;
     static_assert(ROW_BYTES % 16 == 0, "16-byte aligned stage rows");
     static_assert(NPT <= H, "a thread's nodes never straddle the end of a row");
+    static_assert(W / 32 <= 64, "the tile flags of a segment fit two 32-bit masks");
 };
 
 template <typename T, int V>
@@ -188,18 +189,17 @@ __device__ __forceinline__ void fetch_flags(const Items& it, long long item, int
         }
     }
 }
-template <int W>
-__device__ __forceinline__ void keep_flags(const FlagRegs& r, int lane, int* fl, int* fo) {
-    constexpr int NF = W / 32;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int q = lane + 32 * h;
-        if (q < NF) {
-            fl[q] = r.f[h];
-            fo[q] = r.o[h];
-        }
-    }
+// the whole warp: the item's flags as bit masks (tile q: bit q % 32 of word
+// q / 32), written by lane 0 into the stage's slot {flags 0-31, 32-63,
+// other parity's 0-31, 32-63}
+__device__ __forceinline__ void keep_flags(const FlagRegs& r, int lane, uint4* slot) {
+    const unsigned f0 = __ballot_sync(0xffffffffu, r.f[0] != 0), f1 = __ballot_sync(0xffffffffu, r.f[1] != 0);
+    const unsigned o0 = __ballot_sync(0xffffffffu, r.o[0] != 0), o1 = __ballot_sync(0xffffffffu, r.o[1] != 0);
+    if (lane == 0) *slot = make_uint4(f0, f1, o0, o1);
 }
+// tile q's flag and other-parity flag from a stage's masks
+__device__ __forceinline__ int flag_of(const uint4& m, int q) { return ((q < 32 ? m.x : m.y) >> (q & 31)) & 1; }
+__device__ __forceinline__ int flag_other_of(const uint4& m, int q) { return ((q < 32 ? m.z : m.w) >> (q & 31)) & 1; }
 
 // Stage the nine source rows of `item` (plane i row y - e_iy, or plane opp(i)
 // row y at a wall; W nodes and a 16-byte halo each side, the periodic ends by
@@ -332,11 +332,11 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
 template <typename S, int NPT, bool WALLS, typename Items>
 __device__ __forceinline__ void stream_ws(const Items& it) {
     using Gm = Geom<S, NPT>;
-    constexpr int W = Gm::W, NF = W / 32;
+    constexpr int W = Gm::W;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kStages];
     __shared__ __align__(8) unsigned long long empty[kStages];
-    __shared__ int s_fl[kStages][NF], s_fo[kStages][NF];
+    __shared__ uint4 s_fm[kStages];  // tile-flag masks of each stage's item (see keep_flags)
     __shared__ int s_last_issued[kStages];
     __shared__ volatile int s_abort;
 
@@ -379,7 +379,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
             stop = __shfl_sync(0xffffffffu, stop, 0);
             if (stop) break;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            keep_flags<W>(r0, lane, s_fl[stage], s_fo[stage]);
+            keep_flags(r0, lane, &s_fm[stage]);
             it.stage_args(item, stage, lane);
             __syncwarp();
             const LbArgs& A = it.staged(stage);
@@ -405,7 +405,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
             const int j0 = tid * NPT;
             if (ok && j0 < wlen) {
                 const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
-                consume<S, NPT, WALLS>(A, p, sp, j0, s_fl[stage][j0 >> 5], s_fo[stage][j0 >> 5]);
+                consume<S, NPT, WALLS>(A, p, sp, j0, flag_of(s_fm[stage], j0 >> 5), flag_other_of(s_fm[stage], j0 >> 5));
             }
             // the consumer warps leave the segment together (named barrier 1):
             // their stores go out as one burst per segment; one arrival frees the stage
@@ -444,10 +444,10 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
 template <typename S, int NPT, bool WALLS, typename Items>
 __device__ __forceinline__ void stream_bar(const Items& it) {
     using Gm = Geom<S, NPT>;
-    constexpr int W = Gm::W, NF = W / 32;
+    constexpr int W = Gm::W;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) unsigned long long bars[kStages];
-    __shared__ int s_fl[kStages][NF], s_fo[kStages][NF];
+    __shared__ uint4 s_fm[kStages];  // tile-flag masks of each stage's item (see keep_flags)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long n_items = it.count();
@@ -482,7 +482,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         for (int k = 0; k < kStages && k < my_n; ++k) {
             FlagRegs r;
             fetch_flags<W>(it, first + (long long)k * stride, lane, r);
-            keep_flags<W>(r, lane, s_fl[k], s_fo[k]);
+            keep_flags(r, lane, &s_fm[k]);
             issue(k);
         }
     }
@@ -504,13 +504,13 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         const int j0 = tid * NPT;
         if (j0 < wlen) {
             const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
-            consume<S, NPT, WALLS>(A, p, sp, j0, s_fl[stage][j0 >> 5], s_fo[stage][j0 >> 5]);
+            consume<S, NPT, WALLS>(A, p, sp, j0, flag_of(s_fm[stage], j0 >> 5), flag_other_of(s_fm[stage], j0 >> 5));
         }
         // every thread is done with this stage (and every wait ended) before it is refilled
         bad = __syncthreads_or(!ok) != 0;
         if (bad) break;
         if (warp == 0 && k + kStages < my_n) {
-            keep_flags<W>(nf, lane, s_fl[stage], s_fo[stage]);
+            keep_flags(nf, lane, &s_fm[stage]);
             issue(k + kStages);
         }
     }
@@ -525,8 +525,10 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
 }
 
 // ---------------------------------------------------------------- kernels
+// (three CTAs per SM where their stages fit in shared memory: registers for
+// three 288-thread CTAs)
 template <typename S, int NPT, bool WALLS>
-__global__ void __launch_bounds__(kBlock) k_lb_stream_ws(const LbArgs a) {
+__global__ void __launch_bounds__(kBlock, 3 * Geom<S, NPT>::SMEM <= 220 * 1024 ? 3 : 1) k_lb_stream_ws(const LbArgs a) {
     stream_ws<S, NPT, WALLS>(OneLattice<S, NPT>(a));
 }
 template <typename S, int NPT, bool WALLS>
