@@ -423,6 +423,26 @@ void lbib_adjoint_destroy(lbib_adjoint* adj);
  * Errors: LBIB_E_INVALID (sizes, mismatched slabs, membranes), LBIB_E_STATE
  * (slabs at different steps, a poisoned slab), LBIB_E_CUDA. */
 typedef struct lbib_slabs lbib_slabs;
+
+/* Slabs in different processes (one slab per rank, e.g. one per GPU).  The
+ * same decomposition with the exchange done by the caller: after every step
+ * of its slab, a rank sends the faces that leave it and writes the faces that
+ * enter it, then steps again.
+ * lbib_slab_face: out = 1 copies the face that leaves `ctx` on `side` from its
+ *   current post-collision buffer: side 0 (left) the first interior column's
+ *   populations 3, 6, 7 (they stream to the left neighbour's ghost column
+ *   W + 1), side 1 (right) the last interior column's populations 1, 5, 8
+ *   (to the right neighbour's ghost column 0).  out = 0 writes the face that
+ *   enters on `side`: side 0 the ghost column 0's populations 1, 5, 8 (from
+ *   the left neighbour's right face), side 1 the ghost column W + 1's
+ *   populations 3, 6, 7 (from the right neighbour's left face).  buf holds
+ *   3 x NY stored elements ([3][NY], the context's storage type, see
+ *   lbib_storage_bytes): host memory (on_device = 0; the call synchronises
+ *   the stream) or device memory (on_device = 1; enqueued).  Lattice-only
+ *   contexts.  Errors: LBIB_E_INVALID, LBIB_E_CUDA.
+ * lbib_storage_bytes: bytes per stored population (8, 4 or 2). */
+lbib_status lbib_slab_face(lbib_ctx* ctx, int32_t side, int32_t out, void* buf, int32_t on_device);
+int32_t lbib_storage_bytes(const lbib_ctx* ctx);
 lbib_status lbib_slabs_create(lbib_ctx* const* slabs, int32_t n, lbib_slabs** out);
 lbib_status lbib_slabs_step(lbib_slabs* group, int64_t n);
 lbib_status lbib_slabs_sync(lbib_slabs* group);

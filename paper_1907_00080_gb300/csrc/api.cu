@@ -733,6 +733,10 @@ static LbArgs lb_args(const lbib_ctx* c, int src, int gpar, int clear_other) {
     l.omega = 1.0 / c->tau;
     l.gx = c->gx;
     l.gy = c->gy;
+    l.omf = (float)l.omega;
+    l.om3f = (float)(3.0 * l.omega);
+    l.gxf = (float)l.gx;
+    l.gyf = (float)l.gy;
     l.inv_scale = c->inv_scale;
     // half-way walls: the moving-wall term of the bounced-back diagonals;
     // Zou-He wall rows: the wall velocities themselves
@@ -2418,4 +2422,37 @@ extern "C" void lbib_slabs_destroy(lbib_slabs* g) {
     if (!g) return;
     if (g->stream) cudaStreamSynchronize(g->stream);
     delete g;
+}
+
+// ------------------------------------------------------------------ slab faces
+// The faces one x-slab exchanges with its neighbours when the neighbours live
+// in other processes (one slab per rank): the caller moves the 3 x NY stored
+// values of each face between ranks after every step.
+extern "C" int32_t lbib_storage_bytes(const lbib_ctx* c) { return c ? (int32_t)c->pop_elem : -1; }
+
+extern "C" lbib_status lbib_slab_face(lbib_ctx* c, int32_t side, int32_t out, void* buf, int32_t on_device) {
+    if (!c || !buf || (side != 0 && side != 1) || (out != 0 && out != 1)) return LBIB_E_INVALID;
+    if (c->nmem > 0) return fail(c, LBIB_E_INVALID, "slabs carry the lattice only (no membranes)");
+    if (c->nx < 3) return fail(c, LBIB_E_INVALID, "a slab needs at least one interior column");
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    // leaving: first interior column (3, 6, 7) or last interior column (1, 5, 8);
+    // entering: ghost column 0 (1, 5, 8) or ghost column nx - 1 (3, 6, 7)
+    static const int kPlus[3] = {1, 5, 8}, kMinus[3] = {3, 6, 7};
+    const int* dirs = (side == 0) == (out == 1) ? kMinus : kPlus;
+    const int col = out ? (side == 0 ? 1 : c->nx - 2) : (side == 0 ? 0 : c->nx - 1);
+    const size_t e = c->pop_elem, N = (size_t)c->nx * c->ny;
+    char* base = static_cast<char*>(c->f[c->cur]);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    for (int q = 0; q < 3; ++q) {
+        char* colp = base + ((size_t)dirs[q] * N + (size_t)col) * e;
+        char* bufp = static_cast<char*>(buf) + (size_t)q * c->ny * e;
+        if (out)
+            CK(cudaMemcpy2DAsync(bufp, e, colp, (size_t)c->nx * e, e, c->ny, kind, c->stream));
+        else
+            CK(cudaMemcpy2DAsync(colp, (size_t)c->nx * e, bufp, e, e, c->ny, kind, c->stream));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
 }

@@ -95,6 +95,8 @@ _SIGS = {
     "lbib_slabs_sync": (_I, [_P]),
     "lbib_slabs_last_error": (ctypes.c_char_p, [_P]),
     "lbib_slabs_destroy": (None, [_P]),
+    "lbib_slab_face": (_I, [_P, _I32, _I32, _P, _I32]),
+    "lbib_storage_bytes": (_I32, [_P]),
     "lbib_tangent_create": (_I, [_P, ctypes.POINTER(_P)]),
     "lbib_tangent_seed": (_I, [_P, _DP, _DP, _D, _DP, _DP]),
     "lbib_tangent_step": (_I, [_P, _I64]),
@@ -428,6 +430,15 @@ def lbib_slabs_sync(group):
 def lbib_slabs_destroy(group):
     if group:
         load().lbib_slabs_destroy(group)
+
+
+def lbib_slab_face(ctx, side, out, addr, on_device):
+    """addr: host or device address of 3 x NY stored elements"""
+    _check(ctx, load().lbib_slab_face(ctx, int(side), int(out), _P(int(addr)), int(on_device)))
+
+
+def lbib_storage_bytes(ctx):
+    return int(load().lbib_storage_bytes(ctx))
 
 
 def lbib_tangent_create(ctx):
