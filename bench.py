@@ -373,7 +373,9 @@ def lbib_main(args):
     roofline["share_of_kernel_time"] = top["ms_per_launch"] / sum(k["ms_per_launch"] for k in kernels)
     roofline["note"] = ("dominant kernel of the ensemble's time step (all 64 members in one launch), timed alone "
                         "with CUDA events on a scratch copy; algorithmic bytes = 9 populations read + 9 written "
-                        "per node; traffic from the ncu summary of the same kernel under profiles/")
+                        "per node (frac_with_ib also counts the IB coupling's bytes in the flagged force tiles: "
+                        "force read, velocity written, other parity cleared); traffic from the ncu summary of "
+                        "the same kernel under profiles/")
 
     probe = None
     if not args.no_probe and rank == 0:
@@ -449,6 +451,8 @@ def ensemble_kernels(lbib, torch, stream, wls, tiling, groups, precision, pk, tr
     with torch.cuda.stream(stream):
         scratch.step(4)
         scratch.sync()
+        # the force tiles the fused kernel reads, from the markers' positions
+        flagged = sum(flagged_nodes(wl, m.markers()) for wl, m in zip(wls, scratch.members))
         kms = lbib.lbib_ensemble_profile_kernels(scratch.ens, 200)
     scratch.close()
     alg = [0, 0, 0]
@@ -462,6 +466,13 @@ def ensemble_kernels(lbib, torch, stream, wls, tiling, groups, precision, pk, tr
         out.append({"kernel": name, "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": gbs / pk["hbm_gbs"], "ms_per_launch": ms_k, "algorithmic_bytes_per_launch": b,
                     "traffic": traffic.get("%s:ensemble64_%s:%d,%d" % (key[k], precision, tiling[0], tiling[1]))})
+        if k == 1 and ms_k > 0:
+            # the same kernel with the bytes of its IB coupling counted
+            nodes = sum(wl.nx * wl.ny for wl in wls)
+            ib = flagged * ib_bytes_per_flagged_node(precision)
+            out[-1].update(flagged_tile_fraction=flagged / nodes, ib_bytes_per_launch=ib,
+                           achieved_with_ib=(b + ib) / (ms_k * 1e-3) / 1e9,
+                           frac_with_ib=(b + ib) / (ms_k * 1e-3) / 1e9 / pk["hbm_gbs"])
     return out
 
 
@@ -573,6 +584,37 @@ def alg_bytes_per_launch(precision, wl):
     fused = pop * wl.nx * wl.ny
     advance = nv * (9 * cs + 8 + 18 * cs + 64 + 2 * cs)
     return forces, fused, advance
+
+
+def flagged_nodes(wl, xy):
+    """Nodes of the 32-node force tiles that the spreading of markers at xy
+    (N, 2) flags: the tiles holding a node of some marker's 3 x 3 stencil
+    (origin floor(x + 1/2), rows outside the walls dropped), as the force
+    kernel flags them."""
+    import numpy as np
+    tx = (wl.nx + 31) // 32
+    i0 = np.floor(xy[:, 0] + 0.5).astype(np.int64)
+    j0 = np.floor(xy[:, 1] + 0.5).astype(np.int64)
+    tiles = set()
+    for dy in (-1, 0, 1):
+        jj = j0 + dy
+        ok = (jj >= 0) & (jj < wl.ny) if wl.walls else np.ones_like(jj, bool)
+        jj = jj % wl.ny
+        for dx in (-1, 0, 1):
+            ii = (i0 + dx) % wl.nx
+            tiles.update((jj[ok] * tx + ii[ok] // 32).tolist())
+    # the last tile of a row is short when NX is not a multiple of 32
+    last = wl.nx - 32 * (tx - 1)
+    return sum(last if t % tx == tx - 1 else 32 for t in tiles)
+
+
+def ib_bytes_per_flagged_node(precision):
+    """Fused-kernel bytes of the IB coupling per node of a flagged force tile:
+    the fixed-point force read (16), the velocity written for the
+    interpolation (2 values of the compute type) and the other parity's force
+    cleared (16; its tiles are the previous step's, about as many)."""
+    cs = 8 if precision == "f64" else 4
+    return 16 + 2 * cs + 16
 
 
 def hbm_probe(lbib, torch, stream, precision, pk, pk_kind, traffic):

@@ -128,8 +128,8 @@ __device__ __forceinline__ void lb_tile(const LbArgs& a, int bx, int by) {
     C Gx[VEC], Gy[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-        Gx[k] = C(a.gx);
-        Gy[k] = C(a.gy);
+        Gx[k] = LbConst<C>::gx(a);
+        Gy[k] = LbConst<C>::gy(a);
     }
     bool flagged = false;
     if (HAS_IB) {
@@ -158,9 +158,9 @@ __device__ __forceinline__ void lb_tile(const LbArgs& a, int bx, int by) {
     }
 
     // ---- moments, Guo-corrected velocity, BGK collision with Guo source
-    const C om = C(a.omega);
+    const C om = LbConst<C>::om(a);
     const C pre = C(1) - C(0.5) * om;
-    const C om3 = C(3.0 * a.omega);
+    const C om3 = LbConst<C>::om3(a);
     // Zou-He wall rows: the populations from outside rebuilt (warp-uniform: one row per warp)
     const bool zh = WALLS && a.zou_he && (y == 0 || y == ny - 1);
     C out[9][VEC];

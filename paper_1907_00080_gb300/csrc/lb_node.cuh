@@ -2,7 +2,9 @@
 // force back to the compute type, and the moments + Guo-forced BGK collision
 // of one node in the shifted (deviation) form.  Both forms of the fused kernel
 // (row tiles and the persistent bulk-copy pipeline) call the same functions,
-// so they produce the same bits.
+// so they produce the same bits; for 16-bit storage the persistent form runs
+// the collision on the stored (scaled) values (collide_node_scaled), whose
+// results are the row tiles' times an exact power of two.
 //
 // Paper: Coclite, arXiv 1907.00080, Sec. 2.1 (Eqs. BGK, feq, GaussHermite),
 // Sec. 2.2 (Eqs. forcedBGK, ForcingTerm; rho u = sum f e + G/2).
@@ -67,6 +69,22 @@ template <> __device__ __forceinline__ double zh_wall_u<double>(const LbArgs& a,
     return lower ? a.uw_bot : a.uw_top;
 }
 
+// omega, 3 omega and the body force in the compute type (the FP32 kernels
+// read the copies rounded on the host: no FP64 conversion per node)
+template <typename C> struct LbConst;
+template <> struct LbConst<double> {
+    __device__ static double om(const LbArgs& a) { return a.omega; }
+    __device__ static double om3(const LbArgs& a) { return 3.0 * a.omega; }
+    __device__ static double gx(const LbArgs& a) { return a.gx; }
+    __device__ static double gy(const LbArgs& a) { return a.gy; }
+};
+template <> struct LbConst<float> {
+    __device__ static float om(const LbArgs& a) { return a.omf; }
+    __device__ static float om3(const LbArgs& a) { return a.om3f; }
+    __device__ static float gx(const LbArgs& a) { return a.gxf; }
+    __device__ static float gy(const LbArgs& a) { return a.gyf; }
+};
+
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }  // = 1.0f / x, correctly rounded
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
@@ -114,6 +132,49 @@ __device__ __forceinline__ void collide_node(const C (&f)[9], C Gx, C Gy, C om, 
         const C odd = b * eu + g * eG;
         out[ip[p]] = omc * f[ip[p]] + w * (even + odd);
         out[io[p]] = omc * f[io[p]] + w * (even - odd);
+    }
+}
+
+// The plain collision on the stored values of 16-bit storage, s_i = d_i 2^k,
+// without scaling them first: the moments are summed from s and scaled by
+// 2^-k once, and the relaxation runs on s with the weights scaled by 2^k, so
+// that out_s = out 2^k goes to storage with no multiply.  Scaling by a power
+// of two is exact (every intermediate stays a normal FP32 number: |s| is at
+// most 65504 and at least 2^-24 where non-zero, k at most 40), so each
+// rounded operation gives the unscaled one's result times 2^k and the stored
+// bits equal those of collide_node on d = s 2^-k followed by out 2^k.
+__device__ __forceinline__ void collide_node_scaled(const float (&s)[9], float Gx, float Gy, float om, float pre,
+                                                    float inv, float scl, float (&out)[9], float& rho_o,
+                                                    float& ux_o, float& uy_o) {
+    const float drho = (((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8]) * inv;
+    const float jx = ((s[1] - s[3]) + ((s[5] - s[7]) + (s[8] - s[6]))) * inv;
+    const float jy = ((s[2] - s[4]) + ((s[5] - s[7]) + (s[6] - s[8]))) * inv;
+    const float rho = 1.0f + drho;
+    const float rinv = recip(rho);
+    const float ux = (jx + 0.5f * Gx) * rinv;
+    const float uy = (jy + 0.5f * Gy) * rinv;
+    rho_o = rho;
+    ux_o = ux;
+    uy_o = uy;
+    const float uu = ux * ux + uy * uy;
+    const float uG = ux * Gx + uy * Gy;
+    const float omr = om * rho;
+    const float a = om * drho - 1.5f * omr * uu - 3.0f * pre * uG;
+    const float b = 3.0f * omr, c = 4.5f * omr, g = 3.0f * pre, h = 9.0f * pre;
+    const float omc = 1.0f - om;
+    out[0] = omc * s[0] + (wgt<float>(0) * scl) * a;
+    const float eus[4] = {ux, uy, ux + uy, uy - ux};
+    const float eGs[4] = {Gx, Gy, Gx + Gy, Gy - Gx};
+    constexpr int ip[4] = {1, 2, 5, 6};
+    constexpr int io[4] = {3, 4, 7, 8};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float eu = eus[p], eG = eGs[p];
+        const float w = wgt<float>(ip[p]) * scl;
+        const float even = a + eu * (c * eu + h * eG);
+        const float odd = b * eu + g * eG;
+        out[ip[p]] = omc * s[ip[p]] + w * (even + odd);
+        out[io[p]] = omc * s[io[p]] + w * (even - odd);
     }
 }
 

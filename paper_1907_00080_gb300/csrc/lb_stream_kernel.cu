@@ -243,6 +243,19 @@ __device__ __forceinline__ unsigned stage_bytes(const LbArgs& A, ItemRef p) {
     return 9u * (unsigned)((wlen + 2 * Gm::H) * sizeof(S));
 }
 
+// a staged value in the collision's units: the deviation for FP64 and FP32,
+// the stored (scaled) value for 16-bit storage; and back to storage
+template <typename S>
+__device__ __forceinline__ typename Storage<S>::C pulled(S v, float inv) {
+    if constexpr (sizeof(S) == 2) return Storage<S>::raw(v);
+    else return Storage<S>::load(v, inv);
+}
+template <typename S>
+__device__ __forceinline__ S stored(typename Storage<S>::C c, float scl) {
+    if constexpr (sizeof(S) == 2) return Storage<S>::store_raw(c);
+    else return Storage<S>::store(c, scl);
+}
+
 // One thread's NPT nodes of a staged segment: pull from the stage, add the
 // spread force where its tile is flagged, collide, store; write u where
 // flagged; clear the other parity's force where its tile was flagged (and the
@@ -255,11 +268,15 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
     const int nx = A.nx, ny = A.ny, y = p.y;
     const size_t N = (size_t)nx * ny;
     S* __restrict__ dst = static_cast<S*>(A.dst);
-    const C om = C(A.omega);
+    const C om = LbConst<C>::om(A);
     const C pre = C(1) - C(0.5) * om;
-    const C om3 = C(3.0 * A.omega);
+    const C om3 = LbConst<C>::om3(A);
     const float inv = A.inv_scale;
     const float scl = 1.0f / inv;  // 2^k, exact
+    // 16-bit storage collides on the stored (scaled) values and, with an even
+    // node count per thread, converts value pairs
+    constexpr bool kHalf = sizeof(S) == 2;
+    constexpr bool kPair = kHalf && NPT % 2 == 0;
     // pull: f_i(x) = d*_i(x - e_i), or d*_opp(i)(x) where x - e_i is outside the walls
     C f[9][NPT];
 #pragma unroll
@@ -267,31 +284,48 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
         const bool bb = WALLS && (y - cy(i) < 0 || y - cy(i) >= ny);
         const S* rp = sp + i * Gm::ROW + H + j0;
         const Vec<S, NPT> v = *reinterpret_cast<const Vec<S, NPT>*>(rp);
-        if (bb || cx(i) == 0) {
+        // the thread's NPT staged values of this direction in the compute type
+        // (16-bit storage: the stored values, d 2^k)
+        C t[NPT];
+        if constexpr (kPair) {
 #pragma unroll
-            for (int q = 0; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q], inv);
-            if (bb && cx(i) != 0) {
-                // the momentum of a moving wall (diagonals only)
-                const C t = C(cx(i)) * wall_term<C>(A, cy(i) > 0);
-#pragma unroll
-                for (int q = 0; q < NPT; ++q) f[i][q] += t;
+            for (int q = 0; q < NPT; q += 2) {
+                const float2 u = Storage<S>::load2(*reinterpret_cast<const typename Storage<S>::S2*>(&v.v[q]));
+                t[q] = u.x;
+                t[q + 1] = u.y;
             }
-        } else if (cx(i) == 1) {
-            f[i][0] = Storage<S>::load(rp[-1], inv);
-#pragma unroll
-            for (int q = 1; q < NPT; ++q) f[i][q] = Storage<S>::load(v.v[q - 1], inv);
         } else {
 #pragma unroll
-            for (int q = 0; q < NPT - 1; ++q) f[i][q] = Storage<S>::load(v.v[q + 1], inv);
-            f[i][NPT - 1] = Storage<S>::load(rp[NPT], inv);
+            for (int q = 0; q < NPT; ++q) t[q] = pulled<S>(v.v[q], inv);
+        }
+        if (bb || cx(i) == 0) {
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) f[i][q] = t[q];
+            if (bb && cx(i) != 0) {
+                // the momentum of a moving wall (diagonals only; scaled by 2^k
+                // with the stored values: exact)
+                C w = C(cx(i)) * wall_term<C>(A, cy(i) > 0);
+                if constexpr (kHalf) w *= scl;
+#pragma unroll
+                for (int q = 0; q < NPT; ++q) f[i][q] += w;
+            }
+        } else if (cx(i) == 1) {
+            f[i][0] = pulled<S>(rp[-1], inv);
+#pragma unroll
+            for (int q = 1; q < NPT; ++q) f[i][q] = t[q - 1];
+        } else {
+#pragma unroll
+            for (int q = 0; q < NPT - 1; ++q) f[i][q] = t[q + 1];
+            f[i][NPT - 1] = pulled<S>(rp[NPT], inv);
         }
     }
     const size_t node0 = (size_t)y * nx + p.x0 + j0;
     Vec<S, NPT> o[9];
     Vec<C, NPT> pu, pv;
+    C prev[9];  // paired stores: the even node's results wait for the odd one's
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
-        C Gx = C(A.gx), Gy = C(A.gy);
+        C Gx = LbConst<C>::gx(A), Gy = LbConst<C>::gy(A);
         if (flag) {
             const longlong2 g = A.gsum[node0 + q];
             Gx += from_fix<C>(g.x);
@@ -301,10 +335,36 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
 #pragma unroll
         for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
         // Zou-He wall rows: the populations from outside rebuilt
-        if (WALLS && A.zou_he && (y == 0 || y == ny - 1)) zou_he<C>(fq, Gx, Gy, zh_wall_u<C>(A, y == 0), y == 0);
-        collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
+        const bool zh = WALLS && A.zou_he && (y == 0 || y == ny - 1);
+        if constexpr (kHalf) {
+            if (zh) {
+                // on the unscaled deviations, then back to the stored scale (exact)
 #pragma unroll
-        for (int i = 0; i < 9; ++i) o[i].v[q] = Storage<S>::store(out[i], scl);
+                for (int i = 0; i < 9; ++i) fq[i] *= inv;
+                zou_he<C>(fq, Gx, Gy, zh_wall_u<C>(A, y == 0), y == 0);
+                collide_node<C>(fq, Gx, Gy, om, pre, out, rho, pu.v[q], pv.v[q]);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out[i] *= scl;
+            } else {
+                collide_node_scaled(fq, Gx, Gy, om, pre, inv, scl, out, rho, pu.v[q], pv.v[q]);
+            }
+        } else {
+            if (zh) zou_he<C>(fq, Gx, Gy, zh_wall_u<C>(A, y == 0), y == 0);
+            collide<S>(fq, Gx, Gy, om, pre, om3, out, rho, pu.v[q], pv.v[q]);
+        }
+        if constexpr (kPair) {
+            if (q & 1) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    *reinterpret_cast<typename Storage<S>::S2*>(&o[i].v[q - 1]) = Storage<S>::store2(prev[i], out[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) prev[i] = out[i];
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) o[i].v[q] = stored<S>(out[i], scl);
+        }
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];

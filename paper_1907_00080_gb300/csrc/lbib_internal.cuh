@@ -60,15 +60,29 @@ template <> struct Storage<float> {
     __device__ static float load(float s, float) { return s; }
     __device__ static float store(float d, float) { return d; }
 };
+// 16-bit storage also converts the stored values as they are (raw, store_raw:
+// for the collision on the scaled values) and in pairs (two neighbouring
+// nodes' values of one direction in one step; the pair conversions round each
+// value exactly as the single ones do)
 template <> struct Storage<__half> {
     using C = float;
+    using S2 = __half2;
     __device__ static float load(__half s, float inv) { return __half2float(s) * inv; }
     __device__ static __half store(float d, float scale) { return __float2half_rn(d * scale); }
+    __device__ static float raw(__half s) { return __half2float(s); }
+    __device__ static __half store_raw(float s) { return __float2half_rn(s); }
+    __device__ static float2 load2(__half2 s) { return __half22float2(s); }
+    __device__ static __half2 store2(float a, float b) { return __floats2half2_rn(a, b); }
 };
 template <> struct Storage<__nv_bfloat16> {
     using C = float;
+    using S2 = __nv_bfloat162;
     __device__ static float load(__nv_bfloat16 s, float inv) { return __bfloat162float(s) * inv; }
     __device__ static __nv_bfloat16 store(float d, float scale) { return __float2bfloat16_rn(d * scale); }
+    __device__ static float raw(__nv_bfloat16 s) { return __bfloat162float(s); }
+    __device__ static __nv_bfloat16 store_raw(float s) { return __float2bfloat16_rn(s); }
+    __device__ static float2 load2(__nv_bfloat162 s) { return __bfloat1622float2(s); }
+    __device__ static __nv_bfloat162 store2(float a, float b) { return __floats2bfloat162_rn(a, b); }
 };
 
 // ---------------------------------------------------------------- kernel args
@@ -96,6 +110,8 @@ struct LbArgs {
     int nx, ny;
     double omega;          // 1/tau
     double gx, gy;         // body force
+    float omf, om3f;       // omega and 3 omega rounded to FP32 (no FP64 conversion in the FP32 kernels)
+    float gxf, gyf;        // the body force rounded to FP32
     float inv_scale;       // 2^-k for 16-bit storage, 1 otherwise
     double bb_bot, bb_top; // moving walls: 6 w_d u_w (w_d = 1/36) of the lower / upper wall; a
                            // diagonal population bounced back there gains cx(i) times it
