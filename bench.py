@@ -377,9 +377,11 @@ def lbib_main(args):
                         "force read, velocity written, other parity cleared); traffic from the ncu summary of "
                         "the same kernel under profiles/")
 
-    probe = None
+    probe = probe16 = None
     if not args.no_probe and rank == 0:
         probe = hbm_probe(lbib, torch, stream, args.precision, pk, pk_kind, traffic)
+        # the FP16-storage form of the same probe (36 B/node; producer-warp schedule, 4 nodes per thread)
+        probe16 = hbm_probe(lbib, torch, stream, "f16", pk, pk_kind, traffic, tiling=(4, 0))
 
     c2 = None
     if not args.no_c2 and rank == 0:
@@ -417,6 +419,7 @@ def lbib_main(args):
             "roofline": roofline,
             "roofline_kernels": kernels,
             "roofline_hbm_probe": probe,
+            "roofline_hbm_probe_f16": probe16,
             "capillary_640x160": c2,
             "forms": forms,
             "cpu_baseline": cpu,
@@ -617,13 +620,13 @@ def ib_bytes_per_flagged_node(precision):
     return 16 + 2 * cs + 16
 
 
-def hbm_probe(lbib, torch, stream, precision, pk, pk_kind, traffic):
+def hbm_probe(lbib, torch, stream, precision, pk, pk_kind, traffic, tiling=None):
     """Fused kernel on an 8192 x 2048 lattice (1.2 GB of FP32 populations per
     buffer, far above L2) with the capillary's marker density scaled up."""
     from paper_1907_00080_gb300 import inputs
     nx, ny = 8192, 2048
     wl = inputs.probe_lattice(nx, ny, precision)  # 256 soft carriers of 50 markers
-    sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream)
+    sim = lbib.Simulation(wl, cuda_stream=stream.cuda_stream, tiling=tiling)
     vec, ty = sim.tiling
     with torch.cuda.stream(stream):
         sim.step(2)
