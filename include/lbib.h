@@ -103,7 +103,11 @@ typedef enum {
 } lbib_kind;
 
 typedef struct {
-    int32_t nx, ny;          /* lattice size; nx, ny >= 4                       */
+    int32_t nx, ny;          /* lattice size; nx, ny >= 4.  Any nx for FP64 and
+                                FP32 (row tiles take odd nx; the persistent form
+                                needs 16-byte rows: nx a multiple of 2 in FP64,
+                                4 in FP32, 8 in 16-bit storage, else the default
+                                tiling is row tiles); even nx for 16-bit storage */
     lbib_precision prec;
     lbib_init init;
 } lbib_lattice;
@@ -127,8 +131,8 @@ typedef struct {
  * body_force: uniform G_body (2 doubles) added to the spread IB force.
  * cuda_stream: a cudaStream_t to enqueue on, or NULL for a library-owned
  * stream.  Allocates the two population buffers (9 NX NY elements each).
- * Errors: LBIB_E_INVALID (sizes, tau <= 1/2, POISEUILLE without walls),
- * LBIB_E_OOM, LBIB_E_CUDA. */
+ * Errors: LBIB_E_INVALID (sizes, odd nx with 16-bit storage, tau <= 1/2,
+ * POISEUILLE without walls), LBIB_E_OOM, LBIB_E_CUDA. */
 lbib_status lbib_create(const lbib_lattice* lattice, double tau, const double body_force[2],
                         lbib_walls walls, void* cuda_stream, lbib_ctx** out);
 

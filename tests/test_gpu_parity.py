@@ -45,10 +45,8 @@ def assert_markers(prec, got, ref):
 # ---------------------------------------------------------------- lattice only
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("walls", [1, 0])
-@pytest.mark.parametrize("nx,ny", [(200, 37), (64, 6), (8, 5), (130, 16)])
+@pytest.mark.parametrize("nx,ny", [(200, 37), (64, 6), (8, 5), (130, 16), (201, 9), (33, 7)])
 def test_random_populations_stream_collide(prec, walls, nx, ny):
-    if prec == "f32" and nx % 2:
-        pytest.skip("odd nx not used in fp32 runs")
     wl = lattice_only(nx, ny, walls=walls, tau=0.8, g=(1e-5, -2e-6), precision=prec)
     f0 = inputs.random_populations(nx, ny, W9, seed=nx * ny + walls, amp=5e-2)
     s = sim_of(wl)
