@@ -40,7 +40,7 @@ __global__ void k_rest(const MarkerArgs a, void* rest_v, double* A0, double* qa)
         rest[v] = r;
     }
     if (threadIdx.x < 32 * kAreaWarps) {
-        const E A = ring_area_group<C>(a, m, 0, red, 1);
+        const E A = ring_area_group<C>(a, a.mem_off[m], a.mem_n[m], 0, red, 1);
         if (threadIdx.x == 0) {
             const double A0m = etod(A);
             A0[m] = A0m;
@@ -73,6 +73,8 @@ __device__ __forceinline__ void bond_on_element(const MarkerArgs& a, int e, E xa
 }
 
 constexpr int kForceWarps = 10;
+constexpr int kScreenWarps = kForceWarps - 4 - kAreaWarps;  // phase 1: 2 bending, 2 weights, area, screening
+static_assert(kScreenWarps == 2, "two screening warps");
 constexpr int kForceThreads = 32 * kForceWarps;  // threads per force block
 constexpr int kMaxCand = 256;                     // repulsion candidate segments per block
 constexpr int kStageSeg = 48;                     // candidate segments staged in shared memory
@@ -80,10 +82,11 @@ constexpr int kScreenIter = 8;                    // segment boxes per lane load
 
 // One block per work unit (a chunk of up to kChunkV consecutive vertices of one
 // membrane).  The warps split the work of a vertex:
-//   phase 1  warps 0-2  bending geometry of the chunk plus one halo vertex each side
-//            warps 3-4  IB shape functions (MLS / Roma) and stencil origins
-//            warps 5-8  enclosed area of the whole membrane (fixed-order sum)
-//            warp  9    repulsion candidate segments (ascending order)
+//   phase 1  warps 0-1  bending geometry of the chunk plus one halo vertex each side
+//            warps 2-3  IB shape functions (MLS / Roma) and stencil origins
+//            warps 4-7  enclosed area of the whole membrane (fixed-order sum)
+//            warps 8-9  repulsion candidate segments, one half of the segments
+//                       each (ascending order)
 //   phase 2  warps 0-1  stretching, bending, area and bond forces per vertex
 //            warps 2-9  repulsion over (candidate segment, vertex) pairs,
 //                       accumulated per vertex in fixed point (order-free)
@@ -110,7 +113,8 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
     __shared__ C s_F[kChunkV][2];
     __shared__ E red[32 * kAreaWarps];
     __shared__ C s_ca;
-    __shared__ int s_cand[kMaxCand];
+    __shared__ int s_cand[kScreenWarps][kMaxCand];  // each screening warp's hits, ascending
+    __shared__ int s_ncw[kScreenWarps];
     __shared__ int s_ncand;
     // staged candidate segments: box, anchor (first vertex) and the offsets of
     // their vertices from the anchor in the compute type
@@ -127,15 +131,24 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
         load_pos<C>(a, off + k, s_x[p], s_y[p]);
     }
     if (tid < kChunkV) s_rep[tid] = 0ull;
+    // the screening warps fetch this chunk's own segment boxes now (the unit
+    // record carries the membrane's first segment), behind the position loads
+    const int sown0 = u1.z + k0 / kSegV;
+    const int nown = (kn + kSegV - 1) / kSegV;  // <= kChunkV / kSegV <= 32
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), own = o0;
+    if (wid >= 4 + kAreaWarps && a.nmem > 1) {
+        o0 = a.seg_box[sown0];
+        own = lane < nown ? a.seg_box[sown0 + lane] : o0;
+    }
     __syncthreads();
 
     // ---- phase 1
-    if (wid < 3) {
+    if (wid < 2) {
         // theta - theta_0 from the rotation between the rest and the current
         // edge pair, atan2(c d0 - c0 d, d d0 + c c0): no cancellation of two
         // nearly equal angles
         const C kb = par<C>(a.mem_kb[m], float(a.mem_kb[m]));
-        for (int j = tid; j < kn + 2; j += 96) {
+        for (int j = tid; j < kn + 2; j += 64) {
             int k = k0 - 1 + j;
             k = k < 0 ? k + n : (k >= n ? k - n : k);
             const E xL = s_x[j], yL = s_y[j], xv = s_x[j + 1], yv = s_y[j + 1], xR = s_x[j + 2], yR = s_y[j + 2];
@@ -163,12 +176,12 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
             s_nx[j] = nx_;
             s_ny[j] = ny_;
         }
-    } else if (wid < 5) {
+    } else if (wid < 4) {
         // IB shape functions at X^n: nine nearest nodes, Roma weights, MLS
         // (basis 1, dx, dy) re-solved where wall rows drop out.  Node indices are
         // clamped so that a runaway position still stays in range; the advance
         // kernel flags non-finite positions.
-        const int j = tid - 96;
+        const int j = tid - 64;
         if (j < kn) {
             const E xv = s_x[j + 2], yv = s_y[j + 2];
             const C fi0 = fmin(fmax(C(efloor(eaddc(xv, C(0.5)))), C(-1.0e7)), C(1.0e7));
@@ -242,24 +255,26 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
             s_i0[j] = i0w;
             s_j0[j] = j0;
         }
-    } else if (wid < 5 + kAreaWarps) {
+    } else if (wid < 4 + kAreaWarps) {
         // Eq. areaFor with p_ref = 1/3: F_l = c_a (inward normal) l_l
         // c_a = -k_a (1 - A/A_0) p_ref = q (A - A_0), q = k_a p_ref / A_0 from set-up
         const double A0 = a.mem_A0[m], q = a.mem_qa[m];
-        const E A = ring_area_group<C>(a, m, 5, red, 1);
-        if (tid == 32 * 5) s_ca = C(q * (etod(A) - A0));
-    } else if (wid == 9) {
+        // (off, n from the unit record: no dependent load before the ring's)
+        const E A = ring_area_group<C>(a, off, n, 4, red, 1);
+        if (tid == 32 * 4) s_ca = C(q * (etod(A) - A0));
+    } else {
         // Eq. repFor screening, once per block: segments of other membranes whose
         // box comes within d_rep of this chunk's box (the union of its own
-        // segments' boxes), appended in ascending segment order
+        // segments' boxes).  Screening warp sw takes the segments [lo, hi) of
+        // its half and appends its hits in ascending order; the candidate list
+        // is warp 0's hits, then warp 1's: ascending overall
+        const int sw = wid - (4 + kAreaWarps);
+        const int half = (a.nseg + 1) / 2;
+        const int lo = sw == 0 ? 0 : half, hi = sw == 0 ? half : a.nseg;
         int cnt = 0;
         if (a.nmem > 1) {
-            const int sown0 = u1.z + k0 / kSegV;  // the unit record carries the membrane's first segment
-            const int nown = (kn + kSegV - 1) / kSegV;  // <= kChunkV / kSegV <= 32
-            // this chunk's own boxes; the chunk box is formed once the first batch
-            // of candidate boxes is in flight as well
-            const float4 o0 = a.seg_box[sown0];
-            const float4 own = lane < nown ? a.seg_box[sown0 + lane] : o0;
+            // the chunk box (from this chunk's own boxes) is formed once the
+            // first batch of candidate boxes is in flight as well
             float cbx = 0.f, cby = 0.f, chx = 0.f, chy = 0.f;
             auto chunk_box = [&]() {
                 float lo_x = 1e30f, hi_x = -1e30f, lo_y = 1e30f, hi_y = -1e30f;
@@ -286,7 +301,7 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
             const float reach = a.f.d_rep + 2e-3f;
             auto screen = [&](int sg, int mem, const float4& b) {
                 bool hit = false;
-                if (sg < a.nseg && mem != m) {
+                if (sg < hi && mem != m) {
                     const float dx = wrap_half(b.x - cbx, a.f.nx);
                     float dy = b.y - cby;
                     if (!a.walls) dy = wrap_half(dy, a.f.ny);
@@ -294,40 +309,46 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
                 }
                 const unsigned bal = __ballot_sync(kFull, hit);
                 const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                if (hit && pos < kMaxCand) s_cand[pos] = sg;
+                if (hit && pos < kMaxCand) s_cand[sw][pos] = sg;
                 cnt += __popc(bal);
             };
             // batches of 32 kScreenIter segments: every box and owner of a batch in
             // flight at once, then the ordered screen
-            for (int base = 0; base < a.nseg; base += 32 * kScreenIter) {
+            for (int base = lo; base < hi; base += 32 * kScreenIter) {
                 float4 bx[kScreenIter];
                 int bm[kScreenIter];
 #pragma unroll
                 for (int it = 0; it < kScreenIter; ++it) {
                     const int sg = base + 32 * it + lane;
                     bm[it] = m;
-                    if (sg < a.nseg) {
+                    if (sg < hi) {
                         bx[it] = a.seg_box[sg];
                         bm[it] = a.seg_mem[sg];
                     }
                 }
-                if (base == 0) chunk_box();
+                if (base == lo) chunk_box();
 #pragma unroll
                 for (int it = 0; it < kScreenIter; ++it)
-                    if (base + 32 * it < a.nseg) screen(base + 32 * it + lane, bm[it], bx[it]);
+                    if (base + 32 * it < hi) screen(base + 32 * it + lane, bm[it], bx[it]);
             }
-            __syncwarp();
+            if (lane == 0) s_ncw[sw] = cnt;
+            // both screening warps have their counts (named barrier 3)
+            asm volatile("bar.sync 3, %0;" ::"r"(32 * kScreenWarps) : "memory");
+            const int n0 = s_ncw[0], ntot = n0 + s_ncw[1];
             // the first kStageSeg candidates: box, vertex count and first vertex
             // (their positions are staged by the repulsion warps)
-            const int nst = cnt < kStageSeg ? cnt : kStageSeg;
-            for (int ci = lane; ci < nst; ci += 32) {
-                const int sg = s_cand[ci];
+            const int nst = ntot < kStageSeg ? ntot : kStageSeg;
+            for (int ci = tid - 32 * (4 + kAreaWarps); ci < nst; ci += 32 * kScreenWarps) {
+                const int sg = ci < n0 ? s_cand[0][ci] : s_cand[1][ci - n0];
                 s_cbox[ci] = a.seg_box[sg];
                 s_cn[ci] = a.seg_n[sg];
                 s_cv0[ci] = a.seg_v0[sg];
             }
+            cnt = ntot;
+        } else if (lane == 0) {
+            s_ncw[sw] = 0;
         }
-        if (lane == 0) s_ncand = cnt;
+        if (sw == 0 && lane == 0) s_ncand = cnt;
     }
     __syncthreads();
 
@@ -404,7 +425,7 @@ __device__ __forceinline__ void forces_unit(const MarkerArgs& a, int unit) {
         for (int p = tid - 64; p < nscan * kn; p += blockDim.x - 64) {
             const int ci = p / kn, j = p - ci * kn;
             const bool staged = !all_segs && ci < kStageSeg;
-            const int sg = all_segs ? ci : s_cand[ci];
+            const int sg = all_segs ? ci : (ci < s_ncw[0] ? s_cand[0][ci] : s_cand[1][ci - s_ncw[0]]);
             if (all_segs && a.seg_mem[sg] == m) continue;
             const E xv = s_x[j + 2], yv = s_y[j + 2];
             const float hx = float(ehi(xv));
@@ -538,7 +559,7 @@ __global__ void k_seg_boxes(const MarkerArgs a) {
 template <typename C>
 __global__ void k_areas(const MarkerArgs a, double* areas) {
     __shared__ typename Ext<C>::E red[32 * kAreaWarps];
-    const typename Ext<C>::E A = ring_area_group<C>(a, blockIdx.x, 0, red, 1);
+    const typename Ext<C>::E A = ring_area_group<C>(a, a.mem_off[blockIdx.x], a.mem_n[blockIdx.x], 0, red, 1);
     if (threadIdx.x == 0) areas[blockIdx.x] = etod(A);
 }
 

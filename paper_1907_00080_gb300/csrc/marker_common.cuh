@@ -126,15 +126,15 @@ __device__ __forceinline__ EdgeProducts<C> edge_products(E xL, E yL, E xv, E yv,
 // partials are added in warp order), so every caller gets the same bits.  Call
 // from the kAreaWarps consecutive warps starting at `w0` (all their lanes);
 // `red` holds 32 kAreaWarps values; returns the area in every caller after the
-// named barrier `bar` (kAreaWarps * 32 threads).
+// named barrier `bar` (kAreaWarps * 32 threads).  off, n: the membrane's first
+// vertex and vertex count.
 constexpr int kAreaWarps = 4;
 template <typename C>
-__device__ typename Ext<C>::E ring_area_group(const MarkerArgs& a, int m, int w0, typename Ext<C>::E* red,
-                                              int bar) {
+__device__ typename Ext<C>::E ring_area_group(const MarkerArgs& a, int off, int n, int w0,
+                                              typename Ext<C>::E* red, int bar) {
     using E = typename Ext<C>::E;
     const int t = threadIdx.x - 32 * w0;  // 0 .. 32 kAreaWarps - 1
     const int lane = t & 31, w = t >> 5;
-    const int off = a.mem_off[m], n = a.mem_n[m];
     E xr, yr;
     load_pos<C>(a, off, xr, yr);
     E acc = ezero<E>();
