@@ -73,8 +73,9 @@ def autotune(make_sim, precision: str, nx: int, steps: int = 400, reps: int = 2)
 # autotune_ensemble() on a GB300 (3 x 320 time steps per candidate, CUDA
 # events); ensemble of 64 coarse capillaries, NX 512-1008 x NY 160
 ENSEMBLE_TABLE = {
-    # 0.2476 ms per step; (2, 0) x 1: 0.2484, (1, 0) x 2: 0.2554, row tiles (4, 1) x 4: 0.2571, (4, 2) x 4: 0.2586
-    ("f32", 64, 8033280): ((1, 0), 4),
+    # 0.2500 ms per step; (2, 0) x 2: 0.2507, (2, 0) x 4: 0.2519, row tiles (4, 1) x 4: 0.2521,
+    # (1, 0) x 4: 0.2550, (1, 0) x 1: 0.2786
+    ("f32", 64, 8033280): ((2, 0), 1),
 }
 
 

@@ -190,3 +190,29 @@ def test_benchmark_ensemble_takes_its_tuned_shape():
         assert lbib.lbib_step_count(m.ctx) == 20
         assert lbib.lbib_get_tiling(m.ctx) == tuple(tiling)
     ens.close()
+
+
+def test_benchmark_ensemble_members_match_the_oracle():
+    """The full 64-member ensemble (8.03 M nodes, 138,600 markers) in the shape
+    the benchmark times: after 40 steps, the shortest, a middle and the longest
+    member against the oracle at the FP32 bounds (velocity within 1e-5 of the
+    speed scale, markers within 1e-5 lu, bond sets bit-exact)."""
+    from paper_1907_00080_gb300 import lbib, tuning
+    wls = inputs.capillary_ensemble(64, seed=0, precision="f32")
+    (tiling, groups), _ = tuning.ensemble_shape(wls)
+    ens = lbib.Ensemble(wls, tiling=tiling)
+    assert ens.form == 1
+    ens.set_groups(groups)
+    ens.step(40)
+    ens.sync()
+    order = np.argsort([wl.nx for wl in wls])
+    for i in (order[0], order[len(order) // 2], order[-1]):
+        wl, m = wls[i], ens.members[i]
+        r = make_oracle(wl)
+        r.step(40)
+        _, ux, uy = m.fields()
+        _, ux0, uy0 = r.fields()
+        assert vel_err(ux, uy, ux0, uy0) < 1e-5, (wl.name, vel_err(ux, uy, ux0, uy0))
+        assert np.max(np.abs(m.markers() - r.markers())) < 1e-5
+        assert np.array_equal(m.bonds(), r.bonds())
+    ens.close()
