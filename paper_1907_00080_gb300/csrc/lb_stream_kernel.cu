@@ -19,7 +19,8 @@
 //   [x0 - HALO, x0 + W + HALO) of plane i, row y - e_iy   (interior rows)
 //   [x0 - HALO, x0 + W + HALO) of plane opp(i), row y      (half-way bounce-back)
 // The periodic x neighbours at the ends of a row come from separate 16-byte
-// copies of the other end of the row.  The arithmetic per node is
+// copies of the other end of the row (two copies per direction for a
+// segment at one end of its row, three for a segment that is the whole row).  The arithmetic per node is
 // collide_node(), the same as the row-tile kernel's, so both forms give the
 // same bits.  The force tiles are 32 nodes of one row, as in the row-tile
 // form.  The same bodies serve one lattice (arguments in the kernel's
@@ -229,6 +230,16 @@ __device__ __forceinline__ void stage_rows(const LbArgs& A, ItemRef p, uint32_t 
         const uint32_t d = base + i * Gm::ROW_BYTES;
         if (interior) {
             bulk_g2s(d, row + (p.x0 - H), row_bytes, bar);
+        } else if (p.x0 >= H) {
+            // the row's last segment: its left halo and nodes in one copy, the
+            // periodic right halo (the row's first 16 bytes) in another
+            bulk_g2s(d, row + (p.x0 - H), (unsigned)((wlen + H) * sizeof(S)), bar);
+            bulk_g2s(d + (unsigned)((wlen + H) * sizeof(S)), row, 16u, bar);
+        } else if (p.x0 + wlen + H <= nx) {
+            // the row's first segment: the periodic left halo (the row's last
+            // 16 bytes), then its nodes and right halo in one copy
+            bulk_g2s(d, row + (nx - H), 16u, bar);
+            bulk_g2s(d + 16u, row, (unsigned)((wlen + H) * sizeof(S)), bar);
         } else {
             bulk_g2s(d, row + (p.x0 == 0 ? nx - H : p.x0 - H), 16u, bar);
             bulk_g2s(d + 16u, row + p.x0, (unsigned)(wlen * sizeof(S)), bar);
