@@ -18,9 +18,9 @@
 // Staged row of direction i (HALO = one 16-byte chunk on each side):
 //   [x0 - HALO, x0 + W + HALO) of plane i, row y - e_iy   (interior rows)
 //   [x0 - HALO, x0 + W + HALO) of plane opp(i), row y      (half-way bounce-back)
-// The periodic x neighbours at the ends of a row come from separate 16-byte
-// copies of the other end of the row (two copies per direction for a
-// segment at one end of its row, three for a segment that is the whole row).  The arithmetic per node is
+// The periodic x neighbours at the ends of a row come from a separate 16-byte
+// copy of the other end of the row, for the three directions that pull
+// across that end (e_ix = 1 at x = 0, e_ix = -1 at x = NX - 1).  The arithmetic per node is
 // collide_node(), the same as the row-tile kernel's, so both forms give the
 // same bits.  The force tiles are 32 nodes of one row, as in the row-tile
 // form.  The same bodies serve one lattice (arguments in the kernel's
@@ -231,27 +231,36 @@ __device__ __forceinline__ void stage_rows(const LbArgs& A, ItemRef p, uint32_t 
         if (interior) {
             bulk_g2s(d, row + (p.x0 - H), row_bytes, bar);
         } else if (p.x0 >= H) {
-            // the row's last segment: its left halo and nodes in one copy, the
-            // periodic right halo (the row's first 16 bytes) in another
+            // the row's last segment: its left halo and nodes in one copy; the
+            // periodic right halo (the row's first 16 bytes) only for the
+            // directions that pull from it (e_ix = -1)
             bulk_g2s(d, row + (p.x0 - H), (unsigned)((wlen + H) * sizeof(S)), bar);
-            bulk_g2s(d + (unsigned)((wlen + H) * sizeof(S)), row, 16u, bar);
+            if (cx(i) == -1) bulk_g2s(d + (unsigned)((wlen + H) * sizeof(S)), row, 16u, bar);
         } else if (p.x0 + wlen + H <= nx) {
             // the row's first segment: the periodic left halo (the row's last
-            // 16 bytes), then its nodes and right halo in one copy
-            bulk_g2s(d, row + (nx - H), 16u, bar);
+            // 16 bytes) only for e_ix = 1, then its nodes and right halo
+            if (cx(i) == 1) bulk_g2s(d, row + (nx - H), 16u, bar);
             bulk_g2s(d + 16u, row, (unsigned)((wlen + H) * sizeof(S)), bar);
         } else {
-            bulk_g2s(d, row + (p.x0 == 0 ? nx - H : p.x0 - H), 16u, bar);
-            bulk_g2s(d + 16u, row + p.x0, (unsigned)(wlen * sizeof(S)), bar);
-            bulk_g2s(d + 16u + (unsigned)(wlen * sizeof(S)), row + (p.x0 + wlen == nx ? 0 : p.x0 + wlen), 16u, bar);
+            // the whole row in one segment
+            if (cx(i) == 1) bulk_g2s(d, row + (nx - H), 16u, bar);
+            bulk_g2s(d + 16u, row, (unsigned)(wlen * sizeof(S)), bar);
+            if (cx(i) == -1) bulk_g2s(d + 16u + (unsigned)(wlen * sizeof(S)), row, 16u, bar);
         }
     }
 }
+// the bytes stage_rows copies: nine rows of the segment's nodes, with both
+// halos inside the row, one halo at an end of the row plus the periodic halo
+// of the three directions that pull across that end
 template <typename S, int NPT>
 __device__ __forceinline__ unsigned stage_bytes(const LbArgs& A, ItemRef p) {
     using Gm = Geom<S, NPT>;
+    constexpr int H = Gm::H;
     const int wlen = min(Gm::W, A.nx - p.x0);
-    return 9u * (unsigned)((wlen + 2 * Gm::H) * sizeof(S));
+    const bool interior = p.x0 >= H && p.x0 + wlen + H <= A.nx;
+    const bool whole = p.x0 < H && p.x0 + wlen + H > A.nx;
+    const int halos = interior ? 18 : (whole ? 6 : 12);
+    return (unsigned)((9 * wlen + halos * H) * (int)sizeof(S));
 }
 
 // a staged value in the collision's units: the deviation for FP64 and FP32,
