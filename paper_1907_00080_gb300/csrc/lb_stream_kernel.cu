@@ -129,14 +129,19 @@ struct OneLattice {
     int nseg;
     __device__ explicit OneLattice(const LbArgs& a_) : a(a_), nseg((a_.nx + W - 1) / W) {}
     __device__ long long count() const { return (long long)a.ny * nseg; }
+    // (32-bit: the launch refuses work lists of 2^31 items or more)
+    __device__ ItemRef pos(long long item) const {
+        const int it = (int)item, y = it / nseg;
+        return {y, (it - y * nseg) * W};
+    }
     __device__ const LbArgs& locate(long long item, ItemRef& p) const {
-        p = {(int)(item / nseg), (int)(item % nseg) * W};
+        p = pos(item);
         return a;
     }
     // the staging warp (all lanes) prepares stage st for `item`: nothing to copy
     __device__ void stage_args(long long, int, int) const {}
     __device__ const LbArgs& staged(int) const { return a; }
-    __device__ ItemRef staged_pos(long long item, int) const { return {(int)(item / nseg), (int)(item % nseg) * W}; }
+    __device__ ItemRef staged_pos(long long item, int) const { return pos(item); }
 };
 
 // b.off: first item of each member; b.tiles_x: segments per row of each member
@@ -686,6 +691,7 @@ cudaError_t dispatch(bool prepare, bool walls, int grid, int* grid_out, const Lb
     } else {
         items = (long long)a->ny * ((a->nx + Geom<S, NPT>::W - 1) / Geom<S, NPT>::W);
     }
+    if (items >= (1LL << 31)) return cudaErrorInvalidValue;  // item indices are 32-bit in the kernel
     const int g = (int)(items < grid ? items : grid);
     if (g <= 0) return cudaSuccess;
     constexpr int SM = Geom<S, NPT>::SMEM;
