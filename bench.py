@@ -527,9 +527,9 @@ def capillary_line(lbib, torch, stream, precision, pk, traffic, T=1000, steps=5,
 
 def ensemble_e2e(lbib, torch, wls, tiling, groups, stream, T, steps):
     """End to end through the public API with host buffers: per step, every
-    member's populations (FP64) and markers go up from pinned host memory, the
-    ensemble advances T time steps, every member's markers come back (host
-    wall clock)."""
+    member's populations (FP64) and markers go up from pinned host memory
+    (lbib_ensemble_write_state), the ensemble advances T time steps, every
+    member's markers come back (lbib_ensemble_read_markers); host wall clock."""
     ens = lbib.Ensemble(wls, cuda_stream=stream.cuda_stream, tiling=tiling)
     ens.set_groups(groups)
     with torch.cuda.stream(stream):
@@ -546,13 +546,12 @@ def ensemble_e2e(lbib, torch, wls, tiling, groups, stream, T, steps):
             x_out.append(torch.empty((m.nv, 2), dtype=torch.float64, pin_memory=True).numpy())
 
         def one():
-            for m, f, x in zip(ens.members, f_host, x_host):
-                lbib.lbib_write_populations(m.ctx, f)
-                lbib.lbib_write_markers(m.ctx, x, x)
+            # every member's populations and markers up in one call, the
+            # steps, the status check, every member's markers back
+            ens.write_state(f=f_host, xy=x_host)  # X^{n-1} = X^n from the same upload
             ens.step(T)
             ens.sync()
-            for m, xo in zip(ens.members, x_out):
-                lbib.lbib_read_markers(m.ctx, -1, xo)
+            ens.read_markers(x_out)
 
         one()
         torch.cuda.synchronize()
@@ -563,7 +562,7 @@ def ensemble_e2e(lbib, torch, wls, tiling, groups, stream, T, steps):
         dt = time.perf_counter() - t0
     ens.close()
     nodes = sum(wl.nx * wl.ny for wl in wls)
-    h2d = sum(f.nbytes for f in f_host) + 2 * sum(x.nbytes for x in x_host)
+    h2d = sum(f.nbytes for f in f_host) + sum(x.nbytes for x in x_host)
     d2h = sum(x.nbytes for x in x_out)
     return {"value": nodes * T * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps,

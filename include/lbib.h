@@ -300,6 +300,20 @@ lbib_status lbib_diagnostics(lbib_ctx* ctx, double* mass, double* areas);
  * lbib_ensemble_sync: wait for the ensemble's stream and check every member's
  *   device status; call it before reading a member (lbib_ensemble_member
  *   returns the member's context for the lbib_read_* calls).
+ * lbib_ensemble_write_state: every member's state in one call.  f[i]: member
+ *   i's pre-collision populations (9*NY*NX doubles, the layout of
+ *   lbib_write_populations), xy[i] / xy_prev[i]: its marker positions X^n
+ *   and X^{n-1} (as lbib_write_markers; xy_prev NULL or xy_prev[i] NULL means
+ *   X^{n-1} = X^n).  Any of f, xy, or an entry of them may be NULL (that part
+ *   is left as it is).  Host buffers (on_device = 0; pinned memory lets the
+ *   copies run at full speed) or device buffers (populations only;
+ *   on_device = 1).  All copies and conversions go on the ensemble's
+ *   stream, after its pending steps, and the call waits once for them: the
+ *   buffers may be reused on return.  Errors: LBIB_E_INVALID, LBIB_E_STATE
+ *   (a poisoned member), LBIB_E_OOM, LBIB_E_CUDA.
+ * lbib_ensemble_read_markers: every member's marker positions (xy[i]: 2 nv_i
+ *   doubles, host; NULL entries are skipped) after the pending steps, with
+ *   one wait.  Errors: LBIB_E_INVALID, LBIB_E_CUDA.
  */
 typedef struct lbib_ensemble lbib_ensemble;
 lbib_status lbib_ensemble_create(lbib_ctx* const* members, int32_t n, void* cuda_stream, lbib_ensemble** out);
@@ -311,6 +325,9 @@ lbib_status lbib_ensemble_set_groups(lbib_ensemble* ens, int32_t groups);
 int32_t lbib_ensemble_groups(const lbib_ensemble* ens);
 lbib_status lbib_ensemble_profile_kernels(lbib_ensemble* ens, int32_t reps, double* ms_per_launch);
 int32_t lbib_ensemble_launches_per_step(const lbib_ensemble* ens);
+lbib_status lbib_ensemble_write_state(lbib_ensemble* ens, const double* const* f, const double* const* xy,
+                                      const double* const* xy_prev, int32_t on_device);
+lbib_status lbib_ensemble_read_markers(lbib_ensemble* ens, double* const* xy);
 lbib_ctx* lbib_ensemble_member(lbib_ensemble* ens, int32_t i);
 const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
 void lbib_ensemble_destroy(lbib_ensemble* ens);

@@ -971,50 +971,72 @@ extern "C" lbib_status lbib_read_populations(lbib_ctx* c, double* f, int on_devi
     return LBIB_OK;
 }
 
-extern "C" lbib_status lbib_write_populations(lbib_ctx* c, const double* f, int on_device) {
-    if (!c || !f) return LBIB_E_INVALID;
+// the upload of a context's populations, enqueued on stream s (no wait)
+static lbib_status write_populations_on(lbib_ctx* c, const double* f, int on_device, cudaStream_t s) {
     const size_t N = (size_t)c->nx * c->ny;
     lbib_status st;
     const double* in = f;
     if (!on_device) {
         if ((st = ensure_stage(c)) != LBIB_OK) return st;
-        CK(cudaMemcpyAsync(c->stage, f, 9 * N * 8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->stage, f, 9 * N * 8, cudaMemcpyHostToDevice, s));
         in = c->stage;
     }
     // Zou-He walls: the slots the wall rows would stream out through are
     // never pulled; the bounce-back inverse fills them harmlessly
     const bool zh = c->walls == LBIB_WALLS_ZOU_HE;
     CK(launch_stream_in(c->prec, in, c->f[c->cur], c->nx, c->ny, c->walls != LBIB_WALLS_NONE, c->inv_scale,
-                        zh ? 0.0 : bb_term(c->uw_bot), zh ? 0.0 : bb_term(c->uw_top), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+                        zh ? 0.0 : bb_term(c->uw_bot), zh ? 0.0 : bb_term(c->uw_top), s));
     c->fields_valid = false;
     return LBIB_OK;
 }
 
-extern "C" lbib_status lbib_read_markers(lbib_ctx* c, int32_t m, double* xy) {
-    if (!c || !xy || m < -1 || m >= c->nmem) return LBIB_E_INVALID;
+extern "C" lbib_status lbib_write_populations(lbib_ctx* c, const double* f, int on_device) {
+    if (!c || !f) return LBIB_E_INVALID;
+    const lbib_status st = write_populations_on(c, f, on_device, c->stream);
+    if (st != LBIB_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+// the read-back of marker positions, enqueued on stream s (no wait)
+static lbib_status read_markers_on(lbib_ctx* c, int32_t m, double* xy, cudaStream_t s) {
     lbib_status st = finalize(c);
     if (st != LBIB_OK) return st;
     if (c->nv == 0) return LBIB_OK;
     const int off = m < 0 ? 0 : c->h_mem_off[m];
     const int n = m < 0 ? c->nv : c->h_mem_n[m];
-    CK(launch_pos_out(c->prec, c->ma.X, c->xy_stage, c->nv, c->stream));
-    CK(cudaMemcpyAsync(xy, c->xy_stage + 2 * (size_t)off, 16 * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+    CK(launch_pos_out(c->prec, c->ma.X, c->xy_stage, c->nv, s));
+    CK(cudaMemcpyAsync(xy, c->xy_stage + 2 * (size_t)off, 16 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_read_markers(lbib_ctx* c, int32_t m, double* xy) {
+    if (!c || !xy || m < -1 || m >= c->nmem) return LBIB_E_INVALID;
+    const lbib_status st = read_markers_on(c, m, xy, c->stream);
+    if (st != LBIB_OK) return st;
     CK(cudaStreamSynchronize(c->stream));
+    return LBIB_OK;
+}
+
+// the upload of marker positions X^n and X^{n-1}, enqueued on stream s (no wait)
+static lbib_status write_markers_on(lbib_ctx* c, const double* xy, const double* xy_prev, cudaStream_t s) {
+    lbib_status st = finalize(c);
+    if (st != LBIB_OK) return st;
+    if (c->nv == 0) return LBIB_OK;
+    const size_t b = 16 * (size_t)c->nv;
+    CK(cudaMemcpyAsync(c->xy_stage, xy, b, cudaMemcpyHostToDevice, s));
+    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.X, c->nv, s));
+    // X^{n-1} = X^n: the staged copy serves both
+    if (xy_prev && xy_prev != xy) CK(cudaMemcpyAsync(c->xy_stage, xy_prev, b, cudaMemcpyHostToDevice, s));
+    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.Xp, c->nv, s));
+    CK(launch_seg_boxes(c->prec, c->ma, s));
     return LBIB_OK;
 }
 
 extern "C" lbib_status lbib_write_markers(lbib_ctx* c, const double* xy, const double* xy_prev) {
     if (!c || !xy) return LBIB_E_INVALID;
-    lbib_status st = finalize(c);
+    const lbib_status st = write_markers_on(c, xy, xy_prev, c->stream);
     if (st != LBIB_OK) return st;
-    if (c->nv == 0) return LBIB_OK;
-    const size_t b = 16 * (size_t)c->nv;
-    CK(cudaMemcpyAsync(c->xy_stage, xy, b, cudaMemcpyHostToDevice, c->stream));
-    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.X, c->nv, c->stream));
-    CK(cudaMemcpyAsync(c->xy_stage, xy_prev ? xy_prev : xy, b, cudaMemcpyHostToDevice, c->stream));
-    CK(launch_pos_in(c->prec, c->xy_stage, c->ma.Xp, c->nv, c->stream));
-    CK(launch_seg_boxes(c->prec, c->ma, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBIB_OK;
 }
@@ -1559,6 +1581,53 @@ extern "C" lbib_status lbib_ensemble_sync(lbib_ensemble* e) {
 }
 
 extern "C" int32_t lbib_ensemble_size(const lbib_ensemble* e) { return e ? (int32_t)e->m.size() : -1; }
+
+// Every member's state from host (or device) buffers in one call: the copies
+// and conversions of all members are enqueued on the ensemble's stream, after
+// its pending steps, with one wait at the end.
+extern "C" lbib_status lbib_ensemble_write_state(lbib_ensemble* e, const double* const* f,
+                                                 const double* const* xy, const double* const* xy_prev,
+                                                 int32_t on_device) {
+    if (!e || (on_device && xy)) return LBIB_E_INVALID;
+    // the members' own streams may hold work of their own
+    for (lbib_ctx* c : e->m) ECK(cudaStreamSynchronize(c->stream));
+    for (lbib_ctx* c : e->m)
+        if (c->poisoned) return ens_fail(e, LBIB_E_STATE, "a member is poisoned by an earlier device-side failure");
+    // host populations: every member's copy first (back to back on the copy
+    // engine), then the conversions
+    const size_t n = e->m.size();
+    if (f && !on_device) {
+        for (size_t i = 0; i < n; ++i) {
+            lbib_ctx* c = e->m[i];
+            if (!f[i]) continue;
+            const lbib_status st = ensure_stage(c);
+            if (st != LBIB_OK) return ens_fail(e, st, c->err);
+            ECK(cudaMemcpyAsync(c->stage, f[i], 9 * sizeof(double) * (size_t)c->nx * c->ny, cudaMemcpyHostToDevice,
+                                e->stream));
+        }
+    }
+    for (size_t i = 0; i < n; ++i) {
+        lbib_ctx* c = e->m[i];
+        lbib_status st;
+        if (f && f[i] && (st = write_populations_on(c, on_device ? f[i] : c->stage, 1, e->stream)) != LBIB_OK)
+            return ens_fail(e, st, c->err);
+        if (xy && xy[i] && (st = write_markers_on(c, xy[i], xy_prev ? xy_prev[i] : nullptr, e->stream)) != LBIB_OK)
+            return ens_fail(e, st, c->err);
+    }
+    ECK(cudaStreamSynchronize(e->stream));
+    return LBIB_OK;
+}
+
+extern "C" lbib_status lbib_ensemble_read_markers(lbib_ensemble* e, double* const* xy) {
+    if (!e || !xy) return LBIB_E_INVALID;
+    for (size_t i = 0; i < e->m.size(); ++i) {
+        if (!xy[i]) continue;
+        const lbib_status st = read_markers_on(e->m[i], -1, xy[i], e->stream);
+        if (st != LBIB_OK) return ens_fail(e, st, e->m[i]->err);
+    }
+    ECK(cudaStreamSynchronize(e->stream));
+    return LBIB_OK;
+}
 
 extern "C" int32_t lbib_ensemble_form(const lbib_ensemble* e) { return e ? (e->batched ? 1 : 0) : -1; }
 

@@ -81,6 +81,8 @@ _SIGS = {
     "lbib_ensemble_create": (_I, [ctypes.POINTER(_P), _I32, _P, ctypes.POINTER(_P)]),
     "lbib_ensemble_step": (_I, [_P, _I64]),
     "lbib_ensemble_sync": (_I, [_P]),
+    "lbib_ensemble_write_state": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _I32]),
+    "lbib_ensemble_read_markers": (_I, [_P, ctypes.POINTER(_P)]),
     "lbib_ensemble_size": (_I32, [_P]),
     "lbib_ensemble_form": (_I32, [_P]),
     "lbib_ensemble_set_groups": (ctypes.c_int, [_P, _I32]),
@@ -354,6 +356,33 @@ def lbib_ensemble_create(ctxs, cuda_stream=None):
 
 def lbib_ensemble_step(ens, n):
     _echeck(ens, load().lbib_ensemble_step(ens, int(n)))
+
+
+def _ptr_table(arrays, n):
+    """None -> NULL table; else a table of n pointers (None entries -> NULL)"""
+    if arrays is None:
+        return None
+    if len(arrays) != n:
+        raise ValueError("one entry per member")
+    return (_P * n)(*[None if a is None else a.ctypes.data for a in arrays])
+
+
+def lbib_ensemble_write_state(ens, n, f=None, xy=None, xy_prev=None):
+    """f, xy, xy_prev: lists of n C-contiguous float64 host arrays (entries may
+    be None) or None"""
+    for arrs in (f, xy, xy_prev):
+        for a in arrs or ():
+            if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+                raise ValueError("C-contiguous float64 arrays")
+    _echeck(ens, load().lbib_ensemble_write_state(ens, _ptr_table(f, n), _ptr_table(xy, n),
+                                                  _ptr_table(xy_prev, n), 0))
+
+
+def lbib_ensemble_read_markers(ens, xy):
+    for a in xy:
+        if a is not None and (a.dtype != np.float64 or not a.flags.c_contiguous):
+            raise ValueError("C-contiguous float64 arrays")
+    _echeck(ens, load().lbib_ensemble_read_markers(ens, _ptr_table(xy, len(xy))))
 
 
 def lbib_ensemble_sync(ens):
@@ -673,6 +702,15 @@ class Ensemble:
 
     def sync(self):
         lbib_ensemble_sync(self.ens)
+
+    def write_state(self, f=None, xy=None, xy_prev=None):
+        """every member's populations (9, NY, NX) and markers (nv, 2) from host
+        arrays in one call (lists with one entry per member, None to skip)"""
+        lbib_ensemble_write_state(self.ens, len(self.members), f, xy, xy_prev)
+
+    def read_markers(self, out):
+        """every member's markers into the (nv, 2) float64 arrays of `out`"""
+        lbib_ensemble_read_markers(self.ens, out)
 
     def close(self):
         if self.ens:

@@ -216,3 +216,37 @@ def test_benchmark_ensemble_members_match_the_oracle():
         assert np.max(np.abs(m.markers() - r.markers())) < 1e-5
         assert np.array_equal(m.bonds(), r.bonds())
     ens.close()
+
+
+def test_ensemble_state_calls_match_the_member_calls():
+    """lbib_ensemble_write_state / lbib_ensemble_read_markers (all members, one
+    wait) give the same bits as the per-member write and read calls."""
+    from paper_1907_00080_gb300 import lbib
+    wls = small_ensemble(3, "f32", seed=13)
+    runs = []
+    for batched_io in (False, True):
+        ens = lbib.Ensemble(wls, tiling=(1, 0))
+        ens.step(5)
+        ens.sync()
+        f = [np.ascontiguousarray(m.populations() * (1 + 1e-3 * k)) for k, m in enumerate(ens.members)]
+        x = [np.ascontiguousarray(m.markers() + 0.01 * (k + 1)) for k, m in enumerate(ens.members)]
+        if batched_io:
+            ens.write_state(f=f, xy=x, xy_prev=x)
+        else:
+            for m, fk, xk in zip(ens.members, f, x):
+                lbib.lbib_write_populations(m.ctx, fk)
+                lbib.lbib_write_markers(m.ctx, xk, xk)
+        ens.step(7)
+        ens.sync()
+        out = [np.zeros((m.nv, 2)) for m in ens.members]
+        if batched_io:
+            ens.read_markers(out)
+        else:
+            for m, o in zip(ens.members, out):
+                lbib.lbib_read_markers(m.ctx, -1, o)
+        runs.append((out, [m.populations() for m in ens.members]))
+        ens.close()
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(a, b)
