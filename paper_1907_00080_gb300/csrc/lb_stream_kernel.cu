@@ -134,12 +134,18 @@ struct OneLattice {
         const int it = (int)item, y = it / nseg;
         return {y, (it - y * nseg) * W};
     }
-    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
+    __device__ const LbArgs& locate(long long item, ItemRef& p, int& m) const {
         p = pos(item);
+        m = 0;
         return a;
     }
-    // the staging warp (all lanes) prepares stage st for `item`: nothing to copy
-    __device__ void stage_args(long long, int, int) const {}
+    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
+        int m;
+        return locate(item, p, m);
+    }
+    // the staging warp (all lanes) prepares a stage for the item located as
+    // (p, m): nothing to copy
+    __device__ void stage_args(ItemRef, int, int, int) const {}
     __device__ const LbArgs& staged(int) const { return a; }
     __device__ ItemRef staged_pos(long long item, int) const { return pos(item); }
 };
@@ -152,17 +158,21 @@ struct ManyLattices {
     LbArgs* s_args;  // [kStages] in shared memory
     ItemRef* s_pos;  // [kStages]
     __device__ long long count() const { return b.off[b.n]; }
-    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
-        const int m = batch_member(b.off, b.n, (int)item);
+    __device__ const LbArgs& locate(long long item, ItemRef& p, int& m) const {
+        m = batch_member(b.off, b.n, (int)item);
         const int l = (int)item - b.off[m], ns = b.tiles_x[m];
         p = {l / ns, (l % ns) * W};
         return b.a[m];
     }
-    // the staging warp (all lanes) copies the member's arguments, 8-byte
-    // words, and lane 0 the item's position, into stage st's slots
-    __device__ void stage_args(long long item, int st, int lane) const {
-        ItemRef p;
-        const LbArgs& A = locate(item, p);
+    __device__ const LbArgs& locate(long long item, ItemRef& p) const {
+        int m;
+        return locate(item, p, m);
+    }
+    // the staging warp (all lanes) copies the arguments of member m, 8-byte
+    // words, and lane 0 the item's position p, into stage st's slots (the
+    // item was located when its flags were fetched)
+    __device__ void stage_args(ItemRef p, int m, int st, int lane) const {
+        const LbArgs& A = b.a[m];
         constexpr int NW = (int)(sizeof(LbArgs) / 8);
         for (int w = lane; w < NW; w += 32)
             reinterpret_cast<long long*>(&s_args[st])[w] = reinterpret_cast<const long long*>(&A)[w];
@@ -175,15 +185,19 @@ struct ManyLattices {
 // Force-tile flags of one item (segment): W / 32 tiles of 32 nodes, lane q of
 // the fetching warp taking tiles q and q + 32.  Fetched kStages items ahead into
 // registers, stored into the stage's shared slot once that stage is free.
+// The fetch also keeps where the item lies (p, and m, its member in a batch)
+// for its staging.
 struct FlagRegs {
     int f[2], o[2];
+    ItemRef p;
+    int m;
 };
 template <int W, typename Items>
 __device__ __forceinline__ void fetch_flags(const Items& it, long long item, int lane, FlagRegs& r) {
     constexpr int NF = W / 32;
     r.f[0] = r.f[1] = r.o[0] = r.o[1] = 0;
-    ItemRef p;
-    const LbArgs& A = it.locate(item, p);
+    const LbArgs& A = it.locate(item, r.p, r.m);
+    const ItemRef p = r.p;
     if (A.flags == nullptr) return;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -448,7 +462,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
         // segment k - kStages that used the same stage; its tile flags were
         // fetched three segments ahead (their latency stays off the producer's path)
         FlagRegs r0, r1, r2;
-        r0 = r1 = r2 = FlagRegs{{0, 0}, {0, 0}};
+        r0 = r1 = r2 = FlagRegs{{0, 0}, {0, 0}, {0, 0}, 0};
         if (my_n > 0) fetch_flags<W>(it, first, lane, r0);
         if (my_n > 1) fetch_flags<W>(it, first + stride, lane, r1);
         if (my_n > 2) fetch_flags<W>(it, first + 2 * stride, lane, r2);
@@ -465,7 +479,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
             if (stop) break;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             keep_flags(r0, lane, &s_fm[stage]);
-            it.stage_args(item, stage, lane);
+            it.stage_args(r0.p, r0.m, stage, lane);
             __syncwarp();
             const LbArgs& A = it.staged(stage);
             const ItemRef p = it.staged_pos(item, stage);
@@ -549,10 +563,10 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
     // warp 0 (all lanes): stage the k-th item of this CTA into stage k % kStages
     // (its arguments and position, then lane 0 the expected bytes, then lanes
     // 0-8 the copies of one direction each)
-    auto issue = [&](int k) {
+    auto issue = [&](int k, const FlagRegs& r) {
         const long long item = first + (long long)k * stride;
         const int stage = k % kStages;
-        it.stage_args(item, stage, lane);
+        it.stage_args(r.p, r.m, stage, lane);
         __syncwarp();
         const LbArgs& A = it.staged(stage);
         const ItemRef p = it.staged_pos(item, stage);
@@ -568,7 +582,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
             FlagRegs r;
             fetch_flags<W>(it, first + (long long)k * stride, lane, r);
             keep_flags(r, lane, &s_fm[k]);
-            issue(k);
+            issue(k, r);
         }
     }
     __syncthreads();
@@ -578,7 +592,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
     for (; k < my_n; ++k) {
         const int stage = k % kStages;
         // warp 0 fetches the flags of the item it stages at the end of this one
-        FlagRegs nf{{0, 0}, {0, 0}};
+        FlagRegs nf{{0, 0}, {0, 0}, {0, 0}, 0};
         if (warp == 0 && k + kStages < my_n) fetch_flags<W>(it, first + (long long)(k + kStages) * stride, lane, nf);
 
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((k / kStages) & 1));
@@ -596,7 +610,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         if (bad) break;
         if (warp == 0 && k + kStages < my_n) {
             keep_flags(nf, lane, &s_fm[stage]);
-            issue(k + kStages);
+            issue(k + kStages, nf);
         }
     }
     if (bad && tid == 0) {
