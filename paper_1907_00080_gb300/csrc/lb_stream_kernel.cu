@@ -140,7 +140,7 @@ struct OneLattice {
         return a;
     }
     __device__ const LbArgs& locate(long long item, ItemRef& p) const {
-        int m;
+        int m = 0;
         return locate(item, p, m);
     }
     // the staging warp (all lanes) prepares a stage for the item located as
@@ -158,14 +158,16 @@ struct ManyLattices {
     LbArgs* s_args;  // [kStages] in shared memory
     ItemRef* s_pos;  // [kStages]
     __device__ long long count() const { return b.off[b.n]; }
+    // m: on entry a member at or before the item's (a CTA's items ascend:
+    // its previous item's member), on return the item's member
     __device__ const LbArgs& locate(long long item, ItemRef& p, int& m) const {
-        m = batch_member(b.off, b.n, (int)item);
+        while (m + 1 < b.n && b.off[m + 1] <= (int)item) ++m;
         const int l = (int)item - b.off[m], ns = b.tiles_x[m];
         p = {l / ns, (l % ns) * W};
         return b.a[m];
     }
     __device__ const LbArgs& locate(long long item, ItemRef& p) const {
-        int m;
+        int m = batch_member(b.off, b.n, (int)item);
         return locate(item, p, m);
     }
     // the staging warp (all lanes) copies the arguments of member m, 8-byte
@@ -192,10 +194,12 @@ struct FlagRegs {
     ItemRef p;
     int m;
 };
+// (hint: a member at or before the item's, e.g. the CTA's previous item's)
 template <int W, typename Items>
-__device__ __forceinline__ void fetch_flags(const Items& it, long long item, int lane, FlagRegs& r) {
+__device__ __forceinline__ void fetch_flags(const Items& it, long long item, int lane, FlagRegs& r, int hint) {
     constexpr int NF = W / 32;
     r.f[0] = r.f[1] = r.o[0] = r.o[1] = 0;
+    r.m = hint;
     const LbArgs& A = it.locate(item, r.p, r.m);
     const ItemRef p = r.p;
     if (A.flags == nullptr) return;
@@ -463,9 +467,9 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
         // fetched three segments ahead (their latency stays off the producer's path)
         FlagRegs r0, r1, r2;
         r0 = r1 = r2 = FlagRegs{{0, 0}, {0, 0}, {0, 0}, 0};
-        if (my_n > 0) fetch_flags<W>(it, first, lane, r0);
-        if (my_n > 1) fetch_flags<W>(it, first + stride, lane, r1);
-        if (my_n > 2) fetch_flags<W>(it, first + 2 * stride, lane, r2);
+        if (my_n > 0) fetch_flags<W>(it, first, lane, r0, 0);
+        if (my_n > 1) fetch_flags<W>(it, first + stride, lane, r1, r0.m);
+        if (my_n > 2) fetch_flags<W>(it, first + 2 * stride, lane, r2, r1.m);
         for (int k = 0; k < my_n; ++k) {
             const int stage = k % kStages;
             const long long item = first + (long long)k * stride;
@@ -490,7 +494,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
             if (lane == 0) s_last_issued[stage] = k;
             r0 = r1;
             r1 = r2;
-            if (k + 3 < my_n) fetch_flags<W>(it, first + (long long)(k + 3) * stride, lane, r2);
+            if (k + 3 < my_n) fetch_flags<W>(it, first + (long long)(k + 3) * stride, lane, r2, r1.m);
         }
     } else {
         // ---- consumers
@@ -577,10 +581,12 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         if (lane < 9) stage_rows<S, NPT, WALLS>(A, p, smem0 + stage * Gm::STAGE_BYTES, bar, lane, 9);
     };
 
+    // (the member hint stays 0: this schedule serves single lattices, whose
+    // items have no member to search)
     if (warp == 0) {
         for (int k = 0; k < kStages && k < my_n; ++k) {
             FlagRegs r;
-            fetch_flags<W>(it, first + (long long)k * stride, lane, r);
+            fetch_flags<W>(it, first + (long long)k * stride, lane, r, 0);
             keep_flags(r, lane, &s_fm[k]);
             issue(k, r);
         }
@@ -593,7 +599,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         const int stage = k % kStages;
         // warp 0 fetches the flags of the item it stages at the end of this one
         FlagRegs nf{{0, 0}, {0, 0}, {0, 0}, 0};
-        if (warp == 0 && k + kStages < my_n) fetch_flags<W>(it, first + (long long)(k + kStages) * stride, lane, nf);
+        if (warp == 0 && k + kStages < my_n) fetch_flags<W>(it, first + (long long)(k + kStages) * stride, lane, nf, 0);
 
         const bool ok = mbar_wait(smem_addr(&bars[stage]), (uint32_t)((k / kStages) & 1));
         const long long item = first + (long long)k * stride;
