@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kAdvThreads) k_advance(const MarkerArgs a) {
 template <typename C, bool DYN>
 __global__ void __launch_bounds__(kAdvThreads) k_advance_batch(const __grid_constant__ MarkerBatch b) {
     __shared__ MarkerArgs s_a;
-    const int m = batch_member(b.off, b.n, blockIdx.x);
+    const int m = marker_member(b, blockIdx.x);
     stage_args(&s_a, b.args + m);
     advance_unit<C, DYN>(s_a, blockIdx.x - b.off[m], (unsigned)s_a.nau);
 }

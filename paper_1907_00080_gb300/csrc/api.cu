@@ -1407,6 +1407,10 @@ static lbib_status ensemble_batch_tables(lbib_ensemble* e, int ngroups) {
             lb.off[lb.n] = kb;
             fb.off[fb.n] = fu;
             ab.off[ab.n] = au;
+            for (MarkerBatch* mb : {&fb, &ab})
+                for (int k = 0; k < mb->n; ++k)
+                    for (int blk = mb->off[k]; blk < mb->off[k + 1] && blk < kBlockTable; ++blk)
+                        mb->member[blk] = (unsigned char)k;
         }
     }
     const lbib_ctx* c0 = e->m[0];

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kForceThreads) k_forces(const MarkerArgs a) {
 template <typename C>
 __global__ void __launch_bounds__(kForceThreads, 3) k_forces_batch(const __grid_constant__ MarkerBatch b) {
     __shared__ MarkerArgs s_a;
-    const int m = batch_member(b.off, b.n, blockIdx.x);
+    const int m = marker_member(b, blockIdx.x);
     stage_args(&s_a, b.args + m);
     forces_unit<C>(s_a, blockIdx.x - b.off[m]);
 }

@@ -274,11 +274,19 @@ struct LbBatch {
     LbArgs a[kBatchMax];
 };
 // marker kernels: the members' arguments (744 B each) stay in global memory
+// block -> member for the first kBlockTable blocks of a launch (one parameter
+// load where a search over off[] would take several dependent ones)
+constexpr int kBlockTable = 8192;
+static_assert(kBatchMax <= 255, "members fit the byte table");
 struct MarkerBatch {
     int n;
     int off[kBatchMax + 1];     // first block of each member's units
     const MarkerArgs* args;     // [n]
+    unsigned char member[kBlockTable];  // member of block b < min(off[n], kBlockTable)
 };
+__device__ __forceinline__ int marker_member(const MarkerBatch& b, int blk) {
+    return blk < kBlockTable ? (int)b.member[blk] : batch_member(b.off, b.n, blk);
+}
 
 // ---------------------------------------------------------------- launchers
 // lb_kernels.cu
