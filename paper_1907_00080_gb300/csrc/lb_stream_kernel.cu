@@ -424,10 +424,11 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
     }
 }
 
-// Producer-warp schedule (16-bit storage): 288 threads.  Warps 0-7 consume
-// (collide the staged segment; they leave each segment together through named
-// barrier 1), warp 8 produces: lane 0 waits for the stage's "empty" barrier
-// (one arrival once the consumers have passed the segment), the lanes store
+// Producer-warp schedule (16-bit storage, batches): 288 threads.  Warps 0-7
+// consume (collide the staged segment; each frees the stage for its part with
+// its own arrival on the stage's "empty" barrier), warp 8 produces: lane 0
+// waits for that barrier (eight arrivals once the consumers have passed the
+// segment), the lanes store
 // the segment's tile flags, lane 0 sets the expected bytes, then lanes 0-8
 // each issue the copies of one direction.  Stage s also has a "full" barrier
 // (the producer's expect-tx plus the copies' bytes).  Issuing from nine lanes
@@ -452,7 +453,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_addr(&bars[s]), 1);
-            mbar_init(smem_addr(&empty[s]), 1);
+            mbar_init(smem_addr(&empty[s]), kConsumerWarps);
             s_last_issued[s] = -1;
         }
         s_abort = 0;
@@ -510,20 +511,14 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
                 const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
                 consume<S, NPT, WALLS>(A, p, sp, j0, flag_of(s_fm[stage], j0 >> 5), flag_other_of(s_fm[stage], j0 >> 5));
             }
-            // the consumer warps leave the segment together (named barrier 1):
-            // their stores go out as one burst per segment; one arrival frees the stage
-            uint32_t any_bad;
-            asm volatile(
-                "{\n .reg .pred p, q;\n setp.eq.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n"
-                " selp.u32 %0, 1, 0, q;\n}"
-                : "=r"(any_bad)
-                : "r"((uint32_t)ok), "r"(kThreads)
-                : "memory");
-            if (any_bad) {
-                if (tid == 0) s_abort = 1;
+            // each consumer warp frees its share of the stage as soon as it is
+            // done with it (the stage's empty barrier counts the eight warps)
+            if (!ok) {
+                if ((tid & 31) == 0) s_abort = 1;
                 break;
             }
-            if (tid == 0) mbar_arrive(smem_addr(&empty[stage]));
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(smem_addr(&empty[stage]));
         }
     }
     __syncthreads();
