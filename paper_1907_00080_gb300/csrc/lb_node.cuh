@@ -87,6 +87,18 @@ template <> struct LbConst<float> {
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }  // = 1.0f / x, correctly rounded
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// 1 / rho in collide_node and collide_node_scaled.  In FP32 these serve only
+// 16-bit storage, whose stored values are rounded to 2^-11 (FP16) or 2^-8
+// (BF16) relative: there the hardware approximate reciprocal (PTX
+// rcp.approx.ftz.f32, at most 1 ulp of error, 2^-23 relative) is used, which
+// takes fewer instructions than the correctly rounded one.  Every form of a
+// 16-bit run calls it, so the forms still give the same bits.
+template <typename C> __device__ __forceinline__ C recip_node(C x) { return recip(x); }
+template <> __device__ __forceinline__ float recip_node<float>(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // One node: f holds the pulled deviations d_i = f_i - w_i; G the total force
 // (body force plus spread IB force).  Returns the post-collision deviations
@@ -106,7 +118,7 @@ __device__ __forceinline__ void collide_node(const C (&f)[9], C Gx, C Gy, C om, 
     const C jx = (f[1] - f[3]) + ((f[5] - f[7]) + (f[8] - f[6]));
     const C jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
     const C rho = C(1) + drho;
-    const C rinv = recip(rho);
+    const C rinv = recip_node(rho);
     const C ux = (jx + C(0.5) * Gx) * rinv;
     const C uy = (jy + C(0.5) * Gy) * rinv;
     rho_o = rho;
@@ -150,7 +162,7 @@ __device__ __forceinline__ void collide_node_scaled(const float (&s)[9], float G
     const float jx = ((s[1] - s[3]) + ((s[5] - s[7]) + (s[8] - s[6]))) * inv;
     const float jy = ((s[2] - s[4]) + ((s[5] - s[7]) + (s[6] - s[8]))) * inv;
     const float rho = 1.0f + drho;
-    const float rinv = recip(rho);
+    const float rinv = recip_node(rho);
     const float ux = (jx + 0.5f * Gx) * rinv;
     const float uy = (jy + 0.5f * Gy) * rinv;
     rho_o = rho;

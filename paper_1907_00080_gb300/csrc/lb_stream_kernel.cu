@@ -117,7 +117,8 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned
 // Where the items (row segments) of the work list lie, and the arguments of
 // the lattice each belongs to.  locate() is valid at any time; staged(st)
 // is the copy the staging thread made into stage st (for one lattice, the
-// kernel's own parameters).
+// kernel's own parameters), and staged_pos(st) the position of the item it
+// staged there.
 struct ItemRef {
     int y, x0;
 };
@@ -127,7 +128,8 @@ struct OneLattice {
     static constexpr int W = Geom<S, NPT>::W;
     const LbArgs& a;
     int nseg;
-    __device__ explicit OneLattice(const LbArgs& a_) : a(a_), nseg((a_.nx + W - 1) / W) {}
+    ItemRef* s_pos;  // [kStages] in shared memory
+    __device__ OneLattice(const LbArgs& a_, ItemRef* sp) : a(a_), nseg((a_.nx + W - 1) / W), s_pos(sp) {}
     __device__ long long count() const { return (long long)a.ny * nseg; }
     // (32-bit: the launch refuses work lists of 2^31 items or more)
     __device__ ItemRef pos(long long item) const {
@@ -144,10 +146,13 @@ struct OneLattice {
         return locate(item, p, m);
     }
     // the staging warp (all lanes) prepares a stage for the item located as
-    // (p, m): nothing to copy
-    __device__ void stage_args(ItemRef, int, int, int) const {}
+    // (p, m): lane 0 keeps its position in the stage's slot, so that the
+    // consumer threads need no division per segment
+    __device__ void stage_args(ItemRef p, int, int st, int lane) const {
+        if (lane == 0) s_pos[st] = p;
+    }
     __device__ const LbArgs& staged(int) const { return a; }
-    __device__ ItemRef staged_pos(long long item, int) const { return pos(item); }
+    __device__ ItemRef staged_pos(long long, int st) const { return s_pos[st]; }
 };
 
 // b.off: first item of each member; b.tiles_x: segments per row of each member
@@ -302,8 +307,13 @@ __device__ __forceinline__ S stored(typename Storage<S>::C c, float scl) {
 // One thread's NPT nodes of a staged segment: pull from the stage, add the
 // spread force where its tile is flagged, collide, store; write u where
 // flagged; clear the other parity's force where its tile was flagged (and the
-// flag, by the thread at the tile's first node).
-template <typename S, int NPT, bool WALLS>
+// flag, by the thread at the tile's first node).  Three forms, chosen per warp
+// (see consume_warp), with the same arithmetic per node: EDGE, a row next to a
+// wall (bounce-back pulls and the Zou-He rebuild checked per direction);
+// otherwise FORCED, a warp with a flagged force tile among its own, or neither,
+// where the body force is the only force and the collision's force terms are
+// the same for every node.
+template <typename S, int NPT, bool WALLS, bool FORCED, bool EDGE>
 __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp, int j0, int flag, int flag_o) {
     using C = typename Storage<S>::C;
     using Gm = Geom<S, NPT>;
@@ -324,7 +334,7 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
     C f[9][NPT];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const bool bb = WALLS && (y - cy(i) < 0 || y - cy(i) >= ny);
+        const bool bb = WALLS && EDGE && (y - cy(i) < 0 || y - cy(i) >= ny);
         const S* rp = sp + i * Gm::ROW + H + j0;
         const Vec<S, NPT> v = *reinterpret_cast<const Vec<S, NPT>*>(rp);
         // the thread's NPT staged values of this direction in the compute type
@@ -369,7 +379,7 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
         C Gx = LbConst<C>::gx(A), Gy = LbConst<C>::gy(A);
-        if (flag) {
+        if (FORCED && flag) {
             const longlong2 g = A.gsum[node0 + q];
             Gx += from_fix<C>(g.x);
             Gy += from_fix<C>(g.y);
@@ -378,7 +388,7 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
 #pragma unroll
         for (int i = 0; i < 9; ++i) fq[i] = f[i][q];
         // Zou-He wall rows: the populations from outside rebuilt
-        const bool zh = WALLS && A.zou_he && (y == 0 || y == ny - 1);
+        const bool zh = WALLS && EDGE && A.zou_he && (y == 0 || y == ny - 1);
         if constexpr (kHalf) {
             if (zh) {
                 // on the unscaled deviations, then back to the stored scale (exact)
@@ -411,7 +421,7 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];
-    if (flag) {
+    if (FORCED && flag) {
         // velocity for the interpolation to the markers (Sec. 2.3)
         *reinterpret_cast<Vec<C, NPT>*>(static_cast<C*>(A.ux) + node0) = pu;
         *reinterpret_cast<Vec<C, NPT>*>(static_cast<C*>(A.uy) + node0) = pv;
@@ -422,6 +432,27 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
         // the tile's flag was fetched kStages segments ago; nothing reads it again
         if (((p.x0 + j0) & 31) == 0) A.flags_other[(long long)y * A.tiles_x + ((p.x0 + j0) >> 5)] = 0;
     }
+}
+
+// A consumer warp's part of a staged segment (the threads with nodes in it):
+// with SPLIT, the form of consume for the warp, from the segment's row and the
+// flags of the NPT force tiles the warp covers (tiles warp * NPT .. + NPT - 1,
+// all in one word of the stage's masks), a choice uniform over the warp;
+// without, the general form for every warp (the barrier schedule: on the
+// FP32 probe the three forms took 7% longer there, for 13% fewer
+// instructions, while the producer-warp kernels gained).
+template <typename S, int NPT, bool WALLS, bool SPLIT>
+__device__ __forceinline__ void consume_warp(const LbArgs& A, ItemRef p, const S* sp, int tid, const uint4& fm) {
+    static_assert(32 % NPT == 0, "a warp's tiles lie in one mask word");
+    const int j0 = tid * NPT, q0 = (tid >> 5) * NPT;
+    const int flag = flag_of(fm, j0 >> 5), flag_o = flag_other_of(fm, j0 >> 5);
+    const unsigned warp_tiles = ((q0 < 32 ? fm.x : fm.y) >> (q0 & 31)) & ((1u << NPT) - 1u);
+    if (!SPLIT || (WALLS && (p.y == 0 || p.y == A.ny - 1)))
+        consume<S, NPT, WALLS, true, true>(A, p, sp, j0, flag, flag_o);
+    else if (warp_tiles != 0u)
+        consume<S, NPT, WALLS, true, false>(A, p, sp, j0, flag, flag_o);
+    else
+        consume<S, NPT, WALLS, false, false>(A, p, sp, j0, flag, flag_o);
 }
 
 // Producer-warp schedule (16-bit storage, batches): 288 threads.  Warps 0-7
@@ -509,7 +540,7 @@ __device__ __forceinline__ void stream_ws(const Items& it) {
             const int j0 = tid * NPT;
             if (ok && j0 < wlen) {
                 const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
-                consume<S, NPT, WALLS>(A, p, sp, j0, flag_of(s_fm[stage], j0 >> 5), flag_other_of(s_fm[stage], j0 >> 5));
+                consume_warp<S, NPT, WALLS, true>(A, p, sp, tid, s_fm[stage]);
             }
             // each consumer warp frees its share of the stage as soon as it is
             // done with it (the stage's empty barrier counts the eight warps)
@@ -604,7 +635,7 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
         const int j0 = tid * NPT;
         if (j0 < wlen) {
             const S* sp = reinterpret_cast<const S*>(smem + stage * Gm::STAGE_BYTES);
-            consume<S, NPT, WALLS>(A, p, sp, j0, flag_of(s_fm[stage], j0 >> 5), flag_other_of(s_fm[stage], j0 >> 5));
+            consume_warp<S, NPT, WALLS, false>(A, p, sp, tid, s_fm[stage]);
         }
         // every thread is done with this stage (and every wait ended) before it is refilled
         bad = __syncthreads_or(!ok) != 0;
@@ -625,20 +656,27 @@ __device__ __forceinline__ void stream_bar(const Items& it) {
 }
 
 // ---------------------------------------------------------------- kernels
-// (three CTAs per SM where their stages fit in shared memory: registers for
-// three 288-thread CTAs)
+// (the producer-warp kernels are bounded to the registers of as many CTAs per
+// SM as their stages fit in shared memory, at most four)
+constexpr int ctas_per_sm(int smem) {
+    const int c = (220 * 1024) / smem;
+    return c > 4 ? 4 : (c < 1 ? 1 : c);
+}
 template <typename S, int NPT, bool WALLS>
-__global__ void __launch_bounds__(kBlock, 3 * Geom<S, NPT>::SMEM <= 220 * 1024 ? 3 : 1) k_lb_stream_ws(const LbArgs a) {
-    stream_ws<S, NPT, WALLS>(OneLattice<S, NPT>(a));
+__global__ void __launch_bounds__(kBlock, ctas_per_sm(Geom<S, NPT>::SMEM)) k_lb_stream_ws(const LbArgs a) {
+    __shared__ ItemRef s_pos[kStages];
+    stream_ws<S, NPT, WALLS>(OneLattice<S, NPT>(a, s_pos));
 }
 template <typename S, int NPT, bool WALLS>
 __global__ void __launch_bounds__(kThreads) k_lb_stream_bar(const LbArgs a) {
-    stream_bar<S, NPT, WALLS>(OneLattice<S, NPT>(a));
+    __shared__ ItemRef s_pos[kStages];
+    stream_bar<S, NPT, WALLS>(OneLattice<S, NPT>(a, s_pos));
 }
 // batched: the segments of up to kBatchMax lattices (b.off: first item of each
 // member, b.tiles_x: its segments per row)
 template <typename S, int NPT, bool WALLS>
-__global__ void __launch_bounds__(kBlock) k_lb_stream_ws_batch(const __grid_constant__ LbBatch b) {
+__global__ void __launch_bounds__(kBlock, ctas_per_sm(Geom<S, NPT>::SMEM))
+    k_lb_stream_ws_batch(const __grid_constant__ LbBatch b) {
     __shared__ LbArgs s_args[kStages];
     __shared__ ItemRef s_pos[kStages];
     stream_ws<S, NPT, WALLS>(ManyLattices<S, NPT>{b, s_args, s_pos});
