@@ -105,6 +105,18 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity) {
     }
     return false;
 }
+// a population store marked streaming (st.global.cs: evict first in the
+// caches).  The 16-bit kernels store this way: FP16 probe 59.5 -> 55.7 us per
+// 8192 x 1024 launch (a buffer of 151 MB, about the L2), unchanged at 8192 x
+// 2048; the same stores slowed FP32 (97.7 -> 104.3 us), and an evict-first
+// policy on the bulk loads helped neither.
+template <typename V>
+__device__ __forceinline__ void st_stream(V* p, const V& v) {
+    static_assert(sizeof(V) == 4 || sizeof(V) == 8 || sizeof(V) == 16, "vector stores of 4, 8 or 16 bytes");
+    if constexpr (sizeof(V) == 4) __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&v));
+    else if constexpr (sizeof(V) == 8) __stcs(reinterpret_cast<uint2*>(p), *reinterpret_cast<const uint2*>(&v));
+    else __stcs(reinterpret_cast<uint4*>(p), *reinterpret_cast<const uint4*>(&v));
+}
 // global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, unsigned bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -420,7 +432,11 @@ __device__ __forceinline__ void consume(const LbArgs& A, ItemRef p, const S* sp,
         }
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) *reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0) = o[i];
+    for (int i = 0; i < 9; ++i) {
+        Vec<S, NPT>* d = reinterpret_cast<Vec<S, NPT>*>(dst + (size_t)i * N + node0);
+        if constexpr (kHalf) st_stream(d, o[i]);
+        else *d = o[i];
+    }
     if (FORCED && flag) {
         // velocity for the interpolation to the markers (Sec. 2.3)
         *reinterpret_cast<Vec<C, NPT>*>(static_cast<C*>(A.ux) + node0) = pu;
